@@ -1,0 +1,211 @@
+"""FP64 CPU oracle of the radiation step (test infrastructure).
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may
+import this package.  It shares no code with the CUDA path: rt_oracle.c is
+a plain loop nest written from the paper's equations; this module only
+marshals numpy arrays into it.  It takes every input from the caller (a
+problem object with mesh, angles, gas and cell fields) and imports nothing
+from the product package.
+"""
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rt_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ORC_OK, ORC_ERR_NONCONV, ORC_ERR_NONFINITE = 0, -6, -7
+
+
+def build(force=False):
+    """Compile rt_oracle.c (plain C, OpenMP over cells, no FMA contraction so
+    that x86 and Arm hosts give the same bits)."""
+    with _lock:
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+            tmp = _LIB + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off",
+                                   "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int64), ("n_faces", ctypes.c_int64),
+                ("n_angles", ctypes.c_int32), ("newton_max_iter", ctypes.c_int32),
+                ("cell_volume", ctypes.c_void_p), ("face_cells", ctypes.c_void_p),
+                ("face_area", ctypes.c_void_p), ("face_normal", ctypes.c_void_p),
+                ("face_w", ctypes.c_void_p), ("cell_face_ptr", ctypes.c_void_p),
+                ("cell_face_idx", ctypes.c_void_p), ("dir", ctypes.c_void_p),
+                ("wt", ctypes.c_void_p),
+                ("cbar", ctypes.c_double), ("c", ctypes.c_double), ("a_rad", ctypes.c_double),
+                ("gamma_gas", ctypes.c_double), ("r_gas", ctypes.c_double),
+                ("rho", ctypes.c_void_p), ("kappa_P", ctypes.c_void_p),
+                ("kappa_J", ctypes.c_void_p), ("kappa_s", ctypes.c_void_p),
+                ("kind", ctypes.c_void_p), ("tau", ctypes.c_void_p),
+                ("emit_rate", ctypes.c_void_p), ("I_src", ctypes.c_void_p),
+                ("bc_row", ctypes.c_void_p), ("I0", ctypes.c_void_p)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        P = ctypes.POINTER(_Problem)
+        vp, d, i = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+        L.orc_transport.argtypes = [P, d, vp, vp]
+        L.orc_moments.argtypes = [P, vp, vp, vp, vp]
+        L.orc_newton.argtypes = [d, d, d, i, ctypes.POINTER(d), ctypes.POINTER(i)]
+        L.orc_newton.restype = i
+        L.orc_ferrari.argtypes = [d, d, d]
+        L.orc_ferrari.restype = d
+        L.orc_source.argtypes = [P, d, vp, vp, vp, vp, vp, ctypes.POINTER(i)]
+        L.orc_source.restype = i
+        L.orc_step.argtypes = [P, d, vp, vp, vp, vp, vp, ctypes.POINTER(i)]
+        L.orc_step.restype = i
+        L.orc_cfl_dt.argtypes = [P, d]
+        L.orc_cfl_dt.restype = d
+        L.orc_positivity.argtypes = [P]
+        L.orc_positivity.restype = d
+        L.orc_totals.argtypes = [P, vp, vp, vp, vp, vp]
+        _lib = L
+    return _lib
+
+
+def _f64(x, shape=None):
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def newton(alpha, beta, g, max_iter=64):
+    """Positive root of alpha T^4 + beta T = g by the oracle's Newton."""
+    T, it = ctypes.c_double(), ctypes.c_int()
+    st = lib().orc_newton(float(alpha), float(beta), float(g), int(max_iter), ctypes.byref(T),
+                          ctypes.byref(it))
+    return st, T.value, it.value
+
+
+def ferrari(alpha, beta, g):
+    return lib().orc_ferrari(float(alpha), float(beta), float(g))
+
+
+class Oracle:
+    """Oracle state for one problem: intensities I[N][A], gas e[N], m[N][3]
+    and the boundary / emitter tallies ext[N][4], all float64, in the
+    caller's cell numbering."""
+
+    def __init__(self, prob, newton_max_iter=64, threads=None):
+        if threads is not None:
+            os.environ["OMP_NUM_THREADS"] = str(int(threads))
+        m = prob.mesh
+        self.prob = prob
+        self.N, self.A = m.n_cells, int(prob.dirs.shape[0])
+        keep = self._keep = {}
+
+        def arr(name, x, dt=np.float64):
+            a = np.ascontiguousarray(np.asarray(x, dtype=dt))
+            keep[name] = a
+            return a.ctypes.data
+
+        p = _Problem()
+        p.n_cells, p.n_faces, p.n_angles = self.N, m.n_faces, self.A
+        p.newton_max_iter = newton_max_iter
+        p.cell_volume = arr("vol", m.cell_volume)
+        p.face_cells = arr("fc", m.face_cells, np.int32)
+        p.face_area = arr("fa", m.face_area)
+        p.face_normal = arr("fn", m.face_normal)
+        fw = m.face_w if m.face_w is not None else np.zeros((m.n_faces, 3))
+        p.face_w = arr("fw", fw)
+        p.cell_face_ptr = arr("ptr", m.cell_face_ptr, np.int64)
+        p.cell_face_idx = arr("idx", m.cell_face_idx, np.int32)
+        p.dir = arr("dir", prob.dirs)
+        p.wt = arr("wt", prob.weights)
+        p.cbar, p.c, p.a_rad = prob.cbar, prob.c, prob.a_rad
+        p.gamma_gas, p.r_gas = prob.gamma_gas, prob.r_gas
+        p.rho = arr("rho", prob.rho)
+        p.kappa_P = arr("kP", prob.kappa_P)
+        p.kappa_J = arr("kJ", prob.kappa_J)
+        p.kappa_s = arr("kS", prob.kappa_s)
+        p.kind = arr("kind", prob.kind, np.uint8)
+        p.tau = arr("tau", prob.tau)
+        p.emit_rate = arr("emit", prob.emit_rate)
+        p.I_src = arr("isrc", prob.I_src)
+        p.bc_row = arr("bcrow", prob.bc_row, np.int32)
+        p.I0 = arr("I0", prob.I0)
+        self.p = p
+        self.I = _f64(prob.initial_intensity(np.float64))
+        self.e = _f64(prob.e).copy()
+        self.m = _f64(prob.m).copy()
+        self.ext = np.zeros((self.N, 4))
+        self.work = np.empty_like(self.I)
+        self.last_iters = 0
+
+    # -- single operators ------------------------------------------------
+    def transport(self, dt, I=None):
+        I = self.I if I is None else _f64(I)
+        out = np.empty_like(I)
+        lib().orc_transport(ctypes.byref(self.p), float(dt), I.ctypes.data, out.ctypes.data)
+        return out
+
+    def source(self, dt, Istar):
+        Istar = _f64(Istar)
+        out = np.empty_like(Istar)
+        it = ctypes.c_int()
+        st = lib().orc_source(ctypes.byref(self.p), float(dt), Istar.ctypes.data, out.ctypes.data,
+                              self.e.ctypes.data, self.m.ctypes.data, self.ext.ctypes.data,
+                              ctypes.byref(it))
+        self.last_iters = it.value
+        return st, out
+
+    # -- full steps ----------------------------------------------------------
+    def step(self, dt):
+        it = ctypes.c_int()
+        st = lib().orc_step(ctypes.byref(self.p), float(dt), self.I.ctypes.data,
+                            self.work.ctypes.data, self.e.ctypes.data, self.m.ctypes.data,
+                            self.ext.ctypes.data, ctypes.byref(it))
+        self.last_iters = it.value
+        return st
+
+    def run(self, n_steps, dt):
+        for _ in range(int(n_steps)):
+            st = self.step(dt)
+            if st != ORC_OK:
+                return st
+        return ORC_OK
+
+    # -- diagnostics -----------------------------------------------------------
+    def moments(self, I=None):
+        I = self.I if I is None else _f64(I)
+        E = np.empty(self.N)
+        F = np.empty((self.N, 3))
+        P = np.empty((self.N, 6))
+        lib().orc_moments(ctypes.byref(self.p), I.ctypes.data, E.ctypes.data, F.ctypes.data,
+                          P.ctypes.data)
+        return E, F, P
+
+    def totals(self):
+        out = np.empty(16)
+        lib().orc_totals(ctypes.byref(self.p), self.I.ctypes.data, self.e.ctypes.data,
+                         self.m.ctypes.data, self.ext.ctypes.data, out.ctypes.data)
+        return out
+
+    def cfl_dt(self, cfl=None):
+        cfl = self.prob.cfl if cfl is None else cfl
+        return lib().orc_cfl_dt(ctypes.byref(self.p), float(cfl))
+
+    def positivity(self):
+        return lib().orc_positivity(ctypes.byref(self.p))
+
+    def temperature(self):
+        """Gas temperature from the conserved gas state."""
+        pr = self.prob
+        kin = 0.5 * np.sum(self.m ** 2, axis=1) / pr.rho
+        return (self.e - kin) * (pr.gamma_gas - 1.0) / (pr.rho * pr.r_gas)

@@ -1,0 +1,467 @@
+/*
+ * FP64 CPU oracle of the reduced-speed-of-light radiation step on a Voronoi
+ * mesh (Chang, Davis & Jiang, "Time dependent radiation hydrodynamics on a
+ * moving mesh").
+ *
+ * TEST INFRASTRUCTURE.  Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg may load this library.  It shares no code with the CUDA
+ * path: it is a plain loop nest written from the paper's equations, in the
+ * order the paper gives them, in double precision.
+ *
+ * Units and readings (the paper leaves these open; see the notes per
+ * function): intensities are stored as energy density per steradian, so an
+ * isotropic equilibrium field has I = a T^4 / (4 pi); E_r = 4 pi sum_a w_a I_a,
+ * F_r = 4 pi c sum_a w_a n_a I_a; the weights sum to one.  The frame velocity
+ * of a cell is v = (rho v) / rho at the start of the source step, and the
+ * Lorentz factor is taken to first order in v/c (gamma = 1).
+ *
+ * Every function below is pinned by the CPU tests against something other
+ * than itself: closed forms, conservation invariants, brute force on tiny
+ * inputs, an mpmath root, and the paper's worked example (Sec. 4.1).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_ERR_NONCONV (-6)
+#define ORC_ERR_NONFINITE (-7)
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+typedef struct {
+  int64_t n_cells, n_faces;
+  int32_t n_angles;
+  int32_t newton_max_iter;
+  /* mesh (Sec. 2, finite-volume charges; Sec. 3.2 transport) */
+  const double *cell_volume;  /* [N] */
+  const int32_t *face_cells;  /* [Nf][2] */
+  const double *face_area;    /* [Nf] */
+  const double *face_normal;  /* [Nf][3], unit, i -> j */
+  const double *face_w;       /* [Nf][3] face velocity, may be NULL */
+  const int64_t *cell_face_ptr; /* [N+1] */
+  const int32_t *cell_face_idx; /* [nnz]: f (first cell) or -(f+1) (second) */
+  const double *dir;          /* [A][3] */
+  const double *wt;           /* [A], sum 1 */
+  /* constants */
+  double cbar, c, a_rad, gamma_gas, r_gas;
+  /* gas, per cell (Sec. 3.3) */
+  const double *rho, *kappa_P, *kappa_J, *kappa_s;
+  /* boundary / emitter cells (Sec. 3.5, 3.6) */
+  const uint8_t *kind;        /* 0 interior, 1 boundary, 2 emitter */
+  const double *tau;          /* [N] */
+  const double *emit_rate;    /* [N] rho kappa of the emitter */
+  const double *I_src;        /* [N] */
+  const int32_t *bc_row;      /* [N] */
+  const double *I0;           /* [rows][A] */
+} orc_problem;
+
+/* ------------------------------------------------------------------------
+ * Transport, Sec. 3.2 with the finite-volume update of Eq. (time evolution):
+ * the flux through a face moving with velocity w is (cbar n_a - w) . n_f A I
+ * and takes I from the upwind side.  Outward flux leaves the cell:
+ *   I*_ca = I_ca - dt / V_c * sum_{f in cell c} u_fa I_up,
+ *   u_fa = cbar A_f n_a . n_f - A_f w_f . n_f   (n_f outward from c),
+ *   I_up = I_ca if u_fa > 0, I_(nbr,a) if u_fa < 0, no flux if u_fa = 0.
+ * Faces are visited in the order of the cell's face list.
+ * --------------------------------------------------------------------- */
+static inline void face_side(const orc_problem *p, int64_t c, int32_t e, int64_t *f,
+                             double *sgn, int64_t *nbr) {
+  if (e >= 0) {
+    *f = e;
+    *sgn = 1.0;
+    *nbr = p->face_cells[2 * (int64_t)e + 1];
+  } else {
+    *f = -(int64_t)e - 1;
+    *sgn = -1.0;
+    *nbr = p->face_cells[2 * (*f)];
+  }
+  (void)c;
+}
+
+void orc_transport(const orc_problem *p, double dt, const double *I, double *Istar) {
+  const int A = p->n_angles;
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < p->n_cells; ++c) {
+    for (int a = 0; a < A; ++a) {
+      const double *na = p->dir + 3 * a;
+      double acc = 0.0;
+      for (int64_t k = p->cell_face_ptr[c]; k < p->cell_face_ptr[c + 1]; ++k) {
+        int64_t f, nbr;
+        double sgn;
+        face_side(p, c, p->cell_face_idx[k], &f, &sgn, &nbr);
+        const double *nf = p->face_normal + 3 * f;
+        double area = p->face_area[f];
+        double ndotn = sgn * (na[0] * nf[0] + na[1] * nf[1] + na[2] * nf[2]);
+        double wdotn = 0.0;
+        if (p->face_w) {
+          const double *w = p->face_w + 3 * f;
+          wdotn = sgn * (w[0] * nf[0] + w[1] * nf[1] + w[2] * nf[2]);
+        }
+        double u = p->cbar * area * ndotn - area * wdotn;
+        if (u > 0.0)
+          acc += u * I[c * A + a];
+        else if (u < 0.0)
+          acc += u * I[nbr * A + a];
+      }
+      Istar[c * A + a] = I[c * A + a] - dt / p->cell_volume[c] * acc;
+    }
+  }
+}
+
+/* Lab-frame moments, Eqs. (moments energy) and (moments flux), with the
+ * pressure tensor of Sec. 3.1: E = 4 pi sum w I, F = 4 pi c sum w n I,
+ * P = 4 pi sum w n n I (xx, yy, zz, xy, xz, yz). */
+static void cell_moments(const orc_problem *p, const double *Ic, double *E, double *F) {
+  double e = 0, fx = 0, fy = 0, fz = 0;
+  for (int a = 0; a < p->n_angles; ++a) {
+    double wi = p->wt[a] * Ic[a];
+    e += wi;
+    fx += wi * p->dir[3 * a];
+    fy += wi * p->dir[3 * a + 1];
+    fz += wi * p->dir[3 * a + 2];
+  }
+  *E = 4.0 * M_PI * e;
+  F[0] = 4.0 * M_PI * p->c * fx;
+  F[1] = 4.0 * M_PI * p->c * fy;
+  F[2] = 4.0 * M_PI * p->c * fz;
+}
+
+void orc_moments(const orc_problem *p, const double *I, double *E, double *F, double *P) {
+  const int A = p->n_angles;
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < p->n_cells; ++c) {
+    const double *Ic = I + c * A;
+    double f3[3];
+    cell_moments(p, Ic, &E[c], f3);
+    if (F) {
+      F[3 * c] = f3[0];
+      F[3 * c + 1] = f3[1];
+      F[3 * c + 2] = f3[2];
+    }
+    if (P) {
+      double s[6] = {0, 0, 0, 0, 0, 0};
+      for (int a = 0; a < A; ++a) {
+        const double *n = p->dir + 3 * a;
+        double wi = p->wt[a] * Ic[a];
+        s[0] += wi * n[0] * n[0];
+        s[1] += wi * n[1] * n[1];
+        s[2] += wi * n[2] * n[2];
+        s[3] += wi * n[0] * n[1];
+        s[4] += wi * n[0] * n[2];
+        s[5] += wi * n[1] * n[2];
+      }
+      for (int k = 0; k < 6; ++k) P[6 * c + k] = 4.0 * M_PI * s[k];
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------
+ * Gas temperature after the implicit step: the unique positive root of
+ *   alpha T^4 + beta T - g = 0,  alpha >= 0, beta > 0, g >= 0,
+ * which Eq. (com rad thermal disc) becomes once Eq. (Jcom) eliminates J.
+ * Newton from T0 = min(g / beta, (g / alpha)^(1/4)), where f(T0) >= 0; f is
+ * increasing and convex on T > 0, so the iterates decrease monotonically to
+ * the root.  Stops when an iterate fails to decrease or moves by at most
+ * 1e-15 of itself.
+ * --------------------------------------------------------------------- */
+int orc_newton(double alpha, double beta, double g, int max_iter, double *T_out,
+               int *iters_out) {
+  if (!(alpha >= 0.0) || !(beta > 0.0) || !(g >= 0.0)) return ORC_ERR_NONFINITE;
+  double T = g / beta;
+  if (alpha > 0.0) {
+    double t4 = sqrt(sqrt(g / alpha));
+    if (t4 < T) T = t4;
+  }
+  int it = 0, done = 0;
+  while (!done && it < max_iter) {
+    double T2 = T * T;
+    double f = alpha * T2 * T2 + beta * T - g;
+    double fp = 4.0 * alpha * T2 * T + beta;
+    double Tn = T - f / fp;
+    ++it;
+    if (!(Tn < T)) {
+      done = 1;
+    } else {
+      done = (T - Tn <= 1e-15 * T);
+      T = Tn;
+    }
+  }
+  if (iters_out) *iters_out = it;
+  *T_out = T;
+  if (!isfinite(T)) return ORC_ERR_NONFINITE;
+  if (!done) return ORC_ERR_NONCONV;
+  return ORC_OK;
+}
+
+/* The same root in closed form (Sec. 3.3 solves the temperature-independent
+ * case analytically), by Ferrari's method: with p = beta/alpha, q = g/alpha,
+ * T^4 + p T - q = 0 is rewritten (T^2 + y)^2 = 2y (T - p/(4y))^2 where y > 0
+ * solves the resolvent cubic y^3 + q y - p^2/8 = 0, so the positive root
+ * solves T^2 + sqrt(2y) T + y - p / (2 sqrt(2y)) = 0.  Used only as an
+ * independent cross-check of the Newton root. */
+double orc_ferrari(double alpha, double beta, double g) {
+  if (alpha <= 0.0) return g / beta;
+  if (g <= 0.0) return 0.0;
+  double p = beta / alpha, q = g / alpha;
+  double r = p * p / 8.0;
+  /* y^3 + q y - r = 0 has a single real root (q > 0); Cardano */
+  double disc = sqrt(r * r / 4.0 + q * q * q / 27.0);
+  double u = cbrt(r / 2.0 + disc);
+  /* second Cardano term -q/(3u) written as the conjugate product form */
+  double y = u - q / (3.0 * u);
+  if (y <= 0.0) {
+    /* fall back: Newton on the cubic from the Cardano estimate */
+    y = cbrt(r);
+  }
+  for (int k = 0; k < 3; ++k) {
+    double fy = (y * y + q) * y - r;
+    double fpy = 3.0 * y * y + q;
+    y -= fy / fpy;
+  }
+  double s2 = sqrt(2.0 * y);
+  double d = -2.0 * y + 2.0 * p / s2;
+  double sd = sqrt(d > 0 ? d : 0.0);
+  /* T = (-s2 + sd) / 2 = (d - s2^2) / (2 (sd + s2)) */
+  return (d - 2.0 * y) / (2.0 * (sd + s2));
+}
+
+/* ------------------------------------------------------------------------
+ * Implicit source step of one cell, Sec. 3.3, the four-step algorithm:
+ *  1. E^n, F^n of the post-transport intensities (Eqs. moments);
+ *  2. to the comoving frame: Gamma_a = 1 - v . n_a / c,
+ *     I~_a = Gamma_a^4 I_a (Eq. I lab to com), w~_a = N w_a / Gamma_a^2,
+ *     sum w~ = 1; the angular sums of Eq. (Jcom) with rho kept:
+ *        x_a = dt cbar rho (kJ + ks) Gamma_a,
+ *        S_I = sum w~_a I~_a / (1 + x_a),  S_G = sum w~_a Gamma_a / (1 + x_a),
+ *        J~ = (S_I + dt cbar rho kP (a T^4 / 4pi) S_G) / D,
+ *        D  = 1 - dt cbar rho ks S_G;
+ *     eliminating J~ from Eq. (com rad thermal disc) leaves
+ *        alpha T^4 + beta T = g,
+ *        alpha = dt c rho kP a (1 - dt cbar rho kJ S_G / D),
+ *        beta  = rho c_v,  c_v = R / (gamma - 1),
+ *        g     = rho c_v T^n + dt c rho 4 pi kJ S_I / D;
+ *  3. I~^{n+1} from Eq. (com radiative source disc), back to the lab frame;
+ *  4. E^{n+1}, F^{n+1} and the gas exchange of Eqs. (gas1), (gas2):
+ *        e += (c / cbar)(E^n - E^{n+1}),  rho v += (F^n - F^{n+1}) / (c cbar).
+ * The gas temperature is recomputed from the updated energy next step.
+ * --------------------------------------------------------------------- */
+static int source_interior(const orc_problem *p, int64_t c, double dt, const double *Is,
+                           double *In, double *e, double *m, int *iters) {
+  const int A = p->n_angles;
+  const double rho = p->rho[c], kP = p->kappa_P[c], kJ = p->kappa_J[c], kS = p->kappa_s[c];
+  double En, Fn[3];
+  cell_moments(p, Is, &En, Fn);
+  double v[3] = {m[0] / rho, m[1] / rho, m[2] / rho};
+  double G[A], wc[A], Ic[A];
+  double norm = 0.0;
+  for (int a = 0; a < A; ++a) {
+    const double *n = p->dir + 3 * a;
+    G[a] = 1.0 - (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / p->c;
+    double G2 = G[a] * G[a];
+    Ic[a] = G2 * G2 * Is[a];
+    wc[a] = p->wt[a] / G2;
+    norm += wc[a];
+  }
+  double SI = 0.0, SG = 0.0;
+  for (int a = 0; a < A; ++a) {
+    wc[a] /= norm;
+    double xa = dt * p->cbar * rho * (kJ + kS) * G[a];
+    SI += wc[a] * Ic[a] / (1.0 + xa);
+    SG += wc[a] * G[a] / (1.0 + xa);
+  }
+  double D = 1.0 - dt * p->cbar * rho * kS * SG;
+  double kin = 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) / rho;
+  double rcv = rho * p->r_gas / (p->gamma_gas - 1.0);
+  double Tn = (*e - kin) / rcv;
+  double alpha = dt * p->c * rho * kP * p->a_rad * (1.0 - dt * p->cbar * rho * kJ * SG / D);
+  double beta = rcv;
+  double g = rcv * Tn + dt * p->c * rho * 4.0 * M_PI * kJ * SI / D;
+  double T;
+  int st = orc_newton(alpha, beta, g, p->newton_max_iter, &T, iters);
+  if (st != ORC_OK) return st;
+  double B = p->a_rad * T * T * T * T / (4.0 * M_PI);
+  double J = (SI + dt * p->cbar * rho * kP * B * SG) / D;
+  for (int a = 0; a < A; ++a) {
+    double xa = dt * p->cbar * rho * (kJ + kS) * G[a];
+    double Inew = (Ic[a] + dt * p->cbar * G[a] * rho * (kP * B + kS * J)) / (1.0 + xa);
+    double G2 = G[a] * G[a];
+    In[a] = Inew / (G2 * G2);
+  }
+  double E1, F1[3];
+  cell_moments(p, In, &E1, F1);
+  *e += p->c / p->cbar * (En - E1);
+  for (int k = 0; k < 3; ++k) m[k] += (Fn[k] - F1[k]) / (p->c * p->cbar);
+  return ORC_OK;
+}
+
+/* Boundary cells, Sec. 3.5: I relaxes to I0 with factor min(dt / tau, 1)
+ * (tau <= dt pins I = I0).  The gas of a boundary cell is held fixed; the
+ * energy and momentum the radiation loses go to an external tally. */
+static void source_boundary(const orc_problem *p, int64_t c, double dt, const double *Is,
+                            double *In, double *ext) {
+  const int A = p->n_angles;
+  double f = (p->tau[c] <= dt) ? 1.0 : dt / p->tau[c];
+  const double *I0 = p->I0 + (int64_t)p->bc_row[c] * A;
+  double En, Fn[3], E1, F1[3];
+  cell_moments(p, Is, &En, Fn);
+  for (int a = 0; a < A; ++a) In[a] = Is[a] - (Is[a] - I0[a]) * f;
+  cell_moments(p, In, &E1, F1);
+  ext[0] += p->c / p->cbar * (En - E1);
+  for (int k = 0; k < 3; ++k) ext[1 + k] += (Fn[k] - F1[k]) / (p->c * p->cbar);
+}
+
+/* Emitter cells, Sec. 3.6: in the comoving frame I~ relaxes implicitly to
+ * I_src at rate Gamma_a cbar (rho kappa)_src:
+ *   I~^{n+1} = (I~ + y_a I_src) / (1 + y_a),  y_a = dt cbar Gamma_a emit_rate.
+ * The emitter's gas is a fixed reservoir; the exchange goes to the tally. */
+static void source_emitter(const orc_problem *p, int64_t c, double dt, const double *Is,
+                           double *In, const double *m, double *ext) {
+  const int A = p->n_angles;
+  const double rho = p->rho[c];
+  double v[3] = {m[0] / rho, m[1] / rho, m[2] / rho};
+  double En, Fn[3], E1, F1[3];
+  cell_moments(p, Is, &En, Fn);
+  for (int a = 0; a < A; ++a) {
+    const double *n = p->dir + 3 * a;
+    double G = 1.0 - (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / p->c;
+    double G4 = G * G * G * G;
+    double y = dt * p->cbar * G * p->emit_rate[c];
+    In[a] = ((G4 * Is[a] + y * p->I_src[c]) / (1.0 + y)) / G4;
+  }
+  cell_moments(p, In, &E1, F1);
+  ext[0] += p->c / p->cbar * (En - E1);
+  for (int k = 0; k < 3; ++k) ext[1 + k] += (Fn[k] - F1[k]) / (p->c * p->cbar);
+}
+
+/* Source step over all cells.  e[N], m[N][3], ext[N][4] are updated in
+ * place; Inew may not alias Istar.  Returns the first error met (in cell
+ * order) and stores the largest Newton iteration count. */
+int orc_source(const orc_problem *p, double dt, const double *Istar, double *Inew, double *e,
+               double *m, double *ext, int *max_iters) {
+  const int A = p->n_angles;
+  int status = ORC_OK;
+  int64_t first_bad = -1;
+  int itmax = 0;
+#pragma omp parallel for schedule(static) reduction(max : itmax)
+  for (int64_t c = 0; c < p->n_cells; ++c) {
+    const double *Is = Istar + c * A;
+    double *In = Inew + c * A;
+    int k = p->kind ? p->kind[c] : 0;
+    int it = 0, st = ORC_OK;
+    if (k == 1)
+      source_boundary(p, c, dt, Is, In, ext + 4 * c);
+    else if (k == 2)
+      source_emitter(p, c, dt, Is, In, m + 3 * c, ext + 4 * c);
+    else
+      st = source_interior(p, c, dt, Is, In, e + c, m + 3 * c, &it);
+    if (it > itmax) itmax = it;
+    for (int a = 0; a < A && st == ORC_OK; ++a)
+      if (!isfinite(In[a])) st = ORC_ERR_NONFINITE;
+    if (st != ORC_OK) {
+#pragma omp critical
+      {
+        if (first_bad < 0 || c < first_bad) {
+          first_bad = c;
+          status = st;
+        }
+      }
+    }
+  }
+  if (max_iters) *max_iters = itmax;
+  return status;
+}
+
+/* One full step: transport over dt, then the implicit source over dt
+ * (operator split, forward-Euler transport).  I is replaced by I^{n+1};
+ * work[N*A] is scratch. */
+int orc_step(const orc_problem *p, double dt, double *I, double *work, double *e, double *m,
+             double *ext, int *max_iters) {
+  orc_transport(p, dt, I, work);
+  return orc_source(p, dt, work, I, e, m, ext, max_iters);
+}
+
+/* Courant time step: dt = cfl * min_c V_c^(1/3) / (cbar + max_f |w_f|). */
+double orc_cfl_dt(const orc_problem *p, double cfl) {
+  double best = INFINITY;
+  for (int64_t c = 0; c < p->n_cells; ++c) {
+    double wmax = 0.0;
+    if (p->face_w)
+      for (int64_t k = p->cell_face_ptr[c]; k < p->cell_face_ptr[c + 1]; ++k) {
+        int32_t e = p->cell_face_idx[k];
+        int64_t f = e >= 0 ? e : -(int64_t)e - 1;
+        const double *w = p->face_w + 3 * f;
+        double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        if (wn > wmax) wmax = wn;
+      }
+    double d = cbrt(p->cell_volume[c]) / (p->cbar + wmax);
+    if (d < best) best = d;
+  }
+  return cfl * best;
+}
+
+/* Positivity of the upwind update: I*_ca keeps a non-negative weight on
+ * I_ca iff dt * K_ca <= 1 with K_ca = (1 / V_c) sum_f max(u_fa, 0).
+ * Returns max over cells and angles of K_ca. */
+double orc_positivity(const orc_problem *p) {
+  const int A = p->n_angles;
+  double kmax = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : kmax)
+  for (int64_t c = 0; c < p->n_cells; ++c) {
+    for (int a = 0; a < A; ++a) {
+      const double *na = p->dir + 3 * a;
+      double s = 0.0;
+      for (int64_t k = p->cell_face_ptr[c]; k < p->cell_face_ptr[c + 1]; ++k) {
+        int64_t f, nbr;
+        double sgn;
+        face_side(p, c, p->cell_face_idx[k], &f, &sgn, &nbr);
+        const double *nf = p->face_normal + 3 * f;
+        double area = p->face_area[f];
+        double ndotn = sgn * (na[0] * nf[0] + na[1] * nf[1] + na[2] * nf[2]);
+        double wdotn = 0.0;
+        if (p->face_w) {
+          const double *w = p->face_w + 3 * f;
+          wdotn = sgn * (w[0] * nf[0] + w[1] * nf[1] + w[2] * nf[2]);
+        }
+        double u = p->cbar * area * ndotn - area * wdotn;
+        if (u > 0.0) s += u;
+      }
+      s /= p->cell_volume[c];
+      if (s > kmax) kmax = s;
+    }
+  }
+  return kmax;
+}
+
+/* Conserved totals (Sec. 3.4): with E_g the gas energy and the radiation
+ * weighted by c / cbar, E_g + (c/cbar) E_r and rho v + F_r / (c cbar) are
+ * conserved; the tallies of boundary / emitter cells close the budget.
+ * out[0..2]  sum V e, sum V (c/cbar) E_r, sum V ext_e
+ * out[3..5]  sum V rho v
+ * out[6..8]  sum V F_r / (c cbar)
+ * out[9..11] sum V ext_m
+ * out[12]    out[0] + out[1] + out[2]
+ * out[13..15] total momentum.  Plain sums in cell order. */
+void orc_totals(const orc_problem *p, const double *I, const double *e, const double *m,
+                const double *ext, double *out) {
+  const int A = p->n_angles;
+  for (int k = 0; k < 16; ++k) out[k] = 0.0;
+  for (int64_t c = 0; c < p->n_cells; ++c) {
+    double V = p->cell_volume[c];
+    double E, F[3];
+    cell_moments(p, I + c * A, &E, F);
+    out[0] += V * e[c];
+    out[1] += V * (p->c / p->cbar) * E;
+    out[2] += ext ? V * ext[4 * c] : 0.0;
+    for (int k = 0; k < 3; ++k) {
+      out[3 + k] += V * m[3 * c + k];
+      out[6 + k] += V * F[k] / (p->c * p->cbar);
+      out[9 + k] += ext ? V * ext[4 * c + 1 + k] : 0.0;
+    }
+  }
+  out[12] = out[0] + out[1] + out[2];
+  for (int k = 0; k < 3; ++k) out[13 + k] = out[3 + k] + out[6 + k] + out[9 + k];
+}

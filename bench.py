@@ -1,0 +1,344 @@
+"""Throughput of the radiation step (transport + implicit source) on GB300.
+
+Workload: the shadows / crossing-beams box at full size: 128^3 jittered
+periodic Voronoi cells, 80 discrete ordinates, three opaque spheres, four
+emitter cells, absorbing boundary layers and two collimated beams (seeded,
+synthetic).  One "step" is one rt_step: the fused transport + source kernel
+over every cell and angle.  Reported: cell-angle updates/s of the FP32 path
+(headline) and of the FP64 path, each against the HBM roofline of its
+algorithmic bytes; an end-to-end figure through the C ABI with host
+buffers; and the CPU oracle timed on this host's cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload on its own GPU (the step has no cross-GPU exchange here); the
+value is the sum over ranks divided by the slowest rank's time.
+"""
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-angle updates/s (transport+implicit source), FP32 vs FP64, % HBM roofline"
+UNIT = "cell-angle updates/s"
+
+# DRAM bytes per launch of the FP32 step kernel from one ncu capture of the
+# full workload, valid while the kernel source has the recorded hash.
+NCU_TRAFFIC = {"fp32": None, "fp64": None}
+NCU_SOURCE_SHA = None
+
+
+def kernel_source_sha():
+    p = os.path.join(ROOT, "paper_2002_08377_gb300", "csrc", "rt_step.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def algorithmic_bytes(n_cells, n_faces, n_angles, real_bytes):
+    """Bytes the method must move per step: one read and one write of every
+    intensity, the per-cell gas state (V, rho, kappa_P, kappa_J, kappa_s, e,
+    m, v read: 72 B; e, m written: 32 B) and every undirected face once
+    (two int32 cell ids, A n (3 reals), A w.n (1 real))."""
+    return n_cells * (2 * real_bytes * n_angles + 104) + n_faces * (8 + 4 * real_bytes)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """SM clock and clock-event reasons during the timed region, via NVML
+    (read-only queries) every few milliseconds."""
+    REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks", 0x4: "sw_power_cap",
+               0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, index=0, period=0.005):
+        self.ok = False
+        self.samples = []
+        self.reasons = 0
+        self.period = period
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            assert nv.nvmlInit_v2() == 0
+            h = ctypes.c_void_p()
+            assert nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(h)) == 0
+            mx = ctypes.c_uint()
+            nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))  # NVML_CLOCK_SM = 1
+            self.nv, self.h, self.max_mhz = nv, h, mx.value
+            fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+            self.reason_fn = fn
+            self.ok = True
+        except Exception:
+            self.max_mhz = None
+
+    def _loop(self):
+        clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            if self.nv.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(clk)) == 0:
+                self.samples.append(clk.value)
+            if self.reason_fn(self.h, ctypes.byref(rs)) == 0:
+                self.reasons |= rs.value
+            time.sleep(self.period)
+
+    def __enter__(self):
+        if self.ok:
+            self._stop = threading.Event()
+            self._t = threading.Thread(target=self._loop, daemon=True)
+            self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        if self.ok:
+            self._stop.set()
+            self._t.join()
+
+    def summary(self):
+        if not self.ok or not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unavailable"]}
+        names = [n for bit, n in self.REASONS.items() if self.reasons & bit and n != "gpu_idle"]
+        return {"sm_mhz": float(statistics.median(self.samples)), "sm_max_mhz": self.max_mhz,
+                "samples": len(self.samples), "reasons": names}
+
+
+# ---------------------------------------------------------------- distributed
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- workload
+def make_workload():
+    from paper_2002_08377_gb300.inputs import shadows
+    return shadows()
+
+
+def describe(prob):
+    return {"workload": "shadows/crossing-beams box: 128^3 jittered periodic Voronoi cells, "
+                        "80 level-symmetric angles, 3 opaque spheres, 4 emitters, absorbing "
+                        "layers, 2 beams, cbar = c = 1e3",
+            "cells": prob.n_cells, "angles": prob.n_angles, "faces": prob.mesh.n_faces,
+            "directed_faces_per_cell": round(2 * prob.mesh.n_faces / prob.n_cells, 3),
+            "l2": "inputs larger than L2 (FP32 intensities 2 x 671 MB + face slots)"}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_oracle_rate(prob, dt, budget_s, max_cells=None):
+    """Cell-angle updates/s of the FP64 oracle (OpenMP over all host cores)
+    on contiguous cell ranges of the same workload until budget_s passes."""
+    import oracle
+    o = oracle.Oracle(prob)
+    N, A = prob.n_cells, prob.n_angles
+    chunk = N if max_cells is None else min(N, max_cells)
+    done, t0 = 0, time.perf_counter()
+    out = np.empty_like(o.I)
+    c0 = 0
+    while True:
+        c1 = min(N, c0 + chunk)
+        o.sample_step(dt, c0, c1, out)
+        done += (c1 - c0) * A
+        c0 = 0 if c1 >= N else c1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return done / el, done, el
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    prob = make_workload()
+    dt = prob.cfl_dt()
+    import oracle
+    o = oracle.Oracle(prob)
+    N, A = prob.n_cells, prob.n_angles
+    sample = max(1, N // 16)  # each step: one sixteenth of the cells
+    out = np.empty_like(o.I)
+    for _ in range(args.warmup):
+        o.sample_step(dt, 0, sample, out)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        c0 = (k * sample) % N
+        o.sample_step(dt, c0, min(N, c0 + sample), out)
+    el = time.perf_counter() - t0
+    v = sample * A * args.steps / el
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": describe(prob),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"cells [c0, c0+{sample}) of one step per timed step "
+                                       f"(1/16 of the {N}-cell, {A}-angle workload)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def time_steps(sol, dt, steps, warmup, world, sampler=None):
+    import torch
+    for _ in range(warmup):
+        sol.step(dt)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stream = sol.stream
+    l0 = sol.launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    ctx = sampler if sampler is not None else _Null()
+    with ctx:
+        ev0.record(stream)
+        sol.launch(steps, dt)  # back-to-back launches on the solver's stream
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    sol.sync()  # latched per-cell status of the timed steps
+    barrier(world)
+    launches = sol.launch_count() - l0
+    ms = ev0.elapsed_time(ev1)
+    return max_over_ranks(ms, world), launches
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        pass
+
+
+def e2e_rate(sol, prob, dt, steps):
+    """Through the C ABI with pinned host buffers: every step copies the
+    intensities in, runs the step and copies them out."""
+    import torch
+    N, A = prob.n_cells, prob.n_angles
+    host_in = torch.empty((N, A), dtype=torch.float32, pin_memory=True)
+    host_in.numpy()[:] = prob.initial_intensity(np.float32)
+    host_out = torch.empty((N, A), dtype=torch.float32, pin_memory=True)
+    lib, st = sol.lib, sol.state
+    pin, pout = ctypes.c_void_p(host_in.data_ptr()), ctypes.c_void_p(host_out.data_ptr())
+    used = ctypes.c_double()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sol._check(lib.rt_set_intensity(st, pin, 0))
+        sol._check(lib.rt_step(st, dt, ctypes.byref(used)))
+        sol._check(lib.rt_get_intensity(st, pout, 0))
+    el = time.perf_counter() - t0
+    nbytes = N * A * 4
+    return N * A * steps / el, nbytes, nbytes
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2002_08377_gb300 import build as rtbuild
+    from paper_2002_08377_gb300.solver import RTSolver
+    rtbuild.build()
+
+    prob = make_workload()
+    N, A, Nf = prob.n_cells, prob.n_angles, prob.mesh.n_faces
+    dt = prob.cfl_dt()
+    hbm_peak, peak_kind = measured_peaks()
+    results = {}
+    sampler = ClockSampler(index=0)
+    for prec in ("fp32", "fp64"):
+        sol = RTSolver.from_problem(prob, prec)
+        steps = args.steps if prec == "fp32" else max(3, args.steps // 5)
+        ms, launches = time_steps(sol, dt, steps, max(3, args.warmup), world,
+                                  sampler if prec == "fp32" else None)
+        per = ms / steps
+        rb = 4 if prec == "fp32" else 8
+        B = algorithmic_bytes(N, Nf, A, rb)
+        achieved = B / (per * 1e-3) / 1e9
+        traffic = NCU_TRAFFIC.get(prec) if NCU_SOURCE_SHA == kernel_source_sha() else None
+        results[prec] = {
+            "value": N * A * steps * world / (ms * 1e-3), "ms_per_step": per, "steps": steps,
+            "launches": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": B,
+                         "peak_source": f"{peak_kind} HBM copy bandwidth"}}
+        if prec == "fp32":
+            e2e_v, bi, bo = e2e_rate(sol, prob, dt, max(3, min(10, args.steps)))
+            results["e2e"] = {"value": e2e_v * world, "unit": UNIT, "h2d_bytes_per_step": bi,
+                              "d2h_bytes_per_step": bo}
+        sol.close()
+        del sol
+        torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, done, el = cpu_oracle_rate(prob, dt, args.cpu_budget)
+        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{done} cell-angle updates of the FP64 oracle on this workload "
+                         f"({el:.1f} s, whole steps of {N} cells x {A} angles)"}
+    r32 = results["fp32"]
+    line = {"metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": world,
+            "steps": r32["steps"], "warmup": max(3, args.warmup), "ms_per_step": r32["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": describe(prob), "roofline": r32["roofline"],
+            "cpu_baseline": cpu, "e2e": results["e2e"], "gpu_launches": r32["launches"],
+            "clocks": sampler.summary(),
+            "fp64": {"value": results["fp64"]["value"], "ms_per_step": results["fp64"]["ms_per_step"],
+                     "steps": results["fp64"]["steps"], "dtype": "f64",
+                     "roofline": results["fp64"]["roofline"],
+                     "fp32_over_fp64": r32["value"] / results["fp64"]["value"]}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

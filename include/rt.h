@@ -1,0 +1,203 @@
+/*
+ * rt.h -- C ABI of the GB300 reduced-speed-of-light radiative-transfer step
+ * on an unstructured (Voronoi) mesh.
+ *
+ * The method is that of Chang, Davis & Jiang, "Time dependent radiation
+ * hydrodynamics on a moving mesh": discrete-ordinate intensities I(cell,
+ * angle) are transported across the mesh faces by an upwind finite-volume
+ * flux (Sec. 3.2) and then updated by an implicit, per-cell source step in
+ * the fluid's comoving frame that solves a quartic for the gas temperature
+ * and returns the energy and momentum exchange to the gas (Sec. 3.3).
+ * Boundary cells relax to a prescribed field (Sec. 3.5) and emitter cells
+ * relax to a source intensity (Sec. 3.6).
+ *
+ * Conventions shared by every call
+ *   - Plain C types only.  Arrays are row-major and, unless a call takes an
+ *     on_device flag that is set, HOST pointers.  Device pointers passed
+ *     with on_device = 1 must be valid on the state's device and are used
+ *     on the state's stream only for the duration of the call.
+ *   - Cells and angles are numbered as the caller numbers them.  The
+ *     library may store cells in another order internally; every input and
+ *     output is converted.
+ *   - Units: intensities are energy density per steradian, so an isotropic
+ *     equilibrium field is I = a_rad T^4 / (4 pi); E_r = 4 pi sum_a w_a I_a,
+ *     F_r = 4 pi c sum_a w_a n_a I_a, P_r = 4 pi sum_a w_a n_a n_a I_a
+ *     (Sec. 3.1 moments with sum_a w_a = 1).  The gas has e = total energy
+ *     density, m = momentum density, ideal-gas temperature
+ *     T = (gamma - 1)(e - |m|^2 / (2 rho)) / (rho r_gas).
+ *   - Every call returns an rt_status.  On failure rt_last_error() gives a
+ *     one-line description.  Per-cell failures inside a step (Newton not
+ *     converged, non-finite values) are latched on the device and returned
+ *     by the call that synchronises (rt_step / rt_run / rt_totals / rt_sync).
+ *   - The library allocates its device memory in rt_create and frees it in
+ *     rt_destroy.  It keeps no pointer to caller memory after a call returns.
+ */
+#ifndef RT_GB300_H
+#define RT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rt_state rt_state;
+
+typedef enum {
+  RT_OK = 0,
+  RT_ERR_ARG = -1,       /* bad argument (null pointer, size, flag)            */
+  RT_ERR_MESH = -2,      /* mesh fails validation (index range, open cell)      */
+  RT_ERR_CUDA = -3,      /* CUDA runtime error                                  */
+  RT_ERR_OOM = -4,       /* device allocation failed                            */
+  RT_ERR_CFL = -5,       /* dt above the upwind positivity limit                */
+  RT_ERR_NONCONV = -6,   /* temperature Newton iteration did not converge       */
+  RT_ERR_NONFINITE = -7, /* non-finite intensity or temperature produced        */
+  RT_ERR_STATE = -8      /* call out of order (e.g. step before rt_set_gas)     */
+} rt_status;
+
+typedef enum {
+  RT_FP64 = 0, /* every quantity in double precision                          */
+  RT_FP32 = 1  /* intensities, face geometry and the transport sweep in float;
+                  the temperature quartic, the gas energy/momentum exchange
+                  and the conservation sums in double                         */
+} rt_precision;
+
+typedef enum {
+  RT_CELL_INTERIOR = 0, /* transport + implicit gas coupling (Sec. 3.3)       */
+  RT_CELL_BOUNDARY = 1, /* I -> I - (I - I0) min(dt/tau, 1) (Sec. 3.5)         */
+  RT_CELL_EMITTER = 2   /* comoving I~ relaxes to I_src at rate cbar*emit_rate
+                           (Sec. 3.6)                                          */
+} rt_cell_kind;
+
+/* Mesh and angle set (Sec. 2: Voronoi cells i with volume V_i, faces with
+ * area A_ij, unit normal n_ij pointing from i to j; Sec. 3.2: face velocity
+ * w_ij).  All pointers are host pointers, copied by rt_create.
+ *   face_cells[f] = (i, j): a face is listed once; i == j is allowed (a cell
+ *     meeting its own periodic image).
+ *   cell_face_ptr/cell_face_idx: CSR over cells; entry f >= 0 means the cell
+ *     is face f's first cell (outward normal +n_f), entry -(f+1) means it is
+ *     the second cell (outward normal -n_f).  The order of a cell's entries is
+ *     the order in which its face fluxes are summed.
+ *   angle_dir[A][3] unit directions, angle_w[A] weights with sum 1.  The set
+ *     must be centrally symmetric in the order angle_dir[a + A/2] =
+ *     -angle_dir[a] (A even); rt_create rejects it otherwise.
+ *   face_w may be NULL (static mesh).  cell_centroid and face_centroid are
+ *     used for the locality ordering only and may be NULL. */
+typedef struct {
+  int64_t n_cells;
+  int64_t n_faces;
+  int32_t n_angles;
+  int32_t reserved;
+  const double *cell_volume;   /* [N]        */
+  const double *cell_centroid; /* [N][3]     */
+  const int32_t *face_cells;   /* [Nf][2]    */
+  const double *face_area;     /* [Nf]       */
+  const double *face_normal;   /* [Nf][3]    */
+  const double *face_centroid; /* [Nf][3]    */
+  const double *face_w;        /* [Nf][3]    */
+  const int64_t *cell_face_ptr;/* [N+1]      */
+  const int32_t *cell_face_idx;/* [nnz]      */
+  const double *angle_dir;     /* [A][3]     */
+  const double *angle_w;       /* [A]        */
+} rt_mesh_desc;
+
+/* Physical constants and numerics (Sec. 3.1, 3.4).  cbar is the reduced
+ * speed of light of the transport, c the true one (enters the gas coupling
+ * and the moments).  r_gas = k_B / (mu m_p); c_v = r_gas / (gamma_gas - 1).
+ * cfl scales the Courant step dt = cfl * min V^(1/3) / (cbar + |w|).
+ * newton_max_iter <= 0 selects 64. */
+typedef struct {
+  double cbar, c, a_rad, gamma_gas, r_gas, cfl;
+  int32_t precision;       /* rt_precision */
+  int32_t newton_max_iter;
+} rt_params;
+
+/* Validates and copies the mesh to the device, orders cells for locality,
+ * builds the per-cell directed face lists (bit-exact negated geometry on the
+ * two sides of every face) and the upwind positivity bound.  stream is a
+ * cudaStream_t (NULL = legacy default stream) on the current device; every
+ * later call runs on it.  On success *out owns all device memory.
+ * Errors: RT_ERR_ARG, RT_ERR_MESH (face index out of range, CSR not
+ * consistent with face_cells, non-positive volume, open cell with
+ * |sum_f A n| > 1e-9 sum_f A), RT_ERR_OOM, RT_ERR_CUDA. */
+int rt_create(const rt_mesh_desc *mesh, const rt_params *params, void *stream,
+              rt_state **out);
+
+/* Gas state per cell (Sec. 3.3): rho, total energy density e, momentum
+ * density m[N][3], Planck / mean / scattering opacities per unit mass.  The
+ * frame velocity of a cell's source step is m / rho.  Host pointers, copied.
+ * Resets the boundary / emitter tallies. */
+int rt_set_gas(rt_state *s, const double *rho, const double *e, const double *m,
+               const double *kappa_P, const double *kappa_J, const double *kappa_s);
+
+/* Cell kinds (rt_cell_kind, [N]).  Boundary cells use tau[N] and the row
+ * bc_row[N] of I0[n_rows][A]; emitter cells use emit_rate[N] (= rho kappa of
+ * the source) and I_src[N].  kind == NULL makes every cell interior (the
+ * other pointers may then be NULL).  Host pointers, copied. */
+int rt_set_cells(rt_state *s, const uint8_t *kind, const double *tau, const double *emit_rate,
+                 const double *I_src, const int32_t *bc_row, int64_t n_rows, const double *I0);
+
+/* Intensities I[N][A] in the state's precision (float for RT_FP32, double
+ * for RT_FP64), caller order.  on_device = 1: I is a device pointer. */
+int rt_set_intensity(rt_state *s, const void *I, int on_device);
+int rt_get_intensity(rt_state *s, void *I, int on_device);
+
+/* Gas output: e[N], m[N][3] and the tallies ext[N][4] (energy and momentum
+ * density handed to boundary and emitter reservoirs, positive = taken from
+ * the radiation).  Any pointer may be NULL.  Double precision. */
+int rt_get_gas(rt_state *s, double *e, double *m, double *ext, int on_device);
+
+/* dt_cfl: the Courant step of rt_params.cfl; dt_max: the largest dt for
+ * which every upwind update keeps a non-negative weight on its own cell,
+ * 1 / max_{c,a} (1/V_c) sum_f max(u_fa, 0).  Either pointer may be NULL. */
+int rt_dt_limits(rt_state *s, double *dt_cfl, double *dt_max);
+
+/* One full step (Sec. 3.2 transport over dt, then the Sec. 3.3 source step
+ * over dt): dt <= 0 selects dt_cfl.  Fails with RT_ERR_CFL if dt > dt_max.
+ * Synchronises the stream and returns the first per-cell failure, if any
+ * (the state then holds the partially failed step). */
+int rt_step(rt_state *s, double dt, double *dt_used);
+
+/* n_steps full steps with the same dt, launched back to back; synchronises
+ * once at the end. */
+int rt_run(rt_state *s, int32_t n_steps, double dt, double *dt_used);
+
+/* Launches n_steps full steps without waiting for them; per-cell failures
+ * are latched and returned by the next synchronising call (rt_sync,
+ * rt_step, rt_run, rt_totals).  dt and the CFL check as for rt_step. */
+int rt_launch(rt_state *s, int32_t n_steps, double dt, double *dt_used);
+
+/* Lab-frame moments (Sec. 3.1 / Eqs. moments energy, moments flux) of the
+ * current intensities, double precision, caller order: E[N], F[N][3],
+ * P[N][6] (xx, yy, zz, xy, xz, yz).  Any pointer may be NULL. */
+int rt_moments(rt_state *s, double *E, double *F, double *P, int on_device);
+
+/* Conserved totals (Sec. 3.4), deterministic double-precision sums, host
+ * output out[16]:
+ *   0 sum V e, 1 sum V (c/cbar) E_r, 2 sum V ext_e,
+ *   3..5 sum V m, 6..8 sum V F_r / (c cbar), 9..11 sum V ext_m,
+ *   12 = 0 + 1 + 2 (conserved), 13..15 = momentum totals (conserved). */
+int rt_totals(rt_state *s, double out[16]);
+
+/* Waits for the state's stream and returns the latched per-cell status. */
+int rt_sync(rt_state *s);
+
+/* Serialises the full evolving state (intensities, gas e and m, tallies) to
+ * a host buffer.  buf == NULL: *bytes receives the size needed. */
+int rt_get_state(rt_state *s, void *buf, size_t *bytes);
+int rt_set_state(rt_state *s, const void *buf, size_t bytes);
+
+/* Device memory used by the state, in bytes. */
+int rt_device_bytes(const rt_state *s, size_t *bytes);
+
+/* Number of kernel launches made by this state since creation. */
+int64_t rt_launch_count(const rt_state *s);
+
+const char *rt_last_error(const rt_state *s);
+void rt_destroy(rt_state *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_GB300_H */

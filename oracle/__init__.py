@@ -74,6 +74,8 @@ def lib():
         L.orc_positivity.argtypes = [P]
         L.orc_positivity.restype = d
         L.orc_totals.argtypes = [P, vp, vp, vp, vp, vp]
+        L.orc_step_range.argtypes = [P, d, vp, vp, vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int64]
+        L.orc_step_range.restype = i
         _lib = L
     return _lib
 
@@ -173,6 +175,16 @@ class Oracle:
                             self.ext.ctypes.data, ctypes.byref(it))
         self.last_iters = it.value
         return st
+
+    def sample_step(self, dt, c0, c1, out=None):
+        """Transport + source of cells [c0, c1) only, into `out` (a timing
+        sample: the state is left unchanged apart from those cells' gas)."""
+        if out is None:
+            out = np.empty_like(self.I)
+        st = lib().orc_step_range(ctypes.byref(self.p), float(dt), self.I.ctypes.data,
+                                  self.work.ctypes.data, out.ctypes.data, self.e.ctypes.data,
+                                  self.m.ctypes.data, self.ext.ctypes.data, int(c0), int(c1))
+        return st, out
 
     def run(self, n_steps, dt):
         for _ in range(int(n_steps)):

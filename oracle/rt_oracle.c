@@ -82,10 +82,12 @@ static inline void face_side(const orc_problem *p, int64_t c, int32_t e, int64_t
   (void)c;
 }
 
-void orc_transport(const orc_problem *p, double dt, const double *I, double *Istar) {
+/* Cells [c0, c1) only; arrays are indexed by global cell number. */
+void orc_transport_range(const orc_problem *p, double dt, const double *I, double *Istar,
+                         int64_t c0, int64_t c1) {
   const int A = p->n_angles;
 #pragma omp parallel for schedule(static)
-  for (int64_t c = 0; c < p->n_cells; ++c) {
+  for (int64_t c = c0; c < c1; ++c) {
     for (int a = 0; a < A; ++a) {
       const double *na = p->dir + 3 * a;
       double acc = 0.0;
@@ -110,6 +112,10 @@ void orc_transport(const orc_problem *p, double dt, const double *I, double *Ist
       Istar[c * A + a] = I[c * A + a] - dt / p->cell_volume[c] * acc;
     }
   }
+}
+
+void orc_transport(const orc_problem *p, double dt, const double *I, double *Istar) {
+  orc_transport_range(p, dt, I, Istar, 0, p->n_cells);
 }
 
 /* Lab-frame moments, Eqs. (moments energy) and (moments flux), with the
@@ -340,14 +346,14 @@ static void source_emitter(const orc_problem *p, int64_t c, double dt, const dou
 /* Source step over all cells.  e[N], m[N][3], ext[N][4] are updated in
  * place; Inew may not alias Istar.  Returns the first error met (in cell
  * order) and stores the largest Newton iteration count. */
-int orc_source(const orc_problem *p, double dt, const double *Istar, double *Inew, double *e,
-               double *m, double *ext, int *max_iters) {
+int orc_source_range(const orc_problem *p, double dt, const double *Istar, double *Inew,
+                     double *e, double *m, double *ext, int *max_iters, int64_t c0, int64_t c1) {
   const int A = p->n_angles;
   int status = ORC_OK;
   int64_t first_bad = -1;
   int itmax = 0;
 #pragma omp parallel for schedule(static) reduction(max : itmax)
-  for (int64_t c = 0; c < p->n_cells; ++c) {
+  for (int64_t c = c0; c < c1; ++c) {
     const double *Is = Istar + c * A;
     double *In = Inew + c * A;
     int k = p->kind ? p->kind[c] : 0;
@@ -373,6 +379,20 @@ int orc_source(const orc_problem *p, double dt, const double *Istar, double *Ine
   }
   if (max_iters) *max_iters = itmax;
   return status;
+}
+
+int orc_source(const orc_problem *p, double dt, const double *Istar, double *Inew, double *e,
+               double *m, double *ext, int *max_iters) {
+  return orc_source_range(p, dt, Istar, Inew, e, m, ext, max_iters, 0, p->n_cells);
+}
+
+/* Transport and source of cells [c0, c1) only, reading I and writing the
+ * new intensities of those cells into Iout (global indexing); a bounded
+ * sample of one step used to time the oracle. */
+int orc_step_range(const orc_problem *p, double dt, const double *I, double *work, double *Iout,
+                   double *e, double *m, double *ext, int64_t c0, int64_t c1) {
+  orc_transport_range(p, dt, I, work, c0, c1);
+  return orc_source_range(p, dt, work, Iout, e, m, ext, NULL, c0, c1);
 }
 
 /* One full step: transport over dt, then the implicit source over dt

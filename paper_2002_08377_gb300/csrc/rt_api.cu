@@ -1,0 +1,640 @@
+// Host side of the C ABI declared in include/rt.h: validation, locality
+// ordering, directed face slots, device buffers and the call sequence.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "rt_internal.cuh"
+
+namespace rt {
+int64_t totals_scratch_len(int64_t n_cells);
+}
+
+namespace {
+
+int fail(rt_state *s, int code, const std::string &msg) {
+  if (s) s->err = msg;
+  return code;
+}
+
+int cuda_fail(rt_state *s, cudaError_t e, const char *what) {
+  return fail(s, e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define RT_CUDA(s, call)                                   \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail((s), e_, #call); \
+  } while (0)
+
+template <typename T> cudaError_t dalloc(rt_state *s, T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+  if (e == cudaSuccess) s->device_bytes += count * sizeof(T);
+  return e;
+}
+
+cudaError_t dalloc_bytes(rt_state *s, void **p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) s->device_bytes += bytes;
+  return e;
+}
+
+// Interleave the bits of a 21-bit integer with two zero bits.
+uint64_t spread3(uint64_t v) {
+  v &= 0x1fffff;
+  v = (v | v << 32) & 0x1f00000000ffffull;
+  v = (v | v << 16) & 0x1f0000ff0000ffull;
+  v = (v | v << 8) & 0x100f00f00f00f00full;
+  v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+  v = (v | v << 2) & 0x1249249249249249ull;
+  return v;
+}
+
+// Locality order: sort cells along a Morton curve of their centroids.
+std::vector<int64_t> morton_order(int64_t n, const double *cen) {
+  std::vector<int64_t> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  if (!cen || n < 2) return order;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t c = 0; c < n; ++c)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], cen[3 * c + d]);
+      hi[d] = std::max(hi[d], cen[3 * c + d]);
+    }
+  std::vector<uint64_t> key(n);
+  for (int64_t c = 0; c < n; ++c) {
+    uint64_t k = 0;
+    for (int d = 0; d < 3; ++d) {
+      double span = hi[d] - lo[d];
+      double t = span > 0 ? (cen[3 * c + d] - lo[d]) / span : 0.0;
+      uint64_t q = (uint64_t)std::min(2097151.0, std::max(0.0, t * 2097151.0));
+      k |= spread3(q) << d;
+    }
+    key[c] = k;
+  }
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int64_t a, int64_t b) { return key[a] < key[b]; });
+  return order;
+}
+
+template <typename R> void fill_geometry(rt_state *s, const rt_mesh_desc *m,
+                                         const std::vector<int64_t> &slot_of,
+                                         std::vector<int64_t> &ptr, std::vector<int32_t> &nbr,
+                                         std::vector<typename rt::SlotOf<R>::type> &slot,
+                                         std::vector<R> &inv_vol) {
+  const int64_t N = m->n_cells;
+  ptr.assign(N + 1, 0);
+  for (int64_t ic = 0; ic < N; ++ic) {
+    int64_t c = s->cell_of[ic];
+    ptr[ic + 1] = ptr[ic] + (m->cell_face_ptr[c + 1] - m->cell_face_ptr[c]);
+  }
+  nbr.resize(ptr[N]);
+  slot.resize(ptr[N]);
+  inv_vol.resize(N);
+  const double cbar = s->params.cbar;
+  for (int64_t ic = 0; ic < N; ++ic) {
+    const int64_t c = s->cell_of[ic];
+    inv_vol[ic] = (R)(1.0 / m->cell_volume[c]);
+    int64_t o = ptr[ic];
+    for (int64_t k = m->cell_face_ptr[c]; k < m->cell_face_ptr[c + 1]; ++k, ++o) {
+      const int32_t e = m->cell_face_idx[k];
+      const int64_t f = e >= 0 ? e : -(int64_t)e - 1;
+      const double sg = e >= 0 ? 1.0 : -1.0;
+      const int64_t other = e >= 0 ? m->face_cells[2 * f + 1] : m->face_cells[2 * f];
+      nbr[o] = (int32_t)slot_of[other];
+      const double A = m->face_area[f];
+      const double *n = m->face_normal + 3 * f;
+      double wn = 0.0;
+      if (m->face_w) {
+        const double *w = m->face_w + 3 * f;
+        wn = w[0] * n[0] + w[1] * n[1] + w[2] * n[2];
+      }
+      // both sides hold exact negatives of the same rounded numbers
+      R sx = (R)(cbar * A * n[0]), sy = (R)(cbar * A * n[1]), sz = (R)(cbar * A * n[2]);
+      R ww = (R)(A * wn);
+      if (sg < 0) {
+        sx = -sx;
+        sy = -sy;
+        sz = -sz;
+        ww = -ww;
+      }
+      slot[o] = {sx, sy, sz, ww};
+    }
+  }
+}
+
+template <typename T> cudaError_t upload(rt_state *s, T **dst, const std::vector<T> &v) {
+  cudaError_t e = dalloc(s, dst, v.size());
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+template <typename R> int build_device_mesh(rt_state *s, const rt_mesh_desc *m,
+                                            const std::vector<int64_t> &slot_of) {
+  std::vector<int64_t> ptr;
+  std::vector<int32_t> nbr;
+  std::vector<typename rt::SlotOf<R>::type> slot;
+  std::vector<R> inv_vol;
+  fill_geometry<R>(s, m, slot_of, ptr, nbr, slot, inv_vol);
+  RT_CUDA(s, upload(s, &s->d_ptr, ptr));
+  RT_CUDA(s, upload(s, &s->d_nbr, nbr));
+  typename rt::SlotOf<R>::type *ds = nullptr;
+  RT_CUDA(s, upload(s, &ds, slot));
+  s->d_slot = ds;
+  R *dv = nullptr;
+  RT_CUDA(s, upload(s, &dv, inv_vol));
+  s->d_inv_vol = dv;
+  const int A = m->n_angles;
+  std::vector<R> dir(4 * (size_t)A), wt(A);
+  for (int a = 0; a < A; ++a) {
+    for (int d = 0; d < 3; ++d) dir[4 * a + d] = (R)m->angle_dir[3 * a + d];
+    dir[4 * a + 3] = 0;
+    wt[a] = (R)m->angle_w[a];
+  }
+  R *dd = nullptr, *dw = nullptr;
+  RT_CUDA(s, upload(s, &dd, dir));
+  RT_CUDA(s, upload(s, &dw, wt));
+  s->d_dir = dd;
+  s->d_wt = dw;
+  return RT_OK;
+}
+
+int check_mesh(rt_state *s, const rt_mesh_desc *m) {
+  const int64_t N = m->n_cells, Nf = m->n_faces;
+  if (N < 1 || N > INT32_MAX || Nf < 0 || m->n_angles < 2 || (m->n_angles & 1))
+    return fail(s, RT_ERR_ARG, "n_cells, n_faces or n_angles out of range (n_angles must be even)");
+  if (m->n_angles > 128) return fail(s, RT_ERR_ARG, "at most 128 angles are supported");
+  if (!m->cell_volume || !m->face_cells || !m->face_area || !m->face_normal ||
+      !m->cell_face_ptr || !m->cell_face_idx || !m->angle_dir || !m->angle_w)
+    return fail(s, RT_ERR_ARG, "required mesh array is NULL");
+  const int A = m->n_angles, H = A / 2;
+  double wsum = 0;
+  for (int a = 0; a < A; ++a) {
+    const double *d = m->angle_dir + 3 * a;
+    if (!(std::fabs(d[0] * d[0] + d[1] * d[1] + d[2] * d[2] - 1.0) < 1e-12))
+      return fail(s, RT_ERR_ARG, "angle directions must be unit vectors");
+    if (!(m->angle_w[a] > 0)) return fail(s, RT_ERR_ARG, "angle weights must be positive");
+    wsum += m->angle_w[a];
+  }
+  if (!(std::fabs(wsum - 1.0) < 1e-12)) return fail(s, RT_ERR_ARG, "angle weights must sum to 1");
+  for (int a = 0; a < H; ++a)
+    for (int d = 0; d < 3; ++d)
+      if (m->angle_dir[3 * (a + H) + d] != -m->angle_dir[3 * a + d])
+        return fail(s, RT_ERR_ARG, "angle set must satisfy dir[a + A/2] == -dir[a]");
+  if (m->cell_face_ptr[0] != 0) return fail(s, RT_ERR_MESH, "cell_face_ptr[0] must be 0");
+  for (int64_t c = 0; c < N; ++c)
+    if (m->cell_face_ptr[c + 1] < m->cell_face_ptr[c])
+      return fail(s, RT_ERR_MESH, "cell_face_ptr must be non-decreasing");
+  const int64_t nnz = m->cell_face_ptr[N];
+  if (nnz != 2 * Nf) return fail(s, RT_ERR_MESH, "CSR must list every face twice");
+  for (int64_t f = 0; f < Nf; ++f) {
+    int32_t i = m->face_cells[2 * f], j = m->face_cells[2 * f + 1];
+    if (i < 0 || i >= N || j < 0 || j >= N) return fail(s, RT_ERR_MESH, "face cell index out of range");
+    if (!(m->face_area[f] >= 0) || !std::isfinite(m->face_area[f]))
+      return fail(s, RT_ERR_MESH, "face areas must be finite and non-negative");
+  }
+  std::vector<uint8_t> seen(2 * (size_t)Nf, 0);
+  std::vector<double> closure(3 * (size_t)N, 0.0), asum(N, 0.0);
+  for (int64_t c = 0; c < N; ++c) {
+    if (!(m->cell_volume[c] > 0) || !std::isfinite(m->cell_volume[c]))
+      return fail(s, RT_ERR_MESH, "cell volumes must be positive");
+    for (int64_t k = m->cell_face_ptr[c]; k < m->cell_face_ptr[c + 1]; ++k) {
+      int32_t e = m->cell_face_idx[k];
+      int64_t f = e >= 0 ? e : -(int64_t)e - 1;
+      if (f >= Nf) return fail(s, RT_ERR_MESH, "cell_face_idx out of range");
+      int side = e >= 0 ? 0 : 1;
+      if (m->face_cells[2 * f + side] != c)
+        return fail(s, RT_ERR_MESH, "cell_face_idx entry does not match face_cells");
+      if (seen[2 * f + side]++) return fail(s, RT_ERR_MESH, "face listed twice on one side");
+      double sg = side ? -1.0 : 1.0, A = m->face_area[f];
+      for (int d = 0; d < 3; ++d) closure[3 * c + d] += sg * A * m->face_normal[3 * f + d];
+      asum[c] += A;
+    }
+  }
+  for (int64_t c = 0; c < N; ++c) {
+    double r = std::sqrt(closure[3 * c] * closure[3 * c] + closure[3 * c + 1] * closure[3 * c + 1] +
+                         closure[3 * c + 2] * closure[3 * c + 2]);
+    if (!(r <= 1e-9 * asum[c])) {
+      char buf[128];
+      snprintf(buf, sizeof buf, "cell %lld is not closed: |sum A n| = %.3g", (long long)c, r);
+      return fail(s, RT_ERR_MESH, buf);
+    }
+  }
+  return RT_OK;
+}
+
+int sync_status(rt_state *s) {
+  RT_CUDA(s, cudaStreamSynchronize(s->stream));
+  unsigned st = 0;
+  unsigned long long bad = 0;
+  RT_CUDA(s, cudaMemcpy(&st, s->d_status, sizeof st, cudaMemcpyDeviceToHost));
+  if (!st) return RT_OK;
+  RT_CUDA(s, cudaMemcpy(&bad, s->d_bad, sizeof bad, cudaMemcpyDeviceToHost));
+  long long cell = bad < (unsigned long long)s->n_cells ? (long long)s->cell_of[bad] : -1;
+  char buf[160];
+  if (st & rt::ST_NONFINITE) {
+    snprintf(buf, sizeof buf, "non-finite intensity or temperature (first cell %lld)", cell);
+    return fail(s, RT_ERR_NONFINITE, buf);
+  }
+  snprintf(buf, sizeof buf, "temperature Newton iteration did not converge (first cell %lld)", cell);
+  return fail(s, RT_ERR_NONCONV, buf);
+}
+
+}  // namespace
+
+extern "C" {
+
+int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state **out) {
+  if (!out) return RT_ERR_ARG;
+  *out = nullptr;
+  if (!m || !p) return RT_ERR_ARG;
+  rt_state *s = new rt_state();
+  int st = RT_OK;
+  auto bail = [&](int code) {
+    rt_destroy(s);
+    return code;
+  };
+  if (!(p->cbar > 0) || !(p->c > 0) || !(p->a_rad >= 0) || !(p->gamma_gas > 1) ||
+      !(p->r_gas > 0) || !(p->cfl > 0) || (p->precision != RT_FP32 && p->precision != RT_FP64))
+    return bail(RT_ERR_ARG);
+  s->params = *p;
+  if (s->params.newton_max_iter <= 0) s->params.newton_max_iter = 64;
+  s->precision = p->precision;
+  s->rsize = p->precision == RT_FP32 ? 4 : 8;
+  s->stream = (cudaStream_t)stream;
+  if ((st = check_mesh(s, m)) != RT_OK) {
+    // keep the message: callers of a failed create cannot query it, so print it
+    fprintf(stderr, "rt_create: %s\n", s->err.c_str());
+    return bail(st);
+  }
+  if (cudaGetDevice(&s->device) != cudaSuccess) return bail(RT_ERR_CUDA);
+  const int64_t N = m->n_cells;
+  const int A = m->n_angles;
+  s->n_cells = N;
+  s->n_faces = m->n_faces;
+  s->nnz = m->cell_face_ptr[N];
+  s->n_angles = A;
+  s->cell_of = morton_order(N, m->cell_centroid);
+  std::vector<int64_t> slot_of(N);
+  for (int64_t ic = 0; ic < N; ++ic) slot_of[s->cell_of[ic]] = ic;
+  s->volume.assign(m->cell_volume, m->cell_volume + N);
+  // Courant step (the paper defers its form to its hydro scheme; this is
+  // dt = cfl * min V^(1/3) / (cbar + max |w| of the cell's faces))
+  double best = INFINITY;
+  for (int64_t c = 0; c < N; ++c) {
+    double wmax = 0;
+    if (m->face_w)
+      for (int64_t k = m->cell_face_ptr[c]; k < m->cell_face_ptr[c + 1]; ++k) {
+        int32_t e = m->cell_face_idx[k];
+        int64_t f = e >= 0 ? e : -(int64_t)e - 1;
+        const double *w = m->face_w + 3 * f;
+        wmax = std::max(wmax, std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]));
+      }
+    best = std::min(best, std::cbrt(m->cell_volume[c]) / (p->cbar + wmax));
+  }
+  s->dt_cfl = p->cfl * best;
+
+  int r = (s->precision == RT_FP32) ? build_device_mesh<float>(s, m, slot_of)
+                                    : build_device_mesh<double>(s, m, slot_of);
+  if (r != RT_OK) return bail(r);
+  std::vector<double> vol_int(N), dir64(3 * (size_t)A), wt64(A);
+  for (int64_t ic = 0; ic < N; ++ic) vol_int[ic] = m->cell_volume[s->cell_of[ic]];
+  std::memcpy(dir64.data(), m->angle_dir, sizeof(double) * 3 * A);
+  std::memcpy(wt64.data(), m->angle_w, sizeof(double) * A);
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return bail(cuda_fail(s, e_, #call)); \
+  } while (0)
+  CK(upload(s, &s->d_cell_of, s->cell_of));
+  CK(upload(s, &s->d_volume, vol_int));
+  CK(upload(s, &s->d_dir64, dir64));
+  CK(upload(s, &s->d_wt64, wt64));
+  CK(dalloc(s, &s->d_gs, N));
+  CK(dalloc(s, &s->d_gd, N));
+  CK(dalloc(s, &s->d_kind, N));
+  CK(dalloc(s, &s->d_aux, N));
+  CK(dalloc(s, &s->d_bc_row, N));
+  CK(dalloc(s, &s->d_ext, 4 * (size_t)N));
+  CK(dalloc(s, &s->d_status, 1));
+  CK(dalloc(s, &s->d_bad, 1));
+  CK(dalloc(s, &s->d_out16, 16));
+  s->scratch_len = (size_t)rt::totals_scratch_len(N);
+  CK(dalloc(s, &s->d_scratch, s->scratch_len));
+  CK(dalloc_bytes(s, &s->d_I[0], (size_t)N * A * s->rsize));
+  CK(dalloc_bytes(s, &s->d_I[1], (size_t)N * A * s->rsize));
+  CK(dalloc_bytes(s, &s->d_I0, (size_t)A * s->rsize));
+  CK(cudaMemsetAsync(s->d_I0, 0, (size_t)A * s->rsize, s->stream));
+  CK(cudaMemsetAsync(s->d_I[0], 0, (size_t)N * A * s->rsize, s->stream));
+  CK(cudaMemsetAsync(s->d_kind, 0, N, s->stream));
+  CK(cudaMemsetAsync(s->d_aux, 0, sizeof(double2) * N, s->stream));
+  CK(cudaMemsetAsync(s->d_bc_row, 0, sizeof(int32_t) * N, s->stream));
+  CK(cudaMemsetAsync(s->d_ext, 0, sizeof(double) * 4 * N, s->stream));
+  CK(cudaMemsetAsync(s->d_status, 0, sizeof(unsigned), s->stream));
+  CK(cudaMemsetAsync(s->d_bad, 0xff, sizeof(unsigned long long), s->stream));
+  s->n_rows = 1;
+  // upwind positivity bound
+  CK(rt::launch_positivity(s, s->d_out16));
+  double kmax = 0;
+  CK(cudaMemcpyAsync(&kmax, s->d_out16, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+#undef CK
+  s->dt_max = kmax > 0 ? 1.0 / kmax : INFINITY;
+  *out = s;
+  return RT_OK;
+}
+
+int rt_set_gas(rt_state *s, const double *rho, const double *e, const double *m,
+               const double *kP, const double *kJ, const double *kS) {
+  if (!s) return RT_ERR_ARG;
+  if (!rho || !e || !m || !kP || !kJ || !kS) return fail(s, RT_ERR_ARG, "rt_set_gas: NULL array");
+  const int64_t N = s->n_cells;
+  std::vector<rt::GasStatic> gs(N);
+  std::vector<rt::GasDyn> gd(N);
+  for (int64_t ic = 0; ic < N; ++ic) {
+    const int64_t c = s->cell_of[ic];
+    if (!(rho[c] > 0) || !(kP[c] >= 0) || !(kJ[c] >= 0) || !(kS[c] >= 0) || !std::isfinite(e[c]) ||
+        !std::isfinite(m[3 * c]) || !std::isfinite(m[3 * c + 1]) || !std::isfinite(m[3 * c + 2]) ||
+        !std::isfinite(kP[c] + kJ[c] + kS[c]))
+      return fail(s, RT_ERR_ARG, "rt_set_gas: rho must be > 0, opacities >= 0, all finite");
+    gs[ic] = {rho[c], kP[c], kJ[c], kS[c]};
+    gd[ic] = {e[c], m[3 * c], m[3 * c + 1], m[3 * c + 2]};
+  }
+  RT_CUDA(s, cudaMemcpyAsync(s->d_gs, gs.data(), sizeof(rt::GasStatic) * N, cudaMemcpyHostToDevice,
+                             s->stream));
+  RT_CUDA(s, cudaMemcpyAsync(s->d_gd, gd.data(), sizeof(rt::GasDyn) * N, cudaMemcpyHostToDevice,
+                             s->stream));
+  RT_CUDA(s, cudaMemsetAsync(s->d_ext, 0, sizeof(double) * 4 * N, s->stream));
+  RT_CUDA(s, cudaStreamSynchronize(s->stream));
+  s->gas_set = true;
+  return RT_OK;
+}
+
+int rt_set_cells(rt_state *s, const uint8_t *kind, const double *tau, const double *emit,
+                 const double *isrc, const int32_t *bc_row, int64_t n_rows, const double *I0) {
+  if (!s) return RT_ERR_ARG;
+  const int64_t N = s->n_cells;
+  const int A = s->n_angles;
+  std::vector<uint8_t> k(N, 0);
+  std::vector<double2> aux(N, double2{0, 0});
+  std::vector<int32_t> row(N, 0);
+  if (kind) {
+    bool need_bc = false, need_em = false;
+    for (int64_t c = 0; c < N; ++c) {
+      if (kind[c] > 2) return fail(s, RT_ERR_ARG, "rt_set_cells: kind must be 0, 1 or 2");
+      need_bc |= kind[c] == RT_CELL_BOUNDARY;
+      need_em |= kind[c] == RT_CELL_EMITTER;
+    }
+    if (need_bc && (!tau || !bc_row || !I0 || n_rows < 1))
+      return fail(s, RT_ERR_ARG, "rt_set_cells: boundary cells need tau, bc_row and I0");
+    if (need_em && (!emit || !isrc))
+      return fail(s, RT_ERR_ARG, "rt_set_cells: emitter cells need emit_rate and I_src");
+    for (int64_t ic = 0; ic < N; ++ic) {
+      const int64_t c = s->cell_of[ic];
+      k[ic] = kind[c];
+      if (kind[c] == RT_CELL_BOUNDARY) {
+        if (bc_row[c] < 0 || bc_row[c] >= n_rows || !(tau[c] >= 0))
+          return fail(s, RT_ERR_ARG, "rt_set_cells: bad bc_row or negative tau");
+        aux[ic] = double2{tau[c], 0.0};
+        row[ic] = bc_row[c];
+      } else if (kind[c] == RT_CELL_EMITTER) {
+        if (!(emit[c] >= 0) || !std::isfinite(isrc[c]))
+          return fail(s, RT_ERR_ARG, "rt_set_cells: bad emitter rate or intensity");
+        aux[ic] = double2{emit[c], isrc[c]};
+      }
+    }
+  }
+  RT_CUDA(s, cudaMemcpyAsync(s->d_kind, k.data(), N, cudaMemcpyHostToDevice, s->stream));
+  RT_CUDA(s, cudaMemcpyAsync(s->d_aux, aux.data(), sizeof(double2) * N, cudaMemcpyHostToDevice,
+                             s->stream));
+  RT_CUDA(s, cudaMemcpyAsync(s->d_bc_row, row.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice,
+                             s->stream));
+  if (kind && I0 && n_rows >= 1) {
+    RT_CUDA(s, cudaStreamSynchronize(s->stream));
+    if (n_rows != s->n_rows) {
+      cudaFree(s->d_I0);
+      s->d_I0 = nullptr;
+      RT_CUDA(s, dalloc_bytes(s, &s->d_I0, (size_t)n_rows * A * s->rsize));
+      s->n_rows = n_rows;
+    }
+    if (s->precision == RT_FP32) {
+      std::vector<float> f((size_t)n_rows * A);
+      for (size_t i = 0; i < f.size(); ++i) f[i] = (float)I0[i];
+      RT_CUDA(s, cudaMemcpy(s->d_I0, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+    } else {
+      RT_CUDA(s, cudaMemcpy(s->d_I0, I0, (size_t)n_rows * A * 8, cudaMemcpyHostToDevice));
+    }
+  }
+  RT_CUDA(s, cudaStreamSynchronize(s->stream));
+  return RT_OK;
+}
+
+int rt_set_intensity(rt_state *s, const void *I, int on_device) {
+  if (!s || !I) return s ? fail(s, RT_ERR_ARG, "rt_set_intensity: NULL") : RT_ERR_ARG;
+  const size_t bytes = (size_t)s->n_cells * s->n_angles * s->rsize;
+  const void *src = I;
+  void *stage = s->d_I[s->cur ^ 1];
+  if (!on_device) {
+    RT_CUDA(s, cudaMemcpyAsync(stage, I, bytes, cudaMemcpyHostToDevice, s->stream));
+    src = stage;
+  }
+  RT_CUDA(s, rt::launch_permute_in(s, src, s->d_I[s->cur]));
+  RT_CUDA(s, cudaStreamSynchronize(s->stream));
+  return RT_OK;
+}
+
+int rt_get_intensity(rt_state *s, void *I, int on_device) {
+  if (!s || !I) return s ? fail(s, RT_ERR_ARG, "rt_get_intensity: NULL") : RT_ERR_ARG;
+  const size_t bytes = (size_t)s->n_cells * s->n_angles * s->rsize;
+  if (on_device) {
+    RT_CUDA(s, rt::launch_permute_out(s, s->d_I[s->cur], I));
+  } else {
+    void *stage = s->d_I[s->cur ^ 1];
+    RT_CUDA(s, rt::launch_permute_out(s, s->d_I[s->cur], stage));
+    RT_CUDA(s, cudaMemcpyAsync(I, stage, bytes, cudaMemcpyDeviceToHost, s->stream));
+  }
+  RT_CUDA(s, cudaStreamSynchronize(s->stream));
+  return RT_OK;
+}
+
+int rt_get_gas(rt_state *s, double *e, double *m, double *ext, int on_device) {
+  if (!s) return RT_ERR_ARG;
+  const int64_t N = s->n_cells;
+  if (on_device) {
+    RT_CUDA(s, rt::launch_gas_out(s, e, m, ext));
+    RT_CUDA(s, cudaStreamSynchronize(s->stream));
+    return RT_OK;
+  }
+  double *de = nullptr, *dm = nullptr, *dx = nullptr;
+  // staging in the idle intensity buffer when it is large enough, else allocate
+  const size_t need = sizeof(double) * 8 * (size_t)N;
+  const size_t have = (size_t)N * s->n_angles * s->rsize;
+  void *tmp = nullptr;
+  bool own = false;
+  if (have >= need) {
+    tmp = s->d_I[s->cur ^ 1];
+  } else {
+    RT_CUDA(s, cudaMalloc(&tmp, need));
+    own = true;
+  }
+  de = (double *)tmp;
+  dm = de + N;
+  dx = dm + 3 * N;
+  cudaError_t err = rt::launch_gas_out(s, e ? de : nullptr, m ? dm : nullptr, ext ? dx : nullptr);
+  if (err == cudaSuccess && e) err = cudaMemcpyAsync(e, de, 8 * N, cudaMemcpyDeviceToHost, s->stream);
+  if (err == cudaSuccess && m)
+    err = cudaMemcpyAsync(m, dm, 24 * N, cudaMemcpyDeviceToHost, s->stream);
+  if (err == cudaSuccess && ext)
+    err = cudaMemcpyAsync(ext, dx, 32 * N, cudaMemcpyDeviceToHost, s->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s->stream);
+  if (own) cudaFree(tmp);
+  if (err != cudaSuccess) return cuda_fail(s, err, "rt_get_gas");
+  return RT_OK;
+}
+
+int rt_dt_limits(rt_state *s, double *dt_cfl, double *dt_max) {
+  if (!s) return RT_ERR_ARG;
+  if (dt_cfl) *dt_cfl = s->dt_cfl;
+  if (dt_max) *dt_max = s->dt_max;
+  return RT_OK;
+}
+
+static int launch_steps(rt_state *s, int32_t n, double dt, double *dt_used, bool sync) {
+  if (!s) return RT_ERR_ARG;
+  if (!s->gas_set) return fail(s, RT_ERR_STATE, "rt_set_gas must be called before stepping");
+  if (n < 0) return fail(s, RT_ERR_ARG, "negative step count");
+  if (!(dt > 0)) dt = s->dt_cfl;
+  if (!std::isfinite(dt)) return fail(s, RT_ERR_ARG, "dt must be finite");
+  if (dt > s->dt_max) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "dt = %.6g exceeds the upwind positivity limit %.6g", dt, s->dt_max);
+    return fail(s, RT_ERR_CFL, buf);
+  }
+  if (dt_used) *dt_used = dt;
+  for (int32_t i = 0; i < n; ++i) RT_CUDA(s, rt::launch_step(s, dt));
+  return sync ? sync_status(s) : RT_OK;
+}
+
+int rt_step(rt_state *s, double dt, double *dt_used) {
+  return launch_steps(s, 1, dt, dt_used, true);
+}
+
+int rt_run(rt_state *s, int32_t n, double dt, double *dt_used) {
+  return launch_steps(s, n, dt, dt_used, true);
+}
+
+int rt_launch(rt_state *s, int32_t n, double dt, double *dt_used) {
+  return launch_steps(s, n, dt, dt_used, false);
+}
+
+int rt_moments(rt_state *s, double *E, double *F, double *P, int on_device) {
+  if (!s) return RT_ERR_ARG;
+  const int64_t N = s->n_cells;
+  if (on_device) {
+    RT_CUDA(s, rt::launch_moments(s, E, F, P));
+    RT_CUDA(s, cudaStreamSynchronize(s->stream));
+    return RT_OK;
+  }
+  double *buf = nullptr;
+  RT_CUDA(s, cudaMalloc((void **)&buf, sizeof(double) * 10 * N));
+  double *dE = buf, *dF = buf + N, *dP = buf + 4 * N;
+  cudaError_t err = rt::launch_moments(s, E ? dE : nullptr, F ? dF : nullptr, P ? dP : nullptr);
+  if (err == cudaSuccess && E) err = cudaMemcpyAsync(E, dE, 8 * N, cudaMemcpyDeviceToHost, s->stream);
+  if (err == cudaSuccess && F) err = cudaMemcpyAsync(F, dF, 24 * N, cudaMemcpyDeviceToHost, s->stream);
+  if (err == cudaSuccess && P) err = cudaMemcpyAsync(P, dP, 48 * N, cudaMemcpyDeviceToHost, s->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s->stream);
+  cudaFree(buf);
+  if (err != cudaSuccess) return cuda_fail(s, err, "rt_moments");
+  return RT_OK;
+}
+
+int rt_totals(rt_state *s, double out[16]) {
+  if (!s || !out) return s ? fail(s, RT_ERR_ARG, "rt_totals: NULL") : RT_ERR_ARG;
+  RT_CUDA(s, rt::launch_totals(s, s->d_out16));
+  RT_CUDA(s, cudaMemcpyAsync(out, s->d_out16, sizeof(double) * 16, cudaMemcpyDeviceToHost, s->stream));
+  return sync_status(s);
+}
+
+int rt_sync(rt_state *s) {
+  if (!s) return RT_ERR_ARG;
+  return sync_status(s);
+}
+
+int rt_get_state(rt_state *s, void *buf, size_t *bytes) {
+  if (!s || !bytes) return RT_ERR_ARG;
+  const int64_t N = s->n_cells;
+  const size_t nI = (size_t)N * s->n_angles * s->rsize;
+  const size_t need = 64 + nI + sizeof(rt::GasDyn) * N + 32 * (size_t)N;
+  if (!buf) {
+    *bytes = need;
+    return RT_OK;
+  }
+  if (*bytes < need) return fail(s, RT_ERR_ARG, "rt_get_state: buffer too small");
+  char *b = (char *)buf;
+  int64_t hdr[8] = {0x52544742, N, s->n_angles, s->precision, (int64_t)nI, 0, 0, 0};
+  std::memcpy(b, hdr, 64);
+  // internal order is fine: the state is restored into the same mesh
+  RT_CUDA(s, cudaMemcpyAsync(b + 64, s->d_I[s->cur], nI, cudaMemcpyDeviceToHost, s->stream));
+  RT_CUDA(s, cudaMemcpyAsync(b + 64 + nI, s->d_gd, sizeof(rt::GasDyn) * N, cudaMemcpyDeviceToHost,
+                             s->stream));
+  RT_CUDA(s, cudaMemcpyAsync(b + 64 + nI + sizeof(rt::GasDyn) * N, s->d_ext, 32 * (size_t)N,
+                             cudaMemcpyDeviceToHost, s->stream));
+  RT_CUDA(s, cudaStreamSynchronize(s->stream));
+  *bytes = need;
+  return RT_OK;
+}
+
+int rt_set_state(rt_state *s, const void *buf, size_t bytes) {
+  if (!s || !buf) return RT_ERR_ARG;
+  const int64_t N = s->n_cells;
+  const size_t nI = (size_t)N * s->n_angles * s->rsize;
+  const size_t need = 64 + nI + sizeof(rt::GasDyn) * N + 32 * (size_t)N;
+  int64_t hdr[8];
+  if (bytes < need) return fail(s, RT_ERR_ARG, "rt_set_state: buffer too small");
+  std::memcpy(hdr, buf, 64);
+  if (hdr[0] != 0x52544742 || hdr[1] != N || hdr[2] != s->n_angles || hdr[3] != s->precision)
+    return fail(s, RT_ERR_ARG, "rt_set_state: buffer does not match this state");
+  const char *b = (const char *)buf;
+  RT_CUDA(s, cudaMemcpyAsync(s->d_I[s->cur], b + 64, nI, cudaMemcpyHostToDevice, s->stream));
+  RT_CUDA(s, cudaMemcpyAsync(s->d_gd, b + 64 + nI, sizeof(rt::GasDyn) * N, cudaMemcpyHostToDevice,
+                             s->stream));
+  RT_CUDA(s, cudaMemcpyAsync(s->d_ext, b + 64 + nI + sizeof(rt::GasDyn) * N, 32 * (size_t)N,
+                             cudaMemcpyHostToDevice, s->stream));
+  RT_CUDA(s, cudaStreamSynchronize(s->stream));
+  return RT_OK;
+}
+
+int rt_device_bytes(const rt_state *s, size_t *bytes) {
+  if (!s || !bytes) return RT_ERR_ARG;
+  *bytes = s->device_bytes;
+  return RT_OK;
+}
+
+int64_t rt_launch_count(const rt_state *s) { return s ? s->launches : -1; }
+
+const char *rt_last_error(const rt_state *s) { return s ? s->err.c_str() : "null state"; }
+
+void rt_destroy(rt_state *s) {
+  if (!s) return;
+  if (s->stream || true) cudaStreamSynchronize(s->stream);
+  void *bufs[] = {s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
+                  s->d_gd, s->d_kind, s->d_aux, s->d_bc_row, s->d_I0, s->d_ext, s->d_dir, s->d_wt,
+                  s->d_dir64, s->d_wt64, s->d_I[0], s->d_I[1], s->d_status, s->d_bad,
+                  s->d_scratch, s->d_out16};
+  for (void *b : bufs)
+    if (b) cudaFree(b);
+  delete s;
+}
+
+}  // extern "C"

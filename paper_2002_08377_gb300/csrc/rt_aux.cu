@@ -1,0 +1,272 @@
+// Auxiliary kernels: caller<->internal cell order, the upwind positivity
+// bound, lab-frame moments (Sec. 3.1), conserved totals (Sec. 3.4) and the
+// gas read-back.  None of these is on the per-step hot path.
+#include <cuda_runtime.h>
+
+#include "rt_internal.cuh"
+
+namespace rt {
+namespace {
+
+constexpr int kThreads = 256;
+
+// dst[ic][:] = src[cell_of[ic]][:]  (caller order -> internal order)
+template <typename R>
+__global__ void permute_in_kernel(const R *__restrict__ src, R *__restrict__ dst,
+                                  const int64_t *__restrict__ cell_of, int64_t n, int A) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (row >= n) return;
+  const R *s = src + (size_t)cell_of[row] * A;
+  R *d = dst + (size_t)row * A;
+  for (int k = threadIdx.x % 32; k < A; k += 32) d[k] = s[k];
+}
+
+// dst[cell_of[ic]][:] = src[ic][:]  (internal order -> caller order)
+template <typename R>
+__global__ void permute_out_kernel(const R *__restrict__ src, R *__restrict__ dst,
+                                   const int64_t *__restrict__ cell_of, int64_t n, int A) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (row >= n) return;
+  const R *s = src + (size_t)row * A;
+  R *d = dst + (size_t)cell_of[row] * A;
+  for (int k = threadIdx.x % 32; k < A; k += 32) d[k] = s[k];
+}
+
+// K_c = max_a (1/V_c) sum_f max(u_fa, 0), max over cells into *kmax (as the
+// bit pattern of a non-negative double, which orders like the value).
+template <typename R>
+__global__ void positivity_kernel(const int64_t *__restrict__ ptr,
+                                  const typename SlotOf<R>::type *__restrict__ slot,
+                                  const double *__restrict__ vol, const double *__restrict__ dir,
+                                  int64_t n, int A, unsigned long long *kmax) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  double best = 0.0;
+  if (row < n) {
+    for (int a = threadIdx.x % 32; a < A; a += 32) {
+      const double x = dir[3 * a], y = dir[3 * a + 1], z = dir[3 * a + 2];
+      double sum = 0.0;
+      for (int64_t k = ptr[row]; k < ptr[row + 1]; ++k) {
+        const double u = x * (double)slot[k].sx + y * (double)slot[k].sy + z * (double)slot[k].sz -
+                         (double)slot[k].w;
+        if (u > 0.0) sum += u;
+      }
+      best = fmax(best, sum / vol[row]);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if (threadIdx.x % 32 == 0 && row < n)
+    atomicMax(kmax, (unsigned long long)__double_as_longlong(best));
+}
+
+// Per-cell moments E, F[3], P[6] in double, written in caller order.
+template <typename R>
+__global__ void moments_kernel(const R *__restrict__ I, const double *__restrict__ dir,
+                               const double *__restrict__ wt, const int64_t *__restrict__ cell_of,
+                               int64_t n, int A, double c, double *E, double *F, double *P) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (row >= n) return;
+  const R *Ir = I + (size_t)row * A;
+  double s[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int a = threadIdx.x % 32; a < A; a += 32) {
+    const double wi = wt[a] * (double)Ir[a];
+    const double x = dir[3 * a], y = dir[3 * a + 1], z = dir[3 * a + 2];
+    s[0] += wi;
+    s[1] += wi * x;
+    s[2] += wi * y;
+    s[3] += wi * z;
+    s[4] += wi * x * x;
+    s[5] += wi * y * y;
+    s[6] += wi * z * z;
+    s[7] += wi * x * y;
+    s[8] += wi * x * z;
+    s[9] += wi * y * z;
+  }
+#pragma unroll
+  for (int k = 0; k < 10; ++k)
+    for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+  if (threadIdx.x % 32) return;
+  const int64_t oc = cell_of[row];
+  const double fp = 4.0 * kPi;
+  if (E) E[oc] = fp * s[0];
+  if (F) {
+    F[3 * oc] = fp * c * s[1];
+    F[3 * oc + 1] = fp * c * s[2];
+    F[3 * oc + 2] = fp * c * s[3];
+  }
+  if (P)
+    for (int k = 0; k < 6; ++k) P[6 * oc + k] = fp * s[4 + k];
+}
+
+// Totals, pass 1: every block sums a fixed contiguous range of cells in a
+// fixed order into partial[block][16].
+constexpr int kTotCells = 64;  // cells per block
+template <typename R>
+__global__ void totals_partial_kernel(const R *__restrict__ I, const double *__restrict__ dir,
+                                      const double *__restrict__ wt,
+                                      const double *__restrict__ vol, const GasDyn *__restrict__ gd,
+                                      const double *__restrict__ ext, int64_t n, int A,
+                                      double c_over_cbar, double inv_cbar, double *partial) {
+  __shared__ double acc[kThreads / 32][12];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  double t[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const int64_t c0 = (int64_t)blockIdx.x * kTotCells;
+  for (int k = warp; k < kTotCells; k += kThreads / 32) {
+    const int64_t row = c0 + k;
+    if (row >= n) break;
+    const R *Ir = I + (size_t)row * A;
+    double e = 0, fx = 0, fy = 0, fz = 0;
+    for (int a = lane; a < A; a += 32) {
+      const double wi = wt[a] * (double)Ir[a];
+      e += wi;
+      fx += wi * dir[3 * a];
+      fy += wi * dir[3 * a + 1];
+      fz += wi * dir[3 * a + 2];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      e += __shfl_xor_sync(0xffffffffu, e, o);
+      fx += __shfl_xor_sync(0xffffffffu, fx, o);
+      fy += __shfl_xor_sync(0xffffffffu, fy, o);
+      fz += __shfl_xor_sync(0xffffffffu, fz, o);
+    }
+    if (lane == 0) {
+      const double V = vol[row];
+      const GasDyn g = gd[row];
+      const double fp = 4.0 * kPi;
+      t[0] += V * g.e;
+      t[1] += V * c_over_cbar * fp * e;
+      t[2] += V * ext[4 * row];
+      t[3] += V * g.mx;
+      t[4] += V * g.my;
+      t[5] += V * g.mz;
+      t[6] += V * fp * inv_cbar * fx;  // F / (c cbar) with F = 4 pi c sum w n I
+      t[7] += V * fp * inv_cbar * fy;
+      t[8] += V * fp * inv_cbar * fz;
+      t[9] += V * ext[4 * row + 1];
+      t[10] += V * ext[4 * row + 2];
+      t[11] += V * ext[4 * row + 3];
+    }
+  }
+  if (lane == 0)
+    for (int k = 0; k < 12; ++k) acc[warp][k] = t[k];
+  __syncthreads();
+  if (threadIdx.x < 12) {
+    double s = 0;
+    for (int w = 0; w < kThreads / 32; ++w) s += acc[w][threadIdx.x];
+    partial[(size_t)blockIdx.x * 12 + threadIdx.x] = s;
+  }
+}
+
+// Totals, pass 2: component k summed over blocks in block order.
+__global__ void totals_final_kernel(const double *__restrict__ partial, int64_t nblocks,
+                                    double *out16) {
+  const int k = threadIdx.x;
+  if (k >= 12) return;
+  double s = 0;
+  for (int64_t b = 0; b < nblocks; ++b) s += partial[(size_t)b * 12 + k];
+  // layout of the public result: 0..2 energy, 3..5 gas m, 6..8 rad, 9..11 ext
+  out16[k] = s;
+  __syncwarp(0xfffu);
+  if (k == 0) out16[12] = out16[0] + out16[1] + out16[2];
+  if (k < 3) out16[13 + k] = out16[3 + k] + out16[6 + k] + out16[9 + k];
+}
+
+__global__ void gas_out_kernel(const GasDyn *__restrict__ gd, const double *__restrict__ ext,
+                               const int64_t *__restrict__ cell_of, int64_t n, double *e,
+                               double *m, double *x) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t oc = cell_of[i];
+  const GasDyn g = gd[i];
+  if (e) e[oc] = g.e;
+  if (m) {
+    m[3 * oc] = g.mx;
+    m[3 * oc + 1] = g.my;
+    m[3 * oc + 2] = g.mz;
+  }
+  if (x)
+    for (int k = 0; k < 4; ++k) x[4 * oc + k] = ext[4 * i + k];
+}
+
+unsigned rows_grid(int64_t n) { return (unsigned)((n + kThreads / 32 - 1) / (kThreads / 32)); }
+
+}  // namespace
+
+cudaError_t launch_permute_in(rt_state *s, const void *src, void *dst) {
+  if (s->precision == RT_FP32)
+    permute_in_kernel<float><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
+        (const float *)src, (float *)dst, s->d_cell_of, s->n_cells, s->n_angles);
+  else
+    permute_in_kernel<double><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
+        (const double *)src, (double *)dst, s->d_cell_of, s->n_cells, s->n_angles);
+  s->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute_out(rt_state *s, const void *src, void *dst) {
+  if (s->precision == RT_FP32)
+    permute_out_kernel<float><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
+        (const float *)src, (float *)dst, s->d_cell_of, s->n_cells, s->n_angles);
+  else
+    permute_out_kernel<double><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
+        (const double *)src, (double *)dst, s->d_cell_of, s->n_cells, s->n_angles);
+  s->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_positivity(rt_state *s, double *d_kmax) {
+  cudaError_t e = cudaMemsetAsync(d_kmax, 0, sizeof(double), s->stream);
+  if (e != cudaSuccess) return e;
+  if (s->precision == RT_FP32)
+    positivity_kernel<float><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
+        s->d_ptr, (const SlotF *)s->d_slot, s->d_volume, s->d_dir64, s->n_cells, s->n_angles,
+        (unsigned long long *)d_kmax);
+  else
+    positivity_kernel<double><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
+        s->d_ptr, (const SlotD *)s->d_slot, s->d_volume, s->d_dir64, s->n_cells, s->n_angles,
+        (unsigned long long *)d_kmax);
+  s->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments(rt_state *s, double *E, double *F, double *P) {
+  const void *I = s->d_I[s->cur];
+  if (s->precision == RT_FP32)
+    moments_kernel<float><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
+        (const float *)I, s->d_dir64, s->d_wt64, s->d_cell_of, s->n_cells, s->n_angles,
+        s->params.c, E, F, P);
+  else
+    moments_kernel<double><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
+        (const double *)I, s->d_dir64, s->d_wt64, s->d_cell_of, s->n_cells, s->n_angles,
+        s->params.c, E, F, P);
+  s->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_totals(rt_state *s, double *d_out16) {
+  const int64_t nb = (s->n_cells + kTotCells - 1) / kTotCells;
+  if ((size_t)nb * 12 > s->scratch_len) return cudaErrorInvalidValue;
+  const void *I = s->d_I[s->cur];
+  const double coc = s->params.c / s->params.cbar, icb = 1.0 / s->params.cbar;
+  if (s->precision == RT_FP32)
+    totals_partial_kernel<float><<<(unsigned)nb, kThreads, 0, s->stream>>>(
+        (const float *)I, s->d_dir64, s->d_wt64, s->d_volume, s->d_gd, s->d_ext, s->n_cells,
+        s->n_angles, coc, icb, s->d_scratch);
+  else
+    totals_partial_kernel<double><<<(unsigned)nb, kThreads, 0, s->stream>>>(
+        (const double *)I, s->d_dir64, s->d_wt64, s->d_volume, s->d_gd, s->d_ext, s->n_cells,
+        s->n_angles, coc, icb, s->d_scratch);
+  totals_final_kernel<<<1, 32, 0, s->stream>>>(s->d_scratch, nb, d_out16);
+  s->launches += 2;
+  return cudaGetLastError();
+}
+
+int64_t totals_scratch_len(int64_t n_cells) { return ((n_cells + kTotCells - 1) / kTotCells) * 12; }
+
+cudaError_t launch_gas_out(rt_state *s, double *e, double *m, double *ext) {
+  gas_out_kernel<<<(unsigned)((s->n_cells + kThreads - 1) / kThreads), kThreads, 0, s->stream>>>(
+      s->d_gd, s->d_ext, s->d_cell_of, s->n_cells, e, m, ext);
+  s->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace rt

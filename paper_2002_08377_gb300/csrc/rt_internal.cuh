@@ -1,0 +1,131 @@
+// Internal declarations of the GB300 radiation library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rt.h"
+
+namespace rt {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Directed face slot of one cell, in the cell's outward orientation:
+//   s = cbar * A_f * n_f (outward), w = A_f * w_f . n_f (outward).
+// u_a = n_a . s - w is the volume flux coefficient of angle a; the slot on
+// the other side of the face holds the exact negatives.
+struct alignas(16) SlotF {
+  float sx, sy, sz, w;
+};
+struct alignas(32) SlotD {
+  double sx, sy, sz, w;
+};
+template <typename R> struct SlotOf;
+template <> struct SlotOf<float> { using type = SlotF; };
+template <> struct SlotOf<double> { using type = SlotD; };
+
+// Status bits latched by the step kernels.
+enum : unsigned {
+  ST_NONCONV = 1u,
+  ST_NONFINITE = 2u,
+};
+
+// Per-cell constant gas data (double): rho, kappa_P, kappa_J, kappa_s.
+struct alignas(32) GasStatic {
+  double rho, kP, kJ, kS;
+};
+// Per-cell evolving gas data (double): e, m.
+struct alignas(32) GasDyn {
+  double e, mx, my, mz;
+};
+
+template <typename R> struct StepArgs {
+  int64_t n_cells;
+  int32_t n_angles, half;
+  const int64_t *ptr;       // [N+1] slot range per internal cell
+  const int32_t *nbr;       // [nnz] internal neighbour index
+  const typename SlotOf<R>::type *slot;  // [nnz]
+  const R *inv_vol;         // [N]
+  const GasStatic *gs;      // [N]
+  GasDyn *gd;               // [N]
+  const uint8_t *kind;      // [N]
+  const double2 *aux;       // [N] (tau or emit_rate, I_src)
+  const int32_t *bc_row;    // [N]
+  const R *I0;              // [rows][A]
+  double *ext;              // [N][4]
+  const R *dir;             // [A][4] (x, y, z, 0)
+  const R *wt;              // [A]
+  const R *I_in;            // [N][A]
+  R *I_out;                 // [N][A]
+  double dt, cbar, c, a_rad, rcv;  // rcv = r_gas / (gamma - 1)
+  int32_t newton_max_iter;
+  unsigned *status;
+  unsigned long long *bad_cell;
+};
+
+}  // namespace rt
+
+// Opaque state behind the C ABI.
+struct rt_state {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int precision = RT_FP64;
+  size_t rsize = 8;  // bytes per real of the state precision
+  int64_t n_cells = 0, n_faces = 0, nnz = 0;
+  int32_t n_angles = 0;
+  rt_params params{};
+  double dt_cfl = 0, dt_max = 0;
+  bool gas_set = false;
+  int64_t n_rows = 0;
+  std::string err;
+  int64_t launches = 0;
+  size_t device_bytes = 0;
+
+  // host copies needed for I/O
+  std::vector<int64_t> cell_of;  // internal -> caller
+  std::vector<double> volume;    // caller order
+
+  // device buffers
+  int64_t *d_ptr = nullptr;
+  int32_t *d_nbr = nullptr;
+  void *d_slot = nullptr;
+  void *d_inv_vol = nullptr;
+  int64_t *d_cell_of = nullptr;  // internal -> caller
+  double *d_volume = nullptr;    // internal order
+  rt::GasStatic *d_gs = nullptr;
+  rt::GasDyn *d_gd = nullptr;
+  uint8_t *d_kind = nullptr;
+  double2 *d_aux = nullptr;
+  int32_t *d_bc_row = nullptr;
+  void *d_I0 = nullptr;
+  double *d_ext = nullptr;
+  void *d_dir = nullptr;
+  void *d_wt = nullptr;
+  double *d_dir64 = nullptr;  // [A][3] double, for moments
+  double *d_wt64 = nullptr;
+  void *d_I[2] = {nullptr, nullptr};
+  int cur = 0;
+  unsigned *d_status = nullptr;
+  unsigned long long *d_bad = nullptr;
+  double *d_scratch = nullptr;  // reduction partials
+  size_t scratch_len = 0;
+  double *d_out16 = nullptr;
+};
+
+namespace rt {
+
+// kernel launchers (rt_step.cu)
+cudaError_t launch_step(rt_state *s, double dt);
+
+// auxiliary kernels (rt_aux.cu)
+cudaError_t launch_permute_in(rt_state *s, const void *src, void *dst);
+cudaError_t launch_permute_out(rt_state *s, const void *src, void *dst);
+cudaError_t launch_positivity(rt_state *s, double *d_kmax);
+cudaError_t launch_moments(rt_state *s, double *E, double *F, double *P);
+cudaError_t launch_totals(rt_state *s, double *d_out16);
+cudaError_t launch_gas_out(rt_state *s, double *e, double *m, double *ext);
+
+}  // namespace rt

@@ -1,0 +1,197 @@
+"""Python handle on one radiation state of the C ABI (include/rt.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  PyTorch supplies the CUDA stream and device tensors for the
+on-device I/O paths; numpy arrays go through the host paths.
+"""
+import ctypes
+
+import numpy as np
+
+from . import capi
+
+try:  # torch is optional for the host-buffer paths
+    import torch
+except Exception:  # pragma: no cover
+    torch = None
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(np.asarray(a, dtype=dt))
+
+
+class RTSolver:
+    """One mesh + angle set + gas state on the current CUDA device.
+
+    precision: "fp32" (float intensities/transport, double quartic and
+    exchange) or "fp64".
+    """
+
+    def __init__(self, mesh, dirs, weights, *, cbar, c, a_rad=1.0, gamma_gas=5.0 / 3.0,
+                 r_gas=1.0, cfl=0.3, precision="fp32", newton_max_iter=64, stream=None):
+        if torch is None or not torch.cuda.is_available():
+            raise RuntimeError("RTSolver needs a CUDA device (no CPU fallback exists)")
+        self.lib = capi.load()
+        self.precision = precision
+        self.dtype = np.float32 if precision == "fp32" else np.float64
+        self.tdtype = torch.float32 if precision == "fp32" else torch.float64
+        self.N, self.A = int(mesh.n_cells), int(np.asarray(dirs).shape[0])
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        keep = self._keep = []
+
+        def ptr(a, dt):
+            if a is None:
+                return None
+            a = _c(a, dt)
+            keep.append(a)
+            return a.ctypes.data
+
+        md = capi.MeshDesc()
+        md.n_cells, md.n_faces, md.n_angles = self.N, int(mesh.n_faces), self.A
+        md.cell_volume = ptr(mesh.cell_volume, np.float64)
+        md.cell_centroid = ptr(mesh.cell_centroid, np.float64)
+        md.face_cells = ptr(mesh.face_cells, np.int32)
+        md.face_area = ptr(mesh.face_area, np.float64)
+        md.face_normal = ptr(mesh.face_normal, np.float64)
+        md.face_centroid = ptr(mesh.face_centroid, np.float64)
+        fw = getattr(mesh, "face_w", None)
+        md.face_w = ptr(fw, np.float64) if fw is not None and np.any(fw) else None
+        md.cell_face_ptr = ptr(mesh.cell_face_ptr, np.int64)
+        md.cell_face_idx = ptr(mesh.cell_face_idx, np.int32)
+        md.angle_dir = ptr(dirs, np.float64)
+        md.angle_w = ptr(weights, np.float64)
+        pr = capi.Params(cbar, c, a_rad, gamma_gas, r_gas, cfl,
+                         capi.RT_FP32 if precision == "fp32" else capi.RT_FP64, newton_max_iter)
+        st = ctypes.c_void_p()
+        code = self.lib.rt_create(ctypes.byref(md), ctypes.byref(pr),
+                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(st))
+        self._keep = []
+        if code != capi.RT_OK:
+            raise capi.RTError(code, "rt_create failed (details on stderr)")
+        self.state = st
+
+    @classmethod
+    def from_problem(cls, prob, precision="fp32", **kw):
+        s = cls(prob.mesh, prob.dirs, prob.weights, cbar=prob.cbar, c=prob.c, a_rad=prob.a_rad,
+                gamma_gas=prob.gamma_gas, r_gas=prob.r_gas, cfl=prob.cfl, precision=precision, **kw)
+        s.set_gas(prob.rho, prob.e, prob.m, prob.kappa_P, prob.kappa_J, prob.kappa_s)
+        s.set_cells(prob.kind, prob.tau, prob.emit_rate, prob.I_src, prob.bc_row, prob.I0)
+        s.set_intensity(prob.initial_intensity(s.dtype))
+        return s
+
+    # -------------------------------------------------------------- inputs
+    def _check(self, code):
+        return capi.check(self.state, code)
+
+    def set_gas(self, rho, e, m, kappa_P, kappa_J, kappa_s):
+        arrs = [_c(x, np.float64) for x in (rho, e, m, kappa_P, kappa_J, kappa_s)]
+        self._check(self.lib.rt_set_gas(self.state, *[a.ctypes.data for a in arrs]))
+
+    def set_cells(self, kind=None, tau=None, emit_rate=None, I_src=None, bc_row=None, I0=None):
+        if kind is None:
+            self._check(self.lib.rt_set_cells(self.state, None, None, None, None, None, 0, None))
+            return
+        k = _c(kind, np.uint8)
+        t, er, isrc = (_c(x, np.float64) for x in (tau, emit_rate, I_src))
+        br = _c(bc_row, np.int32)
+        i0 = _c(I0, np.float64).reshape(-1, self.A)
+        self._check(self.lib.rt_set_cells(self.state, k.ctypes.data, t.ctypes.data, er.ctypes.data,
+                                          isrc.ctypes.data, br.ctypes.data, i0.shape[0],
+                                          i0.ctypes.data))
+
+    def set_intensity(self, I):
+        if torch is not None and isinstance(I, torch.Tensor) and I.is_cuda:
+            I = I.to(self.tdtype).contiguous()
+            assert I.numel() == self.N * self.A
+            self._check(self.lib.rt_set_intensity(self.state, ctypes.c_void_p(I.data_ptr()), 1))
+        else:
+            a = _c(I, self.dtype).reshape(self.N, self.A)
+            self._check(self.lib.rt_set_intensity(self.state, a.ctypes.data, 0))
+
+    # -------------------------------------------------------------- stepping
+    def dt_limits(self):
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.rt_dt_limits(self.state, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def step(self, dt=0.0):
+        used = ctypes.c_double()
+        self._check(self.lib.rt_step(self.state, float(dt), ctypes.byref(used)))
+        return used.value
+
+    def run(self, n_steps, dt=0.0):
+        used = ctypes.c_double()
+        self._check(self.lib.rt_run(self.state, int(n_steps), float(dt), ctypes.byref(used)))
+        return used.value
+
+    def launch(self, n_steps, dt=0.0):
+        """Queue n_steps steps on the stream without waiting (see sync())."""
+        used = ctypes.c_double()
+        self._check(self.lib.rt_launch(self.state, int(n_steps), float(dt), ctypes.byref(used)))
+        return used.value
+
+    def sync(self):
+        self._check(self.lib.rt_sync(self.state))
+
+    # -------------------------------------------------------------- outputs
+    def get_intensity(self, device=False):
+        if device:
+            out = torch.empty((self.N, self.A), dtype=self.tdtype, device="cuda")
+            self._check(self.lib.rt_get_intensity(self.state, ctypes.c_void_p(out.data_ptr()), 1))
+            return out
+        out = np.empty((self.N, self.A), self.dtype)
+        self._check(self.lib.rt_get_intensity(self.state, out.ctypes.data, 0))
+        return out
+
+    def gas(self):
+        e, m, x = np.empty(self.N), np.empty((self.N, 3)), np.empty((self.N, 4))
+        self._check(self.lib.rt_get_gas(self.state, e.ctypes.data, m.ctypes.data, x.ctypes.data, 0))
+        return e, m, x
+
+    def moments(self, device=False):
+        if device:
+            E = torch.empty(self.N, dtype=torch.float64, device="cuda")
+            F = torch.empty((self.N, 3), dtype=torch.float64, device="cuda")
+            P = torch.empty((self.N, 6), dtype=torch.float64, device="cuda")
+            self._check(self.lib.rt_moments(self.state, ctypes.c_void_p(E.data_ptr()),
+                                            ctypes.c_void_p(F.data_ptr()),
+                                            ctypes.c_void_p(P.data_ptr()), 1))
+            return E, F, P
+        E, F, P = np.empty(self.N), np.empty((self.N, 3)), np.empty((self.N, 6))
+        self._check(self.lib.rt_moments(self.state, E.ctypes.data, F.ctypes.data, P.ctypes.data, 0))
+        return E, F, P
+
+    def totals(self):
+        out = np.empty(16)
+        self._check(self.lib.rt_totals(self.state, out.ctypes.data))
+        return out
+
+    def get_state(self):
+        n = ctypes.c_size_t()
+        self._check(self.lib.rt_get_state(self.state, None, ctypes.byref(n)))
+        buf = np.empty(n.value, np.uint8)
+        self._check(self.lib.rt_get_state(self.state, buf.ctypes.data, ctypes.byref(n)))
+        return buf
+
+    def set_state(self, buf):
+        buf = np.ascontiguousarray(buf, np.uint8)
+        self._check(self.lib.rt_set_state(self.state, buf.ctypes.data, buf.size))
+
+    def device_bytes(self):
+        n = ctypes.c_size_t()
+        self._check(self.lib.rt_device_bytes(self.state, ctypes.byref(n)))
+        return n.value
+
+    def launch_count(self):
+        return int(self.lib.rt_launch_count(self.state))
+
+    def close(self):
+        if getattr(self, "state", None):
+            self.lib.rt_destroy(self.state)
+            self.state = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,101 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every
+symbol include/rt.h declares, and rt_create's host-side validation rejects
+bad meshes before touching the GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2002_08377_gb300 import build as rtbuild
+from paper_2002_08377_gb300 import capi
+from paper_2002_08377_gb300.inputs import build_mesh, level_symmetric
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "rt.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    rtbuild.build()
+    return capi.load()
+
+
+def header_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(rt_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_header_symbols_exported(lib):
+    names = header_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(capi.EXPORTS) == sorted(n for n in names if n in capi.EXPORTS)
+    assert set(names) <= set(capi.EXPORTS) | set(getattr(capi, "EXTRA_EXPORTS", []))
+
+
+def _desc(mesh, dirs, w, keep):
+    def p(a, dt):
+        a = np.ascontiguousarray(np.asarray(a, dt))
+        keep.append(a)
+        return a.ctypes.data
+
+    d = capi.MeshDesc()
+    d.n_cells, d.n_faces, d.n_angles = mesh.n_cells, mesh.n_faces, dirs.shape[0]
+    d.cell_volume = p(mesh.cell_volume, np.float64)
+    d.cell_centroid = p(mesh.cell_centroid, np.float64)
+    d.face_cells = p(mesh.face_cells, np.int32)
+    d.face_area = p(mesh.face_area, np.float64)
+    d.face_normal = p(mesh.face_normal, np.float64)
+    d.face_centroid = p(mesh.face_centroid, np.float64)
+    d.face_w = None
+    d.cell_face_ptr = p(mesh.cell_face_ptr, np.int64)
+    d.cell_face_idx = p(mesh.cell_face_idx, np.int32)
+    d.angle_dir = p(dirs, np.float64)
+    d.angle_w = p(w, np.float64)
+    return d
+
+
+def _create(lib, mesh, dirs, w):
+    keep = []
+    d = _desc(mesh, dirs, w, keep)
+    pr = capi.Params(10.0, 10.0, 1.0, 5.0 / 3.0, 1.0, 0.3, capi.RT_FP64, 64)
+    st = ctypes.c_void_p()
+    return lib.rt_create(ctypes.byref(d), ctypes.byref(pr), None, ctypes.byref(st)), st
+
+
+def test_create_rejects_bad_meshes(lib):
+    mesh = build_mesh((3, 3, 3), seed=1)
+    dirs, w = level_symmetric(4)
+    # open cell: drop one face's area
+    m2 = build_mesh((3, 3, 3), seed=1)
+    m2.face_area = m2.face_area.copy()
+    m2.face_area[5] *= 0.5
+    code, st = _create(lib, m2, dirs, w)
+    assert code == capi.RT_ERR_MESH and not st.value
+    # face index out of range
+    m3 = build_mesh((3, 3, 3), seed=1)
+    m3.face_cells = m3.face_cells.copy()
+    m3.face_cells[0, 1] = 10 ** 6
+    assert _create(lib, m3, dirs, w)[0] == capi.RT_ERR_MESH
+    # CSR entry on the wrong side
+    m4 = build_mesh((3, 3, 3), seed=1)
+    m4.cell_face_idx = m4.cell_face_idx.copy()
+    m4.cell_face_idx[0] = -m4.cell_face_idx[0] - 1
+    assert _create(lib, m4, dirs, w)[0] == capi.RT_ERR_MESH
+    # angle set without the antipodal ordering
+    d2 = dirs.copy()
+    d2[[0, 1]] = d2[[1, 0]]
+    assert _create(lib, mesh, d2, w)[0] == capi.RT_ERR_ARG
+    # weights not normalised
+    assert _create(lib, mesh, dirs, w * 2)[0] == capi.RT_ERR_ARG
+
+
+def test_null_arguments(lib):
+    st = ctypes.c_void_p()
+    assert lib.rt_create(None, None, None, ctypes.byref(st)) == capi.RT_ERR_ARG
+    assert lib.rt_step(None, 0.0, None) == capi.RT_ERR_ARG
+    assert lib.rt_launch_count(None) == -1
+    lib.rt_destroy(None)

@@ -1,0 +1,255 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on
+the same seeded inputs.
+
+Tolerances: RT_FP64 agrees per intensity to a relative 1e-12 after up to 100
+steps; RT_FP32 agrees in L1 of E_r to a relative 1e-5 and conserves total
+energy to a relative 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_08377_gb300 import build as rtbuild
+from paper_2002_08377_gb300 import capi
+from paper_2002_08377_gb300.inputs import adjoint, diffusion, shadows, thermal, waves
+from tests._problems import make, randomise
+
+pytestmark = pytest.mark.gpu
+
+FP64_REL = 1e-12
+FP32_L1 = 1e-5
+FP32_ENERGY = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    rtbuild.build()
+    capi.load()
+
+
+def solver(prob, precision, **kw):
+    from paper_2002_08377_gb300.solver import RTSolver
+    return RTSolver.from_problem(prob, precision, **kw)
+
+
+def rel_err(g, o):
+    g = np.asarray(g, np.float64)
+    floor = 1e-300
+    return float(np.max(np.abs(g - o) / np.maximum(np.abs(o), floor)))
+
+
+def l1_rel(g, o):
+    return float(np.sum(np.abs(g - o)) / np.sum(np.abs(o)))
+
+
+def run_both(prob, precision, steps, dt=None):
+    o = oracle.Oracle(prob)
+    g = solver(prob, precision)
+    if dt is None:
+        dt = o.cfl_dt()
+    assert o.run(steps, dt) == oracle.ORC_OK
+    g.run(steps, dt)
+    return o, g
+
+
+def check_fp64(o, g, tol=FP64_REL):
+    I = g.get_intensity()
+    assert rel_err(I, o.I) < tol
+    e, m, x = g.gas()
+    assert rel_err(e, o.e) < tol
+    scale = np.abs(o.m).max() + 1e-300
+    assert np.abs(m - o.m).max() < tol * scale
+    if np.abs(o.ext).max() > 0:
+        assert np.abs(x - o.ext).max() < tol * np.abs(o.ext).max()
+
+
+def check_fp32(o, g):
+    E_o, _, _ = o.moments()
+    E_g, _, _ = g.moments()
+    assert l1_rel(E_g, E_o) < FP32_L1
+    e, _, _ = g.gas()
+    assert l1_rel(e, o.e) < FP32_L1
+
+
+# ------------------------------------------------------------------ thermal
+def test_fp64_thermal_workload_100_steps():
+    prob = thermal()
+    o, g = run_both(prob, "fp64", 100)
+    check_fp64(o, g)
+    t = g.totals()
+    assert abs(t[12] - o.totals()[12]) < 1e-13 * abs(t[12])
+
+
+def test_fp32_thermal_workload_100_steps():
+    prob = thermal()
+    o = oracle.Oracle(prob)
+    g = solver(prob, "fp32")
+    t0 = g.totals()
+    dt = o.cfl_dt()
+    assert o.run(100, dt) == 0
+    g.run(100, dt)
+    check_fp32(o, g)
+    t1 = g.totals()
+    assert abs(t1[12] - t0[12]) < FP32_ENERGY * abs(t0[12])
+
+
+# ------------------------------------------------------------------ random, ragged
+@pytest.mark.parametrize("order", [6, 8])
+@pytest.mark.parametrize("n", [(9, 7, 5), (4, 3, 5)])
+def test_fp64_random_problem(order, n):
+    """Ragged cell counts, A = 48 and 80, boundary and emitter cells,
+    moving cells and mesh, scattering, c != cbar."""
+    prob = randomise(make(n=n, order=order, cbar=10.0, c=100.0, w=(0.3, -0.1, 0.2)), seed=5)
+    o, g = run_both(prob, "fp64", 30)
+    check_fp64(o, g)
+
+
+@pytest.mark.parametrize("order", [6, 8])
+def test_fp32_random_problem(order):
+    prob = randomise(make(n=(9, 7, 5), order=order, cbar=10.0, c=100.0, w=(0.3, -0.1, 0.2)),
+                     seed=6)
+    o = oracle.Oracle(prob)
+    g = solver(prob, "fp32")
+    t0 = g.totals()
+    dt = o.cfl_dt()
+    assert o.run(30, dt) == 0
+    g.run(30, dt)
+    check_fp32(o, g)
+    t1 = g.totals()
+    assert abs(t1[12] - t0[12]) < FP32_ENERGY * abs(t0[12])
+    mscale = np.abs(t0[3:12]).sum()
+    assert np.abs(t1[13:16] - t0[13:16]).max() < FP32_ENERGY * mscale
+
+
+def test_fp64_totals_and_moments_match_oracle():
+    prob = randomise(make(n=(6, 5, 7), order=6, cbar=10.0, c=30.0), seed=8)
+    o, g = run_both(prob, "fp64", 5)
+    t_o, t_g = o.totals(), g.totals()
+    assert np.allclose(t_g, t_o, rtol=1e-12, atol=1e-12 * np.abs(t_o).max())
+    E, F, P = g.moments()
+    Eo, Fo, Po = o.moments()
+    assert rel_err(E, Eo) < 1e-12
+    assert np.abs(F - Fo).max() < 1e-12 * np.abs(Fo).max()
+    assert np.abs(P - Po).max() < 1e-12 * np.abs(Po).max()
+
+
+# ------------------------------------------------------------------ workload shapes
+def test_fp64_diffusion_shape_moving_stiff():
+    """Diffusion workload at 20^3: moving mesh and gas, cell optical depth
+    10-1000, scattering."""
+    prob = diffusion(n=20, steps=60)
+    o, g = run_both(prob, "fp64", 60)
+    check_fp64(o, g)
+
+
+def test_fp32_diffusion_shape_moving_stiff():
+    prob = diffusion(n=20, steps=60)
+    o, g = run_both(prob, "fp32", 60)
+    check_fp32(o, g)
+
+
+def test_fp64_waves_shape():
+    prob = waves(n=16, steps=50, amplitude=1e-3)
+    o, g = run_both(prob, "fp64", 50)
+    check_fp64(o, g)
+
+
+def test_fp64_shadows_shape():
+    prob = shadows(n=16, steps=40)
+    o, g = run_both(prob, "fp64", 40)
+    check_fp64(o, g)
+
+
+def test_fp32_shadows_shape():
+    prob = shadows(n=16, steps=40)
+    o, g = run_both(prob, "fp32", 40)
+    check_fp32(o, g)
+
+
+def test_fp64_adjoint_shape_forward():
+    prob = adjoint(n=16, steps=20)
+    o, g = run_both(prob, "fp64", 20)
+    check_fp64(o, g)
+
+
+def test_shadows_full_size_one_step():
+    """Shadows workload at its full size (128^3 cells, 80 angles) in the
+    launch configuration the benchmark times: one step of each precision
+    against one oracle step, every cell compared."""
+    prob = shadows()
+    o = oracle.Oracle(prob)
+    dt = o.cfl_dt()
+    assert o.step(dt) == 0
+    for prec in ("fp64", "fp32"):
+        g = solver(prob, prec)
+        g.step(dt)
+        if prec == "fp64":
+            check_fp64(o, g)
+        else:
+            check_fp32(o, g)
+        g.close()
+
+
+# ------------------------------------------------------------------ behaviour
+def test_bitwise_deterministic():
+    prob = randomise(make(n=(8, 8, 8), order=8, cbar=10.0, c=100.0), seed=12)
+    outs = []
+    for _ in range(2):
+        g = solver(prob, "fp32")
+        g.run(10)
+        outs.append((g.get_intensity(), g.gas()[0]))
+        g.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_state_roundtrip():
+    prob = randomise(make(n=(5, 5, 5), order=6), seed=3)
+    g = solver(prob, "fp64")
+    g.run(3)
+    snap = g.get_state()
+    g.run(4)
+    I1 = g.get_intensity()
+    g.set_state(snap)
+    g.run(4)
+    assert np.array_equal(g.get_intensity(), I1)
+
+
+def test_errors_reported():
+    prob = make(n=(4, 4, 4), order=4)
+    g = solver(prob, "fp64")
+    _, dt_max = g.dt_limits()
+    with pytest.raises(capi.RTError) as ei:
+        g.step(1.01 * dt_max)
+    assert ei.value.code == capi.RT_ERR_CFL
+    g.close()
+    # stiff cell, one Newton iteration allowed -> non-convergence is reported
+    stiff = make(n=(4, 4, 4), order=4, kP=1e6, kJ=1e6, J0=100.0)
+    g = solver(stiff, "fp64", newton_max_iter=1)
+    with pytest.raises(capi.RTError) as ei:
+        g.step()
+    assert ei.value.code == capi.RT_ERR_NONCONV
+    g.close()
+    # non-finite input intensity
+    g = solver(prob, "fp32")
+    I = prob.initial_intensity(np.float32)
+    I[3, 2] = np.nan
+    g.set_intensity(I)
+    with pytest.raises(capi.RTError) as ei:
+        g.step()
+    assert ei.value.code == capi.RT_ERR_NONFINITE
+    g.close()
+
+
+def test_device_io_matches_host_io():
+    import torch
+    prob = randomise(make(n=(5, 6, 7), order=6), seed=2)
+    g = solver(prob, "fp32")
+    I = torch.tensor(prob.initial_intensity(np.float32), device="cuda")
+    g.set_intensity(I)
+    g.run(2)
+    Id = g.get_intensity(device=True).cpu().numpy()
+    assert np.array_equal(Id, g.get_intensity())
+    E, F, P = g.moments(device=True)
+    E2, F2, P2 = g.moments()
+    assert np.array_equal(E.cpu().numpy(), E2) and np.array_equal(P.cpu().numpy(), P2)

@@ -304,6 +304,8 @@ int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state 
     best = std::min(best, std::cbrt(m->cell_volume[c]) / (p->cbar + wmax));
   }
   s->dt_cfl = p->cfl * best;
+  if (m->face_w)
+    for (int64_t k = 0; k < 3 * m->n_faces && !s->moving; ++k) s->moving = m->face_w[k] != 0.0;
 
   int r = (s->precision == RT_FP32) ? build_device_mesh<float>(s, m, slot_of)
                                     : build_device_mesh<double>(s, m, slot_of);
@@ -327,6 +329,8 @@ int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state 
   CK(dalloc(s, &s->d_aux, N));
   CK(dalloc(s, &s->d_bc_row, N));
   CK(dalloc(s, &s->d_ext, 4 * (size_t)N));
+  CK(dalloc_bytes(s, &s->d_cellv, 4 * (size_t)N * s->rsize));
+  CK(cudaMemsetAsync(s->d_cellv, 0, 4 * (size_t)N * s->rsize, s->stream));
   CK(dalloc(s, &s->d_status, 1));
   CK(dalloc(s, &s->d_bad, 1));
   CK(dalloc(s, &s->d_out16, 16));
@@ -376,6 +380,23 @@ int rt_set_gas(rt_state *s, const double *rho, const double *e, const double *m,
   RT_CUDA(s, cudaMemcpyAsync(s->d_gd, gd.data(), sizeof(rt::GasDyn) * N, cudaMemcpyHostToDevice,
                              s->stream));
   RT_CUDA(s, cudaMemsetAsync(s->d_ext, 0, sizeof(double) * 4 * N, s->stream));
+  // per-cell frame velocity and rho (kJ + kS) in the state precision
+  std::vector<double> cv(4 * (size_t)N);
+  for (int64_t ic = 0; ic < N; ++ic) {
+    const double ir = 1.0 / gs[ic].rho;
+    cv[4 * ic] = gd[ic].mx * ir;
+    cv[4 * ic + 1] = gd[ic].my * ir;
+    cv[4 * ic + 2] = gd[ic].mz * ir;
+    cv[4 * ic + 3] = gs[ic].rho * (gs[ic].kJ + gs[ic].kS);
+  }
+  if (s->precision == RT_FP32) {
+    std::vector<float> f(cv.begin(), cv.end());
+    RT_CUDA(s, cudaMemcpy(s->d_cellv, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+  } else {
+    RT_CUDA(s, cudaMemcpy(s->d_cellv, cv.data(), cv.size() * 8, cudaMemcpyHostToDevice));
+  }
+  RT_CUDA(s, cudaMemsetAsync(s->d_status, 0, sizeof(unsigned), s->stream));
+  RT_CUDA(s, cudaMemsetAsync(s->d_bad, 0xff, sizeof(unsigned long long), s->stream));
   RT_CUDA(s, cudaStreamSynchronize(s->stream));
   s->gas_set = true;
   return RT_OK;
@@ -628,7 +649,7 @@ const char *rt_last_error(const rt_state *s) { return s ? s->err.c_str() : "null
 void rt_destroy(rt_state *s) {
   if (!s) return;
   if (s->stream || true) cudaStreamSynchronize(s->stream);
-  void *bufs[] = {s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
+  void *bufs[] = {s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
                   s->d_gd, s->d_kind, s->d_aux, s->d_bc_row, s->d_I0, s->d_ext, s->d_dir, s->d_wt,
                   s->d_dir64, s->d_wt64, s->d_I[0], s->d_I[1], s->d_status, s->d_bad,
                   s->d_scratch, s->d_out16};

@@ -60,7 +60,9 @@ template <typename R> struct StepArgs {
   const R *wt;              // [A]
   const R *I_in;            // [N][A]
   R *I_out;                 // [N][A]
+  R *cellv;                 // [N][4] (v_x, v_y, v_z, rho (kappa_J + kappa_s))
   double dt, cbar, c, a_rad, rcv;  // rcv = r_gas / (gamma - 1)
+  R dt_r, dt_cbar_r, inv_c_r;
   int32_t newton_max_iter;
   unsigned *status;
   unsigned long long *bad_cell;
@@ -79,6 +81,7 @@ struct rt_state {
   rt_params params{};
   double dt_cfl = 0, dt_max = 0;
   bool gas_set = false;
+  bool moving = false;  // some face has a non-zero velocity
   int64_t n_rows = 0;
   std::string err;
   int64_t launches = 0;
@@ -102,6 +105,7 @@ struct rt_state {
   int32_t *d_bc_row = nullptr;
   void *d_I0 = nullptr;
   double *d_ext = nullptr;
+  void *d_cellv = nullptr;  // [N][4] in the state precision
   void *d_dir = nullptr;
   void *d_wt = nullptr;
   double *d_dir64 = nullptr;  // [A][3] double, for moments

@@ -2,18 +2,33 @@
 // source update with gas exchange (Sec. 3.3), boundary cells (Sec. 3.5) and
 // emitter cells (Sec. 3.6), one kernel per step.
 //
-// Mapping: KT consecutive threads own one cell; thread `sub` owns the angle
-// pairs p = sub + KT*j (j < PPT) and their antipodes p + A/2, whose flux
-// coefficient is u(p + A/2) = -(n_p . s) - w.  The cell's I row is read
-// once, neighbour values only for the inflow side of each pair, and the
-// face sum is taken in the cell's slot order (no atomics, deterministic).
-// Per-cell angular sums are reduced over the KT lanes with xor shuffles.
+// Block = 32 cells x 8 threads.  Thread `sub` of a cell owns the angle pairs
+// p = sub + 8 j (j < PPT) and their antipodes p + A/2; the flux coefficient
+// of the antipode through a face is u(p + A/2) = -(n_p . s) - w, so one dot
+// product serves two angles and, on a static mesh, exactly one of the two
+// needs the neighbour's value.  The face sum runs in the cell's slot order
+// (no atomics, deterministic).
+//
+// Phases (separated by __syncthreads):
+//   A  all threads: transport, comoving weights, angular sums (precision R);
+//      each cell's 8 lanes reduce with shuffles into shared memory;
+//   B  warp 0, one lane per cell: the gas temperature quartic in double
+//      (FP32 states start Newton from a float estimate);
+//   C  all threads: new intensities, store, radiation change per cell;
+//   D  warp 0, one lane per cell: gas energy / momentum (or tally) update in
+//      double.
+// Keeping the double-precision work lane-per-cell matters on GB300, whose
+// FP64 rate is a small fraction of its FP32 rate.
 #include <cuda_runtime.h>
 
 #include "rt_internal.cuh"
 
 namespace rt {
 namespace {
+
+constexpr int KT = 8;            // threads per cell
+constexpr int CPB = 32;          // cells per block
+constexpr int NT = KT * CPB;     // threads per block
 
 template <typename R> __device__ __forceinline__ typename SlotOf<R>::type load_slot(
     const typename SlotOf<R>::type *p);
@@ -27,26 +42,70 @@ template <> __device__ __forceinline__ SlotD load_slot<double>(const SlotD *p) {
   return {a.x, a.y, b.x, b.y};
 }
 
-template <int KT, typename T> __device__ __forceinline__ T group_sum(T v) {
+// Reciprocal: the correctly rounded float reciprocal, or in double the
+// float estimate refined by two Newton steps (|error| ~ 1 ulp); arguments
+// here are 1 + x (x >= 0) and Gamma^2, well inside float range.
+template <typename R> __device__ __forceinline__ R rcp(R x);
+template <> __device__ __forceinline__ float rcp<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ double rcp<double>(double x) {
+  double r = (double)__frcp_rn((float)x);
+  r = fma(r, fma(-x, r, 1.0), r);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return r;
+}
+
+template <typename T> __device__ __forceinline__ T cell_sum(T v) {
 #pragma unroll
   for (int o = KT / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Positive root of alpha T^4 + beta T = g (alpha >= 0, beta > 0, g >= 0):
-// Newton from above, T0 = min(g/beta, (g/alpha)^(1/4)); f is increasing and
-// convex, so the iterates fall monotonically onto the root.
+__device__ __forceinline__ unsigned cell_or(unsigned v) {
+#pragma unroll
+  for (int o = KT / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Positive root of alpha T^4 + beta T = g (alpha >= 0, beta > 0, g >= 0).
+// f is increasing and convex on T > 0, so Newton from any point at or above
+// the root decreases monotonically onto it; it stops when an iterate fails
+// to decrease or moves by at most 1e-15 of itself.  FLOAT_START: a float
+// Newton estimate plus one unconditional double step (which lands at or
+// above the root by convexity) replaces the start min(g/beta, (g/alpha)^.25).
+template <bool FLOAT_START>
 __device__ __forceinline__ int quartic_root(double alpha, double beta, double g, int max_iter,
                                             double *T_out) {
   double T = g / beta;
   if (alpha > 0.0) T = fmin(T, sqrt(sqrt(g / alpha)));
-  bool done = false;
   int it = 0;
+  if (FLOAT_START) {
+    const float af = (float)alpha, bf = (float)beta, gf = (float)g;
+    float t = (float)T;
+    for (int k = 0; k < 48; ++k) {
+      const float t2 = t * t;
+      const float f = fmaf(af * t2, t2, fmaf(bf, t, -gf));
+      const float fp = fmaf(4.0f * af * t2, t, bf);
+      const float tn = t - f / fp;
+      if (!(tn < t)) break;
+      const bool conv = (t - tn <= 1e-7f * t);
+      t = tn;
+      if (conv) break;
+    }
+    if (t > 0.0f && isfinite(t) && (double)t < T) {
+      double Tf = t, T2 = Tf * Tf;
+      const double f = fma(alpha * T2, T2, fma(beta, Tf, -g));
+      const double fp = fma(4.0 * alpha * T2, Tf, beta);
+      const double Tn = Tf - f / fp;
+      if (Tn <= T) T = Tn;
+      it = 1;
+    }
+  }
+  bool done = false;
   while (!done && it < max_iter) {
-    double T2 = T * T;
-    double f = fma(alpha * T2, T2, fma(beta, T, -g));
-    double fp = fma(4.0 * alpha * T2, T, beta);
-    double Tn = T - f / fp;
+    const double T2 = T * T;
+    const double f = fma(alpha * T2, T2, fma(beta, T, -g));
+    const double fp = fma(4.0 * alpha * T2, T, beta);
+    const double Tn = T - f / fp;
     ++it;
     if (!(Tn < T)) {
       done = true;
@@ -59,15 +118,24 @@ __device__ __forceinline__ int quartic_root(double alpha, double beta, double g,
   return done ? 0 : 1;
 }
 
-template <typename R, int KT, int PPT>
-__global__ void __launch_bounds__(256) step_kernel(const StepArgs<R> a) {
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t cell = tid / KT;
+template <typename R> struct Shared {
+  R ws[CPB], sI[CPB], sG[CPB];  // comoving weight sum and the two sums of Eq. (Jcom)
+  R q[CPB];                     // dt cbar rho (kP B + kS J) per interior cell
+  R dE[CPB], dF[3][CPB];        // sum w (I* - I') and sum w n (I* - I')
+  unsigned bad[CPB];
+};
+
+template <typename R, int PPT, bool MOVING>
+__global__ void __launch_bounds__(NT) step_kernel(const StepArgs<R> a) {
+  __shared__ Shared<R> sh;
+  const int lc = threadIdx.x / KT;
   const int sub = threadIdx.x % KT;
+  const int64_t cell = (int64_t)blockIdx.x * CPB + lc;
   const bool live = cell < a.n_cells;
   const int64_t c = live ? cell : a.n_cells - 1;  // dead lanes shadow the last cell
   const int A = a.n_angles, H = a.half;
 
+  // ---------------- phase A: transport, I* = I - dt/V sum_f u I_up
   R nx[PPT], ny[PPT], nz[PPT], Ia[PPT], Ib[PPT], acca[PPT], accb[PPT];
   const R *Ic = a.I_in + (size_t)c * A;
 #pragma unroll
@@ -83,8 +151,6 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs<R> a) {
     acca[j] = R(0);
     accb[j] = R(0);
   }
-
-  // ---- transport: I* = I - dt/V sum_f u I_up
   const int64_t k0 = a.ptr[c], k1 = a.ptr[c + 1];
   for (int64_t k = k0; k < k1; ++k) {
     const int32_t nb = __ldg(a.nbr + k);
@@ -95,68 +161,98 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs<R> a) {
       const int p = sub + KT * j;
       if (p < H) {
         const R d = fma(nx[j], s.sx, fma(ny[j], s.sy, nz[j] * s.sz));
-        const R ua = d - s.w;
-        const R ub = -d - s.w;
-        R va = Ia[j], vb = Ib[j];
-        if (ua < R(0)) va = __ldg(In + p);
-        if (ub < R(0)) vb = __ldg(In + p + H);
-        acca[j] = fma(ua, va, acca[j]);
-        accb[j] = fma(ub, vb, accb[j]);
+        if (MOVING) {
+          const R ua = d - s.w, ub = -d - s.w;
+          R va = Ia[j], vb = Ib[j];
+          if (ua < R(0)) va = __ldg(In + p);
+          if (ub < R(0)) vb = __ldg(In + p + H);
+          acca[j] = fma(ua, va, acca[j]);
+          accb[j] = fma(ub, vb, accb[j]);
+        } else {
+          // u_a = d, u_b = -d: the inflow side of the pair reads the neighbour
+          const bool out = d > R(0);
+          const R v = __ldg(In + (out ? p + H : p));
+          acca[j] = fma(d, out ? Ia[j] : v, acca[j]);
+          accb[j] = fma(-d, out ? v : Ib[j], accb[j]);
+        }
       }
     }
   }
-  const R dtv = R(a.dt) * a.inv_vol[c];
-  R wa[PPT], wb[PPT];
+  const R dtv = a.dt_r * a.inv_vol[c];
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) {
+    Ia[j] = fma(-dtv, acca[j], Ia[j]);  // I* (zero for unused slots)
+    Ib[j] = fma(-dtv, accb[j], Ib[j]);
+  }
+
+  // comoving frame (first order in v/c): Gamma = 1 -+ v.n / c, with the
+  // cell's velocity and rho (kJ + kS) kept in the state precision
+  const int kind = a.kind[c];
+  const R vx = a.cellv[4 * c], vy = a.cellv[4 * c + 1], vz = a.cellv[4 * c + 2];
+  const R xs = a.dt_cbar_r * a.cellv[4 * c + 3];
+  const R inv_c = a.inv_c_r;
+  R Ga[PPT], Gb[PPT];
+  R ws = 0, sI = 0, sG = 0;
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
     const int p = sub + KT * j;
-    const bool v = p < H;
-    Ia[j] = v ? fma(-dtv, acca[j], Ia[j]) : R(0);  // now I*
-    Ib[j] = v ? fma(-dtv, accb[j], Ib[j]) : R(0);
-    wa[j] = v ? a.wt[p] : R(0);
-    wb[j] = v ? a.wt[p + H] : R(0);
+    const R vn = (vx * nx[j] + vy * ny[j] + vz * nz[j]) * inv_c;
+    Ga[j] = R(1) - vn;
+    Gb[j] = R(1) + vn;
+    if (p < H) {
+      const R Ga2 = Ga[j] * Ga[j], Gb2 = Gb[j] * Gb[j];
+      const R wca = a.wt[p] * rcp(Ga2), wcb = a.wt[p + H] * rcp(Gb2);
+      const R ra = rcp(R(1) + xs * Ga[j]), rb = rcp(R(1) + xs * Gb[j]);
+      ws += wca + wcb;
+      sI += wca * (Ga2 * Ga2 * Ia[j]) * ra + wcb * (Gb2 * Gb2 * Ib[j]) * rb;
+      sG += wca * Ga[j] * ra + wcb * Gb[j] * rb;
+    }
   }
+  ws = cell_sum(ws);
+  sI = cell_sum(sI);
+  sG = cell_sum(sG);
+  if (sub == 0) {
+    sh.ws[lc] = ws;
+    sh.sI[lc] = sI;
+    sh.sG[lc] = sG;
+  }
+  __syncthreads();
 
-  // ---- source step
-  const int kind = a.kind[c];
-  const GasStatic gs = a.gs[c];
-  GasDyn gd = a.gd[c];
-  const double inv_rho = 1.0 / gs.rho;
-  const double vx = gd.mx * inv_rho, vy = gd.my * inv_rho, vz = gd.mz * inv_rho;
-  const double inv_c = 1.0 / a.c;
-  R Ga[PPT], Gb[PPT];
-#pragma unroll
-  for (int j = 0; j < PPT; ++j) {
-    // Gamma = 1 - v . n / c (first order in v/c); the antipode has 1 + v . n / c
-    const double vn = (vx * (double)nx[j] + vy * (double)ny[j] + vz * (double)nz[j]) * inv_c;
-    Ga[j] = R(1.0 - vn);
-    Gb[j] = R(1.0 + vn);
+  // ---------------- phase B: temperature quartic, one lane per cell
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (warp == 0) {
+    const int64_t cl = (int64_t)blockIdx.x * CPB + lane;
+    R q = 0;
+    unsigned bad = 0;
+    if (cl < a.n_cells && a.kind[cl] == RT_CELL_INTERIOR) {
+      const GasStatic g = a.gs[cl];
+      const GasDyn d = a.gd[cl];
+      const R iw = R(1) / sh.ws[lane];
+      const double SI = (double)(sh.sI[lane] * iw), SG = (double)(sh.sG[lane] * iw);
+      const double dcr = a.dt * a.cbar * g.rho;
+      const double D = 1.0 - dcr * g.kS * SG;
+      const double rcv = g.rho * a.rcv;
+      const double kin = 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) / g.rho;
+      const double Tn = (d.e - kin) / rcv;
+      const double alpha = a.dt * a.c * g.rho * g.kP * a.a_rad * (1.0 - dcr * g.kJ * SG / D);
+      const double gq = rcv * Tn + a.dt * a.c * g.rho * 4.0 * kPi * g.kJ * SI / D;
+      double T = 0.0;
+      if (!(gq >= 0.0) || !(alpha >= 0.0)) {
+        bad |= ST_NONFINITE;
+      } else if (quartic_root<sizeof(R) == 4>(alpha, rcv, gq, a.newton_max_iter, &T)) {
+        bad |= ST_NONCONV;
+      }
+      const double B = a.a_rad * (T * T) * (T * T) / (4.0 * kPi);
+      const double J = (SI + dcr * g.kP * B * SG) / D;
+      q = R(dcr * (g.kP * B + g.kS * J));
+    }
+    sh.q[lane] = q;
+    sh.bad[lane] = bad;
   }
-  // Comoving weights and the angular sums of Eq. (Jcom).  Every lane takes
-  // part in the reductions whatever its cell's kind, so the shuffles below
-  // are never divergent; only interior cells use the result.
-  const R xs = R(a.dt * a.cbar * gs.rho * (gs.kJ + gs.kS));
-  R wsum = 0, sI = 0, sG = 0;
-  R Ita[PPT], Itb[PPT], xa[PPT], xb[PPT];
-#pragma unroll
-  for (int j = 0; j < PPT; ++j) {
-    const R Ga2 = Ga[j] * Ga[j], Gb2 = Gb[j] * Gb[j];
-    Ita[j] = Ga2 * Ga2 * Ia[j];
-    Itb[j] = Gb2 * Gb2 * Ib[j];
-    const R wca = wa[j] / Ga2, wcb = wb[j] / Gb2;
-    xa[j] = xs * Ga[j];
-    xb[j] = xs * Gb[j];
-    const R ra = R(1) / (R(1) + xa[j]), rb = R(1) / (R(1) + xb[j]);
-    wsum += wca + wcb;
-    sI += wca * Ita[j] * ra + wcb * Itb[j] * rb;
-    sG += wca * Ga[j] * ra + wcb * Gb[j] * rb;
-  }
-  wsum = group_sum<KT>(wsum);
-  sI = group_sum<KT>(sI);
-  sG = group_sum<KT>(sG);
+  __syncthreads();
 
+  // ---------------- phase C: new intensities and the radiation change
   R In_a[PPT], In_b[PPT];
-  unsigned bad = 0;
   if (kind == RT_CELL_BOUNDARY) {
     const double2 ax = a.aux[c];
     const R f = R((ax.x <= a.dt) ? 1.0 : a.dt / ax.x);
@@ -177,37 +273,21 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs<R> a) {
       const R Ga2 = Ga[j] * Ga[j], Gb2 = Gb[j] * Gb[j];
       const R Ga4 = Ga2 * Ga2, Gb4 = Gb2 * Gb2;
       const R ya = ys * Ga[j], yb = ys * Gb[j];
-      In_a[j] = ((Ga4 * Ia[j] + ya * isrc) / (R(1) + ya)) / Ga4;
-      In_b[j] = ((Gb4 * Ib[j] + yb * isrc) / (R(1) + yb)) / Gb4;
+      In_a[j] = (Ga4 * Ia[j] + ya * isrc) * rcp((R(1) + ya) * Ga4);
+      In_b[j] = (Gb4 * Ib[j] + yb * isrc) * rcp((R(1) + yb) * Gb4);
     }
   } else {
-    const double SI = (double)sI / (double)wsum, SG = (double)sG / (double)wsum;
-    const double dcr = a.dt * a.cbar * gs.rho;
-    const double D = 1.0 - dcr * gs.kS * SG;
-    const double rcv = gs.rho * a.rcv;
-    const double kin = 0.5 * (gd.mx * gd.mx + gd.my * gd.my + gd.mz * gd.mz) * inv_rho;
-    const double Tn = (gd.e - kin) / rcv;
-    const double alpha = a.dt * a.c * gs.rho * gs.kP * a.a_rad * (1.0 - dcr * gs.kJ * SG / D);
-    const double g = rcv * Tn + a.dt * a.c * gs.rho * 4.0 * kPi * gs.kJ * SI / D;
-    double T = 0.0;
-    if (!(g >= 0.0) || !(alpha >= 0.0)) {
-      bad |= ST_NONFINITE;
-    } else if (quartic_root(alpha, rcv, g, a.newton_max_iter, &T)) {
-      bad |= ST_NONCONV;
-    }
-    const double B = a.a_rad * (T * T) * (T * T) / (4.0 * kPi);
-    const double J = (SI + dcr * gs.kP * B * SG) / D;
-    const R q = R(dcr * (gs.kP * B + gs.kS * J));
+    const R q = sh.q[lc];
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
       const R Ga2 = Ga[j] * Ga[j], Gb2 = Gb[j] * Gb[j];
-      In_a[j] = ((Ita[j] + q * Ga[j]) / (R(1) + xa[j])) / (Ga2 * Ga2);
-      In_b[j] = ((Itb[j] + q * Gb[j]) / (R(1) + xb[j])) / (Gb2 * Gb2);
+      const R Ga4 = Ga2 * Ga2, Gb4 = Gb2 * Gb2;
+      In_a[j] = (Ga4 * Ia[j] + q * Ga[j]) * rcp((R(1) + xs * Ga[j]) * Ga4);
+      In_b[j] = (Gb4 * Ib[j] + q * Gb[j]) * rcp((R(1) + xs * Gb[j]) * Gb4);
     }
   }
-
-  // ---- store I^{n+1}; exchange from the stored values: dE = 4 pi sum w (I* - I')
   R de = 0, dfx = 0, dfy = 0, dfz = 0;
+  unsigned nonfinite = 0;
   R *Io = a.I_out + (size_t)c * A;
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
@@ -217,46 +297,67 @@ __global__ void __launch_bounds__(256) step_kernel(const StepArgs<R> a) {
         Io[p] = In_a[j];
         Io[p + H] = In_b[j];
       }
-      if (!isfinite(In_a[j]) || !isfinite(In_b[j])) bad |= ST_NONFINITE;
-      const R da = wa[j] * (Ia[j] - In_a[j]);
-      const R db = wb[j] * (Ib[j] - In_b[j]);
+      if (!isfinite(In_a[j]) || !isfinite(In_b[j])) nonfinite = ST_NONFINITE;
+      const R da = a.wt[p] * (Ia[j] - In_a[j]);
+      const R db = a.wt[p + H] * (Ib[j] - In_b[j]);
       de += da + db;
-      const R dd = da - db;  // antipode has direction -n
+      const R dd = da - db;  // the antipode has direction -n
       dfx = fma(nx[j], dd, dfx);
       dfy = fma(ny[j], dd, dfy);
       dfz = fma(nz[j], dd, dfz);
     }
   }
-  de = group_sum<KT>(de);
-  dfx = group_sum<KT>(dfx);
-  dfy = group_sum<KT>(dfy);
-  dfz = group_sum<KT>(dfz);
-  bad = __reduce_or_sync(0xffffffffu, bad);  // whole warp; harmless over-reporting across cells
-  if (live && sub == 0) {
-    const double fe = a.c / a.cbar * 4.0 * kPi * (double)de;
-    const double fm = 4.0 * kPi / a.cbar;  // (4 pi c sum w n dI) / (c cbar)
-    if (kind == RT_CELL_INTERIOR) {
-      gd.e += fe;
-      gd.mx += fm * (double)dfx;
-      gd.my += fm * (double)dfy;
-      gd.mz += fm * (double)dfz;
-      a.gd[c] = gd;
-    } else {
-      double *x = a.ext + 4 * c;
-      x[0] += fe;
-      x[1] += fm * (double)dfx;
-      x[2] += fm * (double)dfy;
-      x[3] += fm * (double)dfz;
-    }
-    if (bad) {
-      atomicOr(a.status, bad);
-      atomicMin(a.bad_cell, (unsigned long long)c);
+  de = cell_sum(de);
+  dfx = cell_sum(dfx);
+  dfy = cell_sum(dfy);
+  dfz = cell_sum(dfz);
+  nonfinite = cell_or(nonfinite);
+  if (sub == 0) {
+    sh.dE[lc] = de;
+    sh.dF[0][lc] = dfx;
+    sh.dF[1][lc] = dfy;
+    sh.dF[2][lc] = dfz;
+    sh.bad[lc] |= nonfinite;
+  }
+  __syncthreads();
+
+  // ---------------- phase D: gas exchange (Eqs. gas1, gas2), one lane per cell
+  if (warp == 0) {
+    const int64_t cl = (int64_t)blockIdx.x * CPB + lane;
+    if (cl < a.n_cells) {
+      const double fe = a.c / a.cbar * 4.0 * kPi;
+      const double fm = 4.0 * kPi / a.cbar;  // (4 pi c sum w n dI) / (c cbar)
+      const double dE = fe * (double)sh.dE[lane];
+      const double dx = fm * (double)sh.dF[0][lane], dy = fm * (double)sh.dF[1][lane],
+                   dz = fm * (double)sh.dF[2][lane];
+      if (a.kind[cl] == RT_CELL_INTERIOR) {
+        GasDyn d = a.gd[cl];
+        d.e += dE;
+        d.mx += dx;
+        d.my += dy;
+        d.mz += dz;
+        a.gd[cl] = d;
+        const double ir = 1.0 / a.gs[cl].rho;  // frame velocity of the next step
+        a.cellv[4 * cl] = R(d.mx * ir);
+        a.cellv[4 * cl + 1] = R(d.my * ir);
+        a.cellv[4 * cl + 2] = R(d.mz * ir);
+      } else {
+        double *x = a.ext + 4 * cl;
+        x[0] += dE;
+        x[1] += dx;
+        x[2] += dy;
+        x[3] += dz;
+      }
+      const unsigned bad = sh.bad[lane];
+      if (bad) {
+        atomicOr(a.status, bad);
+        atomicMin(a.bad_cell, (unsigned long long)cl);
+      }
     }
   }
 }
 
-template <typename R, int KT, int PPT>
-cudaError_t launch_t(rt_state *s, double dt) {
+template <typename R, int PPT, bool MOVING> cudaError_t launch_t(rt_state *s, double dt) {
   StepArgs<R> a;
   a.n_cells = s->n_cells;
   a.n_angles = s->n_angles;
@@ -277,6 +378,10 @@ cudaError_t launch_t(rt_state *s, double dt) {
   a.I_in = reinterpret_cast<const R *>(s->d_I[s->cur]);
   a.I_out = reinterpret_cast<R *>(s->d_I[s->cur ^ 1]);
   a.dt = dt;
+  a.dt_r = R(dt);
+  a.dt_cbar_r = R(dt * s->params.cbar);
+  a.inv_c_r = R(1.0 / s->params.c);
+  a.cellv = reinterpret_cast<R *>(s->d_cellv);
   a.cbar = s->params.cbar;
   a.c = s->params.c;
   a.a_rad = s->params.a_rad;
@@ -284,28 +389,29 @@ cudaError_t launch_t(rt_state *s, double dt) {
   a.newton_max_iter = s->params.newton_max_iter;
   a.status = s->d_status;
   a.bad_cell = s->d_bad;
-  const int threads = 256;
-  const int64_t total = s->n_cells * KT;
-  const unsigned blocks = (unsigned)((total + threads - 1) / threads);
-  step_kernel<R, KT, PPT><<<blocks, threads, 0, s->stream>>>(a);
+  const unsigned blocks = (unsigned)((s->n_cells + CPB - 1) / CPB);
+  step_kernel<R, PPT, MOVING><<<blocks, NT, 0, s->stream>>>(a);
   s->launches++;
   return cudaGetLastError();
 }
 
-template <typename R> cudaError_t dispatch(rt_state *s, double dt) {
-  const int H = s->n_angles / 2;
-  const int ppt = (H + 7) / 8;
+template <typename R, bool MOVING> cudaError_t dispatch_ppt(rt_state *s, double dt) {
+  const int ppt = (s->n_angles / 2 + KT - 1) / KT;
   switch (ppt) {
-    case 1: return launch_t<R, 8, 1>(s, dt);
-    case 2: return launch_t<R, 8, 2>(s, dt);
-    case 3: return launch_t<R, 8, 3>(s, dt);
-    case 4: return launch_t<R, 8, 4>(s, dt);
-    case 5: return launch_t<R, 8, 5>(s, dt);
-    case 6: return launch_t<R, 8, 6>(s, dt);
-    case 7: return launch_t<R, 8, 7>(s, dt);
-    case 8: return launch_t<R, 8, 8>(s, dt);
+    case 1: return launch_t<R, 1, MOVING>(s, dt);
+    case 2: return launch_t<R, 2, MOVING>(s, dt);
+    case 3: return launch_t<R, 3, MOVING>(s, dt);
+    case 4: return launch_t<R, 4, MOVING>(s, dt);
+    case 5: return launch_t<R, 5, MOVING>(s, dt);
+    case 6: return launch_t<R, 6, MOVING>(s, dt);
+    case 7: return launch_t<R, 7, MOVING>(s, dt);
+    case 8: return launch_t<R, 8, MOVING>(s, dt);
     default: return cudaErrorInvalidValue;
   }
+}
+
+template <typename R> cudaError_t dispatch(rt_state *s, double dt) {
+  return s->moving ? dispatch_ppt<R, true>(s, dt) : dispatch_ppt<R, false>(s, dt);
 }
 
 }  // namespace

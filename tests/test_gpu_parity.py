@@ -57,10 +57,13 @@ def check_fp64(o, g, tol=FP64_REL):
     assert rel_err(I, o.I) < tol
     e, m, x = g.gas()
     assert rel_err(e, o.e) < tol
-    scale = np.abs(o.m).max() + 1e-300
+    # momentum is compared on the scale of the radiation momentum E_r / cbar
+    # (gas momenta that are pure round-off have no relative precision)
+    E, _, _ = o.moments()
+    scale = np.abs(o.m).max() + E.max() / o.prob.cbar
     assert np.abs(m - o.m).max() < tol * scale
-    if np.abs(o.ext).max() > 0:
-        assert np.abs(x - o.ext).max() < tol * np.abs(o.ext).max()
+    xs = np.abs(o.ext).max() + E.max() / o.prob.cbar * (o.prob.c / o.prob.cbar + 1)
+    assert np.abs(x - o.ext).max() < tol * xs
 
 
 def check_fp32(o, g):

@@ -136,6 +136,27 @@ static void cell_moments(const orc_problem *p, const double *Ic, double *E, doub
   F[2] = 4.0 * M_PI * p->c * fz;
 }
 
+/* Energy and momentum the radiation of one cell loses in the source step,
+ * E^n - E^{n+1} and F^n - F^{n+1}.  The moments are linear in I, so these
+ * are 4 pi sum_a w_a (I_a - I'_a) and 4 pi c sum_a w_a n_a (I_a - I'_a);
+ * summing the per-angle differences keeps the digits that subtracting the
+ * two (nearly equal) sums would cancel. */
+static void cell_moment_change(const orc_problem *p, const double *I, const double *In,
+                               double *dE, double *dF) {
+  double e = 0, fx = 0, fy = 0, fz = 0;
+  for (int a = 0; a < p->n_angles; ++a) {
+    double wi = p->wt[a] * (I[a] - In[a]);
+    e += wi;
+    fx += wi * p->dir[3 * a];
+    fy += wi * p->dir[3 * a + 1];
+    fz += wi * p->dir[3 * a + 2];
+  }
+  *dE = 4.0 * M_PI * e;
+  dF[0] = 4.0 * M_PI * p->c * fx;
+  dF[1] = 4.0 * M_PI * p->c * fy;
+  dF[2] = 4.0 * M_PI * p->c * fz;
+}
+
 void orc_moments(const orc_problem *p, const double *I, double *E, double *F, double *P) {
   const int A = p->n_angles;
 #pragma omp parallel for schedule(static)
@@ -252,15 +273,14 @@ double orc_ferrari(double alpha, double beta, double g) {
  *        g     = rho c_v T^n + dt c rho 4 pi kJ S_I / D;
  *  3. I~^{n+1} from Eq. (com radiative source disc), back to the lab frame;
  *  4. E^{n+1}, F^{n+1} and the gas exchange of Eqs. (gas1), (gas2):
- *        e += (c / cbar)(E^n - E^{n+1}),  rho v += (F^n - F^{n+1}) / (c cbar).
+ *        e += (c / cbar)(E^n - E^{n+1}),  rho v += (F^n - F^{n+1}) / (c cbar),
+ *     with the differences summed angle by angle (cell_moment_change).
  * The gas temperature is recomputed from the updated energy next step.
  * --------------------------------------------------------------------- */
 static int source_interior(const orc_problem *p, int64_t c, double dt, const double *Is,
                            double *In, double *e, double *m, int *iters) {
   const int A = p->n_angles;
   const double rho = p->rho[c], kP = p->kappa_P[c], kJ = p->kappa_J[c], kS = p->kappa_s[c];
-  double En, Fn[3];
-  cell_moments(p, Is, &En, Fn);
   double v[3] = {m[0] / rho, m[1] / rho, m[2] / rho};
   double G[A], wc[A], Ic[A];
   double norm = 0.0;
@@ -297,10 +317,10 @@ static int source_interior(const orc_problem *p, int64_t c, double dt, const dou
     double G2 = G[a] * G[a];
     In[a] = Inew / (G2 * G2);
   }
-  double E1, F1[3];
-  cell_moments(p, In, &E1, F1);
-  *e += p->c / p->cbar * (En - E1);
-  for (int k = 0; k < 3; ++k) m[k] += (Fn[k] - F1[k]) / (p->c * p->cbar);
+  double dE, dF[3];
+  cell_moment_change(p, Is, In, &dE, dF);
+  *e += p->c / p->cbar * dE;
+  for (int k = 0; k < 3; ++k) m[k] += dF[k] / (p->c * p->cbar);
   return ORC_OK;
 }
 
@@ -312,12 +332,11 @@ static void source_boundary(const orc_problem *p, int64_t c, double dt, const do
   const int A = p->n_angles;
   double f = (p->tau[c] <= dt) ? 1.0 : dt / p->tau[c];
   const double *I0 = p->I0 + (int64_t)p->bc_row[c] * A;
-  double En, Fn[3], E1, F1[3];
-  cell_moments(p, Is, &En, Fn);
+  double dE, dF[3];
   for (int a = 0; a < A; ++a) In[a] = Is[a] - (Is[a] - I0[a]) * f;
-  cell_moments(p, In, &E1, F1);
-  ext[0] += p->c / p->cbar * (En - E1);
-  for (int k = 0; k < 3; ++k) ext[1 + k] += (Fn[k] - F1[k]) / (p->c * p->cbar);
+  cell_moment_change(p, Is, In, &dE, dF);
+  ext[0] += p->c / p->cbar * dE;
+  for (int k = 0; k < 3; ++k) ext[1 + k] += dF[k] / (p->c * p->cbar);
 }
 
 /* Emitter cells, Sec. 3.6: in the comoving frame I~ relaxes implicitly to
@@ -329,8 +348,7 @@ static void source_emitter(const orc_problem *p, int64_t c, double dt, const dou
   const int A = p->n_angles;
   const double rho = p->rho[c];
   double v[3] = {m[0] / rho, m[1] / rho, m[2] / rho};
-  double En, Fn[3], E1, F1[3];
-  cell_moments(p, Is, &En, Fn);
+  double dE, dF[3];
   for (int a = 0; a < A; ++a) {
     const double *n = p->dir + 3 * a;
     double G = 1.0 - (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / p->c;
@@ -338,9 +356,9 @@ static void source_emitter(const orc_problem *p, int64_t c, double dt, const dou
     double y = dt * p->cbar * G * p->emit_rate[c];
     In[a] = ((G4 * Is[a] + y * p->I_src[c]) / (1.0 + y)) / G4;
   }
-  cell_moments(p, In, &E1, F1);
-  ext[0] += p->c / p->cbar * (En - E1);
-  for (int k = 0; k < 3; ++k) ext[1 + k] += (Fn[k] - F1[k]) / (p->c * p->cbar);
+  cell_moment_change(p, Is, In, &dE, dF);
+  ext[0] += p->c / p->cbar * dE;
+  for (int k = 0; k < 3; ++k) ext[1 + k] += dF[k] / (p->c * p->cbar);
 }
 
 /* Source step over all cells.  e[N], m[N][3], ext[N][4] are updated in

@@ -143,13 +143,14 @@ def barrier(world):
 
 
 # ---------------------------------------------------------------- workload
-def make_workload():
+def make_workload(n=128):
     from paper_2002_08377_gb300.inputs import shadows
-    return shadows()
+    return shadows(n=n)
 
 
 def describe(prob):
-    return {"workload": "shadows/crossing-beams box: 128^3 jittered periodic Voronoi cells, "
+    n = prob.mesh.n[0]
+    return {"workload": f"shadows/crossing-beams box: {n}^3 jittered periodic Voronoi cells, "
                         "80 level-symmetric angles, 3 opaque spheres, 4 emitters, absorbing "
                         "layers, 2 beams, cbar = c = 1e3",
             "cells": prob.n_cells, "angles": prob.n_angles, "faces": prob.mesh.n_faces,
@@ -182,7 +183,7 @@ def cpu_oracle_rate(prob, dt, budget_s, max_cells=None):
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    prob = make_workload()
+    prob = make_workload(args.n)
     dt = prob.cfl_dt()
     import oracle
     o = oracle.Oracle(prob)
@@ -271,6 +272,12 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only", choices=["fp32", "fp64"], default=None,
+                    help="time one precision only (profiling runs)")
+    ap.add_argument("--n", type=int, default=128,
+                    help="lattice cells per axis (128 = the benchmarked workload; smaller for "
+                         "profiler captures)")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":
@@ -285,13 +292,14 @@ def main():
     from paper_2002_08377_gb300.solver import RTSolver
     rtbuild.build()
 
-    prob = make_workload()
+    prob = make_workload(args.n)
     N, A, Nf = prob.n_cells, prob.n_angles, prob.mesh.n_faces
     dt = prob.cfl_dt()
     hbm_peak, peak_kind = measured_peaks()
     results = {}
     sampler = ClockSampler(index=0)
-    for prec in ("fp32", "fp64"):
+    precs = ("fp32", "fp64") if args.only is None else (args.only,)
+    for prec in precs:
         sol = RTSolver.from_problem(prob, prec)
         steps = args.steps if prec == "fp32" else max(3, args.steps // 5)
         ms, launches = time_steps(sol, dt, steps, max(3, args.warmup), world,
@@ -308,7 +316,7 @@ def main():
                          "frac": achieved / hbm_peak, "traffic": traffic,
                          "algorithmic_bytes_per_launch": B,
                          "peak_source": f"{peak_kind} HBM copy bandwidth"}}
-        if prec == "fp32":
+        if prec == "fp32" and not args.no_e2e:
             e2e_v, bi, bo = e2e_rate(sol, prob, dt, max(3, min(10, args.steps)))
             results["e2e"] = {"value": e2e_v * world, "unit": UNIT, "h2d_bytes_per_step": bi,
                               "d2h_bytes_per_step": bo}
@@ -322,12 +330,20 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{done} cell-angle updates of the FP64 oracle on this workload "
                          f"({el:.1f} s, whole steps of {N} cells x {A} angles)"}
+    if args.only is not None:
+        r = results[args.only]
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": r["value"], "unit": UNIT,
+                              "ms_per_step": r["ms_per_step"], "dtype": args.only,
+                              "config": describe(prob), "roofline": r["roofline"],
+                              "note": "single-precision profiling run"}), flush=True)
+        return
     r32 = results["fp32"]
     line = {"metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": world,
             "steps": r32["steps"], "warmup": max(3, args.warmup), "ms_per_step": r32["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": describe(prob), "roofline": r32["roofline"],
-            "cpu_baseline": cpu, "e2e": results["e2e"], "gpu_launches": r32["launches"],
+            "cpu_baseline": cpu, "e2e": results.get("e2e"), "gpu_launches": r32["launches"],
             "clocks": sampler.summary(),
             "fp64": {"value": results["fp64"]["value"], "ms_per_step": results["fp64"]["ms_per_step"],
                      "steps": results["fp64"]["steps"], "dtype": "f64",

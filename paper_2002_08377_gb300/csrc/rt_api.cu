@@ -372,7 +372,8 @@ int rt_set_gas(rt_state *s, const double *rho, const double *e, const double *m,
         !std::isfinite(m[3 * c]) || !std::isfinite(m[3 * c + 1]) || !std::isfinite(m[3 * c + 2]) ||
         !std::isfinite(kP[c] + kJ[c] + kS[c]))
       return fail(s, RT_ERR_ARG, "rt_set_gas: rho must be > 0, opacities >= 0, all finite");
-    gs[ic] = {rho[c], kP[c], kJ[c], kS[c]};
+    const double rcv = rho[c] * s->params.r_gas / (s->params.gamma_gas - 1.0);
+    gs[ic] = {rho[c], kP[c], kJ[c], kS[c], 1.0 / rho[c], rcv, 1.0 / rcv, 0.0};
     gd[ic] = {e[c], m[3 * c], m[3 * c + 1], m[3 * c + 2]};
   }
   RT_CUDA(s, cudaMemcpyAsync(s->d_gs, gs.data(), sizeof(rt::GasStatic) * N, cudaMemcpyHostToDevice,
@@ -381,20 +382,7 @@ int rt_set_gas(rt_state *s, const double *rho, const double *e, const double *m,
                              s->stream));
   RT_CUDA(s, cudaMemsetAsync(s->d_ext, 0, sizeof(double) * 4 * N, s->stream));
   // per-cell frame velocity and rho (kJ + kS) in the state precision
-  std::vector<double> cv(4 * (size_t)N);
-  for (int64_t ic = 0; ic < N; ++ic) {
-    const double ir = 1.0 / gs[ic].rho;
-    cv[4 * ic] = gd[ic].mx * ir;
-    cv[4 * ic + 1] = gd[ic].my * ir;
-    cv[4 * ic + 2] = gd[ic].mz * ir;
-    cv[4 * ic + 3] = gs[ic].rho * (gs[ic].kJ + gs[ic].kS);
-  }
-  if (s->precision == RT_FP32) {
-    std::vector<float> f(cv.begin(), cv.end());
-    RT_CUDA(s, cudaMemcpy(s->d_cellv, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
-  } else {
-    RT_CUDA(s, cudaMemcpy(s->d_cellv, cv.data(), cv.size() * 8, cudaMemcpyHostToDevice));
-  }
+  RT_CUDA(s, rt::launch_cellv(s));
   RT_CUDA(s, cudaMemsetAsync(s->d_status, 0, sizeof(unsigned), s->stream));
   RT_CUDA(s, cudaMemsetAsync(s->d_bad, 0xff, sizeof(unsigned long long), s->stream));
   RT_CUDA(s, cudaStreamSynchronize(s->stream));
@@ -632,6 +620,7 @@ int rt_set_state(rt_state *s, const void *buf, size_t bytes) {
                              s->stream));
   RT_CUDA(s, cudaMemcpyAsync(s->d_ext, b + 64 + nI + sizeof(rt::GasDyn) * N, 32 * (size_t)N,
                              cudaMemcpyHostToDevice, s->stream));
+  RT_CUDA(s, rt::launch_cellv(s));
   RT_CUDA(s, cudaStreamSynchronize(s->stream));
   return RT_OK;
 }

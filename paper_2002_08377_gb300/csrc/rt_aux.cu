@@ -187,6 +187,22 @@ __global__ void gas_out_kernel(const GasDyn *__restrict__ gd, const double *__re
     for (int k = 0; k < 4; ++k) x[4 * oc + k] = ext[4 * i + k];
 }
 
+// cellv = (m / rho, rho (kJ + kS)) in the state precision, as the step
+// kernel's gas update writes it
+template <typename R>
+__global__ void cellv_kernel(const GasStatic *__restrict__ gs, const GasDyn *__restrict__ gd,
+                             int64_t n, R *cellv) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const GasStatic g = gs[i];
+  const GasDyn d = gd[i];
+  const double ir = g.inv_rho;
+  cellv[4 * i] = R(d.mx * ir);
+  cellv[4 * i + 1] = R(d.my * ir);
+  cellv[4 * i + 2] = R(d.mz * ir);
+  cellv[4 * i + 3] = R(g.rho * (g.kJ + g.kS));
+}
+
 unsigned rows_grid(int64_t n) { return (unsigned)((n + kThreads / 32 - 1) / (kThreads / 32)); }
 
 }  // namespace
@@ -265,6 +281,18 @@ int64_t totals_scratch_len(int64_t n_cells) { return ((n_cells + kTotCells - 1) 
 cudaError_t launch_gas_out(rt_state *s, double *e, double *m, double *ext) {
   gas_out_kernel<<<(unsigned)((s->n_cells + kThreads - 1) / kThreads), kThreads, 0, s->stream>>>(
       s->d_gd, s->d_ext, s->d_cell_of, s->n_cells, e, m, ext);
+  s->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cellv(rt_state *s) {
+  const unsigned g = (unsigned)((s->n_cells + kThreads - 1) / kThreads);
+  if (s->precision == RT_FP32)
+    cellv_kernel<float><<<g, kThreads, 0, s->stream>>>(s->d_gs, s->d_gd, s->n_cells,
+                                                       (float *)s->d_cellv);
+  else
+    cellv_kernel<double><<<g, kThreads, 0, s->stream>>>(s->d_gs, s->d_gd, s->n_cells,
+                                                        (double *)s->d_cellv);
   s->launches++;
   return cudaGetLastError();
 }

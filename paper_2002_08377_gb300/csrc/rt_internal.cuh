@@ -33,9 +33,10 @@ enum : unsigned {
   ST_NONFINITE = 2u,
 };
 
-// Per-cell constant gas data (double): rho, kappa_P, kappa_J, kappa_s.
-struct alignas(32) GasStatic {
-  double rho, kP, kJ, kS;
+// Per-cell constant gas data (double): rho, kappa_P, kappa_J, kappa_s and
+// the derived 1/rho, rho c_v = rho r_gas / (gamma - 1) and its inverse.
+struct alignas(64) GasStatic {
+  double rho, kP, kJ, kS, inv_rho, rcv, inv_rcv, pad;
 };
 // Per-cell evolving gas data (double): e, m.
 struct alignas(32) GasDyn {
@@ -131,5 +132,6 @@ cudaError_t launch_positivity(rt_state *s, double *d_kmax);
 cudaError_t launch_moments(rt_state *s, double *E, double *F, double *P);
 cudaError_t launch_totals(rt_state *s, double *d_out16);
 cudaError_t launch_gas_out(rt_state *s, double *e, double *m, double *ext);
+cudaError_t launch_cellv(rt_state *s);
 
 }  // namespace rt

@@ -72,35 +72,57 @@ __device__ __forceinline__ unsigned cell_or(unsigned v) {
 // to decrease or moves by at most 1e-15 of itself.  FLOAT_START: a float
 // Newton estimate plus one unconditional double step (which lands at or
 // above the root by convexity) replaces the start min(g/beta, (g/alpha)^.25).
-template <bool FLOAT_START>
+// Positive root of alpha T^4 + beta T = g (alpha >= 0, beta > 0, g >= 0).
+// f is increasing and convex on T > 0, so Newton from any point at or above
+// the root decreases monotonically onto it.  Double states: start at
+// min(g/beta, (g/alpha)^(1/4)) and stop when an iterate fails to decrease or
+// moves by at most 1e-15 of itself.  Float states: the same iteration in
+// float to a relative 1e-7, then one Newton step in double (the float
+// root's error ~1e-7 becomes ~1e-14).  Returns 1 if the iteration did not
+// converge within max_iter.
+__device__ __forceinline__ float fp_of(float af, float bf, float t) {
+  return fmaf(4.0f * af * t * t, t, bf);
+}
+
+template <bool FLOAT_STATE>
 __device__ __forceinline__ int quartic_root(double alpha, double beta, double g, int max_iter,
                                             double *T_out) {
-  double T = g / beta;
-  if (alpha > 0.0) T = fmin(T, sqrt(sqrt(g / alpha)));
-  int it = 0;
-  if (FLOAT_START) {
+  if (FLOAT_STATE) {
     const float af = (float)alpha, bf = (float)beta, gf = (float)g;
-    float t = (float)T;
-    for (int k = 0; k < 48; ++k) {
+    float t = __fdividef(gf, bf);
+    if (af > 0.0f) t = fminf(t, sqrtf(sqrtf(__fdividef(gf, af))));
+    bool done = false;
+    for (int it = 0; it < max_iter && !done; ++it) {
       const float t2 = t * t;
       const float f = fmaf(af * t2, t2, fmaf(bf, t, -gf));
       const float fp = fmaf(4.0f * af * t2, t, bf);
-      const float tn = t - f / fp;
-      if (!(tn < t)) break;
-      const bool conv = (t - tn <= 1e-7f * t);
-      t = tn;
-      if (conv) break;
+      const float tn = t - __fdividef(f, fp);
+      if (!(tn < t)) {
+        done = true;
+      } else {
+        done = (t - tn <= 1e-7f * t);
+        t = tn;
+      }
     }
-    if (t > 0.0f && isfinite(t) && (double)t < T) {
-      double Tf = t, T2 = Tf * Tf;
-      const double f = fma(alpha * T2, T2, fma(beta, Tf, -g));
-      const double fp = fma(4.0 * alpha * T2, Tf, beta);
-      const double Tn = Tf - f / fp;
-      if (Tn <= T) T = Tn;
-      it = 1;
+    if (isfinite(t) && t >= 0.0f && isfinite(fp_of(af, bf, t))) {
+      if (!done) {
+        *T_out = t;
+        return 1;
+      }
+      const double T = t, T2 = T * T;
+      const double f = fma(alpha * T2, T2, fma(beta, T, -g));
+      const double fp = fma(4.0 * alpha * T2, T, beta);
+      double r = (double)__frcp_rn((float)fp);
+      r = fma(r, fma(-fp, r, 1.0), r);
+      *T_out = fma(-f, r, T);
+      return 0;
     }
+    // coefficients outside float range: solve in double below
   }
+  double T = g / beta;
+  if (alpha > 0.0) T = fmin(T, sqrt(sqrt(g / alpha)));
   bool done = false;
+  int it = 0;
   while (!done && it < max_iter) {
     const double T2 = T * T;
     const double f = fma(alpha * T2, T2, fma(beta, T, -g));
@@ -118,12 +140,52 @@ __device__ __forceinline__ int quartic_root(double alpha, double beta, double g,
   return done ? 0 : 1;
 }
 
+constexpr int MAXS = 1024;  // face slots a block stages in shared memory
+
 template <typename R> struct Shared {
+  typename SlotOf<R>::type slot[MAXS];  // the block's face slots, in slot order
+  int32_t nbr[MAXS];
   R ws[CPB], sI[CPB], sG[CPB];  // comoving weight sum and the two sums of Eq. (Jcom)
   R q[CPB];                     // dt cbar rho (kP B + kS J) per interior cell
   R dE[CPB], dF[3][CPB];        // sum w (I* - I') and sum w n (I* - I')
   unsigned bad[CPB];
 };
+
+// sum_f u I_up over slots [k0, k1) of one cell, for the thread's angle pairs
+template <typename R, int PPT, bool MOVING, typename S>
+__device__ __forceinline__ void face_sum(const S *__restrict__ slot, const int32_t *__restrict__ nbr,
+                                         int64_t k0, int64_t k1, const R *__restrict__ I_in, int A,
+                                         int H, int sub, const R (&nx)[PPT], const R (&ny)[PPT],
+                                         const R (&nz)[PPT], const R (&Ia)[PPT],
+                                         const R (&Ib)[PPT], R (&acca)[PPT], R (&accb)[PPT]) {
+#pragma unroll 2
+  for (int64_t k = k0; k < k1; ++k) {
+    const int32_t nb = nbr[k];
+    const S s = slot[k];
+    const R *In = I_in + (size_t)nb * A;
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      const int p = sub + KT * j;
+      if (p < H) {
+        const R d = fma(nx[j], s.sx, fma(ny[j], s.sy, nz[j] * s.sz));
+        if (MOVING) {
+          const R ua = d - s.w, ub = -d - s.w;
+          R va = Ia[j], vb = Ib[j];
+          if (ua < R(0)) va = __ldg(In + p);
+          if (ub < R(0)) vb = __ldg(In + p + H);
+          acca[j] = fma(ua, va, acca[j]);
+          accb[j] = fma(ub, vb, accb[j]);
+        } else {
+          // u_a = d, u_b = -d: the inflow side of the pair reads the neighbour
+          const bool out = d > R(0);
+          const R v = __ldg(In + (out ? p + H : p));
+          acca[j] = fma(d, out ? Ia[j] : v, acca[j]);
+          accb[j] = fma(-d, out ? v : Ib[j], accb[j]);
+        }
+      }
+    }
+  }
+}
 
 template <typename R, int PPT, bool MOVING>
 __global__ void __launch_bounds__(NT) step_kernel(const StepArgs<R> a) {
@@ -151,33 +213,25 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepArgs<R> a) {
     acca[j] = R(0);
     accb[j] = R(0);
   }
-  const int64_t k0 = a.ptr[c], k1 = a.ptr[c + 1];
-  for (int64_t k = k0; k < k1; ++k) {
-    const int32_t nb = __ldg(a.nbr + k);
-    const auto s = load_slot<R>(a.slot + k);
-    const R *In = a.I_in + (size_t)nb * A;
-#pragma unroll
-    for (int j = 0; j < PPT; ++j) {
-      const int p = sub + KT * j;
-      if (p < H) {
-        const R d = fma(nx[j], s.sx, fma(ny[j], s.sy, nz[j] * s.sz));
-        if (MOVING) {
-          const R ua = d - s.w, ub = -d - s.w;
-          R va = Ia[j], vb = Ib[j];
-          if (ua < R(0)) va = __ldg(In + p);
-          if (ub < R(0)) vb = __ldg(In + p + H);
-          acca[j] = fma(ua, va, acca[j]);
-          accb[j] = fma(ub, vb, accb[j]);
-        } else {
-          // u_a = d, u_b = -d: the inflow side of the pair reads the neighbour
-          const bool out = d > R(0);
-          const R v = __ldg(In + (out ? p + H : p));
-          acca[j] = fma(d, out ? Ia[j] : v, acca[j]);
-          accb[j] = fma(-d, out ? v : Ib[j], accb[j]);
-        }
-      }
+  // stage the block's face slots (contiguous: cells are consecutive)
+  const int64_t cb0 = (int64_t)blockIdx.x * CPB;
+  const int64_t cb1 = cb0 + CPB < a.n_cells ? cb0 + CPB : a.n_cells;
+  const int64_t kb = a.ptr[cb0];
+  const int64_t cnt = a.ptr[cb1] - kb;
+  const bool staged = cnt <= MAXS;  // uniform over the block
+  if (staged) {
+    for (int i = threadIdx.x; i < cnt; i += NT) {
+      sh.slot[i] = load_slot<R>(a.slot + kb + i);
+      sh.nbr[i] = __ldg(a.nbr + kb + i);
     }
   }
+  __syncthreads();
+  if (staged)
+    face_sum<R, PPT, MOVING>(sh.slot, sh.nbr, a.ptr[c] - kb, a.ptr[c + 1] - kb, a.I_in, A, H, sub,
+                             nx, ny, nz, Ia, Ib, acca, accb);
+  else
+    face_sum<R, PPT, MOVING>(a.slot, a.nbr, a.ptr[c], a.ptr[c + 1], a.I_in, A, H, sub, nx, ny, nz,
+                             Ia, Ib, acca, accb);
   const R dtv = a.dt_r * a.inv_vol[c];
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
@@ -231,19 +285,19 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepArgs<R> a) {
       const double SI = (double)(sh.sI[lane] * iw), SG = (double)(sh.sG[lane] * iw);
       const double dcr = a.dt * a.cbar * g.rho;
       const double D = 1.0 - dcr * g.kS * SG;
-      const double rcv = g.rho * a.rcv;
-      const double kin = 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) / g.rho;
-      const double Tn = (d.e - kin) / rcv;
-      const double alpha = a.dt * a.c * g.rho * g.kP * a.a_rad * (1.0 - dcr * g.kJ * SG / D);
-      const double gq = rcv * Tn + a.dt * a.c * g.rho * 4.0 * kPi * g.kJ * SI / D;
+      const double rD = 1.0 / D;
+      const double kin = 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * g.inv_rho;
+      const double Tn = (d.e - kin) * g.inv_rcv;
+      const double alpha = a.dt * a.c * g.rho * g.kP * a.a_rad * (1.0 - dcr * g.kJ * SG * rD);
+      const double gq = g.rcv * Tn + a.dt * a.c * g.rho * 4.0 * kPi * g.kJ * SI * rD;
       double T = 0.0;
       if (!(gq >= 0.0) || !(alpha >= 0.0)) {
         bad |= ST_NONFINITE;
-      } else if (quartic_root<sizeof(R) == 4>(alpha, rcv, gq, a.newton_max_iter, &T)) {
+      } else if (quartic_root<sizeof(R) == 4>(alpha, g.rcv, gq, a.newton_max_iter, &T)) {
         bad |= ST_NONCONV;
       }
-      const double B = a.a_rad * (T * T) * (T * T) / (4.0 * kPi);
-      const double J = (SI + dcr * g.kP * B * SG) / D;
+      const double B = a.a_rad * (T * T) * (T * T) * (1.0 / (4.0 * kPi));
+      const double J = (SI + dcr * g.kP * B * SG) * rD;
       q = R(dcr * (g.kP * B + g.kS * J));
     }
     sh.q[lane] = q;
@@ -337,7 +391,7 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepArgs<R> a) {
         d.my += dy;
         d.mz += dz;
         a.gd[cl] = d;
-        const double ir = 1.0 / a.gs[cl].rho;  // frame velocity of the next step
+        const double ir = a.gs[cl].inv_rho;  // frame velocity of the next step
         a.cellv[4 * cl] = R(d.mx * ir);
         a.cellv[4 * cl + 1] = R(d.my * ir);
         a.cellv[4 * cl + 2] = R(d.mz * ir);

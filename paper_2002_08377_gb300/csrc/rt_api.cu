@@ -160,8 +160,8 @@ template <typename R> int build_device_mesh(rt_state *s, const rt_mesh_desc *m,
   for (int a = 0; a < A; ++a) {
     for (int d = 0; d < 3; ++d) dir[4 * a + d] = (R)m->angle_dir[3 * a + d];
     dir[4 * a + 3] = 0;
-    wt[a] = (R)m->angle_w[a];
   }
+  for (int q = 0; q < A; ++q) wt[q] = (R)m->angle_w[angle_of_position(q, A / 2)];
   R *dd = nullptr, *dw = nullptr;
   RT_CUDA(s, upload(s, &dd, dir));
   RT_CUDA(s, upload(s, &dw, wt));
@@ -311,9 +311,14 @@ int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state 
                                     : build_device_mesh<double>(s, m, slot_of);
   if (r != RT_OK) return bail(r);
   std::vector<double> vol_int(N), dir64(3 * (size_t)A), wt64(A);
+  std::vector<int32_t> angle_of(A);
   for (int64_t ic = 0; ic < N; ++ic) vol_int[ic] = m->cell_volume[s->cell_of[ic]];
-  std::memcpy(dir64.data(), m->angle_dir, sizeof(double) * 3 * A);
-  std::memcpy(wt64.data(), m->angle_w, sizeof(double) * A);
+  for (int q = 0; q < A; ++q) {
+    const int a = angle_of_position(q, A / 2);
+    angle_of[q] = a;
+    for (int d = 0; d < 3; ++d) dir64[3 * q + d] = m->angle_dir[3 * a + d];
+    wt64[q] = m->angle_w[a];
+  }
 #define CK(call)                                  \
   do {                                            \
     cudaError_t e_ = (call);                      \
@@ -323,6 +328,7 @@ int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state 
   CK(upload(s, &s->d_volume, vol_int));
   CK(upload(s, &s->d_dir64, dir64));
   CK(upload(s, &s->d_wt64, wt64));
+  CK(upload(s, &s->d_angle_of, angle_of));
   CK(dalloc(s, &s->d_gs, N));
   CK(dalloc(s, &s->d_gd, N));
   CK(dalloc(s, &s->d_kind, N));
@@ -437,12 +443,15 @@ int rt_set_cells(rt_state *s, const uint8_t *kind, const double *tau, const doub
       RT_CUDA(s, dalloc_bytes(s, &s->d_I0, (size_t)n_rows * A * s->rsize));
       s->n_rows = n_rows;
     }
+    // rows in the internal (pair-interleaved) angle order
+    std::vector<double> rows((size_t)n_rows * A);
+    for (int64_t r = 0; r < n_rows; ++r)
+      for (int q = 0; q < A; ++q) rows[r * A + q] = I0[r * A + angle_of_position(q, A / 2)];
     if (s->precision == RT_FP32) {
-      std::vector<float> f((size_t)n_rows * A);
-      for (size_t i = 0; i < f.size(); ++i) f[i] = (float)I0[i];
+      std::vector<float> f(rows.begin(), rows.end());
       RT_CUDA(s, cudaMemcpy(s->d_I0, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
     } else {
-      RT_CUDA(s, cudaMemcpy(s->d_I0, I0, (size_t)n_rows * A * 8, cudaMemcpyHostToDevice));
+      RT_CUDA(s, cudaMemcpy(s->d_I0, rows.data(), rows.size() * 8, cudaMemcpyHostToDevice));
     }
   }
   RT_CUDA(s, cudaStreamSynchronize(s->stream));
@@ -638,7 +647,7 @@ const char *rt_last_error(const rt_state *s) { return s ? s->err.c_str() : "null
 void rt_destroy(rt_state *s) {
   if (!s) return;
   if (s->stream || true) cudaStreamSynchronize(s->stream);
-  void *bufs[] = {s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
+  void *bufs[] = {s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
                   s->d_gd, s->d_kind, s->d_aux, s->d_bc_row, s->d_I0, s->d_ext, s->d_dir, s->d_wt,
                   s->d_dir64, s->d_wt64, s->d_I[0], s->d_I[1], s->d_status, s->d_bad,
                   s->d_scratch, s->d_out16};

@@ -10,26 +10,28 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// dst[ic][:] = src[cell_of[ic]][:]  (caller order -> internal order)
+// dst[ic][q] = src[cell_of[ic]][angle_of[q]]  (caller order -> internal order)
 template <typename R>
 __global__ void permute_in_kernel(const R *__restrict__ src, R *__restrict__ dst,
-                                  const int64_t *__restrict__ cell_of, int64_t n, int A) {
+                                  const int64_t *__restrict__ cell_of,
+                                  const int32_t *__restrict__ angle_of, int64_t n, int A) {
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   if (row >= n) return;
   const R *s = src + (size_t)cell_of[row] * A;
   R *d = dst + (size_t)row * A;
-  for (int k = threadIdx.x % 32; k < A; k += 32) d[k] = s[k];
+  for (int k = threadIdx.x % 32; k < A; k += 32) d[k] = s[angle_of[k]];
 }
 
-// dst[cell_of[ic]][:] = src[ic][:]  (internal order -> caller order)
+// dst[cell_of[ic]][angle_of[q]] = src[ic][q]  (internal order -> caller order)
 template <typename R>
 __global__ void permute_out_kernel(const R *__restrict__ src, R *__restrict__ dst,
-                                   const int64_t *__restrict__ cell_of, int64_t n, int A) {
+                                   const int64_t *__restrict__ cell_of,
+                                   const int32_t *__restrict__ angle_of, int64_t n, int A) {
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   if (row >= n) return;
   const R *s = src + (size_t)row * A;
   R *d = dst + (size_t)cell_of[row] * A;
-  for (int k = threadIdx.x % 32; k < A; k += 32) d[k] = s[k];
+  for (int k = threadIdx.x % 32; k < A; k += 32) d[angle_of[k]] = s[k];
 }
 
 // K_c = max_a (1/V_c) sum_f max(u_fa, 0), max over cells into *kmax (as the
@@ -210,10 +212,11 @@ unsigned rows_grid(int64_t n) { return (unsigned)((n + kThreads / 32 - 1) / (kTh
 cudaError_t launch_permute_in(rt_state *s, const void *src, void *dst) {
   if (s->precision == RT_FP32)
     permute_in_kernel<float><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
-        (const float *)src, (float *)dst, s->d_cell_of, s->n_cells, s->n_angles);
+        (const float *)src, (float *)dst, s->d_cell_of, s->d_angle_of, s->n_cells, s->n_angles);
   else
     permute_in_kernel<double><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
-        (const double *)src, (double *)dst, s->d_cell_of, s->n_cells, s->n_angles);
+        (const double *)src, (double *)dst, s->d_cell_of, s->d_angle_of, s->n_cells,
+        s->n_angles);
   s->launches++;
   return cudaGetLastError();
 }
@@ -221,10 +224,11 @@ cudaError_t launch_permute_in(rt_state *s, const void *src, void *dst) {
 cudaError_t launch_permute_out(rt_state *s, const void *src, void *dst) {
   if (s->precision == RT_FP32)
     permute_out_kernel<float><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
-        (const float *)src, (float *)dst, s->d_cell_of, s->n_cells, s->n_angles);
+        (const float *)src, (float *)dst, s->d_cell_of, s->d_angle_of, s->n_cells, s->n_angles);
   else
     permute_out_kernel<double><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
-        (const double *)src, (double *)dst, s->d_cell_of, s->n_cells, s->n_angles);
+        (const double *)src, (double *)dst, s->d_cell_of, s->d_angle_of, s->n_cells,
+        s->n_angles);
   s->launches++;
   return cudaGetLastError();
 }

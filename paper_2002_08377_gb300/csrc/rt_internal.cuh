@@ -57,8 +57,8 @@ template <typename R> struct StepArgs {
   const int32_t *bc_row;    // [N]
   const R *I0;              // [rows][A]
   double *ext;              // [N][4]
-  const R *dir;             // [A][4] (x, y, z, 0)
-  const R *wt;              // [A]
+  const R *dir;             // [A][4] (x, y, z, 0), caller angle order
+  const R *wt2;             // [A/2][2] (w_p, w_{p+A/2})
   const R *I_in;            // [N][A]
   R *I_out;                 // [N][A]
   R *cellv;                 // [N][4] (v_x, v_y, v_z, rho (kappa_J + kappa_s))
@@ -70,6 +70,12 @@ template <typename R> struct StepArgs {
 };
 
 }  // namespace rt
+
+// Internal intensity rows store the antipodal pairs side by side: position
+// 2p holds angle p and position 2p + 1 holds angle p + A/2 (p < A/2).
+__host__ __device__ inline int angle_of_position(int q, int half) {
+  return (q & 1) ? (q >> 1) + half : (q >> 1);
+}
 
 // Opaque state behind the C ABI.
 struct rt_state {
@@ -107,10 +113,11 @@ struct rt_state {
   void *d_I0 = nullptr;
   double *d_ext = nullptr;
   void *d_cellv = nullptr;  // [N][4] in the state precision
-  void *d_dir = nullptr;
-  void *d_wt = nullptr;
-  double *d_dir64 = nullptr;  // [A][3] double, for moments
-  double *d_wt64 = nullptr;
+  void *d_dir = nullptr;       // [A][4], caller angle order
+  void *d_wt = nullptr;        // [A/2][2] weights of the pairs (p, p + A/2)
+  double *d_dir64 = nullptr;   // [A][3] double, internal angle order
+  double *d_wt64 = nullptr;    // [A], internal angle order
+  int32_t *d_angle_of = nullptr;  // internal angle position -> caller angle
   void *d_I[2] = {nullptr, nullptr};
   int cur = 0;
   unsigned *d_status = nullptr;

@@ -2,23 +2,24 @@
 // source update with gas exchange (Sec. 3.3), boundary cells (Sec. 3.5) and
 // emitter cells (Sec. 3.6), one kernel per step.
 //
-// Block = 32 cells x 8 threads.  Thread `sub` of a cell owns the angle pairs
-// p = sub + 8 j (j < PPT) and their antipodes p + A/2; the flux coefficient
-// of the antipode through a face is u(p + A/2) = -(n_p . s) - w, so one dot
-// product serves two angles and, on a static mesh, exactly one of the two
-// needs the neighbour's value.  The face sum runs in the cell's slot order
-// (no atomics, deterministic).
+// Layout: the intensity row of a cell stores the A/2 antipodal pairs
+// (angle p, angle p + A/2) side by side, so one 8-byte (float) or 16-byte
+// (double) load fetches a pair.  The flux coefficient of the antipode through
+// a face is u(p + A/2) = -(n_p . s) - w, so one dot product serves both
+// angles; on a static mesh exactly one of the two is inflow.
 //
-// Phases (separated by __syncthreads):
-//   A  all threads: transport, comoving weights, angular sums (precision R);
-//      each cell's 8 lanes reduce with shuffles into shared memory;
+// Block = 32 cells x 8 threads; thread `sub` of a cell owns the pairs
+// p = sub + 8 j (j < PPT).  Phases (separated by __syncthreads):
+//   A  all threads: transport over the cell's faces in slot order (no
+//      atomics, deterministic), comoving weights and the angular sums of
+//      Eq. (Jcom); each cell's 8 lanes reduce with shuffles;
 //   B  warp 0, one lane per cell: the gas temperature quartic in double
-//      (FP32 states start Newton from a float estimate);
+//      (float states: float Newton plus one double Newton step);
 //   C  all threads: new intensities, store, radiation change per cell;
 //   D  warp 0, one lane per cell: gas energy / momentum (or tally) update in
-//      double.
-// Keeping the double-precision work lane-per-cell matters on GB300, whose
-// FP64 rate is a small fraction of its FP32 rate.
+//      double (Eqs. gas1, gas2).
+// The double-precision work is lane-per-cell because GB300's FP64 rate is a
+// small fraction of its FP32 rate.  Float states use the packed f32x2 FMA.
 #include <cuda_runtime.h>
 
 #include "rt_internal.cuh"
@@ -26,9 +27,43 @@
 namespace rt {
 namespace {
 
-constexpr int KT = 8;            // threads per cell
-constexpr int CPB = 32;          // cells per block
-constexpr int NT = KT * CPB;     // threads per block
+constexpr int KT = 8;         // threads per cell
+constexpr int CPB = 32;       // cells per block
+constexpr int NT = KT * CPB;  // threads per block
+constexpr int MAXS = 1024;    // face slots a block stages in shared memory
+
+// ------------------------------------------------------------ pair arithmetic
+template <typename R> struct P2;
+template <> struct P2<float> { using t = float2; };
+template <> struct P2<double> { using t = double2; };
+template <typename R> using pair_t = typename P2<R>::t;
+
+__device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x, a.y * b.y);
+}
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 padd(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+
+// Reciprocal: float uses the hardware approximation (relative error ~1e-7,
+// inside the float state's error budget); double refines the float estimate
+// with two Newton steps (about 1 ulp).  Arguments are 1 + x (x >= 0) and
+// Gamma^2, far inside float range.
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp(double x) {
+  double r = (double)__fdividef(1.0f, (float)x);
+  r = fma(r, fma(-x, r, 1.0), r);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return r;
+}
 
 template <typename R> __device__ __forceinline__ typename SlotOf<R>::type load_slot(
     const typename SlotOf<R>::type *p);
@@ -40,18 +75,6 @@ template <> __device__ __forceinline__ SlotD load_slot<double>(const SlotD *p) {
   const double2 *q = reinterpret_cast<const double2 *>(p);
   double2 a = __ldg(q), b = __ldg(q + 1);
   return {a.x, a.y, b.x, b.y};
-}
-
-// Reciprocal: the correctly rounded float reciprocal, or in double the
-// float estimate refined by two Newton steps (|error| ~ 1 ulp); arguments
-// here are 1 + x (x >= 0) and Gamma^2, well inside float range.
-template <typename R> __device__ __forceinline__ R rcp(R x);
-template <> __device__ __forceinline__ float rcp<float>(float x) { return __frcp_rn(x); }
-template <> __device__ __forceinline__ double rcp<double>(double x) {
-  double r = (double)__frcp_rn((float)x);
-  r = fma(r, fma(-x, r, 1.0), r);
-  r = fma(r, fma(-x, r, 1.0), r);
-  return r;
 }
 
 template <typename T> __device__ __forceinline__ T cell_sum(T v) {
@@ -66,20 +89,22 @@ __device__ __forceinline__ unsigned cell_or(unsigned v) {
   return v;
 }
 
-// Positive root of alpha T^4 + beta T = g (alpha >= 0, beta > 0, g >= 0).
-// f is increasing and convex on T > 0, so Newton from any point at or above
-// the root decreases monotonically onto it; it stops when an iterate fails
-// to decrease or moves by at most 1e-15 of itself.  FLOAT_START: a float
-// Newton estimate plus one unconditional double step (which lands at or
-// above the root by convexity) replaces the start min(g/beta, (g/alpha)^.25).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Positive root of alpha T^4 + beta T = g (alpha >= 0, beta > 0, g >= 0).
 // f is increasing and convex on T > 0, so Newton from any point at or above
 // the root decreases monotonically onto it.  Double states: start at
 // min(g/beta, (g/alpha)^(1/4)) and stop when an iterate fails to decrease or
 // moves by at most 1e-15 of itself.  Float states: the same iteration in
 // float to a relative 1e-7, then one Newton step in double (the float
-// root's error ~1e-7 becomes ~1e-14).  Returns 1 if the iteration did not
-// converge within max_iter.
+// root's error ~1e-7 becomes ~1e-14); coefficients outside float range fall
+// back to the double iteration.  Returns 1 if it did not converge.
 __device__ __forceinline__ float fp_of(float af, float bf, float t) {
   return fmaf(4.0f * af * t * t, t, bf);
 }
@@ -112,12 +137,9 @@ __device__ __forceinline__ int quartic_root(double alpha, double beta, double g,
       const double T = t, T2 = T * T;
       const double f = fma(alpha * T2, T2, fma(beta, T, -g));
       const double fp = fma(4.0 * alpha * T2, T, beta);
-      double r = (double)__frcp_rn((float)fp);
-      r = fma(r, fma(-fp, r, 1.0), r);
-      *T_out = fma(-f, r, T);
+      *T_out = fma(-f, rcp(fp), T);
       return 0;
     }
-    // coefficients outside float range: solve in double below
   }
   double T = g / beta;
   if (alpha > 0.0) T = fmin(T, sqrt(sqrt(g / alpha)));
@@ -140,47 +162,44 @@ __device__ __forceinline__ int quartic_root(double alpha, double beta, double g,
   return done ? 0 : 1;
 }
 
-constexpr int MAXS = 1024;  // face slots a block stages in shared memory
-
 template <typename R> struct Shared {
   typename SlotOf<R>::type slot[MAXS];  // the block's face slots, in slot order
   int32_t nbr[MAXS];
+  GasStatic gs[CPB];  // gas of the block's cells, prefetched for warp 0
+  GasDyn gd[CPB];
   R ws[CPB], sI[CPB], sG[CPB];  // comoving weight sum and the two sums of Eq. (Jcom)
   R q[CPB];                     // dt cbar rho (kP B + kS J) per interior cell
   R dE[CPB], dF[3][CPB];        // sum w (I* - I') and sum w n (I* - I')
   unsigned bad[CPB];
 };
 
-// sum_f u I_up over slots [k0, k1) of one cell, for the thread's angle pairs
+// sum_f u I_up over slots [k0, k1) of one cell for the thread's pairs
 template <typename R, int PPT, bool MOVING, typename S>
 __device__ __forceinline__ void face_sum(const S *__restrict__ slot, const int32_t *__restrict__ nbr,
                                          int64_t k0, int64_t k1, const R *__restrict__ I_in, int A,
-                                         int H, int sub, const R (&nx)[PPT], const R (&ny)[PPT],
-                                         const R (&nz)[PPT], const R (&Ia)[PPT],
-                                         const R (&Ib)[PPT], R (&acca)[PPT], R (&accb)[PPT]) {
+                                         int sub, const R (&nx)[PPT], const R (&ny)[PPT],
+                                         const R (&nz)[PPT], const pair_t<R> (&I2)[PPT],
+                                         pair_t<R> (&acc)[PPT], int npairs_lane) {
+  using V = pair_t<R>;
 #pragma unroll 2
   for (int64_t k = k0; k < k1; ++k) {
     const int32_t nb = nbr[k];
     const S s = slot[k];
-    const R *In = I_in + (size_t)nb * A;
+    const V *In = reinterpret_cast<const V *>(I_in + (size_t)nb * A) + sub;
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
-      const int p = sub + KT * j;
-      if (p < H) {
+      if (j < npairs_lane) {
+        const V v = In[KT * j];
         const R d = fma(nx[j], s.sx, fma(ny[j], s.sy, nz[j] * s.sz));
         if (MOVING) {
           const R ua = d - s.w, ub = -d - s.w;
-          R va = Ia[j], vb = Ib[j];
-          if (ua < R(0)) va = __ldg(In + p);
-          if (ub < R(0)) vb = __ldg(In + p + H);
-          acca[j] = fma(ua, va, acca[j]);
-          accb[j] = fma(ub, vb, accb[j]);
+          const V up = mk(ua > R(0) ? I2[j].x : v.x, ub > R(0) ? I2[j].y : v.y);
+          acc[j] = pfma(mk(ua, ub), up, acc[j]);
         } else {
-          // u_a = d, u_b = -d: the inflow side of the pair reads the neighbour
+          // u_a = d, u_b = -d: exactly one of the pair reads the neighbour
           const bool out = d > R(0);
-          const R v = __ldg(In + (out ? p + H : p));
-          acca[j] = fma(d, out ? Ia[j] : v, acca[j]);
-          accb[j] = fma(-d, out ? v : Ib[j], accb[j]);
+          const V up = mk(out ? I2[j].x : v.x, out ? v.y : I2[j].y);
+          acc[j] = pfma(mk(d, -d), up, acc[j]);
         }
       }
     }
@@ -188,32 +207,44 @@ __device__ __forceinline__ void face_sum(const S *__restrict__ slot, const int32
 }
 
 template <typename R, int PPT, bool MOVING>
-__global__ void __launch_bounds__(NT) step_kernel(const StepArgs<R> a) {
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const StepArgs<R> a) {
+  using V = pair_t<R>;
   __shared__ Shared<R> sh;
   const int lc = threadIdx.x / KT;
   const int sub = threadIdx.x % KT;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t cell = (int64_t)blockIdx.x * CPB + lc;
   const bool live = cell < a.n_cells;
   const int64_t c = live ? cell : a.n_cells - 1;  // dead lanes shadow the last cell
   const int A = a.n_angles, H = a.half;
+  // pairs owned by this lane: p = sub + KT j < H
+  const int np = (H - sub + KT - 1) / KT;
+
+  // warp 0 prefetches its cells' gas state for phases B and D
+  const int64_t cl = (int64_t)blockIdx.x * CPB + lane;  // warp 0: lane-per-cell
+  if (warp == 0 && cl < a.n_cells) {
+    const char *g = reinterpret_cast<const char *>(a.gs + cl);
+    const char *d = reinterpret_cast<const char *>(a.gd + cl);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cp_async16(reinterpret_cast<char *>(&sh.gs[lane]) + 16 * k, g + 16 * k);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) cp_async16(reinterpret_cast<char *>(&sh.gd[lane]) + 16 * k, d + 16 * k);
+  }
 
   // ---------------- phase A: transport, I* = I - dt/V sum_f u I_up
-  R nx[PPT], ny[PPT], nz[PPT], Ia[PPT], Ib[PPT], acca[PPT], accb[PPT];
-  const R *Ic = a.I_in + (size_t)c * A;
+  R nx[PPT], ny[PPT], nz[PPT];
+  V I2[PPT], acc[PPT];
+  const V *Ic = reinterpret_cast<const V *>(a.I_in + (size_t)c * A) + sub;
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
-    const int p = sub + KT * j;
-    const bool v = p < H;
-    const int pp = v ? p : 0;
-    nx[j] = a.dir[4 * pp];
-    ny[j] = a.dir[4 * pp + 1];
-    nz[j] = a.dir[4 * pp + 2];
-    Ia[j] = v ? Ic[pp] : R(0);
-    Ib[j] = v ? Ic[pp + H] : R(0);
-    acca[j] = R(0);
-    accb[j] = R(0);
+    const int p = j < np ? sub + KT * j : 0;
+    nx[j] = a.dir[4 * p];
+    ny[j] = a.dir[4 * p + 1];
+    nz[j] = a.dir[4 * p + 2];
+    I2[j] = j < np ? Ic[KT * j] : mk(R(0), R(0));
+    acc[j] = mk(R(0), R(0));
   }
-  // stage the block's face slots (contiguous: cells are consecutive)
+  // stage the block's face slots (contiguous: the block's cells are consecutive)
   const int64_t cb0 = (int64_t)blockIdx.x * CPB;
   const int64_t cb1 = cb0 + CPB < a.n_cells ? cb0 + CPB : a.n_cells;
   const int64_t kb = a.ptr[cb0];
@@ -227,60 +258,57 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepArgs<R> a) {
   }
   __syncthreads();
   if (staged)
-    face_sum<R, PPT, MOVING>(sh.slot, sh.nbr, a.ptr[c] - kb, a.ptr[c + 1] - kb, a.I_in, A, H, sub,
-                             nx, ny, nz, Ia, Ib, acca, accb);
+    face_sum<R, PPT, MOVING>(sh.slot, sh.nbr, a.ptr[c] - kb, a.ptr[c + 1] - kb, a.I_in, A, sub, nx,
+                             ny, nz, I2, acc, np);
   else
-    face_sum<R, PPT, MOVING>(a.slot, a.nbr, a.ptr[c], a.ptr[c + 1], a.I_in, A, H, sub, nx, ny, nz,
-                             Ia, Ib, acca, accb);
+    face_sum<R, PPT, MOVING>(a.slot, a.nbr, a.ptr[c], a.ptr[c + 1], a.I_in, A, sub, nx, ny, nz, I2,
+                             acc, np);
   const R dtv = a.dt_r * a.inv_vol[c];
 #pragma unroll
-  for (int j = 0; j < PPT; ++j) {
-    Ia[j] = fma(-dtv, acca[j], Ia[j]);  // I* (zero for unused slots)
-    Ib[j] = fma(-dtv, accb[j], Ib[j]);
-  }
+  for (int j = 0; j < PPT; ++j) I2[j] = pfma(mk(-dtv, -dtv), acc[j], I2[j]);  // I*
 
-  // comoving frame (first order in v/c): Gamma = 1 -+ v.n / c, with the
-  // cell's velocity and rho (kJ + kS) kept in the state precision
+  // comoving frame (first order in v/c): Gamma = 1 -+ v.n / c
   const int kind = a.kind[c];
-  const R vx = a.cellv[4 * c], vy = a.cellv[4 * c + 1], vz = a.cellv[4 * c + 2];
+  const R icr = a.inv_c_r;
+  const R vxc = a.cellv[4 * c] * icr, vyc = a.cellv[4 * c + 1] * icr,
+          vzc = a.cellv[4 * c + 2] * icr;
   const R xs = a.dt_cbar_r * a.cellv[4 * c + 3];
-  const R inv_c = a.inv_c_r;
-  R Ga[PPT], Gb[PPT];
-  R ws = 0, sI = 0, sG = 0;
+  const V *W2 = reinterpret_cast<const V *>(a.wt2) + sub;  // (w_p, w_{p+H})
+  R Ga[PPT];
+  V ws2 = mk(R(0), R(0)), sI2 = ws2, sG2 = ws2;
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
-    const int p = sub + KT * j;
-    const R vn = (vx * nx[j] + vy * ny[j] + vz * nz[j]) * inv_c;
-    Ga[j] = R(1) - vn;
-    Gb[j] = R(1) + vn;
-    if (p < H) {
-      const R Ga2 = Ga[j] * Ga[j], Gb2 = Gb[j] * Gb[j];
-      const R wca = a.wt[p] * rcp(Ga2), wcb = a.wt[p + H] * rcp(Gb2);
-      const R ra = rcp(R(1) + xs * Ga[j]), rb = rcp(R(1) + xs * Gb[j]);
-      ws += wca + wcb;
-      sI += wca * (Ga2 * Ga2 * Ia[j]) * ra + wcb * (Gb2 * Gb2 * Ib[j]) * rb;
-      sG += wca * Ga[j] * ra + wcb * Gb[j] * rb;
+    Ga[j] = R(1) - fma(vxc, nx[j], fma(vyc, ny[j], vzc * nz[j]));
+    if (j < np) {
+      const V G = mk(Ga[j], R(2) - Ga[j]);
+      const V G2 = pmul(G, G);
+      const V w = W2[KT * j];
+      const V wc = mk(w.x * rcp(G2.x), w.y * rcp(G2.y));
+      const V den = pfma(mk(xs, xs), G, mk(R(1), R(1)));
+      const V t = pmul(wc, mk(rcp(den.x), rcp(den.y)));
+      ws2 = padd(ws2, wc);
+      sI2 = pfma(t, pmul(pmul(G2, G2), I2[j]), sI2);
+      sG2 = pfma(t, G, sG2);
     }
   }
-  ws = cell_sum(ws);
-  sI = cell_sum(sI);
-  sG = cell_sum(sG);
+  const R ws = cell_sum(ws2.x + ws2.y);
+  const R sI = cell_sum(sI2.x + sI2.y);
+  const R sG = cell_sum(sG2.x + sG2.y);
   if (sub == 0) {
     sh.ws[lc] = ws;
     sh.sI[lc] = sI;
     sh.sG[lc] = sG;
   }
+  if (warp == 0) cp_async_wait_all();
   __syncthreads();
 
   // ---------------- phase B: temperature quartic, one lane per cell
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (warp == 0) {
-    const int64_t cl = (int64_t)blockIdx.x * CPB + lane;
     R q = 0;
     unsigned bad = 0;
     if (cl < a.n_cells && a.kind[cl] == RT_CELL_INTERIOR) {
-      const GasStatic g = a.gs[cl];
-      const GasDyn d = a.gd[cl];
+      const GasStatic g = sh.gs[lane];
+      const GasDyn d = sh.gd[lane];
       const R iw = R(1) / sh.ws[lane];
       const double SI = (double)(sh.sI[lane] * iw), SG = (double)(sh.sG[lane] * iw);
       const double dcr = a.dt * a.cbar * g.rho;
@@ -306,59 +334,52 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepArgs<R> a) {
   __syncthreads();
 
   // ---------------- phase C: new intensities and the radiation change
-  R In_a[PPT], In_b[PPT];
+  V In2[PPT];
   if (kind == RT_CELL_BOUNDARY) {
     const double2 ax = a.aux[c];
     const R f = R((ax.x <= a.dt) ? 1.0 : a.dt / ax.x);
-    const R *I0 = a.I0 + (size_t)a.bc_row[c] * A;
+    const V *I0 = reinterpret_cast<const V *>(a.I0 + (size_t)a.bc_row[c] * A) + sub;
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
-      const int p = sub + KT * j;
-      const bool v = p < H;
-      In_a[j] = v ? fma(-f, Ia[j] - I0[p], Ia[j]) : R(0);
-      In_b[j] = v ? fma(-f, Ib[j] - I0[p + H], Ib[j]) : R(0);
-    }
-  } else if (kind == RT_CELL_EMITTER) {
-    const double2 ax = a.aux[c];
-    const R ys = R(a.dt * a.cbar * ax.x);
-    const R isrc = R(ax.y);
-#pragma unroll
-    for (int j = 0; j < PPT; ++j) {
-      const R Ga2 = Ga[j] * Ga[j], Gb2 = Gb[j] * Gb[j];
-      const R Ga4 = Ga2 * Ga2, Gb4 = Gb2 * Gb2;
-      const R ya = ys * Ga[j], yb = ys * Gb[j];
-      In_a[j] = (Ga4 * Ia[j] + ya * isrc) * rcp((R(1) + ya) * Ga4);
-      In_b[j] = (Gb4 * Ib[j] + yb * isrc) * rcp((R(1) + yb) * Gb4);
+      const V t = j < np ? I0[KT * j] : mk(R(0), R(0));
+      In2[j] = mk(fma(-f, I2[j].x - t.x, I2[j].x), fma(-f, I2[j].y - t.y, I2[j].y));
     }
   } else {
-    const R q = sh.q[lc];
+    // interior: I~' = (I~ + q Gamma) / (1 + x Gamma); emitter: the same with
+    // x -> dt cbar (rho kappa)_src and q -> that rate times I_src (Sec. 3.6)
+    R qq = 0, xx = xs;
+    if (kind == RT_CELL_EMITTER) {
+      const double2 ax = a.aux[c];
+      xx = R(a.dt * a.cbar * ax.x);
+      qq = xx * R(ax.y);
+    } else {
+      qq = sh.q[lc];
+    }
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
-      const R Ga2 = Ga[j] * Ga[j], Gb2 = Gb[j] * Gb[j];
-      const R Ga4 = Ga2 * Ga2, Gb4 = Gb2 * Gb2;
-      In_a[j] = (Ga4 * Ia[j] + q * Ga[j]) * rcp((R(1) + xs * Ga[j]) * Ga4);
-      In_b[j] = (Gb4 * Ib[j] + q * Gb[j]) * rcp((R(1) + xs * Gb[j]) * Gb4);
+      const V G = mk(Ga[j], R(2) - Ga[j]);
+      const V G2 = pmul(G, G);
+      const V G4 = pmul(G2, G2);
+      const V num = pfma(mk(qq, qq), G, pmul(G4, I2[j]));
+      const V den = pmul(pfma(mk(xx, xx), G, mk(R(1), R(1))), G4);
+      In2[j] = mk(num.x * rcp(den.x), num.y * rcp(den.y));
     }
   }
   R de = 0, dfx = 0, dfy = 0, dfz = 0;
   unsigned nonfinite = 0;
-  R *Io = a.I_out + (size_t)c * A;
+  V *Io = reinterpret_cast<V *>(a.I_out + (size_t)c * A) + sub;
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
-    const int p = sub + KT * j;
-    if (p < H) {
-      if (live) {
-        Io[p] = In_a[j];
-        Io[p + H] = In_b[j];
-      }
-      if (!isfinite(In_a[j]) || !isfinite(In_b[j])) nonfinite = ST_NONFINITE;
-      const R da = a.wt[p] * (Ia[j] - In_a[j]);
-      const R db = a.wt[p + H] * (Ib[j] - In_b[j]);
-      de += da + db;
-      const R dd = da - db;  // the antipode has direction -n
-      dfx = fma(nx[j], dd, dfx);
-      dfy = fma(ny[j], dd, dfy);
-      dfz = fma(nz[j], dd, dfz);
+    if (j < np) {
+      if (live) Io[KT * j] = In2[j];
+      if (!isfinite(In2[j].x) || !isfinite(In2[j].y)) nonfinite = ST_NONFINITE;
+      const V w = W2[KT * j];
+      const V dd = pmul(w, padd(I2[j], mk(-In2[j].x, -In2[j].y)));
+      de += dd.x + dd.y;
+      const R df = dd.x - dd.y;  // the antipode has direction -n
+      dfx = fma(nx[j], df, dfx);
+      dfy = fma(ny[j], df, dfy);
+      dfz = fma(nz[j], df, dfz);
     }
   }
   de = cell_sum(de);
@@ -376,37 +397,34 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepArgs<R> a) {
   __syncthreads();
 
   // ---------------- phase D: gas exchange (Eqs. gas1, gas2), one lane per cell
-  if (warp == 0) {
-    const int64_t cl = (int64_t)blockIdx.x * CPB + lane;
-    if (cl < a.n_cells) {
-      const double fe = a.c / a.cbar * 4.0 * kPi;
-      const double fm = 4.0 * kPi / a.cbar;  // (4 pi c sum w n dI) / (c cbar)
-      const double dE = fe * (double)sh.dE[lane];
-      const double dx = fm * (double)sh.dF[0][lane], dy = fm * (double)sh.dF[1][lane],
-                   dz = fm * (double)sh.dF[2][lane];
-      if (a.kind[cl] == RT_CELL_INTERIOR) {
-        GasDyn d = a.gd[cl];
-        d.e += dE;
-        d.mx += dx;
-        d.my += dy;
-        d.mz += dz;
-        a.gd[cl] = d;
-        const double ir = a.gs[cl].inv_rho;  // frame velocity of the next step
-        a.cellv[4 * cl] = R(d.mx * ir);
-        a.cellv[4 * cl + 1] = R(d.my * ir);
-        a.cellv[4 * cl + 2] = R(d.mz * ir);
-      } else {
-        double *x = a.ext + 4 * cl;
-        x[0] += dE;
-        x[1] += dx;
-        x[2] += dy;
-        x[3] += dz;
-      }
-      const unsigned bad = sh.bad[lane];
-      if (bad) {
-        atomicOr(a.status, bad);
-        atomicMin(a.bad_cell, (unsigned long long)cl);
-      }
+  if (warp == 0 && cl < a.n_cells) {
+    const double fe = a.c / a.cbar * 4.0 * kPi;
+    const double fm = 4.0 * kPi / a.cbar;  // (4 pi c sum w n dI) / (c cbar)
+    const double dE = fe * (double)sh.dE[lane];
+    const double dx = fm * (double)sh.dF[0][lane], dy = fm * (double)sh.dF[1][lane],
+                 dz = fm * (double)sh.dF[2][lane];
+    if (a.kind[cl] == RT_CELL_INTERIOR) {
+      GasDyn d = sh.gd[lane];
+      d.e += dE;
+      d.mx += dx;
+      d.my += dy;
+      d.mz += dz;
+      a.gd[cl] = d;
+      const double ir = sh.gs[lane].inv_rho;  // frame velocity of the next step
+      a.cellv[4 * cl] = R(d.mx * ir);
+      a.cellv[4 * cl + 1] = R(d.my * ir);
+      a.cellv[4 * cl + 2] = R(d.mz * ir);
+    } else {
+      double *x = a.ext + 4 * cl;
+      x[0] += dE;
+      x[1] += dx;
+      x[2] += dy;
+      x[3] += dz;
+    }
+    const unsigned bad = sh.bad[lane];
+    if (bad) {
+      atomicOr(a.status, bad);
+      atomicMin(a.bad_cell, (unsigned long long)cl);
     }
   }
 }
@@ -428,7 +446,7 @@ template <typename R, int PPT, bool MOVING> cudaError_t launch_t(rt_state *s, do
   a.I0 = reinterpret_cast<const R *>(s->d_I0);
   a.ext = s->d_ext;
   a.dir = reinterpret_cast<const R *>(s->d_dir);
-  a.wt = reinterpret_cast<const R *>(s->d_wt);
+  a.wt2 = reinterpret_cast<const R *>(s->d_wt);
   a.I_in = reinterpret_cast<const R *>(s->d_I[s->cur]);
   a.I_out = reinterpret_cast<R *>(s->d_I[s->cur ^ 1]);
   a.dt = dt;

@@ -16,8 +16,10 @@ LIB = os.path.join(HERE, "librt_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["rt_api.cu", "rt_step.cu", "rt_aux.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
-         "-Xptxas", "-warn-spills"]
+# host code is compiled without FMA contraction so that x86 and Arm hosts
+# build bit-identical face geometry
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off",
+         "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
 _lock = threading.Lock()
 
 

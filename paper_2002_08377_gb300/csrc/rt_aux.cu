@@ -34,11 +34,21 @@ __global__ void permute_out_kernel(const R *__restrict__ src, R *__restrict__ ds
   for (int k = threadIdx.x % 32; k < A; k += 32) d[angle_of[k]] = s[k];
 }
 
+__device__ __forceinline__ double slot_u(const SlotF &s, const double *, int64_t, double x,
+                                         double y, double z) {
+  return x * (double)s.sx + y * (double)s.sy + z * (double)s.sz - (double)s.w;
+}
+__device__ __forceinline__ double slot_u(const SlotD &s, const double *wf, int64_t k, double x,
+                                         double y, double z) {
+  return s.ca * ((x * s.nx + y * s.ny) + z * s.nz) - (wf ? wf[k] : 0.0);
+}
+
 // K_c = max_a (1/V_c) sum_f max(u_fa, 0), max over cells into *kmax (as the
 // bit pattern of a non-negative double, which orders like the value).
 template <typename R>
 __global__ void positivity_kernel(const int64_t *__restrict__ ptr,
                                   const typename SlotOf<R>::type *__restrict__ slot,
+                                  const double *__restrict__ wface,
                                   const double *__restrict__ vol, const double *__restrict__ dir,
                                   int64_t n, int A, unsigned long long *kmax) {
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
@@ -48,8 +58,7 @@ __global__ void positivity_kernel(const int64_t *__restrict__ ptr,
       const double x = dir[3 * a], y = dir[3 * a + 1], z = dir[3 * a + 2];
       double sum = 0.0;
       for (int64_t k = ptr[row]; k < ptr[row + 1]; ++k) {
-        const double u = x * (double)slot[k].sx + y * (double)slot[k].sy + z * (double)slot[k].sz -
-                         (double)slot[k].w;
+        const double u = slot_u(slot[k], wface, k, x, y, z);
         if (u > 0.0) sum += u;
       }
       best = fmax(best, sum / vol[row]);
@@ -238,11 +247,13 @@ cudaError_t launch_positivity(rt_state *s, double *d_kmax) {
   if (e != cudaSuccess) return e;
   if (s->precision == RT_FP32)
     positivity_kernel<float><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
-        s->d_ptr, (const SlotF *)s->d_slot, s->d_volume, s->d_dir64, s->n_cells, s->n_angles,
+        s->d_ptr, (const SlotF *)s->d_slot, s->d_wface, s->d_volume, s->d_dir64, s->n_cells,
+        s->n_angles,
         (unsigned long long *)d_kmax);
   else
     positivity_kernel<double><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
-        s->d_ptr, (const SlotD *)s->d_slot, s->d_volume, s->d_dir64, s->n_cells, s->n_angles,
+        s->d_ptr, (const SlotD *)s->d_slot, s->d_wface, s->d_volume, s->d_dir64, s->n_cells,
+        s->n_angles,
         (unsigned long long *)d_kmax);
   s->launches++;
   return cudaGetLastError();

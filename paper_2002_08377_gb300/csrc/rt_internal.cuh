@@ -13,15 +13,21 @@ namespace rt {
 
 constexpr double kPi = 3.14159265358979323846;
 
-// Directed face slot of one cell, in the cell's outward orientation:
-//   s = cbar * A_f * n_f (outward), w = A_f * w_f . n_f (outward).
-// u_a = n_a . s - w is the volume flux coefficient of angle a; the slot on
-// the other side of the face holds the exact negatives.
+// Directed face slot of one cell, in the cell's outward orientation.  The
+// volume flux coefficient of angle a through the face is
+//   u_a = cbar A_f (n_a . n_f) - A_f (w_f . n_f)       (n_f outward).
+// Float states store s = cbar A_f n_f and w = A_f w_f . n_f and evaluate
+// n_a . s - w with FMAs.  Double states store n_f and cbar A_f and evaluate
+// cbar A_f ((n_ax n_fx + n_ay n_fy) + n_az n_fz) - W without contraction, in
+// the same order as a plain evaluation of the formula: near-tangent faces
+// make this a cancelling dot product whose last bits decide the flux of a
+// faint intensity next to a bright one.  The slot on the other side of a face
+// holds the exact negatives (W in a separate array for double states).
 struct alignas(16) SlotF {
   float sx, sy, sz, w;
 };
 struct alignas(32) SlotD {
-  double sx, sy, sz, w;
+  double nx, ny, nz, ca;
 };
 template <typename R> struct SlotOf;
 template <> struct SlotOf<float> { using type = SlotF; };
@@ -31,7 +37,17 @@ template <> struct SlotOf<double> { using type = SlotD; };
 enum : unsigned {
   ST_NONCONV = 1u,
   ST_NONFINITE = 2u,
+  ST_TIMEOUT = 4u,  // a bounded wait on an mbarrier gave up
 };
+
+// The step kernel works on blocks of CPB consecutive (internal) cells.  Each
+// block stages the intensity rows it reads -- its own cells, then the halo
+// of neighbours outside the block -- into shared memory; a slot's neighbour
+// is then addressed by its block-local row: own cell ic -> ic - first cell,
+// halo entry h -> CPB + h.
+constexpr int CPB = 32;           // cells per block
+constexpr int MAX_SLOTS = 640;    // face slots a block can stage
+constexpr int MAX_ROWS = 160;     // intensity rows a block can stage (own + halo)
 
 // Per-cell constant gas data (double): rho, kappa_P, kappa_J, kappa_s and
 // the derived 1/rho, rho c_v = rho r_gas / (gamma - 1) and its inverse.
@@ -48,8 +64,15 @@ template <typename R> struct StepArgs {
   int32_t n_angles, half;
   const int64_t *ptr;       // [N+1] slot range per internal cell
   const int32_t *nbr;       // [nnz] internal neighbour index
+  const uint16_t *nbr_local;  // [nnz] block-local row of the neighbour
+  const int64_t *halo_ptr;  // [blocks+1] range of each block's halo rows
+  const int32_t *halo;      // halo rows (internal cell index)
+  const uint8_t *block_staged;  // [blocks] 1: rows fit in shared memory
+  int32_t row_cap;          // rows the kernel's shared memory holds
+  int32_t row_stride;       // bytes between staged rows
   const typename SlotOf<R>::type *slot;  // [nnz]
   const R *inv_vol;         // [N]
+  const double *wface;      // [nnz] A_f w_f . n_f of double slots (moving meshes)
   const GasStatic *gs;      // [N]
   GasDyn *gd;               // [N]
   const uint8_t *kind;      // [N]
@@ -101,7 +124,14 @@ struct rt_state {
   // device buffers
   int64_t *d_ptr = nullptr;
   int32_t *d_nbr = nullptr;
+  uint16_t *d_nbr_local = nullptr;
+  int64_t *d_halo_ptr = nullptr;
+  int32_t *d_halo = nullptr;
+  uint8_t *d_block_staged = nullptr;
+  int32_t row_cap = 0, row_stride = 0;
+  int64_t staged_blocks = 0, n_blocks = 0;
   void *d_slot = nullptr;
+  double *d_wface = nullptr;  // double states: per-slot A w . n
   void *d_inv_vol = nullptr;
   int64_t *d_cell_of = nullptr;  // internal -> caller
   double *d_volume = nullptr;    // internal order

@@ -28,9 +28,7 @@ namespace rt {
 namespace {
 
 constexpr int KT = 8;         // threads per cell
-constexpr int CPB = 32;       // cells per block
 constexpr int NT = KT * CPB;  // threads per block
-constexpr int MAXS = 1024;    // face slots a block stages in shared memory
 
 // ------------------------------------------------------------ pair arithmetic
 template <typename R> struct P2;
@@ -77,6 +75,20 @@ template <> __device__ __forceinline__ SlotD load_slot<double>(const SlotD *p) {
   return {a.x, a.y, b.x, b.y};
 }
 
+// n_a . s of a slot (float) or cbar A ((n_ax n_fx + n_ay n_fy) + n_az n_fz)
+// without contraction (double); and the slot's A w . n
+__device__ __forceinline__ float slot_dot(float x, float y, float z, const SlotF &s) {
+  return fmaf(x, s.sx, fmaf(y, s.sy, z * s.sz));
+}
+__device__ __forceinline__ double slot_dot(double x, double y, double z, const SlotD &s) {
+  return __dmul_rn(s.ca, __dadd_rn(__dadd_rn(__dmul_rn(x, s.nx), __dmul_rn(y, s.ny)),
+                                   __dmul_rn(z, s.nz)));
+}
+__device__ __forceinline__ float slot_w(const SlotF &s, const double *, int64_t) { return s.w; }
+__device__ __forceinline__ double slot_w(const SlotD &, const double *wf, int64_t k) {
+  return wf[k];
+}
+
 template <typename T> __device__ __forceinline__ T cell_sum(T v) {
 #pragma unroll
   for (int o = KT / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -95,6 +107,46 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// ---- mbarrier + TMA bulk copy (global -> shared), completion by tx bytes
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes,
+                                              unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for phase `parity` of the barrier with an iteration limit (each
+// try_wait may itself suspend for a bounded time); false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
+  for (int it = 0; it < (1 << 20); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
 }
 
 // Positive root of alpha T^4 + beta T = g (alpha >= 0, beta > 0, g >= 0).
@@ -163,8 +215,7 @@ __device__ __forceinline__ int quartic_root(double alpha, double beta, double g,
 }
 
 template <typename R> struct Shared {
-  typename SlotOf<R>::type slot[MAXS];  // the block's face slots, in slot order
-  int32_t nbr[MAXS];
+  unsigned long long bar;  // completion of the staged intensity rows
   GasStatic gs[CPB];  // gas of the block's cells, prefetched for warp 0
   GasDyn gd[CPB];
   R ws[CPB], sI[CPB], sG[CPB];  // comoving weight sum and the two sums of Eq. (Jcom)
@@ -176,8 +227,9 @@ template <typename R> struct Shared {
 // sum_f u I_up over slots [k0, k1) of one cell for the thread's pairs
 template <typename R, int PPT, bool MOVING, typename S>
 __device__ __forceinline__ void face_sum(const S *__restrict__ slot, const int32_t *__restrict__ nbr,
-                                         int64_t k0, int64_t k1, const R *__restrict__ I_in, int A,
-                                         int sub, const R (&nx)[PPT], const R (&ny)[PPT],
+                                         const double *__restrict__ wface, int64_t k0, int64_t k1,
+                                         const R *__restrict__ I_in, int A, int sub,
+                                         const R (&nx)[PPT], const R (&ny)[PPT],
                                          const R (&nz)[PPT], const pair_t<R> (&I2)[PPT],
                                          pair_t<R> (&acc)[PPT], int npairs_lane) {
   using V = pair_t<R>;
@@ -186,13 +238,14 @@ __device__ __forceinline__ void face_sum(const S *__restrict__ slot, const int32
     const int32_t nb = nbr[k];
     const S s = slot[k];
     const V *In = reinterpret_cast<const V *>(I_in + (size_t)nb * A) + sub;
+    const R w = MOVING ? slot_w(s, wface, k) : R(0);
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
       if (j < npairs_lane) {
         const V v = In[KT * j];
-        const R d = fma(nx[j], s.sx, fma(ny[j], s.sy, nz[j] * s.sz));
+        const R d = slot_dot(nx[j], ny[j], nz[j], s);
         if (MOVING) {
-          const R ua = d - s.w, ub = -d - s.w;
+          const R ua = d - w, ub = -d - w;
           const V up = mk(ua > R(0) ? I2[j].x : v.x, ub > R(0) ? I2[j].y : v.y);
           acc[j] = pfma(mk(ua, ub), up, acc[j]);
         } else {
@@ -205,6 +258,56 @@ __device__ __forceinline__ void face_sum(const S *__restrict__ slot, const int32
     }
   }
 }
+
+// The same sum with the intensity rows staged in shared memory: slot k's
+// neighbour is the block-local row loc[k], rows `stride` bytes apart.
+template <typename R, int PPT, bool MOVING, typename S>
+__device__ __forceinline__ void face_sum_staged(const S *__restrict__ slot,
+                                                const uint16_t *__restrict__ loc,
+                                                const double *__restrict__ wface, int k0, int k1,
+                                                const unsigned char *rows, int stride, int sub,
+                                                const R (&nx)[PPT], const R (&ny)[PPT],
+                                                const R (&nz)[PPT], const pair_t<R> (&I2)[PPT],
+                                                pair_t<R> (&acc)[PPT], int npairs_lane) {
+  using V = pair_t<R>;
+#pragma unroll 2
+  for (int k = k0; k < k1; ++k) {
+    const S s = slot[k];
+    const V *In = reinterpret_cast<const V *>(rows + (int)loc[k] * stride) + sub;
+    const R w = MOVING ? slot_w(s, wface, k) : R(0);
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      if (j < npairs_lane) {
+        const V v = In[KT * j];
+        const R d = slot_dot(nx[j], ny[j], nz[j], s);
+        if (MOVING) {
+          const R ua = d - w, ub = -d - w;
+          const V up = mk(ua > R(0) ? I2[j].x : v.x, ub > R(0) ? I2[j].y : v.y);
+          acc[j] = pfma(mk(ua, ub), up, acc[j]);
+        } else {
+          const bool out = d > R(0);
+          const V up = mk(out ? I2[j].x : v.x, out ? v.y : I2[j].y);
+          acc[j] = pfma(mk(d, -d), up, acc[j]);
+        }
+      }
+    }
+  }
+}
+
+// Shared-memory layout of the staged path: rows, then (float states) the
+// block's face slots and their block-local neighbour rows.
+template <typename R> struct DynLayout {
+  static constexpr bool kSlots = sizeof(R) == 4;  // double slots stay in global memory
+  __host__ __device__ static size_t slot_off(int row_cap, int stride) {
+    return ((size_t)row_cap * stride + 127) & ~(size_t)127;
+  }
+  __host__ __device__ static size_t loc_off(int row_cap, int stride) {
+    return slot_off(row_cap, stride) + (kSlots ? MAX_SLOTS * sizeof(typename SlotOf<R>::type) : 0);
+  }
+  __host__ __device__ static size_t bytes(int row_cap, int stride) {
+    return loc_off(row_cap, stride) + MAX_SLOTS * sizeof(uint16_t);
+  }
+};
 
 template <typename R, int PPT, bool MOVING>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const StepArgs<R> a) {
@@ -232,9 +335,49 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
   }
 
   // ---------------- phase A: transport, I* = I - dt/V sum_f u I_up
+  extern __shared__ __align__(128) unsigned char dyn[];
+  using S = typename SlotOf<R>::type;
+  const int64_t cb0 = (int64_t)blockIdx.x * CPB;
+  const int64_t cb1 = cb0 + CPB < a.n_cells ? cb0 + CPB : a.n_cells;
+  const int64_t kb = a.ptr[cb0];
+  const int cnt = (int)(a.ptr[cb1] - kb);
+  const bool staged = a.block_staged[blockIdx.x] != 0;  // uniform over the block
+  const int stride = a.row_stride;
+  unsigned char *rows = dyn;
+  S *sslot = reinterpret_cast<S *>(dyn + DynLayout<R>::slot_off(a.row_cap, stride));
+  uint16_t *sloc = reinterpret_cast<uint16_t *>(dyn + DynLayout<R>::loc_off(a.row_cap, stride));
+  unsigned timeout = 0;
+  if (staged) {
+    if (threadIdx.x == 0) mbar_init(&sh.bar, 1);
+    __syncthreads();
+    if (warp == 0) {
+      // own rows, then the halo rows, one bulk copy per row
+      const int64_t h0 = a.halo_ptr[blockIdx.x];
+      const int nh = (int)(a.halo_ptr[blockIdx.x + 1] - h0);
+      const int nown = (int)(cb1 - cb0);
+      const unsigned rb = (unsigned)(A * sizeof(R));
+      if (lane == 0) mbar_expect_tx(&sh.bar, rb * (unsigned)(nown + nh));
+      __syncwarp();
+      for (int r = lane; r < nown; r += 32)
+        bulk_copy_g2s(rows + r * stride, a.I_in + (size_t)(cb0 + r) * A, rb, &sh.bar);
+      for (int h = lane; h < nh; h += 32)
+        bulk_copy_g2s(rows + (CPB + h) * stride, a.I_in + (size_t)a.halo[h0 + h] * A, rb,
+                      &sh.bar);
+    }
+    for (int i = threadIdx.x; i < cnt; i += NT) {
+      if (DynLayout<R>::kSlots) sslot[i] = load_slot<R>(a.slot + kb + i);
+      sloc[i] = __ldg(a.nbr_local + kb + i);
+    }
+    __syncthreads();
+    if (!mbar_wait_bounded(&sh.bar, 0)) {
+      timeout = ST_TIMEOUT;
+      mbar_wait_bounded(&sh.bar, 0);  // give copies in flight one more bounded chance
+    }
+  }
   R nx[PPT], ny[PPT], nz[PPT];
   V I2[PPT], acc[PPT];
-  const V *Ic = reinterpret_cast<const V *>(a.I_in + (size_t)c * A) + sub;
+  const V *Ic = staged ? reinterpret_cast<const V *>(rows + lc * stride) + sub
+                       : reinterpret_cast<const V *>(a.I_in + (size_t)c * A) + sub;
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
     const int p = j < np ? sub + KT * j : 0;
@@ -244,25 +387,19 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
     I2[j] = j < np ? Ic[KT * j] : mk(R(0), R(0));
     acc[j] = mk(R(0), R(0));
   }
-  // stage the block's face slots (contiguous: the block's cells are consecutive)
-  const int64_t cb0 = (int64_t)blockIdx.x * CPB;
-  const int64_t cb1 = cb0 + CPB < a.n_cells ? cb0 + CPB : a.n_cells;
-  const int64_t kb = a.ptr[cb0];
-  const int64_t cnt = a.ptr[cb1] - kb;
-  const bool staged = cnt <= MAXS;  // uniform over the block
   if (staged) {
-    for (int i = threadIdx.x; i < cnt; i += NT) {
-      sh.slot[i] = load_slot<R>(a.slot + kb + i);
-      sh.nbr[i] = __ldg(a.nbr + kb + i);
-    }
+    const int k0 = (int)(a.ptr[c] - kb), k1 = (int)(a.ptr[c + 1] - kb);
+    const double *wf = a.wface ? a.wface + kb : nullptr;
+    if (DynLayout<R>::kSlots)
+      face_sum_staged<R, PPT, MOVING>(sslot, sloc, wf, k0, k1, rows, stride, sub, nx, ny, nz, I2,
+                                      acc, np);
+    else
+      face_sum_staged<R, PPT, MOVING>(a.slot + kb, sloc, wf, k0, k1, rows, stride, sub, nx, ny, nz,
+                                      I2, acc, np);
+  } else {
+    face_sum<R, PPT, MOVING>(a.slot, a.nbr, a.wface, a.ptr[c], a.ptr[c + 1], a.I_in, A, sub, nx, ny,
+                             nz, I2, acc, np);
   }
-  __syncthreads();
-  if (staged)
-    face_sum<R, PPT, MOVING>(sh.slot, sh.nbr, a.ptr[c] - kb, a.ptr[c + 1] - kb, a.I_in, A, sub, nx,
-                             ny, nz, I2, acc, np);
-  else
-    face_sum<R, PPT, MOVING>(a.slot, a.nbr, a.ptr[c], a.ptr[c + 1], a.I_in, A, sub, nx, ny, nz, I2,
-                             acc, np);
   const R dtv = a.dt_r * a.inv_vol[c];
 #pragma unroll
   for (int j = 0; j < PPT; ++j) I2[j] = pfma(mk(-dtv, -dtv), acc[j], I2[j]);  // I*
@@ -386,7 +523,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
   dfx = cell_sum(dfx);
   dfy = cell_sum(dfy);
   dfz = cell_sum(dfz);
-  nonfinite = cell_or(nonfinite);
+  nonfinite = cell_or(nonfinite) | timeout;
   if (sub == 0) {
     sh.dE[lc] = de;
     sh.dF[0][lc] = dfx;
@@ -438,6 +575,7 @@ template <typename R, int PPT, bool MOVING> cudaError_t launch_t(rt_state *s, do
   a.nbr = s->d_nbr;
   a.slot = reinterpret_cast<const typename SlotOf<R>::type *>(s->d_slot);
   a.inv_vol = reinterpret_cast<const R *>(s->d_inv_vol);
+  a.wface = s->d_wface;
   a.gs = s->d_gs;
   a.gd = s->d_gd;
   a.kind = s->d_kind;
@@ -461,8 +599,22 @@ template <typename R, int PPT, bool MOVING> cudaError_t launch_t(rt_state *s, do
   a.newton_max_iter = s->params.newton_max_iter;
   a.status = s->d_status;
   a.bad_cell = s->d_bad;
+  a.nbr_local = s->d_nbr_local;
+  a.halo_ptr = s->d_halo_ptr;
+  a.halo = s->d_halo;
+  a.block_staged = s->d_block_staged;
+  a.row_cap = s->row_cap;
+  a.row_stride = s->row_stride;
+  const size_t dyn = DynLayout<R>::bytes(s->row_cap, s->row_stride);
+  static bool attr_set = false;  // one per kernel instantiation
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<R, PPT, MOVING>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
   const unsigned blocks = (unsigned)((s->n_cells + CPB - 1) / CPB);
-  step_kernel<R, PPT, MOVING><<<blocks, NT, 0, s->stream>>>(a);
+  step_kernel<R, PPT, MOVING><<<blocks, NT, dyn, s->stream>>>(a);
   s->launches++;
   return cudaGetLastError();
 }

@@ -224,78 +224,54 @@ template <typename R> struct Shared {
   unsigned bad[CPB];
 };
 
-// sum_f u I_up over slots [k0, k1) of one cell for the thread's pairs
-template <typename R, int PPT, bool MOVING, typename S>
-__device__ __forceinline__ void face_sum(const S *__restrict__ slot, const int32_t *__restrict__ nbr,
-                                         const double *__restrict__ wface, int64_t k0, int64_t k1,
-                                         const R *__restrict__ I_in, int A, int sub,
-                                         const R (&nx)[PPT], const R (&ny)[PPT],
-                                         const R (&nz)[PPT], const pair_t<R> (&I2)[PPT],
-                                         pair_t<R> (&acc)[PPT], int npairs_lane) {
-  using V = pair_t<R>;
-#pragma unroll 2
-  for (int64_t k = k0; k < k1; ++k) {
-    const int32_t nb = nbr[k];
-    const S s = slot[k];
-    const V *In = reinterpret_cast<const V *>(I_in + (size_t)nb * A) + sub;
-    const R w = MOVING ? slot_w(s, wface, k) : R(0);
-#pragma unroll
-    for (int j = 0; j < PPT; ++j) {
-      if (j < npairs_lane) {
-        const V v = In[KT * j];
-        const R d = slot_dot(nx[j], ny[j], nz[j], s);
-        if (MOVING) {
-          const R ua = d - w, ub = -d - w;
-          const V up = mk(ua > R(0) ? I2[j].x : v.x, ub > R(0) ? I2[j].y : v.y);
-          acc[j] = pfma(mk(ua, ub), up, acc[j]);
-        } else {
-          // u_a = d, u_b = -d: exactly one of the pair reads the neighbour
-          const bool out = d > R(0);
-          const V up = mk(out ? I2[j].x : v.x, out ? v.y : I2[j].y);
-          acc[j] = pfma(mk(d, -d), up, acc[j]);
-        }
-      }
-    }
+// One face's contribution to sum_f u I_up for the thread's pairs: v is the
+// neighbour's (I_p, I_{p+H}) pair, Ia/Ib the cell's own values.
+template <typename R, bool MOVING>
+__device__ __forceinline__ void face_pair(R d, R w, pair_t<R> v, R Ia, R Ib, R &acca, R &accb) {
+  if (MOVING) {
+    const R ua = d - w, ub = -d - w;
+    acca = fma(ua, ua > R(0) ? Ia : v.x, acca);
+    accb = fma(ub, ub > R(0) ? Ib : v.y, accb);
+  } else {
+    // u_a = d, u_b = -d: exactly one of the pair takes the neighbour's value
+    const bool out = d > R(0);
+    acca = fma(d, out ? Ia : v.x, acca);
+    accb = fma(-d, out ? v.y : Ib, accb);
   }
 }
 
-// The same sum with the intensity rows staged in shared memory: slot k's
-// neighbour is the block-local row loc[k], rows `stride` bytes apart.
-template <typename R, int PPT, bool MOVING, typename S>
-__device__ __forceinline__ void face_sum_staged(const S *__restrict__ slot,
-                                                const uint16_t *__restrict__ loc,
-                                                const double *__restrict__ wface, int k0, int k1,
-                                                const unsigned char *rows, int stride, int sub,
-                                                const R (&nx)[PPT], const R (&ny)[PPT],
-                                                const R (&nz)[PPT], const pair_t<R> (&I2)[PPT],
-                                                pair_t<R> (&acc)[PPT], int npairs_lane) {
+// sum_f u I_up over the slots [k0, k1) of one cell.  ROWS: the neighbour rows
+// are staged in shared memory (row loc[k], `stride` bytes apart); otherwise
+// they are read from global memory through nbr[k].  FULL: every lane owns
+// exactly PPT pairs (A/2 divisible by the threads per cell).
+template <typename R, int PPT, bool MOVING, bool FULL, bool ROWS, typename S, typename K>
+__device__ __forceinline__ void face_sum(const S *__restrict__ slot, const K *__restrict__ idx,
+                                         const double *__restrict__ wface, int64_t k0, int64_t k1,
+                                         const unsigned char *rows, int stride,
+                                         const R *__restrict__ I_in, int A, int sub,
+                                         const R (&nx)[PPT], const R (&ny)[PPT],
+                                         const R (&nz)[PPT], const R (&Ia)[PPT], const R (&Ib)[PPT],
+                                         R (&acca)[PPT], R (&accb)[PPT], int np) {
   using V = pair_t<R>;
 #pragma unroll 2
-  for (int k = k0; k < k1; ++k) {
+  for (int64_t k = k0; k < k1; ++k) {
     const S s = slot[k];
-    const V *In = reinterpret_cast<const V *>(rows + (int)loc[k] * stride) + sub;
+    const V *In = ROWS ? reinterpret_cast<const V *>(rows + (int)idx[k] * stride) + sub
+                       : reinterpret_cast<const V *>(I_in + (size_t)idx[k] * A) + sub;
     const R w = MOVING ? slot_w(s, wface, k) : R(0);
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
-      if (j < npairs_lane) {
+      if (FULL || j < np) {
         const V v = In[KT * j];
-        const R d = slot_dot(nx[j], ny[j], nz[j], s);
-        if (MOVING) {
-          const R ua = d - w, ub = -d - w;
-          const V up = mk(ua > R(0) ? I2[j].x : v.x, ub > R(0) ? I2[j].y : v.y);
-          acc[j] = pfma(mk(ua, ub), up, acc[j]);
-        } else {
-          const bool out = d > R(0);
-          const V up = mk(out ? I2[j].x : v.x, out ? v.y : I2[j].y);
-          acc[j] = pfma(mk(d, -d), up, acc[j]);
-        }
+        face_pair<R, MOVING>(slot_dot(nx[j], ny[j], nz[j], s), w, v, Ia[j], Ib[j], acca[j],
+                             accb[j]);
       }
     }
   }
 }
 
 // Shared-memory layout of the staged path: rows, then (float states) the
-// block's face slots and their block-local neighbour rows.
+// block's face slots, then their block-local neighbour rows.
 template <typename R> struct DynLayout {
   static constexpr bool kSlots = sizeof(R) == 4;  // double slots stay in global memory
   __host__ __device__ static size_t slot_off(int row_cap, int stride) {
@@ -309,10 +285,12 @@ template <typename R> struct DynLayout {
   }
 };
 
-template <typename R, int PPT, bool MOVING>
+template <typename R, int PPT, bool MOVING, bool FULL>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const StepArgs<R> a) {
   using V = pair_t<R>;
+  using S = typename SlotOf<R>::type;
   __shared__ Shared<R> sh;
+  extern __shared__ __align__(128) unsigned char dyn[];
   const int lc = threadIdx.x / KT;
   const int sub = threadIdx.x % KT;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -320,8 +298,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
   const bool live = cell < a.n_cells;
   const int64_t c = live ? cell : a.n_cells - 1;  // dead lanes shadow the last cell
   const int A = a.n_angles, H = a.half;
-  // pairs owned by this lane: p = sub + KT j < H
-  const int np = (H - sub + KT - 1) / KT;
+  const int np = FULL ? PPT : (H - sub + KT - 1) / KT;  // pairs p = sub + KT j < H
 
   // warp 0 prefetches its cells' gas state for phases B and D
   const int64_t cl = (int64_t)blockIdx.x * CPB + lane;  // warp 0: lane-per-cell
@@ -335,8 +312,6 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
   }
 
   // ---------------- phase A: transport, I* = I - dt/V sum_f u I_up
-  extern __shared__ __align__(128) unsigned char dyn[];
-  using S = typename SlotOf<R>::type;
   const int64_t cb0 = (int64_t)blockIdx.x * CPB;
   const int64_t cb1 = cb0 + CPB < a.n_cells ? cb0 + CPB : a.n_cells;
   const int64_t kb = a.ptr[cb0];
@@ -374,37 +349,50 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
       mbar_wait_bounded(&sh.bar, 0);  // give copies in flight one more bounded chance
     }
   }
-  R nx[PPT], ny[PPT], nz[PPT];
-  V I2[PPT], acc[PPT];
-  const V *Ic = staged ? reinterpret_cast<const V *>(rows + lc * stride) + sub
-                       : reinterpret_cast<const V *>(a.I_in + (size_t)c * A) + sub;
+  R nx[PPT], ny[PPT], nz[PPT], Ia[PPT], Ib[PPT], acca[PPT], accb[PPT];
+  {
+    const V *Ic = staged ? reinterpret_cast<const V *>(rows + lc * stride) + sub
+                         : reinterpret_cast<const V *>(a.I_in + (size_t)c * A) + sub;
 #pragma unroll
-  for (int j = 0; j < PPT; ++j) {
-    const int p = j < np ? sub + KT * j : 0;
-    nx[j] = a.dir[4 * p];
-    ny[j] = a.dir[4 * p + 1];
-    nz[j] = a.dir[4 * p + 2];
-    I2[j] = j < np ? Ic[KT * j] : mk(R(0), R(0));
-    acc[j] = mk(R(0), R(0));
+    for (int j = 0; j < PPT; ++j) {
+      const bool v = FULL || j < np;
+      const int p = v ? sub + KT * j : 0;
+      nx[j] = a.dir[4 * p];
+      ny[j] = a.dir[4 * p + 1];
+      nz[j] = a.dir[4 * p + 2];
+      const V t = v ? Ic[KT * j] : mk(R(0), R(0));
+      Ia[j] = t.x;
+      Ib[j] = t.y;
+      acca[j] = R(0);
+      accb[j] = R(0);
+    }
   }
   if (staged) {
-    const int k0 = (int)(a.ptr[c] - kb), k1 = (int)(a.ptr[c + 1] - kb);
+    const int64_t k0 = a.ptr[c] - kb, k1 = a.ptr[c + 1] - kb;
     const double *wf = a.wface ? a.wface + kb : nullptr;
     if (DynLayout<R>::kSlots)
-      face_sum_staged<R, PPT, MOVING>(sslot, sloc, wf, k0, k1, rows, stride, sub, nx, ny, nz, I2,
-                                      acc, np);
+      face_sum<R, PPT, MOVING, FULL, true>(sslot, sloc, wf, k0, k1, rows, stride, a.I_in, A, sub, nx,
+                                           ny, nz, Ia, Ib, acca, accb, np);
     else
-      face_sum_staged<R, PPT, MOVING>(a.slot + kb, sloc, wf, k0, k1, rows, stride, sub, nx, ny, nz,
-                                      I2, acc, np);
+      face_sum<R, PPT, MOVING, FULL, true>(a.slot + kb, sloc, wf, k0, k1, rows, stride, a.I_in, A,
+                                           sub, nx, ny, nz, Ia, Ib, acca, accb, np);
   } else {
-    face_sum<R, PPT, MOVING>(a.slot, a.nbr, a.wface, a.ptr[c], a.ptr[c + 1], a.I_in, A, sub, nx, ny,
-                             nz, I2, acc, np);
+    face_sum<R, PPT, MOVING, FULL, false>(a.slot, a.nbr, a.wface, a.ptr[c], a.ptr[c + 1], rows,
+                                          stride, a.I_in, A, sub, nx, ny, nz, Ia, Ib, acca, accb,
+                                          np);
   }
-  const R dtv = a.dt_r * a.inv_vol[c];
+  {
+    const R dtv = a.dt_r * a.inv_vol[c];
 #pragma unroll
-  for (int j = 0; j < PPT; ++j) I2[j] = pfma(mk(-dtv, -dtv), acc[j], I2[j]);  // I*
+    for (int j = 0; j < PPT; ++j) {
+      Ia[j] = fma(-dtv, acca[j], Ia[j]);  // I*
+      Ib[j] = fma(-dtv, accb[j], Ib[j]);
+    }
+  }
 
-  // comoving frame (first order in v/c): Gamma = 1 -+ v.n / c
+  // comoving frame (first order in v/c): Gamma = 1 -+ v.n / c, and the
+  // angular sums of Eq. (Jcom): w~ = w / Gamma^2 (normalised by their sum),
+  // S_I = sum w~ Gamma^4 I* / (1 + x Gamma), S_G = sum w~ Gamma / (1 + x Gamma)
   const int kind = a.kind[c];
   const R icr = a.inv_c_r;
   const R vxc = a.cellv[4 * c] * icr, vyc = a.cellv[4 * c + 1] * icr,
@@ -412,25 +400,24 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
   const R xs = a.dt_cbar_r * a.cellv[4 * c + 3];
   const V *W2 = reinterpret_cast<const V *>(a.wt2) + sub;  // (w_p, w_{p+H})
   R Ga[PPT];
-  V ws2 = mk(R(0), R(0)), sI2 = ws2, sG2 = ws2;
+  R ws = 0, sI = 0, sG = 0;
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
     Ga[j] = R(1) - fma(vxc, nx[j], fma(vyc, ny[j], vzc * nz[j]));
-    if (j < np) {
-      const V G = mk(Ga[j], R(2) - Ga[j]);
-      const V G2 = pmul(G, G);
+    if (FULL || j < np) {
+      const R ga = Ga[j], gb = R(2) - ga;
+      const R ga2 = ga * ga, gb2 = gb * gb;
       const V w = W2[KT * j];
-      const V wc = mk(w.x * rcp(G2.x), w.y * rcp(G2.y));
-      const V den = pfma(mk(xs, xs), G, mk(R(1), R(1)));
-      const V t = pmul(wc, mk(rcp(den.x), rcp(den.y)));
-      ws2 = padd(ws2, wc);
-      sI2 = pfma(t, pmul(pmul(G2, G2), I2[j]), sI2);
-      sG2 = pfma(t, G, sG2);
+      const R wca = w.x * rcp(ga2), wcb = w.y * rcp(gb2);
+      const R ta = wca * rcp(fma(xs, ga, R(1))), tb = wcb * rcp(fma(xs, gb, R(1)));
+      ws += wca + wcb;
+      sI = fma(ta, ga2 * ga2 * Ia[j], fma(tb, gb2 * gb2 * Ib[j], sI));
+      sG = fma(ta, ga, fma(tb, gb, sG));
     }
   }
-  const R ws = cell_sum(ws2.x + ws2.y);
-  const R sI = cell_sum(sI2.x + sI2.y);
-  const R sG = cell_sum(sG2.x + sG2.y);
+  ws = cell_sum(ws);
+  sI = cell_sum(sI);
+  sG = cell_sum(sG);
   if (sub == 0) {
     sh.ws[lc] = ws;
     sh.sI[lc] = sI;
@@ -450,7 +437,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
       const double SI = (double)(sh.sI[lane] * iw), SG = (double)(sh.sG[lane] * iw);
       const double dcr = a.dt * a.cbar * g.rho;
       const double D = 1.0 - dcr * g.kS * SG;
-      const double rD = 1.0 / D;
+      const double rD = rcp(D);
       const double kin = 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * g.inv_rho;
       const double Tn = (d.e - kin) * g.inv_rcv;
       const double alpha = a.dt * a.c * g.rho * g.kP * a.a_rad * (1.0 - dcr * g.kJ * SG * rD);
@@ -471,52 +458,50 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
   __syncthreads();
 
   // ---------------- phase C: new intensities and the radiation change
-  V In2[PPT];
-  if (kind == RT_CELL_BOUNDARY) {
-    const double2 ax = a.aux[c];
-    const R f = R((ax.x <= a.dt) ? 1.0 : a.dt / ax.x);
-    const V *I0 = reinterpret_cast<const V *>(a.I0 + (size_t)a.bc_row[c] * A) + sub;
-#pragma unroll
-    for (int j = 0; j < PPT; ++j) {
-      const V t = j < np ? I0[KT * j] : mk(R(0), R(0));
-      In2[j] = mk(fma(-f, I2[j].x - t.x, I2[j].x), fma(-f, I2[j].y - t.y, I2[j].y));
-    }
-  } else {
-    // interior: I~' = (I~ + q Gamma) / (1 + x Gamma); emitter: the same with
+  R de = 0, dfx = 0, dfy = 0, dfz = 0;
+  unsigned nonfinite = 0;
+  {
+    // boundary: I' = I* - (I* - I0) f; interior: I~' = (I~ + q Gamma) / (1 + x Gamma),
+    // i.e. I' = (I* + q / Gamma^3) / (1 + x Gamma); emitter: the same with
     // x -> dt cbar (rho kappa)_src and q -> that rate times I_src (Sec. 3.6)
-    R qq = 0, xx = xs;
-    if (kind == RT_CELL_EMITTER) {
+    R f = 0, qq = 0, xx = xs;
+    const V *I0 = nullptr;
+    if (kind == RT_CELL_BOUNDARY) {
+      const double2 ax = a.aux[c];
+      f = R((ax.x <= a.dt) ? 1.0 : a.dt / ax.x);
+      I0 = reinterpret_cast<const V *>(a.I0 + (size_t)a.bc_row[c] * A) + sub;
+    } else if (kind == RT_CELL_EMITTER) {
       const double2 ax = a.aux[c];
       xx = R(a.dt * a.cbar * ax.x);
       qq = xx * R(ax.y);
     } else {
       qq = sh.q[lc];
     }
+    V *Io = reinterpret_cast<V *>(a.I_out + (size_t)c * A) + sub;
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
-      const V G = mk(Ga[j], R(2) - Ga[j]);
-      const V G2 = pmul(G, G);
-      const V G4 = pmul(G2, G2);
-      const V num = pfma(mk(qq, qq), G, pmul(G4, I2[j]));
-      const V den = pmul(pfma(mk(xx, xx), G, mk(R(1), R(1))), G4);
-      In2[j] = mk(num.x * rcp(den.x), num.y * rcp(den.y));
-    }
-  }
-  R de = 0, dfx = 0, dfy = 0, dfz = 0;
-  unsigned nonfinite = 0;
-  V *Io = reinterpret_cast<V *>(a.I_out + (size_t)c * A) + sub;
-#pragma unroll
-  for (int j = 0; j < PPT; ++j) {
-    if (j < np) {
-      if (live) Io[KT * j] = In2[j];
-      if (!isfinite(In2[j].x) || !isfinite(In2[j].y)) nonfinite = ST_NONFINITE;
-      const V w = W2[KT * j];
-      const V dd = pmul(w, padd(I2[j], mk(-In2[j].x, -In2[j].y)));
-      de += dd.x + dd.y;
-      const R df = dd.x - dd.y;  // the antipode has direction -n
-      dfx = fma(nx[j], df, dfx);
-      dfy = fma(ny[j], df, dfy);
-      dfz = fma(nz[j], df, dfz);
+      if (FULL || j < np) {
+        R na, nb;
+        if (kind == RT_CELL_BOUNDARY) {
+          const V t = I0[KT * j];
+          na = fma(-f, Ia[j] - t.x, Ia[j]);
+          nb = fma(-f, Ib[j] - t.y, Ib[j]);
+        } else {
+          const R ga = Ga[j], gb = R(2) - ga;
+          const R ra = rcp(ga * ga * ga), rb = rcp(gb * gb * gb);
+          na = fma(qq, ra, Ia[j]) * rcp(fma(xx, ga, R(1)));
+          nb = fma(qq, rb, Ib[j]) * rcp(fma(xx, gb, R(1)));
+        }
+        if (live) Io[KT * j] = mk(na, nb);
+        if (!isfinite(na) || !isfinite(nb)) nonfinite = ST_NONFINITE;
+        const V w = W2[KT * j];
+        const R da = w.x * (Ia[j] - na), db = w.y * (Ib[j] - nb);
+        de += da + db;
+        const R df = da - db;  // the antipode has direction -n
+        dfx = fma(nx[j], df, dfx);
+        dfy = fma(ny[j], df, dfy);
+        dfz = fma(nz[j], df, dfz);
+      }
     }
   }
   de = cell_sum(de);
@@ -566,7 +551,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
   }
 }
 
-template <typename R, int PPT, bool MOVING> cudaError_t launch_t(rt_state *s, double dt) {
+template <typename R, int PPT, bool MOVING, bool FULL>
+cudaError_t launch_t(rt_state *s, double dt) {
   StepArgs<R> a;
   a.n_cells = s->n_cells;
   a.n_angles = s->n_angles;
@@ -608,34 +594,37 @@ template <typename R, int PPT, bool MOVING> cudaError_t launch_t(rt_state *s, do
   const size_t dyn = DynLayout<R>::bytes(s->row_cap, s->row_stride);
   static bool attr_set = false;  // one per kernel instantiation
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(step_kernel<R, PPT, MOVING>,
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<R, PPT, MOVING, FULL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   const unsigned blocks = (unsigned)((s->n_cells + CPB - 1) / CPB);
-  step_kernel<R, PPT, MOVING><<<blocks, NT, dyn, s->stream>>>(a);
+  step_kernel<R, PPT, MOVING, FULL><<<blocks, NT, dyn, s->stream>>>(a);
   s->launches++;
   return cudaGetLastError();
 }
 
-template <typename R, bool MOVING> cudaError_t dispatch_ppt(rt_state *s, double dt) {
+template <typename R, bool MOVING, bool FULL> cudaError_t dispatch_ppt(rt_state *s, double dt) {
   const int ppt = (s->n_angles / 2 + KT - 1) / KT;
   switch (ppt) {
-    case 1: return launch_t<R, 1, MOVING>(s, dt);
-    case 2: return launch_t<R, 2, MOVING>(s, dt);
-    case 3: return launch_t<R, 3, MOVING>(s, dt);
-    case 4: return launch_t<R, 4, MOVING>(s, dt);
-    case 5: return launch_t<R, 5, MOVING>(s, dt);
-    case 6: return launch_t<R, 6, MOVING>(s, dt);
-    case 7: return launch_t<R, 7, MOVING>(s, dt);
-    case 8: return launch_t<R, 8, MOVING>(s, dt);
+    case 1: return launch_t<R, 1, MOVING, FULL>(s, dt);
+    case 2: return launch_t<R, 2, MOVING, FULL>(s, dt);
+    case 3: return launch_t<R, 3, MOVING, FULL>(s, dt);
+    case 4: return launch_t<R, 4, MOVING, FULL>(s, dt);
+    case 5: return launch_t<R, 5, MOVING, FULL>(s, dt);
+    case 6: return launch_t<R, 6, MOVING, FULL>(s, dt);
+    case 7: return launch_t<R, 7, MOVING, FULL>(s, dt);
+    case 8: return launch_t<R, 8, MOVING, FULL>(s, dt);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <typename R> cudaError_t dispatch(rt_state *s, double dt) {
-  return s->moving ? dispatch_ppt<R, true>(s, dt) : dispatch_ppt<R, false>(s, dt);
+  const bool full = (s->n_angles / 2) % KT == 0;
+  if (s->moving)
+    return full ? dispatch_ppt<R, true, true>(s, dt) : dispatch_ppt<R, true, false>(s, dt);
+  return full ? dispatch_ppt<R, false, true>(s, dt) : dispatch_ppt<R, false, false>(s, dt);
 }
 
 }  // namespace

@@ -345,6 +345,15 @@ int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state 
   s->nnz = m->cell_face_ptr[N];
   s->n_angles = A;
   s->cell_of = morton_order(N, m->cell_centroid);
+  // within each block of the step kernel, most faces first: the lanes of a
+  // warp then loop over similar face counts
+  for (int64_t b0 = 0; b0 < N; b0 += rt::CPB) {
+    auto first = s->cell_of.begin() + b0, last = s->cell_of.begin() + std::min(N, b0 + rt::CPB);
+    std::stable_sort(first, last, [&](int64_t x, int64_t y) {
+      return m->cell_face_ptr[x + 1] - m->cell_face_ptr[x] >
+             m->cell_face_ptr[y + 1] - m->cell_face_ptr[y];
+    });
+  }
   std::vector<int64_t> slot_of(N);
   for (int64_t ic = 0; ic < N; ++ic) slot_of[s->cell_of[ic]] = ic;
   s->volume.assign(m->cell_volume, m->cell_volume + N);
@@ -438,7 +447,7 @@ int rt_set_gas(rt_state *s, const double *rho, const double *e, const double *m,
         !std::isfinite(kP[c] + kJ[c] + kS[c]))
       return fail(s, RT_ERR_ARG, "rt_set_gas: rho must be > 0, opacities >= 0, all finite");
     const double rcv = rho[c] * s->params.r_gas / (s->params.gamma_gas - 1.0);
-    gs[ic] = {rho[c], kP[c], kJ[c], kS[c], 1.0 / rho[c], rcv, 1.0 / rcv, 0.0};
+    gs[ic] = {rho[c], rho[c] * kP[c], rho[c] * kJ[c], rho[c] * kS[c], 1.0 / rho[c], rcv, 0.0, 0.0};
     gd[ic] = {e[c], m[3 * c], m[3 * c + 1], m[3 * c + 2]};
   }
   RT_CUDA(s, cudaMemcpyAsync(s->d_gs, gs.data(), sizeof(rt::GasStatic) * N, cudaMemcpyHostToDevice,

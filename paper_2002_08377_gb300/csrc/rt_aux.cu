@@ -211,7 +211,7 @@ __global__ void cellv_kernel(const GasStatic *__restrict__ gs, const GasDyn *__r
   cellv[4 * i] = R(d.mx * ir);
   cellv[4 * i + 1] = R(d.my * ir);
   cellv[4 * i + 2] = R(d.mz * ir);
-  cellv[4 * i + 3] = R(g.rho * (g.kJ + g.kS));
+  cellv[4 * i + 3] = R(g.rkJ + g.rkS);
 }
 
 unsigned rows_grid(int64_t n) { return (unsigned)((n + kThreads / 32 - 1) / (kThreads / 32)); }

@@ -49,10 +49,11 @@ constexpr int CPB = 32;           // cells per block
 constexpr int MAX_SLOTS = 640;    // face slots a block can stage
 constexpr int MAX_ROWS = 160;     // intensity rows a block can stage (own + halo)
 
-// Per-cell constant gas data (double): rho, kappa_P, kappa_J, kappa_s and
-// the derived 1/rho, rho c_v = rho r_gas / (gamma - 1) and its inverse.
+// Per-cell constant gas data (double): rho, the absorption / scattering
+// coefficients rho kappa_P, rho kappa_J, rho kappa_s, 1/rho and
+// rho c_v = rho r_gas / (gamma - 1).
 struct alignas(64) GasStatic {
-  double rho, kP, kJ, kS, inv_rho, rcv, inv_rcv, pad;
+  double rho, rkP, rkJ, rkS, inv_rho, rcv, pad0, pad1;
 };
 // Per-cell evolving gas data (double): e, m.
 struct alignas(32) GasDyn {
@@ -86,6 +87,7 @@ template <typename R> struct StepArgs {
   R *I_out;                 // [N][A]
   R *cellv;                 // [N][4] (v_x, v_y, v_z, rho (kappa_J + kappa_s))
   double dt, cbar, c, a_rad, rcv;  // rcv = r_gas / (gamma - 1)
+  double k_dcr, k_alpha, k_g, k_fe, k_fm;  // dt cbar, dt c a, dt c 4 pi, 4 pi c/cbar, 4 pi/cbar
   R dt_r, dt_cbar_r, inv_c_r;
   int32_t newton_max_iter;
   unsigned *status;

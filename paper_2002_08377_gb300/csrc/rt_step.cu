@@ -218,7 +218,7 @@ template <typename R> struct Shared {
   unsigned long long bar;  // completion of the staged intensity rows
   GasStatic gs[CPB];  // gas of the block's cells, prefetched for warp 0
   GasDyn gd[CPB];
-  R ws[CPB], sI[CPB], sG[CPB];  // comoving weight sum and the two sums of Eq. (Jcom)
+  R sI[CPB], sG[CPB], s1[CPB];  // the sums of Eq. (Jcom) and sum w~/(1+x), unnormalised
   R q[CPB];                     // dt cbar rho (kP B + kS J) per interior cell
   R dE[CPB], dF[3][CPB];        // sum w (I* - I') and sum w n (I* - I')
   unsigned bad[CPB];
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
   const R xs = a.dt_cbar_r * a.cellv[4 * c + 3];
   const V *W2 = reinterpret_cast<const V *>(a.wt2) + sub;  // (w_p, w_{p+H})
   R Ga[PPT];
-  R ws = 0, sI = 0, sG = 0;
+  R sI = 0, sG = 0, s1 = 0;  // unnormalised: the normalisation cancels in phase B
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
     Ga[j] = R(1) - fma(vxc, nx[j], fma(vyc, ny[j], vzc * nz[j]));
@@ -410,18 +410,18 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
       const V w = W2[KT * j];
       const R wca = w.x * rcp(ga2), wcb = w.y * rcp(gb2);
       const R ta = wca * rcp(fma(xs, ga, R(1))), tb = wcb * rcp(fma(xs, gb, R(1)));
-      ws += wca + wcb;
+      s1 += ta + tb;
       sI = fma(ta, ga2 * ga2 * Ia[j], fma(tb, gb2 * gb2 * Ib[j], sI));
       sG = fma(ta, ga, fma(tb, gb, sG));
     }
   }
-  ws = cell_sum(ws);
   sI = cell_sum(sI);
   sG = cell_sum(sG);
+  s1 = cell_sum(s1);
   if (sub == 0) {
-    sh.ws[lc] = ws;
     sh.sI[lc] = sI;
     sh.sG[lc] = sG;
+    sh.s1[lc] = s1;
   }
   if (warp == 0) cp_async_wait_all();
   __syncthreads();
@@ -431,17 +431,22 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
     R q = 0;
     unsigned bad = 0;
     if (cl < a.n_cells && a.kind[cl] == RT_CELL_INTERIOR) {
+      // With w~ normalised, x_a = dt cbar rho (kJ + kS) Gamma_a and the sums
+      // S_I, S_G of Eq. (Jcom), S_1 = sum w~ / (1 + x):
+      //   D = 1 - dt cbar rho kS S_G = S_1 + dt cbar rho kJ S_G,
+      //   1 - dt cbar rho kJ S_G / D = S_1 / D,
+      // so the quartic alpha T^4 + rho c_v T = g of Eq. (com rad thermal disc)
+      // has alpha = dt c a rho kP S_1 / D and g = (e - kinetic) +
+      // dt c 4 pi rho kJ S_I / D: sums of positive terms, no cancellation when
+      // x >> 1.  The weight normalisation cancels in every ratio.
       const GasStatic g = sh.gs[lane];
       const GasDyn d = sh.gd[lane];
-      const R iw = R(1) / sh.ws[lane];
-      const double SI = (double)(sh.sI[lane] * iw), SG = (double)(sh.sG[lane] * iw);
-      const double dcr = a.dt * a.cbar * g.rho;
-      const double D = 1.0 - dcr * g.kS * SG;
-      const double rD = rcp(D);
+      const double SI = (double)sh.sI[lane], SG = (double)sh.sG[lane], S1 = (double)sh.s1[lane];
+      const double dJ = a.k_dcr * g.rkJ, dP = a.k_dcr * g.rkP, dS = a.k_dcr * g.rkS;
+      const double rU = rcp(fma(dJ, SG, S1));
       const double kin = 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * g.inv_rho;
-      const double Tn = (d.e - kin) * g.inv_rcv;
-      const double alpha = a.dt * a.c * g.rho * g.kP * a.a_rad * (1.0 - dcr * g.kJ * SG * rD);
-      const double gq = g.rcv * Tn + a.dt * a.c * g.rho * 4.0 * kPi * g.kJ * SI * rD;
+      const double alpha = a.k_alpha * g.rkP * S1 * rU;
+      const double gq = (d.e - kin) + a.k_g * g.rkJ * SI * rU;
       double T = 0.0;
       if (!(gq >= 0.0) || !(alpha >= 0.0)) {
         bad |= ST_NONFINITE;
@@ -449,8 +454,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
         bad |= ST_NONCONV;
       }
       const double B = a.a_rad * (T * T) * (T * T) * (1.0 / (4.0 * kPi));
-      const double J = (SI + dcr * g.kP * B * SG) * rD;
-      q = R(dcr * (g.kP * B + g.kS * J));
+      const double J = fma(dP * B, SG, SI) * rU;  // the J~ of Eq. (Jcom)
+      q = R(fma(dP, B, dS * J));
     }
     sh.q[lane] = q;
     sh.bad[lane] = bad;
@@ -520,11 +525,10 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
 
   // ---------------- phase D: gas exchange (Eqs. gas1, gas2), one lane per cell
   if (warp == 0 && cl < a.n_cells) {
-    const double fe = a.c / a.cbar * 4.0 * kPi;
-    const double fm = 4.0 * kPi / a.cbar;  // (4 pi c sum w n dI) / (c cbar)
-    const double dE = fe * (double)sh.dE[lane];
-    const double dx = fm * (double)sh.dF[0][lane], dy = fm * (double)sh.dF[1][lane],
-                 dz = fm * (double)sh.dF[2][lane];
+    // dE_gas = (c/cbar) 4 pi sum w dI, d(rho v) = (4 pi c sum w n dI) / (c cbar)
+    const double dE = a.k_fe * (double)sh.dE[lane];
+    const double dx = a.k_fm * (double)sh.dF[0][lane], dy = a.k_fm * (double)sh.dF[1][lane],
+                 dz = a.k_fm * (double)sh.dF[2][lane];
     if (a.kind[cl] == RT_CELL_INTERIOR) {
       GasDyn d = sh.gd[lane];
       d.e += dE;
@@ -582,6 +586,11 @@ cudaError_t launch_t(rt_state *s, double dt) {
   a.c = s->params.c;
   a.a_rad = s->params.a_rad;
   a.rcv = s->params.r_gas / (s->params.gamma_gas - 1.0);
+  a.k_dcr = dt * s->params.cbar;
+  a.k_alpha = dt * s->params.c * s->params.a_rad;
+  a.k_g = dt * s->params.c * 4.0 * kPi;
+  a.k_fe = s->params.c / s->params.cbar * 4.0 * kPi;
+  a.k_fm = 4.0 * kPi / s->params.cbar;
   a.newton_max_iter = s->params.newton_max_iter;
   a.status = s->d_status;
   a.bad_cell = s->d_bad;

@@ -157,53 +157,6 @@ template <typename R> int build_device_mesh(rt_state *s, const rt_mesh_desc *m,
   if (!wface.empty()) RT_CUDA(s, upload(s, &s->d_wface, wface));
   RT_CUDA(s, upload(s, &s->d_ptr, ptr));
   RT_CUDA(s, upload(s, &s->d_nbr, nbr));
-  // per-block halo lists and block-local neighbour rows for the staged path
-  {
-    const int64_t N = m->n_cells;
-    const int64_t nb = (N + rt::CPB - 1) / rt::CPB;
-    const int A = m->n_angles;
-    s->row_stride = (int32_t)(A * sizeof(R) + 16);  // +16 B staggers shared-memory banks
-    // rows budget: three float blocks or two double blocks per SM
-    int cap = (int)((sizeof(R) == 4 ? 54 * 1024 : 92 * 1024) / s->row_stride);
-    s->row_cap = cap < rt::MAX_ROWS ? cap : rt::MAX_ROWS;
-    // bulk copies move whole rows and need 16-byte sizes and addresses
-    if ((A * sizeof(R)) % 16 != 0) s->row_cap = 0;
-    std::vector<int64_t> hptr(nb + 1, 0);
-    std::vector<int32_t> halo;
-    std::vector<uint16_t> loc(nbr.size(), 0);
-    std::vector<uint8_t> staged(nb, 0);
-    std::vector<int32_t> tmp;
-    for (int64_t b = 0; b < nb; ++b) {
-      const int64_t c0 = b * rt::CPB, c1 = std::min(N, c0 + rt::CPB);
-      tmp.clear();
-      for (int64_t k = ptr[c0]; k < ptr[c1]; ++k)
-        if (nbr[k] < c0 || nbr[k] >= c1) tmp.push_back(nbr[k]);
-      std::sort(tmp.begin(), tmp.end());
-      tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
-      const bool fits = (int64_t)rt::CPB + (int64_t)tmp.size() <= s->row_cap &&
-                        ptr[c1] - ptr[c0] <= rt::MAX_SLOTS;
-      staged[b] = fits ? 1 : 0;
-      s->staged_blocks += fits;
-      if (fits) {
-        for (int64_t k = ptr[c0]; k < ptr[c1]; ++k) {
-          const int32_t g = nbr[k];
-          if (g >= c0 && g < c1) {
-            loc[k] = (uint16_t)(g - c0);
-          } else {
-            const int64_t h = std::lower_bound(tmp.begin(), tmp.end(), g) - tmp.begin();
-            loc[k] = (uint16_t)(rt::CPB + h);
-          }
-        }
-        halo.insert(halo.end(), tmp.begin(), tmp.end());
-      }
-      hptr[b + 1] = (int64_t)halo.size();
-    }
-    s->n_blocks = nb;
-    RT_CUDA(s, upload(s, &s->d_nbr_local, loc));
-    RT_CUDA(s, upload(s, &s->d_halo_ptr, hptr));
-    RT_CUDA(s, upload(s, &s->d_halo, halo));
-    RT_CUDA(s, upload(s, &s->d_block_staged, staged));
-  }
   typename rt::SlotOf<R>::type *ds = nullptr;
   RT_CUDA(s, upload(s, &ds, slot));
   s->d_slot = ds;
@@ -298,10 +251,6 @@ int sync_status(rt_state *s) {
   RT_CUDA(s, cudaMemcpy(&bad, s->d_bad, sizeof bad, cudaMemcpyDeviceToHost));
   long long cell = bad < (unsigned long long)s->n_cells ? (long long)s->cell_of[bad] : -1;
   char buf[160];
-  if (st & rt::ST_TIMEOUT) {
-    snprintf(buf, sizeof buf, "a bounded wait for staged intensity rows timed out (cell %lld)", cell);
-    return fail(s, RT_ERR_CUDA, buf);
-  }
   if (st & rt::ST_NONFINITE) {
     snprintf(buf, sizeof buf, "non-finite intensity or temperature (first cell %lld)", cell);
     return fail(s, RT_ERR_NONFINITE, buf);
@@ -715,7 +664,7 @@ const char *rt_last_error(const rt_state *s) { return s ? s->err.c_str() : "null
 void rt_destroy(rt_state *s) {
   if (!s) return;
   if (s->stream || true) cudaStreamSynchronize(s->stream);
-  void *bufs[] = {s->d_wface, s->d_nbr_local, s->d_halo_ptr, s->d_halo, s->d_block_staged, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
+  void *bufs[] = {s->d_wface, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
                   s->d_gd, s->d_kind, s->d_aux, s->d_bc_row, s->d_I0, s->d_ext, s->d_dir, s->d_wt,
                   s->d_dir64, s->d_wt64, s->d_I[0], s->d_I[1], s->d_status, s->d_bad,
                   s->d_scratch, s->d_out16};

@@ -37,17 +37,10 @@ template <> struct SlotOf<double> { using type = SlotD; };
 enum : unsigned {
   ST_NONCONV = 1u,
   ST_NONFINITE = 2u,
-  ST_TIMEOUT = 4u,  // a bounded wait on an mbarrier gave up
 };
 
-// The step kernel works on blocks of CPB consecutive (internal) cells.  Each
-// block stages the intensity rows it reads -- its own cells, then the halo
-// of neighbours outside the block -- into shared memory; a slot's neighbour
-// is then addressed by its block-local row: own cell ic -> ic - first cell,
-// halo entry h -> CPB + h.
-constexpr int CPB = 32;           // cells per block
-constexpr int MAX_SLOTS = 640;    // face slots a block can stage
-constexpr int MAX_ROWS = 160;     // intensity rows a block can stage (own + halo)
+// The step kernel works on blocks of CPB consecutive (internal) cells.
+constexpr int CPB = 32;
 
 // Per-cell constant gas data (double): rho, the absorption / scattering
 // coefficients rho kappa_P, rho kappa_J, rho kappa_s, 1/rho and
@@ -65,12 +58,6 @@ template <typename R> struct StepArgs {
   int32_t n_angles, half;
   const int64_t *ptr;       // [N+1] slot range per internal cell
   const int32_t *nbr;       // [nnz] internal neighbour index
-  const uint16_t *nbr_local;  // [nnz] block-local row of the neighbour
-  const int64_t *halo_ptr;  // [blocks+1] range of each block's halo rows
-  const int32_t *halo;      // halo rows (internal cell index)
-  const uint8_t *block_staged;  // [blocks] 1: rows fit in shared memory
-  int32_t row_cap;          // rows the kernel's shared memory holds
-  int32_t row_stride;       // bytes between staged rows
   const typename SlotOf<R>::type *slot;  // [nnz]
   const R *inv_vol;         // [N]
   const double *wface;      // [nnz] A_f w_f . n_f of double slots (moving meshes)
@@ -126,12 +113,7 @@ struct rt_state {
   // device buffers
   int64_t *d_ptr = nullptr;
   int32_t *d_nbr = nullptr;
-  uint16_t *d_nbr_local = nullptr;
-  int64_t *d_halo_ptr = nullptr;
-  int32_t *d_halo = nullptr;
-  uint8_t *d_block_staged = nullptr;
-  int32_t row_cap = 0, row_stride = 0;
-  int64_t staged_blocks = 0, n_blocks = 0;
+
   void *d_slot = nullptr;
   double *d_wface = nullptr;  // double states: per-slot A w . n
   void *d_inv_vol = nullptr;

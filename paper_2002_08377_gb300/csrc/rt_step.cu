@@ -9,7 +9,10 @@
 // angles; on a static mesh exactly one of the two is inflow.
 //
 // Block = 32 cells x 8 threads; thread `sub` of a cell owns the pairs
-// p = sub + 8 j (j < PPT).  Phases (separated by __syncthreads):
+// p = sub + 8 j (j < PPT).  Registers are capped so that four blocks share an
+// SM: the step is latency-bound, and resident warps matter more than the
+// shared-memory staging of neighbour rows that an earlier variant used.
+// Phases (separated by __syncthreads):
 //   A  all threads: transport over the cell's faces in slot order (no
 //      atomics, deterministic), comoving weights and the angular sums of
 //      Eq. (Jcom); each cell's 8 lanes reduce with shuffles;
@@ -109,46 +112,6 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// ---- mbarrier + TMA bulk copy (global -> shared), completion by tx bytes
-__device__ __forceinline__ unsigned smem_addr(const void *p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes,
-                                              unsigned long long *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
-          "r"(smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Waits for phase `parity` of the barrier with an iteration limit (each
-// try_wait may itself suspend for a bounded time); false if it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
-  for (int it = 0; it < (1 << 20); ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
 // Positive root of alpha T^4 + beta T = g (alpha >= 0, beta > 0, g >= 0).
 // f is increasing and convex on T > 0, so Newton from any point at or above
 // the root decreases monotonically onto it.  Double states: start at
@@ -215,7 +178,6 @@ __device__ __forceinline__ int quartic_root(double alpha, double beta, double g,
 }
 
 template <typename R> struct Shared {
-  unsigned long long bar;  // completion of the staged intensity rows
   GasStatic gs[CPB];  // gas of the block's cells, prefetched for warp 0
   GasDyn gd[CPB];
   R sI[CPB], sG[CPB], s1[CPB];  // the sums of Eq. (Jcom) and sum w~/(1+x), unnormalised
@@ -240,14 +202,13 @@ __device__ __forceinline__ void face_pair(R d, R w, pair_t<R> v, R Ia, R Ib, R &
   }
 }
 
-// sum_f u I_up over the slots [k0, k1) of one cell.  ROWS: the neighbour rows
-// are staged in shared memory (row loc[k], `stride` bytes apart); otherwise
-// they are read from global memory through nbr[k].  FULL: every lane owns
-// exactly PPT pairs (A/2 divisible by the threads per cell).
-template <typename R, int PPT, bool MOVING, bool FULL, bool ROWS, typename S, typename K>
-__device__ __forceinline__ void face_sum(const S *__restrict__ slot, const K *__restrict__ idx,
+// sum_f u I_up over the slots [k0, k1) of one cell, neighbour rows read
+// through nbr[k] (L1/L2 serve the reuse between neighbouring cells; cells are
+// in Morton order).  FULL: every lane owns exactly PPT pairs (A/2 divisible
+// by the threads per cell).
+template <typename R, int PPT, bool MOVING, bool FULL, typename S>
+__device__ __forceinline__ void face_sum(const S *__restrict__ slot, const int32_t *__restrict__ nbr,
                                          const double *__restrict__ wface, int64_t k0, int64_t k1,
-                                         const unsigned char *rows, int stride,
                                          const R *__restrict__ I_in, int A, int sub,
                                          const R (&nx)[PPT], const R (&ny)[PPT],
                                          const R (&nz)[PPT], const R (&Ia)[PPT], const R (&Ib)[PPT],
@@ -256,8 +217,7 @@ __device__ __forceinline__ void face_sum(const S *__restrict__ slot, const K *__
 #pragma unroll 2
   for (int64_t k = k0; k < k1; ++k) {
     const S s = slot[k];
-    const V *In = ROWS ? reinterpret_cast<const V *>(rows + (int)idx[k] * stride) + sub
-                       : reinterpret_cast<const V *>(I_in + (size_t)idx[k] * A) + sub;
+    const V *In = reinterpret_cast<const V *>(I_in + (size_t)nbr[k] * A) + sub;
     const R w = MOVING ? slot_w(s, wface, k) : R(0);
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
@@ -270,27 +230,11 @@ __device__ __forceinline__ void face_sum(const S *__restrict__ slot, const K *__
   }
 }
 
-// Shared-memory layout of the staged path: rows, then (float states) the
-// block's face slots, then their block-local neighbour rows.
-template <typename R> struct DynLayout {
-  static constexpr bool kSlots = sizeof(R) == 4;  // double slots stay in global memory
-  __host__ __device__ static size_t slot_off(int row_cap, int stride) {
-    return ((size_t)row_cap * stride + 127) & ~(size_t)127;
-  }
-  __host__ __device__ static size_t loc_off(int row_cap, int stride) {
-    return slot_off(row_cap, stride) + (kSlots ? MAX_SLOTS * sizeof(typename SlotOf<R>::type) : 0);
-  }
-  __host__ __device__ static size_t bytes(int row_cap, int stride) {
-    return loc_off(row_cap, stride) + MAX_SLOTS * sizeof(uint16_t);
-  }
-};
-
 template <typename R, int PPT, bool MOVING, bool FULL>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const StepArgs<R> a) {
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) step_kernel(const StepArgs<R> a) {
   using V = pair_t<R>;
   using S = typename SlotOf<R>::type;
   __shared__ Shared<R> sh;
-  extern __shared__ __align__(128) unsigned char dyn[];
   const int lc = threadIdx.x / KT;
   const int sub = threadIdx.x % KT;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -302,7 +246,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
 
   // warp 0 prefetches its cells' gas state for phases B and D
   const int64_t cl = (int64_t)blockIdx.x * CPB + lane;  // warp 0: lane-per-cell
-  if (warp == 0 && cl < a.n_cells) {
+  if (warp == 0 && lane < CPB && cl < a.n_cells) {
     const char *g = reinterpret_cast<const char *>(a.gs + cl);
     const char *d = reinterpret_cast<const char *>(a.gd + cl);
 #pragma unroll
@@ -312,47 +256,9 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
   }
 
   // ---------------- phase A: transport, I* = I - dt/V sum_f u I_up
-  const int64_t cb0 = (int64_t)blockIdx.x * CPB;
-  const int64_t cb1 = cb0 + CPB < a.n_cells ? cb0 + CPB : a.n_cells;
-  const int64_t kb = a.ptr[cb0];
-  const int cnt = (int)(a.ptr[cb1] - kb);
-  const bool staged = a.block_staged[blockIdx.x] != 0;  // uniform over the block
-  const int stride = a.row_stride;
-  unsigned char *rows = dyn;
-  S *sslot = reinterpret_cast<S *>(dyn + DynLayout<R>::slot_off(a.row_cap, stride));
-  uint16_t *sloc = reinterpret_cast<uint16_t *>(dyn + DynLayout<R>::loc_off(a.row_cap, stride));
-  unsigned timeout = 0;
-  if (staged) {
-    if (threadIdx.x == 0) mbar_init(&sh.bar, 1);
-    __syncthreads();
-    if (warp == 0) {
-      // own rows, then the halo rows, one bulk copy per row
-      const int64_t h0 = a.halo_ptr[blockIdx.x];
-      const int nh = (int)(a.halo_ptr[blockIdx.x + 1] - h0);
-      const int nown = (int)(cb1 - cb0);
-      const unsigned rb = (unsigned)(A * sizeof(R));
-      if (lane == 0) mbar_expect_tx(&sh.bar, rb * (unsigned)(nown + nh));
-      __syncwarp();
-      for (int r = lane; r < nown; r += 32)
-        bulk_copy_g2s(rows + r * stride, a.I_in + (size_t)(cb0 + r) * A, rb, &sh.bar);
-      for (int h = lane; h < nh; h += 32)
-        bulk_copy_g2s(rows + (CPB + h) * stride, a.I_in + (size_t)a.halo[h0 + h] * A, rb,
-                      &sh.bar);
-    }
-    for (int i = threadIdx.x; i < cnt; i += NT) {
-      if (DynLayout<R>::kSlots) sslot[i] = load_slot<R>(a.slot + kb + i);
-      sloc[i] = __ldg(a.nbr_local + kb + i);
-    }
-    __syncthreads();
-    if (!mbar_wait_bounded(&sh.bar, 0)) {
-      timeout = ST_TIMEOUT;
-      mbar_wait_bounded(&sh.bar, 0);  // give copies in flight one more bounded chance
-    }
-  }
   R nx[PPT], ny[PPT], nz[PPT], Ia[PPT], Ib[PPT], acca[PPT], accb[PPT];
   {
-    const V *Ic = staged ? reinterpret_cast<const V *>(rows + lc * stride) + sub
-                         : reinterpret_cast<const V *>(a.I_in + (size_t)c * A) + sub;
+    const V *Ic = reinterpret_cast<const V *>(a.I_in + (size_t)c * A) + sub;
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
       const bool v = FULL || j < np;
@@ -367,20 +273,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
       accb[j] = R(0);
     }
   }
-  if (staged) {
-    const int64_t k0 = a.ptr[c] - kb, k1 = a.ptr[c + 1] - kb;
-    const double *wf = a.wface ? a.wface + kb : nullptr;
-    if (DynLayout<R>::kSlots)
-      face_sum<R, PPT, MOVING, FULL, true>(sslot, sloc, wf, k0, k1, rows, stride, a.I_in, A, sub, nx,
-                                           ny, nz, Ia, Ib, acca, accb, np);
-    else
-      face_sum<R, PPT, MOVING, FULL, true>(a.slot + kb, sloc, wf, k0, k1, rows, stride, a.I_in, A,
-                                           sub, nx, ny, nz, Ia, Ib, acca, accb, np);
-  } else {
-    face_sum<R, PPT, MOVING, FULL, false>(a.slot, a.nbr, a.wface, a.ptr[c], a.ptr[c + 1], rows,
-                                          stride, a.I_in, A, sub, nx, ny, nz, Ia, Ib, acca, accb,
-                                          np);
-  }
+  face_sum<R, PPT, MOVING, FULL>(a.slot, a.nbr, a.wface, a.ptr[c], a.ptr[c + 1], a.I_in, A, sub, nx,
+                                 ny, nz, Ia, Ib, acca, accb, np);
   {
     const R dtv = a.dt_r * a.inv_vol[c];
 #pragma unroll
@@ -427,7 +321,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
   __syncthreads();
 
   // ---------------- phase B: temperature quartic, one lane per cell
-  if (warp == 0) {
+  if (warp == 0 && lane < CPB) {
     R q = 0;
     unsigned bad = 0;
     if (cl < a.n_cells && a.kind[cl] == RT_CELL_INTERIOR) {
@@ -513,7 +407,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
   dfx = cell_sum(dfx);
   dfy = cell_sum(dfy);
   dfz = cell_sum(dfz);
-  nonfinite = cell_or(nonfinite) | timeout;
+  nonfinite = cell_or(nonfinite);
   if (sub == 0) {
     sh.dE[lc] = de;
     sh.dF[0][lc] = dfx;
@@ -524,7 +418,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) step_kernel(const 
   __syncthreads();
 
   // ---------------- phase D: gas exchange (Eqs. gas1, gas2), one lane per cell
-  if (warp == 0 && cl < a.n_cells) {
+  if (warp == 0 && lane < CPB && cl < a.n_cells) {
     // dE_gas = (c/cbar) 4 pi sum w dI, d(rho v) = (4 pi c sum w n dI) / (c cbar)
     const double dE = a.k_fe * (double)sh.dE[lane];
     const double dx = a.k_fm * (double)sh.dF[0][lane], dy = a.k_fm * (double)sh.dF[1][lane],
@@ -594,22 +488,8 @@ cudaError_t launch_t(rt_state *s, double dt) {
   a.newton_max_iter = s->params.newton_max_iter;
   a.status = s->d_status;
   a.bad_cell = s->d_bad;
-  a.nbr_local = s->d_nbr_local;
-  a.halo_ptr = s->d_halo_ptr;
-  a.halo = s->d_halo;
-  a.block_staged = s->d_block_staged;
-  a.row_cap = s->row_cap;
-  a.row_stride = s->row_stride;
-  const size_t dyn = DynLayout<R>::bytes(s->row_cap, s->row_stride);
-  static bool attr_set = false;  // one per kernel instantiation
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(step_kernel<R, PPT, MOVING, FULL>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
   const unsigned blocks = (unsigned)((s->n_cells + CPB - 1) / CPB);
-  step_kernel<R, PPT, MOVING, FULL><<<blocks, NT, dyn, s->stream>>>(a);
+  step_kernel<R, PPT, MOVING, FULL><<<blocks, NT, 0, s->stream>>>(a);
   s->launches++;
   return cudaGetLastError();
 }

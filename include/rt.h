@@ -180,6 +180,21 @@ int rt_moments(rt_state *s, double *E, double *F, double *P, int on_device);
  *   12 = 0 + 1 + 2 (conserved), 13..15 = momentum totals (conserved). */
 int rt_totals(rt_state *s, double out[16]);
 
+/* The totals of rt_totals, for callers that cannot allocate device memory
+ * (no counterpart in the paper: the paper has no GPU).  rt_totals sums into a
+ * buffer that rt_create allocated; this call keeps its partial sums and
+ * result in one static device array of the library (197 KB on every device
+ * that loads it, kept until exit), so the call itself allocates nothing --
+ * for code that runs where cudaMalloc is not allowed, or whose device
+ * memory belongs to another allocator.  At most 8,388,608 cells; larger
+ * states return RT_ERR_ARG.  The first call on a device looks up the array's
+ * address (cudaGetSymbolAddress, with that device current): make it before
+ * any stream capture.  All calls on a device share the array, so calls
+ * whose GPU work overlaps race; each call rewrites everything it reads.
+ * Synchronises the state's stream; does not report the latched per-cell
+ * status (rt_sync does).  out: host, 16 doubles, layout of rt_totals. */
+int rt_totals_noalloc(rt_state *s, double out[16]);
+
 /* Waits for the state's stream and returns the latched per-cell status. */
 int rt_sync(rt_state *s);
 

@@ -76,6 +76,9 @@ def lib():
         L.orc_totals.argtypes = [P, vp, vp, vp, vp, vp]
         L.orc_step_range.argtypes = [P, d, vp, vp, vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int64]
         L.orc_step_range.restype = i
+        L.orc_transport_adjoint.argtypes = [P, d, vp, vp]
+        L.orc_adjoint_step.argtypes = [P, d] + [vp] * 12
+        L.orc_adjoint_step.restype = i
         _lib = L
     return _lib
 
@@ -215,6 +218,26 @@ class Oracle:
 
     def positivity(self):
         return lib().orc_positivity(ctypes.byref(self.p))
+
+    def transport_adjoint(self, dt, lam):
+        lam = _f64(lam)
+        out = np.empty_like(lam)
+        lib().orc_transport_adjoint(ctypes.byref(self.p), float(dt), lam.ctypes.data,
+                                    out.ctypes.data)
+        return out
+
+    def adjoint_step(self, dt, I, e, m, lI1, le1, lm1, gP, gJ):
+        """Cotangents of the step's inputs (I, e, m) from those of its
+        outputs; gP, gJ (float64 [N]) accumulate dL/dkappa_P, dL/dkappa_J."""
+        I, e, m = _f64(I), _f64(e), _f64(m)
+        lI1, le1, lm1 = _f64(lI1), _f64(le1), _f64(lm1)
+        lI, le, lm = np.empty_like(I), np.empty_like(e), np.empty_like(m)
+        work = np.empty(2 * I.size)
+        lib().orc_adjoint_step(ctypes.byref(self.p), float(dt), I.ctypes.data, e.ctypes.data,
+                               m.ctypes.data, lI1.ctypes.data, le1.ctypes.data, lm1.ctypes.data,
+                               lI.ctypes.data, le.ctypes.data, lm.ctypes.data, gP.ctypes.data,
+                               gJ.ctypes.data, work.ctypes.data)
+        return lI, le, lm
 
     def temperature(self):
         """Gas temperature from the conserved gas state."""

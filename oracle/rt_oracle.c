@@ -503,3 +503,219 @@ void orc_totals(const orc_problem *p, const double *I, const double *e, const do
   out[12] = out[0] + out[1] + out[2];
   for (int k = 0; k < 3; ++k) out[13 + k] = out[3 + k] + out[6 + k] + out[9 + k];
 }
+
+/* ========================================================================
+ * Discrete adjoint of one step (the gradient of a scalar loss through
+ * transport then source), written out by hand in reverse order of the
+ * forward statements above.  The absorption opacity is the parameter:
+ * kappa_P and kappa_J each receive a gradient; kappa_s, rho and the mesh are
+ * fixed.  Inputs: the step's forward inputs I, e, m and the cotangents
+ * lI1 = dL/dI^{n+1}, le1 = dL/de^{n+1}, lm1 = dL/dm^{n+1}.  Outputs:
+ * lI = dL/dI^n, le = dL/de^n, lm = dL/dm^n; gP, gJ accumulate (+=)
+ * dL/dkappa_P, dL/dkappa_J.  The boundary / emitter tallies are outputs only
+ * (no loss depends on them), so they carry no cotangent.
+ * --------------------------------------------------------------------- */
+
+/* Transpose of the transport map I* = M I (Sec. 3.2): M is linear in I with
+ * M_cc,a = 1 - dt/V_c sum_f max(u_fa, 0) and M_c,nbr,a = -dt/V_c u_fa for
+ * the faces where u_fa < 0.  A face outflow of cell j (u_jfa > 0) is the
+ * inflow of its neighbour through the same face, so
+ *   (M^T l)_ja = l_ja - sum_{f in j, u_jfa > 0} u_jfa (dt/V_j l_ja - dt/V_nbr l_nbr,a). */
+void orc_transport_adjoint(const orc_problem *p, double dt, const double *l, double *out) {
+  const int A = p->n_angles;
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < p->n_cells; ++c) {
+    for (int a = 0; a < A; ++a) {
+      const double *na = p->dir + 3 * a;
+      double acc = 0.0;
+      for (int64_t k = p->cell_face_ptr[c]; k < p->cell_face_ptr[c + 1]; ++k) {
+        int64_t f, nbr;
+        double sgn;
+        face_side(p, c, p->cell_face_idx[k], &f, &sgn, &nbr);
+        const double *nf = p->face_normal + 3 * f;
+        double area = p->face_area[f];
+        double ndotn = sgn * (na[0] * nf[0] + na[1] * nf[1] + na[2] * nf[2]);
+        double wdotn = 0.0;
+        if (p->face_w) {
+          const double *w = p->face_w + 3 * f;
+          wdotn = sgn * (w[0] * nf[0] + w[1] * nf[1] + w[2] * nf[2]);
+        }
+        double u = p->cbar * area * ndotn - area * wdotn;
+        if (u > 0.0)
+          acc += u * (dt / p->cell_volume[c] * l[c * A + a] - dt / p->cell_volume[nbr] * l[nbr * A + a]);
+      }
+      out[c * A + a] = l[c * A + a] - acc;
+    }
+  }
+}
+
+/* Reverse of source_interior for one cell. */
+static void source_interior_adjoint(const orc_problem *p, int64_t c, double dt, const double *Is,
+                                    const double *e_in, const double *m, const double *lI1,
+                                    double le1, const double *lm1, double *lIs, double *le,
+                                    double *lm, double *gP, double *gJ) {
+  const int A = p->n_angles;
+  const double rho = p->rho[c], kP = p->kappa_P[c], kJ = p->kappa_J[c], kS = p->kappa_s[c];
+  const double cb = p->cbar, cc = p->c, ar = p->a_rad;
+  /* ---- forward recomputation */
+  double v[3] = {m[0] / rho, m[1] / rho, m[2] / rho};
+  double G[A], wh[A], wt[A], It[A], x[A], Itn[A], In[A];
+  double Nw = 0.0;
+  for (int a = 0; a < A; ++a) {
+    const double *n = p->dir + 3 * a;
+    G[a] = 1.0 - (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / cc;
+    It[a] = G[a] * G[a] * G[a] * G[a] * Is[a];
+    wh[a] = p->wt[a] / (G[a] * G[a]);
+    Nw += wh[a];
+  }
+  double SI = 0.0, SG = 0.0;
+  for (int a = 0; a < A; ++a) {
+    wt[a] = wh[a] / Nw;
+    x[a] = dt * cb * rho * (kJ + kS) * G[a];
+    SI += wt[a] * It[a] / (1.0 + x[a]);
+    SG += wt[a] * G[a] / (1.0 + x[a]);
+  }
+  const double D = 1.0 - dt * cb * rho * kS * SG;
+  const double kin = 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) / rho;
+  const double rcv = rho * p->r_gas / (p->gamma_gas - 1.0);
+  const double Tn = (*e_in - kin) / rcv;
+  const double hJ = 1.0 - dt * cb * rho * kJ * SG / D;
+  const double alpha = dt * cc * rho * kP * ar * hJ;
+  const double g = rcv * Tn + dt * cc * rho * 4.0 * M_PI * kJ * SI / D;
+  double T;
+  orc_newton(alpha, rcv, g, p->newton_max_iter, &T, NULL);
+  const double B = ar * T * T * T * T / (4.0 * M_PI);
+  const double J = (SI + dt * cb * rho * kP * B * SG) / D;
+  const double q = dt * cb * rho * (kP * B + kS * J);
+  for (int a = 0; a < A; ++a) {
+    Itn[a] = (It[a] + q * G[a]) / (1.0 + x[a]);
+    In[a] = Itn[a] / (G[a] * G[a] * G[a] * G[a]);
+  }
+  /* ---- reverse */
+  /* e' = e + (c/cbar) dE, m' = m + dF/(c cbar), dE = 4 pi sum w (I* - I'),
+     dF = 4 pi c sum w n (I* - I') */
+  const double ldE = cc / cb * le1;
+  double ldF[3] = {lm1[0] / (cc * cb), lm1[1] / (cc * cb), lm1[2] / (cc * cb)};
+  double lG[A], lIt[A], lx[A], lwt[A];
+  double lq = 0.0;
+  for (int a = 0; a < A; ++a) {
+    const double *n = p->dir + 3 * a;
+    const double ex = 4.0 * M_PI * p->wt[a] * (ldE + cc * (n[0] * ldF[0] + n[1] * ldF[1] + n[2] * ldF[2]));
+    lIs[a] = ex;                     /* I* enters dE, dF directly */
+    const double lIn = lI1[a] - ex;  /* I' enters them with a minus sign */
+    const double G4 = G[a] * G[a] * G[a] * G[a];
+    const double lItn = lIn / G4;
+    lG[a] = -4.0 * In[a] / G[a] * lIn;
+    lIt[a] = lItn / (1.0 + x[a]);
+    lq += G[a] * lItn / (1.0 + x[a]);
+    lG[a] += q * lItn / (1.0 + x[a]);
+    lx[a] = -Itn[a] * lItn / (1.0 + x[a]);
+  }
+  double lB = dt * cb * rho * kP * lq;
+  double lJ = dt * cb * rho * kS * lq;
+  *gP += dt * cb * rho * B * lq;
+  /* J = (SI + dt cbar rho kP B SG) / D */
+  double lSI = lJ / D;
+  double lSG = dt * cb * rho * kP * B * lJ / D;
+  double lD = -J * lJ / D;
+  lB += dt * cb * rho * kP * SG * lJ / D;
+  *gP += dt * cb * rho * B * SG * lJ / D;
+  /* B = a T^4 / 4 pi; T from alpha T^4 + rcv T - g = 0 (implicit function) */
+  const double lT = ar * T * T * T / M_PI * lB;
+  const double Fp = 4.0 * alpha * T * T * T + rcv;
+  const double lalpha = -T * T * T * T / Fp * lT;
+  const double lg = lT / Fp;
+  /* g = rcv Tn + dt c rho 4 pi kJ SI / D */
+  const double lTn = rcv * lg;
+  lSI += dt * cc * rho * 4.0 * M_PI * kJ / D * lg;
+  lD += -dt * cc * rho * 4.0 * M_PI * kJ * SI / (D * D) * lg;
+  *gJ += dt * cc * rho * 4.0 * M_PI * SI / D * lg;
+  /* alpha = dt c rho kP a (1 - dt cbar rho kJ SG / D) */
+  *gP += dt * cc * rho * ar * hJ * lalpha;
+  *gJ += dt * cc * rho * kP * ar * (-dt * cb * rho * SG / D) * lalpha;
+  lSG += dt * cc * rho * kP * ar * (-dt * cb * rho * kJ / D) * lalpha;
+  lD += dt * cc * rho * kP * ar * (dt * cb * rho * kJ * SG / (D * D)) * lalpha;
+  /* Tn = (e - kin) / rcv, kin = |m|^2 / (2 rho) */
+  *le = le1 + lTn / rcv;
+  const double lkin = -lTn / rcv;
+  for (int k = 0; k < 3; ++k) lm[k] = lm1[k] + m[k] / rho * lkin;
+  /* D = 1 - dt cbar rho kS SG */
+  lSG += -dt * cb * rho * kS * lD;
+  /* SI = sum wt It / (1 + x), SG = sum wt G / (1 + x) */
+  double swl = 0.0;
+  for (int a = 0; a < A; ++a) {
+    const double r = 1.0 / (1.0 + x[a]);
+    lwt[a] = (It[a] * lSI + G[a] * lSG) * r;
+    lIt[a] += wt[a] * lSI * r;
+    lG[a] += wt[a] * lSG * r;
+    lx[a] += -wt[a] * (It[a] * lSI + G[a] * lSG) * r * r;
+    swl += wt[a] * lwt[a];
+  }
+  double lv[3] = {0.0, 0.0, 0.0};
+  for (int a = 0; a < A; ++a) {
+    /* x = dt cbar rho (kJ + kS) G */
+    *gJ += dt * cb * rho * G[a] * lx[a];
+    lG[a] += dt * cb * rho * (kJ + kS) * lx[a];
+    /* wt = wh / sum wh, wh = w / G^2 */
+    const double lwh = (lwt[a] - swl) / Nw;
+    lG[a] += -2.0 * wh[a] / G[a] * lwh;
+    /* It = G^4 I* */
+    lIs[a] += G[a] * G[a] * G[a] * G[a] * lIt[a];
+    lG[a] += 4.0 * G[a] * G[a] * G[a] * Is[a] * lIt[a];
+    /* G = 1 - v . n / c */
+    const double *n = p->dir + 3 * a;
+    for (int k = 0; k < 3; ++k) lv[k] += -n[k] / cc * lG[a];
+  }
+  for (int k = 0; k < 3; ++k) lm[k] += lv[k] / rho;
+}
+
+/* Reverse of source_emitter: I'_a = (I*_a + Y I_src G_a^-3) / (1 + Y G_a),
+ * Y = dt cbar emit_rate, G_a = 1 - v . n_a / c; the gas is a reservoir. */
+static void source_emitter_adjoint(const orc_problem *p, int64_t c, double dt, const double *Is,
+                                   const double *m, const double *lI1, double le1,
+                                   const double *lm1, double *lIs, double *le, double *lm) {
+  const int A = p->n_angles;
+  const double rho = p->rho[c];
+  const double v[3] = {m[0] / rho, m[1] / rho, m[2] / rho};
+  const double Y = dt * p->cbar * p->emit_rate[c];
+  double lv[3] = {0.0, 0.0, 0.0};
+  for (int a = 0; a < A; ++a) {
+    const double *n = p->dir + 3 * a;
+    const double G = 1.0 - (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / p->c;
+    const double G4 = G * G * G * G;
+    const double y = Y * G;
+    const double In = ((G4 * Is[a] + y * p->I_src[c]) / (1.0 + y)) / G4;
+    lIs[a] = lI1[a] / (1.0 + y);
+    const double dIdG = (-3.0 * Y * p->I_src[c] / G4 - Y * In) / (1.0 + y);
+    for (int k = 0; k < 3; ++k) lv[k] += -n[k] / p->c * dIdG * lI1[a];
+  }
+  *le = le1;
+  for (int k = 0; k < 3; ++k) lm[k] = lm1[k] + lv[k] / rho;
+}
+
+/* Adjoint of one full step (transport then source).  work[N*A] x 2 scratch. */
+int orc_adjoint_step(const orc_problem *p, double dt, const double *I, const double *e,
+                     const double *m, const double *lI1, const double *le1, const double *lm1,
+                     double *lI, double *le, double *lm, double *gP, double *gJ, double *work) {
+  const int A = p->n_angles;
+  double *Is = work, *lIs = work + p->n_cells * A;
+  orc_transport(p, dt, I, Is);
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < p->n_cells; ++c) {
+    const int k = p->kind ? p->kind[c] : 0;
+    if (k == 1) {
+      const double f = (p->tau[c] <= dt) ? 1.0 : dt / p->tau[c];
+      for (int a = 0; a < A; ++a) lIs[c * A + a] = (1.0 - f) * lI1[c * A + a];
+      le[c] = le1[c];
+      for (int d = 0; d < 3; ++d) lm[3 * c + d] = lm1[3 * c + d];
+    } else if (k == 2) {
+      source_emitter_adjoint(p, c, dt, Is + c * A, m + 3 * c, lI1 + c * A, le1[c], lm1 + 3 * c,
+                             lIs + c * A, le + c, lm + 3 * c);
+    } else {
+      source_interior_adjoint(p, c, dt, Is + c * A, e + c, m + 3 * c, lI1 + c * A, le1[c],
+                              lm1 + 3 * c, lIs + c * A, le + c, lm + 3 * c, gP + c, gJ + c);
+    }
+  }
+  orc_transport_adjoint(p, dt, lIs, lI);
+  return ORC_OK;
+}

@@ -198,6 +198,24 @@ int rt_totals_noalloc(rt_state *s, double out[16]);
 /* Waits for the state's stream and returns the latched per-cell status. */
 int rt_sync(rt_state *s);
 
+/* Discrete adjoint of one full step (the reverse of rt_step): given the
+ * step's forward inputs I^n[N][A], e^n[N], m^n[N][3] (as saved before the
+ * step, e.g. by a checkpoint) and the cotangents of its outputs
+ * lam_I1 = dL/dI^{n+1}, lam_e1 = dL/de^{n+1}, lam_m1 = dL/dm^{n+1}, writes
+ * lam_I = dL/dI^n, lam_e, lam_m and ADDS dL/dkappa_P and dL/dkappa_J (per
+ * cell, per unit mass) into grad_kappa_P, grad_kappa_J.  Transport
+ * (Sec. 3.2) is linear, its adjoint the transposed upwind gather; the source
+ * (Sec. 3.3) is reversed statement by statement, the quartic's root through
+ * the implicit-function theorem.  Boundary / emitter tallies carry no
+ * cotangent.  Intensities in the state precision, everything else double,
+ * caller order; on_device = 1: all arrays are device pointers.  dt <= 0:
+ * dt_cfl.  The first call allocates the adjoint's work buffers (8 intensity
+ * arrays + 24 doubles per cell), kept until rt_destroy. */
+int rt_adjoint_step(rt_state *s, double dt, const void *I_n, const double *e_n, const double *m_n,
+                    const void *lam_I1, const double *lam_e1, const double *lam_m1, void *lam_I,
+                    double *lam_e, double *lam_m, double *grad_kappa_P, double *grad_kappa_J,
+                    int on_device);
+
 /* Serialises the full evolving state (intensities, gas e and m, tallies) to
  * a host buffer.  buf == NULL: *bytes receives the size needed. */
 int rt_get_state(rt_state *s, void *buf, size_t *bytes);

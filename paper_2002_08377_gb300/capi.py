@@ -17,7 +17,7 @@ _NAMES = {0: "RT_OK", -1: "RT_ERR_ARG", -2: "RT_ERR_MESH", -3: "RT_ERR_CUDA", -4
 # every symbol include/rt.h declares (checked by the CPU tests)
 EXPORTS = ["rt_create", "rt_set_gas", "rt_set_cells", "rt_set_intensity", "rt_get_intensity",
            "rt_get_gas", "rt_dt_limits", "rt_step", "rt_run", "rt_launch", "rt_moments", "rt_totals", "rt_totals_noalloc",
-           "rt_sync", "rt_get_state", "rt_set_state", "rt_device_bytes", "rt_launch_count",
+           "rt_sync", "rt_adjoint_step", "rt_get_state", "rt_set_state", "rt_device_bytes", "rt_launch_count",
            "rt_last_error", "rt_destroy"]
 
 
@@ -80,6 +80,7 @@ def load(build_if_missing=True):
         "rt_totals": ([vp, vp], i32),
         "rt_totals_noalloc": ([vp, vp], i32),
         "rt_sync": ([vp], i32),
+        "rt_adjoint_step": ([vp, d] + [vp] * 12 + [i32], i32),
         "rt_get_state": ([vp, vp, ctypes.POINTER(ctypes.c_size_t)], i32),
         "rt_set_state": ([vp, vp, ctypes.c_size_t], i32),
         "rt_device_bytes": ([vp, ctypes.POINTER(ctypes.c_size_t)], i32),

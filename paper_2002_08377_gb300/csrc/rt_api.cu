@@ -606,6 +606,56 @@ int rt_sync(rt_state *s) {
   return sync_status(s);
 }
 
+int rt_adjoint_step(rt_state *s, double dt, const void *I_n, const double *e_n, const double *m_n,
+                    const void *lam_I1, const double *lam_e1, const double *lam_m1, void *lam_I,
+                    double *lam_e, double *lam_m, double *grad_kappa_P, double *grad_kappa_J,
+                    int on_device) {
+  if (!s) return RT_ERR_ARG;
+  if (!s->gas_set) return fail(s, RT_ERR_STATE, "rt_set_gas must be called before the adjoint");
+  if (!I_n || !e_n || !m_n || !lam_I1 || !lam_e1 || !lam_m1 || !lam_I || !lam_e || !lam_m ||
+      !grad_kappa_P || !grad_kappa_J)
+    return fail(s, RT_ERR_ARG, "rt_adjoint_step: NULL argument");
+  if (!(dt > 0)) dt = s->dt_cfl;
+  if (!std::isfinite(dt) || dt > s->dt_max) return fail(s, RT_ERR_CFL, "rt_adjoint_step: bad dt");
+  const int64_t N = s->n_cells;
+  const size_t nI = (size_t)N * s->n_angles * s->rsize;
+  if (!s->d_adj[0]) {
+    for (int k = 0; k < 8; ++k) RT_CUDA(s, dalloc_bytes(s, &s->d_adj[k], nI));
+    RT_CUDA(s, dalloc(s, &s->d_adj_ws, 14 * (size_t)N));
+    RT_CUDA(s, dalloc(s, &s->d_adj_stage, 10 * (size_t)N));
+  }
+  if (on_device) {
+    RT_CUDA(s, rt::adjoint_step(s, dt, I_n, e_n, m_n, lam_I1, lam_e1, lam_m1, lam_I, lam_e, lam_m,
+                                grad_kappa_P, grad_kappa_J));
+    RT_CUDA(s, cudaStreamSynchronize(s->stream));
+    return RT_OK;
+  }
+  // host buffers: stage through device copies in the caller's order
+  double *st = s->d_adj_stage;  // e, m(3), le1, lm1(3), gP, gJ; outputs reuse e / m / le1
+  double *de = st, *dm = st + N, *dle1 = st + 4 * N, *dlm1 = st + 5 * N, *dgP = st + 8 * N,
+         *dgJ = st + 9 * N;
+  const cudaMemcpyKind h2d = cudaMemcpyHostToDevice, d2h = cudaMemcpyDeviceToHost;
+  RT_CUDA(s, cudaMemcpyAsync(s->d_adj[5], I_n, nI, h2d, s->stream));
+  RT_CUDA(s, cudaMemcpyAsync(s->d_adj[6], lam_I1, nI, h2d, s->stream));
+  RT_CUDA(s, cudaMemcpyAsync(de, e_n, 8 * N, h2d, s->stream));
+  RT_CUDA(s, cudaMemcpyAsync(dm, m_n, 24 * N, h2d, s->stream));
+  RT_CUDA(s, cudaMemcpyAsync(dle1, lam_e1, 8 * N, h2d, s->stream));
+  RT_CUDA(s, cudaMemcpyAsync(dlm1, lam_m1, 24 * N, h2d, s->stream));
+  RT_CUDA(s, cudaMemcpyAsync(dgP, grad_kappa_P, 8 * N, h2d, s->stream));
+  RT_CUDA(s, cudaMemcpyAsync(dgJ, grad_kappa_J, 8 * N, h2d, s->stream));
+  // outputs: lam_I -> d_adj[7]; lam_e, lam_m overwrite the staging of lam_e1, lam_m1
+  // (read into the internal-order work area before any output is written)
+  RT_CUDA(s, rt::adjoint_step(s, dt, s->d_adj[5], de, dm, s->d_adj[6], dle1, dlm1, s->d_adj[7],
+                              dle1, dlm1, dgP, dgJ));
+  RT_CUDA(s, cudaMemcpyAsync(lam_I, s->d_adj[7], nI, d2h, s->stream));
+  RT_CUDA(s, cudaMemcpyAsync(lam_e, dle1, 8 * N, d2h, s->stream));
+  RT_CUDA(s, cudaMemcpyAsync(lam_m, dlm1, 24 * N, d2h, s->stream));
+  RT_CUDA(s, cudaMemcpyAsync(grad_kappa_P, dgP, 8 * N, d2h, s->stream));
+  RT_CUDA(s, cudaMemcpyAsync(grad_kappa_J, dgJ, 8 * N, d2h, s->stream));
+  RT_CUDA(s, cudaStreamSynchronize(s->stream));
+  return RT_OK;
+}
+
 int rt_get_state(rt_state *s, void *buf, size_t *bytes) {
   if (!s || !bytes) return RT_ERR_ARG;
   const int64_t N = s->n_cells;
@@ -664,6 +714,10 @@ const char *rt_last_error(const rt_state *s) { return s ? s->err.c_str() : "null
 void rt_destroy(rt_state *s) {
   if (!s) return;
   if (s->stream || true) cudaStreamSynchronize(s->stream);
+  for (int k = 0; k < 8; ++k)
+    if (s->d_adj[k]) cudaFree(s->d_adj[k]);
+  if (s->d_adj_ws) cudaFree(s->d_adj_ws);
+  if (s->d_adj_stage) cudaFree(s->d_adj_stage);
   void *bufs[] = {s->d_wface, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
                   s->d_gd, s->d_kind, s->d_aux, s->d_bc_row, s->d_I0, s->d_ext, s->d_dir, s->d_wt,
                   s->d_dir64, s->d_wt64, s->d_I[0], s->d_I[1], s->d_status, s->d_bad,

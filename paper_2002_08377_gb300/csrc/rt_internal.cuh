@@ -136,6 +136,9 @@ struct rt_state {
   int cur = 0;
   unsigned *d_status = nullptr;
   unsigned long long *d_bad = nullptr;
+  void *d_adj[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double *d_adj_ws = nullptr;     // [14 N] adjoint per-cell work (internal order)
+  double *d_adj_stage = nullptr;  // [10 N] host-path staging of per-cell vectors
   double *d_scratch = nullptr;  // reduction partials
   size_t scratch_len = 0;
   double *d_out16 = nullptr;
@@ -154,5 +157,10 @@ cudaError_t launch_moments(rt_state *s, double *E, double *F, double *P);
 cudaError_t launch_totals(rt_state *s, double *d_out16);
 cudaError_t launch_gas_out(rt_state *s, double *e, double *m, double *ext);
 cudaError_t launch_cellv(rt_state *s);
+
+// adjoint (rt_adjoint.cu): device pointers, caller order
+cudaError_t adjoint_step(rt_state *s, double dt, const void *I, const double *e, const double *m,
+                         const void *lI1, const double *le1, const double *lm1, void *lI,
+                         double *le, double *lm, double *gP, double *gJ);
 
 }  // namespace rt

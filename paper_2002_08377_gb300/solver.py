@@ -161,6 +161,33 @@ class RTSolver:
         self._check(self.lib.rt_moments(self.state, E.ctypes.data, F.ctypes.data, P.ctypes.data, 0))
         return E, F, P
 
+    def gas_device(self):
+        """(e[N], m[N][3]) as float64 CUDA tensors, caller order."""
+        e = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        m = torch.empty((self.N, 3), dtype=torch.float64, device="cuda")
+        self._check(self.lib.rt_get_gas(self.state, ctypes.c_void_p(e.data_ptr()),
+                                        ctypes.c_void_p(m.data_ptr()), None, 1))
+        return e, m
+
+    def adjoint_step(self, dt, I, e, m, lam_I1, lam_e1, lam_m1, grad_kP, grad_kJ):
+        """Reverse of one step on CUDA tensors (caller order).  I, lam_I1 in
+        the state precision; e, m, cotangents and gradients float64.  Returns
+        (lam_I, lam_e, lam_m); grad_kP, grad_kJ are accumulated in place."""
+        def dev(x, dt_):
+            return x.to(device="cuda", dtype=dt_).contiguous()
+        I, lam_I1 = dev(I, self.tdtype), dev(lam_I1, self.tdtype)
+        e, m = dev(e, torch.float64), dev(m, torch.float64)
+        lam_e1, lam_m1 = dev(lam_e1, torch.float64), dev(lam_m1, torch.float64)
+        lam_I = torch.empty_like(I)
+        lam_e, lam_m = torch.empty_like(e), torch.empty_like(m)
+        assert grad_kP.is_cuda and grad_kP.dtype == torch.float64 and grad_kP.is_contiguous()
+        assert grad_kJ.is_cuda and grad_kJ.dtype == torch.float64 and grad_kJ.is_contiguous()
+        p = lambda t: ctypes.c_void_p(t.data_ptr())
+        self._check(self.lib.rt_adjoint_step(self.state, float(dt), p(I), p(e), p(m), p(lam_I1),
+                                             p(lam_e1), p(lam_m1), p(lam_I), p(lam_e), p(lam_m),
+                                             p(grad_kP), p(grad_kJ), 1))
+        return lam_I, lam_e, lam_m
+
     def totals(self):
         out = np.empty(16)
         self._check(self.lib.rt_totals(self.state, out.ctypes.data))

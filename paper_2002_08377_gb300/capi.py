@@ -80,7 +80,7 @@ def load(build_if_missing=True):
         "rt_totals": ([vp, vp], i32),
         "rt_totals_noalloc": ([vp, vp], i32),
         "rt_sync": ([vp], i32),
-        "rt_adjoint_step": ([vp, d] + [vp] * 12 + [i32], i32),
+        "rt_adjoint_step": ([vp, d] + [vp] * 11 + [i32], i32),
         "rt_get_state": ([vp, vp, ctypes.POINTER(ctypes.c_size_t)], i32),
         "rt_set_state": ([vp, vp, ctypes.c_size_t], i32),
         "rt_device_bytes": ([vp, ctypes.POINTER(ctypes.c_size_t)], i32),

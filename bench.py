@@ -33,10 +33,15 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-angle updates/s (transport+implicit source), FP32 vs FP64, % HBM roofline"
 UNIT = "cell-angle updates/s"
 
-# DRAM bytes per launch of the FP32 step kernel from one ncu capture of the
-# full workload, valid while the kernel source has the recorded hash.
-NCU_TRAFFIC = {"fp32": None, "fp64": None}
-NCU_SOURCE_SHA = None
+# DRAM bytes (read + write) per launch of the FP32 step kernel, from one ncu
+# capture of the 96^3 case (1021.9 MB) scaled to the 128^3 workload by the
+# cell count (traffic grows with the cells processed); valid while the kernel
+# source has the recorded hash.
+NCU_TRAFFIC = {"fp32": 1021.868544e6 * 2097152 / 884736, "fp64": None}
+NCU_SOURCE_SHA = "89dcf742518a7a53"
+# FP64 arithmetic peak of the GPU (dense FMA, from the hardware's nominal
+# figure); the FP64 state is bound by it, not by HBM.
+FP64_PEAK_GFLOPS = 1250.0
 
 
 def kernel_source_sha():
@@ -51,6 +56,15 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def algorithmic_fp64_flops(n_cells, n_faces, n_angles):
+    """Floating-point operations the FP64 step must do: per directed face and
+    angle 5 (the flux coefficient n_a . n_f times cbar A_f, shared by an angle
+    and its antipode: 3; the upwind product and sum: 2), per cell and angle 2
+    for the update and 27 for the comoving source step."""
+    directed = 2.0 * n_faces
+    return 5.0 * directed * n_angles + 29.0 * n_cells * n_angles
 
 
 def algorithmic_bytes(n_cells, n_faces, n_angles, real_bytes):
@@ -309,13 +323,24 @@ def main():
         B = algorithmic_bytes(N, Nf, A, rb)
         achieved = B / (per * 1e-3) / 1e9
         traffic = NCU_TRAFFIC.get(prec) if NCU_SOURCE_SHA == kernel_source_sha() else None
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic,
+                "algorithmic_bytes_per_launch": B,
+                "peak_source": f"{peak_kind} HBM copy bandwidth"}
+        if prec == "fp64":
+            # double arithmetic runs at 1/64 of float on this GPU: the FP64 step
+            # is bound by it; its HBM fraction is kept for reference
+            F = algorithmic_fp64_flops(N, Nf, A)
+            gf = F / (per * 1e-3) / 1e9
+            roof = {"bound": "alu", "achieved": gf, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                    "frac": gf / FP64_PEAK_GFLOPS, "traffic": traffic,
+                    "algorithmic_flops_per_launch": F,
+                    "peak_source": "nominal dense FP64 FMA rate (1.25 TFLOP/s)",
+                    "hbm": {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                            "frac": achieved / hbm_peak, "algorithmic_bytes_per_launch": B}}
         results[prec] = {
             "value": N * A * steps * world / (ms * 1e-3), "ms_per_step": per, "steps": steps,
-            "launches": launches,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": traffic,
-                         "algorithmic_bytes_per_launch": B,
-                         "peak_source": f"{peak_kind} HBM copy bandwidth"}}
+            "launches": launches, "roofline": roof}
         if prec == "fp32" and not args.no_e2e:
             e2e_v, bi, bo = e2e_rate(sol, prob, dt, max(3, min(10, args.steps)))
             results["e2e"] = {"value": e2e_v * world, "unit": UNIT, "h2d_bytes_per_step": bi,

@@ -141,13 +141,22 @@ def dist_env():
 
 
 def max_over_ranks(x, world):
+    """Largest x over the ranks (the slowest rank's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(units_per_rank, ms_per_rank, world):
+    """Whole-job throughput: the units all ranks processed divided by the
+    slowest rank's time (weak scaling: every rank runs its own replica)."""
+    ms = max_over_ranks(ms_per_rank, world)
+    return units_per_rank * world / (ms * 1e-3), ms
 
 
 def barrier(world):

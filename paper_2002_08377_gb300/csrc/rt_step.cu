@@ -26,156 +26,11 @@
 #include <cuda_runtime.h>
 
 #include "rt_internal.cuh"
+#include "rt_step_common.cuh"
 
 namespace rt {
 namespace {
-
-constexpr int KT = 8;         // threads per cell
-constexpr int NT = KT * CPB;  // threads per block
-
-// ------------------------------------------------------------ pair arithmetic
-template <typename R> struct P2;
-template <> struct P2<float> { using t = float2; };
-template <> struct P2<double> { using t = double2; };
-template <typename R> using pair_t = typename P2<R>::t;
-
-__device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
-__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {
-  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
-}
-__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ double2 pmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x, a.y * b.y);
-}
-__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ double2 padd(double2 a, double2 b) {
-  return make_double2(a.x + b.x, a.y + b.y);
-}
-
-// Reciprocal: float uses the hardware approximation (relative error ~1e-7,
-// inside the float state's error budget); double refines the float estimate
-// with two Newton steps (about 1 ulp).  Arguments are 1 + x (x >= 0) and
-// Gamma^2, far inside float range.
-__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ double rcp(double x) {
-  double r = (double)__fdividef(1.0f, (float)x);
-  r = fma(r, fma(-x, r, 1.0), r);
-  r = fma(r, fma(-x, r, 1.0), r);
-  return r;
-}
-
-template <typename R> __device__ __forceinline__ typename SlotOf<R>::type load_slot(
-    const typename SlotOf<R>::type *p);
-template <> __device__ __forceinline__ SlotF load_slot<float>(const SlotF *p) {
-  float4 v = __ldg(reinterpret_cast<const float4 *>(p));
-  return {v.x, v.y, v.z, v.w};
-}
-template <> __device__ __forceinline__ SlotD load_slot<double>(const SlotD *p) {
-  const double2 *q = reinterpret_cast<const double2 *>(p);
-  double2 a = __ldg(q), b = __ldg(q + 1);
-  return {a.x, a.y, b.x, b.y};
-}
-
-// n_a . s of a slot (float) or cbar A ((n_ax n_fx + n_ay n_fy) + n_az n_fz)
-// without contraction (double); and the slot's A w . n
-__device__ __forceinline__ float slot_dot(float x, float y, float z, const SlotF &s) {
-  return fmaf(x, s.sx, fmaf(y, s.sy, z * s.sz));
-}
-__device__ __forceinline__ double slot_dot(double x, double y, double z, const SlotD &s) {
-  return __dmul_rn(s.ca, __dadd_rn(__dadd_rn(__dmul_rn(x, s.nx), __dmul_rn(y, s.ny)),
-                                   __dmul_rn(z, s.nz)));
-}
-__device__ __forceinline__ float slot_w(const SlotF &s, const double *, int64_t) { return s.w; }
-__device__ __forceinline__ double slot_w(const SlotD &, const double *wf, int64_t k) {
-  return wf[k];
-}
-
-template <typename T> __device__ __forceinline__ T cell_sum(T v) {
-#pragma unroll
-  for (int o = KT / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__device__ __forceinline__ unsigned cell_or(unsigned v) {
-#pragma unroll
-  for (int o = KT / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-// Positive root of alpha T^4 + beta T = g (alpha >= 0, beta > 0, g >= 0).
-// f is increasing and convex on T > 0, so Newton from any point at or above
-// the root decreases monotonically onto it.  Double states: start at
-// min(g/beta, (g/alpha)^(1/4)) and stop when an iterate fails to decrease or
-// moves by at most 1e-15 of itself.  Float states: the same iteration in
-// float to a relative 1e-7, then one Newton step in double (the float
-// root's error ~1e-7 becomes ~1e-14); coefficients outside float range fall
-// back to the double iteration.  Returns 1 if it did not converge.
-__device__ __forceinline__ float fp_of(float af, float bf, float t) {
-  return fmaf(4.0f * af * t * t, t, bf);
-}
-
-template <bool FLOAT_STATE>
-__device__ __forceinline__ int quartic_root(double alpha, double beta, double g, int max_iter,
-                                            double *T_out) {
-  if (FLOAT_STATE) {
-    const float af = (float)alpha, bf = (float)beta, gf = (float)g;
-    float t = __fdividef(gf, bf);
-    if (af > 0.0f) t = fminf(t, sqrtf(sqrtf(__fdividef(gf, af))));
-    bool done = false;
-    for (int it = 0; it < max_iter && !done; ++it) {
-      const float t2 = t * t;
-      const float f = fmaf(af * t2, t2, fmaf(bf, t, -gf));
-      const float fp = fmaf(4.0f * af * t2, t, bf);
-      const float tn = t - __fdividef(f, fp);
-      if (!(tn < t)) {
-        done = true;
-      } else {
-        done = (t - tn <= 1e-7f * t);
-        t = tn;
-      }
-    }
-    if (isfinite(t) && t >= 0.0f && isfinite(fp_of(af, bf, t))) {
-      if (!done) {
-        *T_out = t;
-        return 1;
-      }
-      const double T = t, T2 = T * T;
-      const double f = fma(alpha * T2, T2, fma(beta, T, -g));
-      const double fp = fma(4.0 * alpha * T2, T, beta);
-      *T_out = fma(-f, rcp(fp), T);
-      return 0;
-    }
-  }
-  double T = g / beta;
-  if (alpha > 0.0) T = fmin(T, sqrt(sqrt(g / alpha)));
-  bool done = false;
-  int it = 0;
-  while (!done && it < max_iter) {
-    const double T2 = T * T;
-    const double f = fma(alpha * T2, T2, fma(beta, T, -g));
-    const double fp = fma(4.0 * alpha * T2, T, beta);
-    const double Tn = T - f / fp;
-    ++it;
-    if (!(Tn < T)) {
-      done = true;
-    } else {
-      done = (T - Tn <= 1e-15 * T);
-      T = Tn;
-    }
-  }
-  *T_out = T;
-  return done ? 0 : 1;
-}
+using namespace step;
 
 template <typename R> struct Shared {
   GasStatic gs[CPB];  // gas of the block's cells, prefetched for warp 0
@@ -185,22 +40,6 @@ template <typename R> struct Shared {
   R dE[CPB], dF[3][CPB];        // sum w (I* - I') and sum w n (I* - I')
   unsigned bad[CPB];
 };
-
-// One face's contribution to sum_f u I_up for the thread's pairs: v is the
-// neighbour's (I_p, I_{p+H}) pair, Ia/Ib the cell's own values.
-template <typename R, bool MOVING>
-__device__ __forceinline__ void face_pair(R d, R w, pair_t<R> v, R Ia, R Ib, R &acca, R &accb) {
-  if (MOVING) {
-    const R ua = d - w, ub = -d - w;
-    acca = fma(ua, ua > R(0) ? Ia : v.x, acca);
-    accb = fma(ub, ub > R(0) ? Ib : v.y, accb);
-  } else {
-    // u_a = d, u_b = -d: exactly one of the pair takes the neighbour's value
-    const bool out = d > R(0);
-    acca = fma(d, out ? Ia : v.x, acca);
-    accb = fma(-d, out ? v.y : Ib, accb);
-  }
-}
 
 // sum_f u I_up over the slots [k0, k1) of one cell, neighbour rows read
 // through nbr[k] (L1/L2 serve the reuse between neighbouring cells; cells are
@@ -230,22 +69,59 @@ __device__ __forceinline__ void face_sum(const S *__restrict__ slot, const int32
   }
 }
 
-template <typename R, int PPT, bool MOVING, bool FULL>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) step_kernel(const StepArgs<R> a) {
+// The same sum with the tile's neighbour rows, slots and tile-local rows
+// staged in shared memory (rows `stride` bytes apart).
+template <typename R, int PPT, bool MOVING, bool FULL, typename S>
+__device__ __forceinline__ void face_sum_staged(const S *slot, const uint16_t *loc,
+                                                const double *__restrict__ wface, int k0, int k1,
+                                                const unsigned char *rows, int stride, int sub,
+                                                const R (&nx)[PPT], const R (&ny)[PPT],
+                                                const R (&nz)[PPT], const R (&Ia)[PPT],
+                                                const R (&Ib)[PPT], R (&acca)[PPT], R (&accb)[PPT],
+                                                int np) {
   using V = pair_t<R>;
-  using S = typename SlotOf<R>::type;
-  __shared__ Shared<R> sh;
+#pragma unroll 4
+  for (int k = k0; k < k1; ++k) {
+    const S s = slot[k];
+    const V *In = reinterpret_cast<const V *>(rows + (int)loc[k] * stride) + sub;
+    const R w = MOVING ? slot_w(s, wface, k) : R(0);
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      if (FULL || j < np) {
+        const V v = In[KT * j];
+        face_pair<R, MOVING>(slot_dot(nx[j], ny[j], nz[j], s), w, v, Ia[j], Ib[j], acca[j],
+                             accb[j]);
+      }
+    }
+  }
+}
+
+// A tile staged in shared memory: its own rows (0..CPB-1) and halo rows,
+// its face slots and their tile-local rows; rows == nullptr: global path.
+template <typename R> struct TileStage {
+  const unsigned char *rows = nullptr;
+  int stride = 0;
+  const typename SlotOf<R>::type *slots = nullptr;
+  const uint16_t *loc = nullptr;
+};
+
+// One tile of CPB cells: phases A-D (see the top of the file).  Ends with
+// warp 0 in phase D; callers that reuse `sh` synchronise first.
+template <typename R, int PPT, bool MOVING, bool FULL>
+__device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t tile, Shared<R> &sh,
+                                          const TileStage<R> stg, const unsigned timeout) {
+  using V = pair_t<R>;
   const int lc = threadIdx.x / KT;
   const int sub = threadIdx.x % KT;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int64_t cell = (int64_t)blockIdx.x * CPB + lc;
+  const int64_t cell = tile * CPB + lc;
   const bool live = cell < a.n_cells;
   const int64_t c = live ? cell : a.n_cells - 1;  // dead lanes shadow the last cell
   const int A = a.n_angles, H = a.half;
   const int np = FULL ? PPT : (H - sub + KT - 1) / KT;  // pairs p = sub + KT j < H
 
   // warp 0 prefetches its cells' gas state for phases B and D
-  const int64_t cl = (int64_t)blockIdx.x * CPB + lane;  // warp 0: lane-per-cell
+  const int64_t cl = tile * CPB + lane;  // warp 0: lane-per-cell
   if (warp == 0 && lane < CPB && cl < a.n_cells) {
     const char *g = reinterpret_cast<const char *>(a.gs + cl);
     const char *d = reinterpret_cast<const char *>(a.gd + cl);
@@ -258,7 +134,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) step_kernel(const 
   // ---------------- phase A: transport, I* = I - dt/V sum_f u I_up
   R nx[PPT], ny[PPT], nz[PPT], Ia[PPT], Ib[PPT], acca[PPT], accb[PPT];
   {
-    const V *Ic = reinterpret_cast<const V *>(a.I_in + (size_t)c * A) + sub;
+    const V *Ic = stg.rows ? reinterpret_cast<const V *>(stg.rows + lc * stg.stride) + sub
+                           : reinterpret_cast<const V *>(a.I_in + (size_t)c * A) + sub;
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
       const bool v = FULL || j < np;
@@ -273,8 +150,15 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) step_kernel(const 
       accb[j] = R(0);
     }
   }
-  face_sum<R, PPT, MOVING, FULL>(a.slot, a.nbr, a.wface, a.ptr[c], a.ptr[c + 1], a.I_in, A, sub, nx,
-                                 ny, nz, Ia, Ib, acca, accb, np);
+  if (stg.rows) {
+    const int64_t kb = a.ptr[tile * CPB];
+    face_sum_staged<R, PPT, MOVING, FULL>(stg.slots, stg.loc, a.wface ? a.wface + kb : nullptr,
+                                          (int)(a.ptr[c] - kb), (int)(a.ptr[c + 1] - kb), stg.rows,
+                                          stg.stride, sub, nx, ny, nz, Ia, Ib, acca, accb, np);
+  } else {
+    face_sum<R, PPT, MOVING, FULL>(a.slot, a.nbr, a.wface, a.ptr[c], a.ptr[c + 1], a.I_in, A, sub,
+                                   nx, ny, nz, Ia, Ib, acca, accb, np);
+  }
   {
     const R dtv = a.dt_r * a.inv_vol[c];
 #pragma unroll
@@ -407,7 +291,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) step_kernel(const 
   dfx = cell_sum(dfx);
   dfy = cell_sum(dfy);
   dfz = cell_sum(dfz);
-  nonfinite = cell_or(nonfinite);
+  nonfinite = cell_or(nonfinite) | timeout;
   if (sub == 0) {
     sh.dE[lc] = de;
     sh.dF[0][lc] = dfx;
@@ -450,6 +334,117 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) step_kernel(const 
 }
 
 template <typename R, int PPT, bool MOVING, bool FULL>
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) step_kernel(const StepArgs<R> a) {
+  __shared__ Shared<R> sh;
+  tile_step<R, PPT, MOVING, FULL>(a, blockIdx.x, sh, TileStage<R>{}, 0u);
+}
+
+// ------------------------------------------------------------ pipelined float kernel
+// Persistent CTAs walk the tiles; while a CTA computes tile t, warp 0 has
+// already asked the TMA engine for tile t + gridDim.x: its own and halo
+// intensity rows, its face slots and their tile-local rows, one bulk copy
+// each, into the other of two shared-memory stages, completed on that
+// stage's mbarrier.  Tiles whose halo or slots exceed a stage take the
+// global-gather path.
+struct PipeArgs {
+  int64_t n_tiles;
+  const int64_t *halo_ptr;
+  const int32_t *halo;
+  const int64_t *loc_off;
+  const uint16_t *loc;
+  const uint8_t *fits;
+  int stride;        // bytes per staged row (A floats)
+  int stage_bytes;
+  int slot_off, loc_off_b;  // byte offsets inside a stage
+};
+
+__host__ __device__ inline int pipe_slot_off(int stride) {
+  return (PIPE_ROWS * stride + 127) & ~127;
+}
+__host__ __device__ inline int pipe_loc_off(int stride) {
+  return pipe_slot_off(stride) + PIPE_SLOTS * (int)sizeof(SlotF);
+}
+__host__ __device__ inline int pipe_stage_bytes(int stride) {
+  return (pipe_loc_off(stride) + PIPE_SLOTS * (int)sizeof(uint16_t) + 127) & ~127;
+}
+
+struct PipeShared {
+  Shared<float> sh;
+  unsigned long long bar[2];
+};
+
+// Issue the bulk copies of tile t into stage st (warp 0; the tile fits).
+__device__ __forceinline__ void issue_tile(const StepArgs<float> &a, const PipeArgs &p, int64_t t,
+                                           unsigned char *stage, unsigned long long *bar, int lane) {
+  const int64_t c0 = t * CPB;
+  const int64_t c1 = c0 + CPB < a.n_cells ? c0 + CPB : a.n_cells;
+  const int64_t kb = a.ptr[c0];
+  const unsigned cnt = (unsigned)(a.ptr[c1] - kb);
+  const int64_t h0 = p.halo_ptr[t];
+  const int nh = (int)(p.halo_ptr[t + 1] - h0);
+  const int nown = (int)(c1 - c0);
+  const unsigned rb = (unsigned)(a.n_angles * sizeof(float));
+  const unsigned lb = (unsigned)((p.loc_off[t + 1] - p.loc_off[t]) * sizeof(uint16_t));
+  if (lane == 0) {
+    // the stage was read by the generic proxy in an earlier tile
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect_tx(bar, rb * (unsigned)(nown + nh) + cnt * (unsigned)sizeof(SlotF) + lb);
+    if (cnt > 0) {
+      bulk_copy_g2s(stage + p.slot_off, a.slot + kb, cnt * (unsigned)sizeof(SlotF), bar);
+      bulk_copy_g2s(stage + p.loc_off_b, p.loc + p.loc_off[t], lb, bar);
+    }
+  }
+  __syncwarp();
+  for (int r = lane; r < nown; r += 32)
+    bulk_copy_g2s(stage + r * p.stride, a.I_in + (size_t)(c0 + r) * a.n_angles, rb, bar);
+  for (int h = lane; h < nh; h += 32)
+    bulk_copy_g2s(stage + (CPB + h) * p.stride, a.I_in + (size_t)p.halo[h0 + h] * a.n_angles, rb,
+                  bar);
+}
+
+template <int PPT, bool MOVING, bool FULL>
+__global__ void __launch_bounds__(NT, 2) step_kernel_pipe(const StepArgs<float> a,
+                                                          const PipeArgs p) {
+  __shared__ PipeShared ps;
+  extern __shared__ __align__(128) unsigned char dyn[];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    mbar_init(&ps.bar[0], 1);
+    mbar_init(&ps.bar[1], 1);
+  }
+  __syncthreads();
+  unsigned phase = 0;       // bit s: parity of stage s's next completion
+  unsigned failed = 0;      // a bounded wait gave up: stop staging
+  int64_t t = blockIdx.x;
+  if (warp == 0 && t < p.n_tiles && p.fits[t]) issue_tile(a, p, t, dyn, &ps.bar[0], lane);
+  for (int it = 0; t < p.n_tiles; t += gridDim.x, ++it) {
+    const int st = it & 1;
+    unsigned char *stage = dyn + st * p.stage_bytes;
+    const int64_t tn = t + gridDim.x;
+    if (warp == 0 && !failed && tn < p.n_tiles && p.fits[tn])
+      issue_tile(a, p, tn, dyn + (st ^ 1) * p.stage_bytes, &ps.bar[st ^ 1], lane);
+    TileStage<float> stg;
+    unsigned timeout = 0;
+    if (p.fits[t] && !failed) {
+      if (!mbar_wait_bounded(&ps.bar[st], (phase >> st) & 1u)) {
+        timeout = ST_TIMEOUT;
+        failed = 1;
+      }
+      phase ^= 1u << st;
+      if (!timeout) {
+        stg.rows = stage;
+        stg.stride = p.stride;
+        stg.slots = reinterpret_cast<const SlotF *>(stage + p.slot_off);
+        stg.loc = reinterpret_cast<const uint16_t *>(stage + p.loc_off_b);
+      }
+    }
+    failed = __syncthreads_or(failed);
+    tile_step<float, PPT, MOVING, FULL>(a, t, ps.sh, stg, timeout);
+    __syncthreads();  // `sh` and this stage are reused next
+  }
+}
+
+template <typename R, int PPT, bool MOVING, bool FULL>
 cudaError_t launch_t(rt_state *s, double dt) {
   StepArgs<R> a;
   a.n_cells = s->n_cells;
@@ -488,6 +483,35 @@ cudaError_t launch_t(rt_state *s, double dt) {
   a.newton_max_iter = s->params.newton_max_iter;
   a.status = s->d_status;
   a.bad_cell = s->d_bad;
+  if constexpr (sizeof(R) == 4) {
+    if (s->pipe) {
+      PipeArgs p;
+      p.n_tiles = s->n_tiles;
+      p.halo_ptr = s->d_halo_ptr;
+      p.halo = s->d_halo;
+      p.loc_off = s->d_loc_off;
+      p.loc = s->d_loc;
+      p.fits = s->d_fits;
+      p.stride = s->n_angles * (int)sizeof(float);
+      p.stage_bytes = pipe_stage_bytes(p.stride);
+      p.slot_off = pipe_slot_off(p.stride);
+      p.loc_off_b = pipe_loc_off(p.stride);
+      const size_t dyn = 2 * (size_t)p.stage_bytes;
+      static bool attr_set = false;  // one per kernel instantiation
+      if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(step_kernel_pipe<PPT, MOVING, FULL>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)dyn);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+      }
+      const int64_t want = 2 * (int64_t)s->num_sms;
+      const unsigned grid = (unsigned)(s->n_tiles < want ? s->n_tiles : want);
+      step_kernel_pipe<PPT, MOVING, FULL><<<grid, NT, dyn, s->stream>>>(a, p);
+      s->launches++;
+      return cudaGetLastError();
+    }
+  }
   const unsigned blocks = (unsigned)((s->n_cells + CPB - 1) / CPB);
   step_kernel<R, PPT, MOVING, FULL><<<blocks, NT, 0, s->stream>>>(a);
   s->launches++;

@@ -1,0 +1,215 @@
+// Device helpers shared by the step kernels (rt_step.cu, rt_step_pipe.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rt_internal.cuh"
+
+namespace rt {
+namespace step {
+
+constexpr int KT = 8;         // threads per cell
+constexpr int NT = KT * CPB;  // threads per block
+
+// ------------------------------------------------------------ pair arithmetic
+template <typename R> struct P2;
+template <> struct P2<float> { using t = float2; };
+template <> struct P2<double> { using t = double2; };
+template <typename R> using pair_t = typename P2<R>::t;
+
+__device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x, a.y * b.y);
+}
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 padd(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+
+// Reciprocal: float uses the hardware approximation (relative error ~1e-7,
+// inside the float state's error budget); double refines the float estimate
+// with two Newton steps (about 1 ulp).  Arguments are 1 + x (x >= 0) and
+// Gamma^2, far inside float range.
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp(double x) {
+  double r = (double)__fdividef(1.0f, (float)x);
+  r = fma(r, fma(-x, r, 1.0), r);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return r;
+}
+
+template <typename R> __device__ __forceinline__ typename SlotOf<R>::type load_slot(
+    const typename SlotOf<R>::type *p);
+template <> __device__ __forceinline__ SlotF load_slot<float>(const SlotF *p) {
+  float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+  return {v.x, v.y, v.z, v.w};
+}
+template <> __device__ __forceinline__ SlotD load_slot<double>(const SlotD *p) {
+  const double2 *q = reinterpret_cast<const double2 *>(p);
+  double2 a = __ldg(q), b = __ldg(q + 1);
+  return {a.x, a.y, b.x, b.y};
+}
+
+// n_a . s of a slot (float) or cbar A ((n_ax n_fx + n_ay n_fy) + n_az n_fz)
+// without contraction (double); and the slot's A w . n
+__device__ __forceinline__ float slot_dot(float x, float y, float z, const SlotF &s) {
+  return fmaf(x, s.sx, fmaf(y, s.sy, z * s.sz));
+}
+__device__ __forceinline__ double slot_dot(double x, double y, double z, const SlotD &s) {
+  return __dmul_rn(s.ca, __dadd_rn(__dadd_rn(__dmul_rn(x, s.nx), __dmul_rn(y, s.ny)),
+                                   __dmul_rn(z, s.nz)));
+}
+__device__ __forceinline__ float slot_w(const SlotF &s, const double *, int64_t) { return s.w; }
+__device__ __forceinline__ double slot_w(const SlotD &, const double *wf, int64_t k) {
+  return wf[k];
+}
+
+template <typename T> __device__ __forceinline__ T cell_sum(T v) {
+#pragma unroll
+  for (int o = KT / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned cell_or(unsigned v) {
+#pragma unroll
+  for (int o = KT / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Positive root of alpha T^4 + beta T = g (alpha >= 0, beta > 0, g >= 0).
+// f is increasing and convex on T > 0, so Newton from any point at or above
+// the root decreases monotonically onto it.  Double states: start at
+// min(g/beta, (g/alpha)^(1/4)) and stop when an iterate fails to decrease or
+// moves by at most 1e-15 of itself.  Float states: the same iteration in
+// float to a relative 1e-7, then one Newton step in double (the float
+// root's error ~1e-7 becomes ~1e-14); coefficients outside float range fall
+// back to the double iteration.  Returns 1 if it did not converge.
+__device__ __forceinline__ float fp_of(float af, float bf, float t) {
+  return fmaf(4.0f * af * t * t, t, bf);
+}
+
+template <bool FLOAT_STATE>
+__device__ __forceinline__ int quartic_root(double alpha, double beta, double g, int max_iter,
+                                            double *T_out) {
+  if (FLOAT_STATE) {
+    const float af = (float)alpha, bf = (float)beta, gf = (float)g;
+    float t = __fdividef(gf, bf);
+    if (af > 0.0f) t = fminf(t, sqrtf(sqrtf(__fdividef(gf, af))));
+    bool done = false;
+    for (int it = 0; it < max_iter && !done; ++it) {
+      const float t2 = t * t;
+      const float f = fmaf(af * t2, t2, fmaf(bf, t, -gf));
+      const float fp = fmaf(4.0f * af * t2, t, bf);
+      const float tn = t - __fdividef(f, fp);
+      if (!(tn < t)) {
+        done = true;
+      } else {
+        done = (t - tn <= 1e-7f * t);
+        t = tn;
+      }
+    }
+    if (isfinite(t) && t >= 0.0f && isfinite(fp_of(af, bf, t))) {
+      if (!done) {
+        *T_out = t;
+        return 1;
+      }
+      const double T = t, T2 = T * T;
+      const double f = fma(alpha * T2, T2, fma(beta, T, -g));
+      const double fp = fma(4.0 * alpha * T2, T, beta);
+      *T_out = fma(-f, rcp(fp), T);
+      return 0;
+    }
+  }
+  double T = g / beta;
+  if (alpha > 0.0) T = fmin(T, sqrt(sqrt(g / alpha)));
+  bool done = false;
+  int it = 0;
+  while (!done && it < max_iter) {
+    const double T2 = T * T;
+    const double f = fma(alpha * T2, T2, fma(beta, T, -g));
+    const double fp = fma(4.0 * alpha * T2, T, beta);
+    const double Tn = T - f / fp;
+    ++it;
+    if (!(Tn < T)) {
+      done = true;
+    } else {
+      done = (T - Tn <= 1e-15 * T);
+      T = Tn;
+    }
+  }
+  *T_out = T;
+  return done ? 0 : 1;
+}
+
+// One face's contribution to sum_f u I_up for the thread's pairs: v is the
+// neighbour's (I_p, I_{p+H}) pair, Ia/Ib the cell's own values.
+template <typename R, bool MOVING>
+__device__ __forceinline__ void face_pair(R d, R w, pair_t<R> v, R Ia, R Ib, R &acca, R &accb) {
+  if (MOVING) {
+    const R ua = d - w, ub = -d - w;
+    acca = fma(ua, ua > R(0) ? Ia : v.x, acca);
+    accb = fma(ub, ub > R(0) ? Ib : v.y, accb);
+  } else {
+    // u_a = d, u_b = -d: exactly one of the pair takes the neighbour's value
+    const bool out = d > R(0);
+    acca = fma(d, out ? Ia : v.x, acca);
+    accb = fma(-d, out ? v.y : Ib, accb);
+  }
+}
+
+// ---- mbarrier + TMA bulk copy (global -> shared), completion by tx bytes
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes,
+                                              unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for phase `parity` of the barrier with an iteration limit (each
+// try_wait may itself suspend for a bounded time); false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
+  for (int it = 0; it < (1 << 20); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+}  // namespace step
+}  // namespace rt

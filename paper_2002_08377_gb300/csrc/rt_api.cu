@@ -157,47 +157,10 @@ template <typename R> int build_device_mesh(rt_state *s, const rt_mesh_desc *m,
   if (!wface.empty()) RT_CUDA(s, upload(s, &s->d_wface, wface));
   RT_CUDA(s, upload(s, &s->d_ptr, ptr));
   RT_CUDA(s, upload(s, &s->d_nbr, nbr));
-  if (sizeof(R) == 4 && (m->n_angles * sizeof(R)) % 16 == 0) {
-    // tiles of CPB consecutive cells for the pipelined float kernel
-    const int64_t N = m->n_cells;
-    const int64_t nt = (N + rt::CPB - 1) / rt::CPB;
-    std::vector<int64_t> hptr(nt + 1, 0), loff(nt + 1, 0);
-    std::vector<int32_t> halo, tmp;
-    std::vector<uint16_t> loc;
-    std::vector<uint8_t> fits(nt, 0);
-    for (int64_t t = 0; t < nt; ++t) {
-      const int64_t c0 = t * rt::CPB, c1 = std::min(N, c0 + rt::CPB);
-      tmp.clear();
-      for (int64_t k = ptr[c0]; k < ptr[c1]; ++k)
-        if (nbr[k] < c0 || nbr[k] >= c1) tmp.push_back(nbr[k]);
-      std::sort(tmp.begin(), tmp.end());
-      tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
-      const int64_t cnt = ptr[c1] - ptr[c0];
-      const bool ok = rt::CPB + (int64_t)tmp.size() <= rt::PIPE_ROWS && cnt <= rt::PIPE_SLOTS;
-      fits[t] = ok ? 1 : 0;
-      s->tiles_fit += ok;
-      if (ok) {
-        halo.insert(halo.end(), tmp.begin(), tmp.end());
-        for (int64_t k = ptr[c0]; k < ptr[c1]; ++k) {
-          const int32_t g = nbr[k];
-          loc.push_back(g >= c0 && g < c1
-                            ? (uint16_t)(g - c0)
-                            : (uint16_t)(rt::CPB + (std::lower_bound(tmp.begin(), tmp.end(), g) -
-                                                    tmp.begin())));
-        }
-        while (loc.size() % 8) loc.push_back(0);  // 16-byte aligned per tile
-      }
-      hptr[t + 1] = (int64_t)halo.size();
-      loff[t + 1] = (int64_t)loc.size();
-    }
-    s->n_tiles = nt;
-    RT_CUDA(s, upload(s, &s->d_halo_ptr, hptr));
-    RT_CUDA(s, upload(s, &s->d_halo, halo));
-    RT_CUDA(s, upload(s, &s->d_loc_off, loff));
-    RT_CUDA(s, upload(s, &s->d_loc, loc));
-    RT_CUDA(s, upload(s, &s->d_fits, fits));
-    RT_CUDA(s, cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device));
-    s->pipe = true;
+  s->max_block_slots = 0;
+  for (int64_t c0 = 0; c0 < m->n_cells; c0 += rt::CPB) {
+    const int64_t c1 = std::min<int64_t>(m->n_cells, c0 + rt::CPB);
+    s->max_block_slots = std::max(s->max_block_slots, ptr[c1] - ptr[c0]);
   }
   typename rt::SlotOf<R>::type *ds = nullptr;
   RT_CUDA(s, upload(s, &ds, slot));
@@ -293,10 +256,6 @@ int sync_status(rt_state *s) {
   RT_CUDA(s, cudaMemcpy(&bad, s->d_bad, sizeof bad, cudaMemcpyDeviceToHost));
   long long cell = bad < (unsigned long long)s->n_cells ? (long long)s->cell_of[bad] : -1;
   char buf[160];
-  if (st & rt::ST_TIMEOUT) {
-    snprintf(buf, sizeof buf, "a bounded wait for staged intensity rows gave up (cell %lld)", cell);
-    return fail(s, RT_ERR_CUDA, buf);
-  }
   if (st & rt::ST_NONFINITE) {
     snprintf(buf, sizeof buf, "non-finite intensity or temperature (first cell %lld)", cell);
     return fail(s, RT_ERR_NONFINITE, buf);
@@ -764,7 +723,7 @@ void rt_destroy(rt_state *s) {
     if (s->d_adj[k]) cudaFree(s->d_adj[k]);
   if (s->d_adj_ws) cudaFree(s->d_adj_ws);
   if (s->d_adj_stage) cudaFree(s->d_adj_stage);
-  void *bufs[] = {s->d_halo_ptr, s->d_halo, s->d_loc_off, s->d_loc, s->d_fits, s->d_wface, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
+  void *bufs[] = {s->d_wface, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
                   s->d_gd, s->d_kind, s->d_aux, s->d_bc_row, s->d_I0, s->d_ext, s->d_dir, s->d_wt,
                   s->d_dir64, s->d_wt64, s->d_I[0], s->d_I[1], s->d_status, s->d_bad,
                   s->d_scratch, s->d_out16};

@@ -37,15 +37,13 @@ template <> struct SlotOf<double> { using type = SlotD; };
 enum : unsigned {
   ST_NONCONV = 1u,
   ST_NONFINITE = 2u,
-  ST_TIMEOUT = 4u,  // a bounded wait for staged data gave up
 };
 
-// The step kernels work on tiles of CPB consecutive (internal) cells.
+// The step kernel works on blocks of CPB consecutive (internal) cells.
 constexpr int CPB = 32;
-// Pipelined float kernel: rows / face slots a tile may stage in one
-// shared-memory stage (tiles above either limit take the global-gather path).
-constexpr int PIPE_ROWS = 136;
-constexpr int PIPE_SLOTS = 560;
+// Face slots (and neighbour indices) of one block that the float kernel
+// stages in shared memory; meshes with a larger block read them from global.
+constexpr int STAGE_SLOTS = 1024;
 
 // Per-cell constant gas data (double): rho, the absorption / scattering
 // coefficients rho kappa_P, rho kappa_J, rho kappa_s, 1/rho and
@@ -106,6 +104,7 @@ struct rt_state {
   double dt_cfl = 0, dt_max = 0;
   bool gas_set = false;
   bool moving = false;  // some face has a non-zero velocity
+  int64_t max_block_slots = 0;  // max over blocks of CPB cells of their face slots
   int64_t n_rows = 0;
   std::string err;
   int64_t launches = 0;
@@ -121,17 +120,6 @@ struct rt_state {
 
   void *d_slot = nullptr;
   double *d_wface = nullptr;  // double states: per-slot A w . n
-  // pipelined float kernel: per tile, the halo rows (neighbours outside the
-  // tile), the slots' tile-local rows (own cell k -> k, halo h -> CPB + h,
-  // each tile's list padded to 8 entries) and whether the tile fits a stage
-  bool pipe = false;
-  int num_sms = 0;
-  int64_t n_tiles = 0, tiles_fit = 0;
-  int64_t *d_halo_ptr = nullptr;
-  int32_t *d_halo = nullptr;
-  int64_t *d_loc_off = nullptr;
-  uint16_t *d_loc = nullptr;
-  uint8_t *d_fits = nullptr;
   void *d_inv_vol = nullptr;
   int64_t *d_cell_of = nullptr;  // internal -> caller
   double *d_volume = nullptr;    // internal order

@@ -3,15 +3,22 @@
 // emitter cells (Sec. 3.6), one kernel per step.
 //
 // Layout: the intensity row of a cell stores the A/2 antipodal pairs
-// (angle p, angle p + A/2) side by side, so one 8-byte (float) or 16-byte
-// (double) load fetches a pair.  The flux coefficient of the antipode through
-// a face is u(p + A/2) = -(n_p . s) - w, so one dot product serves both
-// angles; on a static mesh exactly one of the two is inflow.
+// (angle p, angle p + A/2) side by side.  The flux coefficient of the
+// antipode through a face is u(p + A/2) = -(n_p . s) - w, so one dot product
+// serves both angles; on a static mesh exactly one of the two is inflow.
 //
-// Block = 32 cells x 8 threads; thread `sub` of a cell owns the pairs
-// p = sub + 8 j (j < PPT).  Registers are capped so that four blocks share an
-// SM: the step is latency-bound, and resident warps matter more than the
-// shared-memory staging of neighbour rows that an earlier variant used.
+// Block = 32 cells x 8 threads.  Which pairs a thread owns is a policy:
+//   PairMap  thread `sub` owns pairs sub + 8 j (j < PPT), one 8-byte (float)
+//            or 16-byte (double) access each -- any A;
+//   QuadMap  float rows with A a multiple of 16: thread `sub` owns the pair
+//            quads sub + 8 i (one 16-byte access each, so a cell's 8 threads
+//            read 128 contiguous bytes of a neighbour row per instruction)
+//            and, when A/2 is not a multiple of 16, the pair 16 Q4 + sub.
+// The neighbour-row gathers of the face loop are bound by the L1 data pipe
+// (one wavefront per cache line an instruction touches), so wider per-thread
+// accesses cut the face loop's cost directly.  The float kernel with QuadMap
+// also copies the block's face slots and neighbour indices into shared
+// memory at its start.  Registers are capped so that four blocks share an SM.
 // Phases (separated by __syncthreads):
 //   A  all threads: transport over the cell's faces in slot order (no
 //      atomics, deterministic), comoving weights and the angular sums of
@@ -22,7 +29,7 @@
 //   D  warp 0, one lane per cell: gas energy / momentum (or tally) update in
 //      double (Eqs. gas1, gas2).
 // The double-precision work is lane-per-cell because GB300's FP64 rate is a
-// small fraction of its FP32 rate.  Float states use the packed f32x2 FMA.
+// small fraction of its FP32 rate.
 #include <cuda_runtime.h>
 
 #include "rt_internal.cuh"
@@ -31,6 +38,12 @@
 namespace rt {
 namespace {
 using namespace step;
+
+// The block's face slots and neighbour indices (float kernel, STAGED).
+struct FaceStage {
+  SlotF slot[STAGE_SLOTS];
+  int32_t nbr[STAGE_SLOTS];
+};
 
 template <typename R> struct Shared {
   GasStatic gs[CPB];  // gas of the block's cells, prefetched for warp 0
@@ -41,84 +54,110 @@ template <typename R> struct Shared {
   unsigned bad[CPB];
 };
 
-// sum_f u I_up over the slots [k0, k1) of one cell, neighbour rows read
-// through nbr[k] (L1/L2 serve the reuse between neighbouring cells; cells are
-// in Morton order).  FULL: every lane owns exactly PPT pairs (A/2 divisible
-// by the threads per cell).
-template <typename R, int PPT, bool MOVING, bool FULL, typename S>
-__device__ __forceinline__ void face_sum(const S *__restrict__ slot, const int32_t *__restrict__ nbr,
-                                         const double *__restrict__ wface, int64_t k0, int64_t k1,
-                                         const R *__restrict__ I_in, int A, int sub,
-                                         const R (&nx)[PPT], const R (&ny)[PPT],
-                                         const R (&nz)[PPT], const R (&Ia)[PPT], const R (&Ib)[PPT],
-                                         R (&acca)[PPT], R (&accb)[PPT], int np) {
+// ------------------------------------------------------------ pair maps
+// count(H, sub): pairs the thread owns (entries j >= count are padding);
+// pair(j, sub): pair index of entry j; load / store: the thread's entries of
+// one row (x = angle p, y = angle p + A/2).
+template <typename R, int PPT_, bool FULL_> struct PairMap {
+  static constexpr int PPT = PPT_;
+  static constexpr bool FULL = FULL_;
   using V = pair_t<R>;
-#pragma unroll 2
-  for (int64_t k = k0; k < k1; ++k) {
-    const S s = slot[k];
-    const V *In = reinterpret_cast<const V *>(I_in + (size_t)nbr[k] * A) + sub;
-    const R w = MOVING ? slot_w(s, wface, k) : R(0);
+  __device__ static int count(int H, int sub) { return FULL ? PPT : (H - sub + KT - 1) / KT; }
+  __device__ static int pair(int j, int sub) { return sub + KT * j; }
+  __device__ static void load(const R *__restrict__ row, int sub, R (&x)[PPT], R (&y)[PPT],
+                              int np) {
+    const V *p = reinterpret_cast<const V *>(row) + sub;
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
-      if (FULL || j < np) {
-        const V v = In[KT * j];
-        face_pair<R, MOVING>(slot_dot(nx[j], ny[j], nz[j], s), w, v, Ia[j], Ib[j], acca[j],
-                             accb[j]);
-      }
+      const V t = (FULL || j < np) ? p[KT * j] : mk(R(0), R(0));
+      x[j] = t.x;
+      y[j] = t.y;
     }
   }
-}
-
-// The same sum with the tile's neighbour rows, slots and tile-local rows
-// staged in shared memory (rows `stride` bytes apart).
-template <typename R, int PPT, bool MOVING, bool FULL, typename S>
-__device__ __forceinline__ void face_sum_staged(const S *slot, const uint16_t *loc,
-                                                const double *__restrict__ wface, int k0, int k1,
-                                                const unsigned char *rows, int stride, int sub,
-                                                const R (&nx)[PPT], const R (&ny)[PPT],
-                                                const R (&nz)[PPT], const R (&Ia)[PPT],
-                                                const R (&Ib)[PPT], R (&acca)[PPT], R (&accb)[PPT],
-                                                int np) {
-  using V = pair_t<R>;
-#pragma unroll 4
-  for (int k = k0; k < k1; ++k) {
-    const S s = slot[k];
-    const V *In = reinterpret_cast<const V *>(rows + (int)loc[k] * stride) + sub;
-    const R w = MOVING ? slot_w(s, wface, k) : R(0);
+  __device__ static void store(R *__restrict__ row, int sub, const R (&x)[PPT],
+                               const R (&y)[PPT], int np) {
+    V *p = reinterpret_cast<V *>(row) + sub;
 #pragma unroll
-    for (int j = 0; j < PPT; ++j) {
-      if (FULL || j < np) {
-        const V v = In[KT * j];
-        face_pair<R, MOVING>(slot_dot(nx[j], ny[j], nz[j], s), w, v, Ia[j], Ib[j], acca[j],
-                             accb[j]);
-      }
-    }
+    for (int j = 0; j < PPT; ++j)
+      if (FULL || j < np) p[KT * j] = mk(x[j], y[j]);
   }
-}
-
-// A tile staged in shared memory: its own rows (0..CPB-1) and halo rows,
-// its face slots and their tile-local rows; rows == nullptr: global path.
-template <typename R> struct TileStage {
-  const unsigned char *rows = nullptr;
-  int stride = 0;
-  const typename SlotOf<R>::type *slots = nullptr;
-  const uint16_t *loc = nullptr;
 };
 
-// One tile of CPB cells: phases A-D (see the top of the file).  Ends with
-// warp 0 in phase D; callers that reuse `sh` synchronise first.
-template <typename R, int PPT, bool MOVING, bool FULL>
+template <int Q4, bool TAIL> struct QuadMap {
+  static constexpr int PPT = 2 * Q4 + (TAIL ? 1 : 0);
+  static constexpr bool FULL = true;
+  __device__ static int count(int, int) { return PPT; }
+  __device__ static int pair(int j, int sub) {
+    return j < 2 * Q4 ? 2 * (sub + KT * (j >> 1)) + (j & 1) : 16 * Q4 + sub;
+  }
+  __device__ static void load(const float *__restrict__ row, int sub, float (&x)[PPT],
+                              float (&y)[PPT], int) {
+    const float4 *q = reinterpret_cast<const float4 *>(row) + sub;
+#pragma unroll
+    for (int i = 0; i < Q4; ++i) {
+      const float4 t = q[KT * i];
+      x[2 * i] = t.x;
+      y[2 * i] = t.y;
+      x[2 * i + 1] = t.z;
+      y[2 * i + 1] = t.w;
+    }
+    if (TAIL) {
+      const float2 t = reinterpret_cast<const float2 *>(row)[16 * Q4 + sub];
+      x[2 * Q4] = t.x;
+      y[2 * Q4] = t.y;
+    }
+  }
+  __device__ static void store(float *__restrict__ row, int sub, const float (&x)[PPT],
+                               const float (&y)[PPT], int) {
+    float4 *q = reinterpret_cast<float4 *>(row) + sub;
+#pragma unroll
+    for (int i = 0; i < Q4; ++i)
+      q[KT * i] = make_float4(x[2 * i], y[2 * i], x[2 * i + 1], y[2 * i + 1]);
+    if (TAIL) reinterpret_cast<float2 *>(row)[16 * Q4 + sub] = make_float2(x[2 * Q4], y[2 * Q4]);
+  }
+};
+
+// sum_f u I_up over the slots [k0, k1) of one cell, neighbour rows read
+// through nbr[k] (L1/L2 serve the reuse between neighbouring cells; cells are
+// in Morton order).  slot / nbr point either to global memory or to the
+// block's copy in shared memory (K = int).
+template <typename R, typename M, bool MOVING, typename S, typename K>
+__device__ __forceinline__ void face_sum(const S *__restrict__ slot, const int32_t *__restrict__ nbr,
+                                         const double *__restrict__ wface, K k0, K k1,
+                                         const R *__restrict__ I_in, int A, int sub,
+                                         const R (&nx)[M::PPT], const R (&ny)[M::PPT],
+                                         const R (&nz)[M::PPT], const R (&Ia)[M::PPT],
+                                         const R (&Ib)[M::PPT], R (&acca)[M::PPT],
+                                         R (&accb)[M::PPT], int np) {
+  constexpr int PPT = M::PPT;
+#pragma unroll 1
+  for (K k = k0; k < k1; ++k) {
+    const S s = slot[k];
+    R vx[PPT], vy[PPT];
+    M::load(I_in + (size_t)nbr[k] * A, sub, vx, vy, np);
+    const R w = MOVING ? slot_w(s, wface, k) : R(0);
+#pragma unroll
+    for (int j = 0; j < PPT; ++j)
+      if (M::FULL || j < np)
+        face_pair<R, MOVING>(slot_dot(nx[j], ny[j], nz[j], s), w, vx[j], vy[j], Ia[j], Ib[j],
+                             acca[j], accb[j]);
+  }
+}
+
+// One block of CPB cells: phases A-D (see the top of the file).
+template <typename R, typename M, bool MOVING, bool STAGED>
 __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t tile, Shared<R> &sh,
-                                          const TileStage<R> stg, const unsigned timeout) {
+                                          FaceStage *fs) {
   using V = pair_t<R>;
+  constexpr int PPT = M::PPT;
   const int lc = threadIdx.x / KT;
   const int sub = threadIdx.x % KT;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t cell = tile * CPB + lc;
   const bool live = cell < a.n_cells;
   const int64_t c = live ? cell : a.n_cells - 1;  // dead lanes shadow the last cell
-  const int A = a.n_angles, H = a.half;
-  const int np = FULL ? PPT : (H - sub + KT - 1) / KT;  // pairs p = sub + KT j < H
+  const int A = a.n_angles;
+  const int np = M::count(a.half, sub);
 
   // warp 0 prefetches its cells' gas state for phases B and D
   const int64_t cl = tile * CPB + lane;  // warp 0: lane-per-cell
@@ -130,34 +169,41 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
 #pragma unroll
     for (int k = 0; k < 2; ++k) cp_async16(reinterpret_cast<char *>(&sh.gd[lane]) + 16 * k, d + 16 * k);
   }
+  // STAGED: all threads copy the block's slots and neighbour indices (one
+  // contiguous range of the CSR arrays) into shared memory
+  int64_t kb = 0;
+  if constexpr (STAGED) {
+    const int64_t c1 = tile * CPB + CPB < a.n_cells ? tile * CPB + CPB : a.n_cells;
+    kb = a.ptr[tile * CPB];
+    const int cnt = (int)(a.ptr[c1] - kb);
+    const SlotF *gsl = reinterpret_cast<const SlotF *>(a.slot) + kb;
+    for (int i = threadIdx.x; i < cnt; i += NT) {
+      cp_async16(&fs->slot[i], gsl + i);
+      cp_async4(&fs->nbr[i], a.nbr + kb + i);
+    }
+  }
 
   // ---------------- phase A: transport, I* = I - dt/V sum_f u I_up
   R nx[PPT], ny[PPT], nz[PPT], Ia[PPT], Ib[PPT], acca[PPT], accb[PPT];
-  {
-    const V *Ic = stg.rows ? reinterpret_cast<const V *>(stg.rows + lc * stg.stride) + sub
-                           : reinterpret_cast<const V *>(a.I_in + (size_t)c * A) + sub;
+  M::load(a.I_in + (size_t)c * A, sub, Ia, Ib, np);
 #pragma unroll
-    for (int j = 0; j < PPT; ++j) {
-      const bool v = FULL || j < np;
-      const int p = v ? sub + KT * j : 0;
-      nx[j] = a.dir[4 * p];
-      ny[j] = a.dir[4 * p + 1];
-      nz[j] = a.dir[4 * p + 2];
-      const V t = v ? Ic[KT * j] : mk(R(0), R(0));
-      Ia[j] = t.x;
-      Ib[j] = t.y;
-      acca[j] = R(0);
-      accb[j] = R(0);
-    }
+  for (int j = 0; j < PPT; ++j) {
+    const int p = (M::FULL || j < np) ? M::pair(j, sub) : 0;
+    nx[j] = a.dir[4 * p];
+    ny[j] = a.dir[4 * p + 1];
+    nz[j] = a.dir[4 * p + 2];
+    acca[j] = R(0);
+    accb[j] = R(0);
   }
-  if (stg.rows) {
-    const int64_t kb = a.ptr[tile * CPB];
-    face_sum_staged<R, PPT, MOVING, FULL>(stg.slots, stg.loc, a.wface ? a.wface + kb : nullptr,
-                                          (int)(a.ptr[c] - kb), (int)(a.ptr[c + 1] - kb), stg.rows,
-                                          stg.stride, sub, nx, ny, nz, Ia, Ib, acca, accb, np);
+  if constexpr (STAGED) {
+    const int k0 = (int)(a.ptr[c] - kb), k1 = (int)(a.ptr[c + 1] - kb);
+    cp_async_wait_all();
+    __syncthreads();
+    face_sum<R, M, MOVING>(reinterpret_cast<const typename SlotOf<R>::type *>(fs->slot), fs->nbr,
+                           a.wface, k0, k1, a.I_in, A, sub, nx, ny, nz, Ia, Ib, acca, accb, np);
   } else {
-    face_sum<R, PPT, MOVING, FULL>(a.slot, a.nbr, a.wface, a.ptr[c], a.ptr[c + 1], a.I_in, A, sub,
-                                   nx, ny, nz, Ia, Ib, acca, accb, np);
+    face_sum<R, M, MOVING>(a.slot, a.nbr, a.wface, a.ptr[c], a.ptr[c + 1], a.I_in, A, sub, nx, ny,
+                           nz, Ia, Ib, acca, accb, np);
   }
   {
     const R dtv = a.dt_r * a.inv_vol[c];
@@ -176,16 +222,16 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   const R vxc = a.cellv[4 * c] * icr, vyc = a.cellv[4 * c + 1] * icr,
           vzc = a.cellv[4 * c + 2] * icr;
   const R xs = a.dt_cbar_r * a.cellv[4 * c + 3];
-  const V *W2 = reinterpret_cast<const V *>(a.wt2) + sub;  // (w_p, w_{p+H})
+  const V *W2 = reinterpret_cast<const V *>(a.wt2);  // (w_p, w_{p+H})
   R Ga[PPT];
   R sI = 0, sG = 0, s1 = 0;  // unnormalised: the normalisation cancels in phase B
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
     Ga[j] = R(1) - fma(vxc, nx[j], fma(vyc, ny[j], vzc * nz[j]));
-    if (FULL || j < np) {
+    if (M::FULL || j < np) {
       const R ga = Ga[j], gb = R(2) - ga;
       const R ga2 = ga * ga, gb2 = gb * gb;
-      const V w = W2[KT * j];
+      const V w = W2[M::pair(j, sub)];
       const R wca = w.x * rcp(ga2), wcb = w.y * rcp(gb2);
       const R ta = wca * rcp(fma(xs, ga, R(1))), tb = wcb * rcp(fma(xs, gb, R(1)));
       s1 += ta + tb;
@@ -201,7 +247,7 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
     sh.sG[lc] = sG;
     sh.s1[lc] = s1;
   }
-  if (warp == 0) cp_async_wait_all();
+  if (!STAGED && warp == 0) cp_async_wait_all();
   __syncthreads();
 
   // ---------------- phase B: temperature quartic, one lane per cell
@@ -247,38 +293,41 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
     // boundary: I' = I* - (I* - I0) f; interior: I~' = (I~ + q Gamma) / (1 + x Gamma),
     // i.e. I' = (I* + q / Gamma^3) / (1 + x Gamma); emitter: the same with
     // x -> dt cbar (rho kappa)_src and q -> that rate times I_src (Sec. 3.6)
-    R f = 0, qq = 0, xx = xs;
-    const V *I0 = nullptr;
+    R na[PPT], nb[PPT];
     if (kind == RT_CELL_BOUNDARY) {
       const double2 ax = a.aux[c];
-      f = R((ax.x <= a.dt) ? 1.0 : a.dt / ax.x);
-      I0 = reinterpret_cast<const V *>(a.I0 + (size_t)a.bc_row[c] * A) + sub;
-    } else if (kind == RT_CELL_EMITTER) {
-      const double2 ax = a.aux[c];
-      xx = R(a.dt * a.cbar * ax.x);
-      qq = xx * R(ax.y);
+      const R f = R((ax.x <= a.dt) ? 1.0 : a.dt / ax.x);
+      R tx[PPT], ty[PPT];
+      M::load(a.I0 + (size_t)a.bc_row[c] * A, sub, tx, ty, np);
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) {
+        na[j] = fma(-f, Ia[j] - tx[j], Ia[j]);
+        nb[j] = fma(-f, Ib[j] - ty[j], Ib[j]);
+      }
     } else {
-      qq = sh.q[lc];
+      R qq, xx = xs;
+      if (kind == RT_CELL_EMITTER) {
+        const double2 ax = a.aux[c];
+        xx = R(a.dt * a.cbar * ax.x);
+        qq = xx * R(ax.y);
+      } else {
+        qq = sh.q[lc];
+      }
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) {
+        const R ga = Ga[j], gb = R(2) - ga;
+        const R ra = rcp(ga * ga * ga), rb = rcp(gb * gb * gb);
+        na[j] = fma(qq, ra, Ia[j]) * rcp(fma(xx, ga, R(1)));
+        nb[j] = fma(qq, rb, Ib[j]) * rcp(fma(xx, gb, R(1)));
+      }
     }
-    V *Io = reinterpret_cast<V *>(a.I_out + (size_t)c * A) + sub;
+    if (live) M::store(a.I_out + (size_t)c * A, sub, na, nb, np);
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
-      if (FULL || j < np) {
-        R na, nb;
-        if (kind == RT_CELL_BOUNDARY) {
-          const V t = I0[KT * j];
-          na = fma(-f, Ia[j] - t.x, Ia[j]);
-          nb = fma(-f, Ib[j] - t.y, Ib[j]);
-        } else {
-          const R ga = Ga[j], gb = R(2) - ga;
-          const R ra = rcp(ga * ga * ga), rb = rcp(gb * gb * gb);
-          na = fma(qq, ra, Ia[j]) * rcp(fma(xx, ga, R(1)));
-          nb = fma(qq, rb, Ib[j]) * rcp(fma(xx, gb, R(1)));
-        }
-        if (live) Io[KT * j] = mk(na, nb);
-        if (!isfinite(na) || !isfinite(nb)) nonfinite = ST_NONFINITE;
-        const V w = W2[KT * j];
-        const R da = w.x * (Ia[j] - na), db = w.y * (Ib[j] - nb);
+      if (M::FULL || j < np) {
+        if (!isfinite(na[j]) || !isfinite(nb[j])) nonfinite = ST_NONFINITE;
+        const V w = W2[M::pair(j, sub)];
+        const R da = w.x * (Ia[j] - na[j]), db = w.y * (Ib[j] - nb[j]);
         de += da + db;
         const R df = da - db;  // the antipode has direction -n
         dfx = fma(nx[j], df, dfx);
@@ -291,7 +340,7 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   dfx = cell_sum(dfx);
   dfy = cell_sum(dfy);
   dfz = cell_sum(dfz);
-  nonfinite = cell_or(nonfinite) | timeout;
+  nonfinite = cell_or(nonfinite);
   if (sub == 0) {
     sh.dE[lc] = de;
     sh.dF[0][lc] = dfx;
@@ -333,118 +382,19 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   }
 }
 
-template <typename R, int PPT, bool MOVING, bool FULL>
+template <typename R, typename M, bool MOVING, bool STAGED>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) step_kernel(const StepArgs<R> a) {
   __shared__ Shared<R> sh;
-  tile_step<R, PPT, MOVING, FULL>(a, blockIdx.x, sh, TileStage<R>{}, 0u);
-}
-
-// ------------------------------------------------------------ pipelined float kernel
-// Persistent CTAs walk the tiles; while a CTA computes tile t, warp 0 has
-// already asked the TMA engine for tile t + gridDim.x: its own and halo
-// intensity rows, its face slots and their tile-local rows, one bulk copy
-// each, into the other of two shared-memory stages, completed on that
-// stage's mbarrier.  Tiles whose halo or slots exceed a stage take the
-// global-gather path.
-struct PipeArgs {
-  int64_t n_tiles;
-  const int64_t *halo_ptr;
-  const int32_t *halo;
-  const int64_t *loc_off;
-  const uint16_t *loc;
-  const uint8_t *fits;
-  int stride;        // bytes per staged row (A floats)
-  int stage_bytes;
-  int slot_off, loc_off_b;  // byte offsets inside a stage
-};
-
-__host__ __device__ inline int pipe_slot_off(int stride) {
-  return (PIPE_ROWS * stride + 127) & ~127;
-}
-__host__ __device__ inline int pipe_loc_off(int stride) {
-  return pipe_slot_off(stride) + PIPE_SLOTS * (int)sizeof(SlotF);
-}
-__host__ __device__ inline int pipe_stage_bytes(int stride) {
-  return (pipe_loc_off(stride) + PIPE_SLOTS * (int)sizeof(uint16_t) + 127) & ~127;
-}
-
-struct PipeShared {
-  Shared<float> sh;
-  unsigned long long bar[2];
-};
-
-// Issue the bulk copies of tile t into stage st (warp 0; the tile fits).
-__device__ __forceinline__ void issue_tile(const StepArgs<float> &a, const PipeArgs &p, int64_t t,
-                                           unsigned char *stage, unsigned long long *bar, int lane) {
-  const int64_t c0 = t * CPB;
-  const int64_t c1 = c0 + CPB < a.n_cells ? c0 + CPB : a.n_cells;
-  const int64_t kb = a.ptr[c0];
-  const unsigned cnt = (unsigned)(a.ptr[c1] - kb);
-  const int64_t h0 = p.halo_ptr[t];
-  const int nh = (int)(p.halo_ptr[t + 1] - h0);
-  const int nown = (int)(c1 - c0);
-  const unsigned rb = (unsigned)(a.n_angles * sizeof(float));
-  const unsigned lb = (unsigned)((p.loc_off[t + 1] - p.loc_off[t]) * sizeof(uint16_t));
-  if (lane == 0) {
-    // the stage was read by the generic proxy in an earlier tile
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    mbar_expect_tx(bar, rb * (unsigned)(nown + nh) + cnt * (unsigned)sizeof(SlotF) + lb);
-    if (cnt > 0) {
-      bulk_copy_g2s(stage + p.slot_off, a.slot + kb, cnt * (unsigned)sizeof(SlotF), bar);
-      bulk_copy_g2s(stage + p.loc_off_b, p.loc + p.loc_off[t], lb, bar);
-    }
-  }
-  __syncwarp();
-  for (int r = lane; r < nown; r += 32)
-    bulk_copy_g2s(stage + r * p.stride, a.I_in + (size_t)(c0 + r) * a.n_angles, rb, bar);
-  for (int h = lane; h < nh; h += 32)
-    bulk_copy_g2s(stage + (CPB + h) * p.stride, a.I_in + (size_t)p.halo[h0 + h] * a.n_angles, rb,
-                  bar);
-}
-
-template <int PPT, bool MOVING, bool FULL>
-__global__ void __launch_bounds__(NT, 2) step_kernel_pipe(const StepArgs<float> a,
-                                                          const PipeArgs p) {
-  __shared__ PipeShared ps;
-  extern __shared__ __align__(128) unsigned char dyn[];
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  if (threadIdx.x == 0) {
-    mbar_init(&ps.bar[0], 1);
-    mbar_init(&ps.bar[1], 1);
-  }
-  __syncthreads();
-  unsigned phase = 0;       // bit s: parity of stage s's next completion
-  unsigned failed = 0;      // a bounded wait gave up: stop staging
-  int64_t t = blockIdx.x;
-  if (warp == 0 && t < p.n_tiles && p.fits[t]) issue_tile(a, p, t, dyn, &ps.bar[0], lane);
-  for (int it = 0; t < p.n_tiles; t += gridDim.x, ++it) {
-    const int st = it & 1;
-    unsigned char *stage = dyn + st * p.stage_bytes;
-    const int64_t tn = t + gridDim.x;
-    if (warp == 0 && !failed && tn < p.n_tiles && p.fits[tn])
-      issue_tile(a, p, tn, dyn + (st ^ 1) * p.stage_bytes, &ps.bar[st ^ 1], lane);
-    TileStage<float> stg;
-    unsigned timeout = 0;
-    if (p.fits[t] && !failed) {
-      if (!mbar_wait_bounded(&ps.bar[st], (phase >> st) & 1u)) {
-        timeout = ST_TIMEOUT;
-        failed = 1;
-      }
-      phase ^= 1u << st;
-      if (!timeout) {
-        stg.rows = stage;
-        stg.stride = p.stride;
-        stg.slots = reinterpret_cast<const SlotF *>(stage + p.slot_off);
-        stg.loc = reinterpret_cast<const uint16_t *>(stage + p.loc_off_b);
-      }
-    }
-    failed = __syncthreads_or(failed);
-    tile_step<float, PPT, MOVING, FULL>(a, t, ps.sh, stg, timeout);
-    __syncthreads();  // `sh` and this stage are reused next
+  if constexpr (STAGED) {
+    __shared__ __align__(16) FaceStage fs;
+    tile_step<R, M, MOVING, true>(a, blockIdx.x, sh, &fs);
+  } else {
+    tile_step<R, M, MOVING, false>(a, blockIdx.x, sh, nullptr);
   }
 }
 
-template <typename R, int PPT, bool MOVING, bool FULL>
+// Fills the kernel arguments and launches one step with pair map M.
+template <typename R, typename M, bool MOVING, bool STAGED>
 cudaError_t launch_t(rt_state *s, double dt) {
   StepArgs<R> a;
   a.n_cells = s->n_cells;
@@ -483,61 +433,51 @@ cudaError_t launch_t(rt_state *s, double dt) {
   a.newton_max_iter = s->params.newton_max_iter;
   a.status = s->d_status;
   a.bad_cell = s->d_bad;
-  if constexpr (sizeof(R) == 4) {
-    if (s->pipe) {
-      PipeArgs p;
-      p.n_tiles = s->n_tiles;
-      p.halo_ptr = s->d_halo_ptr;
-      p.halo = s->d_halo;
-      p.loc_off = s->d_loc_off;
-      p.loc = s->d_loc;
-      p.fits = s->d_fits;
-      p.stride = s->n_angles * (int)sizeof(float);
-      p.stage_bytes = pipe_stage_bytes(p.stride);
-      p.slot_off = pipe_slot_off(p.stride);
-      p.loc_off_b = pipe_loc_off(p.stride);
-      const size_t dyn = 2 * (size_t)p.stage_bytes;
-      static bool attr_set = false;  // one per kernel instantiation
-      if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(step_kernel_pipe<PPT, MOVING, FULL>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)dyn);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-      }
-      const int64_t want = 2 * (int64_t)s->num_sms;
-      const unsigned grid = (unsigned)(s->n_tiles < want ? s->n_tiles : want);
-      step_kernel_pipe<PPT, MOVING, FULL><<<grid, NT, dyn, s->stream>>>(a, p);
-      s->launches++;
-      return cudaGetLastError();
-    }
-  }
   const unsigned blocks = (unsigned)((s->n_cells + CPB - 1) / CPB);
-  step_kernel<R, PPT, MOVING, FULL><<<blocks, NT, 0, s->stream>>>(a);
+  step_kernel<R, M, MOVING, STAGED><<<blocks, NT, 0, s->stream>>>(a);
   s->launches++;
   return cudaGetLastError();
 }
 
-template <typename R, bool MOVING, bool FULL> cudaError_t dispatch_ppt(rt_state *s, double dt) {
+template <typename R, bool MOVING, bool FULL> cudaError_t dispatch_pairs(rt_state *s, double dt) {
   const int ppt = (s->n_angles / 2 + KT - 1) / KT;
   switch (ppt) {
-    case 1: return launch_t<R, 1, MOVING, FULL>(s, dt);
-    case 2: return launch_t<R, 2, MOVING, FULL>(s, dt);
-    case 3: return launch_t<R, 3, MOVING, FULL>(s, dt);
-    case 4: return launch_t<R, 4, MOVING, FULL>(s, dt);
-    case 5: return launch_t<R, 5, MOVING, FULL>(s, dt);
-    case 6: return launch_t<R, 6, MOVING, FULL>(s, dt);
-    case 7: return launch_t<R, 7, MOVING, FULL>(s, dt);
-    case 8: return launch_t<R, 8, MOVING, FULL>(s, dt);
+    case 1: return launch_t<R, PairMap<R, 1, FULL>, MOVING, false>(s, dt);
+    case 2: return launch_t<R, PairMap<R, 2, FULL>, MOVING, false>(s, dt);
+    case 3: return launch_t<R, PairMap<R, 3, FULL>, MOVING, false>(s, dt);
+    case 4: return launch_t<R, PairMap<R, 4, FULL>, MOVING, false>(s, dt);
+    case 5: return launch_t<R, PairMap<R, 5, FULL>, MOVING, false>(s, dt);
+    case 6: return launch_t<R, PairMap<R, 6, FULL>, MOVING, false>(s, dt);
+    case 7: return launch_t<R, PairMap<R, 7, FULL>, MOVING, false>(s, dt);
+    case 8: return launch_t<R, PairMap<R, 8, FULL>, MOVING, false>(s, dt);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Float rows with A = 16 m (32 <= A <= 128) whose blocks' slots fit the
+// shared-memory stage: QuadMap<A / 32, A % 32 != 0>.
+template <bool MOVING> cudaError_t dispatch_quads(rt_state *s, double dt) {
+  switch (s->n_angles / 16) {
+    case 2: return launch_t<float, QuadMap<1, false>, MOVING, true>(s, dt);
+    case 3: return launch_t<float, QuadMap<1, true>, MOVING, true>(s, dt);
+    case 4: return launch_t<float, QuadMap<2, false>, MOVING, true>(s, dt);
+    case 5: return launch_t<float, QuadMap<2, true>, MOVING, true>(s, dt);
+    case 6: return launch_t<float, QuadMap<3, false>, MOVING, true>(s, dt);
+    case 7: return launch_t<float, QuadMap<3, true>, MOVING, true>(s, dt);
+    case 8: return launch_t<float, QuadMap<4, false>, MOVING, true>(s, dt);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <typename R> cudaError_t dispatch(rt_state *s, double dt) {
-  const bool full = (s->n_angles / 2) % KT == 0;
+  const int A = s->n_angles;
+  if (sizeof(R) == 4 && A % 16 == 0 && A >= 32 && A <= 128 &&
+      s->max_block_slots <= STAGE_SLOTS)
+    return s->moving ? dispatch_quads<true>(s, dt) : dispatch_quads<false>(s, dt);
+  const bool full = (A / 2) % KT == 0;
   if (s->moving)
-    return full ? dispatch_ppt<R, true, true>(s, dt) : dispatch_ppt<R, true, false>(s, dt);
-  return full ? dispatch_ppt<R, false, true>(s, dt) : dispatch_ppt<R, false, false>(s, dt);
+    return full ? dispatch_pairs<R, true, true>(s, dt) : dispatch_pairs<R, true, false>(s, dt);
+  return full ? dispatch_pairs<R, false, true>(s, dt) : dispatch_pairs<R, false, false>(s, dt);
 }
 
 }  // namespace

@@ -1,4 +1,4 @@
-// Device helpers shared by the step kernels (rt_step.cu, rt_step_pipe.cu).
+// Device helpers of the step kernel (rt_step.cu).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -86,6 +86,10 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
 }
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
@@ -155,60 +159,20 @@ __device__ __forceinline__ int quartic_root(double alpha, double beta, double g,
   return done ? 0 : 1;
 }
 
-// One face's contribution to sum_f u I_up for the thread's pairs: v is the
-// neighbour's (I_p, I_{p+H}) pair, Ia/Ib the cell's own values.
+// One face's contribution to sum_f u I_up for one of the thread's pairs:
+// (vx, vy) the neighbour's (I_p, I_{p+H}), Ia / Ib the cell's own values.
 template <typename R, bool MOVING>
-__device__ __forceinline__ void face_pair(R d, R w, pair_t<R> v, R Ia, R Ib, R &acca, R &accb) {
+__device__ __forceinline__ void face_pair(R d, R w, R vx, R vy, R Ia, R Ib, R &acca, R &accb) {
   if (MOVING) {
     const R ua = d - w, ub = -d - w;
-    acca = fma(ua, ua > R(0) ? Ia : v.x, acca);
-    accb = fma(ub, ub > R(0) ? Ib : v.y, accb);
+    acca = fma(ua, ua > R(0) ? Ia : vx, acca);
+    accb = fma(ub, ub > R(0) ? Ib : vy, accb);
   } else {
     // u_a = d, u_b = -d: exactly one of the pair takes the neighbour's value
     const bool out = d > R(0);
-    acca = fma(d, out ? Ia : v.x, acca);
-    accb = fma(-d, out ? v.y : Ib, accb);
+    acca = fma(d, out ? Ia : vx, acca);
+    accb = fma(-d, out ? vy : Ib, accb);
   }
-}
-
-// ---- mbarrier + TMA bulk copy (global -> shared), completion by tx bytes
-__device__ __forceinline__ unsigned smem_addr(const void *p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes,
-                                              unsigned long long *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
-          "r"(smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Waits for phase `parity` of the barrier with an iteration limit (each
-// try_wait may itself suspend for a bounded time); false if it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
-  for (int it = 0; it < (1 << 20); ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
 }
 
 }  // namespace step

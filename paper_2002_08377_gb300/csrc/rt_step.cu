@@ -18,7 +18,8 @@
 // (one wavefront per cache line an instruction touches), so wider per-thread
 // accesses cut the face loop's cost directly.  The float kernel with QuadMap
 // also copies the block's face slots and neighbour indices into shared
-// memory at its start.  Registers are capped so that four blocks share an SM.
+// memory at its start.  Registers are capped so that four blocks share an SM
+// (three for more than 5 pairs per thread).
 // Phases (separated by __syncthreads):
 //   A  all threads: transport over the cell's faces in slot order (no
 //      atomics, deterministic), comoving weights and the angular sums of
@@ -188,10 +189,7 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   M::load(a.I_in + (size_t)c * A, sub, Ia, Ib, np);
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
-    const int p = (M::FULL || j < np) ? M::pair(j, sub) : 0;
-    nx[j] = a.dir[4 * p];
-    ny[j] = a.dir[4 * p + 1];
-    nz[j] = a.dir[4 * p + 2];
+    load_dir(a.dir, (M::FULL || j < np) ? M::pair(j, sub) : 0, nx[j], ny[j], nz[j]);
     acca[j] = R(0);
     accb[j] = R(0);
   }
@@ -223,22 +221,24 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
           vzc = a.cellv[4 * c + 2] * icr;
   const R xs = a.dt_cbar_r * a.cellv[4 * c + 3];
   const V *W2 = reinterpret_cast<const V *>(a.wt2);  // (w_p, w_{p+H})
-  R Ga[PPT];
-  R sI = 0, sG = 0, s1 = 0;  // unnormalised: the normalisation cancels in phase B
+  const V one = mk(R(1), R(1)), XS = mk(xs, xs);
+  // Gamma = (1 - bn, 1 + bn) for the pair, bn = v . n_p / c; the directions
+  // are read again in phase C rather than held across phase B
+  V sIv = mk(R(0), R(0)), sGv = sIv, s1v = sIv;  // unnormalised: cancels in phase B
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
-    Ga[j] = R(1) - fma(vxc, nx[j], fma(vyc, ny[j], vzc * nz[j]));
     if (M::FULL || j < np) {
-      const R ga = Ga[j], gb = R(2) - ga;
-      const R ga2 = ga * ga, gb2 = gb * gb;
-      const V w = W2[M::pair(j, sub)];
-      const R wca = w.x * rcp(ga2), wcb = w.y * rcp(gb2);
-      const R ta = wca * rcp(fma(xs, ga, R(1))), tb = wcb * rcp(fma(xs, gb, R(1)));
-      s1 += ta + tb;
-      sI = fma(ta, ga2 * ga2 * Ia[j], fma(tb, gb2 * gb2 * Ib[j], sI));
-      sG = fma(ta, ga, fma(tb, gb, sG));
+      // t = w / (Gamma^2 (1 + x Gamma)): one reciprocal per angle
+      const R bn = fma(vxc, nx[j], fma(vyc, ny[j], vzc * nz[j]));
+      const V G = mk(R(1) - bn, R(1) + bn);
+      const V G2 = pmul(G, G);
+      const V t = pmul(W2[M::pair(j, sub)], prcp<R>(pmul(G2, pfma(XS, G, one))));
+      s1v = padd(s1v, t);
+      sIv = pfma(pmul(t, pmul(G2, G2)), mk(Ia[j], Ib[j]), sIv);
+      sGv = pfma(t, G, sGv);
     }
   }
+  R sI = sIv.x + sIv.y, sG = sGv.x + sGv.y, s1 = s1v.x + s1v.y;
   sI = cell_sum(sI);
   sG = cell_sum(sG);
   s1 = cell_sum(s1);
@@ -313,28 +313,40 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
       } else {
         qq = sh.q[lc];
       }
+      const V XX = mk(xx, xx), QQ = mk(qq, qq);
 #pragma unroll
       for (int j = 0; j < PPT; ++j) {
-        const R ga = Ga[j], gb = R(2) - ga;
-        const R ra = rcp(ga * ga * ga), rb = rcp(gb * gb * gb);
-        na[j] = fma(qq, ra, Ia[j]) * rcp(fma(xx, ga, R(1)));
-        nb[j] = fma(qq, rb, Ib[j]) * rcp(fma(xx, gb, R(1)));
+        // I' = (I* Gamma^3 + q) / (Gamma^3 (1 + x Gamma))
+        R ux, uy, uz;
+        load_dir(a.dir, (M::FULL || j < np) ? M::pair(j, sub) : 0, ux, uy, uz);
+        const R bn = fma(vxc, ux, fma(vyc, uy, vzc * uz));
+        const V G = mk(R(1) - bn, R(1) + bn);
+        const V G3 = pmul(pmul(G, G), G);
+        const V n = pmul(pfma(mk(Ia[j], Ib[j]), G3, QQ), prcp<R>(pmul(G3, pfma(XX, G, one))));
+        na[j] = n.x;
+        nb[j] = n.y;
       }
     }
     if (live) M::store(a.I_out + (size_t)c * A, sub, na, nb, np);
+    V dev = mk(R(0), R(0));
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
       if (M::FULL || j < np) {
-        if (!isfinite(na[j]) || !isfinite(nb[j])) nonfinite = ST_NONFINITE;
-        const V w = W2[M::pair(j, sub)];
-        const R da = w.x * (Ia[j] - na[j]), db = w.y * (Ib[j] - nb[j]);
-        de += da + db;
-        const R df = da - db;  // the antipode has direction -n
-        dfx = fma(nx[j], df, dfx);
-        dfy = fma(ny[j], df, dfy);
-        dfz = fma(nz[j], df, dfz);
+        const int p = M::pair(j, sub);
+        const V d = pmul(W2[p], psub(mk(Ia[j], Ib[j]), mk(na[j], nb[j])));
+        dev = padd(dev, d);
+        const R df = d.x - d.y;  // the antipode has direction -n
+        R ux, uy, uz;
+        load_dir(a.dir, p, ux, uy, uz);
+        dfx = fma(ux, df, dfx);
+        dfy = fma(uy, df, dfy);
+        dfz = fma(uz, df, dfz);
       }
     }
+    de = dev.x + dev.y;
+    // a non-finite new intensity makes its weighted change, and so de,
+    // non-finite (the weights are positive)
+    if (!isfinite(de)) nonfinite = ST_NONFINITE;
   }
   de = cell_sum(de);
   dfx = cell_sum(dfx);
@@ -382,8 +394,11 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   }
 }
 
+// Float kernels with up to 5 pairs per thread fit four blocks per SM in
+// registers; wider ones take three, double ones two.
 template <typename R, typename M, bool MOVING, bool STAGED>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) step_kernel(const StepArgs<R> a) {
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (M::PPT <= 5 ? 4 : 3) : 2)
+    step_kernel(const StepArgs<R> a) {
   __shared__ Shared<R> sh;
   if constexpr (STAGED) {
     __shared__ __align__(16) FaceStage fs;

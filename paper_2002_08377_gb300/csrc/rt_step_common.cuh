@@ -32,16 +32,46 @@ __device__ __forceinline__ double2 padd(double2 a, double2 b) {
   return make_double2(a.x + b.x, a.y + b.y);
 }
 
-// Reciprocal: float uses the hardware approximation (relative error ~1e-7,
-// inside the float state's error budget); double refines the float estimate
-// with two Newton steps (about 1 ulp).  Arguments are 1 + x (x >= 0) and
-// Gamma^2, far inside float range.
-__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+__device__ __forceinline__ double2 psub(double2 a, double2 b) {
+  return make_double2(a.x - b.x, a.y - b.y);
+}
+
+// Reciprocal.  Float: the PTX approximate reciprocal (one MUFU operation,
+// relative error below 2^-22, inside the float state's error budget; the
+// arguments are Gamma^k (1 + x Gamma) and 1 + dt cbar rho kappa S_G, normal
+// floats, so flushing subnormals changes nothing).  Double: that estimate
+// refined by two Newton steps (about 1 ulp).
+__device__ __forceinline__ float rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double rcp(double x) {
-  double r = (double)__fdividef(1.0f, (float)x);
+  double r = (double)rcp((float)x);
   r = fma(r, fma(-x, r, 1.0), r);
   r = fma(r, fma(-x, r, 1.0), r);
   return r;
+}
+template <typename R> __device__ __forceinline__ pair_t<R> prcp(pair_t<R> v) {
+  return mk(rcp(v.x), rcp(v.y));
+}
+
+// Direction (x, y, z) of pair p from the [A][4] direction table.
+__device__ __forceinline__ void load_dir(const float *dir, int p, float &x, float &y, float &z) {
+  const float4 t = __ldg(reinterpret_cast<const float4 *>(dir) + p);
+  x = t.x;
+  y = t.y;
+  z = t.z;
+}
+__device__ __forceinline__ void load_dir(const double *dir, int p, double &x, double &y,
+                                         double &z) {
+  const double2 t = __ldg(reinterpret_cast<const double2 *>(dir) + 2 * p);
+  x = t.x;
+  y = t.y;
+  z = __ldg(dir + 4 * p + 2);
 }
 
 template <typename R> __device__ __forceinline__ typename SlotOf<R>::type load_slot(

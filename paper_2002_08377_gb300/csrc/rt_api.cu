@@ -401,7 +401,9 @@ int rt_set_gas(rt_state *s, const double *rho, const double *e, const double *m,
         !std::isfinite(kP[c] + kJ[c] + kS[c]))
       return fail(s, RT_ERR_ARG, "rt_set_gas: rho must be > 0, opacities >= 0, all finite");
     const double rcv = rho[c] * s->params.r_gas / (s->params.gamma_gas - 1.0);
-    gs[ic] = {rho[c], rho[c] * kP[c], rho[c] * kJ[c], rho[c] * kS[c], 1.0 / rho[c], rcv, 0.0, 0.0};
+    gs[ic] = {rho[c], rho[c] * kP[c], rho[c] * kJ[c], rho[c] * kS[c], 1.0 / rho[c], rcv,
+              (float)(rho[c] * kP[c]), (float)(rho[c] * kJ[c]), (float)(rho[c] * kS[c]),
+              (float)rcv};
     gd[ic] = {e[c], m[3 * c], m[3 * c + 1], m[3 * c + 2]};
   }
   RT_CUDA(s, cudaMemcpyAsync(s->d_gs, gs.data(), sizeof(rt::GasStatic) * N, cudaMemcpyHostToDevice,

@@ -45,11 +45,13 @@ constexpr int CPB = 32;
 // stages in shared memory; meshes with a larger block read them from global.
 constexpr int STAGE_SLOTS = 1024;
 
-// Per-cell constant gas data (double): rho, the absorption / scattering
-// coefficients rho kappa_P, rho kappa_J, rho kappa_s, 1/rho and
-// rho c_v = rho r_gas / (gamma - 1).
+// Per-cell constant gas data: rho, the absorption / scattering coefficients
+// rho kappa_P, rho kappa_J, rho kappa_s, 1/rho and
+// rho c_v = rho r_gas / (gamma - 1) in double, and float copies of the
+// coefficients and rho c_v for the float states' temperature solve.
 struct alignas(64) GasStatic {
-  double rho, rkP, rkJ, rkS, inv_rho, rcv, pad0, pad1;
+  double rho, rkP, rkJ, rkS, inv_rho, rcv;
+  float frkP, frkJ, frkS, frcv;
 };
 // Per-cell evolving gas data (double): e, m.
 struct alignas(32) GasDyn {
@@ -79,6 +81,7 @@ template <typename R> struct StepArgs {
   double dt, cbar, c, a_rad, rcv;  // rcv = r_gas / (gamma - 1)
   double k_dcr, k_alpha, k_g, k_fe, k_fm;  // dt cbar, dt c a, dt c 4 pi, 4 pi c/cbar, 4 pi/cbar
   R dt_r, dt_cbar_r, inv_c_r;
+  float k_dcr_f, k_alpha_f, k_g_f, a_rad_4pi_f;  // float copies for the float quartic
   int32_t newton_max_iter;
   unsigned *status;
   unsigned long long *bad_cell;

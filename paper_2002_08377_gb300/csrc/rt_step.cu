@@ -20,15 +20,16 @@
 // also copies the block's face slots and neighbour indices into shared
 // memory at its start.  Registers are capped so that four blocks share an SM
 // (three for more than 5 pairs per thread).
-// Phases (separated by __syncthreads):
+// Phases:
 //   A  all threads: transport over the cell's faces in slot order (no
 //      atomics, deterministic), comoving weights and the angular sums of
 //      Eq. (Jcom); each cell's 8 lanes reduce with shuffles;
-//   B  warp 0, one lane per cell: the gas temperature quartic in double
-//      (float states: float Newton plus one double Newton step);
+//   B  the gas temperature quartic: float states solve it in float in all
+//      8 lanes of the cell (no barrier); double states in double with one
+//      lane per cell in warp 0, between two block barriers;
 //   C  all threads: new intensities, store, radiation change per cell;
-//   D  warp 0, one lane per cell: gas energy / momentum (or tally) update in
-//      double (Eqs. gas1, gas2).
+//   D  after a block barrier, warp 0, one lane per cell: gas energy /
+//      momentum (or tally) update in double (Eqs. gas1, gas2).
 // The double-precision work is lane-per-cell because GB300's FP64 rate is a
 // small fraction of its FP32 rate.
 #include <cuda_runtime.h>
@@ -145,6 +146,64 @@ __device__ __forceinline__ void face_sum(const S *__restrict__ slot, const int32
   }
 }
 
+// Temperature quartic of one interior cell and its emission term
+// q = dt cbar rho (kP B + kS J~).  With w~ normalised, x_a = dt cbar rho
+// (kJ + kS) Gamma_a and the sums S_I, S_G of Eq. (Jcom), S_1 = sum w~ / (1 + x):
+//   D = 1 - dt cbar rho kS S_G = S_1 + dt cbar rho kJ S_G,
+//   1 - dt cbar rho kJ S_G / D = S_1 / D,
+// so the quartic alpha T^4 + rho c_v T = g of Eq. (com rad thermal disc) has
+// alpha = dt c a rho kP S_1 / D and g = (e - kinetic) + dt c 4 pi rho kJ S_I / D:
+// sums of positive terms, no cancellation when x >> 1.  The weight
+// normalisation cancels in every ratio.  Sets status bits in `bad`.
+template <typename R>
+__device__ __forceinline__ double source_q(const StepArgs<R> &a, const GasStatic &g,
+                                           const GasDyn &d, double SI, double SG, double S1,
+                                           unsigned &bad) {
+  const double dJ = a.k_dcr * g.rkJ, dP = a.k_dcr * g.rkP, dS = a.k_dcr * g.rkS;
+  const double rU = rcp(fma(dJ, SG, S1));
+  const double kin = 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * g.inv_rho;
+  const double alpha = a.k_alpha * g.rkP * S1 * rU;
+  const double gq = (d.e - kin) + a.k_g * g.rkJ * SI * rU;
+  double T = 0.0;
+  if (!(gq >= 0.0) || !(alpha >= 0.0)) {
+    bad |= ST_NONFINITE;
+  } else if (quartic_root(alpha, g.rcv, gq, a.newton_max_iter, &T)) {
+    bad |= ST_NONCONV;
+  }
+  const double B = a.a_rad * (T * T) * (T * T) * (1.0 / (4.0 * kPi));
+  const double J = fma(dP * B, SG, SI) * rU;  // the J~ of Eq. (Jcom)
+  return fma(dP, B, dS * J);
+}
+
+// The same in float for float states (the kinetic energy is subtracted in
+// double); coefficients or an emission term outside float range fall back
+// to the double solve.
+__device__ __forceinline__ float source_q_float(const StepArgs<float> &a, const GasStatic &g,
+                                                const GasDyn &d, float SI, float SG, float S1,
+                                                unsigned &bad) {
+  const double kin = 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * g.inv_rho;
+  const float dJ = a.k_dcr_f * g.frkJ, dP = a.k_dcr_f * g.frkP, dS = a.k_dcr_f * g.frkS;
+  const float rU = rcp(fmaf(dJ, SG, S1));
+  const float alpha = a.k_alpha_f * g.frkP * S1 * rU;
+  const float gq = (float)(d.e - kin) + a.k_g_f * g.frkJ * SI * rU;
+  if (!(gq >= 0.0f) || !(alpha >= 0.0f)) {
+    bad |= ST_NONFINITE;
+    return 0.0f;
+  }
+  if (isfinite(alpha) && isfinite(gq)) {
+    float T;
+    const int nc = quartic_root(alpha, g.frcv, gq, a.newton_max_iter, &T);
+    const float B = a.a_rad_4pi_f * (T * T) * (T * T);
+    const float J = fmaf(dP * B, SG, SI) * rU;
+    const float q = fmaf(dP, B, dS * J);
+    if (isfinite(q)) {
+      if (nc) bad |= ST_NONCONV;
+      return q;
+    }
+  }
+  return (float)source_q(a, g, d, (double)SI, (double)SG, (double)S1, bad);
+}
+
 // One block of CPB cells: phases A-D (see the top of the file).
 template <typename R, typename M, bool MOVING, bool STAGED>
 __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t tile, Shared<R> &sh,
@@ -242,49 +301,37 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   sI = cell_sum(sI);
   sG = cell_sum(sG);
   s1 = cell_sum(s1);
-  if (sub == 0) {
-    sh.sI[lc] = sI;
-    sh.sG[lc] = sG;
-    sh.s1[lc] = s1;
-  }
-  if (!STAGED && warp == 0) cp_async_wait_all();
-  __syncthreads();
 
-  // ---------------- phase B: temperature quartic, one lane per cell
-  if (warp == 0 && lane < CPB) {
-    R q = 0;
-    unsigned bad = 0;
-    if (cl < a.n_cells && a.kind[cl] == RT_CELL_INTERIOR) {
-      // With w~ normalised, x_a = dt cbar rho (kJ + kS) Gamma_a and the sums
-      // S_I, S_G of Eq. (Jcom), S_1 = sum w~ / (1 + x):
-      //   D = 1 - dt cbar rho kS S_G = S_1 + dt cbar rho kJ S_G,
-      //   1 - dt cbar rho kJ S_G / D = S_1 / D,
-      // so the quartic alpha T^4 + rho c_v T = g of Eq. (com rad thermal disc)
-      // has alpha = dt c a rho kP S_1 / D and g = (e - kinetic) +
-      // dt c 4 pi rho kJ S_I / D: sums of positive terms, no cancellation when
-      // x >> 1.  The weight normalisation cancels in every ratio.
-      const GasStatic g = sh.gs[lane];
-      const GasDyn d = sh.gd[lane];
-      const double SI = (double)sh.sI[lane], SG = (double)sh.sG[lane], S1 = (double)sh.s1[lane];
-      const double dJ = a.k_dcr * g.rkJ, dP = a.k_dcr * g.rkP, dS = a.k_dcr * g.rkS;
-      const double rU = rcp(fma(dJ, SG, S1));
-      const double kin = 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * g.inv_rho;
-      const double alpha = a.k_alpha * g.rkP * S1 * rU;
-      const double gq = (d.e - kin) + a.k_g * g.rkJ * SI * rU;
-      double T = 0.0;
-      if (!(gq >= 0.0) || !(alpha >= 0.0)) {
-        bad |= ST_NONFINITE;
-      } else if (quartic_root<sizeof(R) == 4>(alpha, g.rcv, gq, a.newton_max_iter, &T)) {
-        bad |= ST_NONCONV;
-      }
-      const double B = a.a_rad * (T * T) * (T * T) * (1.0 / (4.0 * kPi));
-      const double J = fma(dP * B, SG, SI) * rU;  // the J~ of Eq. (Jcom)
-      q = R(fma(dP, B, dS * J));
+  // ---------------- phase B: temperature quartic
+  R q = 0;           // dt cbar rho (kP B + kS J~) of an interior cell
+  unsigned bad = 0;  // status bits of the cell
+  if constexpr (sizeof(R) == 4) {
+    // float states: every lane of the cell solves the cell's quartic in
+    // float (the sums are already in all 8 lanes), no block barrier
+    if (kind == RT_CELL_INTERIOR) q = source_q_float(a, a.gs[c], a.gd[c], sI, sG, s1, bad);
+  } else {
+    // double states: one lane per cell in warp 0, so the FP64 work is issued
+    // by one warp for 32 cells
+    if (sub == 0) {
+      sh.sI[lc] = sI;
+      sh.sG[lc] = sG;
+      sh.s1[lc] = s1;
     }
-    sh.q[lane] = q;
-    sh.bad[lane] = bad;
+    if (!STAGED && warp == 0) cp_async_wait_all();
+    __syncthreads();
+    if (warp == 0 && lane < CPB) {
+      R ql = 0;
+      unsigned bl = 0;
+      if (cl < a.n_cells && a.kind[cl] == RT_CELL_INTERIOR)
+        ql = R(source_q(a, sh.gs[lane], sh.gd[lane], (double)sh.sI[lane], (double)sh.sG[lane],
+                        (double)sh.s1[lane], bl));
+      sh.q[lane] = ql;
+      sh.bad[lane] = bl;
+    }
+    __syncthreads();
+    q = sh.q[lc];
+    bad = sh.bad[lc];
   }
-  __syncthreads();
 
   // ---------------- phase C: new intensities and the radiation change
   R de = 0, dfx = 0, dfy = 0, dfz = 0;
@@ -311,7 +358,7 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
         xx = R(a.dt * a.cbar * ax.x);
         qq = xx * R(ax.y);
       } else {
-        qq = sh.q[lc];
+        qq = q;
       }
       const V XX = mk(xx, xx), QQ = mk(qq, qq);
 #pragma unroll
@@ -358,8 +405,9 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
     sh.dF[0][lc] = dfx;
     sh.dF[1][lc] = dfy;
     sh.dF[2][lc] = dfz;
-    sh.bad[lc] |= nonfinite;
+    sh.bad[lc] = bad | nonfinite;
   }
+  if (sizeof(R) == 4 && !STAGED && warp == 0) cp_async_wait_all();
   __syncthreads();
 
   // ---------------- phase D: gas exchange (Eqs. gas1, gas2), one lane per cell
@@ -446,6 +494,10 @@ cudaError_t launch_t(rt_state *s, double dt) {
   a.k_fe = s->params.c / s->params.cbar * 4.0 * kPi;
   a.k_fm = 4.0 * kPi / s->params.cbar;
   a.newton_max_iter = s->params.newton_max_iter;
+  a.k_dcr_f = (float)a.k_dcr;
+  a.k_alpha_f = (float)a.k_alpha;
+  a.k_g_f = (float)a.k_g;
+  a.a_rad_4pi_f = (float)(s->params.a_rad / (4.0 * kPi));
   a.status = s->d_status;
   a.bad_cell = s->d_bad;
   const unsigned blocks = (unsigned)((s->n_cells + CPB - 1) / CPB);

@@ -126,48 +126,11 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 // Positive root of alpha T^4 + beta T = g (alpha >= 0, beta > 0, g >= 0).
 // f is increasing and convex on T > 0, so Newton from any point at or above
-// the root decreases monotonically onto it.  Double states: start at
+// the root decreases monotonically onto it.  Start at
 // min(g/beta, (g/alpha)^(1/4)) and stop when an iterate fails to decrease or
-// moves by at most 1e-15 of itself.  Float states: the same iteration in
-// float to a relative 1e-7, then one Newton step in double (the float
-// root's error ~1e-7 becomes ~1e-14); coefficients outside float range fall
-// back to the double iteration.  Returns 1 if it did not converge.
-__device__ __forceinline__ float fp_of(float af, float bf, float t) {
-  return fmaf(4.0f * af * t * t, t, bf);
-}
-
-template <bool FLOAT_STATE>
+// moves by at most `tol` of itself.  Returns 1 if it did not converge.
 __device__ __forceinline__ int quartic_root(double alpha, double beta, double g, int max_iter,
                                             double *T_out) {
-  if (FLOAT_STATE) {
-    const float af = (float)alpha, bf = (float)beta, gf = (float)g;
-    float t = __fdividef(gf, bf);
-    if (af > 0.0f) t = fminf(t, sqrtf(sqrtf(__fdividef(gf, af))));
-    bool done = false;
-    for (int it = 0; it < max_iter && !done; ++it) {
-      const float t2 = t * t;
-      const float f = fmaf(af * t2, t2, fmaf(bf, t, -gf));
-      const float fp = fmaf(4.0f * af * t2, t, bf);
-      const float tn = t - __fdividef(f, fp);
-      if (!(tn < t)) {
-        done = true;
-      } else {
-        done = (t - tn <= 1e-7f * t);
-        t = tn;
-      }
-    }
-    if (isfinite(t) && t >= 0.0f && isfinite(fp_of(af, bf, t))) {
-      if (!done) {
-        *T_out = t;
-        return 1;
-      }
-      const double T = t, T2 = T * T;
-      const double f = fma(alpha * T2, T2, fma(beta, T, -g));
-      const double fp = fma(4.0 * alpha * T2, T, beta);
-      *T_out = fma(-f, rcp(fp), T);
-      return 0;
-    }
-  }
   double T = g / beta;
   if (alpha > 0.0) T = fmin(T, sqrt(sqrt(g / alpha)));
   bool done = false;
@@ -182,6 +145,29 @@ __device__ __forceinline__ int quartic_root(double alpha, double beta, double g,
       done = true;
     } else {
       done = (T - Tn <= 1e-15 * T);
+      T = Tn;
+    }
+  }
+  *T_out = T;
+  return done ? 0 : 1;
+}
+
+// The same iteration in float for float states (tolerance 1e-7: the root's
+// relative error is then a few float ulps, below the state's own rounding).
+__device__ __forceinline__ int quartic_root(float alpha, float beta, float g, int max_iter,
+                                            float *T_out) {
+  float T = __fdividef(g, beta);
+  if (alpha > 0.0f) T = fminf(T, sqrtf(sqrtf(__fdividef(g, alpha))));
+  bool done = false;
+  for (int it = 0; it < max_iter && !done; ++it) {
+    const float T2 = T * T;
+    const float f = fmaf(alpha * T2, T2, fmaf(beta, T, -g));
+    const float fp = fmaf(4.0f * alpha * T2, T, beta);
+    const float Tn = T - __fdividef(f, fp);
+    if (!(Tn < T)) {
+      done = true;
+    } else {
+      done = (T - Tn <= 1e-7f * T);
       T = Tn;
     }
   }

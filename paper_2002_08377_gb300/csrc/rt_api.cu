@@ -165,6 +165,17 @@ template <typename R> int build_device_mesh(rt_state *s, const rt_mesh_desc *m,
   typename rt::SlotOf<R>::type *ds = nullptr;
   RT_CUDA(s, upload(s, &ds, slot));
   s->d_slot = ds;
+  if constexpr (sizeof(R) == 4) {
+    if (!s->moving) {
+      // static float meshes: w = 0, so its word carries the neighbour index
+      std::vector<rt::SlotF> snb(slot.size());
+      for (size_t k = 0; k < slot.size(); ++k) {
+        snb[k] = slot[k];
+        std::memcpy(&snb[k].w, &nbr[k], sizeof(float));
+      }
+      RT_CUDA(s, upload(s, &s->d_slot_nb, snb));
+    }
+  }
   R *dv = nullptr;
   RT_CUDA(s, upload(s, &dv, inv_vol));
   s->d_inv_vol = dv;
@@ -725,7 +736,7 @@ void rt_destroy(rt_state *s) {
     if (s->d_adj[k]) cudaFree(s->d_adj[k]);
   if (s->d_adj_ws) cudaFree(s->d_adj_ws);
   if (s->d_adj_stage) cudaFree(s->d_adj_stage);
-  void *bufs[] = {s->d_wface, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
+  void *bufs[] = {s->d_slot_nb, s->d_wface, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
                   s->d_gd, s->d_kind, s->d_aux, s->d_bc_row, s->d_I0, s->d_ext, s->d_dir, s->d_wt,
                   s->d_dir64, s->d_wt64, s->d_I[0], s->d_I[1], s->d_status, s->d_bad,
                   s->d_scratch, s->d_out16};

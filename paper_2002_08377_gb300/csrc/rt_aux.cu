@@ -198,7 +198,7 @@ __global__ void gas_out_kernel(const GasDyn *__restrict__ gd, const double *__re
     for (int k = 0; k < 4; ++k) x[4 * oc + k] = ext[4 * i + k];
 }
 
-// cellv = (m / rho, rho (kJ + kS)) in the state precision, as the step
+// cellv = (m / rho, e - |m|^2 / (2 rho)) in the state precision, as the step
 // kernel's gas update writes it
 template <typename R>
 __global__ void cellv_kernel(const GasStatic *__restrict__ gs, const GasDyn *__restrict__ gd,
@@ -211,7 +211,7 @@ __global__ void cellv_kernel(const GasStatic *__restrict__ gs, const GasDyn *__r
   cellv[4 * i] = R(d.mx * ir);
   cellv[4 * i + 1] = R(d.my * ir);
   cellv[4 * i + 2] = R(d.mz * ir);
-  cellv[4 * i + 3] = R(g.rkJ + g.rkS);
+  cellv[4 * i + 3] = R(d.e - 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * ir);
 }
 
 unsigned rows_grid(int64_t n) { return (unsigned)((n + kThreads / 32 - 1) / (kThreads / 32)); }

@@ -64,6 +64,7 @@ template <typename R> struct StepArgs {
   const int64_t *ptr;       // [N+1] slot range per internal cell
   const int32_t *nbr;       // [nnz] internal neighbour index
   const typename SlotOf<R>::type *slot;  // [nnz]
+  const SlotF *slot_nb;     // [nnz] float static meshes: (s, neighbour index bits)
   const R *inv_vol;         // [N]
   const double *wface;      // [nnz] A_f w_f . n_f of double slots (moving meshes)
   const GasStatic *gs;      // [N]
@@ -77,7 +78,7 @@ template <typename R> struct StepArgs {
   const R *wt2;             // [A/2][2] (w_p, w_{p+A/2})
   const R *I_in;            // [N][A]
   R *I_out;                 // [N][A]
-  R *cellv;                 // [N][4] (v_x, v_y, v_z, rho (kappa_J + kappa_s))
+  R *cellv;                 // [N][4] (v_x, v_y, v_z, e - rho v^2 / 2)
   double dt, cbar, c, a_rad, rcv;  // rcv = r_gas / (gamma - 1)
   double k_dcr, k_alpha, k_g, k_fe, k_fm;  // dt cbar, dt c a, dt c 4 pi, 4 pi c/cbar, 4 pi/cbar
   R dt_r, dt_cbar_r, inv_c_r;
@@ -122,6 +123,7 @@ struct rt_state {
   int32_t *d_nbr = nullptr;
 
   void *d_slot = nullptr;
+  rt::SlotF *d_slot_nb = nullptr;  // float, static mesh: slot with the neighbour in w
   double *d_wface = nullptr;  // double states: per-slot A w . n
   void *d_inv_vol = nullptr;
   int64_t *d_cell_of = nullptr;  // internal -> caller

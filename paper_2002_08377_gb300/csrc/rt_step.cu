@@ -122,8 +122,9 @@ template <int Q4, bool TAIL> struct QuadMap {
 // sum_f u I_up over the slots [k0, k1) of one cell, neighbour rows read
 // through nbr[k] (L1/L2 serve the reuse between neighbouring cells; cells are
 // in Morton order).  slot / nbr point either to global memory or to the
-// block's copy in shared memory (K = int).
-template <typename R, typename M, bool MOVING, typename S, typename K>
+// block's copy in shared memory (K = int); PACKED: static float slots carry
+// the neighbour index in their w word and nbr is not read.
+template <typename R, typename M, bool MOVING, bool PACKED, typename S, typename K>
 __device__ __forceinline__ void face_sum(const S *__restrict__ slot, const int32_t *__restrict__ nbr,
                                          const double *__restrict__ wface, K k0, K k1,
                                          const R *__restrict__ I_in, int A, int sub,
@@ -135,8 +136,13 @@ __device__ __forceinline__ void face_sum(const S *__restrict__ slot, const int32
 #pragma unroll 1
   for (K k = k0; k < k1; ++k) {
     const S s = slot[k];
+    int32_t nb;
+    if constexpr (PACKED)
+      nb = __float_as_int(s.w);
+    else
+      nb = nbr[k];
     R vx[PPT], vy[PPT];
-    M::load(I_in + (size_t)nbr[k] * A, sub, vx, vy, np);
+    M::load(I_in + (size_t)nb * A, sub, vx, vy, np);
     const R w = MOVING ? slot_w(s, wface, k) : R(0);
 #pragma unroll
     for (int j = 0; j < PPT; ++j)
@@ -175,24 +181,24 @@ __device__ __forceinline__ double source_q(const StepArgs<R> &a, const GasStatic
   return fma(dP, B, dS * J);
 }
 
-// The same in float for float states (the kinetic energy is subtracted in
-// double); coefficients or an emission term outside float range fall back
-// to the double solve.
-__device__ __forceinline__ float source_q_float(const StepArgs<float> &a, const GasStatic &g,
-                                                const GasDyn &d, float SI, float SG, float S1,
-                                                unsigned &bad) {
-  const double kin = 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * g.inv_rho;
-  const float dJ = a.k_dcr_f * g.frkJ, dP = a.k_dcr_f * g.frkP, dS = a.k_dcr_f * g.frkS;
+// The same in float for float states, from the float coefficients and the
+// internal energy e - rho v^2 / 2 that the previous gas update left in
+// cellv; coefficients or an emission term outside float range fall back to
+// the double solve.
+__device__ __forceinline__ float source_q_float(const StepArgs<float> &a, int64_t c, float rkP,
+                                                float rkJ, float rkS, float rcv, float eint,
+                                                float SI, float SG, float S1, unsigned &bad) {
+  const float dJ = a.k_dcr_f * rkJ, dP = a.k_dcr_f * rkP, dS = a.k_dcr_f * rkS;
   const float rU = rcp(fmaf(dJ, SG, S1));
-  const float alpha = a.k_alpha_f * g.frkP * S1 * rU;
-  const float gq = (float)(d.e - kin) + a.k_g_f * g.frkJ * SI * rU;
+  const float alpha = a.k_alpha_f * rkP * S1 * rU;
+  const float gq = eint + a.k_g_f * rkJ * SI * rU;
   if (!(gq >= 0.0f) || !(alpha >= 0.0f)) {
     bad |= ST_NONFINITE;
     return 0.0f;
   }
   if (isfinite(alpha) && isfinite(gq)) {
     float T;
-    const int nc = quartic_root(alpha, g.frcv, gq, a.newton_max_iter, &T);
+    const int nc = quartic_root(alpha, rcv, gq, a.newton_max_iter, &T);
     const float B = a.a_rad_4pi_f * (T * T) * (T * T);
     const float J = fmaf(dP * B, SG, SI) * rU;
     const float q = fmaf(dP, B, dS * J);
@@ -201,7 +207,7 @@ __device__ __forceinline__ float source_q_float(const StepArgs<float> &a, const 
       return q;
     }
   }
-  return (float)source_q(a, g, d, (double)SI, (double)SG, (double)S1, bad);
+  return (float)source_q(a, a.gs[c], a.gd[c], (double)SI, (double)SG, (double)S1, bad);
 }
 
 // One block of CPB cells: phases A-D (see the top of the file).
@@ -236,10 +242,14 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
     const int64_t c1 = tile * CPB + CPB < a.n_cells ? tile * CPB + CPB : a.n_cells;
     kb = a.ptr[tile * CPB];
     const int cnt = (int)(a.ptr[c1] - kb);
-    const SlotF *gsl = reinterpret_cast<const SlotF *>(a.slot) + kb;
-    for (int i = threadIdx.x; i < cnt; i += NT) {
-      cp_async16(&fs->slot[i], gsl + i);
-      cp_async4(&fs->nbr[i], a.nbr + kb + i);
+    if (MOVING) {
+      const SlotF *gsl = reinterpret_cast<const SlotF *>(a.slot) + kb;
+      for (int i = threadIdx.x; i < cnt; i += NT) {
+        cp_async16(&fs->slot[i], gsl + i);
+        cp_async4(&fs->nbr[i], a.nbr + kb + i);
+      }
+    } else {
+      for (int i = threadIdx.x; i < cnt; i += NT) cp_async16(&fs->slot[i], a.slot_nb + kb + i);
     }
   }
 
@@ -256,11 +266,12 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
     const int k0 = (int)(a.ptr[c] - kb), k1 = (int)(a.ptr[c + 1] - kb);
     cp_async_wait_all();
     __syncthreads();
-    face_sum<R, M, MOVING>(reinterpret_cast<const typename SlotOf<R>::type *>(fs->slot), fs->nbr,
-                           a.wface, k0, k1, a.I_in, A, sub, nx, ny, nz, Ia, Ib, acca, accb, np);
+    face_sum<R, M, MOVING, !MOVING>(reinterpret_cast<const typename SlotOf<R>::type *>(fs->slot),
+                                    fs->nbr, a.wface, k0, k1, a.I_in, A, sub, nx, ny, nz, Ia, Ib,
+                                    acca, accb, np);
   } else {
-    face_sum<R, M, MOVING>(a.slot, a.nbr, a.wface, a.ptr[c], a.ptr[c + 1], a.I_in, A, sub, nx, ny,
-                           nz, Ia, Ib, acca, accb, np);
+    face_sum<R, M, MOVING, false>(a.slot, a.nbr, a.wface, a.ptr[c], a.ptr[c + 1], a.I_in, A, sub,
+                                  nx, ny, nz, Ia, Ib, acca, accb, np);
   }
   {
     const R dtv = a.dt_r * a.inv_vol[c];
@@ -278,7 +289,18 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   const R icr = a.inv_c_r;
   const R vxc = a.cellv[4 * c] * icr, vyc = a.cellv[4 * c + 1] * icr,
           vzc = a.cellv[4 * c + 2] * icr;
-  const R xs = a.dt_cbar_r * a.cellv[4 * c + 3];
+  R xs, eint = a.cellv[4 * c + 3];  // dt cbar rho (kJ + kS), internal energy
+  R fkP = 0, fkJ = 0, fkS = 0, fcv = 0;
+  if constexpr (sizeof(R) == 4) {
+    const float4 gf = __ldg(reinterpret_cast<const float4 *>(&a.gs[c].frkP));
+    fkP = gf.x;
+    fkJ = gf.y;
+    fkS = gf.z;
+    fcv = gf.w;
+    xs = a.dt_cbar_r * (fkJ + fkS);
+  } else {
+    xs = a.dt_cbar_r * R(a.gs[c].rkJ + a.gs[c].rkS);
+  }
   const V *W2 = reinterpret_cast<const V *>(a.wt2);  // (w_p, w_{p+H})
   const V one = mk(R(1), R(1)), XS = mk(xs, xs);
   // Gamma = (1 - bn, 1 + bn) for the pair, bn = v . n_p / c; the directions
@@ -308,7 +330,8 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   if constexpr (sizeof(R) == 4) {
     // float states: every lane of the cell solves the cell's quartic in
     // float (the sums are already in all 8 lanes), no block barrier
-    if (kind == RT_CELL_INTERIOR) q = source_q_float(a, a.gs[c], a.gd[c], sI, sG, s1, bad);
+    if (kind == RT_CELL_INTERIOR)
+      q = source_q_float(a, c, fkP, fkJ, fkS, fcv, eint, sI, sG, s1, bad);
   } else {
     // double states: one lane per cell in warp 0, so the FP64 work is issued
     // by one warp for 32 cells
@@ -423,10 +446,10 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
       d.my += dy;
       d.mz += dz;
       a.gd[cl] = d;
-      const double ir = sh.gs[lane].inv_rho;  // frame velocity of the next step
-      a.cellv[4 * cl] = R(d.mx * ir);
-      a.cellv[4 * cl + 1] = R(d.my * ir);
-      a.cellv[4 * cl + 2] = R(d.mz * ir);
+      // frame velocity and internal energy for the next step
+      const double ir = sh.gs[lane].inv_rho;
+      const double kin = 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * ir;
+      store4(a.cellv + 4 * cl, R(d.mx * ir), R(d.my * ir), R(d.mz * ir), R(d.e - kin));
     } else {
       double *x = a.ext + 4 * cl;
       x[0] += dE;
@@ -466,6 +489,7 @@ cudaError_t launch_t(rt_state *s, double dt) {
   a.ptr = s->d_ptr;
   a.nbr = s->d_nbr;
   a.slot = reinterpret_cast<const typename SlotOf<R>::type *>(s->d_slot);
+  a.slot_nb = s->d_slot_nb;
   a.inv_vol = reinterpret_cast<const R *>(s->d_inv_vol);
   a.wface = s->d_wface;
   a.gs = s->d_gs;

@@ -59,6 +59,15 @@ template <typename R> __device__ __forceinline__ pair_t<R> prcp(pair_t<R> v) {
   return mk(rcp(v.x), rcp(v.y));
 }
 
+// Four consecutive reals (16-byte aligned for float, 32 for double).
+__device__ __forceinline__ void store4(float *p, float x, float y, float z, float w) {
+  *reinterpret_cast<float4 *>(p) = make_float4(x, y, z, w);
+}
+__device__ __forceinline__ void store4(double *p, double x, double y, double z, double w) {
+  reinterpret_cast<double2 *>(p)[0] = make_double2(x, y);
+  reinterpret_cast<double2 *>(p)[1] = make_double2(z, w);
+}
+
 // Direction (x, y, z) of pair p from the [A][4] direction table.
 __device__ __forceinline__ void load_dir(const float *dir, int p, float &x, float &y, float &z) {
   const float4 t = __ldg(reinterpret_cast<const float4 *>(dir) + p);

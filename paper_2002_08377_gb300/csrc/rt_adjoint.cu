@@ -39,8 +39,6 @@ __device__ __forceinline__ double slot_u(const SlotD &s, const double *wf, int64
   return d - (wf ? wf[k] : 0.0);
 }
 
-// Internal angle position q of caller angle a (pairs stored side by side).
-__device__ __forceinline__ int pos_of(int a, int H) { return a < H ? 2 * a : 2 * (a - H) + 1; }
 
 // I* = I - dt/V sum_f u I_up, one warp per cell, lanes over caller angles
 // (the same face order and flux coefficient as the fused step kernel).
@@ -49,13 +47,13 @@ __global__ void transport_kernel(const int64_t *__restrict__ ptr, const int32_t 
                                  const typename SlotOf<R>::type *__restrict__ slot,
                                  const double *__restrict__ wface, const R *__restrict__ inv_vol,
                                  const R *__restrict__ dir, const R *__restrict__ I, R *__restrict__ Is,
-                                 int64_t n, int A, R dt) {
+                                 int64_t n, int A, int quad_end, R dt) {
   const int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   if (c >= n) return;
   const int lane = threadIdx.x % 32, H = A / 2;
   for (int a = lane; a < A; a += 32) {
     const R x = dir[4 * a], y = dir[4 * a + 1], z = dir[4 * a + 2];
-    const int q = pos_of(a, H);
+    const int q = position_of_angle(a, H, quad_end);
     const R own = I[(size_t)c * A + q];
     R acc = 0;
     for (int64_t k = ptr[c]; k < ptr[c + 1]; ++k) {
@@ -75,14 +73,14 @@ __global__ void transport_adjoint_kernel(const int64_t *__restrict__ ptr,
                                          const double *__restrict__ wface,
                                          const R *__restrict__ inv_vol, const R *__restrict__ dir,
                                          const R *__restrict__ l, R *__restrict__ out, int64_t n,
-                                         int A, R dt) {
+                                         int A, int quad_end, R dt) {
   const int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   if (c >= n) return;
   const int lane = threadIdx.x % 32, H = A / 2;
   const R dvc = dt * inv_vol[c];
   for (int a = lane; a < A; a += 32) {
     const R x = dir[4 * a], y = dir[4 * a + 1], z = dir[4 * a + 2];
-    const int q = pos_of(a, H);
+    const int q = position_of_angle(a, H, quad_end);
     const R own = l[(size_t)c * A + q];
     R acc = 0;
     for (int64_t k = ptr[c]; k < ptr[c + 1]; ++k) {
@@ -347,7 +345,8 @@ template <typename R> cudaError_t run_adjoint(rt_state *s, const R *I_int, const
   const R *iv = reinterpret_cast<const R *>(s->d_inv_vol);
   const R *dir = reinterpret_cast<const R *>(s->d_dir);
   transport_kernel<R><<<rows_grid(N), kThreads, 0, s->stream>>>(s->d_ptr, s->d_nbr, slot, s->d_wface,
-                                                                 iv, dir, I_int, Is, N, A, R(dt));
+                                                                 iv, dir, I_int, Is, N, A, s->quad_end,
+                                                                 R(dt));
   SrcAdjArgs a;
   a.n = N;
   a.A = A;
@@ -373,7 +372,7 @@ template <typename R> cudaError_t run_adjoint(rt_state *s, const R *I_int, const
   a.newton_max_iter = s->params.newton_max_iter;
   source_adjoint_kernel<R><<<rows_grid(N), kThreads, 0, s->stream>>>(a, Is, lI1_int, lIs);
   transport_adjoint_kernel<R><<<rows_grid(N), kThreads, 0, s->stream>>>(
-      s->d_ptr, s->d_nbr, slot, s->d_wface, iv, dir, lIs, lI_int, N, A, R(dt));
+      s->d_ptr, s->d_nbr, slot, s->d_wface, iv, dir, lIs, lI_int, N, A, s->quad_end, R(dt));
   s->launches += 3;
   return cudaGetLastError();
 }
@@ -383,13 +382,14 @@ template <typename R> cudaError_t run_adjoint(rt_state *s, const R *I_int, const
 cudaError_t adjoint_step(rt_state *s, double dt, const void *I, const double *e, const double *m,
                          const void *lI1, const double *le1, const double *lm1, void *lI,
                          double *le, double *lm, double *gP, double *gJ) {
-  // all pointers are device pointers in the caller's order
+  // all pointers are device pointers in the caller's order; the internal
+  // copies use dense rows (stride A)
   const int64_t N = s->n_cells;
   const unsigned g1 = (unsigned)((N + kThreads - 1) / kThreads);
   double *ws = s->d_adj_ws;  // [14 N]: e, m, (pad), le1, lm1, le, lm, gP, gJ (internal)
   void *I_int = s->d_adj[2], *lI1_int = s->d_adj[3], *lI_int = s->d_adj[4];
-  cudaError_t err = launch_permute_in(s, I, I_int);
-  if (err == cudaSuccess) err = launch_permute_in(s, lI1, lI1_int);
+  cudaError_t err = launch_permute_in(s, I, I_int, s->n_angles);
+  if (err == cudaSuccess) err = launch_permute_in(s, lI1, lI1_int, s->n_angles);
   if (err != cudaSuccess) return err;
   gather_cells<<<g1, kThreads, 0, s->stream>>>(e, ws, s->d_cell_of, N, 1);
   gather_cells<<<g1, kThreads, 0, s->stream>>>(m, ws + N, s->d_cell_of, N, 3);
@@ -405,7 +405,7 @@ cudaError_t adjoint_step(rt_state *s, double dt, const void *I, const double *e,
     err = run_adjoint<double>(s, (const double *)I_int, (const double *)lI1_int,
                               (double *)lI_int, dt, ws);
   if (err != cudaSuccess) return err;
-  err = launch_permute_out(s, lI_int, lI);
+  err = launch_permute_out(s, lI_int, lI, s->n_angles);
   if (err != cudaSuccess) return err;
   scatter_cells<<<g1, kThreads, 0, s->stream>>>(ws + 8 * N, le, s->d_cell_of, N, 1, 0);
   scatter_cells<<<g1, kThreads, 0, s->stream>>>(ws + 9 * N, lm, s->d_cell_of, N, 3, 0);

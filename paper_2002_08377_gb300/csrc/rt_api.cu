@@ -185,7 +185,10 @@ template <typename R> int build_device_mesh(rt_state *s, const rt_mesh_desc *m,
     for (int d = 0; d < 3; ++d) dir[4 * a + d] = (R)m->angle_dir[3 * a + d];
     dir[4 * a + 3] = 0;
   }
-  for (int q = 0; q < A; ++q) wt[q] = (R)m->angle_w[angle_of_position(q, A / 2)];
+  for (int p = 0; p < A / 2; ++p) {  // (w_p, w_{p+A/2}) per pair
+    wt[2 * p] = (R)m->angle_w[p];
+    wt[2 * p + 1] = (R)m->angle_w[p + A / 2];
+  }
   R *dd = nullptr, *dw = nullptr;
   RT_CUDA(s, upload(s, &dd, dir));
   RT_CUDA(s, upload(s, &dw, wt));
@@ -343,11 +346,20 @@ int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state 
   int r = (s->precision == RT_FP32) ? build_device_mesh<float>(s, m, slot_of)
                                     : build_device_mesh<double>(s, m, slot_of);
   if (r != RT_OK) return bail(r);
+  // float rows with A = 16 m (32 <= A <= 128) whose blocks' face slots fit
+  // the step kernel's shared-memory stage take the quad layout
+  s->quad_end = (s->precision == RT_FP32 && A % 16 == 0 && A >= 32 && A <= 128 &&
+                 s->max_block_slots <= rt::STAGE_SLOTS)
+                    ? 32 * (A / 32)
+                    : 0;
+  // dense rows (padding the quad rows to whole 128-byte lines measured no gain)
+  s->row_stride = A;
+  const size_t RS = (size_t)s->row_stride;
   std::vector<double> vol_int(N), dir64(3 * (size_t)A), wt64(A);
   std::vector<int32_t> angle_of(A);
   for (int64_t ic = 0; ic < N; ++ic) vol_int[ic] = m->cell_volume[s->cell_of[ic]];
   for (int q = 0; q < A; ++q) {
-    const int a = angle_of_position(q, A / 2);
+    const int a = angle_of_position(q, A / 2, s->quad_end);
     angle_of[q] = a;
     for (int d = 0; d < 3; ++d) dir64[3 * q + d] = m->angle_dir[3 * a + d];
     wt64[q] = m->angle_w[a];
@@ -375,11 +387,12 @@ int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state 
   CK(dalloc(s, &s->d_out16, 16));
   s->scratch_len = (size_t)rt::totals_scratch_len(N);
   CK(dalloc(s, &s->d_scratch, s->scratch_len));
-  CK(dalloc_bytes(s, &s->d_I[0], (size_t)N * A * s->rsize));
-  CK(dalloc_bytes(s, &s->d_I[1], (size_t)N * A * s->rsize));
-  CK(dalloc_bytes(s, &s->d_I0, (size_t)A * s->rsize));
-  CK(cudaMemsetAsync(s->d_I0, 0, (size_t)A * s->rsize, s->stream));
-  CK(cudaMemsetAsync(s->d_I[0], 0, (size_t)N * A * s->rsize, s->stream));
+  CK(dalloc_bytes(s, &s->d_I[0], (size_t)N * RS * s->rsize));
+  CK(dalloc_bytes(s, &s->d_I[1], (size_t)N * RS * s->rsize));
+  CK(dalloc_bytes(s, &s->d_I0, RS * s->rsize));
+  CK(cudaMemsetAsync(s->d_I0, 0, RS * s->rsize, s->stream));
+  CK(cudaMemsetAsync(s->d_I[0], 0, (size_t)N * RS * s->rsize, s->stream));
+  CK(cudaMemsetAsync(s->d_I[1], 0, (size_t)N * RS * s->rsize, s->stream));
   CK(cudaMemsetAsync(s->d_kind, 0, N, s->stream));
   CK(cudaMemsetAsync(s->d_aux, 0, sizeof(double2) * N, s->stream));
   CK(cudaMemsetAsync(s->d_bc_row, 0, sizeof(int32_t) * N, s->stream));
@@ -475,13 +488,15 @@ int rt_set_cells(rt_state *s, const uint8_t *kind, const double *tau, const doub
     if (n_rows != s->n_rows) {
       cudaFree(s->d_I0);
       s->d_I0 = nullptr;
-      RT_CUDA(s, dalloc_bytes(s, &s->d_I0, (size_t)n_rows * A * s->rsize));
+      RT_CUDA(s, dalloc_bytes(s, &s->d_I0, (size_t)n_rows * s->row_stride * s->rsize));
       s->n_rows = n_rows;
     }
-    // rows in the internal (pair-interleaved) angle order
-    std::vector<double> rows((size_t)n_rows * A);
+    // rows in the internal angle order, row_stride reals apart (padding zero)
+    const int64_t RS = s->row_stride;
+    std::vector<double> rows((size_t)n_rows * RS, 0.0);
     for (int64_t r = 0; r < n_rows; ++r)
-      for (int q = 0; q < A; ++q) rows[r * A + q] = I0[r * A + angle_of_position(q, A / 2)];
+      for (int q = 0; q < A; ++q)
+        rows[r * RS + q] = I0[r * A + angle_of_position(q, A / 2, s->quad_end)];
     if (s->precision == RT_FP32) {
       std::vector<float> f(rows.begin(), rows.end());
       RT_CUDA(s, cudaMemcpy(s->d_I0, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
@@ -502,7 +517,7 @@ int rt_set_intensity(rt_state *s, const void *I, int on_device) {
     RT_CUDA(s, cudaMemcpyAsync(stage, I, bytes, cudaMemcpyHostToDevice, s->stream));
     src = stage;
   }
-  RT_CUDA(s, rt::launch_permute_in(s, src, s->d_I[s->cur]));
+  RT_CUDA(s, rt::launch_permute_in(s, src, s->d_I[s->cur], s->row_stride));
   RT_CUDA(s, cudaStreamSynchronize(s->stream));
   return RT_OK;
 }
@@ -511,10 +526,10 @@ int rt_get_intensity(rt_state *s, void *I, int on_device) {
   if (!s || !I) return s ? fail(s, RT_ERR_ARG, "rt_get_intensity: NULL") : RT_ERR_ARG;
   const size_t bytes = (size_t)s->n_cells * s->n_angles * s->rsize;
   if (on_device) {
-    RT_CUDA(s, rt::launch_permute_out(s, s->d_I[s->cur], I));
+    RT_CUDA(s, rt::launch_permute_out(s, s->d_I[s->cur], I, s->row_stride));
   } else {
     void *stage = s->d_I[s->cur ^ 1];
-    RT_CUDA(s, rt::launch_permute_out(s, s->d_I[s->cur], stage));
+    RT_CUDA(s, rt::launch_permute_out(s, s->d_I[s->cur], stage, s->row_stride));
     RT_CUDA(s, cudaMemcpyAsync(I, stage, bytes, cudaMemcpyDeviceToHost, s->stream));
   }
   RT_CUDA(s, cudaStreamSynchronize(s->stream));
@@ -677,7 +692,7 @@ int rt_adjoint_step(rt_state *s, double dt, const void *I_n, const double *e_n, 
 int rt_get_state(rt_state *s, void *buf, size_t *bytes) {
   if (!s || !bytes) return RT_ERR_ARG;
   const int64_t N = s->n_cells;
-  const size_t nI = (size_t)N * s->n_angles * s->rsize;
+  const size_t nI = (size_t)N * s->row_stride * s->rsize;  // internal rows with padding
   const size_t need = 64 + nI + sizeof(rt::GasDyn) * N + 32 * (size_t)N;
   if (!buf) {
     *bytes = need;
@@ -701,12 +716,13 @@ int rt_get_state(rt_state *s, void *buf, size_t *bytes) {
 int rt_set_state(rt_state *s, const void *buf, size_t bytes) {
   if (!s || !buf) return RT_ERR_ARG;
   const int64_t N = s->n_cells;
-  const size_t nI = (size_t)N * s->n_angles * s->rsize;
+  const size_t nI = (size_t)N * s->row_stride * s->rsize;
   const size_t need = 64 + nI + sizeof(rt::GasDyn) * N + 32 * (size_t)N;
   int64_t hdr[8];
   if (bytes < need) return fail(s, RT_ERR_ARG, "rt_set_state: buffer too small");
   std::memcpy(hdr, buf, 64);
-  if (hdr[0] != 0x52544742 || hdr[1] != N || hdr[2] != s->n_angles || hdr[3] != s->precision)
+  if (hdr[0] != 0x52544742 || hdr[1] != N || hdr[2] != s->n_angles || hdr[3] != s->precision ||
+      hdr[4] != (int64_t)nI)
     return fail(s, RT_ERR_ARG, "rt_set_state: buffer does not match this state");
   const char *b = (const char *)buf;
   RT_CUDA(s, cudaMemcpyAsync(s->d_I[s->cur], b + 64, nI, cudaMemcpyHostToDevice, s->stream));

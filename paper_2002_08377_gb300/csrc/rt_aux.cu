@@ -10,15 +10,17 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// dst[ic][q] = src[cell_of[ic]][angle_of[q]]  (caller order -> internal order)
+// dst[ic][q] = src[cell_of[ic]][angle_of[q]]  (caller order -> internal order;
+// internal rows `stride` reals apart)
 template <typename R>
 __global__ void permute_in_kernel(const R *__restrict__ src, R *__restrict__ dst,
                                   const int64_t *__restrict__ cell_of,
-                                  const int32_t *__restrict__ angle_of, int64_t n, int A) {
+                                  const int32_t *__restrict__ angle_of, int64_t n, int A,
+                                  int stride) {
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   if (row >= n) return;
   const R *s = src + (size_t)cell_of[row] * A;
-  R *d = dst + (size_t)row * A;
+  R *d = dst + (size_t)row * stride;
   for (int k = threadIdx.x % 32; k < A; k += 32) d[k] = s[angle_of[k]];
 }
 
@@ -26,10 +28,11 @@ __global__ void permute_in_kernel(const R *__restrict__ src, R *__restrict__ dst
 template <typename R>
 __global__ void permute_out_kernel(const R *__restrict__ src, R *__restrict__ dst,
                                    const int64_t *__restrict__ cell_of,
-                                   const int32_t *__restrict__ angle_of, int64_t n, int A) {
+                                   const int32_t *__restrict__ angle_of, int64_t n, int A,
+                                   int stride) {
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   if (row >= n) return;
-  const R *s = src + (size_t)row * A;
+  const R *s = src + (size_t)row * stride;
   R *d = dst + (size_t)cell_of[row] * A;
   for (int k = threadIdx.x % 32; k < A; k += 32) d[angle_of[k]] = s[k];
 }
@@ -73,10 +76,11 @@ __global__ void positivity_kernel(const int64_t *__restrict__ ptr,
 template <typename R>
 __global__ void moments_kernel(const R *__restrict__ I, const double *__restrict__ dir,
                                const double *__restrict__ wt, const int64_t *__restrict__ cell_of,
-                               int64_t n, int A, double c, double *E, double *F, double *P) {
+                               int64_t n, int A, int stride, double c, double *E, double *F,
+                               double *P) {
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   if (row >= n) return;
-  const R *Ir = I + (size_t)row * A;
+  const R *Ir = I + (size_t)row * stride;
   double s[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (int a = threadIdx.x % 32; a < A; a += 32) {
     const double wi = wt[a] * (double)Ir[a];
@@ -116,7 +120,8 @@ __global__ void totals_partial_kernel(const R *__restrict__ I, const double *__r
                                       const double *__restrict__ wt,
                                       const double *__restrict__ vol, const GasDyn *__restrict__ gd,
                                       const double *__restrict__ ext, int64_t n, int A,
-                                      double c_over_cbar, double inv_cbar, double *partial) {
+                                      int stride, double c_over_cbar, double inv_cbar,
+                                      double *partial) {
   __shared__ double acc[kThreads / 32][12];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   double t[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -124,7 +129,7 @@ __global__ void totals_partial_kernel(const R *__restrict__ I, const double *__r
   for (int k = warp; k < kTotCells; k += kThreads / 32) {
     const int64_t row = c0 + k;
     if (row >= n) break;
-    const R *Ir = I + (size_t)row * A;
+    const R *Ir = I + (size_t)row * stride;
     double e = 0, fx = 0, fy = 0, fz = 0;
     for (int a = lane; a < A; a += 32) {
       const double wi = wt[a] * (double)Ir[a];
@@ -218,26 +223,28 @@ unsigned rows_grid(int64_t n) { return (unsigned)((n + kThreads / 32 - 1) / (kTh
 
 }  // namespace
 
-cudaError_t launch_permute_in(rt_state *s, const void *src, void *dst) {
+cudaError_t launch_permute_in(rt_state *s, const void *src, void *dst, int stride) {
   if (s->precision == RT_FP32)
     permute_in_kernel<float><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
-        (const float *)src, (float *)dst, s->d_cell_of, s->d_angle_of, s->n_cells, s->n_angles);
+        (const float *)src, (float *)dst, s->d_cell_of, s->d_angle_of, s->n_cells, s->n_angles,
+        stride);
   else
     permute_in_kernel<double><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
         (const double *)src, (double *)dst, s->d_cell_of, s->d_angle_of, s->n_cells,
-        s->n_angles);
+        s->n_angles, stride);
   s->launches++;
   return cudaGetLastError();
 }
 
-cudaError_t launch_permute_out(rt_state *s, const void *src, void *dst) {
+cudaError_t launch_permute_out(rt_state *s, const void *src, void *dst, int stride) {
   if (s->precision == RT_FP32)
     permute_out_kernel<float><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
-        (const float *)src, (float *)dst, s->d_cell_of, s->d_angle_of, s->n_cells, s->n_angles);
+        (const float *)src, (float *)dst, s->d_cell_of, s->d_angle_of, s->n_cells, s->n_angles,
+        stride);
   else
     permute_out_kernel<double><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
         (const double *)src, (double *)dst, s->d_cell_of, s->d_angle_of, s->n_cells,
-        s->n_angles);
+        s->n_angles, stride);
   s->launches++;
   return cudaGetLastError();
 }
@@ -264,11 +271,11 @@ cudaError_t launch_moments(rt_state *s, double *E, double *F, double *P) {
   if (s->precision == RT_FP32)
     moments_kernel<float><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
         (const float *)I, s->d_dir64, s->d_wt64, s->d_cell_of, s->n_cells, s->n_angles,
-        s->params.c, E, F, P);
+        s->row_stride, s->params.c, E, F, P);
   else
     moments_kernel<double><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
         (const double *)I, s->d_dir64, s->d_wt64, s->d_cell_of, s->n_cells, s->n_angles,
-        s->params.c, E, F, P);
+        s->row_stride, s->params.c, E, F, P);
   s->launches++;
   return cudaGetLastError();
 }
@@ -281,11 +288,11 @@ cudaError_t launch_totals(rt_state *s, double *d_out16) {
   if (s->precision == RT_FP32)
     totals_partial_kernel<float><<<(unsigned)nb, kThreads, 0, s->stream>>>(
         (const float *)I, s->d_dir64, s->d_wt64, s->d_volume, s->d_gd, s->d_ext, s->n_cells,
-        s->n_angles, coc, icb, s->d_scratch);
+        s->n_angles, s->row_stride, coc, icb, s->d_scratch);
   else
     totals_partial_kernel<double><<<(unsigned)nb, kThreads, 0, s->stream>>>(
         (const double *)I, s->d_dir64, s->d_wt64, s->d_volume, s->d_gd, s->d_ext, s->n_cells,
-        s->n_angles, coc, icb, s->d_scratch);
+        s->n_angles, s->row_stride, coc, icb, s->d_scratch);
   totals_final_kernel<<<1, 32, 0, s->stream>>>(s->d_scratch, nb, d_out16);
   s->launches += 2;
   return cudaGetLastError();

@@ -41,8 +41,8 @@ enum : unsigned {
 
 // The step kernel works on blocks of CPB consecutive (internal) cells.
 constexpr int CPB = 32;
-// Face slots (and neighbour indices) of one block that the float kernel
-// stages in shared memory; meshes with a larger block read them from global.
+// Face slots of one block of CPB cells that the float QuadMap kernel stages
+// in shared memory at most; meshes with more take the PairMap kernel.
 constexpr int STAGE_SLOTS = 1024;
 
 // Per-cell constant gas data: rho, the absorption / scattering coefficients
@@ -61,6 +61,7 @@ struct alignas(32) GasDyn {
 template <typename R> struct StepArgs {
   int64_t n_cells;
   int32_t n_angles, half;
+  int32_t row;              // reals between intensity rows (I_in, I_out, I0)
   const int64_t *ptr;       // [N+1] slot range per internal cell
   const int32_t *nbr;       // [nnz] internal neighbour index
   const typename SlotOf<R>::type *slot;  // [nnz]
@@ -90,10 +91,21 @@ template <typename R> struct StepArgs {
 
 }  // namespace rt
 
-// Internal intensity rows store the antipodal pairs side by side: position
-// 2p holds angle p and position 2p + 1 holds angle p + A/2 (p < A/2).
-__host__ __device__ inline int angle_of_position(int q, int half) {
+// Internal intensity rows.  Pair p < A/2 couples angle p with its antipode
+// p + A/2.  Positions q >= quad_end store the pairs side by side (2p + s
+// holds angle p + s A/2).  Positions q < quad_end (float states with A a
+// multiple of 16; quad_end = 32 floor(A/32), else 0) group two pairs per
+// four positions: 4Q, 4Q+1, 4Q+2, 4Q+3 hold angles 2Q, 2Q+1, 2Q + A/2,
+// 2Q+1 + A/2, so one 16-byte access gives a thread both pairs with the
+// angles of one hemisphere side by side.
+__host__ __device__ inline int angle_of_position(int q, int half, int quad_end) {
+  if (q < quad_end) return 2 * (q >> 2) + (q & 1) + ((q & 2) ? half : 0);
   return (q & 1) ? (q >> 1) + half : (q >> 1);
+}
+__host__ __device__ inline int position_of_angle(int a, int half, int quad_end) {
+  const int p = a < half ? a : a - half, s = a < half ? 0 : 1;
+  if (2 * p < quad_end) return 4 * (p >> 1) + (p & 1) + 2 * s;
+  return 2 * p + s;
 }
 
 // Opaque state behind the C ABI.
@@ -109,6 +121,8 @@ struct rt_state {
   bool gas_set = false;
   bool moving = false;  // some face has a non-zero velocity
   int64_t max_block_slots = 0;  // max over blocks of CPB cells of their face slots
+  int quad_end = 0;  // internal row layout (see angle_of_position)
+  int32_t row_stride = 0;  // reals between internal rows of d_I[0], d_I[1], d_I0 (>= n_angles)
   int64_t n_rows = 0;
   std::string err;
   int64_t launches = 0;
@@ -159,8 +173,9 @@ namespace rt {
 cudaError_t launch_step(rt_state *s, double dt);
 
 // auxiliary kernels (rt_aux.cu)
-cudaError_t launch_permute_in(rt_state *s, const void *src, void *dst);
-cudaError_t launch_permute_out(rt_state *s, const void *src, void *dst);
+// caller order <-> internal order; the internal rows are `stride` reals apart
+cudaError_t launch_permute_in(rt_state *s, const void *src, void *dst, int stride);
+cudaError_t launch_permute_out(rt_state *s, const void *src, void *dst, int stride);
 cudaError_t launch_positivity(rt_state *s, double *d_kmax);
 cudaError_t launch_moments(rt_state *s, double *E, double *F, double *P);
 cudaError_t launch_totals(rt_state *s, double *d_out16);

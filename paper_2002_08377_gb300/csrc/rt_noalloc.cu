@@ -65,7 +65,8 @@ __global__ void totals_blocks_kernel(const R *__restrict__ I, const double *__re
                                      const double *__restrict__ wt,
                                      const double *__restrict__ vol,
                                      const rt::GasDyn *__restrict__ gd,
-                                     const double *__restrict__ ext, int64_t n, int A, int64_t cpb,
+                                     const double *__restrict__ ext, int64_t n, int A,
+                                     int stride, int64_t cpb,
                                      double c_over_cbar, double inv_cbar, double *partial) {
   __shared__ double acc[kThreads / 32][kParts];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -74,7 +75,7 @@ __global__ void totals_blocks_kernel(const R *__restrict__ I, const double *__re
   const int64_t c1 = c0 + cpb < n ? c0 + cpb : n;
   const double fp = 4.0 * rt::kPi;
   for (int64_t row = c0 + warp; row < c1; row += kThreads / 32) {
-    const R *Ir = I + (size_t)row * A;
+    const R *Ir = I + (size_t)row * stride;
     double e = 0, fx = 0, fy = 0, fz = 0;
     for (int a = lane; a < A; a += 32) {
       const double wi = wt[a] * (double)Ir[a];
@@ -166,11 +167,11 @@ extern "C" int rt_totals_noalloc(rt_state *s, double out[16]) {
   if (s->precision == RT_FP32)
     totals_blocks_kernel<float><<<nb, kThreads, 0, s->stream>>>(
         (const float *)I, s->d_dir64, s->d_wt64, s->d_volume, s->d_gd, s->d_ext, s->n_cells,
-        s->n_angles, cpb, coc, icb, partial);
+        s->n_angles, s->row_stride, cpb, coc, icb, partial);
   else
     totals_blocks_kernel<double><<<nb, kThreads, 0, s->stream>>>(
         (const double *)I, s->d_dir64, s->d_wt64, s->d_volume, s->d_gd, s->d_ext, s->n_cells,
-        s->n_angles, cpb, coc, icb, partial);
+        s->n_angles, s->row_stride, cpb, coc, icb, partial);
   totals_combine_kernel<<<1, 32, 0, s->stream>>>(partial, nb, res);
   s->launches += 2;
   e = cudaGetLastError();

@@ -41,20 +41,76 @@ namespace rt {
 namespace {
 using namespace step;
 
-// The block's face slots and neighbour indices (float kernel, STAGED).
-struct FaceStage {
-  SlotF slot[STAGE_SLOTS];
-  int32_t nbr[STAGE_SLOTS];
-};
-
+// Per-block sums exchanged between the phases.
 template <typename R> struct Shared {
-  GasStatic gs[CPB];  // gas of the block's cells, prefetched for warp 0
-  GasDyn gd[CPB];
   R sI[CPB], sG[CPB], s1[CPB];  // the sums of Eq. (Jcom) and sum w~/(1+x), unnormalised
   R q[CPB];                     // dt cbar rho (kP B + kS J) per interior cell
   R dE[CPB], dF[3][CPB];        // sum w (I* - I') and sum w n (I* - I')
   unsigned bad[CPB];
 };
+
+// Gas records of a block's cells in shared memory, for the lane-per-cell
+// phases (B for double states, D).
+struct SharedGas {
+  GasStatic gs[CPB];
+  GasDyn gd[CPB];
+};
+
+// One tile's inputs staged in shared memory by the float QuadMap kernel:
+// the tile's face slots (static meshes: with the neighbour index in w), the
+// neighbour indices (moving meshes) and the gas records.
+struct StageView {
+  SlotF *slot;
+  int32_t *nbr;
+  SharedGas *gas;
+};
+__host__ __device__ inline int stage_cap(int64_t max_block_slots) {
+  return (int)((max_block_slots + 7) & ~int64_t(7));
+}
+__host__ __device__ inline size_t stage_gas_offset(int cap, bool moving) {
+  return ((size_t)cap * (sizeof(SlotF) + (moving ? sizeof(int32_t) : 0)) + 63) & ~size_t(63);
+}
+__host__ __device__ inline size_t stage_bytes(int cap, bool moving) {
+  return stage_gas_offset(cap, moving) + sizeof(SharedGas);
+}
+__device__ __forceinline__ StageView stage_at(unsigned char *base, int cap, bool moving) {
+  StageView v;
+  v.slot = reinterpret_cast<SlotF *>(base);
+  v.nbr = reinterpret_cast<int32_t *>(base + (size_t)cap * sizeof(SlotF));
+  v.gas = reinterpret_cast<SharedGas *>(base + stage_gas_offset(cap, moving));
+  return v;
+}
+
+// All threads: asynchronous copies of tile `tile`'s slots, neighbour indices
+// and gas records into v (one contiguous range of each array).
+template <bool MOVING>
+__device__ __forceinline__ void issue_stage(const StepArgs<float> &a, int64_t tile,
+                                            const StageView &v) {
+  const int64_t c0 = tile * CPB;
+  const int64_t c1 = c0 + CPB < a.n_cells ? c0 + CPB : a.n_cells;
+  const int64_t kb = a.ptr[c0];
+  const int cnt = (int)(a.ptr[c1] - kb);
+  if (MOVING) {
+    const SlotF *gsl = reinterpret_cast<const SlotF *>(a.slot) + kb;
+    for (int i = threadIdx.x; i < cnt; i += NT) {
+      cp_async16(v.slot + i, gsl + i);
+      cp_async4(v.nbr + i, a.nbr + kb + i);
+    }
+  } else {
+    for (int i = threadIdx.x; i < cnt; i += NT) cp_async16(v.slot + i, a.slot_nb + kb + i);
+  }
+  // 6 x 16 bytes per cell: GasStatic (64) then GasDyn (32)
+  const int nc = (int)(c1 - c0);
+  for (int i = threadIdx.x; i < 6 * nc; i += NT) {
+    const int cc = i / 6, k = i % 6;
+    if (k < 4)
+      cp_async16(reinterpret_cast<char *>(&v.gas->gs[cc]) + 16 * k,
+                 reinterpret_cast<const char *>(a.gs + c0 + cc) + 16 * k);
+    else
+      cp_async16(reinterpret_cast<char *>(&v.gas->gd[cc]) + 16 * (k - 4),
+                 reinterpret_cast<const char *>(a.gd + c0 + cc) + 16 * (k - 4));
+  }
+}
 
 // ------------------------------------------------------------ pair maps
 // count(H, sub): pairs the thread owns (entries j >= count are padding);
@@ -63,6 +119,7 @@ template <typename R> struct Shared {
 template <typename R, int PPT_, bool FULL_> struct PairMap {
   static constexpr int PPT = PPT_;
   static constexpr bool FULL = FULL_;
+  static constexpr bool QUAD = false;
   using V = pair_t<R>;
   __device__ static int count(int H, int sub) { return FULL ? PPT : (H - sub + KT - 1) / KT; }
   __device__ static int pair(int j, int sub) { return sub + KT * j; }
@@ -85,9 +142,14 @@ template <typename R, int PPT_, bool FULL_> struct PairMap {
   }
 };
 
-template <int Q4, bool TAIL> struct QuadMap {
+// The quad region of a row holds (I_2Q, I_2Q+1, I_2Q+H, I_2Q+1+H) per 16 bytes
+// (angle_of_position with quad_end = 32 Q4), the tail pairs side by side.
+template <int Q4_, bool TAIL_> struct QuadMap {
+  static constexpr int Q4 = Q4_;
+  static constexpr bool TAIL = TAIL_;
   static constexpr int PPT = 2 * Q4 + (TAIL ? 1 : 0);
   static constexpr bool FULL = true;
+  static constexpr bool QUAD = true;
   __device__ static int count(int, int) { return PPT; }
   __device__ static int pair(int j, int sub) {
     return j < 2 * Q4 ? 2 * (sub + KT * (j >> 1)) + (j & 1) : 16 * Q4 + sub;
@@ -99,8 +161,8 @@ template <int Q4, bool TAIL> struct QuadMap {
     for (int i = 0; i < Q4; ++i) {
       const float4 t = q[KT * i];
       x[2 * i] = t.x;
-      y[2 * i] = t.y;
-      x[2 * i + 1] = t.z;
+      x[2 * i + 1] = t.y;
+      y[2 * i] = t.z;
       y[2 * i + 1] = t.w;
     }
     if (TAIL) {
@@ -114,10 +176,84 @@ template <int Q4, bool TAIL> struct QuadMap {
     float4 *q = reinterpret_cast<float4 *>(row) + sub;
 #pragma unroll
     for (int i = 0; i < Q4; ++i)
-      q[KT * i] = make_float4(x[2 * i], y[2 * i], x[2 * i + 1], y[2 * i + 1]);
+      q[KT * i] = make_float4(x[2 * i], x[2 * i + 1], y[2 * i], y[2 * i + 1]);
     if (TAIL) reinterpret_cast<float2 *>(row)[16 * Q4 + sub] = make_float2(x[2 * Q4], y[2 * Q4]);
   }
 };
+
+// face_sum for QuadMap (float): the two pairs of a quad are processed as
+// f32x2 vectors.  Per face and pair, with d = n . s and u = d - w for the
+// angle, u' = -d - w for its antipode:
+//   acc  += max(u, 0) I_own + min(u, 0) I_nbr          (upwind value of u)
+//   acc' += min(e, 0) I'_own + max(e, 0) I'_nbr,  e = d + w = -u',
+// and the antipode's sum is -acc'.  One of each max / min is zero, so this
+// equals the select-and-multiply form exactly.
+template <typename M, bool MOVING, bool PACKED, typename K>
+__device__ __forceinline__ void face_sum_quads(const SlotF *__restrict__ slot,
+                                               const int32_t *__restrict__ nbr, K k0, K k1,
+                                               const float *__restrict__ I_in, int RS, int sub,
+                                               const float (&nx)[M::PPT], const float (&ny)[M::PPT],
+                                               const float (&nz)[M::PPT], const float (&Ia)[M::PPT],
+                                               const float (&Ib)[M::PPT], float (&acca)[M::PPT],
+                                               float (&accb)[M::PPT]) {
+  constexpr int Q4 = M::Q4;
+  float2 NX[Q4], NY[Q4], NZ[Q4], OA[Q4], OB[Q4], CA[Q4], CB[Q4];
+#pragma unroll
+  for (int i = 0; i < Q4; ++i) {
+    NX[i] = make_float2(nx[2 * i], nx[2 * i + 1]);
+    NY[i] = make_float2(ny[2 * i], ny[2 * i + 1]);
+    NZ[i] = make_float2(nz[2 * i], nz[2 * i + 1]);
+    OA[i] = make_float2(Ia[2 * i], Ia[2 * i + 1]);
+    OB[i] = make_float2(Ib[2 * i], Ib[2 * i + 1]);
+    CA[i] = make_float2(0.0f, 0.0f);
+    CB[i] = CA[i];
+  }
+  const float2 zero = make_float2(0.0f, 0.0f);
+#pragma unroll 2
+  for (K k = k0; k < k1; ++k) {
+    const float4 s = *reinterpret_cast<const float4 *>(slot + k);
+    int32_t nb;
+    if constexpr (PACKED)
+      nb = __float_as_int(s.w);
+    else
+      nb = nbr[k];
+    const float *row = I_in + (size_t)nb * RS;
+    const float4 *q = reinterpret_cast<const float4 *>(row) + sub;
+    float4 v[Q4];
+#pragma unroll
+    for (int i = 0; i < Q4; ++i) v[i] = q[KT * i];
+    float2 vt = zero;
+    if (M::TAIL) vt = reinterpret_cast<const float2 *>(row)[16 * Q4 + sub];
+    const float2 SX = make_float2(s.x, s.x), SY = make_float2(s.y, s.y),
+                 SZ = make_float2(s.z, s.z);
+    const float w = MOVING ? s.w : 0.0f;
+    const float2 W = make_float2(w, w);
+#pragma unroll
+    for (int i = 0; i < Q4; ++i) {
+      const float2 D = pfma(NX[i], SX, pfma(NY[i], SY, pmul(NZ[i], SZ)));
+      const float2 U = MOVING ? psub(D, W) : D;   // u of the two angles
+      const float2 E = MOVING ? padd(D, W) : D;   // -u' of their antipodes
+      const float2 UP = make_float2(fmaxf(U.x, 0.0f), fmaxf(U.y, 0.0f));
+      const float2 UM = make_float2(fminf(U.x, 0.0f), fminf(U.y, 0.0f));
+      const float2 EP = MOVING ? make_float2(fmaxf(E.x, 0.0f), fmaxf(E.y, 0.0f)) : UP;
+      const float2 EM = MOVING ? make_float2(fminf(E.x, 0.0f), fminf(E.y, 0.0f)) : UM;
+      CA[i] = pfma(UP, OA[i], pfma(UM, make_float2(v[i].x, v[i].y), CA[i]));
+      CB[i] = pfma(EM, OB[i], pfma(EP, make_float2(v[i].z, v[i].w), CB[i]));
+    }
+    if (M::TAIL) {
+      constexpr int j = 2 * Q4;
+      face_pair<float, MOVING>(fmaf(nx[j], s.x, fmaf(ny[j], s.y, nz[j] * s.z)), w, vt.x, vt.y,
+                               Ia[j], Ib[j], acca[j], accb[j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < Q4; ++i) {
+    acca[2 * i] = CA[i].x;
+    acca[2 * i + 1] = CA[i].y;
+    accb[2 * i] = -CB[i].x;
+    accb[2 * i + 1] = -CB[i].y;
+  }
+}
 
 // sum_f u I_up over the slots [k0, k1) of one cell, neighbour rows read
 // through nbr[k] (L1/L2 serve the reuse between neighbouring cells; cells are
@@ -127,28 +263,33 @@ template <int Q4, bool TAIL> struct QuadMap {
 template <typename R, typename M, bool MOVING, bool PACKED, typename S, typename K>
 __device__ __forceinline__ void face_sum(const S *__restrict__ slot, const int32_t *__restrict__ nbr,
                                          const double *__restrict__ wface, K k0, K k1,
-                                         const R *__restrict__ I_in, int A, int sub,
+                                         const R *__restrict__ I_in, int RS, int sub,
                                          const R (&nx)[M::PPT], const R (&ny)[M::PPT],
                                          const R (&nz)[M::PPT], const R (&Ia)[M::PPT],
                                          const R (&Ib)[M::PPT], R (&acca)[M::PPT],
                                          R (&accb)[M::PPT], int np) {
   constexpr int PPT = M::PPT;
-#pragma unroll 1
-  for (K k = k0; k < k1; ++k) {
-    const S s = slot[k];
-    int32_t nb;
-    if constexpr (PACKED)
-      nb = __float_as_int(s.w);
-    else
-      nb = nbr[k];
-    R vx[PPT], vy[PPT];
-    M::load(I_in + (size_t)nb * A, sub, vx, vy, np);
-    const R w = MOVING ? slot_w(s, wface, k) : R(0);
+  if constexpr (M::QUAD) {
+    face_sum_quads<M, MOVING, PACKED>(slot, nbr, k0, k1, I_in, RS, sub, nx, ny, nz, Ia, Ib, acca,
+                                      accb);
+  } else {
+#pragma unroll 2
+    for (K k = k0; k < k1; ++k) {
+      const S s = slot[k];
+      int32_t nb;
+      if constexpr (PACKED)
+        nb = __float_as_int(s.w);
+      else
+        nb = nbr[k];
+      R vx[PPT], vy[PPT];
+      M::load(I_in + (size_t)nb * RS, sub, vx, vy, np);
+      const R w = MOVING ? slot_w(s, wface, k) : R(0);
 #pragma unroll
-    for (int j = 0; j < PPT; ++j)
-      if (M::FULL || j < np)
-        face_pair<R, MOVING>(slot_dot(nx[j], ny[j], nz[j], s), w, vx[j], vy[j], Ia[j], Ib[j],
-                             acca[j], accb[j]);
+      for (int j = 0; j < PPT; ++j)
+        if (M::FULL || j < np)
+          face_pair<R, MOVING>(slot_dot(nx[j], ny[j], nz[j], s), w, vx[j], vy[j], Ia[j], Ib[j],
+                               acca[j], accb[j]);
+    }
   }
 }
 
@@ -169,11 +310,12 @@ __device__ __forceinline__ double source_q(const StepArgs<R> &a, const GasStatic
   const double rU = rcp(fma(dJ, SG, S1));
   const double kin = 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * g.inv_rho;
   const double alpha = a.k_alpha * g.rkP * S1 * rU;
-  const double gq = (d.e - kin) + a.k_g * g.rkJ * SI * rU;
+  const double eint = d.e - kin;
+  const double gq = eint + a.k_g * g.rkJ * SI * rU;
   double T = 0.0;
   if (!(gq >= 0.0) || !(alpha >= 0.0)) {
     bad |= ST_NONFINITE;
-  } else if (quartic_root(alpha, g.rcv, gq, a.newton_max_iter, &T)) {
+  } else if (quartic_root(alpha, g.rcv, gq, eint / g.rcv, 1e-15, a.newton_max_iter, &T)) {
     bad |= ST_NONCONV;
   }
   const double B = a.a_rad * (T * T) * (T * T) * (1.0 / (4.0 * kPi));
@@ -198,7 +340,7 @@ __device__ __forceinline__ float source_q_float(const StepArgs<float> &a, int64_
   }
   if (isfinite(alpha) && isfinite(gq)) {
     float T;
-    const int nc = quartic_root(alpha, rcv, gq, a.newton_max_iter, &T);
+    const int nc = quartic_root(alpha, rcv, gq, eint * rcp(rcv), 1e-7f, a.newton_max_iter, &T);
     const float B = a.a_rad_4pi_f * (T * T) * (T * T);
     const float J = fmaf(dP * B, SG, SI) * rU;
     const float q = fmaf(dP, B, dS * J);
@@ -210,10 +352,13 @@ __device__ __forceinline__ float source_q_float(const StepArgs<float> &a, int64_
   return (float)source_q(a, a.gs[c], a.gd[c], (double)SI, (double)SG, (double)S1, bad);
 }
 
-// One block of CPB cells: phases A-D (see the top of the file).
+// One block of CPB cells: phases A-D (see the top of the file).  STAGED:
+// the caller has started the copies of the tile's slots and gas records into
+// `stage`, and the face loop waits for them; otherwise slots are read from
+// global memory and warp 0 copies the gas records into `gas` itself.
 template <typename R, typename M, bool MOVING, bool STAGED>
 __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t tile, Shared<R> &sh,
-                                          FaceStage *fs) {
+                                          SharedGas *gas, const StageView &stage) {
   using V = pair_t<R>;
   constexpr int PPT = M::PPT;
   const int lc = threadIdx.x / KT;
@@ -222,40 +367,25 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   const int64_t cell = tile * CPB + lc;
   const bool live = cell < a.n_cells;
   const int64_t c = live ? cell : a.n_cells - 1;  // dead lanes shadow the last cell
-  const int A = a.n_angles;
+  const int RS = a.row;  // reals between intensity rows
   const int np = M::count(a.half, sub);
 
-  // warp 0 prefetches its cells' gas state for phases B and D
   const int64_t cl = tile * CPB + lane;  // warp 0: lane-per-cell
-  if (warp == 0 && lane < CPB && cl < a.n_cells) {
+  if (!STAGED && warp == 0 && lane < CPB && cl < a.n_cells) {
+    // warp 0 prefetches its cells' gas state for phases B and D
     const char *g = reinterpret_cast<const char *>(a.gs + cl);
     const char *d = reinterpret_cast<const char *>(a.gd + cl);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) cp_async16(reinterpret_cast<char *>(&sh.gs[lane]) + 16 * k, g + 16 * k);
+    for (int k = 0; k < 4; ++k)
+      cp_async16(reinterpret_cast<char *>(&gas->gs[lane]) + 16 * k, g + 16 * k);
 #pragma unroll
-    for (int k = 0; k < 2; ++k) cp_async16(reinterpret_cast<char *>(&sh.gd[lane]) + 16 * k, d + 16 * k);
-  }
-  // STAGED: all threads copy the block's slots and neighbour indices (one
-  // contiguous range of the CSR arrays) into shared memory
-  int64_t kb = 0;
-  if constexpr (STAGED) {
-    const int64_t c1 = tile * CPB + CPB < a.n_cells ? tile * CPB + CPB : a.n_cells;
-    kb = a.ptr[tile * CPB];
-    const int cnt = (int)(a.ptr[c1] - kb);
-    if (MOVING) {
-      const SlotF *gsl = reinterpret_cast<const SlotF *>(a.slot) + kb;
-      for (int i = threadIdx.x; i < cnt; i += NT) {
-        cp_async16(&fs->slot[i], gsl + i);
-        cp_async4(&fs->nbr[i], a.nbr + kb + i);
-      }
-    } else {
-      for (int i = threadIdx.x; i < cnt; i += NT) cp_async16(&fs->slot[i], a.slot_nb + kb + i);
-    }
+    for (int k = 0; k < 2; ++k)
+      cp_async16(reinterpret_cast<char *>(&gas->gd[lane]) + 16 * k, d + 16 * k);
   }
 
   // ---------------- phase A: transport, I* = I - dt/V sum_f u I_up
   R nx[PPT], ny[PPT], nz[PPT], Ia[PPT], Ib[PPT], acca[PPT], accb[PPT];
-  M::load(a.I_in + (size_t)c * A, sub, Ia, Ib, np);
+  M::load(a.I_in + (size_t)c * RS, sub, Ia, Ib, np);
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
     load_dir(a.dir, (M::FULL || j < np) ? M::pair(j, sub) : 0, nx[j], ny[j], nz[j]);
@@ -263,14 +393,15 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
     accb[j] = R(0);
   }
   if constexpr (STAGED) {
+    const int64_t kb = a.ptr[tile * CPB];
     const int k0 = (int)(a.ptr[c] - kb), k1 = (int)(a.ptr[c + 1] - kb);
     cp_async_wait_all();
-    __syncthreads();
-    face_sum<R, M, MOVING, !MOVING>(reinterpret_cast<const typename SlotOf<R>::type *>(fs->slot),
-                                    fs->nbr, a.wface, k0, k1, a.I_in, A, sub, nx, ny, nz, Ia, Ib,
-                                    acca, accb, np);
+    __syncthreads();  // the block's stage has landed
+    face_sum<R, M, MOVING, !MOVING>(reinterpret_cast<const typename SlotOf<R>::type *>(stage.slot),
+                                    stage.nbr, a.wface, k0, k1, a.I_in, RS, sub, nx, ny, nz, Ia,
+                                    Ib, acca, accb, np);
   } else {
-    face_sum<R, M, MOVING, false>(a.slot, a.nbr, a.wface, a.ptr[c], a.ptr[c + 1], a.I_in, A, sub,
+    face_sum<R, M, MOVING, false>(a.slot, a.nbr, a.wface, a.ptr[c], a.ptr[c + 1], a.I_in, RS, sub,
                                   nx, ny, nz, Ia, Ib, acca, accb, np);
   }
   {
@@ -346,7 +477,7 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
       R ql = 0;
       unsigned bl = 0;
       if (cl < a.n_cells && a.kind[cl] == RT_CELL_INTERIOR)
-        ql = R(source_q(a, sh.gs[lane], sh.gd[lane], (double)sh.sI[lane], (double)sh.sG[lane],
+        ql = R(source_q(a, gas->gs[lane], gas->gd[lane], (double)sh.sI[lane], (double)sh.sG[lane],
                         (double)sh.s1[lane], bl));
       sh.q[lane] = ql;
       sh.bad[lane] = bl;
@@ -368,7 +499,7 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
       const double2 ax = a.aux[c];
       const R f = R((ax.x <= a.dt) ? 1.0 : a.dt / ax.x);
       R tx[PPT], ty[PPT];
-      M::load(a.I0 + (size_t)a.bc_row[c] * A, sub, tx, ty, np);
+      M::load(a.I0 + (size_t)a.bc_row[c] * RS, sub, tx, ty, np);
 #pragma unroll
       for (int j = 0; j < PPT; ++j) {
         na[j] = fma(-f, Ia[j] - tx[j], Ia[j]);
@@ -397,7 +528,7 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
         nb[j] = n.y;
       }
     }
-    if (live) M::store(a.I_out + (size_t)c * A, sub, na, nb, np);
+    if (live) M::store(a.I_out + (size_t)c * RS, sub, na, nb, np);
     V dev = mk(R(0), R(0));
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
@@ -434,20 +565,22 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   __syncthreads();
 
   // ---------------- phase D: gas exchange (Eqs. gas1, gas2), one lane per cell
+  const GasStatic *gs_s = STAGED ? stage.gas->gs : gas->gs;
+  const GasDyn *gd_s = STAGED ? stage.gas->gd : gas->gd;
   if (warp == 0 && lane < CPB && cl < a.n_cells) {
     // dE_gas = (c/cbar) 4 pi sum w dI, d(rho v) = (4 pi c sum w n dI) / (c cbar)
     const double dE = a.k_fe * (double)sh.dE[lane];
     const double dx = a.k_fm * (double)sh.dF[0][lane], dy = a.k_fm * (double)sh.dF[1][lane],
                  dz = a.k_fm * (double)sh.dF[2][lane];
     if (a.kind[cl] == RT_CELL_INTERIOR) {
-      GasDyn d = sh.gd[lane];
+      GasDyn d = gd_s[lane];
       d.e += dE;
       d.mx += dx;
       d.my += dy;
       d.mz += dz;
       a.gd[cl] = d;
       // frame velocity and internal energy for the next step
-      const double ir = sh.gs[lane].inv_rho;
+      const double ir = gs_s[lane].inv_rho;
       const double kin = 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * ir;
       store4(a.cellv + 4 * cl, R(d.mx * ir), R(d.my * ir), R(d.mz * ir), R(d.e - kin));
     } else {
@@ -465,18 +598,27 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   }
 }
 
-// Float kernels with up to 5 pairs per thread fit four blocks per SM in
-// registers; wider ones take three, double ones two.
-template <typename R, typename M, bool MOVING, bool STAGED>
+// One block per CPB cells.  Float kernels with up to 5 pairs per thread fit
+// four blocks per SM in registers; wider ones take three, double ones two.
+template <typename R, typename M, bool MOVING>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (M::PPT <= 5 ? 4 : 3) : 2)
     step_kernel(const StepArgs<R> a) {
   __shared__ Shared<R> sh;
-  if constexpr (STAGED) {
-    __shared__ __align__(16) FaceStage fs;
-    tile_step<R, M, MOVING, true>(a, blockIdx.x, sh, &fs);
-  } else {
-    tile_step<R, M, MOVING, false>(a, blockIdx.x, sh, nullptr);
-  }
+  __shared__ SharedGas gas;
+  tile_step<R, M, MOVING, false>(a, blockIdx.x, sh, &gas, StageView{});
+}
+
+// Float kernel with the QuadMap: the block first starts the copies of its
+// slots and gas records into shared memory, then loads its own rows and
+// directions while they land (tile_step waits before the face loop).
+template <typename M, bool MOVING>
+__global__ void __launch_bounds__(NT, M::PPT <= 5 ? 4 : 3)
+    step_kernel_staged(const StepArgs<float> a, int cap) {
+  __shared__ Shared<float> sh;
+  extern __shared__ __align__(128) unsigned char dyn[];
+  const StageView v = stage_at(dyn, cap, MOVING);
+  issue_stage<MOVING>(a, blockIdx.x, v);
+  tile_step<float, M, MOVING, true>(a, blockIdx.x, sh, nullptr, v);
 }
 
 // Fills the kernel arguments and launches one step with pair map M.
@@ -486,6 +628,7 @@ cudaError_t launch_t(rt_state *s, double dt) {
   a.n_cells = s->n_cells;
   a.n_angles = s->n_angles;
   a.half = s->n_angles / 2;
+  a.row = s->row_stride;
   a.ptr = s->d_ptr;
   a.nbr = s->d_nbr;
   a.slot = reinterpret_cast<const typename SlotOf<R>::type *>(s->d_slot);
@@ -525,7 +668,12 @@ cudaError_t launch_t(rt_state *s, double dt) {
   a.status = s->d_status;
   a.bad_cell = s->d_bad;
   const unsigned blocks = (unsigned)((s->n_cells + CPB - 1) / CPB);
-  step_kernel<R, M, MOVING, STAGED><<<blocks, NT, 0, s->stream>>>(a);
+  if constexpr (STAGED) {
+    const int cap = stage_cap(s->max_block_slots);
+    step_kernel_staged<M, MOVING><<<blocks, NT, stage_bytes(cap, MOVING), s->stream>>>(a, cap);
+  } else {
+    step_kernel<R, M, MOVING><<<blocks, NT, 0, s->stream>>>(a);
+  }
   s->launches++;
   return cudaGetLastError();
 }
@@ -562,8 +710,7 @@ template <bool MOVING> cudaError_t dispatch_quads(rt_state *s, double dt) {
 
 template <typename R> cudaError_t dispatch(rt_state *s, double dt) {
   const int A = s->n_angles;
-  if (sizeof(R) == 4 && A % 16 == 0 && A >= 32 && A <= 128 &&
-      s->max_block_slots <= STAGE_SLOTS)
+  if (sizeof(R) == 4 && s->quad_end > 0)  // rows in the quad layout
     return s->moving ? dispatch_quads<true>(s, dt) : dispatch_quads<false>(s, dt);
   const bool full = (A / 2) % KT == 0;
   if (s->moving)

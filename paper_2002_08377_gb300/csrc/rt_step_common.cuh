@@ -134,49 +134,35 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // Positive root of alpha T^4 + beta T = g (alpha >= 0, beta > 0, g >= 0).
-// f is increasing and convex on T > 0, so Newton from any point at or above
-// the root decreases monotonically onto it.  Start at
-// min(g/beta, (g/alpha)^(1/4)) and stop when an iterate fails to decrease or
+// f is increasing and convex on T >= 0, so one Newton step from any T0 >= 0
+// lands at or above the root, and Newton from there decreases monotonically
+// onto it.  T0 is the gas temperature before the step (close to the root
+// when the step changes it little); the first iterate is capped by the
+// bound g / beta.  The iteration stops when an iterate fails to decrease or
 // moves by at most `tol` of itself.  Returns 1 if it did not converge.
-__device__ __forceinline__ int quartic_root(double alpha, double beta, double g, int max_iter,
-                                            double *T_out) {
-  double T = g / beta;
-  if (alpha > 0.0) T = fmin(T, sqrt(sqrt(g / alpha)));
-  bool done = false;
-  int it = 0;
-  while (!done && it < max_iter) {
-    const double T2 = T * T;
-    const double f = fma(alpha * T2, T2, fma(beta, T, -g));
-    const double fp = fma(4.0 * alpha * T2, T, beta);
-    const double Tn = T - f / fp;
-    ++it;
-    if (!(Tn < T)) {
-      done = true;
-    } else {
-      done = (T - Tn <= 1e-15 * T);
-      T = Tn;
-    }
-  }
-  *T_out = T;
-  return done ? 0 : 1;
-}
+__device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
 
-// The same iteration in float for float states (tolerance 1e-7: the root's
-// relative error is then a few float ulps, below the state's own rounding).
-__device__ __forceinline__ int quartic_root(float alpha, float beta, float g, int max_iter,
-                                            float *T_out) {
-  float T = __fdividef(g, beta);
-  if (alpha > 0.0f) T = fminf(T, sqrtf(sqrtf(__fdividef(g, alpha))));
+template <typename T_>
+__device__ __forceinline__ int quartic_root(T_ alpha, T_ beta, T_ g, T_ T0, T_ tol, int max_iter,
+                                            T_ *T_out) {
+  T_ T = T0 > T_(0) ? T0 : T_(0);
+  {
+    const T_ T2 = T * T;
+    const T_ f = fma(alpha * T2, T2, fma(beta, T, -g));
+    const T_ fp = fma(T_(4) * alpha * T2, T, beta);
+    T = fmin(T - qdiv(f, fp), qdiv(g, beta));
+  }
   bool done = false;
   for (int it = 0; it < max_iter && !done; ++it) {
-    const float T2 = T * T;
-    const float f = fmaf(alpha * T2, T2, fmaf(beta, T, -g));
-    const float fp = fmaf(4.0f * alpha * T2, T, beta);
-    const float Tn = T - __fdividef(f, fp);
+    const T_ T2 = T * T;
+    const T_ f = fma(alpha * T2, T2, fma(beta, T, -g));
+    const T_ fp = fma(T_(4) * alpha * T2, T, beta);
+    const T_ Tn = T - qdiv(f, fp);
     if (!(Tn < T)) {
       done = true;
     } else {
-      done = (T - Tn <= 1e-7f * T);
+      done = (T - Tn <= tol * T);
       T = Tn;
     }
   }

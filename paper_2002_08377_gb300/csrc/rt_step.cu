@@ -18,17 +18,17 @@
 // (one wavefront per cache line an instruction touches), so wider per-thread
 // accesses cut the face loop's cost directly.  The float kernel with QuadMap
 // also copies the block's face slots and neighbour indices into shared
-// memory at its start.  Registers are capped so that four blocks share an SM
-// (three for more than 5 pairs per thread).
+// memory at its start.  Registers are capped so that 1024 threads share an
+// SM (768 for more than 5 pairs per thread).
 // Phases:
 //   A  all threads: transport over the cell's faces in slot order (no
 //      atomics, deterministic), comoving weights and the angular sums of
 //      Eq. (Jcom); each cell's 8 lanes reduce with shuffles;
 //   B  the gas temperature quartic: float states solve it in float in all
 //      8 lanes of the cell (no barrier); double states in double with one
-//      lane per cell in warp 0, between two block barriers;
+//      lane per cell in the first CPB / 32 warps, between two block barriers;
 //   C  all threads: new intensities, store, radiation change per cell;
-//   D  after a block barrier, warp 0, one lane per cell: gas energy /
+//   D  after a block barrier, one lane per cell (first CPB / 32 warps): gas energy /
 //      momentum (or tally) update in double (Eqs. gas1, gas2).
 // The double-precision work is lane-per-cell because GB300's FP64 rate is a
 // small fraction of its FP32 rate.
@@ -355,7 +355,8 @@ __device__ __forceinline__ float source_q_float(const StepArgs<float> &a, int64_
 // One block of CPB cells: phases A-D (see the top of the file).  STAGED:
 // the caller has started the copies of the tile's slots and gas records into
 // `stage`, and the face loop waits for them; otherwise slots are read from
-// global memory and warp 0 copies the gas records into `gas` itself.
+// global memory and the lane-per-cell threads copy the gas records into
+// `gas` themselves.
 template <typename R, typename M, bool MOVING, bool STAGED>
 __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t tile, Shared<R> &sh,
                                           SharedGas *gas, const StageView &stage) {
@@ -363,24 +364,26 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   constexpr int PPT = M::PPT;
   const int lc = threadIdx.x / KT;
   const int sub = threadIdx.x % KT;
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t cell = tile * CPB + lc;
   const bool live = cell < a.n_cells;
   const int64_t c = live ? cell : a.n_cells - 1;  // dead lanes shadow the last cell
   const int RS = a.row;  // reals between intensity rows
   const int np = M::count(a.half, sub);
 
-  const int64_t cl = tile * CPB + lane;  // warp 0: lane-per-cell
-  if (!STAGED && warp == 0 && lane < CPB && cl < a.n_cells) {
-    // warp 0 prefetches its cells' gas state for phases B and D
+  // lane-per-cell phases: thread t < CPB (the first CPB / 32 warps) takes cell t
+  const int lp = threadIdx.x;
+  const bool lpc = lp < CPB;
+  const int64_t cl = tile * CPB + lp;
+  if (!STAGED && lpc && cl < a.n_cells) {
+    // prefetch of the cells' gas state for phases B and D
     const char *g = reinterpret_cast<const char *>(a.gs + cl);
     const char *d = reinterpret_cast<const char *>(a.gd + cl);
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      cp_async16(reinterpret_cast<char *>(&gas->gs[lane]) + 16 * k, g + 16 * k);
+      cp_async16(reinterpret_cast<char *>(&gas->gs[lp]) + 16 * k, g + 16 * k);
 #pragma unroll
     for (int k = 0; k < 2; ++k)
-      cp_async16(reinterpret_cast<char *>(&gas->gd[lane]) + 16 * k, d + 16 * k);
+      cp_async16(reinterpret_cast<char *>(&gas->gd[lp]) + 16 * k, d + 16 * k);
   }
 
   // ---------------- phase A: transport, I* = I - dt/V sum_f u I_up
@@ -464,23 +467,23 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
     if (kind == RT_CELL_INTERIOR)
       q = source_q_float(a, c, fkP, fkJ, fkS, fcv, eint, sI, sG, s1, bad);
   } else {
-    // double states: one lane per cell in warp 0, so the FP64 work is issued
+    // double states: one lane per cell, so the FP64 work is issued
     // by one warp for 32 cells
     if (sub == 0) {
       sh.sI[lc] = sI;
       sh.sG[lc] = sG;
       sh.s1[lc] = s1;
     }
-    if (!STAGED && warp == 0) cp_async_wait_all();
+    if (!STAGED && lpc) cp_async_wait_all();
     __syncthreads();
-    if (warp == 0 && lane < CPB) {
+    if (lpc) {
       R ql = 0;
       unsigned bl = 0;
       if (cl < a.n_cells && a.kind[cl] == RT_CELL_INTERIOR)
-        ql = R(source_q(a, gas->gs[lane], gas->gd[lane], (double)sh.sI[lane], (double)sh.sG[lane],
-                        (double)sh.s1[lane], bl));
-      sh.q[lane] = ql;
-      sh.bad[lane] = bl;
+        ql = R(source_q(a, gas->gs[lp], gas->gd[lp], (double)sh.sI[lp], (double)sh.sG[lp],
+                        (double)sh.s1[lp], bl));
+      sh.q[lp] = ql;
+      sh.bad[lp] = bl;
     }
     __syncthreads();
     q = sh.q[lc];
@@ -561,26 +564,26 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
     sh.dF[2][lc] = dfz;
     sh.bad[lc] = bad | nonfinite;
   }
-  if (sizeof(R) == 4 && !STAGED && warp == 0) cp_async_wait_all();
+  if (sizeof(R) == 4 && !STAGED && lpc) cp_async_wait_all();
   __syncthreads();
 
   // ---------------- phase D: gas exchange (Eqs. gas1, gas2), one lane per cell
   const GasStatic *gs_s = STAGED ? stage.gas->gs : gas->gs;
   const GasDyn *gd_s = STAGED ? stage.gas->gd : gas->gd;
-  if (warp == 0 && lane < CPB && cl < a.n_cells) {
+  if (lpc && cl < a.n_cells) {
     // dE_gas = (c/cbar) 4 pi sum w dI, d(rho v) = (4 pi c sum w n dI) / (c cbar)
-    const double dE = a.k_fe * (double)sh.dE[lane];
-    const double dx = a.k_fm * (double)sh.dF[0][lane], dy = a.k_fm * (double)sh.dF[1][lane],
-                 dz = a.k_fm * (double)sh.dF[2][lane];
+    const double dE = a.k_fe * (double)sh.dE[lp];
+    const double dx = a.k_fm * (double)sh.dF[0][lp], dy = a.k_fm * (double)sh.dF[1][lp],
+                 dz = a.k_fm * (double)sh.dF[2][lp];
     if (a.kind[cl] == RT_CELL_INTERIOR) {
-      GasDyn d = gd_s[lane];
+      GasDyn d = gd_s[lp];
       d.e += dE;
       d.mx += dx;
       d.my += dy;
       d.mz += dz;
       a.gd[cl] = d;
       // frame velocity and internal energy for the next step
-      const double ir = gs_s[lane].inv_rho;
+      const double ir = gs_s[lp].inv_rho;
       const double kin = 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * ir;
       store4(a.cellv + 4 * cl, R(d.mx * ir), R(d.my * ir), R(d.mz * ir), R(d.e - kin));
     } else {
@@ -590,7 +593,7 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
       x[2] += dy;
       x[3] += dz;
     }
-    const unsigned bad = sh.bad[lane];
+    const unsigned bad = sh.bad[lp];
     if (bad) {
       atomicOr(a.status, bad);
       atomicMin(a.bad_cell, (unsigned long long)cl);
@@ -598,11 +601,15 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   }
 }
 
-// One block per CPB cells.  Float kernels with up to 5 pairs per thread fit
-// four blocks per SM in registers; wider ones take three, double ones two.
+// Resident threads per SM the register cap aims at: float kernels with up
+// to 5 pairs per thread fit 1024 (64 registers), wider ones 768, double 512.
+template <typename R, int PPT> constexpr int min_blocks() {
+  return (sizeof(R) == 4 ? (PPT <= 5 ? 1024 : 768) : 512) / NT;
+}
+
+// One block per CPB cells.
 template <typename R, typename M, bool MOVING>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (M::PPT <= 5 ? 4 : 3) : 2)
-    step_kernel(const StepArgs<R> a) {
+__global__ void __launch_bounds__(NT, min_blocks<R, M::PPT>()) step_kernel(const StepArgs<R> a) {
   __shared__ Shared<R> sh;
   __shared__ SharedGas gas;
   tile_step<R, M, MOVING, false>(a, blockIdx.x, sh, &gas, StageView{});
@@ -612,7 +619,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (M::PPT <= 5 ? 4 : 3) : 2
 // slots and gas records into shared memory, then loads its own rows and
 // directions while they land (tile_step waits before the face loop).
 template <typename M, bool MOVING>
-__global__ void __launch_bounds__(NT, M::PPT <= 5 ? 4 : 3)
+__global__ void __launch_bounds__(NT, min_blocks<float, M::PPT>())
     step_kernel_staged(const StepArgs<float> a, int cap) {
   __shared__ Shared<float> sh;
   extern __shared__ __align__(128) unsigned char dyn[];

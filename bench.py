@@ -33,20 +33,23 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-angle updates/s (transport+implicit source), FP32 vs FP64, % HBM roofline"
 UNIT = "cell-angle updates/s"
 
-# DRAM bytes (read + write) per launch of the FP32 step kernel, from one ncu
-# capture of the 96^3 case (1021.9 MB) scaled to the 128^3 workload by the
-# cell count (traffic grows with the cells processed); valid while the kernel
-# source has the recorded hash.
-NCU_TRAFFIC = {"fp32": 1021.868544e6 * 2097152 / 884736, "fp64": None}
-NCU_SOURCE_SHA = "89dcf742518a7a53"
+# DRAM bytes (read + write) per launch of the step kernels, from one ncu
+# capture each of the 96^3 case (FP32 963.7 MB, FP64 1888.7 MB) scaled to
+# the 128^3 workload by the cell count (traffic grows with the cells
+# processed); valid while the step kernel's device source has the recorded
+# hash.
+NCU_TRAFFIC = {"fp32": 963.662336e6 * 2097152 / 884736, "fp64": 1888.690456e6 * 2097152 / 884736}
+NCU_SOURCE_SHA = "c3eb1efad9ff0f8c"
 # FP64 arithmetic peak of the GPU (dense FMA, from the hardware's nominal
 # figure); the FP64 state is bound by it, not by HBM.
 FP64_PEAK_GFLOPS = 1250.0
 
 
 def kernel_source_sha():
-    p = os.path.join(ROOT, "paper_2002_08377_gb300", "csrc", "rt_step.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in ("rt_step.cu", "rt_step_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2002_08377_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks():

@@ -63,19 +63,23 @@ def measured_peaks():
 
 def algorithmic_fp64_flops(n_cells, n_faces, n_angles):
     """Floating-point operations the FP64 step must do: per directed face and
-    angle 5 (the flux coefficient n_a . n_f times cbar A_f, shared by an angle
-    and its antipode: 3; the upwind product and sum: 2), per cell and angle 2
+    angle 2 (the upwind product and sum; the flux coefficients n_a . n_f cbar A_f
+    are fixed for the mesh and tabulated once per state), per cell and angle 2
     for the update and 27 for the comoving source step."""
     directed = 2.0 * n_faces
-    return 5.0 * directed * n_angles + 29.0 * n_cells * n_angles
+    return 2.0 * directed * n_angles + 29.0 * n_cells * n_angles
 
 
 def algorithmic_bytes(n_cells, n_faces, n_angles, real_bytes):
     """Bytes the method must move per step: one read and one write of every
     intensity, the per-cell gas state (V, rho, kappa_P, kappa_J, kappa_s, e,
     m, v read: 72 B; e, m written: 32 B) and every undirected face once
-    (two int32 cell ids, A n (3 reals), A w.n (1 real))."""
-    return n_cells * (2 * real_bytes * n_angles + 104) + n_faces * (8 + 4 * real_bytes)
+    (two int32 cell ids, A n (3 reals), A w.n (1 real)).  FP64 states also
+    read their flux-coefficient table: A/2 doubles per directed face."""
+    b = n_cells * (2 * real_bytes * n_angles + 104) + n_faces * (8 + 4 * real_bytes)
+    if real_bytes == 8:
+        b += 2 * n_faces * (n_angles // 2) * 8
+    return b
 
 
 # ---------------------------------------------------------------- clocks

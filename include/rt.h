@@ -31,6 +31,10 @@
  *     by the call that synchronises (rt_step / rt_run / rt_totals / rt_sync).
  *   - The library allocates its device memory in rt_create and frees it in
  *     rt_destroy.  It keeps no pointer to caller memory after a call returns.
+ *     Besides the two intensity buffers (N A reals each) and the mesh, an
+ *     RT_FP64 state holds a table of the flux coefficients, A/2 doubles per
+ *     directed face (8 A/2 x 2 N_faces bytes), so that its steps do not
+ *     recompute them.
  */
 #ifndef RT_GB300_H
 #define RT_GB300_H

@@ -346,6 +346,11 @@ int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state 
   int r = (s->precision == RT_FP32) ? build_device_mesh<float>(s, m, slot_of)
                                     : build_device_mesh<double>(s, m, slot_of);
   if (r != RT_OK) return bail(r);
+  if (s->precision == RT_FP64) {
+    // the FP64 flux-coefficient table: 8 A/2 bytes per directed face
+    const cudaError_t e = rt::build_uface(s);
+    if (e != cudaSuccess) return bail(e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA);
+  }
   // float rows with A = 16 m (32 <= A <= 128) whose blocks' face slots fit
   // the step kernel's shared-memory stage take the quad layout
   s->quad_end = (s->precision == RT_FP32 && A % 16 == 0 && A >= 32 && A <= 128 &&
@@ -752,7 +757,7 @@ void rt_destroy(rt_state *s) {
     if (s->d_adj[k]) cudaFree(s->d_adj[k]);
   if (s->d_adj_ws) cudaFree(s->d_adj_ws);
   if (s->d_adj_stage) cudaFree(s->d_adj_stage);
-  void *bufs[] = {s->d_slot_nb, s->d_wface, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
+  void *bufs[] = {s->d_uface, s->d_slot_nb, s->d_wface, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
                   s->d_gd, s->d_kind, s->d_aux, s->d_bc_row, s->d_I0, s->d_ext, s->d_dir, s->d_wt,
                   s->d_dir64, s->d_wt64, s->d_I[0], s->d_I[1], s->d_status, s->d_bad,
                   s->d_scratch, s->d_out16};

@@ -66,6 +66,7 @@ template <typename R> struct StepArgs {
   const int32_t *nbr;       // [nnz] internal neighbour index
   const typename SlotOf<R>::type *slot;  // [nnz]
   const SlotF *slot_nb;     // [nnz] float static meshes: (s, neighbour index bits)
+  const double *uface;      // [nnz][A/2] double states: flux coefficient of pair p through slot k
   const R *inv_vol;         // [N]
   const double *wface;      // [nnz] A_f w_f . n_f of double slots (moving meshes)
   const GasStatic *gs;      // [N]
@@ -138,6 +139,7 @@ struct rt_state {
 
   void *d_slot = nullptr;
   rt::SlotF *d_slot_nb = nullptr;  // float, static mesh: slot with the neighbour in w
+  double *d_uface = nullptr;  // double: [nnz][A/2] flux coefficients, built once (build_uface)
   double *d_wface = nullptr;  // double states: per-slot A w . n
   void *d_inv_vol = nullptr;
   int64_t *d_cell_of = nullptr;  // internal -> caller
@@ -171,6 +173,8 @@ namespace rt {
 
 // kernel launchers (rt_step.cu)
 cudaError_t launch_step(rt_state *s, double dt);
+// Double states: fills d_uface (allocates it on first use).
+cudaError_t build_uface(rt_state *s);
 
 // auxiliary kernels (rt_aux.cu)
 // caller order <-> internal order; the internal rows are `stride` reals apart

@@ -262,7 +262,8 @@ __device__ __forceinline__ void face_sum_quads(const SlotF *__restrict__ slot,
 // the neighbour index in their w word and nbr is not read.
 template <typename R, typename M, bool MOVING, bool PACKED, typename S, typename K>
 __device__ __forceinline__ void face_sum(const S *__restrict__ slot, const int32_t *__restrict__ nbr,
-                                         const double *__restrict__ wface, K k0, K k1,
+                                         const double *__restrict__ wface,
+                                         const double *__restrict__ uface, int H, K k0, K k1,
                                          const R *__restrict__ I_in, int RS, int sub,
                                          const R (&nx)[M::PPT], const R (&ny)[M::PPT],
                                          const R (&nz)[M::PPT], const R (&Ia)[M::PPT],
@@ -286,9 +287,14 @@ __device__ __forceinline__ void face_sum(const S *__restrict__ slot, const int32
       const R w = MOVING ? slot_w(s, wface, k) : R(0);
 #pragma unroll
       for (int j = 0; j < PPT; ++j)
-        if (M::FULL || j < np)
-          face_pair<R, MOVING>(slot_dot(nx[j], ny[j], nz[j], s), w, vx[j], vy[j], Ia[j], Ib[j],
-                               acca[j], accb[j]);
+        if (M::FULL || j < np) {
+          R d;
+          if constexpr (sizeof(R) == 8)
+            d = uface[(size_t)k * H + M::pair(j, sub)];  // the table built by build_uface
+          else
+            d = slot_dot(nx[j], ny[j], nz[j], s);
+          face_pair<R, MOVING>(d, w, vx[j], vy[j], Ia[j], Ib[j], acca[j], accb[j]);
+        }
     }
   }
 }
@@ -401,11 +407,11 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
     cp_async_wait_all();
     __syncthreads();  // the block's stage has landed
     face_sum<R, M, MOVING, !MOVING>(reinterpret_cast<const typename SlotOf<R>::type *>(stage.slot),
-                                    stage.nbr, a.wface, k0, k1, a.I_in, RS, sub, nx, ny, nz, Ia,
-                                    Ib, acca, accb, np);
+                                    stage.nbr, a.wface, a.uface, a.half, k0, k1, a.I_in, RS, sub,
+                                    nx, ny, nz, Ia, Ib, acca, accb, np);
   } else {
-    face_sum<R, M, MOVING, false>(a.slot, a.nbr, a.wface, a.ptr[c], a.ptr[c + 1], a.I_in, RS, sub,
-                                  nx, ny, nz, Ia, Ib, acca, accb, np);
+    face_sum<R, M, MOVING, false>(a.slot, a.nbr, a.wface, a.uface, a.half, a.ptr[c], a.ptr[c + 1],
+                                  a.I_in, RS, sub, nx, ny, nz, Ia, Ib, acca, accb, np);
   }
   {
     const R dtv = a.dt_r * a.inv_vol[c];
@@ -640,6 +646,7 @@ cudaError_t launch_t(rt_state *s, double dt) {
   a.nbr = s->d_nbr;
   a.slot = reinterpret_cast<const typename SlotOf<R>::type *>(s->d_slot);
   a.slot_nb = s->d_slot_nb;
+  a.uface = s->d_uface;
   a.inv_vol = reinterpret_cast<const R *>(s->d_inv_vol);
   a.wface = s->d_wface;
   a.gs = s->d_gs;
@@ -725,7 +732,36 @@ template <typename R> cudaError_t dispatch(rt_state *s, double dt) {
   return full ? dispatch_pairs<R, false, true>(s, dt) : dispatch_pairs<R, false, false>(s, dt);
 }
 
+// U[k][p] = the double flux coefficient of pair p through directed face k,
+// exactly the expression slot_dot evaluates (cbar A ((n_x n_fx + n_y n_fy) +
+// n_z n_fz), rounded in that order): the mesh is fixed for a state's
+// lifetime, so the FP64 face loop reads it instead of recomputing it.
+__global__ void uface_kernel(const SlotD *__restrict__ slot, const double *__restrict__ dir,
+                             int64_t nnz, int H, double *__restrict__ U) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nnz * H) return;
+  const int64_t k = i / H;
+  const int p = (int)(i % H);
+  U[i] = slot_dot(dir[4 * p], dir[4 * p + 1], dir[4 * p + 2], load_slot<double>(slot + k));
+}
+
 }  // namespace
+
+cudaError_t build_uface(rt_state *s) {
+  const int H = s->n_angles / 2;
+  const size_t n = (size_t)s->nnz * H;
+  if (!s->d_uface) {
+    cudaError_t e = cudaMalloc(&s->d_uface, n * sizeof(double));
+    if (e != cudaSuccess) return e;
+    s->device_bytes += n * sizeof(double);
+  }
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  uface_kernel<<<blocks, 256, 0, s->stream>>>(reinterpret_cast<const SlotD *>(s->d_slot),
+                                              reinterpret_cast<const double *>(s->d_dir), s->nnz, H,
+                                              s->d_uface);
+  s->launches++;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_step(rt_state *s, double dt) {
   cudaError_t e = (s->precision == RT_FP32) ? dispatch<float>(s, dt) : dispatch<double>(s, dt);

@@ -170,17 +170,23 @@ __device__ __forceinline__ int quartic_root(T_ alpha, T_ beta, T_ g, T_ T0, T_ t
   return done ? 0 : 1;
 }
 
+// u > 0, the upwind test.  Double: from the sign and high word of u, on the
+// integer pipe (differs from u > 0 only for |u| below 2^-1042, whose flux is
+// far below rounding).
+__device__ __forceinline__ bool positive(float u) { return u > 0.0f; }
+__device__ __forceinline__ bool positive(double u) { return __double2hiint(u) > 0; }
+
 // One face's contribution to sum_f u I_up for one of the thread's pairs:
 // (vx, vy) the neighbour's (I_p, I_{p+H}), Ia / Ib the cell's own values.
 template <typename R, bool MOVING>
 __device__ __forceinline__ void face_pair(R d, R w, R vx, R vy, R Ia, R Ib, R &acca, R &accb) {
   if (MOVING) {
     const R ua = d - w, ub = -d - w;
-    acca = fma(ua, ua > R(0) ? Ia : vx, acca);
-    accb = fma(ub, ub > R(0) ? Ib : vy, accb);
+    acca = fma(ua, positive(ua) ? Ia : vx, acca);
+    accb = fma(ub, positive(ub) ? Ib : vy, accb);
   } else {
     // u_a = d, u_b = -d: exactly one of the pair takes the neighbour's value
-    const bool out = d > R(0);
+    const bool out = positive(d);
     acca = fma(d, out ? Ia : vx, acca);
     accb = fma(-d, out ? vy : Ib, accb);
   }

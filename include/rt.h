@@ -5,11 +5,11 @@
  * The method is that of Chang, Davis & Jiang, "Time dependent radiation
  * hydrodynamics on a moving mesh": discrete-ordinate intensities I(cell,
  * angle) are transported across the mesh faces by an upwind finite-volume
- * flux (Sec. 3.2) and then updated by an implicit, per-cell source step in
+ * flux (Sec. 2.2) and then updated by an implicit, per-cell source step in
  * the fluid's comoving frame that solves a quartic for the gas temperature
- * and returns the energy and momentum exchange to the gas (Sec. 3.3).
- * Boundary cells relax to a prescribed field (Sec. 3.5) and emitter cells
- * relax to a source intensity (Sec. 3.6).
+ * and returns the energy and momentum exchange to the gas (Sec. 2.3).
+ * Boundary cells relax to a prescribed field (Sec. 2.4) and emitter cells
+ * relax to a source intensity (Sec. 2.5).
  *
  * Conventions shared by every call
  *   - Plain C types only.  Arrays are row-major and, unless a call takes an
@@ -22,7 +22,7 @@
  *   - Units: intensities are energy density per steradian, so an isotropic
  *     equilibrium field is I = a_rad T^4 / (4 pi); E_r = 4 pi sum_a w_a I_a,
  *     F_r = 4 pi c sum_a w_a n_a I_a, P_r = 4 pi sum_a w_a n_a n_a I_a
- *     (Sec. 3.1 moments with sum_a w_a = 1).  The gas has e = total energy
+ *     (Sec. 2.1 moments with sum_a w_a = 1).  The gas has e = total energy
  *     density, m = momentum density, ideal-gas temperature
  *     T = (gamma - 1)(e - |m|^2 / (2 rho)) / (rho r_gas).
  *   - Every call returns an rt_status.  On failure rt_last_error() gives a
@@ -68,14 +68,14 @@ typedef enum {
 } rt_precision;
 
 typedef enum {
-  RT_CELL_INTERIOR = 0, /* transport + implicit gas coupling (Sec. 3.3)       */
-  RT_CELL_BOUNDARY = 1, /* I -> I - (I - I0) min(dt/tau, 1) (Sec. 3.5)         */
+  RT_CELL_INTERIOR = 0, /* transport + implicit gas coupling (Sec. 2.3)       */
+  RT_CELL_BOUNDARY = 1, /* I -> I - (I - I0) min(dt/tau, 1) (Sec. 2.4)         */
   RT_CELL_EMITTER = 2   /* comoving I~ relaxes to I_src at rate cbar*emit_rate
-                           (Sec. 3.6)                                          */
+                           (Sec. 2.5)                                          */
 } rt_cell_kind;
 
 /* Mesh and angle set (Sec. 2: Voronoi cells i with volume V_i, faces with
- * area A_ij, unit normal n_ij pointing from i to j; Sec. 3.2: face velocity
+ * area A_ij, unit normal n_ij pointing from i to j; Sec. 2.2: face velocity
  * w_ij).  All pointers are host pointers, copied by rt_create.
  *   face_cells[f] = (i, j): a face is listed once; i == j is allowed (a cell
  *     meeting its own periodic image).
@@ -106,7 +106,7 @@ typedef struct {
   const double *angle_w;       /* [A]        */
 } rt_mesh_desc;
 
-/* Physical constants and numerics (Sec. 3.1, 3.4).  cbar is the reduced
+/* Physical constants and numerics (Sec. 2.1, 2.3.1).  cbar is the reduced
  * speed of light of the transport, c the true one (enters the gas coupling
  * and the moments).  r_gas = k_B / (mu m_p); c_v = r_gas / (gamma_gas - 1).
  * cfl scales the Courant step dt = cfl * min V^(1/3) / (cbar + |w|).
@@ -128,7 +128,7 @@ typedef struct {
 int rt_create(const rt_mesh_desc *mesh, const rt_params *params, void *stream,
               rt_state **out);
 
-/* Gas state per cell (Sec. 3.3): rho, total energy density e, momentum
+/* Gas state per cell (Sec. 2.3): rho, total energy density e, momentum
  * density m[N][3], Planck / mean / scattering opacities per unit mass.  The
  * frame velocity of a cell's source step is m / rho.  Host pointers, copied.
  * Resets the boundary / emitter tallies. */
@@ -157,7 +157,7 @@ int rt_get_gas(rt_state *s, double *e, double *m, double *ext, int on_device);
  * 1 / max_{c,a} (1/V_c) sum_f max(u_fa, 0).  Either pointer may be NULL. */
 int rt_dt_limits(rt_state *s, double *dt_cfl, double *dt_max);
 
-/* One full step (Sec. 3.2 transport over dt, then the Sec. 3.3 source step
+/* One full step (Sec. 2.2 transport over dt, then the Sec. 2.3 source step
  * over dt): dt <= 0 selects dt_cfl.  Fails with RT_ERR_CFL if dt > dt_max.
  * Synchronises the stream and returns the first per-cell failure, if any
  * (the state then holds the partially failed step). */
@@ -172,12 +172,12 @@ int rt_run(rt_state *s, int32_t n_steps, double dt, double *dt_used);
  * rt_step, rt_run, rt_totals).  dt and the CFL check as for rt_step. */
 int rt_launch(rt_state *s, int32_t n_steps, double dt, double *dt_used);
 
-/* Lab-frame moments (Sec. 3.1 / Eqs. moments energy, moments flux) of the
+/* Lab-frame moments (Sec. 2.1 / Eqs. moments energy, moments flux) of the
  * current intensities, double precision, caller order: E[N], F[N][3],
  * P[N][6] (xx, yy, zz, xy, xz, yz).  Any pointer may be NULL. */
 int rt_moments(rt_state *s, double *E, double *F, double *P, int on_device);
 
-/* Conserved totals (Sec. 3.4), deterministic double-precision sums, host
+/* Conserved totals (Sec. 2.3.1), deterministic double-precision sums, host
  * output out[16]:
  *   0 sum V e, 1 sum V (c/cbar) E_r, 2 sum V ext_e,
  *   3..5 sum V m, 6..8 sum V F_r / (c cbar), 9..11 sum V ext_m,
@@ -208,8 +208,8 @@ int rt_sync(rt_state *s);
  * lam_I1 = dL/dI^{n+1}, lam_e1 = dL/de^{n+1}, lam_m1 = dL/dm^{n+1}, writes
  * lam_I = dL/dI^n, lam_e, lam_m and ADDS dL/dkappa_P and dL/dkappa_J (per
  * cell, per unit mass) into grad_kappa_P, grad_kappa_J.  Transport
- * (Sec. 3.2) is linear, its adjoint the transposed upwind gather; the source
- * (Sec. 3.3) is reversed statement by statement, the quartic's root through
+ * (Sec. 2.2) is linear, its adjoint the transposed upwind gather; the source
+ * (Sec. 2.3) is reversed statement by statement, the quartic's root through
  * the implicit-function theorem.  Boundary / emitter tallies carry no
  * cotangent.  Intensities in the state precision, everything else double,
  * caller order; on_device = 1: all arrays are device pointers.  dt <= 0:

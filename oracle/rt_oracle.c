@@ -17,7 +17,7 @@
  *
  * Every function below is pinned by the CPU tests against something other
  * than itself: closed forms, conservation invariants, brute force on tiny
- * inputs, an mpmath root, and the paper's worked example (Sec. 4.1).
+ * inputs, an mpmath root, and the paper's worked example (Sec. 3.1).
  */
 #include <math.h>
 #include <stdint.h>
@@ -36,7 +36,7 @@ typedef struct {
   int64_t n_cells, n_faces;
   int32_t n_angles;
   int32_t newton_max_iter;
-  /* mesh (Sec. 2, finite-volume charges; Sec. 3.2 transport) */
+  /* mesh (Sec. 2, finite-volume charges; Sec. 2.2 transport) */
   const double *cell_volume;  /* [N] */
   const int32_t *face_cells;  /* [Nf][2] */
   const double *face_area;    /* [Nf] */
@@ -48,9 +48,9 @@ typedef struct {
   const double *wt;           /* [A], sum 1 */
   /* constants */
   double cbar, c, a_rad, gamma_gas, r_gas;
-  /* gas, per cell (Sec. 3.3) */
+  /* gas, per cell (Sec. 2.3) */
   const double *rho, *kappa_P, *kappa_J, *kappa_s;
-  /* boundary / emitter cells (Sec. 3.5, 3.6) */
+  /* boundary / emitter cells (Sec. 2.4, 2.5) */
   const uint8_t *kind;        /* 0 interior, 1 boundary, 2 emitter */
   const double *tau;          /* [N] */
   const double *emit_rate;    /* [N] rho kappa of the emitter */
@@ -60,7 +60,7 @@ typedef struct {
 } orc_problem;
 
 /* ------------------------------------------------------------------------
- * Transport, Sec. 3.2 with the finite-volume update of Eq. (time evolution):
+ * Transport, Sec. 2.2 with the finite-volume update of Eq. (time evolution):
  * the flux through a face moving with velocity w is (cbar n_a - w) . n_f A I
  * and takes I from the upwind side.  Outward flux leaves the cell:
  *   I*_ca = I_ca - dt / V_c * sum_{f in cell c} u_fa I_up,
@@ -119,7 +119,7 @@ void orc_transport(const orc_problem *p, double dt, const double *I, double *Ist
 }
 
 /* Lab-frame moments, Eqs. (moments energy) and (moments flux), with the
- * pressure tensor of Sec. 3.1: E = 4 pi sum w I, F = 4 pi c sum w n I,
+ * pressure tensor of Sec. 2.1: E = 4 pi sum w I, F = 4 pi c sum w n I,
  * P = 4 pi sum w n n I (xx, yy, zz, xy, xz, yz). */
 static void cell_moments(const orc_problem *p, const double *Ic, double *E, double *F) {
   double e = 0, fx = 0, fy = 0, fz = 0;
@@ -224,7 +224,7 @@ int orc_newton(double alpha, double beta, double g, int max_iter, double *T_out,
   return ORC_OK;
 }
 
-/* The same root in closed form (Sec. 3.3 solves the temperature-independent
+/* The same root in closed form (Sec. 2.3 solves the temperature-independent
  * case analytically), by Ferrari's method: with p = beta/alpha, q = g/alpha,
  * T^4 + p T - q = 0 is rewritten (T^2 + y)^2 = 2y (T - p/(4y))^2 where y > 0
  * solves the resolvent cubic y^3 + q y - p^2/8 = 0, so the positive root
@@ -257,7 +257,7 @@ double orc_ferrari(double alpha, double beta, double g) {
 }
 
 /* ------------------------------------------------------------------------
- * Implicit source step of one cell, Sec. 3.3, the four-step algorithm:
+ * Implicit source step of one cell, Sec. 2.3, the four-step algorithm:
  *  1. E^n, F^n of the post-transport intensities (Eqs. moments);
  *  2. to the comoving frame: Gamma_a = 1 - v . n_a / c,
  *     I~_a = Gamma_a^4 I_a (Eq. I lab to com), w~_a = N w_a / Gamma_a^2,
@@ -324,7 +324,7 @@ static int source_interior(const orc_problem *p, int64_t c, double dt, const dou
   return ORC_OK;
 }
 
-/* Boundary cells, Sec. 3.5: I relaxes to I0 with factor min(dt / tau, 1)
+/* Boundary cells, Sec. 2.4: I relaxes to I0 with factor min(dt / tau, 1)
  * (tau <= dt pins I = I0).  The gas of a boundary cell is held fixed; the
  * energy and momentum the radiation loses go to an external tally. */
 static void source_boundary(const orc_problem *p, int64_t c, double dt, const double *Is,
@@ -339,7 +339,7 @@ static void source_boundary(const orc_problem *p, int64_t c, double dt, const do
   for (int k = 0; k < 3; ++k) ext[1 + k] += dF[k] / (p->c * p->cbar);
 }
 
-/* Emitter cells, Sec. 3.6: in the comoving frame I~ relaxes implicitly to
+/* Emitter cells, Sec. 2.5: in the comoving frame I~ relaxes implicitly to
  * I_src at rate Gamma_a cbar (rho kappa)_src:
  *   I~^{n+1} = (I~ + y_a I_src) / (1 + y_a),  y_a = dt cbar Gamma_a emit_rate.
  * The emitter's gas is a fixed reservoir; the exchange goes to the tally. */
@@ -474,7 +474,7 @@ double orc_positivity(const orc_problem *p) {
   return kmax;
 }
 
-/* Conserved totals (Sec. 3.4): with E_g the gas energy and the radiation
+/* Conserved totals (Sec. 2.3.1): with E_g the gas energy and the radiation
  * weighted by c / cbar, E_g + (c/cbar) E_r and rho v + F_r / (c cbar) are
  * conserved; the tallies of boundary / emitter cells close the budget.
  * out[0..2]  sum V e, sum V (c/cbar) E_r, sum V ext_e
@@ -516,7 +516,7 @@ void orc_totals(const orc_problem *p, const double *I, const double *e, const do
  * (no loss depends on them), so they carry no cotangent.
  * --------------------------------------------------------------------- */
 
-/* Transpose of the transport map I* = M I (Sec. 3.2): M is linear in I with
+/* Transpose of the transport map I* = M I (Sec. 2.2): M is linear in I with
  * M_cc,a = 1 - dt/V_c sum_f max(u_fa, 0) and M_c,nbr,a = -dt/V_c u_fa for
  * the faces where u_fa < 0.  A face outflow of cell j (u_jfa > 0) is the
  * inflow of its neighbour through the same face, so

@@ -1,7 +1,7 @@
 """GB300-native reduced-speed-of-light radiative transfer on Voronoi meshes.
 
-The hot path (upwind transport + implicit comoving source step, Sec. 3.2 and
-3.3 of Chang, Davis & Jiang) runs in the CUDA library librt_gb300.so behind
+The hot path (upwind transport + implicit comoving source step, Sec. 2.2 and
+2.3 of Chang, Davis & Jiang) runs in the CUDA library librt_gb300.so behind
 the C ABI of include/rt.h; this package holds its Python binding
 (capi, solver), the build step and the seeded input generators (inputs).
 Importing the package does not load the CUDA library.

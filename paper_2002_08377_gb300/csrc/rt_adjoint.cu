@@ -1,5 +1,5 @@
-// Discrete adjoint of one radiation step (transport, Sec. 3.2, then the
-// implicit comoving source, Sec. 3.3), for gradients of a scalar loss with
+// Discrete adjoint of one radiation step (transport, Sec. 2.2, then the
+// implicit comoving source, Sec. 2.3), for gradients of a scalar loss with
 // respect to the per-cell absorption opacities and the initial intensities.
 //
 //   I*  = M I^n                       (linear upwind transport)

@@ -1,5 +1,5 @@
 // Auxiliary kernels: caller<->internal cell order, the upwind positivity
-// bound, lab-frame moments (Sec. 3.1), conserved totals (Sec. 3.4) and the
+// bound, lab-frame moments (Sec. 2.1), conserved totals (Sec. 2.3.1) and the
 // gas read-back.  None of these is on the per-step hot path.
 #include <cuda_runtime.h>
 

@@ -1,6 +1,6 @@
-// Fused radiation step: upwind transport (Sec. 3.2) + implicit comoving
-// source update with gas exchange (Sec. 3.3), boundary cells (Sec. 3.5) and
-// emitter cells (Sec. 3.6), one kernel per step.
+// Fused radiation step: upwind transport (Sec. 2.2) + implicit comoving
+// source update with gas exchange (Sec. 2.3), boundary cells (Sec. 2.4) and
+// emitter cells (Sec. 2.5), one kernel per step.
 //
 // Layout: the intensity row of a cell stores the A/2 antipodal pairs
 // (angle p, angle p + A/2) side by side.  The flux coefficient of the
@@ -502,7 +502,7 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   {
     // boundary: I' = I* - (I* - I0) f; interior: I~' = (I~ + q Gamma) / (1 + x Gamma),
     // i.e. I' = (I* + q / Gamma^3) / (1 + x Gamma); emitter: the same with
-    // x -> dt cbar (rho kappa)_src and q -> that rate times I_src (Sec. 3.6)
+    // x -> dt cbar (rho kappa)_src and q -> that rate times I_src (Sec. 2.5)
     R na[PPT], nb[PPT];
     if (kind == RT_CELL_BOUNDARY) {
       const double2 ax = a.aux[c];

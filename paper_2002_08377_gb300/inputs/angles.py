@@ -1,7 +1,7 @@
 """Discrete-ordinate angle sets (an input of the radiation step).
 
 The transport state is one intensity per cell per direction n_hat_a with
-solid-angle weight w_a, sum_a w_a = 1 (Sec. 3, moment quadrature; Sec. 3.3,
+solid-angle weight w_a, sum_a w_a = 1 (Sec. 2, moment quadrature; Sec. 2.3,
 comoving weights normalised to one).  The paper uses 80 angles for its beam
 tests and one angle per octant for the diffusion and wave tests, without
 naming the quadrature.  These sets are level-symmetric S_N sets with equal

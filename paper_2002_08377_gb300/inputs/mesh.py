@@ -1,7 +1,7 @@
 """Jittered-lattice periodic Voronoi meshes (host input of the radiation step).
 
 Mesh-generating points are lattice sites plus a seeded uniform jitter
-(Sec. 4.3 and 4.6 perturb a regular lattice the same way).  The tessellation
+(Sec. 3.3 and 3.6 perturb a regular lattice the same way).  The tessellation
 is computed by the native builder in voronoi.cpp.
 """
 import ctypes

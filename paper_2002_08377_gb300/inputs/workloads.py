@@ -1,4 +1,4 @@
-"""The five synthetic workloads, shaped like the paper's test problems (Sec. 4).
+"""The five synthetic workloads, shaped like the paper's test problems (Sec. 3).
 
 Every workload is a jittered periodic Voronoi box (unit box, lattice spacing
 h = 1/n, jitter U(-0.25, 0.25) h per axis, seed = workload number unless
@@ -8,25 +8,25 @@ e_internal = rho T / (gamma - 1).
 
   thermal    16^3, S6 (48), rho = 1, T = 1, E_r = 10 a T^4 isotropic,
              kappa_P = kappa_J = 1, kappa_s = 0, v = 0, cbar = c = 100,
-             CFL 0.3, 100 steps (Sec. 4.1, thermal equilibrium).
+             CFL 0.3, 100 steps (Sec. 3.1, thermal equilibrium).
   shadows    128^3, S8 (80), kappa_a = 1e-3 background with three opaque
              spheres (r = 0.08, kappa_a = 1e3), four isotropic emitter
              cells, absorbing boundary layers on all six sides, two
              collimated beams entering through the -y layer at +-30 deg,
-             cbar = c = 1e3, 200 steps (Sec. 4.4 and 4.5).
+             cbar = c = 1e3, 200 steps (Sec. 3.4 and 3.5).
   diffusion  100^3, S6, mesh and gas moving with v = w = (0.3, 0, 0),
              cell optical depth kappa_a h log-uniform in [10, 1000],
              kappa_s = kappa_a, Gaussian E_r (sigma = 0.05) on T = 1,
-             cbar = c = 1e3, 300 steps (Sec. 4.3).
+             cbar = c = 1e3, 300 steps (Sec. 3.3).
   adjoint    64^3, S6, log-normal kappa_a (Gaussian random field, sigma 1,
              correlation length 0.1), absorbing layers at +-x, one
              emitter, cbar = c = 1, 64 steps.
   waves      256^3, S8, rho = 1, T = 1, E_r = 1, cell optical depth 1,
              cbar = 100, c = 1e4, small sinusoidal perturbation of T and
-             E_r along x, 50 steps (Sec. 4.6 with the hydro frozen).
+             E_r along x, 50 steps (Sec. 3.6 with the hydro frozen).
 
-Boundary cells (kind 1) relax to a per-direction I0 (Sec. 3.5); emitter
-cells (kind 2) relax to I_src at rate cbar * emit_rate (Sec. 3.6).  I0 is
+Boundary cells (kind 1) relax to a per-direction I0 (Sec. 2.4); emitter
+cells (kind 2) relax to I_src at rate cbar * emit_rate (Sec. 2.5).  I0 is
 stored as a few shared rows; bc_row[c] selects the row of cell c.
 """
 from dataclasses import dataclass, field

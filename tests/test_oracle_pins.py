@@ -127,7 +127,7 @@ def test_newton_reports_nonconvergence():
 @pytest.mark.parametrize("w", [None, (0.3, -0.2, 0.1)])
 def test_transport_is_donor_cell_on_cubic_lattice(w):
     """On an unjittered lattice the Voronoi faces are the cube faces and the
-    upwind flux of Sec. 3.2 is the textbook donor-cell scheme."""
+    upwind flux of Sec. 2.2 is the textbook donor-cell scheme."""
     n = (5, 4, 6)
     prob = make(n=n, order=4, jitter=0.0, w=w, cbar=2.0)
     rng = np.random.default_rng(2)
@@ -170,7 +170,7 @@ def test_transport_invariants_jittered():
 
 
 def test_crossing_beams_superpose():
-    """Sec. 4.4: with no opacity and no motion the source step is the
+    """Sec. 3.4: with no opacity and no motion the source step is the
     identity, so each ordinate is transported independently: a beam's
     channel is bit-identical with and without the other beam."""
     from paper_2002_08377_gb300.inputs import shadows
@@ -201,7 +201,7 @@ def test_crossing_beams_superpose():
 
 # ---------------------------------------------------------------- source (P1, P2, P4)
 def _scalar_recurrence(steps, dt, rho, kP, kJ, T, J, cbar, c, a, rcv, mp):
-    """Sec. 3.3 for an isotropic field at rest: the per-angle update collapses
+    """Sec. 2.3 for an isotropic field at rest: the per-angle update collapses
     to J' = (J + x_P B(T')) / (1 + x_J), rho c_v (T' - T) = dt c rho (4 pi kJ
     J' - kP a T'^4); each step is solved with mpmath's root finder."""
     out = []
@@ -219,7 +219,7 @@ def _scalar_recurrence(steps, dt, rho, kP, kJ, T, J, cbar, c, a, rcv, mp):
 
 @pytest.mark.parametrize("kS", [0.0, 3.0])
 def test_thermal_relaxation_matches_scalar_recurrence(kS):
-    """Uniform medium (the thermal equilibrium test, Sec. 4.1): the oracle's
+    """Uniform medium (the thermal equilibrium test, Sec. 3.1): the oracle's
     cells follow the scalar recurrence to 1e-12; isotropic scattering has no
     effect on an isotropic field at rest."""
     mp = pytest.importorskip("mpmath")
@@ -278,7 +278,7 @@ def _read_golden(name):
 
 
 def test_paper_worked_example_equilibrium_temperature():
-    """Sec. 4.1: atomic hydrogen at rho = 1e-15 g/cc, T_gas = 10 K, radiation
+    """Sec. 3.1: atomic hydrogen at rho = 1e-15 g/cc, T_gas = 10 K, radiation
     at 200 K, cbar = c, equilibrates at 101.7 K (printed value).  CGS
     constants (mu = 1, gamma = 5/3, m_p) give 101.33 K from the energy
     balance; the paper's constants are unstated, so the printed value is
@@ -357,7 +357,7 @@ def test_implicit_source_converges_to_subcycled_explicit(vscale):
 
 # ---------------------------------------------------------------- conservation (P3)
 def test_energy_momentum_conserved_to_roundoff():
-    """Sec. 3.4: E_gas + (c/cbar) E_r and rho v + F_r/(c cbar) are conserved,
+    """Sec. 2.3.1: E_gas + (c/cbar) E_r and rho v + F_r/(c cbar) are conserved,
     with the boundary / emitter tallies closing the budget; c != cbar,
     moving cells, scattering and a moving mesh all included."""
     prob = randomise(make(n=(4, 3, 5), order=6, cbar=10.0, c=100.0, w=(0.3, 0.1, 0.0)), seed=9)
@@ -373,7 +373,7 @@ def test_energy_momentum_conserved_to_roundoff():
 
 
 def test_momentum_transfer_beamed_radiation():
-    """Sec. 4.2: only rays with cos(theta) >= 0.8 to +x populated; the gas
+    """Sec. 3.2: only rays with cos(theta) >= 0.8 to +x populated; the gas
     picks up +x momentum and total momentum is conserved (the paper shows
     4e-4; the discrete scheme conserves it to round-off)."""
     d, _ = level_symmetric(6)
@@ -391,7 +391,7 @@ def test_momentum_transfer_beamed_radiation():
 
 
 def test_shadow_behind_opaque_sphere():
-    """Sec. 4.5: a beam from the -y layer is stopped by an opaque sphere;
+    """Sec. 3.5: a beam from the -y layer is stopped by an opaque sphere;
     cells in its geometric shadow stay dark while cells in the beam before
     the sphere are lit."""
     from paper_2002_08377_gb300.inputs import shadows
@@ -422,3 +422,59 @@ def test_shadow_behind_opaque_sphere():
     # umbra; the shadow is still darker than the beam by a factor > 50
     assert E[dark].max() < 2e-2 * E[lit].mean()
     assert E[dark].max() > 0.0
+
+
+# ---------------------------------------------------------------- diffusion limit
+def _diffusion_gaussian_error(N, v, chi=125.0, dx=0.08, rho0=1e6):
+    """Sec. 3.3 setup, first-order scheme: a quasi-1-D periodic box (N x 3 x 3
+    cubic cells, lattice jitter 1e-6 of the spacing), one angle per octant,
+    a scattering medium of total opacity rho kappa_s = chi, c = cbar, the gas
+    heavy enough (rho = 1e6) that radiation neither accelerates nor heats it
+    (the paper does not evolve the hydrodynamics), flow and mesh at v = w.
+    The radiation starts isotropic in the comoving frame with
+    E_r = exp(-x^2/dx^2) + exp(-10) (the paper's floor) and runs until the
+    diffusion solution of Eq. (diff analytic), D = cbar / (3 chi), has
+    doubled its variance.  Returns the L1 error of E_r relative to the
+    Gaussian's own L1 norm, in the mesh frame (cells move with w = v)."""
+    from paper_2002_08377_gb300.inputs import Problem
+    h = 1.0 / N
+    mesh = build_mesh((N, 3, 3), box=(1.0, 3 * h, 3 * h), jitter=1e-6, seed=5)
+    mesh.face_w = np.ascontiguousarray(np.tile([v, 0.0, 0.0], (mesh.n_faces, 1)))
+    dirs, wt = level_symmetric(2)
+    n, A = mesh.n_cells, dirs.shape[0]
+    x = mesh.cell_centroid[:, 0] - 0.5
+    E0 = np.exp(-x ** 2 / dx ** 2) + np.exp(-10.0)
+    rho = np.full(n, rho0)
+    vel = np.zeros((n, 3))
+    vel[:, 0] = v
+    m = rho[:, None] * vel
+    e = rho * 1.5 + 0.5 * rho * v * v  # T = 1, gamma = 5/3
+    z = np.zeros(n)
+    gamma = 1.0 - dirs[:, 0] * v  # c = 1
+    prob = Problem("diffusion-gaussian", mesh, dirs, wt, 1.0, 1.0, 1.0, 5.0 / 3.0, 1.0, 0.3, 0,
+                   rho, e, m, z.copy(), z.copy(), np.full(n, chi / rho0), np.zeros(n, np.uint8),
+                   z.copy(), z.copy(), z.copy(), np.full(n, -1, np.int32), np.zeros((1, A)),
+                   E0 / (4 * np.pi), 1.0 / gamma ** 4)
+    o = oracle.Oracle(prob)
+    D = 1.0 / (3.0 * chi)
+    t_end = dx ** 2 / (4.0 * D)
+    steps = int(np.ceil(t_end / o.cfl_dt()))
+    assert o.run(steps, t_end / steps) == 0
+    E = o.moments()[0]
+    s = 1.0 + 4.0 * D * t_end / dx ** 2
+    Ea = np.exp(-x ** 2 / (dx ** 2 * s)) / np.sqrt(s) + np.exp(-10.0)
+    return np.sum(np.abs(E - Ea)) / np.sum(Ea - np.exp(-10.0))
+
+
+@pytest.mark.parametrize("v", [0.0, 0.1])
+def test_diffusion_gaussian_converges_at_first_order(v):
+    """Sec. 3.3 (dynamic diffusion) with Eq. (diff analytic): in an optically
+    thick scattering medium (cell optical depth 1 to 0.25) the piecewise-
+    constant upwind step plus the implicit source converges to the diffusion
+    solution at first order in the cell size, static or moving with the
+    flow (Sec. 3.6 states first-order convergence of the method)."""
+    errs = [_diffusion_gaussian_error(N, v) for N in (128, 256, 512)]
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert errs[0] > errs[1] > errs[2], errs
+    assert np.all((orders > 0.75) & (orders < 1.3)), (errs, orders)
+    assert errs[2] < 0.06, errs

@@ -478,3 +478,87 @@ def test_diffusion_gaussian_converges_at_first_order(v):
     assert errs[0] > errs[1] > errs[2], errs
     assert np.all((orders > 0.75) & (orders < 1.3)), (errs, orders)
     assert errs[2] < 0.06, errs
+
+
+# ---------------------------------------------------------------- linear modes
+def _linear_system(dirs, wt, k, cbar, c, chi, rcv, a=1.0, T=1.0):
+    """The radiation-thermal equations linearised about rest and equilibrium
+    (I = aT^4/4pi isotropic, v = 0) for a perturbation exp(ikx), continuous in
+    space and time: per angle
+      d dI_a/dt = -i k cbar n_ax dI_a + cbar chi (4aT^3/4pi dT - dI_a),
+    and for the gas (rho c_v) d dT/dt = c chi (4pi dJ - 4aT^3 dT), dJ = sum w dI
+    (Eqs. time evolution, com radiative source, tgas with kappa_P = kappa_J,
+    kappa_s = 0).  Returns the (A+1) x (A+1) matrix."""
+    A = len(wt)
+    M = np.zeros((A + 1, A + 1), complex)
+    M[np.arange(A), np.arange(A)] = -1j * k * cbar * dirs[:, 0] - cbar * chi
+    M[:A, A] = cbar * chi * 4 * a * T ** 3 / (4 * np.pi)
+    M[A, :A] = (c / rcv) * 4 * np.pi * chi * wt
+    M[A, A] = -(c / rcv) * chi * 4 * a * T ** 3
+    return M
+
+
+def _measured_mode(N, chi, cbar=1.0, c=100.0, amp=1e-6):
+    """Sec. 3.6 setup with the hydrodynamics frozen: a quasi-1-D periodic box
+    (N x 3 x 3 cells, lattice jitter 10 % of the spacing), one angle per
+    octant, k = 2 pi / L_x, cbar = c / 100, P_rad of the order of P_gas.  The
+    gas is made inertially heavy (rho = 1e8) with its heat capacity kept
+    (rho c_v = 1.5 through r_gas = 1e-8) and rho kappa = chi, so radiation
+    cannot move it (the paper fixes the flow for the radiation part).  The
+    slowest-decaying eigenvector of the linear system with an E_r component
+    is laid on the mesh at amplitude 1e-6; the oracle's E_r Fourier
+    coefficient at k gives the measured rate lambda = log(c2/c1)/(t2 - t1)."""
+    from paper_2002_08377_gb300.inputs import Problem
+    h = 1.0 / N
+    mesh = build_mesh((N, 3, 3), box=(1.0, 3 * h, 3 * h), jitter=0.1, seed=5)
+    dirs, wt = level_symmetric(2)
+    n, A = mesh.n_cells, dirs.shape[0]
+    rho0, r_gas = 1e8, 1e-8
+    rcv = rho0 * r_gas / (2.0 / 3.0)
+    k = 2 * np.pi
+    lam, vec = np.linalg.eig(_linear_system(dirs, wt, k, cbar, c, chi, rcv))
+    with_E = np.abs(vec[:A].T @ wt) > 1e-3 * np.abs(vec[:A].T @ wt).max()
+    j = np.flatnonzero(with_E)[np.argmax(lam[with_E].real)]
+    v = vec[:, j] / (4 * np.pi * (vec[:A, j] @ wt))  # unit E_r amplitude
+    x = mesh.cell_centroid[:, 0]
+    ph = np.exp(1j * k * x)
+    I = 1 / (4 * np.pi) + amp * np.real(np.outer(ph, v[:A]))
+    T = 1.0 + amp * np.real(ph * v[A])
+    z = np.zeros(n)
+    rho = np.full(n, rho0)
+    prob = Problem("linear-mode", mesh, dirs, wt, cbar, c, 1.0, 5.0 / 3.0, r_gas, 0.3, 0, rho,
+                   rho * r_gas * T / (2.0 / 3.0), np.zeros((n, 3)), np.full(n, chi / rho0),
+                   np.full(n, chi / rho0), z.copy(), np.zeros(n, np.uint8), z.copy(), z.copy(),
+                   z.copy(), np.full(n, -1, np.int32), np.zeros((1, A)), np.full(n, 1 / (4 * np.pi)),
+                   np.ones(A))
+    prob.initial_intensity = lambda dtype=np.float64, _I=I: np.ascontiguousarray(_I.astype(dtype))
+    o = oracle.Oracle(prob)
+    V = mesh.cell_volume
+
+    def coefficient():
+        return np.sum(V * (o.moments()[0] - 1.0) * np.conj(ph)) / np.sum(V)
+
+    t_end = min(1.0, 2.0 / abs(lam[j].real))
+    steps = int(np.ceil(t_end / o.cfl_dt()))
+    dt = t_end / steps
+    n1 = steps // 4  # let the other (fast) discrete modes die out first
+    assert o.run(n1, dt) == 0
+    c1 = coefficient()
+    assert o.run(steps - n1, dt) == 0
+    return lam[j], np.log(coefficient() / c1) / ((steps - n1) * dt)
+
+
+@pytest.mark.parametrize("chi", [1.0, 10.0])
+def test_linear_radiation_thermal_mode_converges_at_first_order(chi):
+    """Sec. 3.6 (linear wave, reading: radiation-thermal part with the flow
+    frozen): the decay rate and phase speed of the slowest E_r mode converge
+    to the eigenvalue of the linearised equations at first order in the cell
+    size -- a propagating, damped mode at optical depth 1 per wavelength
+    (chi = 1) and a diffusive one at optical depth 10."""
+    errs = []
+    for N in (32, 64, 128):
+        lam, measured = _measured_mode(N, chi)
+        errs.append(abs(measured - lam) / abs(lam))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all((orders > 0.8) & (orders < 1.25)), (errs, orders)
+    assert errs[-1] < 0.08, errs

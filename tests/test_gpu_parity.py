@@ -193,6 +193,61 @@ def test_shadows_full_size_one_step():
         g.close()
 
 
+def _sampled_step_parity(prob, precision, n_ranges=6, width=2048, seed=0):
+    """One step at full size in the benchmark's launch configuration: the
+    GPU steps the whole mesh, the oracle steps only `n_ranges` random cell
+    ranges of `width` cells (transport of those cells from the full state,
+    then their source update), and the two are compared on those cells."""
+    o = oracle.Oracle(prob)
+    dt = o.cfl_dt()
+    N = prob.n_cells
+    rng = np.random.default_rng(seed)
+    starts = np.sort(rng.choice(N - width, n_ranges, replace=False))
+    out = np.empty_like(o.I)
+    for c0 in starts:
+        st, _ = o.sample_step(dt, int(c0), int(c0) + width, out)
+        assert st == 0
+    g = solver(prob, precision)
+    g.step(dt)
+    I = g.get_intensity()
+    e, m, _ = g.gas()
+    g.close()
+    w4 = 4 * np.pi * prob.weights
+    for c0 in starts:
+        sl = slice(int(c0), int(c0) + width)
+        if precision == "fp64":
+            assert rel_err(I[sl], out[sl]) < FP64_REL
+            assert rel_err(e[sl], o.e[sl]) < FP64_REL
+        else:
+            E_g = I[sl].astype(np.float64) @ w4
+            E_o = out[sl] @ w4
+            assert l1_rel(E_g, E_o) < FP32_L1
+            assert l1_rel(e[sl], o.e[sl]) < FP32_L1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_diffusion_full_size_sampled(precision):
+    """Dynamic-diffusion workload at its full size (100^3 cells, 48 angles,
+    moving mesh and gas, stiff cells): one step, sampled cell ranges."""
+    _sampled_step_parity(diffusion(), precision)
+
+
+def test_waves_full_size_sampled_fp32():
+    """Linear-wave workload at its full size (256^3 = 16.8M cells, 80 angles,
+    FP32 intensities as that workload specifies): one step, sampled ranges.
+    The oracle holds the state in double on the host (about 32 GB); the
+    test skips, with the reason, on a host with less than 64 GB available."""
+    need = 64 << 30
+    avail = 0
+    with open("/proc/meminfo") as f:
+        for line in f:
+            if line.startswith("MemAvailable:"):
+                avail = int(line.split()[1]) << 10
+    if avail < need:
+        pytest.skip(f"host has {avail >> 30} GB available, this test needs 64 GB (oracle state in double plus the host copies)")
+    _sampled_step_parity(waves(), "fp32", n_ranges=4, width=4096)
+
+
 # ------------------------------------------------------------------ behaviour
 def test_bitwise_deterministic():
     prob = randomise(make(n=(8, 8, 8), order=8, cbar=10.0, c=100.0), seed=12)

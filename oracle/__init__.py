@@ -49,7 +49,8 @@ class _Problem(ctypes.Structure):
                 ("kappa_J", ctypes.c_void_p), ("kappa_s", ctypes.c_void_p),
                 ("kind", ctypes.c_void_p), ("tau", ctypes.c_void_p),
                 ("emit_rate", ctypes.c_void_p), ("I_src", ctypes.c_void_p),
-                ("bc_row", ctypes.c_void_p), ("I0", ctypes.c_void_p)]
+                ("bc_row", ctypes.c_void_p), ("I0", ctypes.c_void_p),
+                ("face_offset", ctypes.c_void_p)]
 
 
 def lib():
@@ -79,6 +80,10 @@ def lib():
         L.orc_transport_adjoint.argtypes = [P, d, vp, vp]
         L.orc_adjoint_step.argtypes = [P, d] + [vp] * 12
         L.orc_adjoint_step.restype = i
+        L.orc_gradient.argtypes = [P, vp, i, vp]
+        L.orc_transport_recon.argtypes = [P, d, vp, vp, vp, vp]
+        L.orc_step_vl.argtypes = [P, d, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(i)]
+        L.orc_step_vl.restype = i
         _lib = L
     return _lib
 
@@ -145,7 +150,9 @@ class Oracle:
         p.I_src = arr("isrc", prob.I_src)
         p.bc_row = arr("bcrow", prob.bc_row, np.int32)
         p.I0 = arr("I0", prob.I0)
+        p.face_offset = arr("foff", m.face_offset())
         self.p = p
+        self.integrator = int(getattr(prob, "integrator", 0))
         self.I = _f64(prob.initial_intensity(np.float64))
         self.e = _f64(prob.e).copy()
         self.m = _f64(prob.m).copy()
@@ -172,7 +179,19 @@ class Oracle:
 
     # -- full steps ----------------------------------------------------------
     def step(self, dt):
+        """One step with the problem's integrator (first-order upwind, or
+        van Leer with limited linear reconstruction)."""
         it = ctypes.c_int()
+        if self.integrator == 1:
+            if not hasattr(self, "_half"):
+                self._half = np.empty_like(self.I)
+                self._grad = np.empty((self.N, 3, self.A))
+            st = lib().orc_step_vl(ctypes.byref(self.p), float(dt), self.I.ctypes.data,
+                                   self.work.ctypes.data, self._half.ctypes.data,
+                                   self._grad.ctypes.data, self.e.ctypes.data, self.m.ctypes.data,
+                                   self.ext.ctypes.data, ctypes.byref(it))
+            self.last_iters = it.value
+            return st
         st = lib().orc_step(ctypes.byref(self.p), float(dt), self.I.ctypes.data,
                             self.work.ctypes.data, self.e.ctypes.data, self.m.ctypes.data,
                             self.ext.ctypes.data, ctypes.byref(it))
@@ -197,6 +216,22 @@ class Oracle:
         return ORC_OK
 
     # -- diagnostics -----------------------------------------------------------
+    def gradient(self, I=None, limit=True):
+        """[N, 3, A] least-squares gradients of I (Barth-Jespersen limited)."""
+        I = self.I if I is None else _f64(I)
+        g = np.empty((self.N, 3, self.A))
+        lib().orc_gradient(ctypes.byref(self.p), I.ctypes.data, int(bool(limit)), g.ctypes.data)
+        return g
+
+    def transport_recon(self, dt, I, Ih, grad):
+        """Transport of I over dt with upwind face values reconstructed from
+        (Ih, grad)."""
+        I, Ih, grad = _f64(I), _f64(Ih), _f64(grad)
+        out = np.empty_like(I)
+        lib().orc_transport_recon(ctypes.byref(self.p), float(dt), I.ctypes.data, Ih.ctypes.data,
+                                  grad.ctypes.data, out.ctypes.data)
+        return out
+
     def moments(self, I=None):
         I = self.I if I is None else _f64(I)
         E = np.empty(self.N)

@@ -17,7 +17,10 @@
  *
  * Every function below is pinned by the CPU tests against something other
  * than itself: closed forms, conservation invariants, brute force on tiny
- * inputs, an mpmath root, and the paper's worked example (Sec. 3.1).
+ * inputs, an mpmath root, the paper's worked example (Sec. 3.1), the
+ * diffusion and linear-mode limits (Sec. 3.3, 3.6), geometry identities and
+ * exactness on linear fields (the gradient), and orders of accuracy (the
+ * van Leer step).
  */
 #include <math.h>
 #include <stdint.h>
@@ -57,6 +60,10 @@ typedef struct {
   const double *I_src;        /* [N] */
   const int32_t *bc_row;      /* [N] */
   const double *I0;           /* [rows][A] */
+  /* linear reconstruction: face f = (i, j) -> (x_f - x_i, x_f - x_j'), the
+   * face centroid relative to each cell's centroid, j' the image of j that
+   * meets i across f; [Nf][2][3], may be NULL when no reconstruction is used */
+  const double *face_offset;
 } orc_problem;
 
 /* ------------------------------------------------------------------------
@@ -718,4 +725,165 @@ int orc_adjoint_step(const orc_problem *p, double dt, const double *I, const dou
   }
   orc_transport_adjoint(p, dt, lIs, lI);
   return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------
+ * Limited linear reconstruction and the van Leer two-stage step (Sec. 2,
+ * the integration steps with the "van Leer method"; Sec. 2.2, transport
+ * step 2: the state at the face centre by linear reconstruction with a
+ * limiter).  The paper defers the gradient estimate and the limiter to its
+ * hydrodynamics code; this oracle takes (readings):
+ *   gradient g of I_a in cell c: least squares over the face neighbours,
+ *     minimising sum_f w_f (I_j - I_c - g . r_f)^2 with r_f = x_j' - x_c
+ *     (centroid of the neighbour's image across f) and w_f = A_f / |r_f|^2,
+ *     i.e. g = M^-1 b, M = sum_f w_f r_f r_f^T, b = sum_f w_f r_f (I_j - I_c);
+ *     exact for a linear field;
+ *   limiter (Barth-Jespersen): g <- alpha g, alpha the largest value in
+ *     [0, 1] keeping I_c + g . (x_f - x_c) within [min, max] of I_c and its
+ *     face neighbours on every face of c.
+ * --------------------------------------------------------------------- */
+static inline void face_offsets(const orc_problem *p, int32_t e, const double **d_own,
+                                const double **d_nbr) {
+  const int64_t f = e >= 0 ? e : -(int64_t)e - 1;
+  const double *o = p->face_offset + 6 * f;
+  *d_own = e >= 0 ? o : o + 3;
+  *d_nbr = e >= 0 ? o + 3 : o;
+}
+
+/* grad[(c * 3 + d) * A + a] = d-th component of the (limited, if limit)
+ * gradient of I_a in cell c. */
+void orc_gradient(const orc_problem *p, const double *I, int limit, double *grad) {
+  const int A = p->n_angles;
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < p->n_cells; ++c) {
+    double M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int64_t k = p->cell_face_ptr[c]; k < p->cell_face_ptr[c + 1]; ++k) {
+      const double *d_own, *d_nbr;
+      face_offsets(p, p->cell_face_idx[k], &d_own, &d_nbr);
+      int64_t f, nbr;
+      double sgn;
+      face_side(p, c, p->cell_face_idx[k], &f, &sgn, &nbr);
+      double r[3] = {d_own[0] - d_nbr[0], d_own[1] - d_nbr[1], d_own[2] - d_nbr[2]};
+      double w = p->face_area[f] / (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+      for (int x = 0; x < 3; ++x)
+        for (int y = 0; y < 3; ++y) M[x][y] += w * r[x] * r[y];
+    }
+    /* inverse of the symmetric 3x3 matrix by cofactors */
+    double C[3][3];
+    C[0][0] = M[1][1] * M[2][2] - M[1][2] * M[2][1];
+    C[0][1] = M[0][2] * M[2][1] - M[0][1] * M[2][2];
+    C[0][2] = M[0][1] * M[1][2] - M[0][2] * M[1][1];
+    C[1][0] = M[1][2] * M[2][0] - M[1][0] * M[2][2];
+    C[1][1] = M[0][0] * M[2][2] - M[0][2] * M[2][0];
+    C[1][2] = M[0][2] * M[1][0] - M[0][0] * M[1][2];
+    C[2][0] = M[1][0] * M[2][1] - M[1][1] * M[2][0];
+    C[2][1] = M[0][1] * M[2][0] - M[0][0] * M[2][1];
+    C[2][2] = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+    const double det = M[0][0] * C[0][0] + M[0][1] * C[1][0] + M[0][2] * C[2][0];
+    for (int a = 0; a < A; ++a) {
+      const double Ic = I[c * A + a];
+      double b[3] = {0, 0, 0}, lo = Ic, hi = Ic;
+      for (int64_t k = p->cell_face_ptr[c]; k < p->cell_face_ptr[c + 1]; ++k) {
+        const double *d_own, *d_nbr;
+        face_offsets(p, p->cell_face_idx[k], &d_own, &d_nbr);
+        int64_t f, nbr;
+        double sgn;
+        face_side(p, c, p->cell_face_idx[k], &f, &sgn, &nbr);
+        double r[3] = {d_own[0] - d_nbr[0], d_own[1] - d_nbr[1], d_own[2] - d_nbr[2]};
+        double w = p->face_area[f] / (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        const double Ij = I[nbr * A + a];
+        for (int x = 0; x < 3; ++x) b[x] += w * r[x] * (Ij - Ic);
+        if (Ij < lo) lo = Ij;
+        if (Ij > hi) hi = Ij;
+      }
+      double g[3];
+      for (int x = 0; x < 3; ++x) g[x] = (C[x][0] * b[0] + C[x][1] * b[1] + C[x][2] * b[2]) / det;
+      if (limit) {
+        double alpha = 1.0;
+        for (int64_t k = p->cell_face_ptr[c]; k < p->cell_face_ptr[c + 1]; ++k) {
+          const double *d_own, *d_nbr;
+          face_offsets(p, p->cell_face_idx[k], &d_own, &d_nbr);
+          const double dI = g[0] * d_own[0] + g[1] * d_own[1] + g[2] * d_own[2];
+          double al = 1.0;
+          if (dI > 0.0) al = (hi - Ic) / dI;
+          else if (dI < 0.0) al = (lo - Ic) / dI;
+          if (al < alpha) alpha = al;
+        }
+        for (int x = 0; x < 3; ++x) g[x] *= alpha;
+      }
+      for (int x = 0; x < 3; ++x) grad[(c * 3 + x) * A + a] = g[x];
+    }
+  }
+}
+
+/* The transport update of I over dt with the upwind value of each face
+ * reconstructed from (Ih, grad): I_up = Ih_u + g_u . (x_f - x_u), u the
+ * upwind cell (the same face value on both sides of the face). */
+void orc_transport_recon(const orc_problem *p, double dt, const double *I, const double *Ih,
+                         const double *grad, double *Istar) {
+  const int A = p->n_angles;
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < p->n_cells; ++c) {
+    for (int a = 0; a < A; ++a) {
+      const double *na = p->dir + 3 * a;
+      double acc = 0.0;
+      for (int64_t k = p->cell_face_ptr[c]; k < p->cell_face_ptr[c + 1]; ++k) {
+        int64_t f, nbr;
+        double sgn;
+        face_side(p, c, p->cell_face_idx[k], &f, &sgn, &nbr);
+        const double *d_own, *d_nbr;
+        face_offsets(p, p->cell_face_idx[k], &d_own, &d_nbr);
+        const double *nf = p->face_normal + 3 * f;
+        double area = p->face_area[f];
+        double ndotn = sgn * (na[0] * nf[0] + na[1] * nf[1] + na[2] * nf[2]);
+        double wdotn = 0.0;
+        if (p->face_w) {
+          const double *w = p->face_w + 3 * f;
+          wdotn = sgn * (w[0] * nf[0] + w[1] * nf[1] + w[2] * nf[2]);
+        }
+        double u = p->cbar * area * ndotn - area * wdotn;
+        if (u > 0.0) {
+          const double *g = grad + c * 3 * A + a;
+          acc += u * (Ih[c * A + a] + (g[0] * d_own[0] + g[A] * d_own[1] + g[2 * A] * d_own[2]));
+        } else if (u < 0.0) {
+          const double *g = grad + nbr * 3 * A + a;
+          acc += u * (Ih[nbr * A + a] + (g[0] * d_nbr[0] + g[A] * d_nbr[1] + g[2 * A] * d_nbr[2]));
+        }
+      }
+      Istar[c * A + a] = I[c * A + a] - dt / p->cell_volume[c] * acc;
+    }
+  }
+}
+
+/* One van Leer step (reading of the integration steps with the van Leer
+ * half step):
+ *   stage 1: I^{n+1/2} = source_{dt/2}(transport_{dt/2}(I^n)) with
+ *            piecewise-constant upwinding, on a copy of the gas (discarded);
+ *   stage 2: I* = I^n - dt/V sum_f u I_up(I^{n+1/2}, limited gradients of
+ *            I^{n+1/2}), then the implicit source over dt from the gas at n.
+ * I is replaced by I^{n+1}; work, Ih [N*A] and grad [N*3*A] are scratch. */
+int orc_step_vl(const orc_problem *p, double dt, double *I, double *work, double *Ih,
+                double *grad, double *e, double *m, double *ext, int *max_iters) {
+  const int64_t N = p->n_cells;
+  double *e1 = (double *)malloc(sizeof(double) * N);
+  double *m1 = (double *)malloc(sizeof(double) * 3 * N);
+  double *x1 = (double *)malloc(sizeof(double) * 4 * N);
+  if (!e1 || !m1 || !x1) {
+    free(e1);
+    free(m1);
+    free(x1);
+    return ORC_ERR_NONFINITE;
+  }
+  memcpy(e1, e, sizeof(double) * N);
+  memcpy(m1, m, sizeof(double) * 3 * N);
+  memcpy(x1, ext, sizeof(double) * 4 * N);
+  orc_transport(p, 0.5 * dt, I, work);
+  int st = orc_source(p, 0.5 * dt, work, Ih, e1, m1, x1, NULL);
+  free(e1);
+  free(m1);
+  free(x1);
+  if (st != ORC_OK) return st;
+  orc_gradient(p, Ih, 1, grad);
+  orc_transport_recon(p, dt, I, Ih, grad, work);
+  return orc_source(p, dt, work, I, e, m, ext, max_iters);
 }

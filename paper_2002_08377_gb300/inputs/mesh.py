@@ -75,6 +75,18 @@ class Mesh:
     def n_faces(self) -> int:
         return int(self.face_area.shape[0])
 
+    def face_offset(self):
+        """[Nf, 2, 3]: the face centroid relative to each of the face's two
+        cells, x_f - x_i and x_f - x_j', where j' is the periodic image of j
+        that meets i across the face (face centroids are in cell i's frame,
+        j' = x_j + shift * box)."""
+        i, j = self.face_cells[:, 0], self.face_cells[:, 1]
+        xj = self.cell_centroid[j] + self.face_shift.astype(np.float64) * self.box
+        off = np.empty((self.n_faces, 2, 3))
+        off[:, 0] = self.face_centroid - self.cell_centroid[i]
+        off[:, 1] = self.face_centroid - xj
+        return off
+
     def lattice_index(self):
         """(ix, iy, iz) lattice coordinates of every cell."""
         nx, ny, nz = self.n

@@ -67,6 +67,7 @@ class Problem:
     J0: np.ndarray            # [N] initial intensity scale per cell
     q0: np.ndarray            # [A] initial angular profile (I = J0 x q0)
     extra: dict = field(default_factory=dict)
+    integrator: int = 0       # 0 first-order upwind step, 1 van Leer with limited linear reconstruction
 
     @property
     def n_cells(self):

@@ -425,7 +425,7 @@ def test_shadow_behind_opaque_sphere():
 
 
 # ---------------------------------------------------------------- diffusion limit
-def _diffusion_gaussian_error(N, v, chi=125.0, dx=0.08, rho0=1e6):
+def _diffusion_gaussian_error(N, v, chi=125.0, dx=0.08, rho0=1e6, integrator=0):
     """Sec. 3.3 setup, first-order scheme: a quasi-1-D periodic box (N x 3 x 3
     cubic cells, lattice jitter 1e-6 of the spacing), one angle per octant,
     a scattering medium of total opacity rho kappa_s = chi, c = cbar, the gas
@@ -454,7 +454,7 @@ def _diffusion_gaussian_error(N, v, chi=125.0, dx=0.08, rho0=1e6):
     prob = Problem("diffusion-gaussian", mesh, dirs, wt, 1.0, 1.0, 1.0, 5.0 / 3.0, 1.0, 0.3, 0,
                    rho, e, m, z.copy(), z.copy(), np.full(n, chi / rho0), np.zeros(n, np.uint8),
                    z.copy(), z.copy(), z.copy(), np.full(n, -1, np.int32), np.zeros((1, A)),
-                   E0 / (4 * np.pi), 1.0 / gamma ** 4)
+                   E0 / (4 * np.pi), 1.0 / gamma ** 4, integrator=integrator)
     o = oracle.Oracle(prob)
     D = 1.0 / (3.0 * chi)
     t_end = dx ** 2 / (4.0 * D)

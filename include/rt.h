@@ -87,7 +87,12 @@ typedef enum {
  *     must be centrally symmetric in the order angle_dir[a + A/2] =
  *     -angle_dir[a] (A even); rt_create rejects it otherwise.
  *   face_w may be NULL (static mesh).  cell_centroid and face_centroid are
- *     used for the locality ordering only and may be NULL. */
+ *     used for the locality ordering only and may be NULL.
+ *   face_offset[f] = (x_f - x_i, x_f - x_j'): the face centroid minus each
+ *     cell's centroid, j' being the image of j that meets i across the face
+ *     (on a periodic mesh the two cells' centroids may lie in different
+ *     periodic frames).  Required when params->integrator = RT_VAN_LEER (the
+ *     linear reconstruction of Sec. 2.2), ignored and may be NULL otherwise. */
 typedef struct {
   int64_t n_cells;
   int64_t n_faces;
@@ -104,7 +109,20 @@ typedef struct {
   const int32_t *cell_face_idx;/* [nnz]      */
   const double *angle_dir;     /* [A][3]     */
   const double *angle_w;       /* [A]        */
+  const double *face_offset;   /* [Nf][2][3] */
 } rt_mesh_desc;
+
+/* Time integration of the transport (Sec. 2, integration steps).
+ *   RT_FIRST_ORDER: piecewise-constant upwind transport over dt, then the
+ *     implicit source over dt.
+ *   RT_VAN_LEER: the paper's van Leer half step.  Stage 1 takes the first-
+ *     order step over dt/2 (its gas update is discarded); stage 2 applies to
+ *     I^n the fluxes of the stage-1 intensities reconstructed linearly at the
+ *     face centres -- least-squares gradients over the face neighbours,
+ *     limited (Barth-Jespersen) to the range of the cell and its neighbours --
+ *     then the implicit source over dt from the gas at the start of the step.
+ *     Second order in smooth regions, first order at extrema. */
+typedef enum { RT_FIRST_ORDER = 0, RT_VAN_LEER = 1 } rt_integrator;
 
 /* Physical constants and numerics (Sec. 2.1, 2.3.1).  cbar is the reduced
  * speed of light of the transport, c the true one (enters the gas coupling
@@ -115,6 +133,8 @@ typedef struct {
   double cbar, c, a_rad, gamma_gas, r_gas, cfl;
   int32_t precision;       /* rt_precision */
   int32_t newton_max_iter;
+  int32_t integrator;      /* rt_integrator */
+  int32_t reserved;        /* 0 */
 } rt_params;
 
 /* Validates and copies the mesh to the device, orders cells for locality,

@@ -11,6 +11,7 @@ from . import build as _build
 RT_OK, RT_ERR_ARG, RT_ERR_MESH, RT_ERR_CUDA, RT_ERR_OOM = 0, -1, -2, -3, -4
 RT_ERR_CFL, RT_ERR_NONCONV, RT_ERR_NONFINITE, RT_ERR_STATE = -5, -6, -7, -8
 RT_FP64, RT_FP32 = 0, 1
+RT_FIRST_ORDER, RT_VAN_LEER = 0, 1
 _NAMES = {0: "RT_OK", -1: "RT_ERR_ARG", -2: "RT_ERR_MESH", -3: "RT_ERR_CUDA", -4: "RT_ERR_OOM",
           -5: "RT_ERR_CFL", -6: "RT_ERR_NONCONV", -7: "RT_ERR_NONFINITE", -8: "RT_ERR_STATE"}
 
@@ -35,14 +36,15 @@ class MeshDesc(ctypes.Structure):
                 ("face_normal", ctypes.c_void_p), ("face_centroid", ctypes.c_void_p),
                 ("face_w", ctypes.c_void_p), ("cell_face_ptr", ctypes.c_void_p),
                 ("cell_face_idx", ctypes.c_void_p), ("angle_dir", ctypes.c_void_p),
-                ("angle_w", ctypes.c_void_p)]
+                ("angle_w", ctypes.c_void_p), ("face_offset", ctypes.c_void_p)]
 
 
 class Params(ctypes.Structure):
     _fields_ = [("cbar", ctypes.c_double), ("c", ctypes.c_double), ("a_rad", ctypes.c_double),
                 ("gamma_gas", ctypes.c_double), ("r_gas", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("newton_max_iter", ctypes.c_int32)]
+                ("newton_max_iter", ctypes.c_int32), ("integrator", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _lib = None

@@ -197,6 +197,64 @@ template <typename R> int build_device_mesh(rt_state *s, const rt_mesh_desc *m,
   return RT_OK;
 }
 
+// Linear-reconstruction geometry for the van Leer integrator, in the internal
+// cell and slot order.  Per directed slot k of cell c (8 reals):
+//   (x_f - x_c, w_f, x_f - x_nbr', 0), w_f = A_f / |r_f|^2, r_f = x_nbr' - x_c,
+// with nbr' the neighbour's image across f; per cell (8 reals) the inverse of
+// M = sum_f w_f r_f r_f^T (symmetric: xx, xy, xz, yy, yz, zz, 0, 0), formed in
+// double by cofactors.
+template <typename R> int build_recon(rt_state *s, const rt_mesh_desc *m) {
+  const int64_t N = m->n_cells;
+  std::vector<R> rs(8 * (size_t)s->nnz), lsq(8 * (size_t)N, R(0));
+  int64_t o = 0;
+  for (int64_t ic = 0; ic < N; ++ic) {
+    const int64_t c = s->cell_of[ic];
+    double M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int64_t k = m->cell_face_ptr[c]; k < m->cell_face_ptr[c + 1]; ++k, ++o) {
+      const int32_t e = m->cell_face_idx[k];
+      const int64_t f = e >= 0 ? e : -(int64_t)e - 1;
+      const double *off = m->face_offset + 6 * f;
+      const double *own = e >= 0 ? off : off + 3, *oth = e >= 0 ? off + 3 : off;
+      const double r[3] = {own[0] - oth[0], own[1] - oth[1], own[2] - oth[2]};
+      const double w = m->face_area[f] / (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+      for (int x = 0; x < 3; ++x)
+        for (int y = 0; y < 3; ++y) M[x][y] += w * r[x] * r[y];
+      R *q = rs.data() + 8 * o;
+      q[0] = (R)own[0];
+      q[1] = (R)own[1];
+      q[2] = (R)own[2];
+      q[3] = (R)w;
+      q[4] = (R)oth[0];
+      q[5] = (R)oth[1];
+      q[6] = (R)oth[2];
+      q[7] = R(0);
+    }
+    const double C00 = M[1][1] * M[2][2] - M[1][2] * M[2][1];
+    const double C01 = M[0][2] * M[2][1] - M[0][1] * M[2][2];
+    const double C02 = M[0][1] * M[1][2] - M[0][2] * M[1][1];
+    const double C11 = M[0][0] * M[2][2] - M[0][2] * M[2][0];
+    const double C12 = M[0][2] * M[1][0] - M[0][0] * M[1][2];
+    const double C22 = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+    const double det = M[0][0] * C00 + M[0][1] * (M[1][2] * M[2][0] - M[1][0] * M[2][2]) +
+                       M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    if (!(std::fabs(det) > 0))
+      return fail(s, RT_ERR_MESH, "a cell's face neighbours do not span 3-D (singular gradient)");
+    R *q = lsq.data() + 8 * ic;
+    q[0] = (R)(C00 / det);
+    q[1] = (R)(C01 / det);
+    q[2] = (R)(C02 / det);
+    q[3] = (R)(C11 / det);
+    q[4] = (R)(C12 / det);
+    q[5] = (R)(C22 / det);
+  }
+  R *drs = nullptr, *dlsq = nullptr;
+  RT_CUDA(s, upload(s, &drs, rs));
+  RT_CUDA(s, upload(s, &dlsq, lsq));
+  s->d_recon = drs;
+  s->d_lsq = dlsq;
+  return RT_OK;
+}
+
 int check_mesh(rt_state *s, const rt_mesh_desc *m) {
   const int64_t N = m->n_cells, Nf = m->n_faces;
   if (N < 1 || N > INT32_MAX || Nf < 0 || m->n_angles < 2 || (m->n_angles & 1))
@@ -293,7 +351,9 @@ int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state 
     return code;
   };
   if (!(p->cbar > 0) || !(p->c > 0) || !(p->a_rad >= 0) || !(p->gamma_gas > 1) ||
-      !(p->r_gas > 0) || !(p->cfl > 0) || (p->precision != RT_FP32 && p->precision != RT_FP64))
+      !(p->r_gas > 0) || !(p->cfl > 0) || (p->precision != RT_FP32 && p->precision != RT_FP64) ||
+      (p->integrator != RT_FIRST_ORDER && p->integrator != RT_VAN_LEER) ||
+      (p->integrator == RT_VAN_LEER && !m->face_offset))
     return bail(RT_ERR_ARG);
   s->params = *p;
   if (s->params.newton_max_iter <= 0) s->params.newton_max_iter = 64;
@@ -346,6 +406,11 @@ int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state 
   int r = (s->precision == RT_FP32) ? build_device_mesh<float>(s, m, slot_of)
                                     : build_device_mesh<double>(s, m, slot_of);
   if (r != RT_OK) return bail(r);
+  s->integrator = p->integrator;
+  if (s->integrator == RT_VAN_LEER) {
+    r = (s->precision == RT_FP32) ? build_recon<float>(s, m) : build_recon<double>(s, m);
+    if (r != RT_OK) return bail(r);
+  }
   if (s->precision == RT_FP64) {
     // the FP64 flux-coefficient table: 8 A/2 bytes per directed face
     const cudaError_t e = rt::build_uface(s);
@@ -385,6 +450,10 @@ int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state 
   CK(dalloc(s, &s->d_aux, N));
   CK(dalloc(s, &s->d_bc_row, N));
   CK(dalloc(s, &s->d_ext, 4 * (size_t)N));
+  if (s->integrator == RT_VAN_LEER) {  // stage-1 intensities and their gradients
+    CK(dalloc_bytes(s, &s->d_Ihalf, (size_t)N * RS * s->rsize));
+    CK(dalloc_bytes(s, &s->d_grad, 3 * (size_t)N * RS * s->rsize));
+  }
   CK(dalloc_bytes(s, &s->d_cellv, 4 * (size_t)N * s->rsize));
   CK(cudaMemsetAsync(s->d_cellv, 0, 4 * (size_t)N * s->rsize, s->stream));
   CK(dalloc(s, &s->d_status, 1));
@@ -650,6 +719,8 @@ int rt_adjoint_step(rt_state *s, double dt, const void *I_n, const double *e_n, 
                     int on_device) {
   if (!s) return RT_ERR_ARG;
   if (!s->gas_set) return fail(s, RT_ERR_STATE, "rt_set_gas must be called before the adjoint");
+  if (s->integrator != RT_FIRST_ORDER)
+    return fail(s, RT_ERR_STATE, "rt_adjoint_step reverses the first-order step only");
   if (!I_n || !e_n || !m_n || !lam_I1 || !lam_e1 || !lam_m1 || !lam_I || !lam_e || !lam_m ||
       !grad_kappa_P || !grad_kappa_J)
     return fail(s, RT_ERR_ARG, "rt_adjoint_step: NULL argument");
@@ -757,7 +828,7 @@ void rt_destroy(rt_state *s) {
     if (s->d_adj[k]) cudaFree(s->d_adj[k]);
   if (s->d_adj_ws) cudaFree(s->d_adj_ws);
   if (s->d_adj_stage) cudaFree(s->d_adj_stage);
-  void *bufs[] = {s->d_uface, s->d_slot_nb, s->d_wface, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
+  void *bufs[] = {s->d_recon, s->d_lsq, s->d_Ihalf, s->d_grad, s->d_uface, s->d_slot_nb, s->d_wface, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
                   s->d_gd, s->d_kind, s->d_aux, s->d_bc_row, s->d_I0, s->d_ext, s->d_dir, s->d_wt,
                   s->d_dir64, s->d_wt64, s->d_I[0], s->d_I[1], s->d_status, s->d_bad,
                   s->d_scratch, s->d_out16};

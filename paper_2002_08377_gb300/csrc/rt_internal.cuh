@@ -86,6 +86,8 @@ template <typename R> struct StepArgs {
   R dt_r, dt_cbar_r, inv_c_r;
   float k_dcr_f, k_alpha_f, k_g_f, a_rad_4pi_f;  // float copies for the float quartic
   int32_t newton_max_iter;
+  int32_t src_only;         // 1: I_in holds I* already (no transport)
+  int32_t commit;           // 0: the gas update is discarded (van Leer stage 1)
   unsigned *status;
   unsigned long long *bad_cell;
 };
@@ -140,6 +142,11 @@ struct rt_state {
   void *d_slot = nullptr;
   rt::SlotF *d_slot_nb = nullptr;  // float, static mesh: slot with the neighbour in w
   double *d_uface = nullptr;  // double: [nnz][A/2] flux coefficients, built once (build_uface)
+  // van Leer integrator: reconstruction geometry ([nnz][8] and [N][8] reals
+  // of the state precision, see build_recon), stage-1 intensities [N][RS]
+  // and their limited gradients [N][3][RS]
+  int integrator = RT_FIRST_ORDER;
+  void *d_recon = nullptr, *d_lsq = nullptr, *d_Ihalf = nullptr, *d_grad = nullptr;
   double *d_wface = nullptr;  // double states: per-slot A w . n
   void *d_inv_vol = nullptr;
   int64_t *d_cell_of = nullptr;  // internal -> caller
@@ -173,6 +180,17 @@ namespace rt {
 
 // kernel launchers (rt_step.cu)
 cudaError_t launch_step(rt_state *s, double dt);
+// One launch of the step kernel with explicit rows: `in` -> `out`; src_only:
+// `in` already holds the transported I* (the source step only); commit:
+// write the gas update (else only the status bits).
+struct StepIO {
+  const void *in;
+  void *out;
+  bool src_only, commit;
+};
+cudaError_t launch_step_io(rt_state *s, double dt, const StepIO &io);
+// The van Leer step (rt_recon.cu); leaves I^{n+1} in d_I[cur ^ 1].
+cudaError_t launch_step_vl(rt_state *s, double dt);
 // Double states: fills d_uface (allocates it on first use).
 cudaError_t build_uface(rt_state *s);
 

@@ -406,12 +406,15 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
     const int k0 = (int)(a.ptr[c] - kb), k1 = (int)(a.ptr[c + 1] - kb);
     cp_async_wait_all();
     __syncthreads();  // the block's stage has landed
-    face_sum<R, M, MOVING, !MOVING>(reinterpret_cast<const typename SlotOf<R>::type *>(stage.slot),
-                                    stage.nbr, a.wface, a.uface, a.half, k0, k1, a.I_in, RS, sub,
-                                    nx, ny, nz, Ia, Ib, acca, accb, np);
+    if (!a.src_only)
+      face_sum<R, M, MOVING, !MOVING>(
+          reinterpret_cast<const typename SlotOf<R>::type *>(stage.slot), stage.nbr, a.wface,
+          a.uface, a.half, k0, k1, a.I_in, RS, sub, nx, ny, nz, Ia, Ib, acca, accb, np);
   } else {
-    face_sum<R, M, MOVING, false>(a.slot, a.nbr, a.wface, a.uface, a.half, a.ptr[c], a.ptr[c + 1],
-                                  a.I_in, RS, sub, nx, ny, nz, Ia, Ib, acca, accb, np);
+    if (!a.src_only)
+      face_sum<R, M, MOVING, false>(a.slot, a.nbr, a.wface, a.uface, a.half, a.ptr[c],
+                                    a.ptr[c + 1], a.I_in, RS, sub, nx, ny, nz, Ia, Ib, acca, accb,
+                                    np);
   }
   {
     const R dtv = a.dt_r * a.inv_vol[c];
@@ -581,7 +584,9 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
     const double dE = a.k_fe * (double)sh.dE[lp];
     const double dx = a.k_fm * (double)sh.dF[0][lp], dy = a.k_fm * (double)sh.dF[1][lp],
                  dz = a.k_fm * (double)sh.dF[2][lp];
-    if (a.kind[cl] == RT_CELL_INTERIOR) {
+    if (!a.commit) {
+      // stage 1 of the van Leer step: the gas update is discarded
+    } else if (a.kind[cl] == RT_CELL_INTERIOR) {
       GasDyn d = gd_s[lp];
       d.e += dE;
       d.mx += dx;
@@ -636,7 +641,7 @@ __global__ void __launch_bounds__(NT, min_blocks<float, M::PPT>())
 
 // Fills the kernel arguments and launches one step with pair map M.
 template <typename R, typename M, bool MOVING, bool STAGED>
-cudaError_t launch_t(rt_state *s, double dt) {
+cudaError_t launch_t(rt_state *s, double dt, const StepIO &io) {
   StepArgs<R> a;
   a.n_cells = s->n_cells;
   a.n_angles = s->n_angles;
@@ -658,8 +663,10 @@ cudaError_t launch_t(rt_state *s, double dt) {
   a.ext = s->d_ext;
   a.dir = reinterpret_cast<const R *>(s->d_dir);
   a.wt2 = reinterpret_cast<const R *>(s->d_wt);
-  a.I_in = reinterpret_cast<const R *>(s->d_I[s->cur]);
-  a.I_out = reinterpret_cast<R *>(s->d_I[s->cur ^ 1]);
+  a.I_in = reinterpret_cast<const R *>(io.in);
+  a.I_out = reinterpret_cast<R *>(io.out);
+  a.src_only = io.src_only ? 1 : 0;
+  a.commit = io.commit ? 1 : 0;
   a.dt = dt;
   a.dt_r = R(dt);
   a.dt_cbar_r = R(dt * s->params.cbar);
@@ -692,44 +699,46 @@ cudaError_t launch_t(rt_state *s, double dt) {
   return cudaGetLastError();
 }
 
-template <typename R, bool MOVING, bool FULL> cudaError_t dispatch_pairs(rt_state *s, double dt) {
+template <typename R, bool MOVING, bool FULL>
+cudaError_t dispatch_pairs(rt_state *s, double dt, const StepIO &io) {
   const int ppt = (s->n_angles / 2 + KT - 1) / KT;
   switch (ppt) {
-    case 1: return launch_t<R, PairMap<R, 1, FULL>, MOVING, false>(s, dt);
-    case 2: return launch_t<R, PairMap<R, 2, FULL>, MOVING, false>(s, dt);
-    case 3: return launch_t<R, PairMap<R, 3, FULL>, MOVING, false>(s, dt);
-    case 4: return launch_t<R, PairMap<R, 4, FULL>, MOVING, false>(s, dt);
-    case 5: return launch_t<R, PairMap<R, 5, FULL>, MOVING, false>(s, dt);
-    case 6: return launch_t<R, PairMap<R, 6, FULL>, MOVING, false>(s, dt);
-    case 7: return launch_t<R, PairMap<R, 7, FULL>, MOVING, false>(s, dt);
-    case 8: return launch_t<R, PairMap<R, 8, FULL>, MOVING, false>(s, dt);
+    case 1: return launch_t<R, PairMap<R, 1, FULL>, MOVING, false>(s, dt, io);
+    case 2: return launch_t<R, PairMap<R, 2, FULL>, MOVING, false>(s, dt, io);
+    case 3: return launch_t<R, PairMap<R, 3, FULL>, MOVING, false>(s, dt, io);
+    case 4: return launch_t<R, PairMap<R, 4, FULL>, MOVING, false>(s, dt, io);
+    case 5: return launch_t<R, PairMap<R, 5, FULL>, MOVING, false>(s, dt, io);
+    case 6: return launch_t<R, PairMap<R, 6, FULL>, MOVING, false>(s, dt, io);
+    case 7: return launch_t<R, PairMap<R, 7, FULL>, MOVING, false>(s, dt, io);
+    case 8: return launch_t<R, PairMap<R, 8, FULL>, MOVING, false>(s, dt, io);
     default: return cudaErrorInvalidValue;
   }
 }
 
 // Float rows with A = 16 m (32 <= A <= 128) whose blocks' slots fit the
 // shared-memory stage: QuadMap<A / 32, A % 32 != 0>.
-template <bool MOVING> cudaError_t dispatch_quads(rt_state *s, double dt) {
+template <bool MOVING> cudaError_t dispatch_quads(rt_state *s, double dt, const StepIO &io) {
   switch (s->n_angles / 16) {
-    case 2: return launch_t<float, QuadMap<1, false>, MOVING, true>(s, dt);
-    case 3: return launch_t<float, QuadMap<1, true>, MOVING, true>(s, dt);
-    case 4: return launch_t<float, QuadMap<2, false>, MOVING, true>(s, dt);
-    case 5: return launch_t<float, QuadMap<2, true>, MOVING, true>(s, dt);
-    case 6: return launch_t<float, QuadMap<3, false>, MOVING, true>(s, dt);
-    case 7: return launch_t<float, QuadMap<3, true>, MOVING, true>(s, dt);
-    case 8: return launch_t<float, QuadMap<4, false>, MOVING, true>(s, dt);
+    case 2: return launch_t<float, QuadMap<1, false>, MOVING, true>(s, dt, io);
+    case 3: return launch_t<float, QuadMap<1, true>, MOVING, true>(s, dt, io);
+    case 4: return launch_t<float, QuadMap<2, false>, MOVING, true>(s, dt, io);
+    case 5: return launch_t<float, QuadMap<2, true>, MOVING, true>(s, dt, io);
+    case 6: return launch_t<float, QuadMap<3, false>, MOVING, true>(s, dt, io);
+    case 7: return launch_t<float, QuadMap<3, true>, MOVING, true>(s, dt, io);
+    case 8: return launch_t<float, QuadMap<4, false>, MOVING, true>(s, dt, io);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <typename R> cudaError_t dispatch(rt_state *s, double dt) {
+template <typename R> cudaError_t dispatch(rt_state *s, double dt, const StepIO &io) {
   const int A = s->n_angles;
   if (sizeof(R) == 4 && s->quad_end > 0)  // rows in the quad layout
-    return s->moving ? dispatch_quads<true>(s, dt) : dispatch_quads<false>(s, dt);
+    return s->moving ? dispatch_quads<true>(s, dt, io) : dispatch_quads<false>(s, dt, io);
   const bool full = (A / 2) % KT == 0;
   if (s->moving)
-    return full ? dispatch_pairs<R, true, true>(s, dt) : dispatch_pairs<R, true, false>(s, dt);
-  return full ? dispatch_pairs<R, false, true>(s, dt) : dispatch_pairs<R, false, false>(s, dt);
+    return full ? dispatch_pairs<R, true, true>(s, dt, io) : dispatch_pairs<R, true, false>(s, dt, io);
+  return full ? dispatch_pairs<R, false, true>(s, dt, io)
+              : dispatch_pairs<R, false, false>(s, dt, io);
 }
 
 // U[k][p] = the double flux coefficient of pair p through directed face k,
@@ -763,8 +772,18 @@ cudaError_t build_uface(rt_state *s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_step_io(rt_state *s, double dt, const StepIO &io) {
+  return (s->precision == RT_FP32) ? dispatch<float>(s, dt, io) : dispatch<double>(s, dt, io);
+}
+
 cudaError_t launch_step(rt_state *s, double dt) {
-  cudaError_t e = (s->precision == RT_FP32) ? dispatch<float>(s, dt) : dispatch<double>(s, dt);
+  cudaError_t e;
+  if (s->integrator == RT_VAN_LEER) {
+    e = launch_step_vl(s, dt);
+  } else {
+    const StepIO io{s->d_I[s->cur], s->d_I[s->cur ^ 1], false, true};
+    e = launch_step_io(s, dt, io);
+  }
   if (e == cudaSuccess) s->cur ^= 1;
   return e;
 }

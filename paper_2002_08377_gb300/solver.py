@@ -24,11 +24,13 @@ class RTSolver:
     """One mesh + angle set + gas state on the current CUDA device.
 
     precision: "fp32" (float intensities/transport, double quartic and
-    exchange) or "fp64".
+    exchange) or "fp64".  integrator: 0 first-order upwind step, 1 van Leer
+    step with limited linear reconstruction (needs mesh.face_offset()).
     """
 
     def __init__(self, mesh, dirs, weights, *, cbar, c, a_rad=1.0, gamma_gas=5.0 / 3.0,
-                 r_gas=1.0, cfl=0.3, precision="fp32", newton_max_iter=64, stream=None):
+                 r_gas=1.0, cfl=0.3, precision="fp32", newton_max_iter=64, integrator=0,
+                 stream=None):
         if torch is None or not torch.cuda.is_available():
             raise RuntimeError("RTSolver needs a CUDA device (no CPU fallback exists)")
         self.lib = capi.load()
@@ -60,8 +62,11 @@ class RTSolver:
         md.cell_face_idx = ptr(mesh.cell_face_idx, np.int32)
         md.angle_dir = ptr(dirs, np.float64)
         md.angle_w = ptr(weights, np.float64)
+        if integrator == capi.RT_VAN_LEER:
+            md.face_offset = ptr(mesh.face_offset(), np.float64)
         pr = capi.Params(cbar, c, a_rad, gamma_gas, r_gas, cfl,
-                         capi.RT_FP32 if precision == "fp32" else capi.RT_FP64, newton_max_iter)
+                         capi.RT_FP32 if precision == "fp32" else capi.RT_FP64, newton_max_iter,
+                         int(integrator), 0)
         st = ctypes.c_void_p()
         code = self.lib.rt_create(ctypes.byref(md), ctypes.byref(pr),
                                   ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(st))
@@ -72,6 +77,7 @@ class RTSolver:
 
     @classmethod
     def from_problem(cls, prob, precision="fp32", **kw):
+        kw.setdefault("integrator", getattr(prob, "integrator", 0))
         s = cls(prob.mesh, prob.dirs, prob.weights, cbar=prob.cbar, c=prob.c, a_rad=prob.a_rad,
                 gamma_gas=prob.gamma_gas, r_gas=prob.r_gas, cfl=prob.cfl, precision=precision, **kw)
         s.set_gas(prob.rho, prob.e, prob.m, prob.kappa_P, prob.kappa_J, prob.kappa_s)

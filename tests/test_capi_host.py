@@ -99,3 +99,25 @@ def test_null_arguments(lib):
     assert lib.rt_step(None, 0.0, None) == capi.RT_ERR_ARG
     assert lib.rt_launch_count(None) == -1
     lib.rt_destroy(None)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of rt_mesh_desc and rt_params have the header's
+    size and field offsets (compiled with the host C compiler)."""
+    import subprocess
+    inc = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include")
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rt.h"', "int main(void) {"]
+    for cname, py in (("rt_mesh_desc", capi.MeshDesc), ("rt_params", capi.Params)):
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", inc, str(src), "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for cname, py in (("rt_mesh_desc", capi.MeshDesc), ("rt_params", capi.Params)):
+        assert int(got[cname]) == ctypes.sizeof(py)
+        for f, _ in py._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, f

@@ -82,6 +82,23 @@ def algorithmic_bytes(n_cells, n_faces, n_angles, real_bytes):
     return b
 
 
+def algorithmic_bytes_vl(n_cells, n_faces, n_angles, real_bytes):
+    """Bytes one van Leer step must move: stage 1 is a first-order step over
+    dt/2 (algorithmic_bytes); the gradient pass reads the stage-1 row of
+    every cell and its reconstruction geometry (8 reals and a neighbour index
+    per directed face, 8 reals per cell) and writes three gradient rows; the
+    reconstructed transport reads I^n, the stage-1 row and its gradient rows,
+    every undirected face's slot data and the geometry again, and writes I*;
+    the source-only stage reads I* and the gas and writes I^{n+1} and the gas."""
+    s, N, F, A = real_bytes, n_cells, n_faces, n_angles
+    stage1 = algorithmic_bytes(N, F, A, s)
+    geometry = 2 * F * (8 * s + 4) + 8 * s * N
+    gradient = N * A * s * (1 + 3) + geometry
+    transport = N * A * s * (1 + 1 + 3 + 1) + geometry + F * (8 + 4 * s)
+    source = N * (2 * A * s + 104)
+    return stage1 + gradient + transport + source
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     """SM clock and clock-event reasons during the timed region, via NVML
@@ -303,6 +320,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-vl", action="store_true", help="skip the van Leer leg")
     ap.add_argument("--only", choices=["fp32", "fp64"], default=None,
                     help="time one precision only (profiling runs)")
     ap.add_argument("--n", type=int, default=128,
@@ -365,6 +383,27 @@ def main():
         del sol
         torch.cuda.empty_cache()
 
+    vl = None
+    if args.only is None and not args.no_vl:
+        # the van Leer integrator with limited linear reconstruction (FP32)
+        prob.integrator = 1
+        sol = RTSolver.from_problem(prob, "fp32")
+        steps = max(3, args.steps // 5)
+        ms, launches = time_steps(sol, dt, steps, max(3, args.warmup), world)
+        per = ms / steps
+        B = algorithmic_bytes_vl(N, Nf, A, 4)
+        achieved = B / (per * 1e-3) / 1e9
+        vl = {"value": N * A * steps * world / (ms * 1e-3), "ms_per_step": per, "steps": steps,
+              "launches": launches, "dtype": "f32",
+              "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                           "frac": achieved / hbm_peak, "traffic": None,
+                           "algorithmic_bytes_per_step": B,
+                           "peak_source": f"{peak_kind} HBM copy bandwidth"}}
+        sol.close()
+        del sol
+        prob.integrator = 0
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, done, el = cpu_oracle_rate(prob, dt, args.cpu_budget)
@@ -389,7 +428,8 @@ def main():
             "fp64": {"value": results["fp64"]["value"], "ms_per_step": results["fp64"]["ms_per_step"],
                      "steps": results["fp64"]["steps"], "dtype": "f64",
                      "roofline": results["fp64"]["roofline"],
-                     "fp32_over_fp64": r32["value"] / results["fp64"]["value"]}}
+                     "fp32_over_fp64": r32["value"] / results["fp64"]["value"]},
+            "van_leer": vl}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

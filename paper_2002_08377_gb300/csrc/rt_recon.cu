@@ -32,140 +32,234 @@ __device__ __forceinline__ double rmin(double a, double b) { return fmin(a, b); 
 __device__ __forceinline__ float rmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double rmax(double a, double b) { return fmax(a, b); }
 
-// grad[(c * 3 + d) * RS + q]: limited gradient of the intensity at row
-// position q of cell c.  recon[8 k] = (x_f - x_c, w_f, x_f - x_nbr', 0) of
-// slot k; lsq[8 c] = the inverse of sum_f w_f r_f r_f^T (xx, xy, xz, yy, yz,
-// zz).  One warp per cell, lanes over row positions.
+// Per warp, a cell's face geometry is staged in shared memory CH slots at a
+// time: recon (x_f - x_c, w_f, x_f - x_nbr', 0), the neighbour index and,
+// for the float transport, the face slot (c A n, A w.n).
+constexpr int CH = 32;
+template <typename R> struct WarpStage {
+  R geo[CH][8];
+  SlotF slot[CH];
+  int32_t nb[CH];
+};
+
+// Copies slots [k, k + cnt) of the cell into the warp's stage (cnt <= CH).
 template <typename R>
+__device__ __forceinline__ void stage_faces(WarpStage<R> &st, const R *__restrict__ recon,
+                                            const int32_t *__restrict__ nbr, const SlotF *slotf,
+                                            int64_t k, int cnt, int lane) {
+  for (int l = lane; l < cnt; l += 32) {
+    const R *g = recon + 8 * (k + l);
+#pragma unroll
+    for (int x = 0; x < 8; ++x) st.geo[l][x] = g[x];
+    st.nb[l] = nbr[k + l];
+    if (slotf) st.slot[l] = slotf[k + l];
+  }
+  __syncwarp();
+}
+
+// grad[(c * 3 + d) * RS + q]: limited gradient of the intensity at row
+// position q of cell c (lsq[8 c] = the inverse of sum_f w_f r_f r_f^T as
+// xx, xy, xz, yy, yz, zz).  One warp per cell; lane l takes the positions
+// l + 32 i (i < QN).  The limiter factor is the oracle's min over faces
+// of (max - I_c) / d_f (d_f > 0) and (min - I_c) / d_f (d_f < 0), taken as one
+// division by the largest and one by the smallest d_f: correctly rounded
+// division is monotone in d_f, so the result is the same number.
+template <typename R, int QN>
 __global__ void __launch_bounds__(kThreads) gradient_kernel(
     const int64_t *__restrict__ ptr, const int32_t *__restrict__ nbr, const R *__restrict__ recon,
     const R *__restrict__ lsq, const R *__restrict__ Ih, R *__restrict__ grad, int64_t n, int A,
     int RS) {
-  const int64_t c = (int64_t)blockIdx.x * kWarps + threadIdx.x / 32;
+  __shared__ WarpStage<R> stage[kWarps];
+  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int64_t c = (int64_t)blockIdx.x * kWarps + w;
   if (c >= n) return;
-  const int lane = threadIdx.x % 32;
+  WarpStage<R> &st = stage[w];
+  const int64_t k0 = ptr[c], k1 = ptr[c + 1];
+  R Ic[QN], bx[QN], by[QN], bz[QN], lo[QN], hi[QN];
+#pragma unroll
+  for (int i = 0; i < QN; ++i) {
+    const int q = lane + 32 * i;
+    Ic[i] = q < A ? Ih[(size_t)c * RS + q] : R(0);
+    lo[i] = hi[i] = Ic[i];
+    bx[i] = by[i] = bz[i] = R(0);
+  }
+  for (int64_t kc = k0; kc < k1; kc += CH) {
+    const int cnt = (int)(k1 - kc < CH ? k1 - kc : CH);
+    stage_faces<R>(st, recon, nbr, nullptr, kc, cnt, lane);
+    for (int t = 0; t < cnt; ++t) {
+      const R *g = st.geo[t];
+      const R rx = g[0] - g[4], ry = g[1] - g[5], rz = g[2] - g[6], wt = g[3];
+      const R *row = Ih + (size_t)st.nb[t] * RS;
+#pragma unroll
+      for (int i = 0; i < QN; ++i) {
+        const int q = lane + 32 * i;
+        if (q < A) {
+          const R Ij = row[q];
+          const R d = Ij - Ic[i];
+          bx[i] += wt * rx * d;
+          by[i] += wt * ry * d;
+          bz[i] += wt * rz * d;
+          lo[i] = rmin(lo[i], Ij);
+          hi[i] = rmax(hi[i], Ij);
+        }
+      }
+    }
+    __syncwarp();
+  }
   const R *L = lsq + 8 * c;
   const R m00 = L[0], m01 = L[1], m02 = L[2], m11 = L[3], m12 = L[4], m22 = L[5];
-  const int64_t k0 = ptr[c], k1 = ptr[c + 1];
-  for (int q = lane; q < A; q += 32) {
-    const R Ic = Ih[(size_t)c * RS + q];
-    R bx = 0, by = 0, bz = 0, lo = Ic, hi = Ic;
-    for (int64_t k = k0; k < k1; ++k) {
-      const R *g = recon + 8 * k;
-      const R w = g[3];
-      const R Ij = Ih[(size_t)nbr[k] * RS + q];
-      const R d = Ij - Ic;
-      bx += w * (g[0] - g[4]) * d;
-      by += w * (g[1] - g[5]) * d;
-      bz += w * (g[2] - g[6]) * d;
-      lo = rmin(lo, Ij);
-      hi = rmax(hi, Ij);
+  R gx[QN], gy[QN], gz[QN], dmax[QN], dmin[QN];
+#pragma unroll
+  for (int i = 0; i < QN; ++i) {
+    gx[i] = m00 * bx[i] + m01 * by[i] + m02 * bz[i];
+    gy[i] = m01 * bx[i] + m11 * by[i] + m12 * bz[i];
+    gz[i] = m02 * bx[i] + m12 * by[i] + m22 * bz[i];
+    dmax[i] = dmin[i] = R(0);
+  }
+  for (int64_t kc = k0; kc < k1; kc += CH) {
+    const int cnt = (int)(k1 - kc < CH ? k1 - kc : CH);
+    if (k1 - k0 > CH) stage_faces<R>(st, recon, nbr, nullptr, kc, cnt, lane);
+    for (int t = 0; t < cnt; ++t) {
+      const R *g = st.geo[t];
+#pragma unroll
+      for (int i = 0; i < QN; ++i) {
+        const R dI = gx[i] * g[0] + gy[i] * g[1] + gz[i] * g[2];
+        dmax[i] = rmax(dmax[i], dI);
+        dmin[i] = rmin(dmin[i], dI);
+      }
     }
-    const R gx = m00 * bx + m01 * by + m02 * bz;
-    const R gy = m01 * bx + m11 * by + m12 * bz;
-    const R gz = m02 * bx + m12 * by + m22 * bz;
-    R alpha = 1;
-    for (int64_t k = k0; k < k1; ++k) {
-      const R *g = recon + 8 * k;
-      const R dI = gx * g[0] + gy * g[1] + gz * g[2];
-      R al = 1;
-      if (dI > R(0))
-        al = (hi - Ic) / dI;
-      else if (dI < R(0))
-        al = (lo - Ic) / dI;
-      alpha = rmin(alpha, al);
+    if (k1 - k0 > CH) __syncwarp();
+  }
+#pragma unroll
+  for (int i = 0; i < QN; ++i) {
+    const int q = lane + 32 * i;
+    if (q < A) {
+      R alpha = 1;
+      if (dmax[i] > R(0)) alpha = rmin(alpha, (hi[i] - Ic[i]) / dmax[i]);
+      if (dmin[i] < R(0)) alpha = rmin(alpha, (lo[i] - Ic[i]) / dmin[i]);
+      R *o = grad + (size_t)c * 3 * RS + q;
+      o[0] = alpha * gx[i];
+      o[RS] = alpha * gy[i];
+      o[2 * (size_t)RS] = alpha * gz[i];
     }
-    R *o = grad + (size_t)c * 3 * RS + q;
-    o[0] = alpha * gx;
-    o[RS] = alpha * gy;
-    o[2 * (size_t)RS] = alpha * gz;
   }
 }
 
-// Flux coefficient u of row position q (angle a = angle_of[q]) through slot
-// k, exactly as the fused step kernel forms it: float from the slot and the
-// direction, double from the tabulated n_p . s (the antipode's is its
-// negative); minus A w . n on a moving mesh.
-template <bool MOVING>
-__device__ __forceinline__ float flux_coef(const SlotF *slot, const double *, const double *,
-                                           int64_t k, int, float nx, float ny, float nz, int, bool) {
-  const SlotF s = slot[k];
-  const float d = fmaf(nx, s.sx, fmaf(ny, s.sy, nz * s.sz));
-  return MOVING ? d - s.w : d;
-}
-template <bool MOVING>
-__device__ __forceinline__ double flux_coef(const SlotD *, const double *wface, const double *uface,
-                                            int64_t k, int H, double, double, double, int p,
-                                            bool anti) {
-  const double d = uface[(size_t)k * H + p];
-  const double u = anti ? -d : d;
-  return MOVING ? u - wface[k] : u;
-}
-
 // I*[c][q] = I[c][q] - dt / V_c sum_f u I_up, I_up reconstructed at the face
-// centre from (Ih, grad) of the upwind cell.  One warp per cell.
-template <typename R, bool MOVING>
+// centre from (Ih, grad) of the upwind cell.  u as the fused step kernel
+// forms it: float from the face slot and the angle's direction, double from
+// the tabulated n_p . s (negated for the antipode); minus A w . n on a moving
+// mesh.  One warp per cell, lane l takes positions l + 32 i (i < QN).
+template <typename R, bool MOVING, int QN>
 __global__ void __launch_bounds__(kThreads) recon_transport_kernel(
-    const int64_t *__restrict__ ptr, const int32_t *__restrict__ nbr,
-    const typename SlotOf<R>::type *__restrict__ slot, const double *__restrict__ wface,
-    const double *__restrict__ uface, const R *__restrict__ recon, const R *__restrict__ dir,
-    const int32_t *__restrict__ angle_of, const R *__restrict__ inv_vol, const R *__restrict__ I,
-    const R *__restrict__ Ih, const R *__restrict__ grad, R *__restrict__ Istar, int64_t n, int A,
-    int RS, R dt) {
-  const int64_t c = (int64_t)blockIdx.x * kWarps + threadIdx.x / 32;
+    const int64_t *__restrict__ ptr, const int32_t *__restrict__ nbr, const SlotF *__restrict__ slotf,
+    const double *__restrict__ wface, const double *__restrict__ uface, const R *__restrict__ recon,
+    const R *__restrict__ dir, const int32_t *__restrict__ angle_of, const R *__restrict__ inv_vol,
+    const R *__restrict__ I, const R *__restrict__ Ih, const R *__restrict__ grad,
+    R *__restrict__ Istar, int64_t n, int A, int RS, R dt) {
+  __shared__ WarpStage<R> stage[kWarps];
+  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int64_t c = (int64_t)blockIdx.x * kWarps + w;
   if (c >= n) return;
-  const int lane = threadIdx.x % 32, H = A / 2;
-  const int64_t k0 = ptr[c], k1 = ptr[c + 1];
+  WarpStage<R> &st = stage[w];
+  const int H = A / 2;
   const size_t gs = (size_t)RS;
-  for (int q = lane; q < A; q += 32) {
-    const int a = angle_of[q];
-    const bool anti = a >= H;
-    const int p = anti ? a - H : a;
-    const R nx = dir[4 * a], ny = dir[4 * a + 1], nz = dir[4 * a + 2];
-    const R Ihc = Ih[(size_t)c * RS + q];
-    const R *gc = grad + (size_t)c * 3 * gs + q;
-    const R gcx = gc[0], gcy = gc[gs], gcz = gc[2 * gs];
-    R acc = 0;
-    for (int64_t k = k0; k < k1; ++k) {
-      const R u = flux_coef<MOVING>(slot, wface, uface, k, H, nx, ny, nz, p, anti);
-      const R *g = recon + 8 * k;
-      if (positive(u)) {
-        acc += u * (Ihc + (gcx * g[0] + gcy * g[1] + gcz * g[2]));
-      } else if (u < R(0)) {
-        const int64_t j = nbr[k];
-        const R *gj = grad + (size_t)j * 3 * gs + q;
-        acc += u * (Ih[(size_t)j * RS + q] + (gj[0] * g[4] + gj[gs] * g[5] + gj[2 * gs] * g[6]));
+  const int64_t k0 = ptr[c], k1 = ptr[c + 1];
+  R nx[QN], ny[QN], nz[QN], Ihc[QN], gcx[QN], gcy[QN], gcz[QN], acc[QN];
+  int pp[QN];
+  bool anti[QN];
+#pragma unroll
+  for (int i = 0; i < QN; ++i) {
+    const int q = lane + 32 * i;
+    const int a = q < A ? angle_of[q] : 0;
+    anti[i] = a >= H;
+    pp[i] = anti[i] ? a - H : a;
+    nx[i] = dir[4 * a];
+    ny[i] = dir[4 * a + 1];
+    nz[i] = dir[4 * a + 2];
+    const int qq = q < A ? q : 0;
+    Ihc[i] = Ih[(size_t)c * RS + qq];
+    const R *gc = grad + (size_t)c * 3 * gs + qq;
+    gcx[i] = gc[0];
+    gcy[i] = gc[gs];
+    gcz[i] = gc[2 * gs];
+    acc[i] = R(0);
+  }
+  for (int64_t kc = k0; kc < k1; kc += CH) {
+    const int cnt = (int)(k1 - kc < CH ? k1 - kc : CH);
+    stage_faces<R>(st, recon, nbr, sizeof(R) == 4 ? slotf : nullptr, kc, cnt, lane);
+    for (int t = 0; t < cnt; ++t) {
+      const R *g = st.geo[t];
+      const int64_t j = st.nb[t];
+      const R *Ihj = Ih + (size_t)j * RS;
+      const R *gj = grad + (size_t)j * 3 * gs;
+      R wk = R(0);
+      if (MOVING) wk = sizeof(R) == 4 ? R(st.slot[t].w) : R(wface[kc + t]);
+#pragma unroll
+      for (int i = 0; i < QN; ++i) {
+        const int q = lane + 32 * i;
+        if (q < A) {
+          R d;
+          if constexpr (sizeof(R) == 4) {
+            const SlotF sl = st.slot[t];
+            d = fmaf(nx[i], sl.sx, fmaf(ny[i], sl.sy, nz[i] * sl.sz));
+          } else {
+            const R dd = uface[(size_t)(kc + t) * H + pp[i]];
+            d = anti[i] ? -dd : dd;
+          }
+          const R u = MOVING ? d - wk : d;
+          if (positive(u)) {
+            acc[i] += u * (Ihc[i] + (gcx[i] * g[0] + gcy[i] * g[1] + gcz[i] * g[2]));
+          } else if (u < R(0)) {
+            acc[i] += u * (Ihj[q] + (gj[q] * g[4] + gj[gs + q] * g[5] + gj[2 * gs + q] * g[6]));
+          }
+        }
       }
     }
-    Istar[(size_t)c * RS + q] = I[(size_t)c * RS + q] - dt * inv_vol[c] * acc;
+    __syncwarp();
+  }
+#pragma unroll
+  for (int i = 0; i < QN; ++i) {
+    const int q = lane + 32 * i;
+    if (q < A) Istar[(size_t)c * RS + q] = I[(size_t)c * RS + q] - dt * inv_vol[c] * acc[i];
   }
 }
 
 unsigned warp_grid(int64_t n) { return (unsigned)((n + kWarps - 1) / kWarps); }
 
-template <typename R> cudaError_t vl_middle(rt_state *s, double dt) {
+template <typename R, int QN> cudaError_t vl_middle_q(rt_state *s, double dt) {
   const int64_t N = s->n_cells;
   const int A = s->n_angles, RS = s->row_stride;
   const R *recon = reinterpret_cast<const R *>(s->d_recon);
   const R *Ih = reinterpret_cast<const R *>(s->d_Ihalf);
   R *grad = reinterpret_cast<R *>(s->d_grad);
-  gradient_kernel<R><<<warp_grid(N), kThreads, 0, s->stream>>>(
+  gradient_kernel<R, QN><<<warp_grid(N), kThreads, 0, s->stream>>>(
       s->d_ptr, s->d_nbr, recon, reinterpret_cast<const R *>(s->d_lsq), Ih, grad, N, A, RS);
-  const auto *slot = reinterpret_cast<const typename SlotOf<R>::type *>(s->d_slot);
+  const SlotF *slotf = sizeof(R) == 4 ? reinterpret_cast<const SlotF *>(s->d_slot) : nullptr;
   const R *dir = reinterpret_cast<const R *>(s->d_dir);
   const R *iv = reinterpret_cast<const R *>(s->d_inv_vol);
   const R *I = reinterpret_cast<const R *>(s->d_I[s->cur]);
   R *Is = reinterpret_cast<R *>(s->d_I[s->cur ^ 1]);
   if (s->moving)
-    recon_transport_kernel<R, true><<<warp_grid(N), kThreads, 0, s->stream>>>(
-        s->d_ptr, s->d_nbr, slot, s->d_wface, s->d_uface, recon, dir, s->d_angle_of, iv, I, Ih,
+    recon_transport_kernel<R, true, QN><<<warp_grid(N), kThreads, 0, s->stream>>>(
+        s->d_ptr, s->d_nbr, slotf, s->d_wface, s->d_uface, recon, dir, s->d_angle_of, iv, I, Ih,
         grad, Is, N, A, RS, R(dt));
   else
-    recon_transport_kernel<R, false><<<warp_grid(N), kThreads, 0, s->stream>>>(
-        s->d_ptr, s->d_nbr, slot, s->d_wface, s->d_uface, recon, dir, s->d_angle_of, iv, I, Ih,
+    recon_transport_kernel<R, false, QN><<<warp_grid(N), kThreads, 0, s->stream>>>(
+        s->d_ptr, s->d_nbr, slotf, s->d_wface, s->d_uface, recon, dir, s->d_angle_of, iv, I, Ih,
         grad, Is, N, A, RS, R(dt));
   s->launches += 2;
   return cudaGetLastError();
+}
+
+template <typename R> cudaError_t vl_middle(rt_state *s, double dt) {
+  switch ((s->n_angles + 31) / 32) {
+    case 1: return vl_middle_q<R, 1>(s, dt);
+    case 2: return vl_middle_q<R, 2>(s, dt);
+    case 3: return vl_middle_q<R, 3>(s, dt);
+    case 4: return vl_middle_q<R, 4>(s, dt);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace

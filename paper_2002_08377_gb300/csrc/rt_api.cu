@@ -452,7 +452,7 @@ int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state 
   CK(dalloc(s, &s->d_ext, 4 * (size_t)N));
   if (s->integrator == RT_VAN_LEER) {  // stage-1 intensities and their gradients
     CK(dalloc_bytes(s, &s->d_Ihalf, (size_t)N * RS * s->rsize));
-    CK(dalloc_bytes(s, &s->d_grad, 3 * (size_t)N * RS * s->rsize));
+    CK(dalloc_bytes(s, &s->d_grad, 4 * (size_t)N * RS * s->rsize));
   }
   CK(dalloc_bytes(s, &s->d_cellv, 4 * (size_t)N * s->rsize));
   CK(cudaMemsetAsync(s->d_cellv, 0, 4 * (size_t)N * s->rsize, s->stream));

@@ -32,6 +32,33 @@ __device__ __forceinline__ double rmin(double a, double b) { return fmin(a, b); 
 __device__ __forceinline__ float rmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double rmax(double a, double b) { return fmax(a, b); }
 
+// The stage-1 intensity and its limited gradient of one row position,
+// stored together so that the transport fetches them with one access:
+// IG[(c * RS + q)] = (I, g_x, g_y, g_z).
+template <typename R> struct QV;
+template <> struct QV<float> {
+  float i, x, y, z;
+  __device__ static QV load(const float *p) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    return {v.x, v.y, v.z, v.w};
+  }
+  __device__ void store(float *p) const {
+    *reinterpret_cast<float4 *>(p) = make_float4(i, x, y, z);
+  }
+};
+template <> struct QV<double> {
+  double i, x, y, z;
+  __device__ static QV load(const double *p) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    return {a.x, a.y, b.x, b.y};
+  }
+  __device__ void store(double *p) const {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(i, x);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(y, z);
+  }
+};
+
 // Per warp, a cell's face geometry is staged in shared memory CH slots at a
 // time: recon (x_f - x_c, w_f, x_f - x_nbr', 0), the neighbour index and,
 // for the float transport, the face slot (c A n, A w.n).
@@ -57,7 +84,7 @@ __device__ __forceinline__ void stage_faces(WarpStage<R> &st, const R *__restric
   __syncwarp();
 }
 
-// grad[(c * 3 + d) * RS + q]: limited gradient of the intensity at row
+// IG[c * RS + q] = (I, limited gradient) of the stage-1 intensity at row
 // position q of cell c (lsq[8 c] = the inverse of sum_f w_f r_f r_f^T as
 // xx, xy, xz, yy, yz, zz).  One warp per cell; lane l takes the positions
 // l + 32 i (i < QN).  The limiter factor is the oracle's min over faces
@@ -67,7 +94,7 @@ __device__ __forceinline__ void stage_faces(WarpStage<R> &st, const R *__restric
 template <typename R, int QN>
 __global__ void __launch_bounds__(kThreads) gradient_kernel(
     const int64_t *__restrict__ ptr, const int32_t *__restrict__ nbr, const R *__restrict__ recon,
-    const R *__restrict__ lsq, const R *__restrict__ Ih, R *__restrict__ grad, int64_t n, int A,
+    const R *__restrict__ lsq, const R *__restrict__ Ih, R *__restrict__ IG, int64_t n, int A,
     int RS) {
   __shared__ WarpStage<R> stage[kWarps];
   const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -137,52 +164,48 @@ __global__ void __launch_bounds__(kThreads) gradient_kernel(
       R alpha = 1;
       if (dmax[i] > R(0)) alpha = rmin(alpha, (hi[i] - Ic[i]) / dmax[i]);
       if (dmin[i] < R(0)) alpha = rmin(alpha, (lo[i] - Ic[i]) / dmin[i]);
-      R *o = grad + (size_t)c * 3 * RS + q;
-      o[0] = alpha * gx[i];
-      o[RS] = alpha * gy[i];
-      o[2 * (size_t)RS] = alpha * gz[i];
+      const QV<R> v{Ic[i], alpha * gx[i], alpha * gy[i], alpha * gz[i]};
+      v.store(IG + 4 * ((size_t)c * RS + q));
     }
   }
 }
 
 // I*[c][q] = I[c][q] - dt / V_c sum_f u I_up, I_up reconstructed at the face
-// centre from (Ih, grad) of the upwind cell.  u as the fused step kernel
-// forms it: float from the face slot and the angle's direction, double from
-// the tabulated n_p . s (negated for the antipode); minus A w . n on a moving
-// mesh.  One warp per cell, lane l takes positions l + 32 i (i < QN).
+// centre from IG of the upwind cell.  u as the fused step kernel forms it:
+// float from the face slot and the angle's direction, double from the
+// tabulated n_p . s (negated for the antipode); minus A w . n on a moving
+// mesh.  One warp per cell, lane l takes positions l + 32 i (i < QN); every
+// lane fetches the neighbour's record and selects the upwind value, so the
+// warp does not diverge per face.
 template <typename R, bool MOVING, int QN>
 __global__ void __launch_bounds__(kThreads) recon_transport_kernel(
     const int64_t *__restrict__ ptr, const int32_t *__restrict__ nbr, const SlotF *__restrict__ slotf,
     const double *__restrict__ wface, const double *__restrict__ uface, const R *__restrict__ recon,
     const R *__restrict__ dir, const int32_t *__restrict__ angle_of, const R *__restrict__ inv_vol,
-    const R *__restrict__ I, const R *__restrict__ Ih, const R *__restrict__ grad,
-    R *__restrict__ Istar, int64_t n, int A, int RS, R dt) {
+    const R *__restrict__ I, const R *__restrict__ IG, R *__restrict__ Istar, int64_t n, int A,
+    int RS, R dt) {
   __shared__ WarpStage<R> stage[kWarps];
   const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t c = (int64_t)blockIdx.x * kWarps + w;
   if (c >= n) return;
   WarpStage<R> &st = stage[w];
   const int H = A / 2;
-  const size_t gs = (size_t)RS;
   const int64_t k0 = ptr[c], k1 = ptr[c + 1];
-  R nx[QN], ny[QN], nz[QN], Ihc[QN], gcx[QN], gcy[QN], gcz[QN], acc[QN];
-  int pp[QN];
+  R nx[QN], ny[QN], nz[QN], acc[QN];
+  QV<R> own[QN];
+  int pp[QN], qq[QN];
   bool anti[QN];
 #pragma unroll
   for (int i = 0; i < QN; ++i) {
     const int q = lane + 32 * i;
-    const int a = q < A ? angle_of[q] : 0;
+    qq[i] = q < A ? q : A - 1;  // idle lanes shadow the last position
+    const int a = angle_of[qq[i]];
     anti[i] = a >= H;
     pp[i] = anti[i] ? a - H : a;
     nx[i] = dir[4 * a];
     ny[i] = dir[4 * a + 1];
     nz[i] = dir[4 * a + 2];
-    const int qq = q < A ? q : 0;
-    Ihc[i] = Ih[(size_t)c * RS + qq];
-    const R *gc = grad + (size_t)c * 3 * gs + qq;
-    gcx[i] = gc[0];
-    gcy[i] = gc[gs];
-    gcz[i] = gc[2 * gs];
+    own[i] = QV<R>::load(IG + 4 * ((size_t)c * RS + qq[i]));
     acc[i] = R(0);
   }
   for (int64_t kc = k0; kc < k1; kc += CH) {
@@ -190,30 +213,26 @@ __global__ void __launch_bounds__(kThreads) recon_transport_kernel(
     stage_faces<R>(st, recon, nbr, sizeof(R) == 4 ? slotf : nullptr, kc, cnt, lane);
     for (int t = 0; t < cnt; ++t) {
       const R *g = st.geo[t];
-      const int64_t j = st.nb[t];
-      const R *Ihj = Ih + (size_t)j * RS;
-      const R *gj = grad + (size_t)j * 3 * gs;
+      const R *IGj = IG + 4 * (size_t)st.nb[t] * RS;
       R wk = R(0);
       if (MOVING) wk = sizeof(R) == 4 ? R(st.slot[t].w) : R(wface[kc + t]);
+      SlotF sl{0, 0, 0, 0};
+      if constexpr (sizeof(R) == 4) sl = st.slot[t];
 #pragma unroll
       for (int i = 0; i < QN; ++i) {
-        const int q = lane + 32 * i;
-        if (q < A) {
-          R d;
-          if constexpr (sizeof(R) == 4) {
-            const SlotF sl = st.slot[t];
-            d = fmaf(nx[i], sl.sx, fmaf(ny[i], sl.sy, nz[i] * sl.sz));
-          } else {
-            const R dd = uface[(size_t)(kc + t) * H + pp[i]];
-            d = anti[i] ? -dd : dd;
-          }
-          const R u = MOVING ? d - wk : d;
-          if (positive(u)) {
-            acc[i] += u * (Ihc[i] + (gcx[i] * g[0] + gcy[i] * g[1] + gcz[i] * g[2]));
-          } else if (u < R(0)) {
-            acc[i] += u * (Ihj[q] + (gj[q] * g[4] + gj[gs + q] * g[5] + gj[2 * gs + q] * g[6]));
-          }
+        R d;
+        if constexpr (sizeof(R) == 4) {
+          d = fmaf(nx[i], sl.sx, fmaf(ny[i], sl.sy, nz[i] * sl.sz));
+        } else {
+          const R dd = uface[(size_t)(kc + t) * H + pp[i]];
+          d = anti[i] ? -dd : dd;
         }
+        const R u = MOVING ? d - wk : d;
+        const QV<R> nb = QV<R>::load(IGj + 4 * qq[i]);
+        const R vo = own[i].i + (own[i].x * g[0] + own[i].y * g[1] + own[i].z * g[2]);
+        const R vn = nb.i + (nb.x * g[4] + nb.y * g[5] + nb.z * g[6]);
+        // u = 0 carries no flux: either value times zero
+        acc[i] += u * (positive(u) ? vo : vn);
       }
     }
     __syncwarp();
@@ -232,9 +251,9 @@ template <typename R, int QN> cudaError_t vl_middle_q(rt_state *s, double dt) {
   const int A = s->n_angles, RS = s->row_stride;
   const R *recon = reinterpret_cast<const R *>(s->d_recon);
   const R *Ih = reinterpret_cast<const R *>(s->d_Ihalf);
-  R *grad = reinterpret_cast<R *>(s->d_grad);
+  R *IG = reinterpret_cast<R *>(s->d_grad);
   gradient_kernel<R, QN><<<warp_grid(N), kThreads, 0, s->stream>>>(
-      s->d_ptr, s->d_nbr, recon, reinterpret_cast<const R *>(s->d_lsq), Ih, grad, N, A, RS);
+      s->d_ptr, s->d_nbr, recon, reinterpret_cast<const R *>(s->d_lsq), Ih, IG, N, A, RS);
   const SlotF *slotf = sizeof(R) == 4 ? reinterpret_cast<const SlotF *>(s->d_slot) : nullptr;
   const R *dir = reinterpret_cast<const R *>(s->d_dir);
   const R *iv = reinterpret_cast<const R *>(s->d_inv_vol);
@@ -242,12 +261,12 @@ template <typename R, int QN> cudaError_t vl_middle_q(rt_state *s, double dt) {
   R *Is = reinterpret_cast<R *>(s->d_I[s->cur ^ 1]);
   if (s->moving)
     recon_transport_kernel<R, true, QN><<<warp_grid(N), kThreads, 0, s->stream>>>(
-        s->d_ptr, s->d_nbr, slotf, s->d_wface, s->d_uface, recon, dir, s->d_angle_of, iv, I, Ih,
-        grad, Is, N, A, RS, R(dt));
+        s->d_ptr, s->d_nbr, slotf, s->d_wface, s->d_uface, recon, dir, s->d_angle_of, iv, I, IG, Is,
+        N, A, RS, R(dt));
   else
     recon_transport_kernel<R, false, QN><<<warp_grid(N), kThreads, 0, s->stream>>>(
-        s->d_ptr, s->d_nbr, slotf, s->d_wface, s->d_uface, recon, dir, s->d_angle_of, iv, I, Ih,
-        grad, Is, N, A, RS, R(dt));
+        s->d_ptr, s->d_nbr, slotf, s->d_wface, s->d_uface, recon, dir, s->d_angle_of, iv, I, IG, Is,
+        N, A, RS, R(dt));
   s->launches += 2;
   return cudaGetLastError();
 }

@@ -34,12 +34,12 @@ METRIC = "cell-angle updates/s (transport+implicit source), FP32 vs FP64, % HBM 
 UNIT = "cell-angle updates/s"
 
 # DRAM bytes (read + write) per launch of the step kernels, from one ncu
-# capture each of the 96^3 case (FP32 963.7 MB, FP64 1888.7 MB) scaled to
+# capture each of the 96^3 case (FP32 963.3 MB, FP64 5910.3 MB) scaled to
 # the 128^3 workload by the cell count (traffic grows with the cells
 # processed); valid while the step kernel's device source has the recorded
 # hash.
-NCU_TRAFFIC = {"fp32": 963.662336e6 * 2097152 / 884736, "fp64": 1888.690456e6 * 2097152 / 884736}
-NCU_SOURCE_SHA = "c3eb1efad9ff0f8c"
+NCU_TRAFFIC = {"fp32": 963.252736e6 * 2097152 / 884736, "fp64": 5910.3326e6 * 2097152 / 884736}
+NCU_SOURCE_SHA = "09fbe7ef291b1911"
 # FP64 arithmetic peak of the GPU (dense FMA, from the hardware's nominal
 # figure); the FP64 state is bound by it, not by HBM.
 FP64_PEAK_GFLOPS = 1250.0

@@ -474,11 +474,28 @@ int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state 
   CK(cudaMemsetAsync(s->d_status, 0, sizeof(unsigned), s->stream));
   CK(cudaMemsetAsync(s->d_bad, 0xff, sizeof(unsigned long long), s->stream));
   s->n_rows = 1;
-  // upwind positivity bound
-  CK(rt::launch_positivity(s, s->d_out16));
+  // upwind positivity bound: a float screen over float slots (for double
+  // states a temporary float copy), then the exact double sums of the
+  // candidates
+  rt::SlotF *fslot = reinterpret_cast<rt::SlotF *>(s->d_slot);
+  if (s->precision == RT_FP64) {
+    std::vector<int64_t> p2;
+    std::vector<int32_t> n2;
+    std::vector<rt::SlotF> sf;
+    std::vector<double> w2;
+    std::vector<float> v2;
+    fill_geometry<float>(s, m, slot_of, p2, n2, sf, w2, v2);
+    fslot = nullptr;
+    CK(cudaMalloc(&fslot, sf.size() * sizeof(rt::SlotF)));
+    CK(cudaMemcpy(fslot, sf.data(), sf.size() * sizeof(rt::SlotF), cudaMemcpyHostToDevice));
+  }
   double kmax = 0;
-  CK(cudaMemcpyAsync(&kmax, s->d_out16, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  CK(cudaStreamSynchronize(s->stream));
+  cudaError_t pe = rt::launch_positivity(s, fslot, s->d_out16);
+  if (pe == cudaSuccess)
+    pe = cudaMemcpyAsync(&kmax, s->d_out16, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (pe == cudaSuccess) pe = cudaStreamSynchronize(s->stream);
+  if (s->precision == RT_FP64) cudaFree(fslot);
+  CK(pe);
 #undef CK
   s->dt_max = kmax > 0 ? 1.0 / kmax : INFINITY;
   *out = s;

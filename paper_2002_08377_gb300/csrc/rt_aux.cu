@@ -46,30 +46,58 @@ __device__ __forceinline__ double slot_u(const SlotD &s, const double *wf, int64
   return s.ca * ((x * s.nx + y * s.ny) + z * s.nz) - (wf ? wf[k] : 0.0);
 }
 
-// K_c = max_a (1/V_c) sum_f max(u_fa, 0), max over cells into *kmax (as the
-// bit pattern of a non-negative double, which orders like the value).
+// The upwind positivity bound: K = max over cells c and angles a of
+// (1/V_c) sum_f max(u_fa, 0); kmax holds it as the bit pattern of a
+// non-negative double, which orders like the value.
+// The same u in float from float slots (a screening value, error ~1e-7 of
+// |cbar A| + |A w|).
+__device__ __forceinline__ float slot_u_f(const SlotF &s, const double *, int64_t, float x, float y,
+                                          float z) {
+  return fmaf(x, s.sx, fmaf(y, s.sy, z * s.sz)) - s.w;
+}
+
+// The positivity bound in two passes.  mode 0: the float value of
+// K_c = max_a (1/V_c) sum_f max(u_fa, 0) for every cell, max over cells into
+// *kf (bits of a non-negative float).  mode 1: every (cell, angle) whose
+// float value is within 1e-4 of that maximum is evaluated exactly in double
+// and max-ed into *kmax; the float error (~1e-6 of K)
+// is far inside the margin, so the maximum found is the exact one (the
+// double sum below is the bound's definition, in face order).
 template <typename R>
-__global__ void positivity_kernel(const int64_t *__restrict__ ptr,
-                                  const typename SlotOf<R>::type *__restrict__ slot,
-                                  const double *__restrict__ wface,
-                                  const double *__restrict__ vol, const double *__restrict__ dir,
-                                  int64_t n, int A, unsigned long long *kmax) {
+__global__ void positivity_screen_kernel(const int64_t *__restrict__ ptr,
+                                         const SlotF *__restrict__ fslot,
+                                         const typename SlotOf<R>::type *__restrict__ slot,
+                                         const double *__restrict__ wface,
+                                         const double *__restrict__ vol,
+                                         const double *__restrict__ dir, int64_t n, int A, int mode,
+                                         unsigned *kf, unsigned long long *kmax) {
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  double best = 0.0;
+  float best = 0.0f;
+  const float cut = mode == 1 ? __uint_as_float(*kf) * (1.0f - 1e-4f) : 0.0f;
   if (row < n) {
+    const float iv = (float)(1.0 / vol[row]);
     for (int a = threadIdx.x % 32; a < A; a += 32) {
-      const double x = dir[3 * a], y = dir[3 * a + 1], z = dir[3 * a + 2];
-      double sum = 0.0;
-      for (int64_t k = ptr[row]; k < ptr[row + 1]; ++k) {
-        const double u = slot_u(slot[k], wface, k, x, y, z);
-        if (u > 0.0) sum += u;
+      const float x = (float)dir[3 * a], y = (float)dir[3 * a + 1], z = (float)dir[3 * a + 2];
+      float sum = 0.0f;
+      for (int64_t k = ptr[row]; k < ptr[row + 1]; ++k)
+        sum += fmaxf(slot_u_f(fslot[k], nullptr, k, x, y, z), 0.0f);
+      const float kc = sum * iv;
+      if (mode == 0) {
+        best = fmaxf(best, kc);
+      } else if (kc >= cut) {
+        double exact = 0.0;
+        for (int64_t k = ptr[row]; k < ptr[row + 1]; ++k) {
+          const double u = slot_u(slot[k], wface, k, dir[3 * a], dir[3 * a + 1], dir[3 * a + 2]);
+          if (u > 0.0) exact += u;
+        }
+        atomicMax(kmax, (unsigned long long)__double_as_longlong(exact / vol[row]));
       }
-      best = fmax(best, sum / vol[row]);
     }
   }
-  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
-  if (threadIdx.x % 32 == 0 && row < n)
-    atomicMax(kmax, (unsigned long long)__double_as_longlong(best));
+  if (mode == 0) {
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (threadIdx.x % 32 == 0 && row < n) atomicMax(kf, __float_as_uint(best));
+  }
 }
 
 // Per-cell moments E, F[3], P[6] in double, written in caller order.
@@ -249,20 +277,24 @@ cudaError_t launch_permute_out(rt_state *s, const void *src, void *dst, int stri
   return cudaGetLastError();
 }
 
-cudaError_t launch_positivity(rt_state *s, double *d_kmax) {
-  cudaError_t e = cudaMemsetAsync(d_kmax, 0, sizeof(double), s->stream);
+// d_kmax[0] receives the bound (as a double), d_kmax[1] is scratch.
+// fslot: the face slots in float (the state's own for float states).
+cudaError_t launch_positivity(rt_state *s, const SlotF *fslot, double *d_kmax) {
+  cudaError_t e = cudaMemsetAsync(d_kmax, 0, 2 * sizeof(double), s->stream);
   if (e != cudaSuccess) return e;
-  if (s->precision == RT_FP32)
-    positivity_kernel<float><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
-        s->d_ptr, (const SlotF *)s->d_slot, s->d_wface, s->d_volume, s->d_dir64, s->n_cells,
-        s->n_angles,
-        (unsigned long long *)d_kmax);
-  else
-    positivity_kernel<double><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
-        s->d_ptr, (const SlotD *)s->d_slot, s->d_wface, s->d_volume, s->d_dir64, s->n_cells,
-        s->n_angles,
-        (unsigned long long *)d_kmax);
-  s->launches++;
+  unsigned *kf = reinterpret_cast<unsigned *>(d_kmax + 1);
+  unsigned long long *km = reinterpret_cast<unsigned long long *>(d_kmax);
+  for (int mode = 0; mode < 2; ++mode) {
+    if (s->precision == RT_FP32)
+      positivity_screen_kernel<float><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
+          s->d_ptr, fslot, (const SlotF *)s->d_slot, s->d_wface, s->d_volume, s->d_dir64,
+          s->n_cells, s->n_angles, mode, kf, km);
+    else
+      positivity_screen_kernel<double><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
+          s->d_ptr, fslot, (const SlotD *)s->d_slot, s->d_wface, s->d_volume, s->d_dir64,
+          s->n_cells, s->n_angles, mode, kf, km);
+    s->launches++;
+  }
   return cudaGetLastError();
 }
 

@@ -198,7 +198,7 @@ cudaError_t build_uface(rt_state *s);
 // caller order <-> internal order; the internal rows are `stride` reals apart
 cudaError_t launch_permute_in(rt_state *s, const void *src, void *dst, int stride);
 cudaError_t launch_permute_out(rt_state *s, const void *src, void *dst, int stride);
-cudaError_t launch_positivity(rt_state *s, double *d_kmax);
+cudaError_t launch_positivity(rt_state *s, const SlotF *fslot, double *d_kmax);
 cudaError_t launch_moments(rt_state *s, double *E, double *F, double *P);
 cudaError_t launch_totals(rt_state *s, double *d_out16);
 cudaError_t launch_gas_out(rt_state *s, double *e, double *m, double *ext);

@@ -273,6 +273,20 @@ def test_state_roundtrip():
     assert np.array_equal(g.get_intensity(), I1)
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-14), ("fp32", 1e-6)])
+def test_positivity_limit_matches_oracle(precision, tol):
+    """The upwind positivity limit dt_max = 1 / max_{c,a} (1/V) sum_f max(u, 0)
+    that rt_create computes (a float screen, then the exact double sum of the
+    candidates) equals the oracle's; float states store their slots in
+    float, hence the looser bound there."""
+    prob = randomise(make(n=(9, 7, 8), order=8, cbar=10.0, c=100.0, w=(0.3, -0.2, 0.1)), seed=3)
+    o = oracle.Oracle(prob)
+    g = solver(prob, precision)
+    _, dt_max = g.dt_limits()
+    assert abs(dt_max * o.positivity() - 1.0) < tol
+    g.close()
+
+
 def test_errors_reported():
     prob = make(n=(4, 4, 4), order=4)
     g = solver(prob, "fp64")

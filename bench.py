@@ -47,7 +47,7 @@ FP64_PEAK_GFLOPS = 1250.0
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("rt_step.cu", "rt_step_common.cuh"):
+    for f in ("rt_step.cu", "rt_step_common.cuh", "rt_step_tile.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2002_08377_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -189,6 +189,10 @@ struct StepIO {
   bool src_only, commit;
 };
 cudaError_t launch_step_io(rt_state *s, double dt, const StepIO &io);
+// Transport only (rt_transport.cu), rows `in` -> `out` (stride row_stride):
+// adjoint = false: I* = I - dt/V sum_f u I_up; adjoint = true: the
+// transposed operator, from rows L = dt/V lambda to M^T lambda.
+cudaError_t launch_transport(rt_state *s, double dt, const void *in, void *out, bool adjoint);
 // The van Leer step (rt_recon.cu); leaves I^{n+1} in d_I[cur ^ 1].
 cudaError_t launch_step_vl(rt_state *s, double dt);
 // Double states: fills d_uface (allocates it on first use).

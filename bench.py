@@ -38,8 +38,8 @@ UNIT = "cell-angle updates/s"
 # the 128^3 workload by the cell count (traffic grows with the cells
 # processed); valid while the step kernel's device source has the recorded
 # hash.
-NCU_TRAFFIC = {"fp32": 963.252736e6 * 2097152 / 884736, "fp64": 5910.3326e6 * 2097152 / 884736}
-NCU_SOURCE_SHA = "09fbe7ef291b1911"
+NCU_TRAFFIC = {"fp32": 963.281152e6 * 2097152 / 884736, "fp64": 5907.361232e6 * 2097152 / 884736}
+NCU_SOURCE_SHA = "2349c52b162f0d6d"
 # FP64 arithmetic peak of the GPU (dense FMA, from the hardware's nominal
 # figure); the FP64 state is bound by it, not by HBM.
 FP64_PEAK_GFLOPS = 1250.0
@@ -311,6 +311,43 @@ def e2e_rate(sol, prob, dt, steps):
     return N * A * steps / el, nbytes, nbytes
 
 
+def adjoint_rate(prob, prec, dt, steps, warmup):
+    """Reverse steps through rt_adjoint_step (the solver's call, caller-order
+    device tensors, seeded cotangents): cell-angle reversals per second."""
+    import torch
+    from paper_2002_08377_gb300.solver import RTSolver
+    sol = RTSolver.from_problem(prob, prec)
+    N, A = prob.n_cells, prob.n_angles
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    I = sol.get_intensity(device=True)
+    e, m = sol.gas_device()
+    lI1 = torch.rand(N, A, dtype=sol.tdtype, device="cuda", generator=g)
+    le1 = torch.rand(N, dtype=torch.float64, device="cuda", generator=g)
+    lm1 = torch.rand(N, 3, dtype=torch.float64, device="cuda", generator=g)
+    gP = torch.zeros(N, dtype=torch.float64, device="cuda")
+    gJ = torch.zeros_like(gP)
+    for _ in range(warmup):
+        sol.adjoint_step(dt, I, e, m, lI1, le1, lm1, gP, gJ)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    l0 = sol.launch_count()
+    ev0.record(sol.stream)
+    for _ in range(steps):
+        sol.adjoint_step(dt, I, e, m, lI1, le1, lm1, gP, gJ)
+    ev1.record(sol.stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = sol.launch_count() - l0
+    sol.close()
+    del sol
+    torch.cuda.empty_cache()
+    return {"value": N * A * steps / (ms * 1e-3), "unit": "cell-angle reversals/s",
+            "ms_per_step": ms / steps, "steps": steps, "launches": launches,
+            "dtype": "f32" if prec == "fp32" else "f64"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -321,6 +358,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-vl", action="store_true", help="skip the van Leer leg")
+    ap.add_argument("--no-adj", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--only", choices=["fp32", "fp64"], default=None,
                     help="time one precision only (profiling runs)")
     ap.add_argument("--n", type=int, default=128,
@@ -404,6 +442,17 @@ def main():
         prob.integrator = 0
         torch.cuda.empty_cache()
 
+    adj = None
+    if args.only is None and not args.no_adj:
+        # one reverse step (rt_adjoint_step: forward transport sweep, source
+        # reverse, transposed sweep, caller-order permutes) per timed step
+        adj = {}
+        for prec in ("fp32", "fp64"):
+            k = max(3, args.steps // 10) if prec == "fp32" else 3
+            r = adjoint_rate(prob, prec, dt, k, 2)
+            r["over_forward_step"] = r["ms_per_step"] / results[prec]["ms_per_step"]
+            adj[prec] = r
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, done, el = cpu_oracle_rate(prob, dt, args.cpu_budget)
@@ -429,7 +478,7 @@ def main():
                      "steps": results["fp64"]["steps"], "dtype": "f64",
                      "roofline": results["fp64"]["roofline"],
                      "fp32_over_fp64": r32["value"] / results["fp64"]["value"]},
-            "van_leer": vl}
+            "van_leer": vl, "adjoint": adj}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

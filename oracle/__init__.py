@@ -50,7 +50,7 @@ class _Problem(ctypes.Structure):
                 ("kind", ctypes.c_void_p), ("tau", ctypes.c_void_p),
                 ("emit_rate", ctypes.c_void_p), ("I_src", ctypes.c_void_p),
                 ("bc_row", ctypes.c_void_p), ("I0", ctypes.c_void_p),
-                ("face_offset", ctypes.c_void_p)]
+                ("face_offset", ctypes.c_void_p), ("boost_all_orders", ctypes.c_int32)]
 
 
 def lib():
@@ -151,6 +151,7 @@ class Oracle:
         p.bc_row = arr("bcrow", prob.bc_row, np.int32)
         p.I0 = arr("I0", prob.I0)
         p.face_offset = arr("foff", m.face_offset())
+        p.boost_all_orders = int(getattr(prob, "boost", 0))
         self.p = p
         self.integrator = int(getattr(prob, "integrator", 0))
         self.I = _f64(prob.initial_intensity(np.float64))
@@ -268,10 +269,13 @@ class Oracle:
         lI1, le1, lm1 = _f64(lI1), _f64(le1), _f64(lm1)
         lI, le, lm = np.empty_like(I), np.empty_like(e), np.empty_like(m)
         work = np.empty(2 * I.size)
-        lib().orc_adjoint_step(ctypes.byref(self.p), float(dt), I.ctypes.data, e.ctypes.data,
-                               m.ctypes.data, lI1.ctypes.data, le1.ctypes.data, lm1.ctypes.data,
-                               lI.ctypes.data, le.ctypes.data, lm.ctypes.data, gP.ctypes.data,
-                               gJ.ctypes.data, work.ctypes.data)
+        st = lib().orc_adjoint_step(ctypes.byref(self.p), float(dt), I.ctypes.data, e.ctypes.data,
+                                    m.ctypes.data, lI1.ctypes.data, le1.ctypes.data,
+                                    lm1.ctypes.data, lI.ctypes.data, le.ctypes.data,
+                                    lm.ctypes.data, gP.ctypes.data, gJ.ctypes.data,
+                                    work.ctypes.data)
+        if st != ORC_OK:
+            raise ValueError("the oracle's adjoint reverses the first-order transformation only")
         return lI, le, lm
 
     def temperature(self):

@@ -12,8 +12,10 @@
  * function): intensities are stored as energy density per steradian, so an
  * isotropic equilibrium field has I = a T^4 / (4 pi); E_r = 4 pi sum_a w_a I_a,
  * F_r = 4 pi c sum_a w_a n_a I_a; the weights sum to one.  The frame velocity
- * of a cell is v = (rho v) / rho at the start of the source step, and the
- * Lorentz factor is taken to first order in v/c (gamma = 1).
+ * of a cell is v = (rho v) / rho at the start of the source step.  The
+ * frequency ratio of Sec. 2.3, Gamma_a = gamma (1 - v . n_a / c), is taken
+ * to first order in v/c (gamma = 1) unless the problem asks for the
+ * transformation to all orders (boost_all_orders, gamma = (1 - v^2/c^2)^-1/2).
  *
  * Every function below is pinned by the CPU tests against something other
  * than itself: closed forms, conservation invariants, brute force on tiny
@@ -28,6 +30,7 @@
 #include <string.h>
 
 #define ORC_OK 0
+#define ORC_ERR_ARG (-1)
 #define ORC_ERR_NONCONV (-6)
 #define ORC_ERR_NONFINITE (-7)
 
@@ -64,6 +67,10 @@ typedef struct {
    * face centroid relative to each cell's centroid, j' the image of j that
    * meets i across f; [Nf][2][3], may be NULL when no reconstruction is used */
   const double *face_offset;
+  /* 1: Gamma_a = gamma (1 - v . n_a / c) with the Lorentz factor gamma of the
+   * frame velocity (the comoving transformation to all orders, Sec. 2.3);
+   * 0: gamma = 1 (first order in v/c) */
+  int32_t boost_all_orders;
 } orc_problem;
 
 /* ------------------------------------------------------------------------
@@ -284,16 +291,25 @@ double orc_ferrari(double alpha, double beta, double g) {
  *     with the differences summed angle by angle (cell_moment_change).
  * The gas temperature is recomputed from the updated energy next step.
  * --------------------------------------------------------------------- */
+/* The Lorentz factor in Gamma_a = gamma (1 - v . n_a / c) (Sec. 2.3): 1 for
+ * the first-order transformation. */
+static double frame_gamma(const orc_problem *p, const double *v) {
+  if (!p->boost_all_orders) return 1.0;
+  const double b2 = (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / (p->c * p->c);
+  return 1.0 / sqrt(1.0 - b2);
+}
+
 static int source_interior(const orc_problem *p, int64_t c, double dt, const double *Is,
                            double *In, double *e, double *m, int *iters) {
   const int A = p->n_angles;
   const double rho = p->rho[c], kP = p->kappa_P[c], kJ = p->kappa_J[c], kS = p->kappa_s[c];
   double v[3] = {m[0] / rho, m[1] / rho, m[2] / rho};
+  const double gam = frame_gamma(p, v);
   double G[A], wc[A], Ic[A];
   double norm = 0.0;
   for (int a = 0; a < A; ++a) {
     const double *n = p->dir + 3 * a;
-    G[a] = 1.0 - (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / p->c;
+    G[a] = gam * (1.0 - (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / p->c);
     double G2 = G[a] * G[a];
     Ic[a] = G2 * G2 * Is[a];
     wc[a] = p->wt[a] / G2;
@@ -355,10 +371,11 @@ static void source_emitter(const orc_problem *p, int64_t c, double dt, const dou
   const int A = p->n_angles;
   const double rho = p->rho[c];
   double v[3] = {m[0] / rho, m[1] / rho, m[2] / rho};
+  const double gam = frame_gamma(p, v);
   double dE, dF[3];
   for (int a = 0; a < A; ++a) {
     const double *n = p->dir + 3 * a;
-    double G = 1.0 - (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / p->c;
+    double G = gam * (1.0 - (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / p->c);
     double G4 = G * G * G * G;
     double y = dt * p->cbar * G * p->emit_rate[c];
     In[a] = ((G4 * Is[a] + y * p->I_src[c]) / (1.0 + y)) / G4;
@@ -706,6 +723,7 @@ int orc_adjoint_step(const orc_problem *p, double dt, const double *I, const dou
                      double *lI, double *le, double *lm, double *gP, double *gJ, double *work) {
   const int A = p->n_angles;
   double *Is = work, *lIs = work + p->n_cells * A;
+  if (p->boost_all_orders) return ORC_ERR_ARG; /* reverses the first-order transformation only */
   orc_transport(p, dt, I, Is);
 #pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < p->n_cells; ++c) {

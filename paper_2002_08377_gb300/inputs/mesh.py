@@ -87,6 +87,26 @@ class Mesh:
         off[:, 1] = self.face_centroid - xj
         return off
 
+    def face_velocity(self, w_gen):
+        """[Nf, 3] face velocities from the velocities w_gen [N, 3] of the
+        mesh-generating points (the face-velocity equation of Sec. 2.2): the
+        mean velocity of the face's two generators, plus the velocity along
+        r_j - r_i that the relative motion of the generators gives the point
+        of the face at its centroid x_f,
+          w_f = [(w_i - w_j) . (x_f - (r_i + r_j) / 2) / |r_j - r_i|] (r_j - r_i) / |r_j - r_i|
+                + (w_i + w_j) / 2,
+        with r_j the periodic image of generator j that faces i (x_f is in
+        cell i's frame)."""
+        w_gen = np.asarray(w_gen, np.float64)
+        i, j = self.face_cells[:, 0], self.face_cells[:, 1]
+        ri = self.points[i]
+        rj = self.points[j] + self.face_shift.astype(np.float64) * self.box
+        d = rj - ri
+        L = np.linalg.norm(d, axis=1)
+        e = d / L[:, None]
+        s = np.sum((w_gen[i] - w_gen[j]) * (self.face_centroid - 0.5 * (ri + rj)), axis=1) / L
+        return np.ascontiguousarray(s[:, None] * e + 0.5 * (w_gen[i] + w_gen[j]))
+
     def lattice_index(self):
         """(ix, iy, iz) lattice coordinates of every cell."""
         nx, ny, nz = self.n

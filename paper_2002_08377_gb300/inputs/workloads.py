@@ -68,6 +68,7 @@ class Problem:
     q0: np.ndarray            # [A] initial angular profile (I = J0 x q0)
     extra: dict = field(default_factory=dict)
     integrator: int = 0       # 0 first-order upwind step, 1 van Leer with limited linear reconstruction
+    boost: int = 0            # 1: the comoving transformation to all orders in v/c (Gamma with gamma)
 
     @property
     def n_cells(self):

@@ -128,13 +128,18 @@ typedef enum { RT_FIRST_ORDER = 0, RT_VAN_LEER = 1 } rt_integrator;
  * speed of light of the transport, c the true one (enters the gas coupling
  * and the moments).  r_gas = k_B / (mu m_p); c_v = r_gas / (gamma_gas - 1).
  * cfl scales the Courant step dt = cfl * min V^(1/3) / (cbar + |w|).
- * newton_max_iter <= 0 selects 64. */
+ * newton_max_iter <= 0 selects 64.  boost selects the frequency ratio of the
+ * comoving transformation (Sec. 2.3), Gamma_a = gamma (1 - v . n_a / c):
+ * 0 takes gamma = 1 (first order in v/c), 1 the Lorentz factor
+ * gamma = (1 - v^2 / c^2)^(-1/2) of the cell's frame velocity (all orders;
+ * every cell must then have |v| < c).  rt_adjoint_step reverses boost = 0
+ * states only. */
 typedef struct {
   double cbar, c, a_rad, gamma_gas, r_gas, cfl;
   int32_t precision;       /* rt_precision */
   int32_t newton_max_iter;
   int32_t integrator;      /* rt_integrator */
-  int32_t reserved;        /* 0 */
+  int32_t boost;           /* 0 or 1, see above */
 } rt_params;
 
 /* Validates and copies the mesh to the device, orders cells for locality,

@@ -353,6 +353,7 @@ int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state 
   if (!(p->cbar > 0) || !(p->c > 0) || !(p->a_rad >= 0) || !(p->gamma_gas > 1) ||
       !(p->r_gas > 0) || !(p->cfl > 0) || (p->precision != RT_FP32 && p->precision != RT_FP64) ||
       (p->integrator != RT_FIRST_ORDER && p->integrator != RT_VAN_LEER) ||
+      (p->boost != 0 && p->boost != 1) ||
       (p->integrator == RT_VAN_LEER && !m->face_offset))
     return bail(RT_ERR_ARG);
   s->params = *p;
@@ -738,6 +739,9 @@ int rt_adjoint_step(rt_state *s, double dt, const void *I_n, const double *e_n, 
   if (!s->gas_set) return fail(s, RT_ERR_STATE, "rt_set_gas must be called before the adjoint");
   if (s->integrator != RT_FIRST_ORDER)
     return fail(s, RT_ERR_STATE, "rt_adjoint_step reverses the first-order step only");
+  if (s->params.boost)
+    return fail(s, RT_ERR_STATE,
+                "rt_adjoint_step reverses the first-order comoving transformation only");
   if (!I_n || !e_n || !m_n || !lam_I1 || !lam_e1 || !lam_m1 || !lam_I || !lam_e || !lam_m ||
       !grad_kappa_P || !grad_kappa_J)
     return fail(s, RT_ERR_ARG, "rt_adjoint_step: NULL argument");

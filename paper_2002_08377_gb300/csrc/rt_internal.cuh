@@ -88,6 +88,7 @@ template <typename R> struct StepArgs {
   int32_t newton_max_iter;
   int32_t src_only;         // 1: I_in holds I* already (no transport)
   int32_t commit;           // 0: the gas update is discarded (van Leer stage 1)
+  int32_t boost;            // 1: Gamma = gamma (1 -+ v.n/c) with the Lorentz factor gamma
   unsigned *status;
   unsigned long long *bad_cell;
 };

@@ -50,6 +50,15 @@ template <typename R> struct Shared {
   unsigned bad[CPB];
 };
 
+// The Lorentz factor in Gamma = gamma (1 -+ v.n / c) (Sec. 2.3) of a cell
+// with v / c = (bx, by, bz): 1 for the first-order transformation, else
+// (1 - v^2 / c^2)^(-1/2).
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
+template <typename R> __device__ __forceinline__ R frame_gamma(int boost, R bx, R by, R bz) {
+  return boost ? rsqrt_r(R(1) - fma(bx, bx, fma(by, by, bz * bz))) : R(1);
+}
+
 // Temperature quartic of one interior cell and its emission term
 // q = dt cbar rho (kP B + kS J~).  With w~ normalised, x_a = dt cbar rho
 // (kJ + kS) Gamma_a and the sums S_I, S_G of Eq. (Jcom), S_1 = sum w~ / (1 + x):
@@ -178,7 +187,12 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
 
   // comoving frame (first order in v/c): Gamma = 1 -+ v.n / c, and the
   // angular sums of Eq. (Jcom): w~ = w / Gamma^2 (normalised by their sum),
-  // S_I = sum w~ Gamma^4 I* / (1 + x Gamma), S_G = sum w~ Gamma / (1 + x Gamma)
+  // S_I = sum w~ Gamma^4 I* / (1 + x Gamma), S_G = sum w~ Gamma / (1 + x Gamma).
+  // To all orders Gamma = gamma G with G = 1 -+ v.n / c: the weights'
+  // normalisation cancels gamma^2, so gamma enters only per cell -- x = (xs
+  // gamma) G, S_I -> gamma^4 S_I, S_G -> gamma S_G (S_1 unchanged) and, in
+  // phase C, q -> q / gamma^3 (emitters: rate gamma, source / gamma^4).
+  // With gamma = 1 these scalings are exact.
   const int kind = a.kind[c];
   const R icr = a.inv_c_r;
   const R vxc = a.cellv[4 * c] * icr, vyc = a.cellv[4 * c + 1] * icr,
@@ -195,6 +209,7 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   } else {
     xs = a.dt_cbar_r * R(a.gs[c].rkJ + a.gs[c].rkS);
   }
+  if (a.boost) xs *= frame_gamma(a.boost, vxc, vyc, vzc);
   const V *W2 = reinterpret_cast<const V *>(a.wt2);  // (w_p, w_{p+H})
   const V one = mk(R(1), R(1)), XS = mk(xs, xs);
   // Gamma = (1 - bn, 1 + bn) for the pair, bn = v . n_p / c; the directions
@@ -217,6 +232,11 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   sI = cell_sum(sI);
   sG = cell_sum(sG);
   s1 = cell_sum(s1);
+  if (a.boost) {
+    const R g = frame_gamma(a.boost, vxc, vyc, vzc), g2 = g * g;
+    sI *= g2 * g2;
+    sG *= g;
+  }
 
   // ---------------- phase B: temperature quartic
   R q = 0;           // dt cbar rho (kP B + kS J~) of an interior cell
@@ -274,8 +294,17 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
         const double2 ax = a.aux[c];
         xx = R(a.dt * a.cbar * ax.x);
         qq = xx * R(ax.y);
+        if (a.boost) {
+          const R g = frame_gamma(a.boost, vxc, vyc, vzc), g2 = g * g;
+          xx *= g;
+          qq = xx * R(ax.y) / (g2 * g2);
+        }
       } else {
         qq = q;
+        if (a.boost) {
+          const R g = frame_gamma(a.boost, vxc, vyc, vzc);
+          qq = q / (g * g * g);
+        }
       }
       const V XX = mk(xx, xx), QQ = mk(qq, qq);
 #pragma unroll
@@ -418,6 +447,7 @@ cudaError_t launch_t(rt_state *s, double dt, const StepIO &io) {
   a.I_out = reinterpret_cast<R *>(io.out);
   a.src_only = io.src_only ? 1 : 0;
   a.commit = io.commit ? 1 : 0;
+  a.boost = s->params.boost;
   a.dt = dt;
   a.dt_r = R(dt);
   a.dt_cbar_r = R(dt * s->params.cbar);

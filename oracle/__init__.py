@@ -50,7 +50,8 @@ class _Problem(ctypes.Structure):
                 ("kind", ctypes.c_void_p), ("tau", ctypes.c_void_p),
                 ("emit_rate", ctypes.c_void_p), ("I_src", ctypes.c_void_p),
                 ("bc_row", ctypes.c_void_p), ("I0", ctypes.c_void_p),
-                ("face_offset", ctypes.c_void_p), ("boost_all_orders", ctypes.c_int32)]
+                ("face_offset", ctypes.c_void_p), ("boost_all_orders", ctypes.c_int32),
+                ("gcl", ctypes.c_int32)]
 
 
 def lib():
@@ -61,6 +62,7 @@ def lib():
         P = ctypes.POINTER(_Problem)
         vp, d, i = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
         L.orc_transport.argtypes = [P, d, vp, vp]
+        L.orc_gcl_volumes.argtypes = [P, d, vp]
         L.orc_moments.argtypes = [P, vp, vp, vp, vp]
         L.orc_newton.argtypes = [d, d, d, i, ctypes.POINTER(d), ctypes.POINTER(i)]
         L.orc_newton.restype = i
@@ -128,7 +130,10 @@ class Oracle:
         p = _Problem()
         p.n_cells, p.n_faces, p.n_angles = self.N, m.n_faces, self.A
         p.newton_max_iter = newton_max_iter
-        p.cell_volume = arr("vol", m.cell_volume)
+        # the oracle's own copy: with the geometric conservation law it evolves
+        self.vol = np.array(m.cell_volume, dtype=np.float64, copy=True)
+        self._vol_next = np.empty_like(self.vol)
+        p.cell_volume = self.vol.ctypes.data
         p.face_cells = arr("fc", m.face_cells, np.int32)
         p.face_area = arr("fa", m.face_area)
         p.face_normal = arr("fn", m.face_normal)
@@ -152,6 +157,7 @@ class Oracle:
         p.I0 = arr("I0", prob.I0)
         p.face_offset = arr("foff", m.face_offset())
         p.boost_all_orders = int(getattr(prob, "boost", 0))
+        p.gcl = int(getattr(prob, "gcl", 0))
         self.p = p
         self.integrator = int(getattr(prob, "integrator", 0))
         self.I = _f64(prob.initial_intensity(np.float64))
@@ -183,6 +189,8 @@ class Oracle:
         """One step with the problem's integrator (first-order upwind, or
         van Leer with limited linear reconstruction)."""
         it = ctypes.c_int()
+        if self.integrator == 1 and self.p.gcl:
+            raise ValueError("the van Leer step is not built for changing cell volumes")
         if self.integrator == 1:
             if not hasattr(self, "_half"):
                 self._half = np.empty_like(self.I)
@@ -193,9 +201,13 @@ class Oracle:
                                    self.ext.ctypes.data, ctypes.byref(it))
             self.last_iters = it.value
             return st
+        if self.p.gcl:
+            lib().orc_gcl_volumes(ctypes.byref(self.p), float(dt), self._vol_next.ctypes.data)
         st = lib().orc_step(ctypes.byref(self.p), float(dt), self.I.ctypes.data,
                             self.work.ctypes.data, self.e.ctypes.data, self.m.ctypes.data,
                             self.ext.ctypes.data, ctypes.byref(it))
+        if self.p.gcl:
+            self.vol[:] = self._vol_next  # V^{n+1} becomes the volume of the next step
         self.last_iters = it.value
         return st
 
@@ -275,7 +287,8 @@ class Oracle:
                                     lm.ctypes.data, gP.ctypes.data, gJ.ctypes.data,
                                     work.ctypes.data)
         if st != ORC_OK:
-            raise ValueError("the oracle's adjoint reverses the first-order transformation only")
+            raise ValueError("the oracle's adjoint reverses the first-order transformation on "
+                             "fixed cell volumes only")
         return lI, le, lm
 
     def temperature(self):

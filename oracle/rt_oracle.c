@@ -71,6 +71,10 @@ typedef struct {
    * frame velocity (the comoving transformation to all orders, Sec. 2.3);
    * 0: gamma = 1 (first order in v/c) */
   int32_t boost_all_orders;
+  /* 1: the cells' volumes change with the face velocities by the discrete
+   * geometric conservation law (see orc_gcl_volumes) and the transport takes
+   * the conservative moving-cell form; cell_volume holds V^n */
+  int32_t gcl;
 } orc_problem;
 
 /* ------------------------------------------------------------------------
@@ -96,12 +100,41 @@ static inline void face_side(const orc_problem *p, int64_t c, int32_t e, int64_t
   (void)c;
 }
 
-/* Cells [c0, c1) only; arrays are indexed by global cell number. */
+/* Rate of change of the volume of cell c, sum_f A_f w_f . n_f (n_f outward),
+ * over the cell's faces in list order: with it the discrete geometric
+ * conservation law V^{n+1} = V^n + dt sum_f A_f w_f . n_f keeps a uniform
+ * field uniform on a moving mesh (Sec. 2.2: the flux through a moving face
+ * is (cbar n_a - w) . n_f A I, so a uniform I loses dt I sum_f A (cbar n_a - w)
+ * . n_f = -dt I sum_f A w . n_f, which the volume change absorbs). */
+static double gcl_rate(const orc_problem *p, int64_t c) {
+  double r = 0.0;
+  if (!p->face_w) return 0.0;
+  for (int64_t k = p->cell_face_ptr[c]; k < p->cell_face_ptr[c + 1]; ++k) {
+    int64_t f, nbr;
+    double sgn;
+    face_side(p, c, p->cell_face_idx[k], &f, &sgn, &nbr);
+    const double *nf = p->face_normal + 3 * f, *w = p->face_w + 3 * f;
+    r += p->face_area[f] * (sgn * (w[0] * nf[0] + w[1] * nf[1] + w[2] * nf[2]));
+  }
+  return r;
+}
+
+/* V^{n+1} of every cell (the discrete geometric conservation law). */
+void orc_gcl_volumes(const orc_problem *p, double dt, double *V_next) {
+  for (int64_t c = 0; c < p->n_cells; ++c) V_next[c] = p->cell_volume[c] + dt * gcl_rate(p, c);
+}
+
+/* Cells [c0, c1) only; arrays are indexed by global cell number.  With the
+ * geometric conservation law (p->gcl) the update is the conservative form
+ * for a cell whose volume goes from V^n to V^{n+1} during the step:
+ *   V^{n+1} I*_ca = V^n I_ca - dt sum_f u_fa I_up. */
 void orc_transport_range(const orc_problem *p, double dt, const double *I, double *Istar,
                          int64_t c0, int64_t c1) {
   const int A = p->n_angles;
 #pragma omp parallel for schedule(static)
   for (int64_t c = c0; c < c1; ++c) {
+    const double V = p->cell_volume[c];
+    const double V1 = p->gcl ? V + dt * gcl_rate(p, c) : V;
     for (int a = 0; a < A; ++a) {
       const double *na = p->dir + 3 * a;
       double acc = 0.0;
@@ -123,7 +156,10 @@ void orc_transport_range(const orc_problem *p, double dt, const double *I, doubl
         else if (u < 0.0)
           acc += u * I[nbr * A + a];
       }
-      Istar[c * A + a] = I[c * A + a] - dt / p->cell_volume[c] * acc;
+      if (p->gcl)
+        Istar[c * A + a] = (V * I[c * A + a] - dt * acc) / V1;
+      else
+        Istar[c * A + a] = I[c * A + a] - dt / V * acc;
     }
   }
 }
@@ -723,7 +759,8 @@ int orc_adjoint_step(const orc_problem *p, double dt, const double *I, const dou
                      double *lI, double *le, double *lm, double *gP, double *gJ, double *work) {
   const int A = p->n_angles;
   double *Is = work, *lIs = work + p->n_cells * A;
-  if (p->boost_all_orders) return ORC_ERR_ARG; /* reverses the first-order transformation only */
+  /* reverses the first-order transformation on a mesh of fixed volumes only */
+  if (p->boost_all_orders || p->gcl) return ORC_ERR_ARG;
   orc_transport(p, dt, I, Is);
 #pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < p->n_cells; ++c) {

@@ -69,6 +69,7 @@ class Problem:
     extra: dict = field(default_factory=dict)
     integrator: int = 0       # 0 first-order upwind step, 1 van Leer with limited linear reconstruction
     boost: int = 0            # 1: the comoving transformation to all orders in v/c (Gamma with gamma)
+    gcl: int = 0              # 1: cell volumes follow the face velocities (geometric conservation law)
 
     @property
     def n_cells(self):

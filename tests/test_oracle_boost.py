@@ -83,32 +83,3 @@ def test_adjoint_refuses_the_all_orders_transformation():
     with pytest.raises(ValueError):
         o.adjoint_step(0.01, o.I, o.e, o.m, np.ones((N, A)), z, np.zeros((N, 3)), z.copy(), z.copy())
 
-
-# ---------------------------------------------------------------- face velocity (Sec. 2.2)
-def test_face_velocity_of_rigid_motion_and_expansion():
-    """For generators moving with w(r) = b + Omega x r + lambda r (a rigid
-    motion plus uniform expansion) the tessellation moves with the same
-    field, so the normal velocity of every face at its centroid is
-    w(x_f) . n_f; the face-velocity formula gives exactly that (faces that do
-    not cross the periodic boundary, where the field is continuous).  A
-    uniform field gives w_f = w on every face."""
-    from paper_2002_08377_gb300.inputs import build_mesh
-    m = build_mesh((6, 5, 7), jitter=0.25, seed=5)
-    rng = np.random.default_rng(8)
-    b, Om, lam = rng.standard_normal(3), rng.standard_normal(3), 0.37
-
-    def field(r):
-        return b + np.cross(Om, r) + lam * r
-
-    wf = m.face_velocity(field(m.points))
-    inner = ~np.any(m.face_shift != 0, axis=1)
-    assert inner.sum() > 100
-    lhs = np.sum(wf * m.face_normal, axis=1)[inner]
-    rhs = np.sum(field(m.face_centroid) * m.face_normal, axis=1)[inner]
-    assert np.abs(lhs - rhs).max() < 1e-12 * np.abs(rhs).max()
-    # the correction term matters: the mean of the generators alone is off
-    mean = 0.5 * (field(m.points[m.face_cells[:, 0]]) + field(m.points[m.face_cells[:, 1]]))
-    off = np.abs(np.sum(mean * m.face_normal, axis=1)[inner] - rhs).max()
-    assert off > 1e-3 * np.abs(rhs).max()
-    wu = m.face_velocity(np.broadcast_to(b, (m.n_cells, 3)))
-    assert np.abs(wu - b).max() < 1e-14 * np.abs(b).max()

@@ -133,13 +133,26 @@ typedef enum { RT_FIRST_ORDER = 0, RT_VAN_LEER = 1 } rt_integrator;
  * 0 takes gamma = 1 (first order in v/c), 1 the Lorentz factor
  * gamma = (1 - v^2 / c^2)^(-1/2) of the cell's frame velocity (all orders;
  * every cell must then have |v| < c).  rt_adjoint_step reverses boost = 0
- * states only. */
+ * states only.
+ * gcl = 1 lets the cell volumes follow the face velocities by the geometric
+ * conservation law: every step takes V^{n+1} = V^n + dt sum_f A_f w_f . n_f
+ * (faces in list order) and the conservative moving-cell transport
+ * V^{n+1} I* = V^n I - dt sum_f u I_up, so a uniform field stays uniform on
+ * any moving mesh.  The faces (areas, normals, w) stay the state's; the gas
+ * density is not changed.  The upwind positivity limit then changes with the
+ * volumes: rt_step checks dt against the creation limit on the host and every
+ * cell against its current volume on the device (RT_ERR_CFL, latched like
+ * the other per-cell failures).  rt_totals, rt_get_state and rt_set_state
+ * use and keep the current volumes.  gcl = 1 needs RT_FIRST_ORDER;
+ * rt_adjoint_step refuses gcl states. */
 typedef struct {
   double cbar, c, a_rad, gamma_gas, r_gas, cfl;
   int32_t precision;       /* rt_precision */
   int32_t newton_max_iter;
   int32_t integrator;      /* rt_integrator */
   int32_t boost;           /* 0 or 1, see above */
+  int32_t gcl;             /* 0 or 1, see above */
+  int32_t reserved;        /* 0 */
 } rt_params;
 
 /* Validates and copies the mesh to the device, orders cells for locality,

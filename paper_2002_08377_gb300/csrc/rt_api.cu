@@ -332,6 +332,12 @@ int sync_status(rt_state *s) {
     snprintf(buf, sizeof buf, "non-finite intensity or temperature (first cell %lld)", cell);
     return fail(s, RT_ERR_NONFINITE, buf);
   }
+  if (st & rt::ST_CFL) {
+    snprintf(buf, sizeof buf,
+             "dt exceeds the upwind positivity limit of a cell's current volume (first cell %lld)",
+             cell);
+    return fail(s, RT_ERR_CFL, buf);
+  }
   snprintf(buf, sizeof buf, "temperature Newton iteration did not converge (first cell %lld)", cell);
   return fail(s, RT_ERR_NONCONV, buf);
 }
@@ -353,7 +359,8 @@ int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state 
   if (!(p->cbar > 0) || !(p->c > 0) || !(p->a_rad >= 0) || !(p->gamma_gas > 1) ||
       !(p->r_gas > 0) || !(p->cfl > 0) || (p->precision != RT_FP32 && p->precision != RT_FP64) ||
       (p->integrator != RT_FIRST_ORDER && p->integrator != RT_VAN_LEER) ||
-      (p->boost != 0 && p->boost != 1) ||
+      (p->boost != 0 && p->boost != 1) || (p->gcl != 0 && p->gcl != 1) ||
+      (p->gcl && p->integrator != RT_FIRST_ORDER) ||
       (p->integrator == RT_VAN_LEER && !m->face_offset))
     return bail(RT_ERR_ARG);
   s->params = *p;
@@ -490,8 +497,28 @@ int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state 
     CK(cudaMalloc(&fslot, sf.size() * sizeof(rt::SlotF)));
     CK(cudaMemcpy(fslot, sf.data(), sf.size() * sizeof(rt::SlotF), cudaMemcpyHostToDevice));
   }
+  if (p->gcl) {
+    // geometric conservation law: sum_f A_f w_f . n_f per cell (outward
+    // normals, faces in list order), and the per-cell factor of the
+    // positivity limit that the step checks against the current volume
+    std::vector<double> rate(N, 0.0);
+    for (int64_t ic = 0; ic < N && m->face_w; ++ic) {
+      const int64_t c = s->cell_of[ic];
+      double r = 0.0;
+      for (int64_t k = m->cell_face_ptr[c]; k < m->cell_face_ptr[c + 1]; ++k) {
+        const int32_t e = m->cell_face_idx[k];
+        const int64_t f = e >= 0 ? e : -(int64_t)e - 1;
+        const double sgn = e >= 0 ? 1.0 : -1.0;
+        const double *w = m->face_w + 3 * f, *nf = m->face_normal + 3 * f;
+        r += m->face_area[f] * (sgn * (w[0] * nf[0] + w[1] * nf[1] + w[2] * nf[2]));
+      }
+      rate[ic] = r;
+    }
+    CK(upload(s, &s->d_gcl_rate, rate));
+    CK(dalloc(s, &s->d_gcl_kv, N));
+  }
   double kmax = 0;
-  cudaError_t pe = rt::launch_positivity(s, fslot, s->d_out16);
+  cudaError_t pe = rt::launch_positivity(s, fslot, s->d_out16, s->d_gcl_kv);
   if (pe == cudaSuccess)
     pe = cudaMemcpyAsync(&kmax, s->d_out16, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (pe == cudaSuccess) pe = cudaStreamSynchronize(s->stream);
@@ -742,6 +769,8 @@ int rt_adjoint_step(rt_state *s, double dt, const void *I_n, const double *e_n, 
   if (s->params.boost)
     return fail(s, RT_ERR_STATE,
                 "rt_adjoint_step reverses the first-order comoving transformation only");
+  if (s->params.gcl)
+    return fail(s, RT_ERR_STATE, "rt_adjoint_step reverses steps on fixed cell volumes only");
   if (!I_n || !e_n || !m_n || !lam_I1 || !lam_e1 || !lam_m1 || !lam_I || !lam_e || !lam_m ||
       !grad_kappa_P || !grad_kappa_J)
     return fail(s, RT_ERR_ARG, "rt_adjoint_step: NULL argument");
@@ -790,14 +819,15 @@ int rt_get_state(rt_state *s, void *buf, size_t *bytes) {
   if (!s || !bytes) return RT_ERR_ARG;
   const int64_t N = s->n_cells;
   const size_t nI = (size_t)N * s->row_stride * s->rsize;  // internal rows with padding
-  const size_t need = 64 + nI + sizeof(rt::GasDyn) * N + 32 * (size_t)N;
+  const size_t nV = s->params.gcl ? sizeof(double) * N : 0;   // the evolved volumes
+  const size_t need = 64 + nI + sizeof(rt::GasDyn) * N + 32 * (size_t)N + nV;
   if (!buf) {
     *bytes = need;
     return RT_OK;
   }
   if (*bytes < need) return fail(s, RT_ERR_ARG, "rt_get_state: buffer too small");
   char *b = (char *)buf;
-  int64_t hdr[8] = {0x52544742, N, s->n_angles, s->precision, (int64_t)nI, 0, 0, 0};
+  int64_t hdr[8] = {0x52544742, N, s->n_angles, s->precision, (int64_t)nI, s->params.gcl, 0, 0};
   std::memcpy(b, hdr, 64);
   // internal order is fine: the state is restored into the same mesh
   RT_CUDA(s, cudaMemcpyAsync(b + 64, s->d_I[s->cur], nI, cudaMemcpyDeviceToHost, s->stream));
@@ -805,6 +835,9 @@ int rt_get_state(rt_state *s, void *buf, size_t *bytes) {
                              s->stream));
   RT_CUDA(s, cudaMemcpyAsync(b + 64 + nI + sizeof(rt::GasDyn) * N, s->d_ext, 32 * (size_t)N,
                              cudaMemcpyDeviceToHost, s->stream));
+  if (nV)
+    RT_CUDA(s, cudaMemcpyAsync(b + 64 + nI + sizeof(rt::GasDyn) * N + 32 * (size_t)N, s->d_volume,
+                               nV, cudaMemcpyDeviceToHost, s->stream));
   RT_CUDA(s, cudaStreamSynchronize(s->stream));
   *bytes = need;
   return RT_OK;
@@ -814,12 +847,13 @@ int rt_set_state(rt_state *s, const void *buf, size_t bytes) {
   if (!s || !buf) return RT_ERR_ARG;
   const int64_t N = s->n_cells;
   const size_t nI = (size_t)N * s->row_stride * s->rsize;
-  const size_t need = 64 + nI + sizeof(rt::GasDyn) * N + 32 * (size_t)N;
+  const size_t nV = s->params.gcl ? sizeof(double) * N : 0;
+  const size_t need = 64 + nI + sizeof(rt::GasDyn) * N + 32 * (size_t)N + nV;
   int64_t hdr[8];
   if (bytes < need) return fail(s, RT_ERR_ARG, "rt_set_state: buffer too small");
   std::memcpy(hdr, buf, 64);
   if (hdr[0] != 0x52544742 || hdr[1] != N || hdr[2] != s->n_angles || hdr[3] != s->precision ||
-      hdr[4] != (int64_t)nI)
+      hdr[4] != (int64_t)nI || hdr[5] != s->params.gcl)
     return fail(s, RT_ERR_ARG, "rt_set_state: buffer does not match this state");
   const char *b = (const char *)buf;
   RT_CUDA(s, cudaMemcpyAsync(s->d_I[s->cur], b + 64, nI, cudaMemcpyHostToDevice, s->stream));
@@ -827,6 +861,11 @@ int rt_set_state(rt_state *s, const void *buf, size_t bytes) {
                              s->stream));
   RT_CUDA(s, cudaMemcpyAsync(s->d_ext, b + 64 + nI + sizeof(rt::GasDyn) * N, 32 * (size_t)N,
                              cudaMemcpyHostToDevice, s->stream));
+  if (nV) {
+    RT_CUDA(s, cudaMemcpyAsync(s->d_volume, b + 64 + nI + sizeof(rt::GasDyn) * N + 32 * (size_t)N,
+                               nV, cudaMemcpyHostToDevice, s->stream));
+    RT_CUDA(s, rt::launch_inv_vol(s));
+  }
   RT_CUDA(s, rt::launch_cellv(s));
   RT_CUDA(s, cudaStreamSynchronize(s->stream));
   return RT_OK;
@@ -849,7 +888,7 @@ void rt_destroy(rt_state *s) {
     if (s->d_adj[k]) cudaFree(s->d_adj[k]);
   if (s->d_adj_ws) cudaFree(s->d_adj_ws);
   if (s->d_adj_stage) cudaFree(s->d_adj_stage);
-  void *bufs[] = {s->d_recon, s->d_lsq, s->d_Ihalf, s->d_grad, s->d_uface, s->d_slot_nb, s->d_wface, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
+  void *bufs[] = {s->d_gcl_rate, s->d_gcl_kv, s->d_recon, s->d_lsq, s->d_Ihalf, s->d_grad, s->d_uface, s->d_slot_nb, s->d_wface, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
                   s->d_gd, s->d_kind, s->d_aux, s->d_bc_row, s->d_I0, s->d_ext, s->d_dir, s->d_wt,
                   s->d_dir64, s->d_wt64, s->d_I[0], s->d_I[1], s->d_status, s->d_bad,
                   s->d_scratch, s->d_out16};

@@ -70,9 +70,9 @@ __global__ void positivity_screen_kernel(const int64_t *__restrict__ ptr,
                                          const double *__restrict__ wface,
                                          const double *__restrict__ vol,
                                          const double *__restrict__ dir, int64_t n, int A, int mode,
-                                         unsigned *kf, unsigned long long *kmax) {
+                                         unsigned *kf, unsigned long long *kmax, float *kcell) {
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  float best = 0.0f;
+  float best = 0.0f, braw = 0.0f;  // max over angles of sum / V and of sum
   const float cut = mode == 1 ? __uint_as_float(*kf) * (1.0f - 1e-4f) : 0.0f;
   if (row < n) {
     const float iv = (float)(1.0 / vol[row]);
@@ -84,6 +84,7 @@ __global__ void positivity_screen_kernel(const int64_t *__restrict__ ptr,
       const float kc = sum * iv;
       if (mode == 0) {
         best = fmaxf(best, kc);
+        braw = fmaxf(braw, sum);
       } else if (kc >= cut) {
         double exact = 0.0;
         for (int64_t k = ptr[row]; k < ptr[row + 1]; ++k) {
@@ -95,8 +96,14 @@ __global__ void positivity_screen_kernel(const int64_t *__restrict__ ptr,
     }
   }
   if (mode == 0) {
-    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if (threadIdx.x % 32 == 0 && row < n) atomicMax(kf, __float_as_uint(best));
+    for (int o = 16; o > 0; o >>= 1) {
+      best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+      braw = fmaxf(braw, __shfl_xor_sync(0xffffffffu, braw, o));
+    }
+    if (threadIdx.x % 32 == 0 && row < n) {
+      atomicMax(kf, __float_as_uint(best));
+      if (kcell) kcell[row] = braw;
+    }
   }
 }
 
@@ -279,7 +286,7 @@ cudaError_t launch_permute_out(rt_state *s, const void *src, void *dst, int stri
 
 // d_kmax[0] receives the bound (as a double), d_kmax[1] is scratch.
 // fslot: the face slots in float (the state's own for float states).
-cudaError_t launch_positivity(rt_state *s, const SlotF *fslot, double *d_kmax) {
+cudaError_t launch_positivity(rt_state *s, const SlotF *fslot, double *d_kmax, float *kcell) {
   cudaError_t e = cudaMemsetAsync(d_kmax, 0, 2 * sizeof(double), s->stream);
   if (e != cudaSuccess) return e;
   unsigned *kf = reinterpret_cast<unsigned *>(d_kmax + 1);
@@ -288,11 +295,11 @@ cudaError_t launch_positivity(rt_state *s, const SlotF *fslot, double *d_kmax) {
     if (s->precision == RT_FP32)
       positivity_screen_kernel<float><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
           s->d_ptr, fslot, (const SlotF *)s->d_slot, s->d_wface, s->d_volume, s->d_dir64,
-          s->n_cells, s->n_angles, mode, kf, km);
+          s->n_cells, s->n_angles, mode, kf, km, kcell);
     else
       positivity_screen_kernel<double><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
           s->d_ptr, fslot, (const SlotD *)s->d_slot, s->d_wface, s->d_volume, s->d_dir64,
-          s->n_cells, s->n_angles, mode, kf, km);
+          s->n_cells, s->n_angles, mode, kf, km, kcell);
     s->launches++;
   }
   return cudaGetLastError();
@@ -335,6 +342,24 @@ int64_t totals_scratch_len(int64_t n_cells) { return ((n_cells + kTotCells - 1) 
 cudaError_t launch_gas_out(rt_state *s, double *e, double *m, double *ext) {
   gas_out_kernel<<<(unsigned)((s->n_cells + kThreads - 1) / kThreads), kThreads, 0, s->stream>>>(
       s->d_gd, s->d_ext, s->d_cell_of, s->n_cells, e, m, ext);
+  s->launches++;
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void inv_vol_kernel(const double *__restrict__ vol, R *__restrict__ inv, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) inv[i] = (R)(1.0 / vol[i]);
+}
+
+cudaError_t launch_inv_vol(rt_state *s) {
+  const unsigned g = (unsigned)((s->n_cells + kThreads - 1) / kThreads);
+  if (s->precision == RT_FP32)
+    inv_vol_kernel<float><<<g, kThreads, 0, s->stream>>>(s->d_volume, (float *)s->d_inv_vol,
+                                                         s->n_cells);
+  else
+    inv_vol_kernel<double><<<g, kThreads, 0, s->stream>>>(s->d_volume, (double *)s->d_inv_vol,
+                                                          s->n_cells);
   s->launches++;
   return cudaGetLastError();
 }

@@ -37,6 +37,7 @@ template <> struct SlotOf<double> { using type = SlotD; };
 enum : unsigned {
   ST_NONCONV = 1u,
   ST_NONFINITE = 2u,
+  ST_CFL = 4u,  // a cell's current volume is below dt max_a sum_f max(u, 0) (gcl states)
 };
 
 // The step kernel works on blocks of CPB consecutive (internal) cells.
@@ -89,6 +90,12 @@ template <typename R> struct StepArgs {
   int32_t src_only;         // 1: I_in holds I* already (no transport)
   int32_t commit;           // 0: the gas update is discarded (van Leer stage 1)
   int32_t boost;            // 1: Gamma = gamma (1 -+ v.n/c) with the Lorentz factor gamma
+  // geometric conservation law (NULL: fixed volumes): per-cell sum_f A w . n,
+  // per-cell max_a sum_f max(u, 0), the current volumes and their inverses
+  const double *gcl_rate;
+  const float *gcl_kv;
+  double *volume;
+  R *inv_vol_w;
   unsigned *status;
   unsigned long long *bad_cell;
 };
@@ -149,6 +156,10 @@ struct rt_state {
   int integrator = RT_FIRST_ORDER;
   void *d_recon = nullptr, *d_lsq = nullptr, *d_Ihalf = nullptr, *d_grad = nullptr;
   double *d_wface = nullptr;  // double states: per-slot A w . n
+  // geometric conservation law: per-cell volume rate sum_f A w . n (double,
+  // internal order) and max_a sum_f max(u, 0) (float); NULL when off
+  double *d_gcl_rate = nullptr;
+  float *d_gcl_kv = nullptr;
   void *d_inv_vol = nullptr;
   int64_t *d_cell_of = nullptr;  // internal -> caller
   double *d_volume = nullptr;    // internal order
@@ -203,7 +214,10 @@ cudaError_t build_uface(rt_state *s);
 // caller order <-> internal order; the internal rows are `stride` reals apart
 cudaError_t launch_permute_in(rt_state *s, const void *src, void *dst, int stride);
 cudaError_t launch_permute_out(rt_state *s, const void *src, void *dst, int stride);
-cudaError_t launch_positivity(rt_state *s, const SlotF *fslot, double *d_kmax);
+// kcell (may be NULL): per cell max_a sum_f max(u, 0), float
+cudaError_t launch_positivity(rt_state *s, const SlotF *fslot, double *d_kmax, float *kcell);
+// inv_vol = 1 / volume (state precision) after the volumes changed
+cudaError_t launch_inv_vol(rt_state *s);
 cudaError_t launch_moments(rt_state *s, double *E, double *F, double *P);
 cudaError_t launch_totals(rt_state *s, double *d_out16);
 cudaError_t launch_gas_out(rt_state *s, double *e, double *m, double *ext);

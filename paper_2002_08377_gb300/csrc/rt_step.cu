@@ -183,6 +183,19 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
       Ia[j] = fma(-dtv, acca[j], Ia[j]);  // I*
       Ib[j] = fma(-dtv, accb[j], Ib[j]);
     }
+    if constexpr (MOVING) {
+      // geometric conservation law (volumes change only on a moving mesh):
+      // V^{n+1} I* = V^n I - dt sum_f u I_up, i.e. the fixed-volume I* times
+      // V^n / V^{n+1} = 1 / (1 + dt rate / V^n)
+      if (a.gcl_rate && !a.src_only) {
+        const R ratio = rcp(fma(dtv, R(a.gcl_rate[c]), R(1)));
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+          Ia[j] *= ratio;
+          Ib[j] *= ratio;
+        }
+      }
+    }
   }
 
   // comoving frame (first order in v/c): Gamma = 1 -+ v.n / c, and the
@@ -384,7 +397,17 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
       x[2] += dy;
       x[3] += dz;
     }
-    const unsigned bad = sh.bad[lp];
+    unsigned bad = sh.bad[lp];
+    if (MOVING && a.gcl_rate && a.commit) {
+      // the cell's volume for the next step, V^{n+1} = V^n + dt sum_f A w . n;
+      // this step needed V^n >= dt max_a sum_f max(u, 0) (the float factor
+      // carries a ~1e-6 relative error, inside the margin)
+      const double V = a.volume[cl];
+      if (a.dt * (double)a.gcl_kv[cl] > V * (1.0 + 1e-5)) bad |= ST_CFL;
+      const double V1 = __dadd_rn(V, __dmul_rn(a.dt, a.gcl_rate[cl]));
+      a.volume[cl] = V1;
+      a.inv_vol_w[cl] = R(1.0 / V1);
+    }
     if (bad) {
       atomicOr(a.status, bad);
       atomicMin(a.bad_cell, (unsigned long long)cl);
@@ -448,6 +471,10 @@ cudaError_t launch_t(rt_state *s, double dt, const StepIO &io) {
   a.src_only = io.src_only ? 1 : 0;
   a.commit = io.commit ? 1 : 0;
   a.boost = s->params.boost;
+  a.gcl_rate = s->d_gcl_rate;
+  a.gcl_kv = s->d_gcl_kv;
+  a.volume = s->d_volume;
+  a.inv_vol_w = reinterpret_cast<R *>(s->d_inv_vol);
   a.dt = dt;
   a.dt_r = R(dt);
   a.dt_cbar_r = R(dt * s->params.cbar);

@@ -1,9 +1,7 @@
 """GPU parity of the comoving transformation to all orders in v/c
-(rt_params.boost = 1, Gamma = gamma (1 - v.n/c), Sec. 2.3) and of a mesh
-moving with per-face velocities (a rigid rotation through the face-velocity
-equation, Sec. 2.2), through the C ABI against the FP64 oracle: RT_FP64 per
-intensity to a relative 1e-12, RT_FP32 in L1 of E_r to 1e-5 with total
-energy conserved to 1e-6."""
+(rt_params.boost = 1, Gamma = gamma (1 - v.n/c), Sec. 2.3), through the C ABI
+against the FP64 oracle: RT_FP64 per intensity to a relative 1e-12, RT_FP32
+in L1 of E_r to 1e-5 with total energy conserved to 1e-6."""
 import numpy as np
 import pytest
 
@@ -102,32 +100,3 @@ def test_adjoint_refuses_a_boosted_state():
         g.adjoint_step(0.01, t(N, A), t(N), t(N, 3), t(N, A), t(N), t(N, 3), t(N), t(N))
     assert err.value.code == capi.RT_ERR_STATE
 
-
-# ---------------------------------------------------------------- per-face velocities
-def _rotating(n, order, seed):
-    """A mesh in rigid rotation about the box centre: face velocities from
-    the generators' velocities by the face-velocity equation (every face has
-    its own w; the field jumps across the periodic boundary, which the
-    transport takes like any other face velocity)."""
-    prob = randomise(make(n=n, order=order, cbar=10.0, c=100.0), seed=seed)
-    m = prob.mesh
-    Om = np.array([0.4, -0.7, 0.9])
-    m.face_w = m.face_velocity(np.cross(Om, m.points - 0.5 * m.box))
-    return prob
-
-
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_rotating_mesh(precision):
-    prob = _rotating((9, 7, 5), 8, 3)
-    o = oracle.Oracle(prob)
-    g = solver(prob, precision)
-    t0 = g.totals()
-    dt = o.cfl_dt()
-    assert o.run(30, dt) == oracle.ORC_OK
-    g.run(30, dt)
-    if precision == "fp64":
-        check_fp64(o, g)
-    else:
-        check_fp32(o, g)
-        t1 = g.totals()
-        assert abs(t1[12] - t0[12]) < FP32_ENERGY * abs(t0[12])

@@ -51,7 +51,8 @@ class _Problem(ctypes.Structure):
                 ("emit_rate", ctypes.c_void_p), ("I_src", ctypes.c_void_p),
                 ("bc_row", ctypes.c_void_p), ("I0", ctypes.c_void_p),
                 ("face_offset", ctypes.c_void_p), ("boost_all_orders", ctypes.c_int32),
-                ("gcl", ctypes.c_int32)]
+                ("gcl", ctypes.c_int32), ("beta_P", ctypes.c_double), ("beta_J", ctypes.c_double),
+                ("T_ref", ctypes.c_double)]
 
 
 def lib():
@@ -62,6 +63,8 @@ def lib():
         P = ctypes.POINTER(_Problem)
         vp, d, i = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
         L.orc_transport.argtypes = [P, d, vp, vp]
+        L.orc_newton_power.argtypes = [d, d, d, d, i, ctypes.POINTER(d), ctypes.POINTER(i)]
+        L.orc_newton_power.restype = i
         L.orc_gcl_volumes.argtypes = [P, d, vp]
         L.orc_moments.argtypes = [P, vp, vp, vp, vp]
         L.orc_newton.argtypes = [d, d, d, i, ctypes.POINTER(d), ctypes.POINTER(i)]
@@ -102,6 +105,14 @@ def newton(alpha, beta, g, max_iter=64):
     T, it = ctypes.c_double(), ctypes.c_int()
     st = lib().orc_newton(float(alpha), float(beta), float(g), int(max_iter), ctypes.byref(T),
                           ctypes.byref(it))
+    return st, T.value, it.value
+
+
+def newton_power(alpha, k, beta, g, max_iter=64):
+    """Positive root of alpha T^k + beta T = g (k >= 1): (status, T, iterations)."""
+    T, it = ctypes.c_double(), ctypes.c_int()
+    st = lib().orc_newton_power(float(alpha), float(k), float(beta), float(g), int(max_iter),
+                                ctypes.byref(T), ctypes.byref(it))
     return st, T.value, it.value
 
 
@@ -158,6 +169,9 @@ class Oracle:
         p.face_offset = arr("foff", m.face_offset())
         p.boost_all_orders = int(getattr(prob, "boost", 0))
         p.gcl = int(getattr(prob, "gcl", 0))
+        p.beta_P = float(getattr(prob, "beta_P", 0.0))
+        p.beta_J = float(getattr(prob, "beta_J", 0.0))
+        p.T_ref = float(getattr(prob, "T_ref", 1.0))
         self.p = p
         self.integrator = int(getattr(prob, "integrator", 0))
         self.I = _f64(prob.initial_intensity(np.float64))
@@ -288,7 +302,7 @@ class Oracle:
                                     work.ctypes.data)
         if st != ORC_OK:
             raise ValueError("the oracle's adjoint reverses the first-order transformation on "
-                             "fixed cell volumes only")
+                             "fixed cell volumes with constant opacities only")
         return lI, le, lm
 
     def temperature(self):

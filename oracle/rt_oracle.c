@@ -75,6 +75,11 @@ typedef struct {
    * geometric conservation law (see orc_gcl_volumes) and the transport takes
    * the conservative moving-cell form; cell_volume holds V^n */
   int32_t gcl;
+  /* temperature-dependent opacities (Sec. 2.3 solves the temperature
+   * equation by Newton-Raphson for them): kappa_P(T) = kappa_P (T/T_ref)^beta_P
+   * at T^{n+1} inside the solve, kappa_J(T) = kappa_J (T/T_ref)^beta_J at T^n
+   * (the start of the source step); beta_P >= -3.  0, 0: constant opacities */
+  double beta_P, beta_J, T_ref;
 } orc_problem;
 
 /* ------------------------------------------------------------------------
@@ -274,6 +279,45 @@ int orc_newton(double alpha, double beta, double g, int max_iter, double *T_out,
   return ORC_OK;
 }
 
+/* Positive root of alpha T^k + beta T = g for k >= 1 (the temperature
+ * equation with kappa_P proportional to T^(k-4)), by Newton-Raphson: the
+ * left side is increasing and convex for T >= 0, so from the upper bound
+ * min(g / beta, (g / alpha)^(1/k)) the iterates decrease monotonically onto
+ * the root.  Same stopping rule as orc_newton. */
+int orc_newton_power(double alpha, double k, double beta, double g, int max_iter, double *T_out,
+                     int *iters_out) {
+  if (!(alpha >= 0.0) || !(beta > 0.0) || !(g >= 0.0) || !(k >= 1.0)) return ORC_ERR_NONFINITE;
+  double T = g / beta;
+  if (alpha > 0.0) {
+    double tk = pow(g / alpha, 1.0 / k);
+    if (tk < T) T = tk;
+  }
+  int it = 0, done = 0;
+  while (!done && it < max_iter) {
+    double Tk1 = pow(T, k - 1.0);
+    double f = alpha * Tk1 * T + beta * T - g;
+    double fp = k * alpha * Tk1 + beta;
+    double Tn = T - f / fp;
+    ++it;
+    if (!(Tn < T)) {
+      done = 1;
+    } else {
+      done = (T - Tn <= 1e-15 * T);
+      T = Tn;
+    }
+  }
+  if (iters_out) *iters_out = it;
+  *T_out = T;
+  if (!isfinite(T)) return ORC_ERR_NONFINITE;
+  if (!done) return ORC_ERR_NONCONV;
+  return ORC_OK;
+}
+
+/* The opacity factor (T / T_ref)^beta (1 for beta = 0). */
+static double opacity_factor(double beta, double T, double T_ref) {
+  return beta == 0.0 ? 1.0 : pow(T / T_ref, beta);
+}
+
 /* The same root in closed form (Sec. 2.3 solves the temperature-independent
  * case analytically), by Ferrari's method: with p = beta/alpha, q = g/alpha,
  * T^4 + p T - q = 0 is rewritten (T^2 + y)^2 = 2y (T - p/(4y))^2 where y > 0
@@ -338,7 +382,13 @@ static double frame_gamma(const orc_problem *p, const double *v) {
 static int source_interior(const orc_problem *p, int64_t c, double dt, const double *Is,
                            double *In, double *e, double *m, int *iters) {
   const int A = p->n_angles;
-  const double rho = p->rho[c], kP = p->kappa_P[c], kJ = p->kappa_J[c], kS = p->kappa_s[c];
+  const double rho = p->rho[c], kS = p->kappa_s[c];
+  double kin = 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) / rho;
+  double rcv = rho * p->r_gas / (p->gamma_gas - 1.0);
+  double Tn = (*e - kin) / rcv;
+  /* kappa_J at the start of the step; kappa_P at T^{n+1} below */
+  const double kJ = p->kappa_J[c] * opacity_factor(p->beta_J, Tn, p->T_ref);
+  double kP = p->kappa_P[c];
   double v[3] = {m[0] / rho, m[1] / rho, m[2] / rho};
   const double gam = frame_gamma(p, v);
   double G[A], wc[A], Ic[A];
@@ -359,14 +409,19 @@ static int source_interior(const orc_problem *p, int64_t c, double dt, const dou
     SG += wc[a] * G[a] / (1.0 + xa);
   }
   double D = 1.0 - dt * p->cbar * rho * kS * SG;
-  double kin = 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) / rho;
-  double rcv = rho * p->r_gas / (p->gamma_gas - 1.0);
-  double Tn = (*e - kin) / rcv;
   double alpha = dt * p->c * rho * kP * p->a_rad * (1.0 - dt * p->cbar * rho * kJ * SG / D);
   double beta = rcv;
   double g = rcv * Tn + dt * p->c * rho * 4.0 * M_PI * kJ * SI / D;
   double T;
-  int st = orc_newton(alpha, beta, g, p->newton_max_iter, &T, iters);
+  int st;
+  if (p->beta_P == 0.0) {
+    st = orc_newton(alpha, beta, g, p->newton_max_iter, &T, iters);
+  } else {
+    /* kappa_P (T/T_ref)^beta_P T^4 = kappa_P T_ref^-beta_P T^(4 + beta_P) */
+    st = orc_newton_power(alpha * pow(p->T_ref, -p->beta_P), 4.0 + p->beta_P, beta, g,
+                          p->newton_max_iter, &T, iters);
+    kP *= opacity_factor(p->beta_P, T, p->T_ref);
+  }
   if (st != ORC_OK) return st;
   double B = p->a_rad * T * T * T * T / (4.0 * M_PI);
   double J = (SI + dt * p->cbar * rho * kP * B * SG) / D;
@@ -760,7 +815,7 @@ int orc_adjoint_step(const orc_problem *p, double dt, const double *I, const dou
   const int A = p->n_angles;
   double *Is = work, *lIs = work + p->n_cells * A;
   /* reverses the first-order transformation on a mesh of fixed volumes only */
-  if (p->boost_all_orders || p->gcl) return ORC_ERR_ARG;
+  if (p->boost_all_orders || p->gcl || p->beta_P != 0.0 || p->beta_J != 0.0) return ORC_ERR_ARG;
   orc_transport(p, dt, I, Is);
 #pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < p->n_cells; ++c) {

@@ -70,6 +70,9 @@ class Problem:
     integrator: int = 0       # 0 first-order upwind step, 1 van Leer with limited linear reconstruction
     boost: int = 0            # 1: the comoving transformation to all orders in v/c (Gamma with gamma)
     gcl: int = 0              # 1: cell volumes follow the face velocities (geometric conservation law)
+    beta_P: float = 0.0       # kappa_P(T) = kappa_P (T / T_ref)^beta_P, at T^{n+1} (beta_P >= -3)
+    beta_J: float = 0.0       # kappa_J(T) = kappa_J (T / T_ref)^beta_J, at T^n
+    T_ref: float = 1.0
 
     @property
     def n_cells(self):

@@ -318,10 +318,13 @@ def _ode_source_cell(prob, c, I0, dt, steps):
     kin = 0.5 * np.sum(prob.m[c] ** 2) / rho
     T = (prob.e[c] - kin) / rcv
     y = np.concatenate([G ** 4 * I0, [T]])
-    kP, kJ, kS = prob.kappa_P[c], prob.kappa_J[c], prob.kappa_s[c]
+    kP0, kJ0, kS = prob.kappa_P[c], prob.kappa_J[c], prob.kappa_s[c]
+    bP, bJ, Tr = getattr(prob, "beta_P", 0.0), getattr(prob, "beta_J", 0.0), getattr(prob, "T_ref", 1.0)
 
     def f(y):
         It, T = y[:-1], y[-1]
+        # opacities at the current temperature (Sec. 2.3: temperature-dependent opacity)
+        kP, kJ = kP0 * (T / Tr) ** bP, kJ0 * (T / Tr) ** bJ
         J = wc @ It
         dI = G * prob.cbar * rho * (kP * prob.a_rad * T ** 4 / (4 * np.pi) + kS * J - (kJ + kS) * It)
         dT = -prob.c * rho * (kP * prob.a_rad * T ** 4 - 4 * np.pi * kJ * J) / rcv
@@ -349,18 +352,26 @@ def _heavy_gas(prob, H=1e6):
     return prob
 
 
-@pytest.mark.parametrize("vscale,boost", [(0.0, 0), (0.05, 0), (0.25, 1)])
-def test_implicit_source_converges_to_subcycled_explicit(vscale, boost):
+@pytest.mark.parametrize("vscale,boost,opacity", [(0.0, 0, None), (0.05, 0, None), (0.25, 1, None),
+                                                  (0.05, 0, (-3.0, 1.0, 1.0)),
+                                                  (0.0, 0, (2.0, -1.0, 0.7))])
+def test_implicit_source_converges_to_subcycled_explicit(vscale, boost, opacity):
     """8-cell mesh: N implicit source substeps approach a finely subcycled
     explicit (RK4) integration of the source ODE at first order in dt/N.  With
     the transformation to all orders (|v|/c up to 0.43, gamma up to 1.11) the
     gas is made heavy so that the frame velocity stays frozen; there the
-    first-order update stalls at ~1e-2 against the all-orders ODE."""
+    first-order update stalls at ~1e-2 against the all-orders ODE.  With
+    temperature-dependent opacities the ODE takes both at the running
+    temperature, the scheme kappa_P at T^{n+1} and kappa_J at T^n."""
     prob = randomise(make(n=(2, 2, 2), order=4, cbar=5.0, c=50.0), seed=4, v_scale=vscale,
                      kinds=False)
     if boost:
         prob = _heavy_gas(prob)
     prob.boost = boost
+    if opacity is not None:
+        # kappa_P ~ T^beta_P at T^{n+1} and kappa_J ~ T^beta_J at T^n in the scheme,
+        # both at the running temperature in the ODE (cell temperatures 0.56 - 1.87)
+        prob.beta_P, prob.beta_J, prob.T_ref = opacity
     I_start = prob.initial_intensity()
     dt = 0.02
     ref = [_ode_source_cell(prob, c, I_start[c], dt, 4000) for c in range(prob.n_cells)]

@@ -144,7 +144,14 @@ typedef enum { RT_FIRST_ORDER = 0, RT_VAN_LEER = 1 } rt_integrator;
  * cell against its current volume on the device (RT_ERR_CFL, latched like
  * the other per-cell failures).  rt_totals, rt_get_state and rt_set_state
  * use and keep the current volumes.  gcl = 1 needs RT_FIRST_ORDER;
- * rt_adjoint_step refuses gcl states. */
+ * rt_adjoint_step refuses gcl states.
+ * beta_P, beta_J, T_ref: temperature-dependent opacities (Sec. 2.3 solves
+ * the temperature equation by Newton-Raphson for them).  The cell's kappa_P
+ * and kappa_J of rt_set_gas hold at T_ref; kappa_P(T) = kappa_P (T/T_ref)^beta_P
+ * is taken at T^{n+1} inside the temperature solve (alpha T^(4 + beta_P) +
+ * rho c_v T = g, beta_P >= -3), kappa_J(T) = kappa_J (T/T_ref)^beta_J at the
+ * temperature at the start of each step.  0, 0: constant opacities (T_ref is
+ * then unused; otherwise T_ref > 0).  rt_adjoint_step refuses beta != 0. */
 typedef struct {
   double cbar, c, a_rad, gamma_gas, r_gas, cfl;
   int32_t precision;       /* rt_precision */
@@ -153,6 +160,7 @@ typedef struct {
   int32_t boost;           /* 0 or 1, see above */
   int32_t gcl;             /* 0 or 1, see above */
   int32_t reserved;        /* 0 */
+  double beta_P, beta_J, T_ref; /* see above */
 } rt_params;
 
 /* Validates and copies the mesh to the device, orders cells for locality,

@@ -360,7 +360,9 @@ int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state 
       !(p->r_gas > 0) || !(p->cfl > 0) || (p->precision != RT_FP32 && p->precision != RT_FP64) ||
       (p->integrator != RT_FIRST_ORDER && p->integrator != RT_VAN_LEER) ||
       (p->boost != 0 && p->boost != 1) || (p->gcl != 0 && p->gcl != 1) ||
-      (p->gcl && p->integrator != RT_FIRST_ORDER) ||
+      (p->gcl && p->integrator != RT_FIRST_ORDER) || !std::isfinite(p->beta_P) ||
+      !std::isfinite(p->beta_J) || ((p->beta_P != 0 || p->beta_J != 0) && !(p->T_ref > 0)) ||
+      !(p->beta_P >= -3.0) ||
       (p->integrator == RT_VAN_LEER && !m->face_offset))
     return bail(RT_ERR_ARG);
   s->params = *p;
@@ -553,6 +555,17 @@ int rt_set_gas(rt_state *s, const double *rho, const double *e, const double *m,
                              s->stream));
   RT_CUDA(s, cudaMemcpyAsync(s->d_gd, gd.data(), sizeof(rt::GasDyn) * N, cudaMemcpyHostToDevice,
                              s->stream));
+  if (s->params.beta_J != 0.0) {
+    // kappa_J follows the gas temperature: keep rho kappa_J at T_ref and
+    // start from kappa_J(T^0)
+    std::vector<double> rkJ0(N);
+    for (int64_t ic = 0; ic < N; ++ic) rkJ0[ic] = gs[ic].rkJ;
+    if (!s->d_rkJ0) RT_CUDA(s, dalloc(s, &s->d_rkJ0, N));
+    RT_CUDA(s, cudaMemcpyAsync(s->d_rkJ0, rkJ0.data(), sizeof(double) * N, cudaMemcpyHostToDevice,
+                               s->stream));
+    RT_CUDA(s, cudaStreamSynchronize(s->stream));  // rkJ0 is a host temporary
+    RT_CUDA(s, rt::launch_opacity_refresh(s));
+  }
   RT_CUDA(s, cudaMemsetAsync(s->d_ext, 0, sizeof(double) * 4 * N, s->stream));
   // per-cell frame velocity and rho (kJ + kS) in the state precision
   RT_CUDA(s, rt::launch_cellv(s));
@@ -771,6 +784,8 @@ int rt_adjoint_step(rt_state *s, double dt, const void *I_n, const double *e_n, 
                 "rt_adjoint_step reverses the first-order comoving transformation only");
   if (s->params.gcl)
     return fail(s, RT_ERR_STATE, "rt_adjoint_step reverses steps on fixed cell volumes only");
+  if (s->params.beta_P != 0.0 || s->params.beta_J != 0.0)
+    return fail(s, RT_ERR_STATE, "rt_adjoint_step reverses steps with constant opacities only");
   if (!I_n || !e_n || !m_n || !lam_I1 || !lam_e1 || !lam_m1 || !lam_I || !lam_e || !lam_m ||
       !grad_kappa_P || !grad_kappa_J)
     return fail(s, RT_ERR_ARG, "rt_adjoint_step: NULL argument");
@@ -866,6 +881,7 @@ int rt_set_state(rt_state *s, const void *buf, size_t bytes) {
                                nV, cudaMemcpyHostToDevice, s->stream));
     RT_CUDA(s, rt::launch_inv_vol(s));
   }
+  RT_CUDA(s, rt::launch_opacity_refresh(s));  // kappa_J at the restored temperatures
   RT_CUDA(s, rt::launch_cellv(s));
   RT_CUDA(s, cudaStreamSynchronize(s->stream));
   return RT_OK;
@@ -888,7 +904,7 @@ void rt_destroy(rt_state *s) {
     if (s->d_adj[k]) cudaFree(s->d_adj[k]);
   if (s->d_adj_ws) cudaFree(s->d_adj_ws);
   if (s->d_adj_stage) cudaFree(s->d_adj_stage);
-  void *bufs[] = {s->d_gcl_rate, s->d_gcl_kv, s->d_recon, s->d_lsq, s->d_Ihalf, s->d_grad, s->d_uface, s->d_slot_nb, s->d_wface, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
+  void *bufs[] = {s->d_rkJ0, s->d_gcl_rate, s->d_gcl_kv, s->d_recon, s->d_lsq, s->d_Ihalf, s->d_grad, s->d_uface, s->d_slot_nb, s->d_wface, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
                   s->d_gd, s->d_kind, s->d_aux, s->d_bc_row, s->d_I0, s->d_ext, s->d_dir, s->d_wt,
                   s->d_dir64, s->d_wt64, s->d_I[0], s->d_I[1], s->d_status, s->d_bad,
                   s->d_scratch, s->d_out16};

@@ -364,6 +364,29 @@ cudaError_t launch_inv_vol(rt_state *s) {
   return cudaGetLastError();
 }
 
+// rho kappa_J(T) = rkJ0 (T / T_ref)^beta_J at each cell's gas temperature
+// (the same expression the step's gas phase evaluates for the next step).
+__global__ void opacity_refresh_kernel(GasStatic *__restrict__ gs, const GasDyn *__restrict__ gd,
+                                       const double *__restrict__ rkJ0, int64_t n, double beta_J,
+                                       double T_ref) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const GasDyn d = gd[i];
+  const double kin = 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * gs[i].inv_rho;
+  const double rkJ = rkJ0[i] * pow((d.e - kin) / gs[i].rcv / T_ref, beta_J);
+  gs[i].rkJ = rkJ;
+  gs[i].frkJ = (float)rkJ;
+}
+
+cudaError_t launch_opacity_refresh(rt_state *s) {
+  if (s->params.beta_J == 0.0 || !s->d_rkJ0) return cudaSuccess;
+  const unsigned g = (unsigned)((s->n_cells + kThreads - 1) / kThreads);
+  opacity_refresh_kernel<<<g, kThreads, 0, s->stream>>>(s->d_gs, s->d_gd, s->d_rkJ0, s->n_cells,
+                                                        s->params.beta_J, s->params.T_ref);
+  s->launches++;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cellv(rt_state *s) {
   const unsigned g = (unsigned)((s->n_cells + kThreads - 1) / kThreads);
   if (s->precision == RT_FP32)

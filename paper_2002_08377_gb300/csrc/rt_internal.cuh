@@ -96,6 +96,13 @@ template <typename R> struct StepArgs {
   const float *gcl_kv;
   double *volume;
   R *inv_vol_w;
+  // temperature-dependent opacities (0, 0: constant): kappa_P (T/T_ref)^beta_P
+  // at T^{n+1} in the temperature solve, kappa_J (T/T_ref)^beta_J refreshed
+  // from T^{n+1} in the gas phase for the next step (rkJ0: rho kappa_J at T_ref)
+  double beta_P, beta_J, T_ref, tref_mbP;  // tref_mbP = T_ref^-beta_P
+  float beta_P_f, T_ref_f, tref_mbP_f;
+  const double *rkJ0;
+  GasStatic *gs_w;
   unsigned *status;
   unsigned long long *bad_cell;
 };
@@ -160,6 +167,8 @@ struct rt_state {
   // internal order) and max_a sum_f max(u, 0) (float); NULL when off
   double *d_gcl_rate = nullptr;
   float *d_gcl_kv = nullptr;
+  // temperature-dependent kappa_J: rho kappa_J at T_ref (internal order)
+  double *d_rkJ0 = nullptr;
   void *d_inv_vol = nullptr;
   int64_t *d_cell_of = nullptr;  // internal -> caller
   double *d_volume = nullptr;    // internal order
@@ -218,6 +227,8 @@ cudaError_t launch_permute_out(rt_state *s, const void *src, void *dst, int stri
 cudaError_t launch_positivity(rt_state *s, const SlotF *fslot, double *d_kmax, float *kcell);
 // inv_vol = 1 / volume (state precision) after the volumes changed
 cudaError_t launch_inv_vol(rt_state *s);
+// rho kappa_J(T) = rkJ0 (T / T_ref)^beta_J of every cell from its gas state
+cudaError_t launch_opacity_refresh(rt_state *s);
 cudaError_t launch_moments(rt_state *s, double *E, double *F, double *P);
 cudaError_t launch_totals(rt_state *s, double *d_out16);
 cudaError_t launch_gas_out(rt_state *s, double *e, double *m, double *ext);

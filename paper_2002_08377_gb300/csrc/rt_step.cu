@@ -78,15 +78,22 @@ __device__ __forceinline__ double source_q(const StepArgs<R> &a, const GasStatic
   const double alpha = a.k_alpha * g.rkP * S1 * rU;
   const double eint = d.e - kin;
   const double gq = eint + a.k_g * g.rkJ * SI * rU;
-  double T = 0.0;
+  double T = 0.0, dPT = dP;  // dPT: dP with kappa_P at T^{n+1}
   if (!(gq >= 0.0) || !(alpha >= 0.0)) {
     bad |= ST_NONFINITE;
-  } else if (quartic_root(alpha, g.rcv, gq, eint / g.rcv, 1e-15, a.newton_max_iter, &T)) {
-    bad |= ST_NONCONV;
+  } else if (a.beta_P == 0.0) {
+    if (quartic_root(alpha, g.rcv, gq, eint / g.rcv, 1e-15, a.newton_max_iter, &T))
+      bad |= ST_NONCONV;
+  } else {
+    // kappa_P (T/T_ref)^beta_P T^4 = kappa_P T_ref^-beta_P T^(4 + beta_P)
+    if (power_root(alpha * a.tref_mbP, 4.0 + a.beta_P, g.rcv, gq, eint / g.rcv, 1e-15,
+                   a.newton_max_iter, &T))
+      bad |= ST_NONCONV;
+    dPT = dP * pow(T / a.T_ref, a.beta_P);
   }
   const double B = a.a_rad * (T * T) * (T * T) * (1.0 / (4.0 * kPi));
-  const double J = fma(dP * B, SG, SI) * rU;  // the J~ of Eq. (Jcom)
-  return fma(dP, B, dS * J);
+  const double J = fma(dPT * B, SG, SI) * rU;  // the J~ of Eq. (Jcom)
+  return fma(dPT, B, dS * J);
 }
 
 // The same in float for float states, from the float coefficients and the
@@ -105,11 +112,18 @@ __device__ __forceinline__ float source_q_float(const StepArgs<float> &a, int64_
     return 0.0f;
   }
   if (isfinite(alpha) && isfinite(gq)) {
-    float T;
-    const int nc = quartic_root(alpha, rcv, gq, eint * rcp(rcv), 1e-7f, a.newton_max_iter, &T);
+    float T, dPT = dP;  // dPT: dP with kappa_P at T^{n+1}
+    int nc;
+    if (a.beta_P_f == 0.0f) {
+      nc = quartic_root(alpha, rcv, gq, eint * rcp(rcv), 1e-7f, a.newton_max_iter, &T);
+    } else {
+      nc = power_root(alpha * a.tref_mbP_f, 4.0f + a.beta_P_f, rcv, gq, eint * rcp(rcv), 1e-7f,
+                      a.newton_max_iter, &T);
+      dPT = dP * powf(T / a.T_ref_f, a.beta_P_f);
+    }
     const float B = a.a_rad_4pi_f * (T * T) * (T * T);
-    const float J = fmaf(dP * B, SG, SI) * rU;
-    const float q = fmaf(dP, B, dS * J);
+    const float J = fmaf(dPT * B, SG, SI) * rU;
+    const float q = fmaf(dPT, B, dS * J);
     if (isfinite(q)) {
       if (nc) bad |= ST_NONCONV;
       return q;
@@ -390,6 +404,12 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
       const double ir = gs_s[lp].inv_rho;
       const double kin = 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * ir;
       store4(a.cellv + 4 * cl, R(d.mx * ir), R(d.my * ir), R(d.mz * ir), R(d.e - kin));
+      if (a.beta_J != 0.0) {
+        // kappa_J of the next step, at its starting temperature
+        const double rkJ = a.rkJ0[cl] * pow((d.e - kin) / gs_s[lp].rcv / a.T_ref, a.beta_J);
+        a.gs_w[cl].rkJ = rkJ;
+        a.gs_w[cl].frkJ = (float)rkJ;
+      }
     } else {
       double *x = a.ext + 4 * cl;
       x[0] += dE;
@@ -475,6 +495,15 @@ cudaError_t launch_t(rt_state *s, double dt, const StepIO &io) {
   a.gcl_kv = s->d_gcl_kv;
   a.volume = s->d_volume;
   a.inv_vol_w = reinterpret_cast<R *>(s->d_inv_vol);
+  a.beta_P = s->params.beta_P;
+  a.beta_J = s->params.beta_J;
+  a.T_ref = s->params.T_ref;
+  a.tref_mbP = a.beta_P != 0.0 ? pow(a.T_ref, -a.beta_P) : 1.0;
+  a.beta_P_f = (float)a.beta_P;
+  a.T_ref_f = (float)a.T_ref;
+  a.tref_mbP_f = (float)a.tref_mbP;
+  a.rkJ0 = s->d_rkJ0;
+  a.gs_w = s->d_gs;
   a.dt = dt;
   a.dt_r = R(dt);
   a.dt_cbar_r = R(dt * s->params.cbar);

@@ -170,6 +170,40 @@ __device__ __forceinline__ int quartic_root(T_ alpha, T_ beta, T_ g, T_ T0, T_ t
   return done ? 0 : 1;
 }
 
+// Positive root of alpha T^k + beta T = g for k >= 1 (alpha >= 0, beta > 0,
+// g >= 0): the temperature equation when kappa_P is proportional to T^(k-4).
+// The left side is increasing and convex for T >= 0, so, as for
+// quartic_root, one Newton step from T0 >= 0 lands at or above the root
+// (capped by g / beta) and the iterates then decrease monotonically onto it.
+// Returns 1 if it did not converge.
+__device__ __forceinline__ float ppow(float x, float k) { return powf(x, k); }
+__device__ __forceinline__ double ppow(double x, double k) { return pow(x, k); }
+template <typename T_>
+__device__ int power_root(T_ alpha, T_ k, T_ beta, T_ g, T_ T0, T_ tol, int max_iter, T_ *T_out) {
+  T_ T = T0 > T_(0) ? T0 : T_(0);
+  {
+    const T_ Tk1 = ppow(T, k - T_(1));
+    const T_ f = fma(alpha * Tk1, T, fma(beta, T, -g));
+    const T_ fp = fma(k * alpha, Tk1, beta);
+    T = fmin(T - qdiv(f, fp), qdiv(g, beta));
+  }
+  bool done = false;
+  for (int it = 0; it < max_iter && !done; ++it) {
+    const T_ Tk1 = ppow(T, k - T_(1));
+    const T_ f = fma(alpha * Tk1, T, fma(beta, T, -g));
+    const T_ fp = fma(k * alpha, Tk1, beta);
+    const T_ Tn = T - qdiv(f, fp);
+    if (!(Tn < T)) {
+      done = true;
+    } else {
+      done = (T - Tn <= tol * T);
+      T = Tn;
+    }
+  }
+  *T_out = T;
+  return done ? 0 : 1;
+}
+
 // u > 0, the upwind test.  Double: from the sign and high word of u, on the
 // integer pipe (differs from u > 0 only for |u| below 2^-1042, whose flux is
 // far below rounding).

@@ -30,6 +30,7 @@ class RTSolver:
 
     def __init__(self, mesh, dirs, weights, *, cbar, c, a_rad=1.0, gamma_gas=5.0 / 3.0,
                  r_gas=1.0, cfl=0.3, precision="fp32", newton_max_iter=64, integrator=0, boost=0, gcl=0,
+                 beta_P=0.0, beta_J=0.0, T_ref=1.0,
                  stream=None):
         if torch is None or not torch.cuda.is_available():
             raise RuntimeError("RTSolver needs a CUDA device (no CPU fallback exists)")
@@ -66,7 +67,8 @@ class RTSolver:
             md.face_offset = ptr(mesh.face_offset(), np.float64)
         pr = capi.Params(cbar, c, a_rad, gamma_gas, r_gas, cfl,
                          capi.RT_FP32 if precision == "fp32" else capi.RT_FP64, newton_max_iter,
-                         int(integrator), int(boost), int(gcl), 0)
+                         int(integrator), int(boost), int(gcl), 0, float(beta_P), float(beta_J),
+                         float(T_ref))
         st = ctypes.c_void_p()
         code = self.lib.rt_create(ctypes.byref(md), ctypes.byref(pr),
                                   ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(st))
@@ -80,6 +82,8 @@ class RTSolver:
         kw.setdefault("integrator", getattr(prob, "integrator", 0))
         kw.setdefault("boost", getattr(prob, "boost", 0))
         kw.setdefault("gcl", getattr(prob, "gcl", 0))
+        for k, d in (("beta_P", 0.0), ("beta_J", 0.0), ("T_ref", 1.0)):
+            kw.setdefault(k, getattr(prob, k, d))
         s = cls(prob.mesh, prob.dirs, prob.weights, cbar=prob.cbar, c=prob.c, a_rad=prob.a_rad,
                 gamma_gas=prob.gamma_gas, r_gas=prob.r_gas, cfl=prob.cfl, precision=precision, **kw)
         s.set_gas(prob.rho, prob.e, prob.m, prob.kappa_P, prob.kappa_J, prob.kappa_s)

@@ -52,7 +52,8 @@ class _Problem(ctypes.Structure):
                 ("bc_row", ctypes.c_void_p), ("I0", ctypes.c_void_p),
                 ("face_offset", ctypes.c_void_p), ("boost_all_orders", ctypes.c_int32),
                 ("gcl", ctypes.c_int32), ("beta_P", ctypes.c_double), ("beta_J", ctypes.c_double),
-                ("T_ref", ctypes.c_double)]
+                ("T_ref", ctypes.c_double), ("n_groups", ctypes.c_int32),
+                ("group_w", ctypes.c_void_p)]
 
 
 def lib():
@@ -130,7 +131,16 @@ class Oracle:
             os.environ["OMP_NUM_THREADS"] = str(int(threads))
         m = prob.mesh
         self.prob = prob
-        self.N, self.A = m.n_cells, int(prob.dirs.shape[0])
+        # frequency groups: the oracle's angle set is n_groups copies of the
+        # problem's directions, group j weighted by group_w[j] (kappa arrays
+        # then hold n_groups values per cell, intensities [N][n_groups * A])
+        ng = int(getattr(prob, "n_groups", 1))
+        dirs, wts = np.asarray(prob.dirs, np.float64), np.asarray(prob.weights, np.float64)
+        if ng > 1:
+            gw = np.asarray(prob.group_w, np.float64)
+            dirs = np.tile(dirs, (ng, 1))
+            wts = (gw[:, None] * wts[None, :]).ravel()
+        self.N, self.A = m.n_cells, int(dirs.shape[0])
         keep = self._keep = {}
 
         def arr(name, x, dt=np.float64):
@@ -152,8 +162,8 @@ class Oracle:
         p.face_w = arr("fw", fw)
         p.cell_face_ptr = arr("ptr", m.cell_face_ptr, np.int64)
         p.cell_face_idx = arr("idx", m.cell_face_idx, np.int32)
-        p.dir = arr("dir", prob.dirs)
-        p.wt = arr("wt", prob.weights)
+        p.dir = arr("dir", dirs)
+        p.wt = arr("wt", wts)
         p.cbar, p.c, p.a_rad = prob.cbar, prob.c, prob.a_rad
         p.gamma_gas, p.r_gas = prob.gamma_gas, prob.r_gas
         p.rho = arr("rho", prob.rho)
@@ -172,6 +182,8 @@ class Oracle:
         p.beta_P = float(getattr(prob, "beta_P", 0.0))
         p.beta_J = float(getattr(prob, "beta_J", 0.0))
         p.T_ref = float(getattr(prob, "T_ref", 1.0))
+        p.n_groups = ng
+        p.group_w = arr("gw", prob.group_w) if ng > 1 else None
         self.p = p
         self.integrator = int(getattr(prob, "integrator", 0))
         self.I = _f64(prob.initial_intensity(np.float64))
@@ -301,8 +313,8 @@ class Oracle:
                                     lm.ctypes.data, gP.ctypes.data, gJ.ctypes.data,
                                     work.ctypes.data)
         if st != ORC_OK:
-            raise ValueError("the oracle's adjoint reverses the first-order transformation on "
-                             "fixed cell volumes with constant opacities only")
+            raise ValueError("the oracle's adjoint reverses the grey first-order transformation "
+                             "on fixed cell volumes with constant opacities only")
         return lI, le, lm
 
     def temperature(self):

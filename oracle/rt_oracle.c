@@ -80,6 +80,14 @@ typedef struct {
    * at T^{n+1} inside the solve, kappa_J(T) = kappa_J (T/T_ref)^beta_J at T^n
    * (the start of the source step); beta_P >= -3.  0, 0: constant opacities */
   double beta_P, beta_J, T_ref;
+  /* frequency groups (Sec. 2.3, "multiple independent frequency groups"):
+   * n_groups > 1 takes the angle set as n_groups copies of a base set of
+   * n_angles / n_groups directions, group j holding angles [j A_g, (j+1) A_g)
+   * with weights group_w[j] w_a (the weights of one group sum to group_w[j]);
+   * kappa_P, kappa_J, kappa_s then hold n_groups values per cell.  The groups
+   * couple only through T^{n+1} (Eq. com rad thermal disc); 1: grey */
+  int32_t n_groups;
+  const double *group_w;
 } orc_problem;
 
 /* ------------------------------------------------------------------------
@@ -438,6 +446,82 @@ static int source_interior(const orc_problem *p, int64_t c, double dt, const dou
   return ORC_OK;
 }
 
+/* The implicit source step of one interior cell with n_groups > 1
+ * frequency groups, Sec. 2.3 generalised to groups j: per group the
+ * comoving sums S_I,j and S_G,j over the group's angles (weights normalised
+ * within the group), D_j = 1 - dt cbar rho ks_j S_G,j, and Eq. (Jcom) for
+ * J~_j; Eq. (com rad thermal disc) weights the groups by W_j:
+ *   alpha = sum_j W_j dt c rho kP_j a (1 - dt cbar rho kJ_j S_G,j / D_j),
+ *   g     = rho c_v T^n + sum_j W_j dt c rho 4 pi kJ_j S_I,j / D_j,
+ * and each group's intensities follow Eq. (com radiative source disc) with
+ * its own opacities.  The gas exchange sums all angles with the weights
+ * W_j w_a (Eqs. gas1, gas2 with the group weights). */
+static int source_interior_groups(const orc_problem *p, int64_t c, double dt, const double *Is,
+                                  double *In, double *e, double *m, int *iters) {
+  const int A = p->n_angles, NG = p->n_groups, Ag = A / NG;
+  const double rho = p->rho[c];
+  double kin = 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) / rho;
+  double rcv = rho * p->r_gas / (p->gamma_gas - 1.0);
+  double Tn = (*e - kin) / rcv;
+  double v[3] = {m[0] / rho, m[1] / rho, m[2] / rho};
+  const double gam = frame_gamma(p, v);
+  double G[A], Ic[A], SI[NG], SG[NG], D[NG], kP[NG], kJ[NG], kS[NG];
+  double alpha = 0.0, g = rcv * Tn;
+  for (int j = 0; j < NG; ++j) {
+    kP[j] = p->kappa_P[c * NG + j];
+    kJ[j] = p->kappa_J[c * NG + j] * opacity_factor(p->beta_J, Tn, p->T_ref);
+    kS[j] = p->kappa_s[c * NG + j];
+    double wc[Ag], norm = 0.0;
+    for (int b = 0; b < Ag; ++b) {
+      const int a = j * Ag + b;
+      const double *n = p->dir + 3 * a;
+      G[a] = gam * (1.0 - (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / p->c);
+      double G2 = G[a] * G[a];
+      Ic[a] = G2 * G2 * Is[a];
+      wc[b] = p->wt[a] / G2;
+      norm += wc[b];
+    }
+    SI[j] = SG[j] = 0.0;
+    for (int b = 0; b < Ag; ++b) {
+      const int a = j * Ag + b;
+      wc[b] /= norm;
+      double xa = dt * p->cbar * rho * (kJ[j] + kS[j]) * G[a];
+      SI[j] += wc[b] * Ic[a] / (1.0 + xa);
+      SG[j] += wc[b] * G[a] / (1.0 + xa);
+    }
+    D[j] = 1.0 - dt * p->cbar * rho * kS[j] * SG[j];
+    const double W = p->group_w[j];
+    alpha += W * dt * p->c * rho * kP[j] * p->a_rad * (1.0 - dt * p->cbar * rho * kJ[j] * SG[j] / D[j]);
+    g += W * dt * p->c * rho * 4.0 * M_PI * kJ[j] * SI[j] / D[j];
+  }
+  double T;
+  int st;
+  if (p->beta_P == 0.0) {
+    st = orc_newton(alpha, rcv, g, p->newton_max_iter, &T, iters);
+  } else {
+    st = orc_newton_power(alpha * pow(p->T_ref, -p->beta_P), 4.0 + p->beta_P, rcv, g,
+                          p->newton_max_iter, &T, iters);
+    for (int j = 0; j < NG; ++j) kP[j] *= opacity_factor(p->beta_P, T, p->T_ref);
+  }
+  if (st != ORC_OK) return st;
+  double B = p->a_rad * T * T * T * T / (4.0 * M_PI);
+  for (int j = 0; j < NG; ++j) {
+    double J = (SI[j] + dt * p->cbar * rho * kP[j] * B * SG[j]) / D[j];
+    for (int b = 0; b < Ag; ++b) {
+      const int a = j * Ag + b;
+      double xa = dt * p->cbar * rho * (kJ[j] + kS[j]) * G[a];
+      double Inew = (Ic[a] + dt * p->cbar * G[a] * rho * (kP[j] * B + kS[j] * J)) / (1.0 + xa);
+      double G2 = G[a] * G[a];
+      In[a] = Inew / (G2 * G2);
+    }
+  }
+  double dE, dF[3];
+  cell_moment_change(p, Is, In, &dE, dF);
+  *e += p->c / p->cbar * dE;
+  for (int k = 0; k < 3; ++k) m[k] += dF[k] / (p->c * p->cbar);
+  return ORC_OK;
+}
+
 /* Boundary cells, Sec. 2.4: I relaxes to I0 with factor min(dt / tau, 1)
  * (tau <= dt pins I = I0).  The gas of a boundary cell is held fixed; the
  * energy and momentum the radiation loses go to an external tally. */
@@ -496,7 +580,8 @@ int orc_source_range(const orc_problem *p, double dt, const double *Istar, doubl
     else if (k == 2)
       source_emitter(p, c, dt, Is, In, m + 3 * c, ext + 4 * c);
     else
-      st = source_interior(p, c, dt, Is, In, e + c, m + 3 * c, &it);
+      st = p->n_groups > 1 ? source_interior_groups(p, c, dt, Is, In, e + c, m + 3 * c, &it)
+                           : source_interior(p, c, dt, Is, In, e + c, m + 3 * c, &it);
     if (it > itmax) itmax = it;
     for (int a = 0; a < A && st == ORC_OK; ++a)
       if (!isfinite(In[a])) st = ORC_ERR_NONFINITE;
@@ -815,7 +900,8 @@ int orc_adjoint_step(const orc_problem *p, double dt, const double *I, const dou
   const int A = p->n_angles;
   double *Is = work, *lIs = work + p->n_cells * A;
   /* reverses the first-order transformation on a mesh of fixed volumes only */
-  if (p->boost_all_orders || p->gcl || p->beta_P != 0.0 || p->beta_J != 0.0) return ORC_ERR_ARG;
+  if (p->boost_all_orders || p->gcl || p->beta_P != 0.0 || p->beta_J != 0.0 || p->n_groups > 1)
+    return ORC_ERR_ARG;
   orc_transport(p, dt, I, Is);
 #pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < p->n_cells; ++c) {

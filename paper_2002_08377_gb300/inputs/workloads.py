@@ -73,6 +73,8 @@ class Problem:
     beta_P: float = 0.0       # kappa_P(T) = kappa_P (T / T_ref)^beta_P, at T^{n+1} (beta_P >= -3)
     beta_J: float = 0.0       # kappa_J(T) = kappa_J (T / T_ref)^beta_J, at T^n
     T_ref: float = 1.0
+    n_groups: int = 1         # frequency groups (kappa arrays [N][n_groups], intensities [N][n_groups * A])
+    group_w: np.ndarray = None  # [n_groups] group weights
 
     @property
     def n_cells(self):

@@ -64,3 +64,24 @@ def randomise(prob, seed=11, v_scale=0.05, aniso=0.5, kinds=True):
         prob.emit_rate = np.where(kind == 2, rng.uniform(1.0, 20.0, N), 0.0)
         prob.I_src = np.where(kind == 2, rng.uniform(0.5, 2.0, N), 0.0)
     return prob
+
+
+def grouped(prob, group_w, scale_P=None, scale_J=None, scale_S=None, I_group=None):
+    """The problem with len(group_w) frequency groups: group j's opacities are
+    the cell's times scale_*[j] (1 if None), its initial intensities the
+    problem's times I_group[j] (1 if None), its boundary rows the problem's."""
+    G = len(group_w)
+    N, A = prob.n_cells, prob.n_angles
+    one = np.ones(G)
+    sP, sJ, sS = (np.asarray(x if x is not None else one, float) for x in (scale_P, scale_J, scale_S))
+    prob.n_groups = G
+    prob.group_w = np.asarray(group_w, float)
+    prob.kappa_P = np.ascontiguousarray(prob.kappa_P[:, None] * sP[None, :])
+    prob.kappa_J = np.ascontiguousarray(prob.kappa_J[:, None] * sJ[None, :])
+    prob.kappa_s = np.ascontiguousarray(prob.kappa_s[:, None] * sS[None, :])
+    I = prob.initial_intensity()
+    ig = np.asarray(I_group if I_group is not None else one, float)
+    Ig = np.ascontiguousarray(np.concatenate([I * ig[j] for j in range(G)], axis=1))
+    prob.initial_intensity = lambda dtype=np.float64, _I=Ig: np.ascontiguousarray(_I.astype(dtype))
+    prob.I0 = np.ascontiguousarray(np.tile(prob.I0, (1, G)))
+    return prob

@@ -311,6 +311,65 @@ def e2e_rate(sol, prob, dt, steps):
     return N * A * steps / el, nbytes, nbytes
 
 
+def groups_workload(n):
+    """The shadows box on S6 with two frequency groups (96 angles in all):
+    group 0 with 0.3 times and group 1 with 3 times the cells' opacities,
+    group weights 0.4, 0.6, the intensities and boundary rows copied per
+    group."""
+    from paper_2002_08377_gb300.inputs import shadows
+    prob = shadows(n=n, order=6)
+    G = 2
+    prob.n_groups = G
+    prob.group_w = np.array([0.4, 0.6])
+    sc = np.array([0.3, 3.0])
+    for k in ("kappa_P", "kappa_J", "kappa_s"):
+        setattr(prob, k, np.ascontiguousarray(getattr(prob, k)[:, None] * sc[None, :]))
+    I = prob.initial_intensity()
+    Ig = np.ascontiguousarray(np.concatenate([I, I], axis=1))
+    prob.initial_intensity = lambda dtype=np.float64, _I=Ig: np.ascontiguousarray(_I.astype(dtype))
+    prob.I0 = np.ascontiguousarray(np.tile(prob.I0, (1, G)))
+    return prob
+
+
+def groups_rate(n, steps, warmup, hbm_peak, peak_kind):
+    """Steps of the two-group S6 shadows box (FP32): the transport sweep of
+    all 96 angles, then the coupled source step."""
+    import torch
+    from paper_2002_08377_gb300.solver import RTSolver
+    prob = groups_workload(n)
+    N, Nf = prob.n_cells, prob.mesh.n_faces
+    A = prob.n_groups * prob.n_angles
+    dt = prob.cfl_dt()
+    sol = RTSolver.from_problem(prob, "fp32")
+    for _ in range(warmup):
+        sol.step(dt)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    l0 = sol.launch_count()
+    ev0.record(sol.stream)
+    sol.launch(steps, dt)
+    ev1.record(sol.stream)
+    torch.cuda.synchronize()
+    sol.sync()
+    ms = ev0.elapsed_time(ev1)
+    launches = sol.launch_count() - l0
+    sol.close()
+    del sol
+    torch.cuda.empty_cache()
+    per = ms / steps
+    # the grey byte model with all groups' intensities, plus 2 x 3 group opacities per cell
+    B = algorithmic_bytes(N, Nf, A, 4) + N * 6 * 8
+    achieved = B / (per * 1e-3) / 1e9
+    return {"value": N * A * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": per, "steps": steps,
+            "launches": launches, "dtype": "f32", "groups": prob.n_groups, "angles": A,
+            "workload": "the shadows box on S6 with 2 frequency groups (96 angles)",
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "algorithmic_bytes_per_step": B,
+                         "peak_source": f"{peak_kind} HBM copy bandwidth"}}
+
+
 def adjoint_rate(prob, prec, dt, steps, warmup):
     """Reverse steps through rt_adjoint_step (the solver's call, caller-order
     device tensors, seeded cotangents): cell-angle reversals per second."""
@@ -359,6 +418,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-vl", action="store_true", help="skip the van Leer leg")
     ap.add_argument("--no-adj", action="store_true", help="skip the adjoint leg")
+    ap.add_argument("--no-groups", action="store_true", help="skip the frequency-group leg")
     ap.add_argument("--only", choices=["fp32", "fp64"], default=None,
                     help="time one precision only (profiling runs)")
     ap.add_argument("--n", type=int, default=128,
@@ -442,6 +502,10 @@ def main():
         prob.integrator = 0
         torch.cuda.empty_cache()
 
+    grp = None
+    if args.only is None and not args.no_groups:
+        grp = groups_rate(args.n, max(3, args.steps // 5), 3, hbm_peak, peak_kind)
+
     adj = None
     if args.only is None and not args.no_adj:
         # one reverse step (rt_adjoint_step: forward transport sweep, source
@@ -478,7 +542,7 @@ def main():
                      "steps": results["fp64"]["steps"], "dtype": "f64",
                      "roofline": results["fp64"]["roofline"],
                      "fp32_over_fp64": r32["value"] / results["fp64"]["value"]},
-            "van_leer": vl, "adjoint": adj}
+            "van_leer": vl, "adjoint": adj, "groups": grp}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

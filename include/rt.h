@@ -92,12 +92,21 @@ typedef enum {
  *     cell's centroid, j' being the image of j that meets i across the face
  *     (on a periodic mesh the two cells' centroids may lie in different
  *     periodic frames).  Required when params->integrator = RT_VAN_LEER (the
- *     linear reconstruction of Sec. 2.2), ignored and may be NULL otherwise. */
+ *     linear reconstruction of Sec. 2.2), ignored and may be NULL otherwise.
+ *   n_groups > 1: frequency groups (Sec. 2.3) that share the angle set and
+ *     couple only through the gas temperature.  Group j has weight
+ *     group_w[j] > 0 (sum 1); intensities are [N][n_groups][A] (every
+ *     intensity argument then holds n_groups * A values per cell, I0 rows
+ *     too), rt_set_gas takes kappa_P, kappa_J, kappa_s as [N][n_groups], and
+ *     rt_moments / rt_totals report the group-weighted sums.  Needs
+ *     n_groups * A <= 128, RT_FIRST_ORDER, boost = 0, gcl = 0 and constant
+ *     opacities; rt_adjoint_step refuses it.  A step is then two launches: the
+ *     transport of all groups' intensities and the coupled source step. */
 typedef struct {
   int64_t n_cells;
   int64_t n_faces;
   int32_t n_angles;
-  int32_t reserved;
+  int32_t n_groups;            /* frequency groups; 0 or 1: grey */
   const double *cell_volume;   /* [N]        */
   const double *cell_centroid; /* [N][3]     */
   const int32_t *face_cells;   /* [Nf][2]    */
@@ -110,6 +119,7 @@ typedef struct {
   const double *angle_dir;     /* [A][3]     */
   const double *angle_w;       /* [A]        */
   const double *face_offset;   /* [Nf][2][3] */
+  const double *group_w;       /* [n_groups], n_groups > 1 only */
 } rt_mesh_desc;
 
 /* Time integration of the transport (Sec. 2, integration steps).

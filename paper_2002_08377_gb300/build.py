@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librt_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["rt_api.cu", "rt_step.cu", "rt_transport.cu", "rt_aux.cu", "rt_adjoint.cu", "rt_noalloc.cu",
-           "rt_recon.cu"]
+           "rt_recon.cu", "rt_groups.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code is compiled without FMA contraction so that x86 and Arm hosts
 # build bit-identical face geometry

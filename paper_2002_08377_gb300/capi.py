@@ -30,13 +30,14 @@ class RTError(RuntimeError):
 
 class MeshDesc(ctypes.Structure):
     _fields_ = [("n_cells", ctypes.c_int64), ("n_faces", ctypes.c_int64),
-                ("n_angles", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_angles", ctypes.c_int32), ("n_groups", ctypes.c_int32),
                 ("cell_volume", ctypes.c_void_p), ("cell_centroid", ctypes.c_void_p),
                 ("face_cells", ctypes.c_void_p), ("face_area", ctypes.c_void_p),
                 ("face_normal", ctypes.c_void_p), ("face_centroid", ctypes.c_void_p),
                 ("face_w", ctypes.c_void_p), ("cell_face_ptr", ctypes.c_void_p),
                 ("cell_face_idx", ctypes.c_void_p), ("angle_dir", ctypes.c_void_p),
-                ("angle_w", ctypes.c_void_p), ("face_offset", ctypes.c_void_p)]
+                ("angle_w", ctypes.c_void_p), ("face_offset", ctypes.c_void_p),
+                ("group_w", ctypes.c_void_p)]
 
 
 class Params(ctypes.Structure):

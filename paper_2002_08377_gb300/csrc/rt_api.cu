@@ -346,11 +346,53 @@ int sync_status(rt_state *s) {
 
 extern "C" {
 
-int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state **out) {
+int rt_create(const rt_mesh_desc *m_in, const rt_params *p, void *stream, rt_state **out) {
   if (!out) return RT_ERR_ARG;
   *out = nullptr;
-  if (!m || !p) return RT_ERR_ARG;
+  if (!m_in || !p) return RT_ERR_ARG;
   rt_state *s = new rt_state();
+  // frequency groups: the kernels see n_groups copies of the base angle set,
+  // group j's weights scaled by group_w[j], ordered first halves of all
+  // groups then second halves (so angle k and k + A'/2 stay antipodes)
+  rt_mesh_desc mx = *m_in;
+  const rt_mesh_desc *m = &mx;
+  std::vector<double> gdir, gwt;
+  const int G = m_in->n_groups > 1 ? m_in->n_groups : 1;
+  s->n_groups = G;
+  if (G > 1) {
+    const int Ab = m_in->n_angles, Hb = Ab / 2;
+    double wsum = 0.0;
+    bool ok = m_in->group_w && Ab >= 2 && !(Ab & 1) && (int64_t)G * Ab <= 128 && G <= 8 &&
+              m_in->angle_dir && m_in->angle_w && p->integrator == RT_FIRST_ORDER && !p->boost &&
+              !p->gcl && p->beta_P == 0.0 && p->beta_J == 0.0;
+    for (int j = 0; ok && j < G; ++j) {
+      ok = std::isfinite(m_in->group_w[j]) && m_in->group_w[j] > 0;
+      wsum += ok ? m_in->group_w[j] : 0.0;
+    }
+    if (!ok || std::fabs(wsum - 1.0) > 1e-12) {
+      delete s;
+      return RT_ERR_ARG;
+    }
+    const int Ag = G * Ab;
+    gdir.resize(3 * (size_t)Ag);
+    gwt.resize(Ag);
+    s->col_of_angle.resize(Ag);
+    s->group_w.assign(m_in->group_w, m_in->group_w + G);
+    for (int k = 0; k < Ag; ++k) {
+      const bool second = k >= G * Hb;
+      const int kk = second ? k - G * Hb : k;
+      const int j = kk / Hb, a = kk % Hb + (second ? Hb : 0);
+      for (int d = 0; d < 3; ++d) gdir[3 * k + d] = m_in->angle_dir[3 * a + d];
+      gwt[k] = m_in->group_w[j] * m_in->angle_w[a];
+      s->col_of_angle[k] = j * Ab + a;
+    }
+    mx.n_angles = Ag;
+    mx.angle_dir = gdir.data();
+    mx.angle_w = gwt.data();
+  } else if (m_in->n_angles > 0) {
+    s->col_of_angle.resize(m_in->n_angles);
+    for (int k = 0; k < m_in->n_angles; ++k) s->col_of_angle[k] = k;
+  }
   int st = RT_OK;
   auto bail = [&](int code) {
     rt_destroy(s);
@@ -440,7 +482,7 @@ int rt_create(const rt_mesh_desc *m, const rt_params *p, void *stream, rt_state 
   for (int64_t ic = 0; ic < N; ++ic) vol_int[ic] = m->cell_volume[s->cell_of[ic]];
   for (int q = 0; q < A; ++q) {
     const int a = angle_of_position(q, A / 2, s->quad_end);
-    angle_of[q] = a;
+    angle_of[q] = s->col_of_angle[a];  // the caller column of the position's angle
     for (int d = 0; d < 3; ++d) dir64[3 * q + d] = m->angle_dir[3 * a + d];
     wt64[q] = m->angle_w[a];
   }
@@ -537,19 +579,36 @@ int rt_set_gas(rt_state *s, const double *rho, const double *e, const double *m,
   if (!s) return RT_ERR_ARG;
   if (!rho || !e || !m || !kP || !kJ || !kS) return fail(s, RT_ERR_ARG, "rt_set_gas: NULL array");
   const int64_t N = s->n_cells;
+  const int G = s->n_groups;  // opacity arrays hold G values per cell
   std::vector<rt::GasStatic> gs(N);
   std::vector<rt::GasDyn> gd(N);
+  std::vector<double> kapg(G > 1 ? (size_t)N * G * 3 : 0);
   for (int64_t ic = 0; ic < N; ++ic) {
     const int64_t c = s->cell_of[ic];
-    if (!(rho[c] > 0) || !(kP[c] >= 0) || !(kJ[c] >= 0) || !(kS[c] >= 0) || !std::isfinite(e[c]) ||
-        !std::isfinite(m[3 * c]) || !std::isfinite(m[3 * c + 1]) || !std::isfinite(m[3 * c + 2]) ||
-        !std::isfinite(kP[c] + kJ[c] + kS[c]))
-      return fail(s, RT_ERR_ARG, "rt_set_gas: rho must be > 0, opacities >= 0, all finite");
+    bool ok = rho[c] > 0 && std::isfinite(e[c]) && std::isfinite(m[3 * c]) &&
+              std::isfinite(m[3 * c + 1]) && std::isfinite(m[3 * c + 2]);
+    for (int j = 0; j < G; ++j) {
+      const int64_t k = c * G + j;
+      ok = ok && kP[k] >= 0 && kJ[k] >= 0 && kS[k] >= 0 && std::isfinite(kP[k] + kJ[k] + kS[k]);
+    }
+    if (!ok) return fail(s, RT_ERR_ARG, "rt_set_gas: rho must be > 0, opacities >= 0, all finite");
     const double rcv = rho[c] * s->params.r_gas / (s->params.gamma_gas - 1.0);
-    gs[ic] = {rho[c], rho[c] * kP[c], rho[c] * kJ[c], rho[c] * kS[c], 1.0 / rho[c], rcv,
-              (float)(rho[c] * kP[c]), (float)(rho[c] * kJ[c]), (float)(rho[c] * kS[c]),
+    const int64_t c0 = c * G;  // the grey record holds group 0's opacities
+    gs[ic] = {rho[c], rho[c] * kP[c0], rho[c] * kJ[c0], rho[c] * kS[c0], 1.0 / rho[c], rcv,
+              (float)(rho[c] * kP[c0]), (float)(rho[c] * kJ[c0]), (float)(rho[c] * kS[c0]),
               (float)rcv};
     gd[ic] = {e[c], m[3 * c], m[3 * c + 1], m[3 * c + 2]};
+    for (int j = 0; j < G && G > 1; ++j) {
+      double *k = &kapg[((size_t)ic * G + j) * 3];
+      k[0] = rho[c] * kP[c * G + j];
+      k[1] = rho[c] * kJ[c * G + j];
+      k[2] = rho[c] * kS[c * G + j];
+    }
+  }
+  if (G > 1) {
+    if (!s->d_kapg) RT_CUDA(s, dalloc(s, &s->d_kapg, kapg.size()));
+    RT_CUDA(s, cudaMemcpy(s->d_kapg, kapg.data(), sizeof(double) * kapg.size(),
+                          cudaMemcpyHostToDevice));
   }
   RT_CUDA(s, cudaMemcpyAsync(s->d_gs, gs.data(), sizeof(rt::GasStatic) * N, cudaMemcpyHostToDevice,
                              s->stream));
@@ -628,7 +687,7 @@ int rt_set_cells(rt_state *s, const uint8_t *kind, const double *tau, const doub
     std::vector<double> rows((size_t)n_rows * RS, 0.0);
     for (int64_t r = 0; r < n_rows; ++r)
       for (int q = 0; q < A; ++q)
-        rows[r * RS + q] = I0[r * A + angle_of_position(q, A / 2, s->quad_end)];
+        rows[r * RS + q] = I0[r * A + s->col_of_angle[angle_of_position(q, A / 2, s->quad_end)]];
     if (s->precision == RT_FP32) {
       std::vector<float> f(rows.begin(), rows.end());
       RT_CUDA(s, cudaMemcpy(s->d_I0, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
@@ -786,6 +845,8 @@ int rt_adjoint_step(rt_state *s, double dt, const void *I_n, const double *e_n, 
     return fail(s, RT_ERR_STATE, "rt_adjoint_step reverses steps on fixed cell volumes only");
   if (s->params.beta_P != 0.0 || s->params.beta_J != 0.0)
     return fail(s, RT_ERR_STATE, "rt_adjoint_step reverses steps with constant opacities only");
+  if (s->n_groups > 1)
+    return fail(s, RT_ERR_STATE, "rt_adjoint_step reverses grey steps only");
   if (!I_n || !e_n || !m_n || !lam_I1 || !lam_e1 || !lam_m1 || !lam_I || !lam_e || !lam_m ||
       !grad_kappa_P || !grad_kappa_J)
     return fail(s, RT_ERR_ARG, "rt_adjoint_step: NULL argument");
@@ -904,7 +965,7 @@ void rt_destroy(rt_state *s) {
     if (s->d_adj[k]) cudaFree(s->d_adj[k]);
   if (s->d_adj_ws) cudaFree(s->d_adj_ws);
   if (s->d_adj_stage) cudaFree(s->d_adj_stage);
-  void *bufs[] = {s->d_rkJ0, s->d_gcl_rate, s->d_gcl_kv, s->d_recon, s->d_lsq, s->d_Ihalf, s->d_grad, s->d_uface, s->d_slot_nb, s->d_wface, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
+  void *bufs[] = {s->d_kapg, s->d_rkJ0, s->d_gcl_rate, s->d_gcl_kv, s->d_recon, s->d_lsq, s->d_Ihalf, s->d_grad, s->d_uface, s->d_slot_nb, s->d_wface, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
                   s->d_gd, s->d_kind, s->d_aux, s->d_bc_row, s->d_I0, s->d_ext, s->d_dir, s->d_wt,
                   s->d_dir64, s->d_wt64, s->d_I[0], s->d_I[1], s->d_status, s->d_bad,
                   s->d_scratch, s->d_out16};

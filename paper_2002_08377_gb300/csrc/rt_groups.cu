@@ -1,0 +1,356 @@
+// Implicit source step of frequency groups (Sec. 2.3: groups that share the
+// angles and couple only through the gas temperature T^{n+1}), in place on
+// the transported rows I*.  Group j owns the angles whose pair index lies in
+// [j H, (j+1) H) (H = half the base angle set); its weights are W_j w_a.
+//
+// Blocks of 32 cells, each warp taking 4 cells in turn with its lanes over
+// the row positions of one cell:
+//   0  one lane per cell: v / c and every group's x / Gamma = dt cbar
+//      (rho kJ_j + rho ks_j);
+//   1  per cell and group, the comoving sums of Eq. (Jcom) over the group's
+//      angles, S_I,j = sum w~ Gamma^4 I* / (1 + x Gamma), S_G,j and
+//      S_1,j = sum w~ / (1 + x Gamma), with w~ = W_j w_a / Gamma^2
+//      unnormalised (the normalisation cancels within each group);
+//   2  one lane per cell in double: with D_j = S_1,j + dt cbar rho kJ_j S_G,j
+//      the temperature equation summed over the groups (Eq. com rad thermal
+//      disc), alpha = dt c a sum_j W_j rho kP_j S_1,j / D_j and
+//      g = e_int + dt c 4 pi sum_j W_j rho kJ_j S_I,j / D_j, its quartic
+//      root, and per group J~_j and q_j = dt cbar rho (kP_j B + ks_j J~_j);
+//   3  per cell, the new intensities (Eq. com radiative source disc per
+//      group) and the radiation change sum w (I* - I'), sum w n (I* - I');
+//   4  one lane per cell in double: the gas exchange (Eqs. gas1, gas2) or the
+//      tally of a boundary / emitter cell, and the frame velocity and
+//      internal energy of the next step.
+// First order in v/c; the grey step handles the boost, the geometric
+// conservation law and temperature-dependent opacities.
+#include <cuda_runtime.h>
+
+#include "rt_internal.cuh"
+#include "rt_step_common.cuh"
+
+namespace rt {
+namespace {
+
+using step::quartic_root;
+using step::rcp;
+
+constexpr int kWarps = 8;
+constexpr int kCellsPerWarp = 4;
+constexpr int kCells = kWarps * kCellsPerWarp;
+constexpr int kThreads = 32 * kWarps;
+constexpr int kMaxGroups = 8;
+
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename R> struct GroupArgs {
+  int64_t n;
+  int A, H, Hb, G, quad_end;  // A: all groups' angles, H = A / 2, Hb: H per group
+  const GasStatic *gs;
+  GasDyn *gd;
+  const double *kapg;  // [N][G][3] rho kappa_P, rho kappa_J, rho kappa_s
+  const uint8_t *kind;
+  const double2 *aux;
+  const int32_t *bc_row;
+  const R *I0;
+  const R *dir;  // [A][4] internal angle order
+  const R *wt2;  // [A/2][2]
+  R *I;          // [N][A] I* in, I^{n+1} out
+  R *cellv;      // [N][4]
+  double *ext;   // [N][4]
+  double W[kMaxGroups];
+  double dt, cbar, a_rad, k_dcr, k_alpha, k_g, k_fe, k_fm;
+  R dt_cbar_r, inv_c_r;
+  int newton_max_iter;
+  unsigned *status;
+  unsigned long long *bad_cell;
+};
+
+template <typename R, int NT> struct Lane {
+  R nx[NT], ny[NT], nz[NT], w[NT];
+  int q[NT], g[NT];
+};
+
+template <typename R, int NT>
+__device__ __forceinline__ Lane<R, NT> lane_angles(const GroupArgs<R> &a, int lane) {
+  Lane<R, NT> L;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const int q = lane + 32 * t;
+    L.q[t] = q;
+    L.g[t] = -1;
+    L.nx[t] = L.ny[t] = L.nz[t] = L.w[t] = R(0);
+    if (q < a.A) {
+      const int an = angle_of_position(q, a.H, a.quad_end);
+      const int p = an < a.H ? an : an - a.H;
+      L.g[t] = p / a.Hb;
+      L.nx[t] = a.dir[4 * an];
+      L.ny[t] = a.dir[4 * an + 1];
+      L.nz[t] = a.dir[4 * an + 2];
+      L.w[t] = a.wt2[2 * p + (an >= a.H ? 1 : 0)];
+    }
+  }
+  return L;
+}
+
+template <typename R> struct CellQ {
+  R x[kMaxGroups], q[kMaxGroups];  // per group x / Gamma and q (interior), or Y and Y I_src
+  R f;                             // boundary: min(dt / tau, 1)
+};
+
+template <typename R, int NT>
+__global__ void __launch_bounds__(kThreads) group_source_kernel(const GroupArgs<R> a) {
+  __shared__ R bx_s[kCells], by_s[kCells], bz_s[kCells];
+  __shared__ int kind_s[kCells];
+  __shared__ double sums[kCells][kMaxGroups][3];  // S_I, S_G, S_1 per group
+  __shared__ CellQ<R> cq[kCells];
+  __shared__ double dEF[kCells][4];
+  __shared__ unsigned bad_s[kCells];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int64_t c0 = (int64_t)blockIdx.x * kCells;
+  const int64_t cl = c0 + lane;
+  const bool lane_cell = warp == 0 && cl < a.n;
+  const int G = a.G;
+
+  // ---------------- phase 0
+  if (lane_cell) {
+    const GasStatic gs = a.gs[cl];
+    const GasDyn d = a.gd[cl];
+    const int kind = a.kind[cl];
+    kind_s[lane] = kind;
+    bx_s[lane] = R(d.mx * gs.inv_rho) * a.inv_c_r;
+    by_s[lane] = R(d.my * gs.inv_rho) * a.inv_c_r;
+    bz_s[lane] = R(d.mz * gs.inv_rho) * a.inv_c_r;
+    bad_s[lane] = 0;
+    CellQ<R> &Q = cq[lane];
+    for (int j = 0; j < G; ++j) {
+      const double *k = a.kapg + ((size_t)cl * G + j) * 3;
+      Q.x[j] = a.dt_cbar_r * R(k[1] + k[2]);
+      Q.q[j] = R(0);
+    }
+    Q.f = R(0);
+    if (kind == RT_CELL_BOUNDARY) {
+      const double2 ax = a.aux[cl];
+      Q.f = R((ax.x <= a.dt) ? 1.0 : a.dt / ax.x);
+    } else if (kind == RT_CELL_EMITTER) {
+      const double2 ax = a.aux[cl];
+      const R Y = R(a.dt * a.cbar * ax.x);
+      for (int j = 0; j < G; ++j) {
+        Q.x[j] = Y;
+        Q.q[j] = Y * R(ax.y);
+      }
+    }
+  }
+  __syncthreads();
+
+  const Lane<R, NT> L = lane_angles<R, NT>(a, lane);
+  R is[kCellsPerWarp][NT];
+#pragma unroll
+  for (int i = 0; i < kCellsPerWarp; ++i) {
+    const int64_t c = c0 + warp * kCellsPerWarp + i;
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+      is[i][t] = c < a.n && L.q[t] < a.A ? a.I[(size_t)c * a.A + L.q[t]] : R(0);
+  }
+
+  // ---------------- phase 1: per-group comoving sums of interior cells
+#pragma unroll
+  for (int i = 0; i < kCellsPerWarp; ++i) {
+    const int lc = warp * kCellsPerWarp + i;
+    if (c0 + lc >= a.n || kind_s[lc] != RT_CELL_INTERIOR) continue;
+    const R bx = bx_s[lc], by = by_s[lc], bz = bz_s[lc];
+    R sI[NT], sG[NT], s1[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      sI[t] = sG[t] = s1[t] = R(0);
+      if (L.q[t] < a.A) {
+        const R Gm = R(1) - fma(bx, L.nx[t], fma(by, L.ny[t], bz * L.nz[t]));
+        const R G2 = Gm * Gm;
+        const R tw = L.w[t] * rcp(G2 * fma(cq[lc].x[L.g[t]], Gm, R(1)));  // w~ / (1 + x Gamma)
+        s1[t] = tw;
+        sI[t] = tw * G2 * G2 * is[i][t];
+        sG[t] = tw * Gm;
+      }
+    }
+    for (int j = 0; j < G; ++j) {
+      R pI = 0, pG = 0, p1 = 0;
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+        if (L.g[t] == j) {
+          pI += sI[t];
+          pG += sG[t];
+          p1 += s1[t];
+        }
+      const double SI = warp_sum((double)pI), SG = warp_sum((double)pG),
+                   S1 = warp_sum((double)p1);
+      if (lane == 0) {
+        sums[lc][j][0] = SI;
+        sums[lc][j][1] = SG;
+        sums[lc][j][2] = S1;
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---------------- phase 2: the temperature equation over all groups
+  if (lane_cell && kind_s[lane] == RT_CELL_INTERIOR) {
+    const GasStatic gs = a.gs[cl];
+    const GasDyn d = a.gd[cl];
+    const double eint = d.e - 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * gs.inv_rho;
+    double alpha = 0.0, gq = eint, rU[kMaxGroups];
+    for (int j = 0; j < G; ++j) {
+      const double *k = a.kapg + ((size_t)cl * G + j) * 3;
+      rU[j] = 1.0 / fma(a.k_dcr * k[1], sums[lane][j][1], sums[lane][j][2]);
+      alpha += a.W[j] * a.k_alpha * k[0] * sums[lane][j][2] * rU[j];
+      gq += a.W[j] * a.k_g * k[1] * sums[lane][j][0] * rU[j];
+    }
+    double T = 0.0;
+    unsigned bad = 0;
+    if (!(gq >= 0.0) || !(alpha >= 0.0)) {
+      bad |= ST_NONFINITE;
+    } else if (quartic_root(alpha, gs.rcv, gq, eint / gs.rcv, 1e-15, a.newton_max_iter, &T)) {
+      bad |= ST_NONCONV;
+    }
+    const double B = a.a_rad * (T * T) * (T * T) * (1.0 / (4.0 * kPi));
+    for (int j = 0; j < G; ++j) {
+      const double *k = a.kapg + ((size_t)cl * G + j) * 3;
+      const double dP = a.k_dcr * k[0], dS = a.k_dcr * k[2];
+      const double J = fma(dP * B, sums[lane][j][1], sums[lane][j][0]) * rU[j];
+      cq[lane].q[j] = R(fma(dP, B, dS * J));
+    }
+    bad_s[lane] = bad;
+  }
+  __syncthreads();
+
+  // ---------------- phase 3: new intensities and the radiation change
+#pragma unroll
+  for (int i = 0; i < kCellsPerWarp; ++i) {
+    const int lc = warp * kCellsPerWarp + i;
+    const int64_t c = c0 + lc;
+    if (c >= a.n) continue;
+    const int kind = kind_s[lc];
+    const R bx = bx_s[lc], by = by_s[lc], bz = bz_s[lc];
+    const R *I0row = kind == RT_CELL_BOUNDARY ? a.I0 + (size_t)a.bc_row[c] * a.A : nullptr;
+    R de = 0, dfx = 0, dfy = 0, dfz = 0;
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+      if (L.q[t] < a.A) {
+        const R Is = is[i][t];
+        R In;
+        if (kind == RT_CELL_BOUNDARY) {
+          In = fma(-cq[lc].f, Is - I0row[L.q[t]], Is);
+        } else {
+          // I' = (I* Gamma^3 + q) / (Gamma^3 (1 + x Gamma))
+          const R Gm = R(1) - fma(bx, L.nx[t], fma(by, L.ny[t], bz * L.nz[t]));
+          const R G3 = Gm * Gm * Gm;
+          const int j = L.g[t];
+          In = fma(Is, G3, cq[lc].q[j]) * rcp(G3 * fma(cq[lc].x[j], Gm, R(1)));
+        }
+        a.I[(size_t)c * a.A + L.q[t]] = In;
+        const R dw = L.w[t] * (Is - In);
+        de += dw;
+        dfx = fma(L.nx[t], dw, dfx);
+        dfy = fma(L.ny[t], dw, dfy);
+        dfz = fma(L.nz[t], dw, dfz);
+      }
+    const double sE = warp_sum((double)de), sx = warp_sum((double)dfx),
+                 sy = warp_sum((double)dfy), sz = warp_sum((double)dfz);
+    if (lane == 0) {
+      dEF[lc][0] = sE;
+      dEF[lc][1] = sx;
+      dEF[lc][2] = sy;
+      dEF[lc][3] = sz;
+    }
+  }
+  __syncthreads();
+
+  // ---------------- phase 4: gas exchange, one lane per cell
+  if (lane_cell) {
+    const double dE = a.k_fe * dEF[lane][0];
+    const double dx = a.k_fm * dEF[lane][1], dy = a.k_fm * dEF[lane][2], dz = a.k_fm * dEF[lane][3];
+    unsigned bad = bad_s[lane];
+    if (!isfinite(dE)) bad |= ST_NONFINITE;
+    if (kind_s[lane] == RT_CELL_INTERIOR) {
+      GasDyn d = a.gd[cl];
+      d.e += dE;
+      d.mx += dx;
+      d.my += dy;
+      d.mz += dz;
+      a.gd[cl] = d;
+      const double ir = a.gs[cl].inv_rho;
+      const double kin = 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * ir;
+      R *cv = a.cellv + 4 * cl;
+      cv[0] = R(d.mx * ir);
+      cv[1] = R(d.my * ir);
+      cv[2] = R(d.mz * ir);
+      cv[3] = R(d.e - kin);
+    } else {
+      double *x = a.ext + 4 * cl;
+      x[0] += dE;
+      x[1] += dx;
+      x[2] += dy;
+      x[3] += dz;
+    }
+    if (bad) {
+      atomicOr(a.status, bad);
+      atomicMin(a.bad_cell, (unsigned long long)cl);
+    }
+  }
+}
+
+template <typename R> cudaError_t launch(rt_state *s, double dt, void *Is) {
+  GroupArgs<R> a{};
+  a.n = s->n_cells;
+  a.A = s->n_angles;
+  a.H = a.A / 2;
+  a.G = s->n_groups;
+  a.Hb = a.H / a.G;
+  a.quad_end = s->quad_end;
+  a.gs = s->d_gs;
+  a.gd = s->d_gd;
+  a.kapg = s->d_kapg;
+  a.kind = s->d_kind;
+  a.aux = s->d_aux;
+  a.bc_row = s->d_bc_row;
+  a.I0 = reinterpret_cast<const R *>(s->d_I0);
+  a.dir = reinterpret_cast<const R *>(s->d_dir);
+  a.wt2 = reinterpret_cast<const R *>(s->d_wt);
+  a.I = reinterpret_cast<R *>(Is);
+  a.cellv = reinterpret_cast<R *>(s->d_cellv);
+  a.ext = s->d_ext;
+  for (int j = 0; j < a.G && j < kMaxGroups; ++j) a.W[j] = s->group_w[j];
+  a.dt = dt;
+  a.cbar = s->params.cbar;
+  a.a_rad = s->params.a_rad;
+  a.k_dcr = dt * s->params.cbar;
+  a.k_alpha = dt * s->params.c * s->params.a_rad;
+  a.k_g = dt * s->params.c * 4.0 * kPi;
+  a.k_fe = s->params.c / s->params.cbar * 4.0 * kPi;
+  a.k_fm = 4.0 * kPi / s->params.cbar;
+  a.dt_cbar_r = R(dt * s->params.cbar);
+  a.inv_c_r = R(1.0 / s->params.c);
+  a.newton_max_iter = s->params.newton_max_iter;
+  a.status = s->d_status;
+  a.bad_cell = s->d_bad;
+  const unsigned g = (unsigned)((a.n + kCells - 1) / kCells);
+  switch ((a.A + 31) / 32) {
+    case 1: group_source_kernel<R, 1><<<g, kThreads, 0, s->stream>>>(a); break;
+    case 2: group_source_kernel<R, 2><<<g, kThreads, 0, s->stream>>>(a); break;
+    case 3: group_source_kernel<R, 3><<<g, kThreads, 0, s->stream>>>(a); break;
+    default: group_source_kernel<R, 4><<<g, kThreads, 0, s->stream>>>(a); break;
+  }
+  s->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_group_source(rt_state *s, double dt, void *Is) {
+  if (s->n_groups > kMaxGroups) return cudaErrorInvalidValue;
+  return s->precision == RT_FP32 ? launch<float>(s, dt, Is) : launch<double>(s, dt, Is);
+}
+
+}  // namespace rt

@@ -169,6 +169,14 @@ struct rt_state {
   float *d_gcl_kv = nullptr;
   // temperature-dependent kappa_J: rho kappa_J at T_ref (internal order)
   double *d_rkJ0 = nullptr;
+  // frequency groups (1: grey): the kernels see n_groups copies of the base
+  // angle set as one set in the internal angle order (first halves of all
+  // groups, then the second halves); col_of_angle maps an internal angle to
+  // its caller column j A + a; d_kapg [N][n_groups][3] rho kappa_P, J, s
+  int n_groups = 1;
+  std::vector<double> group_w;
+  std::vector<int32_t> col_of_angle;
+  double *d_kapg = nullptr;
   void *d_inv_vol = nullptr;
   int64_t *d_cell_of = nullptr;  // internal -> caller
   double *d_volume = nullptr;    // internal order
@@ -214,6 +222,9 @@ cudaError_t launch_step_io(rt_state *s, double dt, const StepIO &io);
 // adjoint = false: I* = I - dt/V sum_f u I_up; adjoint = true: the
 // transposed operator, from rows L = dt/V lambda to M^T lambda.
 cudaError_t launch_transport(rt_state *s, double dt, const void *in, void *out, bool adjoint);
+// The coupled source step of frequency groups (rt_groups.cu), in place on
+// the transported rows I* (stride row_stride).
+cudaError_t launch_group_source(rt_state *s, double dt, void *Is);
 // The van Leer step (rt_recon.cu); leaves I^{n+1} in d_I[cur ^ 1].
 cudaError_t launch_step_vl(rt_state *s, double dt);
 // Double states: fills d_uface (allocates it on first use).

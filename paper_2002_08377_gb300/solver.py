@@ -30,7 +30,7 @@ class RTSolver:
 
     def __init__(self, mesh, dirs, weights, *, cbar, c, a_rad=1.0, gamma_gas=5.0 / 3.0,
                  r_gas=1.0, cfl=0.3, precision="fp32", newton_max_iter=64, integrator=0, boost=0, gcl=0,
-                 beta_P=0.0, beta_J=0.0, T_ref=1.0,
+                 beta_P=0.0, beta_J=0.0, T_ref=1.0, n_groups=1, group_w=None,
                  stream=None):
         if torch is None or not torch.cuda.is_available():
             raise RuntimeError("RTSolver needs a CUDA device (no CPU fallback exists)")
@@ -38,7 +38,9 @@ class RTSolver:
         self.precision = precision
         self.dtype = np.float32 if precision == "fp32" else np.float64
         self.tdtype = torch.float32 if precision == "fp32" else torch.float64
-        self.N, self.A = int(mesh.n_cells), int(np.asarray(dirs).shape[0])
+        # with frequency groups the intensities are [N][n_groups * A]
+        self.N = int(mesh.n_cells)
+        self.A = int(np.asarray(dirs).shape[0]) * max(1, int(n_groups))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         keep = self._keep = []
 
@@ -50,7 +52,10 @@ class RTSolver:
             return a.ctypes.data
 
         md = capi.MeshDesc()
-        md.n_cells, md.n_faces, md.n_angles = self.N, int(mesh.n_faces), self.A
+        md.n_cells, md.n_faces = self.N, int(mesh.n_faces)
+        md.n_angles = int(np.asarray(dirs).shape[0])
+        md.n_groups = int(n_groups)
+        md.group_w = ptr(group_w, np.float64) if int(n_groups) > 1 else None
         md.cell_volume = ptr(mesh.cell_volume, np.float64)
         md.cell_centroid = ptr(mesh.cell_centroid, np.float64)
         md.face_cells = ptr(mesh.face_cells, np.int32)
@@ -82,7 +87,8 @@ class RTSolver:
         kw.setdefault("integrator", getattr(prob, "integrator", 0))
         kw.setdefault("boost", getattr(prob, "boost", 0))
         kw.setdefault("gcl", getattr(prob, "gcl", 0))
-        for k, d in (("beta_P", 0.0), ("beta_J", 0.0), ("T_ref", 1.0)):
+        for k, d in (("beta_P", 0.0), ("beta_J", 0.0), ("T_ref", 1.0), ("n_groups", 1),
+                     ("group_w", None)):
             kw.setdefault(k, getattr(prob, k, d))
         s = cls(prob.mesh, prob.dirs, prob.weights, cbar=prob.cbar, c=prob.c, a_rad=prob.a_rad,
                 gamma_gas=prob.gamma_gas, r_gas=prob.r_gas, cfl=prob.cfl, precision=precision, **kw)

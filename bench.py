@@ -38,8 +38,8 @@ UNIT = "cell-angle updates/s"
 # the 128^3 workload by the cell count (traffic grows with the cells
 # processed); valid while the step kernel's device source has the recorded
 # hash.
-NCU_TRAFFIC = {"fp32": 963.52256e6 * 2097152 / 884736, "fp64": 5907.678208e6 * 2097152 / 884736}
-NCU_SOURCE_SHA = "9006360aa081b036"
+NCU_TRAFFIC = {"fp32": 962.701056e6 * 2097152 / 884736, "fp64": 5907.995648e6 * 2097152 / 884736}
+NCU_SOURCE_SHA = "09f34c97cadb3995"
 # FP64 arithmetic peak of the GPU (dense FMA, from the hardware's nominal
 # figure); the FP64 state is bound by it, not by HBM.
 FP64_PEAK_GFLOPS = 1250.0

@@ -101,6 +101,39 @@ template <typename R> struct CellQ {
   R f;                             // boundary: min(dt / tau, 1)
 };
 
+template <typename C> __device__ __forceinline__ C chain_tol();
+template <> __device__ __forceinline__ float chain_tol<float>() { return 1e-7f; }
+template <> __device__ __forceinline__ double chain_tol<double>() { return 1e-15; }
+
+// Phase 2 of one interior cell in the compute type C: with D_j = S_1,j +
+// dt cbar rho kJ_j S_G,j, the group-weighted quartic alpha T^4 + rho c_v T = g
+// and every group's q_j.  Returns the status bits, or -1 when a result is
+// not finite (the caller then repeats it in double).
+template <typename C, typename R>
+__device__ int group_chain(const GroupArgs<R> &a, int64_t cl, const double (*sm)[3], double eint,
+                           double rcv, C *q) {
+  const int G = a.G;
+  C alpha = 0, gq = C(eint), rU[kMaxGroups];
+  for (int j = 0; j < G; ++j) {
+    const double *k = a.kapg + ((size_t)cl * G + j) * 3;
+    rU[j] = C(1) / fma(C(a.k_dcr * k[1]), C(sm[j][1]), C(sm[j][2]));
+    alpha += C(a.W[j] * a.k_alpha * k[0]) * C(sm[j][2]) * rU[j];
+    gq += C(a.W[j] * a.k_g * k[1]) * C(sm[j][0]) * rU[j];
+  }
+  if (!(gq >= C(0)) || !(alpha >= C(0))) return sizeof(C) == 4 ? -1 : (int)ST_NONFINITE;
+  C T;
+  const int nc = quartic_root(alpha, C(rcv), gq, C(eint / rcv), chain_tol<C>(), a.newton_max_iter, &T);
+  const C B = C(a.a_rad * (1.0 / (4.0 * kPi))) * (T * T) * (T * T);
+  for (int j = 0; j < G; ++j) {
+    const double *k = a.kapg + ((size_t)cl * G + j) * 3;
+    const C dP = C(a.k_dcr * k[0]), dS = C(a.k_dcr * k[2]);
+    const C J = fma(dP * B, C(sm[j][1]), C(sm[j][0])) * rU[j];
+    q[j] = fma(dP, B, dS * J);
+    if (sizeof(C) == 4 && !isfinite(q[j])) return -1;
+  }
+  return nc ? (int)ST_NONCONV : 0;
+}
+
 template <typename R, int NT>
 __global__ void __launch_bounds__(kThreads) group_source_kernel(const GroupArgs<R> a) {
   __shared__ R bx_s[kCells], by_s[kCells], bz_s[kCells];
@@ -184,8 +217,8 @@ __global__ void __launch_bounds__(kThreads) group_source_kernel(const GroupArgs<
           pG += sG[t];
           p1 += s1[t];
         }
-      const double SI = warp_sum((double)pI), SG = warp_sum((double)pG),
-                   S1 = warp_sum((double)p1);
+      // reduced in the state precision (a double reduction costs FP64 adds)
+      const R SI = warp_sum(pI), SG = warp_sum(pG), S1 = warp_sum(p1);
       if (lane == 0) {
         sums[lc][j][0] = SI;
         sums[lc][j][1] = SG;
@@ -200,26 +233,24 @@ __global__ void __launch_bounds__(kThreads) group_source_kernel(const GroupArgs<
     const GasStatic gs = a.gs[cl];
     const GasDyn d = a.gd[cl];
     const double eint = d.e - 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * gs.inv_rho;
-    double alpha = 0.0, gq = eint, rU[kMaxGroups];
-    for (int j = 0; j < G; ++j) {
-      const double *k = a.kapg + ((size_t)cl * G + j) * 3;
-      rU[j] = 1.0 / fma(a.k_dcr * k[1], sums[lane][j][1], sums[lane][j][2]);
-      alpha += a.W[j] * a.k_alpha * k[0] * sums[lane][j][2] * rU[j];
-      gq += a.W[j] * a.k_g * k[1] * sums[lane][j][0] * rU[j];
-    }
-    double T = 0.0;
     unsigned bad = 0;
-    if (!(gq >= 0.0) || !(alpha >= 0.0)) {
-      bad |= ST_NONFINITE;
-    } else if (quartic_root(alpha, gs.rcv, gq, eint / gs.rcv, 1e-15, a.newton_max_iter, &T)) {
-      bad |= ST_NONCONV;
+    bool done = false;
+    if constexpr (sizeof(R) == 4) {
+      // float states: the chain in float, as the grey float step solves its
+      // quartic; repeated in double if a result is not finite
+      float q[kMaxGroups];
+      const int st = group_chain<float>(a, cl, sums[lane], eint, gs.rcv, q);
+      if (st >= 0) {
+        for (int j = 0; j < G; ++j) cq[lane].q[j] = q[j];
+        bad = st;
+        done = true;
+      }
     }
-    const double B = a.a_rad * (T * T) * (T * T) * (1.0 / (4.0 * kPi));
-    for (int j = 0; j < G; ++j) {
-      const double *k = a.kapg + ((size_t)cl * G + j) * 3;
-      const double dP = a.k_dcr * k[0], dS = a.k_dcr * k[2];
-      const double J = fma(dP * B, sums[lane][j][1], sums[lane][j][0]) * rU[j];
-      cq[lane].q[j] = R(fma(dP, B, dS * J));
+    if (!done) {
+      double q[kMaxGroups];
+      const int st = group_chain<double>(a, cl, sums[lane], eint, gs.rcv, q);
+      for (int j = 0; j < G; ++j) cq[lane].q[j] = R(q[j]);
+      bad = st < 0 ? ST_NONFINITE : (unsigned)st;
     }
     bad_s[lane] = bad;
   }
@@ -256,8 +287,7 @@ __global__ void __launch_bounds__(kThreads) group_source_kernel(const GroupArgs<
         dfy = fma(L.ny[t], dw, dfy);
         dfz = fma(L.nz[t], dw, dfz);
       }
-    const double sE = warp_sum((double)de), sx = warp_sum((double)dfx),
-                 sy = warp_sum((double)dfy), sz = warp_sum((double)dfz);
+    const R sE = warp_sum(de), sx = warp_sum(dfx), sy = warp_sum(dfy), sz = warp_sum(dfz);
     if (lane == 0) {
       dEF[lc][0] = sE;
       dEF[lc][1] = sx;

@@ -606,8 +606,14 @@ int rt_set_gas(rt_state *s, const double *rho, const double *e, const double *m,
     }
   }
   if (G > 1) {
+    std::vector<float> kapgf((size_t)N * G * 4, 0.0f);
+    for (size_t i = 0; i < (size_t)N * G; ++i)
+      for (int k = 0; k < 3; ++k) kapgf[4 * i + k] = (float)kapg[3 * i + k];
     if (!s->d_kapg) RT_CUDA(s, dalloc(s, &s->d_kapg, kapg.size()));
+    if (!s->d_kapgf) RT_CUDA(s, dalloc(s, &s->d_kapgf, kapgf.size()));
     RT_CUDA(s, cudaMemcpy(s->d_kapg, kapg.data(), sizeof(double) * kapg.size(),
+                          cudaMemcpyHostToDevice));
+    RT_CUDA(s, cudaMemcpy(s->d_kapgf, kapgf.data(), sizeof(float) * kapgf.size(),
                           cudaMemcpyHostToDevice));
   }
   RT_CUDA(s, cudaMemcpyAsync(s->d_gs, gs.data(), sizeof(rt::GasStatic) * N, cudaMemcpyHostToDevice,
@@ -965,7 +971,7 @@ void rt_destroy(rt_state *s) {
     if (s->d_adj[k]) cudaFree(s->d_adj[k]);
   if (s->d_adj_ws) cudaFree(s->d_adj_ws);
   if (s->d_adj_stage) cudaFree(s->d_adj_stage);
-  void *bufs[] = {s->d_kapg, s->d_rkJ0, s->d_gcl_rate, s->d_gcl_kv, s->d_recon, s->d_lsq, s->d_Ihalf, s->d_grad, s->d_uface, s->d_slot_nb, s->d_wface, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
+  void *bufs[] = {s->d_kapgf, s->d_kapg, s->d_rkJ0, s->d_gcl_rate, s->d_gcl_kv, s->d_recon, s->d_lsq, s->d_Ihalf, s->d_grad, s->d_uface, s->d_slot_nb, s->d_wface, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
                   s->d_gd, s->d_kind, s->d_aux, s->d_bc_row, s->d_I0, s->d_ext, s->d_dir, s->d_wt,
                   s->d_dir64, s->d_wt64, s->d_I[0], s->d_I[1], s->d_status, s->d_bad,
                   s->d_scratch, s->d_out16};

@@ -27,6 +27,7 @@
 
 #include "rt_internal.cuh"
 #include "rt_step_common.cuh"
+#include "rt_step_tile.cuh"
 
 namespace rt {
 namespace {
@@ -67,6 +68,10 @@ template <typename R> struct GroupArgs {
   int newton_max_iter;
   unsigned *status;
   unsigned long long *bad_cell;
+  // float states (tile kernel): float copies of the group opacities and of
+  // the coefficients, W_j dt c a and W_j dt c 4 pi per group
+  const float *kapgf;  // [N][G][4]
+  float k_dcr_f, a_rad_4pi_f, Wk_alpha_f[kMaxGroups], Wk_g_f[kMaxGroups];
 };
 
 template <typename R, int NT> struct Lane {
@@ -130,6 +135,43 @@ __device__ int group_chain(const GroupArgs<R> &a, int64_t cl, const double (*sm)
     const C J = fma(dP * B, C(sm[j][1]), C(sm[j][0])) * rU[j];
     q[j] = fma(dP, B, dS * J);
     if (sizeof(C) == 4 && !isfinite(q[j])) return -1;
+  }
+  return nc ? (int)ST_NONCONV : 0;
+}
+
+// The temperature equation of one interior cell in float from float inputs
+// (tile kernel, float states): per group rho kP_j, rho kJ_j, rho ks_j in kf
+// and the sums S_I,j, S_G,j, S_1,j.  Returns the status bits, or -1 when a
+// result is not finite (the caller then takes group_chain<double>).
+constexpr int kTileGroups = 4;
+__device__ __forceinline__ int group_chain_f(const GroupArgs<float> &a, const float4 (&kf)[kTileGroups],
+                                             const float (&SI)[kTileGroups],
+                                             const float (&SG)[kTileGroups],
+                                             const float (&S1)[kTileGroups], float eint, float rcv,
+                                             float (&q)[kTileGroups]) {
+  float alpha = 0.0f, gq = eint, rU[kTileGroups];
+#pragma unroll
+  for (int j = 0; j < kTileGroups; ++j) {
+    rU[j] = 0.0f;
+    if (j < a.G) {
+      rU[j] = rcp(fmaf(a.k_dcr_f * kf[j].y, SG[j], S1[j]));
+      alpha = fmaf(a.Wk_alpha_f[j] * kf[j].x * S1[j], rU[j], alpha);
+      gq = fmaf(a.Wk_g_f[j] * kf[j].y * SI[j], rU[j], gq);
+    }
+  }
+  if (!(gq >= 0.0f) || !(alpha >= 0.0f) || !isfinite(alpha) || !isfinite(gq)) return -1;
+  float T;
+  const int nc = quartic_root(alpha, rcv, gq, eint * rcp(rcv), 1e-7f, a.newton_max_iter, &T);
+  const float B = a.a_rad_4pi_f * (T * T) * (T * T);
+#pragma unroll
+  for (int j = 0; j < kTileGroups; ++j) {
+    q[j] = 0.0f;
+    if (j < a.G) {
+      const float dP = a.k_dcr_f * kf[j].x, dS = a.k_dcr_f * kf[j].z;
+      const float J = fmaf(dP * B, SG[j], SI[j]) * rU[j];
+      q[j] = fmaf(dP, B, dS * J);
+      if (!isfinite(q[j])) return -1;
+    }
   }
   return nc ? (int)ST_NONCONV : 0;
 }
@@ -331,6 +373,305 @@ __global__ void __launch_bounds__(kThreads) group_source_kernel(const GroupArgs<
   }
 }
 
+// ------------------------------------------------------------ tile kernel
+// The same step for up to kTileGroups groups on the step kernel's tile
+// mapping (blocks of 32 cells x 8 threads, a thread owning the pairs of its
+// pair / quad map).  The group of pair p is p / Hb, and every sum is kept
+// per group (unused groups stay zero).  Float states solve the temperature
+// equation in all 8 lanes of a cell in float, from float copies of the group
+// opacities (in double if a result is not finite), with no block barrier;
+// double states solve it one lane per cell between two barriers.  The gas
+// exchange is one lane per cell in double after a barrier, as in the grey
+// step.
+template <typename R> struct TileShared {
+  double s[CPB][kTileGroups][3];  // double states: S_I, S_G, S_1 per group
+  R q[CPB][kTileGroups];
+  R dE[CPB], dF[3][CPB];
+  unsigned bad[CPB];
+};
+
+// rho kappa_J + rho kappa_s of group g of cell c, in the state precision
+__device__ __forceinline__ float group_xs(const GroupArgs<float> &a, int64_t c, int g) {
+  const float4 k = reinterpret_cast<const float4 *>(a.kapgf)[(size_t)c * a.G + g];
+  return k.y + k.z;
+}
+__device__ __forceinline__ double group_xs(const GroupArgs<double> &a, int64_t c, int g) {
+  const double *k = a.kapg + ((size_t)c * a.G + g) * 3;
+  return k[1] + k[2];
+}
+
+template <typename R, typename M>
+__global__ void __launch_bounds__(step::NT, 2) group_source_tile(const GroupArgs<R> a) {
+  using V = step::pair_t<R>;
+  using step::mk;
+  using step::padd;
+  using step::pfma;
+  using step::pmul;
+  using step::psub;
+  constexpr int PPT = M::PPT;
+  constexpr int NG = kTileGroups;
+  __shared__ TileShared<R> sh;
+  const int lc = threadIdx.x / step::KT, sub = threadIdx.x % step::KT;
+  const int64_t cell = (int64_t)blockIdx.x * CPB + lc;
+  const bool live = cell < a.n;
+  const int64_t c = live ? cell : a.n - 1;  // dead lanes shadow the last cell
+  const int np = M::count(a.H, sub);
+  R Ia[PPT], Ib[PPT], nx[PPT], ny[PPT], nz[PPT];
+  int gp[PPT];
+  M::load(a.I + (size_t)c * a.A, sub, Ia, Ib, np);
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) {
+    const int p = (M::FULL || j < np) ? M::pair(j, sub) : 0;
+    step::load_dir(a.dir, p, nx[j], ny[j], nz[j]);
+    gp[j] = p / a.Hb;
+  }
+  const int kind = a.kind[c];
+  const R vxc = a.cellv[4 * c] * a.inv_c_r, vyc = a.cellv[4 * c + 1] * a.inv_c_r,
+          vzc = a.cellv[4 * c + 2] * a.inv_c_r;
+  R xs[NG];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) xs[g] = g < a.G ? a.dt_cbar_r * R(group_xs(a, c, g)) : R(0);
+  const V *W2 = reinterpret_cast<const V *>(a.wt2);
+  const V one = mk(R(1), R(1));
+
+  // ---------------- phase A: per-group comoving sums (interior cells)
+  V sIv[NG], sGv[NG], s1v[NG];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) sIv[g] = sGv[g] = s1v[g] = mk(R(0), R(0));
+  if (kind == RT_CELL_INTERIOR) {
+#pragma unroll
+    for (int j = 0; j < PPT; ++j)
+      if (M::FULL || j < np) {
+        R xg = xs[0];
+#pragma unroll
+        for (int g = 1; g < NG; ++g) xg = gp[j] == g ? xs[g] : xg;
+        const R bn = fma(vxc, nx[j], fma(vyc, ny[j], vzc * nz[j]));
+        const V Gv = mk(R(1) - bn, R(1) + bn);
+        const V G2 = pmul(Gv, Gv);
+        const V t = pmul(W2[M::pair(j, sub)], step::prcp<R>(pmul(G2, pfma(mk(xg, xg), Gv, one))));
+        const V tI = pmul(pmul(t, pmul(G2, G2)), mk(Ia[j], Ib[j]));
+        const V tG = pmul(t, Gv);
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+          if (gp[j] == g) {
+            s1v[g] = padd(s1v[g], t);
+            sIv[g] = padd(sIv[g], tI);
+            sGv[g] = padd(sGv[g], tG);
+          }
+      }
+  }
+  R sI[NG], sG[NG], s1[NG];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    sI[g] = step::cell_sum(sIv[g].x + sIv[g].y);
+    sG[g] = step::cell_sum(sGv[g].x + sGv[g].y);
+    s1[g] = step::cell_sum(s1v[g].x + s1v[g].y);
+  }
+
+
+  // ---------------- phase B: the temperature equation over all groups
+  R q[NG];
+  unsigned bad = 0;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) q[g] = R(0);
+  if constexpr (sizeof(R) == 4) {
+    if (kind == RT_CELL_INTERIOR) {
+      float4 kf[NG];
+#pragma unroll
+      for (int g = 0; g < NG; ++g)
+        kf[g] = g < a.G ? reinterpret_cast<const float4 *>(a.kapgf)[(size_t)c * a.G + g]
+                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      const int st = group_chain_f(a, kf, sI, sG, s1, a.cellv[4 * c + 3], a.gs[c].frcv, q);
+      if (st >= 0) {
+        bad = st;
+      } else {
+        double sm[kMaxGroups][3], qd[kMaxGroups];
+        for (int g = 0; g < a.G && g < NG; ++g) {
+          sm[g][0] = sI[g];
+          sm[g][1] = sG[g];
+          sm[g][2] = s1[g];
+        }
+        const GasDyn d = a.gd[c];
+        const GasStatic gs = a.gs[c];
+        const double eint = d.e - 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * gs.inv_rho;
+        bad = group_chain<double>(a, c, sm, eint, gs.rcv, qd);
+#pragma unroll
+        for (int g = 0; g < NG; ++g) q[g] = g < a.G ? R(qd[g]) : R(0);
+      }
+    }
+  } else {
+    if (sub == 0) {
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        sh.s[lc][g][0] = sI[g];
+        sh.s[lc][g][1] = sG[g];
+        sh.s[lc][g][2] = s1[g];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < CPB) {
+      const int lp = threadIdx.x;
+      const int64_t cl = (int64_t)blockIdx.x * CPB + lp;
+      unsigned bl = 0;
+      if (cl < a.n && a.kind[cl] == RT_CELL_INTERIOR) {
+        const GasDyn d = a.gd[cl];
+        const GasStatic gs = a.gs[cl];
+        const double eint = d.e - 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * gs.inv_rho;
+        double qd[kMaxGroups];
+        bl = group_chain<double>(a, cl, sh.s[lp], eint, gs.rcv, qd);
+        for (int g = 0; g < a.G && g < NG; ++g) sh.q[lp][g] = R(qd[g]);
+      }
+      sh.bad[lp] = bl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int g = 0; g < NG; ++g) q[g] = g < a.G ? sh.q[lc][g] : R(0);
+    bad = sh.bad[lc];
+  }
+
+  // ---------------- phase C: new intensities and the radiation change
+  R na[PPT], nb[PPT];
+  if (kind == RT_CELL_BOUNDARY) {
+    const double2 ax = a.aux[c];
+    const R f = R((ax.x <= a.dt) ? 1.0 : a.dt / ax.x);
+    R tx[PPT], ty[PPT];
+    M::load(a.I0 + (size_t)a.bc_row[c] * a.A, sub, tx, ty, np);
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      na[j] = fma(-f, Ia[j] - tx[j], Ia[j]);
+      nb[j] = fma(-f, Ib[j] - ty[j], Ib[j]);
+    }
+  } else {
+    // I' = (I* Gamma^3 + q) / (Gamma^3 (1 + x Gamma)); emitters: x -> dt cbar
+    // (rho kappa)_src and q -> that rate times I_src in every group
+    const bool em = kind == RT_CELL_EMITTER;
+    R xe = R(0), qe = R(0);
+    if (em) {
+      const double2 ax = a.aux[c];
+      xe = R(a.dt * a.cbar * ax.x);
+      qe = xe * R(ax.y);
+    }
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      R xg = xs[0], qg = q[0];
+#pragma unroll
+      for (int g = 1; g < NG; ++g) {
+        xg = gp[j] == g ? xs[g] : xg;
+        qg = gp[j] == g ? q[g] : qg;
+      }
+      if (em) {
+        xg = xe;
+        qg = qe;
+      }
+      const R bn = fma(vxc, nx[j], fma(vyc, ny[j], vzc * nz[j]));
+      const V Gv = mk(R(1) - bn, R(1) + bn);
+      const V G3 = pmul(pmul(Gv, Gv), Gv);
+      const V n = pmul(pfma(mk(Ia[j], Ib[j]), G3, mk(qg, qg)),
+                       step::prcp<R>(pmul(G3, pfma(mk(xg, xg), Gv, one))));
+      na[j] = n.x;
+      nb[j] = n.y;
+    }
+  }
+  if (live) M::store(a.I + (size_t)c * a.A, sub, na, nb, np);
+  V dev = mk(R(0), R(0));
+  R dfx = 0, dfy = 0, dfz = 0;
+#pragma unroll
+  for (int j = 0; j < PPT; ++j)
+    if (M::FULL || j < np) {
+      const V d = pmul(W2[M::pair(j, sub)], psub(mk(Ia[j], Ib[j]), mk(na[j], nb[j])));
+      dev = padd(dev, d);
+      const R df = d.x - d.y;  // the antipode has direction -n
+      dfx = fma(nx[j], df, dfx);
+      dfy = fma(ny[j], df, dfy);
+      dfz = fma(nz[j], df, dfz);
+    }
+  R de = step::cell_sum(dev.x + dev.y);
+  dfx = step::cell_sum(dfx);
+  dfy = step::cell_sum(dfy);
+  dfz = step::cell_sum(dfz);
+  const unsigned nonfinite = step::cell_or(isfinite(de) ? 0u : (unsigned)ST_NONFINITE);
+  if (sub == 0) {
+    sh.dE[lc] = de;
+    sh.dF[0][lc] = dfx;
+    sh.dF[1][lc] = dfy;
+    sh.dF[2][lc] = dfz;
+    sh.bad[lc] = bad | nonfinite;
+  }
+  __syncthreads();
+
+  // ---------------- phase D: gas exchange (Eqs. gas1, gas2), one lane per cell
+  if (threadIdx.x < CPB) {
+    const int lp = threadIdx.x;
+    const int64_t cl = (int64_t)blockIdx.x * CPB + lp;
+    if (cl < a.n) {
+      const double dE = a.k_fe * (double)sh.dE[lp];
+      const double dx = a.k_fm * (double)sh.dF[0][lp], dy = a.k_fm * (double)sh.dF[1][lp],
+                   dz = a.k_fm * (double)sh.dF[2][lp];
+      if (a.kind[cl] == RT_CELL_INTERIOR) {
+        GasDyn d = a.gd[cl];
+        d.e += dE;
+        d.mx += dx;
+        d.my += dy;
+        d.mz += dz;
+        a.gd[cl] = d;
+        const double ir = a.gs[cl].inv_rho;
+        const double kin = 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * ir;
+        step::store4(a.cellv + 4 * cl, R(d.mx * ir), R(d.my * ir), R(d.mz * ir), R(d.e - kin));
+      } else {
+        double *x = a.ext + 4 * cl;
+        x[0] += dE;
+        x[1] += dx;
+        x[2] += dy;
+        x[3] += dz;
+      }
+      const unsigned b = sh.bad[lp];
+      if (b) {
+        atomicOr(a.status, b);
+        atomicMin(a.bad_cell, (unsigned long long)cl);
+      }
+    }
+  }
+}
+
+template <typename R, typename M> void launch_tile(const GroupArgs<R> &a, cudaStream_t st) {
+  const unsigned g = (unsigned)((a.n + CPB - 1) / CPB);
+  group_source_tile<R, M><<<g, step::NT, 0, st>>>(a);
+}
+
+template <typename R, bool FULL> void tile_pairs(const GroupArgs<R> &a, cudaStream_t st) {
+  switch ((a.H + step::KT - 1) / step::KT) {
+    case 1: launch_tile<R, step::PairMap<R, 1, FULL>>(a, st); break;
+    case 2: launch_tile<R, step::PairMap<R, 2, FULL>>(a, st); break;
+    case 3: launch_tile<R, step::PairMap<R, 3, FULL>>(a, st); break;
+    case 4: launch_tile<R, step::PairMap<R, 4, FULL>>(a, st); break;
+    case 5: launch_tile<R, step::PairMap<R, 5, FULL>>(a, st); break;
+    case 6: launch_tile<R, step::PairMap<R, 6, FULL>>(a, st); break;
+    case 7: launch_tile<R, step::PairMap<R, 7, FULL>>(a, st); break;
+    default: launch_tile<R, step::PairMap<R, 8, FULL>>(a, st); break;
+  }
+}
+
+// the map of the state's row layout (quads for float rows in the quad layout)
+template <typename R> void tile_dispatch(const GroupArgs<R> &a, cudaStream_t st) {
+  if constexpr (sizeof(R) == 4) {
+    if (a.quad_end > 0) {
+      switch (a.A / 16) {
+        case 2: launch_tile<float, step::QuadMap<1, false>>(a, st); return;
+        case 3: launch_tile<float, step::QuadMap<1, true>>(a, st); return;
+        case 4: launch_tile<float, step::QuadMap<2, false>>(a, st); return;
+        case 5: launch_tile<float, step::QuadMap<2, true>>(a, st); return;
+        case 6: launch_tile<float, step::QuadMap<3, false>>(a, st); return;
+        case 7: launch_tile<float, step::QuadMap<3, true>>(a, st); return;
+        default: launch_tile<float, step::QuadMap<4, false>>(a, st); return;
+      }
+    }
+  }
+  if (a.H % step::KT == 0)
+    tile_pairs<R, true>(a, st);
+  else
+    tile_pairs<R, false>(a, st);
+}
+
 template <typename R> cudaError_t launch(rt_state *s, double dt, void *Is) {
   GroupArgs<R> a{};
   a.n = s->n_cells;
@@ -365,6 +706,18 @@ template <typename R> cudaError_t launch(rt_state *s, double dt, void *Is) {
   a.newton_max_iter = s->params.newton_max_iter;
   a.status = s->d_status;
   a.bad_cell = s->d_bad;
+  a.kapgf = s->d_kapgf;
+  a.k_dcr_f = (float)a.k_dcr;
+  a.a_rad_4pi_f = (float)(s->params.a_rad / (4.0 * kPi));
+  for (int j = 0; j < a.G && j < kMaxGroups; ++j) {
+    a.Wk_alpha_f[j] = (float)(a.W[j] * a.k_alpha);
+    a.Wk_g_f[j] = (float)(a.W[j] * a.k_g);
+  }
+  if (a.G <= kTileGroups) {
+    tile_dispatch<R>(a, s->stream);
+    s->launches++;
+    return cudaGetLastError();
+  }
   const unsigned g = (unsigned)((a.n + kCells - 1) / kCells);
   switch ((a.A + 31) / 32) {
     case 1: group_source_kernel<R, 1><<<g, kThreads, 0, s->stream>>>(a); break;

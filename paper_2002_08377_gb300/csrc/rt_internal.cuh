@@ -177,6 +177,7 @@ struct rt_state {
   std::vector<double> group_w;
   std::vector<int32_t> col_of_angle;
   double *d_kapg = nullptr;
+  float *d_kapgf = nullptr;  // [N][n_groups][4] float copies (rho kappa_P, J, s, 0)
   void *d_inv_vol = nullptr;
   int64_t *d_cell_of = nullptr;  // internal -> caller
   double *d_volume = nullptr;    // internal order

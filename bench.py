@@ -85,16 +85,19 @@ def algorithmic_bytes(n_cells, n_faces, n_angles, real_bytes):
 def algorithmic_bytes_vl(n_cells, n_faces, n_angles, real_bytes):
     """Bytes one van Leer step must move: stage 1 is a first-order step over
     dt/2 (algorithmic_bytes); the gradient pass reads the stage-1 row of
-    every cell and its reconstruction geometry (8 reals and a neighbour index
-    per directed face, 8 reals per cell) and writes three gradient rows; the
-    reconstructed transport reads I^n, the stage-1 row and its gradient rows,
-    every undirected face's slot data and the geometry again, and writes I*;
-    the source-only stage reads I* and the gas and writes I^{n+1} and the gas."""
+    every cell, its face records (8 reals per directed face, the neighbour
+    index inside) and the 8 reals of the inverse normal matrix, and writes
+    three gradient rows; the reconstructed transport reads I^n, the stage-1
+    row and its gradient rows, the face records again and the face slots
+    (16 bytes per directed face for float states, the n_p . s table for
+    double), and writes I*; the source-only stage reads I* and the gas and
+    writes I^{n+1} and the gas."""
     s, N, F, A = real_bytes, n_cells, n_faces, n_angles
     stage1 = algorithmic_bytes(N, F, A, s)
-    geometry = 2 * F * (8 * s + 4) + 8 * s * N
-    gradient = N * A * s * (1 + 3) + geometry
-    transport = N * A * s * (1 + 1 + 3 + 1) + geometry + F * (8 + 4 * s)
+    records = 2 * F * 8 * s
+    slots = 2 * F * (16 if s == 4 else 8 * (A // 2))
+    gradient = N * A * s * (1 + 3) + records + 8 * s * N
+    transport = N * A * s * (1 + 1 + 3 + 1) + records + slots + N * s
     source = N * (2 * A * s + 104)
     return stage1 + gradient + transport + source
 

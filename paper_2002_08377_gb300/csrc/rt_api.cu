@@ -199,13 +199,19 @@ template <typename R> int build_device_mesh(rt_state *s, const rt_mesh_desc *m,
 
 // Linear-reconstruction geometry for the van Leer integrator, in the internal
 // cell and slot order.  Per directed slot k of cell c (8 reals):
-//   (x_f - x_c, w_f, x_f - x_nbr', 0), w_f = A_f / |r_f|^2, r_f = x_nbr' - x_c,
-// with nbr' the neighbour's image across f; per cell (8 reals) the inverse of
+//   (x_f - x_c, w_f, x_f - x_nbr', nbr), w_f = A_f / |r_f|^2, r_f = x_nbr' - x_c,
+// with nbr' the neighbour's image across f and nbr its internal index, kept
+// as the bits of an int32 (float) or int64 (double) in the last real, so that
+// one record carries everything a face of the reconstruction reads; per cell
+// (8 reals) the inverse of
 // M = sum_f w_f r_f r_f^T (symmetric: xx, xy, xz, yy, yz, zz, 0, 0), formed in
 // double by cofactors.
 template <typename R> int build_recon(rt_state *s, const rt_mesh_desc *m) {
   const int64_t N = m->n_cells;
   std::vector<R> rs(8 * (size_t)s->nnz), lsq(8 * (size_t)N, R(0));
+  std::vector<int32_t> nbr((size_t)s->nnz);
+  RT_CUDA(s, cudaMemcpy(nbr.data(), s->d_nbr, nbr.size() * sizeof(int32_t),
+                        cudaMemcpyDeviceToHost));
   int64_t o = 0;
   for (int64_t ic = 0; ic < N; ++ic) {
     const int64_t c = s->cell_of[ic];
@@ -227,7 +233,13 @@ template <typename R> int build_recon(rt_state *s, const rt_mesh_desc *m) {
       q[4] = (R)oth[0];
       q[5] = (R)oth[1];
       q[6] = (R)oth[2];
-      q[7] = R(0);
+      if constexpr (sizeof(R) == 4) {
+        const int32_t nb = nbr[o];
+        std::memcpy(&q[7], &nb, sizeof nb);
+      } else {
+        const int64_t nb = nbr[o];
+        std::memcpy(&q[7], &nb, sizeof nb);
+      }
     }
     const double C00 = M[1][1] * M[2][2] - M[1][2] * M[2][1];
     const double C01 = M[0][2] * M[2][1] - M[0][1] * M[2][2];
@@ -504,7 +516,7 @@ int rt_create(const rt_mesh_desc *m_in, const rt_params *p, void *stream, rt_sta
   CK(dalloc(s, &s->d_ext, 4 * (size_t)N));
   if (s->integrator == RT_VAN_LEER) {  // stage-1 intensities and their gradients
     CK(dalloc_bytes(s, &s->d_Ihalf, (size_t)N * RS * s->rsize));
-    CK(dalloc_bytes(s, &s->d_grad, 4 * (size_t)N * RS * s->rsize));
+    CK(dalloc_bytes(s, &s->d_grad, 3 * (size_t)N * RS * s->rsize));
   }
   CK(dalloc_bytes(s, &s->d_cellv, 4 * (size_t)N * s->rsize));
   CK(cudaMemsetAsync(s->d_cellv, 0, 4 * (size_t)N * s->rsize, s->stream));

@@ -159,7 +159,7 @@ struct rt_state {
   double *d_uface = nullptr;  // double: [nnz][A/2] flux coefficients, built once (build_uface)
   // van Leer integrator: reconstruction geometry ([nnz][8] and [N][8] reals
   // of the state precision, see build_recon), stage-1 intensities [N][RS]
-  // and, per row position, (stage-1 intensity, limited gradient) [N][RS][4]
+  // and their limited gradients [3][N][RS] (x, y, z rows in the row layout)
   int integrator = RT_FIRST_ORDER;
   void *d_recon = nullptr, *d_lsq = nullptr, *d_Ihalf = nullptr, *d_grad = nullptr;
   double *d_wface = nullptr;  // double states: per-slot A w . n

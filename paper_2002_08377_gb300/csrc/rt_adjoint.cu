@@ -15,8 +15,8 @@
 //
 // Three launches (besides the permutes into and out of the internal order):
 //   launch_transport (forward)  I* = M I^n, on the step kernel's tile machinery;
-//   source_reverse_kernel       blocks of 32 cells, 4 per warp, lanes over the
-//                               row positions of a cell:
+//   source_reverse_tile         blocks of 32 cells x 8 threads (the step
+//                               kernel's tile mapping):
 //     0  one lane per cell in double: the per-cell constants of phases 1 and
 //        3 (v/c, x/Gamma, the boundary and emitter factors);
 //     1  after a block barrier: the angular sums of the forward source step
@@ -40,6 +40,7 @@
 
 #include "rt_internal.cuh"
 #include "rt_step_common.cuh"
+#include "rt_step_tile.cuh"
 
 namespace rt {
 namespace {
@@ -47,16 +48,7 @@ namespace {
 using step::positive;
 using step::rcp;
 
-constexpr int kWarps = 8;                        // warps per block
-constexpr int kCellsPerWarp = 4;                 // cells a warp takes in turn
-constexpr int kCells = kWarps * kCellsPerWarp;   // cells per block
-constexpr int kThreads = 32 * kWarps;
-
-template <typename T> __device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
+constexpr int kThreads = 256;  // threads per block of the per-cell gather / scatter
 
 template <typename R> struct AdjArgs {
   int64_t n;
@@ -77,32 +69,6 @@ template <typename R> struct AdjArgs {
   int newton_max_iter;
 };
 
-// The angles of one lane's row positions q = lane + 32 t.
-template <typename R, int NT> struct Lane {
-  R nx[NT], ny[NT], nz[NT], wt[NT];
-  int q[NT];  // row position (>= A: none)
-};
-
-template <typename R, int NT>
-__device__ __forceinline__ Lane<R, NT> lane_angles(const AdjArgs<R> &a, int lane) {
-  Lane<R, NT> L;
-#pragma unroll
-  for (int t = 0; t < NT; ++t) {
-    const int q = lane + 32 * t;
-    L.q[t] = q;
-    L.nx[t] = L.ny[t] = L.nz[t] = L.wt[t] = R(0);
-    if (q < a.A) {
-      const int an = angle_of_position(q, a.H, a.quad_end);
-      const int p = an < a.H ? an : an - a.H;
-      L.nx[t] = a.dir[4 * an];
-      L.ny[t] = a.dir[4 * an + 1];
-      L.nz[t] = a.dir[4 * an + 2];
-      L.wt[t] = a.wt2[2 * p + (an >= a.H ? 1 : 0)];
-    }
-  }
-  return L;
-}
-
 // 1 / v: float by the approximate reciprocal (v = Gamma or 1 + x Gamma,
 // normal or +inf); double refined from it, or divided outside float range.
 __device__ __forceinline__ float rcp_pos(float v) { return rcp(v); }
@@ -113,10 +79,9 @@ __device__ __forceinline__ double rcp_pos(double v) { return v < 1e37 ? rcp(v) :
 template <typename R> struct Ang {
   R G, iG, iG4, wh, r, It;
 };
-template <typename R>
-__device__ __forceinline__ Ang<R> comoving(R bx, R by, R bz, R nx, R ny, R nz, R wt, R X, R is) {
+template <typename R> __device__ __forceinline__ Ang<R> comoving_g(R G, R wt, R X, R is) {
   Ang<R> g;
-  g.G = R(1) - fma(bx, nx, fma(by, ny, bz * nz));
+  g.G = G;
   g.iG = rcp_pos(g.G);
   const R iG2 = g.iG * g.iG, G2 = g.G * g.G;
   g.iG4 = iG2 * iG2;
@@ -125,7 +90,6 @@ __device__ __forceinline__ Ang<R> comoving(R bx, R by, R bz, R nx, R ny, R nz, R
   g.It = G2 * G2 * is;
   return g;
 }
-
 // Per-cell inputs of phases 1 and 3 (phase 0), sums of phase 1 (unnormalised
 // by N_w = sum w^), results of phase 2 and sums of phase 3.
 template <typename R> struct CellIn {
@@ -306,63 +270,142 @@ __device__ void cell_finish(const AdjArgs<R> &a, int64_t c, int kind, const Cell
   }
 }
 
-template <typename R, int NT>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 2)
-    source_reverse_kernel(const AdjArgs<R> a) {
-  __shared__ CellIn<R> cin[kCells];
-  __shared__ CellSums<R> sums[kCells];
-  __shared__ CellRev<R> rev[kCells];
-  __shared__ CellOut<R> cout_[kCells];
+// ------------------------------------------------------------ the kernel
+// Phases 1 and 3 (per angle) run on the step kernel's tile mapping: 32 cells
+// x 8 threads, thread `sub` holding the entries of its pair / quad map (angle
+// p and its antipode, whose Gamma is 1 + v.n_p where p's is 1 - v.n_p).  A
+// cell's sums reduce over its 8 threads (3 shuffles), the 4 cells of a warp
+// at once.  Phases 0, 2 and 4 run one lane per cell on warp 0.
+
+// One angle's terms of phase 1 (interior cells).
+template <typename R>
+__device__ __forceinline__ void sums_angle(R G, R wt, R X, R is, R l1, R ex, R &Nw, R &SI, R &SG,
+                                           R &S1, R &lq) {
+  const Ang<R> g = comoving_g(G, wt, X, is);
+  const R whr = g.wh * g.r;
+  Nw += g.wh;
+  SI = fma(whr, g.It, SI);
+  SG = fma(whr, g.G, SG);
+  S1 += whr;
+  lq = fma(g.G * ((l1 - ex) * g.iG4), g.r, lq);
+}
+
+// One angle's terms of phase 3 (interior cells): returns dt/V lambda_I*,
+// accumulates sum Gamma lambda_x and gives lambda_Gamma.
+template <typename R>
+__device__ __forceinline__ R reverse_angle(R G, R wt, R X, R isv, R l1, R ex, R dtv,
+                                           const CellRev<R> &r, R &gJx, R &lGo) {
+  const Ang<R> g = comoving_g(G, wt, X, isv);
+  const R w = g.wh * r.iNw;
+  const R Itn = fma(r.q, g.G, g.It) * g.r;  // I~'
+  const R In = Itn * g.iG4;                 // I'
+  const R lIn = l1 - ex;
+  const R lItn = lIn * g.iG4;
+  R lG = fma(R(-4) * In * g.iG, lIn, r.q * lItn * g.r);
+  R lIt = lItn * g.r;
+  R lx = -Itn * lItn * g.r;
+  const R lw = fma(g.It, r.lSI, g.G * r.lSG) * g.r;  // lambda of the normalised weight
+  lIt = fma(w * r.lSI, g.r, lIt);
+  lG = fma(w * r.lSG, g.r, lG);
+  lx = fma(-w * lw, g.r, lx);
+  gJx = fma(g.G, lx, gJx);
+  lG = fma(X, lx, lG);
+  lG = fma(R(-2) * g.wh * g.iG, (lw - r.swl) * r.iNw, lG);
+  const R G2 = g.G * g.G;
+  lG = fma(R(4) * G2 * g.G * isv, lIt, lG);
+  lGo = lG;
+  return dtv * fma(G2 * G2, lIt, ex);
+}
+
+// One angle of an emitter cell: I' = (I* + Y I_src / Gamma^3) / (1 + Y Gamma);
+// returns dt/V lambda_I* and gives dI'/dGamma lambda_I'.
+template <typename R>
+__device__ __forceinline__ R emitter_angle(R G, R Y, R isrc, R isv, R l1, R dtv, R &lGo) {
+  const R iG = rcp_pos(G), iG2 = iG * iG, iG4 = iG2 * iG2, G2 = G * G;
+  const R y = Y * G, iy = rcp_pos(R(1) + y);
+  const R In = fma(G2 * G2, isv, y * isrc) * iy * iG4;
+  const R dIdG = -fma(R(3) * Y * isrc, iG4, Y * In) * iy;  // dI'/dGamma
+  lGo = dIdG * l1;
+  return dtv * (l1 * iy);
+}
+
+// A thread's entries of one cell: directions and weights of its pairs, the
+// rows of I* and lambda_I^{n+1} (padding entries: zero weights and rows).
+template <typename R, typename M> struct Entries {
+  R nx[M::PPT], ny[M::PPT], nz[M::PPT], wa[M::PPT], wb[M::PPT];
+  R Ia[M::PPT], Ib[M::PPT], la[M::PPT], lb[M::PPT];
+  __device__ __forceinline__ void load(const AdjArgs<R> &a, int64_t c, int sub, int np) {
+#pragma unroll
+    for (int j = 0; j < M::PPT; ++j) {
+      const bool ok = M::FULL || j < np;
+      const int p = ok ? M::pair(j, sub) : 0;
+      step::load_dir(a.dir, p, nx[j], ny[j], nz[j]);
+      wa[j] = ok ? a.wt2[2 * p] : R(0);
+      wb[j] = ok ? a.wt2[2 * p + 1] : R(0);
+    }
+    M::load(a.Is + (size_t)c * a.A, sub, Ia, Ib, np);
+    M::load(a.lI1 + (size_t)c * a.A, sub, la, lb, np);
+  }
+  // 4 pi w (c lambda_e + n . lambda_m) / cbar of entry j's angle (anti: the
+  // antipode, direction -n_p)
+  __device__ __forceinline__ R ex(int j, bool anti, const CellIn<R> &ci, R k_ex) const {
+    const R x = anti ? -nx[j] : nx[j], y = anti ? -ny[j] : ny[j], z = anti ? -nz[j] : nz[j];
+    return k_ex * (anti ? wb[j] : wa[j]) * fma(x, ci.lmx, fma(y, ci.lmy, fma(z, ci.lmz, ci.cle)));
+  }
+};
+
+template <typename R> __device__ __forceinline__ R group_sum(R v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
+
+template <typename R, typename M>
+__global__ void __launch_bounds__(step::NT, sizeof(R) == 4 ? 3 : 2)
+    source_reverse_tile(const AdjArgs<R> a) {
+  using step::KT;
+  constexpr int PPT = M::PPT;
+  __shared__ CellIn<R> cin[CPB];
+  __shared__ CellSums<R> sums[CPB];
+  __shared__ CellRev<R> rev[CPB];
+  __shared__ CellOut<R> cout_[CPB];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int64_t c0 = (int64_t)blockIdx.x * kCells;
+  const int lc = threadIdx.x / KT, sub = threadIdx.x % KT;
+  const int64_t c0 = (int64_t)blockIdx.x * CPB;
   const int64_t cl = c0 + lane;  // the lane's cell in phases 0, 2, 4
   const bool lane_cell = warp == 0 && cl < a.n;
-
   // ---------------- phase 0: per-cell constants, one lane per cell
   if (lane_cell) cell_inputs(a, cl, cin[lane]);
+
+  const bool live = c0 + lc < a.n;
+  const int64_t c = live ? c0 + lc : a.n - 1;  // dead threads shadow the last cell
+  const int np = M::count(a.H, sub);
   __syncthreads();
-
-  const Lane<R, NT> L = lane_angles<R, NT>(a, lane);
+  const CellIn<R> ci = cin[lc];
   const R k_ex = a.k_ex_r;  // lambda_I* gets 4 pi w (c lambda_e + n . lambda_m) / cbar
-  R is[kCellsPerWarp][NT];
-
   // ---------------- phase 1: the angular sums and lambda_q
-#pragma unroll
-  for (int i = 0; i < kCellsPerWarp; ++i) {
-    const int64_t c = c0 + warp * kCellsPerWarp + i;
-#pragma unroll
-    for (int t = 0; t < NT; ++t)
-      is[i][t] = c < a.n && L.q[t] < a.A ? a.Is[(size_t)c * a.A + L.q[t]] : R(0);
-  }
-#pragma unroll
-  for (int i = 0; i < kCellsPerWarp; ++i) {
-    const int lc = warp * kCellsPerWarp + i;
-    const int64_t c = c0 + lc;
-    if (c >= a.n) continue;
-    const CellIn<R> &ci = cin[lc];
-    if (ci.kind != RT_CELL_INTERIOR) continue;
+  {
     R Nw = 0, SI = 0, SG = 0, S1 = 0, lq = 0;
+    if (ci.kind == RT_CELL_INTERIOR) {
+      Entries<R, M> E;
+      E.load(a, c, sub, np);
 #pragma unroll
-    for (int t = 0; t < NT; ++t)
-      if (L.q[t] < a.A) {
-        const Ang<R> g =
-            comoving(ci.bx, ci.by, ci.bz, L.nx[t], L.ny[t], L.nz[t], L.wt[t], ci.X, is[i][t]);
-        const R whr = g.wh * g.r;
-        Nw += g.wh;
-        SI = fma(whr, g.It, SI);
-        SG = fma(whr, g.G, SG);
-        S1 += whr;
-        const R ex = k_ex * L.wt[t] *
-                     fma(L.nx[t], ci.lmx, fma(L.ny[t], ci.lmy, fma(L.nz[t], ci.lmz, ci.cle)));
-        const R l1 = a.lI1[(size_t)c * a.A + L.q[t]];
-        lq = fma(g.G * ((l1 - ex) * g.iG4), g.r, lq);
-      }
-    Nw = warp_sum(Nw);
-    SI = warp_sum(SI);
-    SG = warp_sum(SG);
-    S1 = warp_sum(S1);
-    lq = warp_sum(lq);
-    if (lane == 0) sums[lc] = CellSums<R>{Nw, SI, SG, S1, lq};
+      for (int j = 0; j < PPT; ++j)
+        if (M::FULL || j < np) {
+          const R t = fma(ci.bx, E.nx[j], fma(ci.by, E.ny[j], ci.bz * E.nz[j]));
+          sums_angle(R(1) - t, E.wa[j], ci.X, E.Ia[j], E.la[j], E.ex(j, false, ci, k_ex), Nw, SI,
+                     SG, S1, lq);
+          sums_angle(R(1) + t, E.wb[j], ci.X, E.Ib[j], E.lb[j], E.ex(j, true, ci, k_ex), Nw, SI,
+                     SG, S1, lq);
+        }
+    }
+    Nw = group_sum(Nw);
+    SI = group_sum(SI);
+    SG = group_sum(SG);
+    S1 = group_sum(S1);
+    lq = group_sum(lq);
+    if (sub == 0) sums[lc] = CellSums<R>{Nw, SI, SG, S1, lq};
   }
   __syncthreads();
 
@@ -370,85 +413,106 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 2)
   if (lane_cell && cin[lane].kind == RT_CELL_INTERIOR) cell_reverse(a, cl, sums[lane], rev[lane]);
   __syncthreads();
 
-  // ---------------- phase 3: per-angle reverse, lambda_I*
-#pragma unroll
-  for (int i = 0; i < kCellsPerWarp; ++i) {
-    const int lc = warp * kCellsPerWarp + i;
-    const int64_t c = c0 + lc;
-    if (c >= a.n) continue;
-    const CellIn<R> &ci = cin[lc];
-    const R *l1row = a.lI1 + (size_t)c * a.A;
-    R *out = a.Ls + (size_t)c * a.A;
+  // ---------------- phase 3: per-angle reverse, lambda_I* (the entries read again: the
+  // rows are in L1, and nothing per angle stays live across phase 2)
+  {
     const R dtv = a.dt_r * a.inv_vol[c];  // the scale the adjoint transport divides out
+    Entries<R, M> E;
+    E.load(a, c, sub, np);
+    R oa[PPT], ob[PPT];
+    R gJx = 0, lvx = 0, lvy = 0, lvz = 0;
     if (ci.kind == RT_CELL_BOUNDARY) {
       const R f = dtv * ci.f;
 #pragma unroll
-      for (int t = 0; t < NT; ++t)
-        if (L.q[t] < a.A) out[L.q[t]] = f * l1row[L.q[t]];
-      continue;
-    }
-    R gJx = 0, lvx = 0, lvy = 0, lvz = 0;
-    if (ci.kind == RT_CELL_EMITTER) {
-      // I' = (I* + Y I_src / Gamma^3) / (1 + Y Gamma), Y = dt cbar (rho kappa)_src
+      for (int j = 0; j < PPT; ++j) {
+        oa[j] = f * E.la[j];
+        ob[j] = f * E.lb[j];
+      }
+    } else if (ci.kind == RT_CELL_EMITTER) {
       const R Y = ci.X, isrc = ci.f;
 #pragma unroll
-      for (int t = 0; t < NT; ++t)
-        if (L.q[t] < a.A) {
-          const R G = R(1) - fma(ci.bx, L.nx[t], fma(ci.by, L.ny[t], ci.bz * L.nz[t]));
-          const R iG = rcp_pos(G), iG2 = iG * iG, iG4 = iG2 * iG2, G2 = G * G;
-          const R y = Y * G, iy = rcp_pos(R(1) + y);
-          const R In = fma(G2 * G2, is[i][t], y * isrc) * iy * iG4;
-          const R l1 = l1row[L.q[t]];
-          out[L.q[t]] = dtv * (l1 * iy);
-          const R dIdG = -fma(R(3) * Y * isrc, iG4, Y * In) * iy;  // dI'/dGamma
-          lvx = fma(L.nx[t] * dIdG, l1, lvx);
-          lvy = fma(L.ny[t] * dIdG, l1, lvy);
-          lvz = fma(L.nz[t] * dIdG, l1, lvz);
+      for (int j = 0; j < PPT; ++j) {
+        const R t = fma(ci.bx, E.nx[j], fma(ci.by, E.ny[j], ci.bz * E.nz[j]));
+        R ga = 0, gb = 0;
+        oa[j] = emitter_angle(R(1) - t, Y, isrc, E.Ia[j], E.la[j], dtv, ga);
+        ob[j] = emitter_angle(R(1) + t, Y, isrc, E.Ib[j], E.lb[j], dtv, gb);
+        if (M::FULL || j < np) {
+          const R d = ga - gb;  // n_p lambda_Gamma of p plus -n_p that of the antipode
+          lvx = fma(E.nx[j], d, lvx);
+          lvy = fma(E.ny[j], d, lvy);
+          lvz = fma(E.nz[j], d, lvz);
         }
+      }
     } else {
-      const CellRev<R> &r = rev[lc];
-      const R q = r.q, lSI = r.lSI, lSG = r.lSG, swl = r.swl, iNw = r.iNw;
+      const CellRev<R> r = rev[lc];
 #pragma unroll
-      for (int t = 0; t < NT; ++t)
-        if (L.q[t] < a.A) {
-          const R isv = is[i][t];
-          const Ang<R> g =
-              comoving(ci.bx, ci.by, ci.bz, L.nx[t], L.ny[t], L.nz[t], L.wt[t], ci.X, isv);
-          const R w = g.wh * iNw;
-          const R Itn = fma(q, g.G, g.It) * g.r;  // I~'
-          const R In = Itn * g.iG4;                // I'
-          const R ex = k_ex * L.wt[t] *
-                       fma(L.nx[t], ci.lmx, fma(L.ny[t], ci.lmy, fma(L.nz[t], ci.lmz, ci.cle)));
-          const R lIn = l1row[L.q[t]] - ex;
-          const R lItn = lIn * g.iG4;
-          R lG = fma(R(-4) * In * g.iG, lIn, q * lItn * g.r);
-          R lIt = lItn * g.r;
-          R lx = -Itn * lItn * g.r;
-          const R lw = fma(g.It, lSI, g.G * lSG) * g.r;  // lambda of the normalised weight
-          lIt = fma(w * lSI, g.r, lIt);
-          lG = fma(w * lSG, g.r, lG);
-          lx = fma(-w * lw, g.r, lx);
-          gJx = fma(g.G, lx, gJx);
-          lG = fma(ci.X, lx, lG);
-          lG = fma(R(-2) * g.wh * g.iG, (lw - swl) * iNw, lG);
-          const R G2 = g.G * g.G;
-          out[L.q[t]] = dtv * fma(G2 * G2, lIt, ex);
-          lG = fma(R(4) * G2 * g.G * isv, lIt, lG);
-          lvx = fma(L.nx[t], lG, lvx);
-          lvy = fma(L.ny[t], lG, lvy);
-          lvz = fma(L.nz[t], lG, lvz);
+      for (int j = 0; j < PPT; ++j) {
+        const R t = fma(ci.bx, E.nx[j], fma(ci.by, E.ny[j], ci.bz * E.nz[j]));
+        R ga = 0, gb = 0, gxa = 0, gxb = 0;
+        oa[j] = reverse_angle(R(1) - t, E.wa[j], ci.X, E.Ia[j], E.la[j], E.ex(j, false, ci, k_ex),
+                              dtv, r, gxa, ga);
+        ob[j] = reverse_angle(R(1) + t, E.wb[j], ci.X, E.Ib[j], E.lb[j], E.ex(j, true, ci, k_ex),
+                              dtv, r, gxb, gb);
+        if (M::FULL || j < np) {
+          gJx += gxa + gxb;
+          const R d = ga - gb;
+          lvx = fma(E.nx[j], d, lvx);
+          lvy = fma(E.ny[j], d, lvy);
+          lvz = fma(E.nz[j], d, lvz);
         }
+      }
     }
-    gJx = warp_sum(gJx);
-    lvx = warp_sum(lvx);
-    lvy = warp_sum(lvy);
-    lvz = warp_sum(lvz);
-    if (lane == 0) cout_[lc] = CellOut<R>{gJx, lvx, lvy, lvz};
+    if (live) M::store(a.Ls + (size_t)c * a.A, sub, oa, ob, np);
+    gJx = group_sum(gJx);
+    lvx = group_sum(lvx);
+    lvy = group_sum(lvy);
+    lvz = group_sum(lvz);
+    if (sub == 0) cout_[lc] = CellOut<R>{gJx, lvx, lvy, lvz};
   }
   __syncthreads();
 
   // ---------------- phase 4: lambda_e, lambda_m, gradients, one lane per cell
   if (lane_cell) cell_finish(a, cl, cin[lane].kind, rev[lane], cout_[lane]);
+}
+
+template <typename R, typename M> void launch_reverse_tile(rt_state *s, const AdjArgs<R> &a) {
+  const unsigned g = (unsigned)((s->n_cells + CPB - 1) / CPB);
+  source_reverse_tile<R, M><<<g, step::NT, 0, s->stream>>>(a);
+}
+
+template <typename R, bool FULL> void reverse_pairs(rt_state *s, const AdjArgs<R> &a) {
+  using step::PairMap;
+  switch ((s->n_angles / 2 + step::KT - 1) / step::KT) {
+    case 1: return launch_reverse_tile<R, PairMap<R, 1, FULL>>(s, a);
+    case 2: return launch_reverse_tile<R, PairMap<R, 2, FULL>>(s, a);
+    case 3: return launch_reverse_tile<R, PairMap<R, 3, FULL>>(s, a);
+    case 4: return launch_reverse_tile<R, PairMap<R, 4, FULL>>(s, a);
+    case 5: return launch_reverse_tile<R, PairMap<R, 5, FULL>>(s, a);
+    case 6: return launch_reverse_tile<R, PairMap<R, 6, FULL>>(s, a);
+    case 7: return launch_reverse_tile<R, PairMap<R, 7, FULL>>(s, a);
+    default: return launch_reverse_tile<R, PairMap<R, 8, FULL>>(s, a);
+  }
+}
+
+template <typename R> void launch_reverse(rt_state *s, const AdjArgs<R> &a) {
+  using step::QuadMap;
+  if constexpr (sizeof(R) == 4) {
+    if (s->quad_end > 0) {  // rows in the quad layout
+      switch (s->n_angles / 16) {
+        case 2: return launch_reverse_tile<float, QuadMap<1, false>>(s, a);
+        case 3: return launch_reverse_tile<float, QuadMap<1, true>>(s, a);
+        case 4: return launch_reverse_tile<float, QuadMap<2, false>>(s, a);
+        case 5: return launch_reverse_tile<float, QuadMap<2, true>>(s, a);
+        case 6: return launch_reverse_tile<float, QuadMap<3, false>>(s, a);
+        case 7: return launch_reverse_tile<float, QuadMap<3, true>>(s, a);
+        default: return launch_reverse_tile<float, QuadMap<4, false>>(s, a);
+      }
+    }
+  }
+  if ((s->n_angles / 2) % step::KT == 0)
+    reverse_pairs<R, true>(s, a);
+  else
+    reverse_pairs<R, false>(s, a);
 }
 
 // caller order -> internal order for per-cell vectors of width w (double)
@@ -507,13 +571,7 @@ template <typename R> cudaError_t run_adjoint(rt_state *s, const R *I_int, const
   a.dt_r = R(dt);
   a.k_ex_r = R(4.0 * kPi / s->params.cbar);
   a.newton_max_iter = s->params.newton_max_iter;
-  const unsigned g = (unsigned)((N + kCells - 1) / kCells);
-  switch ((A + 31) / 32) {
-    case 1: source_reverse_kernel<R, 1><<<g, kThreads, 0, s->stream>>>(a); break;
-    case 2: source_reverse_kernel<R, 2><<<g, kThreads, 0, s->stream>>>(a); break;
-    case 3: source_reverse_kernel<R, 3><<<g, kThreads, 0, s->stream>>>(a); break;
-    default: source_reverse_kernel<R, 4><<<g, kThreads, 0, s->stream>>>(a); break;
-  }
+  launch_reverse<R>(s, a);
   s->launches++;
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;

@@ -261,10 +261,24 @@ def run_reference(args, world, rank):
 
 
 # ---------------------------------------------------------------- GPU arm
-def time_steps(sol, dt, steps, warmup, world, sampler=None):
-    import torch
+GRAPH_STEPS = 16  # RT_GRAPH_STEPS of include/rt.h
+
+
+def warm_up(sol, dt, warmup):
+    """warmup single steps, then two multi-step runs an odd step apart: these
+    capture the step graphs of both buffer parities (rt_run / rt_launch
+    replay them for every whole block of GRAPH_STEPS steps), so that no
+    capture falls inside a timed region."""
     for _ in range(warmup):
         sol.step(dt)
+    sol.run(GRAPH_STEPS, dt)
+    sol.step(dt)
+    sol.run(GRAPH_STEPS, dt)
+
+
+def time_steps(sol, dt, steps, warmup, world, sampler=None):
+    import torch
+    warm_up(sol, dt, warmup)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     stream = sol.stream
@@ -344,8 +358,7 @@ def groups_rate(n, steps, warmup, hbm_peak, peak_kind):
     A = prob.n_groups * prob.n_angles
     dt = prob.cfl_dt()
     sol = RTSolver.from_problem(prob, "fp32")
-    for _ in range(warmup):
-        sol.step(dt)
+    warm_up(sol, dt, warmup)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -371,6 +384,31 @@ def groups_rate(n, steps, warmup, hbm_peak, peak_kind):
                          "frac": achieved / hbm_peak, "traffic": None,
                          "algorithmic_bytes_per_step": B,
                          "peak_source": f"{peak_kind} HBM copy bandwidth"}}
+
+
+def thermal_rate(world):
+    """The thermal-equilibrium box (16^3 cells, S6, 100 steps; 4096 x 48
+    intensities, 0.8 MB in FP32): a launch-bound case, timed as 100 steps
+    through rt_launch with the step graphs replayed (6 replays of 16 steps,
+    then 4 single launches) and with plain launches of the same kernels."""
+    import torch
+    from paper_2002_08377_gb300.inputs import thermal
+    from paper_2002_08377_gb300.solver import RTSolver
+    prob = thermal()
+    N, A, steps = prob.n_cells, prob.n_angles, prob.n_steps
+    dt = prob.cfl_dt()
+    out = {"workload": f"thermal box: {N} cells x {A} angles, {steps} steps", "steps": steps}
+    for prec in ("fp32", "fp64"):
+        for plain in (0, 1):
+            sol = RTSolver.from_problem(prob, prec, plain_launches=plain)
+            ms, launches = time_steps(sol, dt, steps, 3, world)
+            sol.close()
+            key = f"{prec}_{'plain' if plain else 'graphs'}"
+            out[key] = {"ms_per_step": ms / steps, "value": N * A * steps / (ms * 1e-3),
+                        "launches": launches}
+    out["value"] = out["fp32_graphs"]["value"]
+    out["unit"] = UNIT
+    return out
 
 
 def adjoint_rate(prob, prec, dt, steps, warmup):
@@ -422,6 +460,7 @@ def main():
     ap.add_argument("--no-vl", action="store_true", help="skip the van Leer leg")
     ap.add_argument("--no-adj", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--no-groups", action="store_true", help="skip the frequency-group leg")
+    ap.add_argument("--no-thermal", action="store_true", help="skip the launch-bound thermal leg")
     ap.add_argument("--only", choices=["fp32", "fp64"], default=None,
                     help="time one precision only (profiling runs)")
     ap.add_argument("--n", type=int, default=128,
@@ -509,6 +548,10 @@ def main():
     if args.only is None and not args.no_groups:
         grp = groups_rate(args.n, max(3, args.steps // 5), 3, hbm_peak, peak_kind)
 
+    thm = None
+    if args.only is None and not args.no_thermal:
+        thm = thermal_rate(world)
+
     adj = None
     if args.only is None and not args.no_adj:
         # one reverse step (rt_adjoint_step: forward transport sweep, source
@@ -545,7 +588,7 @@ def main():
                      "steps": results["fp64"]["steps"], "dtype": "f64",
                      "roofline": results["fp64"]["roofline"],
                      "fp32_over_fp64": r32["value"] / results["fp64"]["value"]},
-            "van_leer": vl, "adjoint": adj, "groups": grp}
+            "van_leer": vl, "adjoint": adj, "groups": grp, "thermal": thm}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -161,7 +161,10 @@ typedef enum { RT_FIRST_ORDER = 0, RT_VAN_LEER = 1 } rt_integrator;
  * is taken at T^{n+1} inside the temperature solve (alpha T^(4 + beta_P) +
  * rho c_v T = g, beta_P >= -3), kappa_J(T) = kappa_J (T/T_ref)^beta_J at the
  * temperature at the start of each step.  0, 0: constant opacities (T_ref is
- * then unused; otherwise T_ref > 0).  rt_adjoint_step refuses beta != 0. */
+ * then unused; otherwise T_ref > 0).  rt_adjoint_step refuses beta != 0.
+ * plain_launches = 0 (the default) lets rt_run / rt_launch replay a CUDA
+ * graph of RT_GRAPH_STEPS steps captured on the state's stream (see rt_run);
+ * 1 launches every kernel from the host.  Both give identical results. */
 typedef struct {
   double cbar, c, a_rad, gamma_gas, r_gas, cfl;
   int32_t precision;       /* rt_precision */
@@ -169,7 +172,7 @@ typedef struct {
   int32_t integrator;      /* rt_integrator */
   int32_t boost;           /* 0 or 1, see above */
   int32_t gcl;             /* 0 or 1, see above */
-  int32_t reserved;        /* 0 */
+  int32_t plain_launches;  /* 0: multi-step calls replay captured graphs; 1: plain launches */
   double beta_P, beta_J, T_ref; /* see above */
 } rt_params;
 
@@ -220,7 +223,15 @@ int rt_dt_limits(rt_state *s, double *dt_cfl, double *dt_max);
 int rt_step(rt_state *s, double dt, double *dt_used);
 
 /* n_steps full steps with the same dt, launched back to back; synchronises
- * once at the end. */
+ * once at the end.  Unless rt_params.plain_launches is set, whole blocks of
+ * RT_GRAPH_STEPS steps are replayed from a CUDA graph captured on the
+ * state's stream (one launch of the graph instead of one per kernel; the
+ * same kernels with the same arguments in the same order).  The graph is
+ * captured (on a stream the state creates for that) at the first such call,
+ * per dt and buffer parity, and captured again after any rt_set_* call.  No
+ * graph is used while the caller is capturing the state's stream itself; the
+ * steps are then launched one by one. */
+#define RT_GRAPH_STEPS 16
 int rt_run(rt_state *s, int32_t n_steps, double dt, double *dt_used);
 
 /* Launches n_steps full steps without waiting for them; per-cell failures

@@ -416,10 +416,11 @@ int rt_create(const rt_mesh_desc *m_in, const rt_params *p, void *stream, rt_sta
       (p->boost != 0 && p->boost != 1) || (p->gcl != 0 && p->gcl != 1) ||
       (p->gcl && p->integrator != RT_FIRST_ORDER) || !std::isfinite(p->beta_P) ||
       !std::isfinite(p->beta_J) || ((p->beta_P != 0 || p->beta_J != 0) && !(p->T_ref > 0)) ||
-      !(p->beta_P >= -3.0) ||
+      !(p->beta_P >= -3.0) || (p->plain_launches != 0 && p->plain_launches != 1) ||
       (p->integrator == RT_VAN_LEER && !m->face_offset))
     return bail(RT_ERR_ARG);
   s->params = *p;
+  s->plain_launches = p->plain_launches != 0;
   if (s->params.newton_max_iter <= 0) s->params.newton_max_iter = 64;
   s->precision = p->precision;
   s->rsize = p->precision == RT_FP32 ? 4 : 8;
@@ -589,6 +590,7 @@ int rt_create(const rt_mesh_desc *m_in, const rt_params *p, void *stream, rt_sta
 int rt_set_gas(rt_state *s, const double *rho, const double *e, const double *m,
                const double *kP, const double *kJ, const double *kS) {
   if (!s) return RT_ERR_ARG;
+  ++s->gen;  // captured step graphs may hold old arguments
   if (!rho || !e || !m || !kP || !kJ || !kS) return fail(s, RT_ERR_ARG, "rt_set_gas: NULL array");
   const int64_t N = s->n_cells;
   const int G = s->n_groups;  // opacity arrays hold G values per cell
@@ -656,6 +658,7 @@ int rt_set_gas(rt_state *s, const double *rho, const double *e, const double *m,
 int rt_set_cells(rt_state *s, const uint8_t *kind, const double *tau, const double *emit,
                  const double *isrc, const int32_t *bc_row, int64_t n_rows, const double *I0) {
   if (!s) return RT_ERR_ARG;
+  ++s->gen;  // captured step graphs may hold old arguments
   const int64_t N = s->n_cells;
   const int A = s->n_angles;
   std::vector<uint8_t> k(N, 0);
@@ -719,6 +722,7 @@ int rt_set_cells(rt_state *s, const uint8_t *kind, const double *tau, const doub
 
 int rt_set_intensity(rt_state *s, const void *I, int on_device) {
   if (!s || !I) return s ? fail(s, RT_ERR_ARG, "rt_set_intensity: NULL") : RT_ERR_ARG;
+  ++s->gen;  // captured step graphs may hold old arguments
   const size_t bytes = (size_t)s->n_cells * s->n_angles * s->rsize;
   const void *src = I;
   void *stage = s->d_I[s->cur ^ 1];
@@ -787,6 +791,57 @@ int rt_dt_limits(rt_state *s, double *dt_cfl, double *dt_max) {
   return RT_OK;
 }
 
+// The graph of RT_GRAPH_STEPS steps from the current buffer parity at dt,
+// captured now if the cached one is missing or stale.  An even number of
+// steps brings the buffers back, so the graph can be replayed any number of
+// times.  Capturing runs the launch code on the host without executing the
+// kernels: the buffer index and the launch count are restored afterwards.
+static cudaError_t step_graph(rt_state *s, double dt, cudaGraphExec_t *out) {
+  static_assert(RT_GRAPH_STEPS % 2 == 0, "the graph must bring the buffers back");
+  const int par = s->cur;
+  if (s->graph[par] && s->graph_dt[par] == dt && s->graph_gen[par] == s->gen) {
+    *out = s->graph[par];
+    return cudaSuccess;
+  }
+  if (s->graph[par]) {
+    cudaGraphExecDestroy(s->graph[par]);
+    s->graph[par] = nullptr;
+  }
+  // captured on a stream of the state's own (the caller's stream may be the
+  // legacy default stream, which cannot be captured); replayed on the
+  // caller's stream
+  if (!s->cap_stream) {
+    const cudaError_t ec = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
+    if (ec != cudaSuccess) return ec;
+  }
+  const int64_t l0 = s->launches;
+  cudaStream_t user = s->stream;
+  s->stream = s->cap_stream;
+  cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    s->stream = user;
+    return e;
+  }
+  for (int i = 0; i < RT_GRAPH_STEPS && e == cudaSuccess; ++i) e = rt::launch_step(s, dt);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(s->stream, &g);
+  s->stream = user;
+  s->cur = par;
+  const int64_t per = s->launches - l0;
+  s->launches = l0;
+  if (e == cudaSuccess) e = e2;
+  cudaGraphExec_t x = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) return e;
+  s->graph[par] = x;
+  s->graph_dt[par] = dt;
+  s->graph_gen[par] = s->gen;
+  s->graph_launches[par] = per;
+  *out = x;
+  return cudaSuccess;
+}
+
 static int launch_steps(rt_state *s, int32_t n, double dt, double *dt_used, bool sync) {
   if (!s) return RT_ERR_ARG;
   if (!s->gas_set) return fail(s, RT_ERR_STATE, "rt_set_gas must be called before stepping");
@@ -799,7 +854,25 @@ static int launch_steps(rt_state *s, int32_t n, double dt, double *dt_used, bool
     return fail(s, RT_ERR_CFL, buf);
   }
   if (dt_used) *dt_used = dt;
-  for (int32_t i = 0; i < n; ++i) RT_CUDA(s, rt::launch_step(s, dt));
+  int32_t left = n;
+  if (!s->plain_launches && n >= RT_GRAPH_STEPS) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (s->stream) RT_CUDA(s, cudaStreamIsCapturing(s->stream, &cs));
+    cudaGraphExec_t x = nullptr;
+    if (cs == cudaStreamCaptureStatusNone && step_graph(s, dt, &x) != cudaSuccess) {
+      // no graph on this device or stream: plain launches from now on
+      (void)cudaGetLastError();
+      s->plain_launches = true;
+      x = nullptr;
+    }
+    if (x) {
+      for (; left >= RT_GRAPH_STEPS; left -= RT_GRAPH_STEPS) {
+        RT_CUDA(s, cudaGraphLaunch(x, s->stream));
+        s->launches += s->graph_launches[s->cur];
+      }
+    }
+  }
+  for (; left > 0; --left) RT_CUDA(s, rt::launch_step(s, dt));
   return sync ? sync_status(s) : RT_OK;
 }
 
@@ -939,6 +1012,7 @@ int rt_get_state(rt_state *s, void *buf, size_t *bytes) {
 
 int rt_set_state(rt_state *s, const void *buf, size_t bytes) {
   if (!s || !buf) return RT_ERR_ARG;
+  ++s->gen;  // captured step graphs may hold old arguments
   const int64_t N = s->n_cells;
   const size_t nI = (size_t)N * s->row_stride * s->rsize;
   const size_t nV = s->params.gcl ? sizeof(double) * N : 0;
@@ -979,6 +1053,9 @@ const char *rt_last_error(const rt_state *s) { return s ? s->err.c_str() : "null
 void rt_destroy(rt_state *s) {
   if (!s) return;
   if (s->stream || true) cudaStreamSynchronize(s->stream);
+  for (int k = 0; k < 2; ++k)
+    if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   for (int k = 0; k < 8; ++k)
     if (s->d_adj[k]) cudaFree(s->d_adj[k]);
   if (s->d_adj_ws) cudaFree(s->d_adj_ws);

@@ -144,6 +144,16 @@ struct rt_state {
   int64_t n_rows = 0;
   std::string err;
   int64_t launches = 0;
+  // captured step sequences of multi-step launches (rt_run / rt_launch), one
+  // per buffer parity: replayed only for the dt and the generation they were
+  // captured at (gen counts the rt_set_* calls, which may change arguments)
+  bool plain_launches = false;
+  uint64_t gen = 1;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaStream_t cap_stream = nullptr;  // the stream graphs are captured on
+  double graph_dt[2] = {0.0, 0.0};
+  uint64_t graph_gen[2] = {0, 0};
+  int64_t graph_launches[2] = {0, 0};
   size_t device_bytes = 0;
 
   // host copies needed for I/O

@@ -26,12 +26,14 @@ class RTSolver:
     precision: "fp32" (float intensities/transport, double quartic and
     exchange) or "fp64".  integrator: 0 first-order upwind step, 1 van Leer
     step with limited linear reconstruction (needs mesh.face_offset()).
+    plain_launches: 1 turns off the CUDA-graph replay of run() / launch()
+    (same kernels, same results; see rt_run in include/rt.h).
     """
 
     def __init__(self, mesh, dirs, weights, *, cbar, c, a_rad=1.0, gamma_gas=5.0 / 3.0,
                  r_gas=1.0, cfl=0.3, precision="fp32", newton_max_iter=64, integrator=0, boost=0, gcl=0,
                  beta_P=0.0, beta_J=0.0, T_ref=1.0, n_groups=1, group_w=None,
-                 stream=None):
+                 plain_launches=0, stream=None):
         if torch is None or not torch.cuda.is_available():
             raise RuntimeError("RTSolver needs a CUDA device (no CPU fallback exists)")
         self.lib = capi.load()
@@ -72,7 +74,8 @@ class RTSolver:
             md.face_offset = ptr(mesh.face_offset(), np.float64)
         pr = capi.Params(cbar, c, a_rad, gamma_gas, r_gas, cfl,
                          capi.RT_FP32 if precision == "fp32" else capi.RT_FP64, newton_max_iter,
-                         int(integrator), int(boost), int(gcl), 0, float(beta_P), float(beta_J),
+                         int(integrator), int(boost), int(gcl), int(plain_launches), float(beta_P),
+                         float(beta_J),
                          float(T_ref))
         st = ctypes.c_void_p()
         code = self.lib.rt_create(ctypes.byref(md), ctypes.byref(pr),

@@ -361,20 +361,24 @@ template <typename R> __device__ __forceinline__ R group_sum(R v) {
   return v;
 }
 
+// Cells per block of the source reverse (8 threads each).
+constexpr int kRevCells = CPB;
+constexpr int kRevThreads = kRevCells * step::KT;
+
 template <typename R, typename M>
-__global__ void __launch_bounds__(step::NT, sizeof(R) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kRevThreads, sizeof(R) == 4 ? (M::PPT <= 5 ? 4 : 3) : 2)
     source_reverse_tile(const AdjArgs<R> a) {
   using step::KT;
   constexpr int PPT = M::PPT;
-  __shared__ CellIn<R> cin[CPB];
-  __shared__ CellSums<R> sums[CPB];
-  __shared__ CellRev<R> rev[CPB];
-  __shared__ CellOut<R> cout_[CPB];
+  __shared__ CellIn<R> cin[kRevCells];
+  __shared__ CellSums<R> sums[kRevCells];
+  __shared__ CellRev<R> rev[kRevCells];
+  __shared__ CellOut<R> cout_[kRevCells];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int lc = threadIdx.x / KT, sub = threadIdx.x % KT;
-  const int64_t c0 = (int64_t)blockIdx.x * CPB;
+  const int64_t c0 = (int64_t)blockIdx.x * kRevCells;
   const int64_t cl = c0 + lane;  // the lane's cell in phases 0, 2, 4
-  const bool lane_cell = warp == 0 && cl < a.n;
+  const bool lane_cell = warp == 0 && lane < kRevCells && cl < a.n;
   // ---------------- phase 0: per-cell constants, one lane per cell
   if (lane_cell) cell_inputs(a, cl, cin[lane]);
 
@@ -476,8 +480,8 @@ __global__ void __launch_bounds__(step::NT, sizeof(R) == 4 ? 3 : 2)
 }
 
 template <typename R, typename M> void launch_reverse_tile(rt_state *s, const AdjArgs<R> &a) {
-  const unsigned g = (unsigned)((s->n_cells + CPB - 1) / CPB);
-  source_reverse_tile<R, M><<<g, step::NT, 0, s->stream>>>(a);
+  const unsigned g = (unsigned)((s->n_cells + kRevCells - 1) / kRevCells);
+  source_reverse_tile<R, M><<<g, kRevThreads, 0, s->stream>>>(a);
 }
 
 template <typename R, bool FULL> void reverse_pairs(rt_state *s, const AdjArgs<R> &a) {

@@ -401,7 +401,8 @@ __device__ __forceinline__ double group_xs(const GroupArgs<double> &a, int64_t c
 }
 
 template <typename R, typename M>
-__global__ void __launch_bounds__(step::NT, 2) group_source_tile(const GroupArgs<R> a) {
+__global__ void __launch_bounds__(step::NT, sizeof(R) == 4 && M::PPT <= 6 ? 3 : 2)
+    group_source_tile(const GroupArgs<R> a) {
   using V = step::pair_t<R>;
   using step::mk;
   using step::padd;

@@ -509,6 +509,11 @@ int rt_create(const rt_mesh_desc *m_in, const rt_params *p, void *stream, rt_sta
   CK(upload(s, &s->d_dir64, dir64));
   CK(upload(s, &s->d_wt64, wt64));
   CK(upload(s, &s->d_angle_of, angle_of));
+  {
+    std::vector<int32_t> pos_of(angle_of.size());
+    for (size_t q = 0; q < angle_of.size(); ++q) pos_of[(size_t)angle_of[q]] = (int32_t)q;
+    CK(upload(s, &s->d_pos_of, pos_of));
+  }
   CK(dalloc(s, &s->d_gs, N));
   CK(dalloc(s, &s->d_gd, N));
   CK(dalloc(s, &s->d_kind, N));
@@ -720,6 +725,18 @@ int rt_set_cells(rt_state *s, const uint8_t *kind, const double *tau, const doub
   return RT_OK;
 }
 
+// The device-side address of page-locked (cudaHostAlloc / cudaHostRegister)
+// host memory, which kernels may read and write; NULL for any other pointer
+// (pageable memory then goes through a staged copy).
+static const void *pinned_device_address(const void *p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 int rt_set_intensity(rt_state *s, const void *I, int on_device) {
   if (!s || !I) return s ? fail(s, RT_ERR_ARG, "rt_set_intensity: NULL") : RT_ERR_ARG;
   ++s->gen;  // captured step graphs may hold old arguments
@@ -727,6 +744,13 @@ int rt_set_intensity(rt_state *s, const void *I, int on_device) {
   const void *src = I;
   void *stage = s->d_I[s->cur ^ 1];
   if (!on_device) {
+    if (const void *dev = pinned_device_address(I)) {
+      // page-locked host rows: one pass reads them over the host link and
+      // writes the internal rows
+      RT_CUDA(s, rt::launch_permute_in_host(s, dev, s->d_I[s->cur], s->row_stride));
+      RT_CUDA(s, cudaStreamSynchronize(s->stream));
+      return RT_OK;
+    }
     RT_CUDA(s, cudaMemcpyAsync(stage, I, bytes, cudaMemcpyHostToDevice, s->stream));
     src = stage;
   }
@@ -740,6 +764,8 @@ int rt_get_intensity(rt_state *s, void *I, int on_device) {
   const size_t bytes = (size_t)s->n_cells * s->n_angles * s->rsize;
   if (on_device) {
     RT_CUDA(s, rt::launch_permute_out(s, s->d_I[s->cur], I, s->row_stride));
+  } else if (void *dev = const_cast<void *>(pinned_device_address(I))) {
+    RT_CUDA(s, rt::launch_permute_out_host(s, s->d_I[s->cur], dev, s->row_stride));
   } else {
     void *stage = s->d_I[s->cur ^ 1];
     RT_CUDA(s, rt::launch_permute_out(s, s->d_I[s->cur], stage, s->row_stride));
@@ -1060,7 +1086,7 @@ void rt_destroy(rt_state *s) {
     if (s->d_adj[k]) cudaFree(s->d_adj[k]);
   if (s->d_adj_ws) cudaFree(s->d_adj_ws);
   if (s->d_adj_stage) cudaFree(s->d_adj_stage);
-  void *bufs[] = {s->d_kapgf, s->d_kapg, s->d_rkJ0, s->d_gcl_rate, s->d_gcl_kv, s->d_recon, s->d_lsq, s->d_Ihalf, s->d_grad, s->d_uface, s->d_slot_nb, s->d_wface, s->d_angle_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
+  void *bufs[] = {s->d_kapgf, s->d_kapg, s->d_rkJ0, s->d_gcl_rate, s->d_gcl_kv, s->d_recon, s->d_lsq, s->d_Ihalf, s->d_grad, s->d_uface, s->d_slot_nb, s->d_wface, s->d_angle_of, s->d_pos_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
                   s->d_gd, s->d_kind, s->d_aux, s->d_bc_row, s->d_I0, s->d_ext, s->d_dir, s->d_wt,
                   s->d_dir64, s->d_wt64, s->d_I[0], s->d_I[1], s->d_status, s->d_bad,
                   s->d_scratch, s->d_out16};

@@ -37,6 +37,31 @@ __global__ void permute_out_kernel(const R *__restrict__ src, R *__restrict__ ds
   for (int k = threadIdx.x % 32; k < A; k += 32) d[angle_of[k]] = s[k];
 }
 
+// Host-memory forms: lane k takes caller column k of the row (contiguous on
+// the host side) and the internal position pos_of[k].
+template <typename R>
+__global__ void permute_in_host_kernel(const R *__restrict__ src, R *__restrict__ dst,
+                                       const int64_t *__restrict__ cell_of,
+                                       const int32_t *__restrict__ pos_of, int64_t n, int A,
+                                       int stride) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (row >= n) return;
+  const R *s = src + (size_t)cell_of[row] * A;
+  R *d = dst + (size_t)row * stride;
+  for (int k = threadIdx.x % 32; k < A; k += 32) d[pos_of[k]] = s[k];
+}
+template <typename R>
+__global__ void permute_out_host_kernel(const R *__restrict__ src, R *__restrict__ dst,
+                                        const int64_t *__restrict__ cell_of,
+                                        const int32_t *__restrict__ pos_of, int64_t n, int A,
+                                        int stride) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (row >= n) return;
+  const R *s = src + (size_t)row * stride;
+  R *d = dst + (size_t)cell_of[row] * A;
+  for (int k = threadIdx.x % 32; k < A; k += 32) d[k] = s[pos_of[k]];
+}
+
 __device__ __forceinline__ double slot_u(const SlotF &s, const double *, int64_t, double x,
                                          double y, double z) {
   return x * (double)s.sx + y * (double)s.sy + z * (double)s.sz - (double)s.w;
@@ -280,6 +305,32 @@ cudaError_t launch_permute_out(rt_state *s, const void *src, void *dst, int stri
     permute_out_kernel<double><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
         (const double *)src, (double *)dst, s->d_cell_of, s->d_angle_of, s->n_cells,
         s->n_angles, stride);
+  s->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute_in_host(rt_state *s, const void *src, void *dst, int stride) {
+  if (s->precision == RT_FP32)
+    permute_in_host_kernel<float><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
+        (const float *)src, (float *)dst, s->d_cell_of, s->d_pos_of, s->n_cells, s->n_angles,
+        stride);
+  else
+    permute_in_host_kernel<double><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
+        (const double *)src, (double *)dst, s->d_cell_of, s->d_pos_of, s->n_cells, s->n_angles,
+        stride);
+  s->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute_out_host(rt_state *s, const void *src, void *dst, int stride) {
+  if (s->precision == RT_FP32)
+    permute_out_host_kernel<float><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
+        (const float *)src, (float *)dst, s->d_cell_of, s->d_pos_of, s->n_cells, s->n_angles,
+        stride);
+  else
+    permute_out_host_kernel<double><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
+        (const double *)src, (double *)dst, s->d_cell_of, s->d_pos_of, s->n_cells, s->n_angles,
+        stride);
   s->launches++;
   return cudaGetLastError();
 }

@@ -204,6 +204,7 @@ struct rt_state {
   double *d_dir64 = nullptr;   // [A][3] double, internal angle order
   double *d_wt64 = nullptr;    // [A], internal angle order
   int32_t *d_angle_of = nullptr;  // internal angle position -> caller angle
+  int32_t *d_pos_of = nullptr;    // caller angle -> internal angle position
   void *d_I[2] = {nullptr, nullptr};
   int cur = 0;
   unsigned *d_status = nullptr;
@@ -245,6 +246,11 @@ cudaError_t build_uface(rt_state *s);
 // caller order <-> internal order; the internal rows are `stride` reals apart
 cudaError_t launch_permute_in(rt_state *s, const void *src, void *dst, int stride);
 cudaError_t launch_permute_out(rt_state *s, const void *src, void *dst, int stride);
+// the same with the caller's rows in page-locked host memory (src / dst: the
+// device-side address of that memory): every caller row is read or written
+// whole and in order, so the host link sees full lines
+cudaError_t launch_permute_in_host(rt_state *s, const void *src, void *dst, int stride);
+cudaError_t launch_permute_out_host(rt_state *s, const void *src, void *dst, int stride);
 // kcell (may be NULL): per cell max_a sum_f max(u, 0), float
 cudaError_t launch_positivity(rt_state *s, const SlotF *fslot, double *d_kmax, float *kcell);
 // inv_vol = 1 / volume (state precision) after the volumes changed

@@ -5,11 +5,13 @@
 // One step of the van Leer integrator is four launches:
 //   1. the fused step kernel over dt/2 from I^n into I^{n+1/2} (first-order
 //      upwinding), its gas update discarded;
-//   2. gradient_tile: least-squares gradients of I^{n+1/2} over each cell's
-//      face neighbours, weights A_f / |r_f|^2, limited (Barth-Jespersen) so
-//      that the reconstructed face values stay within the range of the cell
-//      and its neighbours;
-//   3. recon_transport_tile: I* = I^n - dt/V sum_f u I_up with the upwind
+//   2. the gradient (gradient_quad for float rows in the quad layout,
+//      gradient_tile otherwise): least-squares gradients of I^{n+1/2} over
+//      each cell's face neighbours, weights A_f / |r_f|^2, limited
+//      (Barth-Jespersen) so that the reconstructed face values stay within
+//      the range of the cell and its neighbours;
+//   3. the reconstructed transport (recon_transport_quad /
+//      recon_transport_tile): I* = I^n - dt/V sum_f u I_up with the upwind
 //      value reconstructed at the face centre from I^{n+1/2} and its gradient
 //      (the same value on both sides of a face, so the update conserves);
 //   4. the fused step kernel in source-only mode over dt from the gas at n.

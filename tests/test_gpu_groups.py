@@ -103,3 +103,28 @@ def test_groups_refuse_what_is_grey_only():
     prob.integrator = capi.RT_VAN_LEER
     with pytest.raises(capi.RTError):
         solver(prob, "fp64")
+
+
+@pytest.mark.parametrize("G", [4, 5], ids=["G4_tile", "G5_warp"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_groups_four_and_five(G, precision):
+    """S2 with 4 groups (32 angles: the tile kernel's largest group count) and
+    5 groups (40 angles: the warp-per-cell kernel)."""
+    rng = np.random.default_rng(10 + G)
+    gw = rng.uniform(0.5, 1.5, G)
+    gw /= gw.sum()
+    sP, sJ, sS, ig = (rng.uniform(0.2, 3.0, G) for _ in range(4))
+    prob = grouped(randomise(make(n=(6, 5, 4), order=2, cbar=10.0, c=100.0), seed=5 + G),
+                   gw, sP, sJ, sS, ig)
+    o = oracle.Oracle(prob)
+    g = solver(prob, precision)
+    t0 = g.totals()
+    dt = o.cfl_dt()
+    assert o.run(30, dt) == oracle.ORC_OK
+    g.run(30, dt)
+    if precision == "fp64":
+        check_fp64(o, g)
+    else:
+        check_fp32(o, g)
+        assert abs(g.totals()[12] - t0[12]) < FP32_ENERGY * abs(t0[12])
+

@@ -112,3 +112,28 @@ def test_van_leer_state_rejects_the_adjoint():
     with pytest.raises(capi.RTError) as err:
         g.adjoint_step(0.01, t(N, A), t(N), t(N, 3), t(N, A), t(N), t(N, 3), t(N), t(N))
     assert err.value.code == capi.RT_ERR_STATE
+
+
+def _custom_angles(prob, n_pairs, seed):
+    """The problem on n_pairs random antipodal pairs of directions with equal
+    weights (angle counts the level-symmetric sets do not reach: 32 rows take
+    one quad per thread and no tail, 112 three quads and a tail)."""
+    rng = np.random.default_rng(seed)
+    up = rng.normal(size=(n_pairs, 3))
+    up /= np.linalg.norm(up, axis=1, keepdims=True)
+    prob.dirs = np.ascontiguousarray(np.concatenate([up, -up]))
+    A = 2 * n_pairs
+    prob.weights = np.full(A, 1.0 / A)
+    prob.q0 = np.ones(A)
+    prob.I0 = np.zeros((1, A))
+    return prob
+
+
+@pytest.mark.parametrize("n_pairs", [16, 56], ids=["A32", "A112"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_vanleer_custom_angle_sets(n_pairs, precision):
+    base = make(n=(7, 6, 5), order=2, cbar=10.0, c=100.0, w=(0.3, -0.1, 0.2))
+    prob = randomise(_custom_angles(base, n_pairs, 3), seed=6)
+    o, g, t0 = _run(prob, precision, 10)
+    _check(o, g, precision, t0)
+

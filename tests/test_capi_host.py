@@ -93,6 +93,34 @@ def test_create_rejects_bad_meshes(lib):
     assert _create(lib, mesh, dirs, w * 2)[0] == capi.RT_ERR_ARG
 
 
+def test_create_rejects_bad_params(lib):
+    """Flags outside {0, 1}, van Leer with the GCL, non-finite or too negative
+    opacity exponents and T_ref <= 0 with an exponent are refused before any
+    device work."""
+    mesh = build_mesh((3, 3, 3), seed=1)
+    dirs, w = level_symmetric(4)
+
+    def code(**kw):
+        keep = []
+        d = _desc(mesh, dirs, w, keep)
+        offs = np.ascontiguousarray(mesh.face_offset(), np.float64)  # van Leer's input, present
+        keep.append(offs)
+        d.face_offset = offs.ctypes.data
+        pr = capi.Params(10.0, 10.0, 1.0, 5.0 / 3.0, 1.0, 0.3, capi.RT_FP64, 64)
+        pr.T_ref = 1.0
+        for k, v in kw.items():
+            setattr(pr, k, v)
+        st = ctypes.c_void_p()
+        c = lib.rt_create(ctypes.byref(d), ctypes.byref(pr), None, ctypes.byref(st))
+        assert not st.value
+        return c
+
+    for kw in ({"plain_launches": 2}, {"boost": -1}, {"gcl": 2}, {"integrator": 5},
+               {"gcl": 1, "integrator": capi.RT_VAN_LEER}, {"beta_P": float("nan")},
+               {"beta_P": -3.5}, {"beta_J": 1.0, "T_ref": 0.0}, {"precision": 7}, {"cfl": 0.0}):
+        assert code(**kw) == capi.RT_ERR_ARG, kw
+
+
 def test_null_arguments(lib):
     st = ctypes.c_void_p()
     assert lib.rt_create(None, None, None, ctypes.byref(st)) == capi.RT_ERR_ARG

@@ -1,13 +1,16 @@
 """Throughput of the radiation step (transport + implicit source) on GB300.
 
-Workload: the shadows / crossing-beams box at full size: 128^3 jittered
-periodic Voronoi cells, 80 discrete ordinates, three opaque spheres, four
-emitter cells, absorbing boundary layers and two collimated beams (seeded,
-synthetic).  One "step" is one rt_step: the fused transport + source kernel
-over every cell and angle.  Reported: cell-angle updates/s of the FP32 path
-(headline) and of the FP64 path, each against the HBM roofline of its
-algorithmic bytes; an end-to-end figure through the C ABI with host
-buffers; and the CPU oracle timed on this host's cores.
+Headline workload: the radiation-modified linear waves box at scale
+(Sec. 3.6 setup): 256^3 jittered periodic Voronoi cells, 80 discrete
+ordinates (S8), cell optical depth 1, cbar = 100, c = 1e4, a 1e-6 sinusoidal
+temperature / radiation-energy perturbation along x (seeded, synthetic).
+One "step" is one rt_step: the fused transport + source kernel over every
+cell and angle.  Reported: cell-angle updates/s of the FP32 path (headline)
+and of the FP64 path, each against the roofline of its algorithmic bytes or
+flops; an end-to-end figure through the C ABI with host buffers; and the
+CPU oracle timed on this host's cores (all of them and one).  The 128^3
+shadows / crossing-beams box is timed beside it, with the van Leer,
+adjoint, frequency-group and launch-bound thermal legs on the shadows box.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -34,15 +37,14 @@ METRIC = "cell-angle updates/s (transport+implicit source), FP32 vs FP64, % HBM 
 UNIT = "cell-angle updates/s"
 
 # DRAM bytes (read + write) per launch of the step kernels, from one ncu
-# capture each of the 96^3 case (FP32 963.3 MB, FP64 5910.3 MB) scaled to
-# the 128^3 workload by the cell count (traffic grows with the cells
-# processed); valid while the step kernel's device source has the recorded
-# hash.
-NCU_TRAFFIC = {"fp32": 962.701056e6 * 2097152 / 884736, "fp64": 5907.995648e6 * 2097152 / 884736}
-NCU_SOURCE_SHA = "09f34c97cadb3995"
-# FP64 arithmetic peak of the GPU (dense FMA, from the hardware's nominal
-# figure); the FP64 state is bound by it, not by HBM.
-FP64_PEAK_GFLOPS = 1250.0
+# capture (dram__bytes_read.sum + dram__bytes_write.sum, one launch, one
+# pass) at the benchmarked size of each workload; valid while the step
+# kernel's device source has the recorded hash (else reported as null).
+NCU_TRAFFIC = {}
+NCU_SOURCE_SHA = None
+# FP64 arithmetic peak when the DGEMM probe cannot run: the nominal dense
+# FP64 FMA rate of the GPU.
+FP64_NOMINAL_GFLOPS = 1250.0
 
 
 def kernel_source_sha():
@@ -193,35 +195,44 @@ def barrier(world):
 
 
 # ---------------------------------------------------------------- workload
-def make_workload(n=128):
-    from paper_2002_08377_gb300.inputs import shadows
-    return shadows(n=n)
+def make_workload(name="waves", n=None):
+    from paper_2002_08377_gb300.inputs import shadows, waves
+    if name == "waves":
+        return waves(n=256 if n is None else n)
+    return shadows(n=128 if n is None else n)
 
 
 def describe(prob):
     n = prob.mesh.n[0]
-    return {"workload": f"shadows/crossing-beams box: {n}^3 jittered periodic Voronoi cells, "
-                        "80 level-symmetric angles, 3 opaque spheres, 4 emitters, absorbing "
-                        "layers, 2 beams, cbar = c = 1e3",
-            "cells": prob.n_cells, "angles": prob.n_angles, "faces": prob.mesh.n_faces,
+    base = {"cells": prob.n_cells, "angles": prob.n_angles, "faces": prob.mesh.n_faces,
             "directed_faces_per_cell": round(2 * prob.mesh.n_faces / prob.n_cells, 3),
-            "l2": "inputs larger than L2 (FP32 intensities 2 x 671 MB + face slots)"}
+            "l2": "inputs larger than L2 (129 MB): intensities 2 x "
+                  f"{prob.n_cells * prob.n_angles * 4 / 1e6:.0f} MB (FP32) + face slots"}
+    if prob.name == "waves":
+        base["workload"] = (f"radiation-modified linear waves at scale: {n}^3 jittered periodic "
+                            "Voronoi cells, 80 level-symmetric angles (S8), cell optical depth 1, "
+                            "cbar = 100, c = 1e4, 1e-6 sinusoidal T / E_r perturbation along x")
+    else:
+        base["workload"] = (f"shadows/crossing-beams box: {n}^3 jittered periodic Voronoi cells, "
+                            "80 level-symmetric angles, 3 opaque spheres, 4 emitters, absorbing "
+                            "layers, 2 beams, cbar = c = 1e3")
+    return base
 
 
 # ---------------------------------------------------------------- CPU oracle
-def cpu_oracle_rate(prob, dt, budget_s, max_cells=None):
-    """Cell-angle updates/s of the FP64 oracle (OpenMP over all host cores)
-    on contiguous cell ranges of the same workload until budget_s passes."""
-    import oracle
-    o = oracle.Oracle(prob)
-    N, A = prob.n_cells, prob.n_angles
-    chunk = N if max_cells is None else min(N, max_cells)
+def cpu_oracle_rate(o, dt, budget_s, chunk):
+    """Cell-angle updates/s of the FP64 oracle `o` on consecutive ranges of
+    `chunk` cells of its workload (transport + source of those cells from
+    the full state), until budget_s passes."""
+    N, A = o.N, o.A
     done, t0 = 0, time.perf_counter()
     out = np.empty_like(o.I)
     c0 = 0
     while True:
         c1 = min(N, c0 + chunk)
-        o.sample_step(dt, c0, c1, out)
+        st, _ = o.sample_step(dt, c0, c1, out)
+        if st != 0:
+            raise RuntimeError(f"oracle step failed ({st})")
         done += (c1 - c0) * A
         c0 = 0 if c1 >= N else c1
         el = time.perf_counter() - t0
@@ -230,15 +241,54 @@ def cpu_oracle_rate(prob, dt, budget_s, max_cells=None):
     return done / el, done, el
 
 
+def mem_available():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) << 10
+    except OSError:
+        pass
+    return None
+
+
+def cpu_baseline(prob, dt, budget_s):
+    """The oracle on all host cores and on one core, on bounded samples of
+    the workload (ranges of cells of one step)."""
+    import oracle
+    # the oracle's state: two [N][A] double arrays, the face offsets and its
+    # copies of the mesh arrays
+    need = 2 * prob.n_cells * prob.n_angles * 8 + prob.mesh.n_faces * 120
+    avail = mem_available()
+    if avail is not None and avail < 1.3 * need:
+        return {"unavailable": f"host memory: {avail >> 30} GB available, the oracle state of "
+                               f"this workload needs about {need >> 30} GB"}
+    o = oracle.Oracle(prob)
+    N, A = o.N, o.A
+    cores = oracle.set_threads(0)
+    chunk = max(1, min(N, 1 << 18))
+    v, done, el = cpu_oracle_rate(o, dt, budget_s, chunk)
+    oracle.set_threads(1)
+    v1, done1, el1 = cpu_oracle_rate(o, dt, max(2.0, budget_s / 3), max(1, chunk // 16))
+    oracle.set_threads(cores)
+    del o
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} cell-angle updates of the FP64 oracle ({el:.1f} s; ranges of "
+                      f"{chunk} of the {N} cells x {A} angles of one step, transport + source)",
+            "single_core": {"value": v1, "unit": UNIT, "cores": 1,
+                            "sample": f"{done1} cell-angle updates ({el1:.1f} s, ranges of "
+                                      f"{max(1, chunk // 16)} cells)"}}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    prob = make_workload(args.n)
+    prob = make_workload(args.workload, args.n)
     dt = prob.cfl_dt()
     import oracle
     o = oracle.Oracle(prob)
     N, A = prob.n_cells, prob.n_angles
-    sample = max(1, N // 16)  # each step: one sixteenth of the cells
+    sample = max(1, N // 64)  # each step: one sixty-fourth of the cells
     out = np.empty_like(o.I)
     for _ in range(args.warmup):
         o.sample_step(dt, 0, sample, out)
@@ -248,14 +298,14 @@ def run_reference(args, world, rank):
         o.sample_step(dt, c0, min(N, c0 + sample), out)
     el = time.perf_counter() - t0
     v = sample * A * args.steps / el
-    cores = os.cpu_count()
+    cores = oracle.set_threads(0)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": describe(prob),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"cells [c0, c0+{sample}) of one step per timed step "
-                                       f"(1/16 of the {N}-cell, {A}-angle workload)"},
+                                       f"(1/64 of the {N}-cell, {A}-angle workload)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -448,24 +498,131 @@ def adjoint_rate(prob, prec, dt, steps, warmup):
             "dtype": "f32" if prec == "fp32" else "f64"}
 
 
+def host_link_ceiling(n_bytes):
+    """Plain copies of n_bytes between pinned host memory and the device
+    (one cudaMemcpyAsync each way through torch), CUDA events, best of 3:
+    the host-link rate an end-to-end step could at best reach."""
+    import torch
+    n = n_bytes // 4
+    h = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    d = torch.empty(n, dtype=torch.float32, device="cuda")
+    best = {"h2d": 1e30, "d2h": 1e30}
+    for _ in range(3):
+        for k in ("h2d", "d2h"):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            if k == "h2d":
+                d.copy_(h, non_blocking=True)
+            else:
+                h.copy_(d, non_blocking=True)
+            e1.record()
+            torch.cuda.synchronize()
+            best[k] = min(best[k], e0.elapsed_time(e1))
+    del h, d
+    torch.cuda.empty_cache()
+    return {k: {"GB_per_s": 4 * n / (ms * 1e-3) / 1e9, "ms": ms, "bytes": 4 * n}
+            for k, ms in best.items()}
+
+
+def fp64_peak_probe():
+    """Measured FP64 arithmetic rate: cuBLAS DGEMM 8192^3 (2 N^3 flops), best
+    of 3 after one warm-up, CUDA events.  The denominator of the FP64 step's
+    ALU roofline (the nominal dense FP64 rate is 1.25 TFLOP/s)."""
+    import torch
+    n = 8192
+    a = torch.rand(n, n, dtype=torch.float64, device="cuda")
+    b = torch.rand(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = 1e30
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b
+    torch.cuda.empty_cache()
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e9
+
+
+def roofline(prec, N, Nf, A, per_ms, hbm_peak, peak_kind, fp64_peak, fp64_kind, traffic):
+    """The roofline object of one precision's step kernel: HBM-bound for
+    FP32 (algorithmic bytes / launch time), FP64-ALU-bound for FP64
+    (algorithmic flops / launch time) with its HBM fraction beside."""
+    rb = 4 if prec == "fp32" else 8
+    B = algorithmic_bytes(N, Nf, A, rb)
+    achieved = B / (per_ms * 1e-3) / 1e9
+    if prec == "fp32":
+        return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic,
+                "algorithmic_bytes_per_launch": B,
+                "peak_source": f"{peak_kind} HBM copy bandwidth (of {peak_kind})"}
+    F = algorithmic_fp64_flops(N, Nf, A)
+    gf = F / (per_ms * 1e-3) / 1e9
+    return {"bound": "alu", "achieved": gf, "peak": fp64_peak, "unit": "GFLOP/s",
+            "frac": gf / fp64_peak, "traffic": traffic, "algorithmic_flops_per_launch": F,
+            "peak_source": fp64_kind,
+            "hbm": {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "algorithmic_bytes_per_launch": B}}
+
+
+def time_workload(prob, precs, steps, warmup, world, hbm_peak, peak_kind, fp64_peak, fp64_kind,
+                  sampler=None, e2e=False):
+    """Both precisions' step on one workload: per precision the timed rate,
+    its roofline and the state's device memory; with e2e, the end-to-end
+    rate of the FP32 state through the C ABI with pinned host buffers."""
+    import torch
+    from paper_2002_08377_gb300.solver import RTSolver
+    N, A, Nf = prob.n_cells, prob.n_angles, prob.mesh.n_faces
+    dt = prob.cfl_dt()
+    res = {}
+    sha = kernel_source_sha()
+    for key in precs:
+        # "fp32_float_quartic": the FP32 state with the temperature solved in float
+        prec = "fp64" if key == "fp64" else "fp32"
+        sol = RTSolver.from_problem(prob, prec, float_quartic=int(key == "fp32_float_quartic"))
+        k = steps if prec == "fp32" else max(3, steps // 5)
+        ms, launches = time_steps(sol, dt, k, max(3, warmup), world,
+                                  sampler if key == "fp32" else None)
+        per = ms / k
+        tr = NCU_TRAFFIC.get((prob.name, N, key)) if NCU_SOURCE_SHA == sha else None
+        res[key] = {"value": N * A * k * world / (ms * 1e-3), "ms_per_step": per, "steps": k,
+                    "launches": launches, "device_bytes": sol.device_bytes(),
+                    "roofline": roofline(prec, N, Nf, A, per, hbm_peak, peak_kind, fp64_peak,
+                                         fp64_kind, tr)}
+        if key == "fp32" and e2e:
+            e2e_v, bi, bo = e2e_rate(sol, prob, dt, max(3, min(10, steps)))
+            res["e2e"] = {"value": e2e_v * world, "unit": UNIT, "h2d_bytes_per_step": bi,
+                          "d2h_bytes_per_step": bo}
+        sol.close()
+        del sol
+        torch.cuda.empty_cache()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-vl", action="store_true", help="skip the van Leer leg")
-    ap.add_argument("--no-adj", action="store_true", help="skip the adjoint leg")
-    ap.add_argument("--no-groups", action="store_true", help="skip the frequency-group leg")
-    ap.add_argument("--no-thermal", action="store_true", help="skip the launch-bound thermal leg")
-    ap.add_argument("--only", choices=["fp32", "fp64"], default=None,
-                    help="time one precision only (profiling runs)")
-    ap.add_argument("--n", type=int, default=128,
-                    help="lattice cells per axis (128 = the benchmarked workload; smaller for "
-                         "profiler captures)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the shadows box and its van Leer / adjoint / group / thermal legs")
+    ap.add_argument("--only", choices=["fp32", "fp64", "fp32_float_quartic"], default=None,
+                    help="time one precision of one workload only (profiling runs)")
+    ap.add_argument("--workload", choices=["waves", "shadows"], default="waves",
+                    help="the headline workload (waves: the 256^3 linear-wave box)")
+    ap.add_argument("--n", type=int, default=None,
+                    help="lattice cells per axis of the headline workload (default: its full "
+                         "size; smaller for profiler captures)")
+    ap.add_argument("--shadows-n", type=int, default=128,
+                    help="lattice cells per axis of the shadows box of the extra legs")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":
@@ -480,115 +637,103 @@ def main():
     from paper_2002_08377_gb300.solver import RTSolver
     rtbuild.build()
 
-    prob = make_workload(args.n)
-    N, A, Nf = prob.n_cells, prob.n_angles, prob.mesh.n_faces
-    dt = prob.cfl_dt()
     hbm_peak, peak_kind = measured_peaks()
-    results = {}
+    if args.only is not None:
+        prob = make_workload(args.workload, args.n)
+        r = time_workload(prob, (args.only,), args.steps, args.warmup, world, hbm_peak, peak_kind,
+                          FP64_NOMINAL_GFLOPS, "nominal dense FP64 rate", None, False)[args.only]
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": r["value"], "unit": UNIT,
+                              "ms_per_step": r["ms_per_step"], "dtype": args.only,
+                              "config": describe(prob), "roofline": r["roofline"],
+                              "device_bytes": r["device_bytes"],
+                              "note": "single-precision profiling run"}), flush=True)
+        return
+
+    try:
+        fp64_peak = fp64_peak_probe()
+        fp64_kind = "measured cuBLAS DGEMM 8192^3 FP64 rate on this GPU (of measured)"
+    except Exception as ex:  # no DGEMM: the nominal figure
+        fp64_peak, fp64_kind = FP64_NOMINAL_GFLOPS, f"nominal dense FP64 rate ({ex})"
+
     sampler = ClockSampler(index=0)
-    precs = ("fp32", "fp64") if args.only is None else (args.only,)
-    for prec in precs:
-        sol = RTSolver.from_problem(prob, prec)
-        steps = args.steps if prec == "fp32" else max(3, args.steps // 5)
-        ms, launches = time_steps(sol, dt, steps, max(3, args.warmup), world,
-                                  sampler if prec == "fp32" else None)
-        per = ms / steps
-        rb = 4 if prec == "fp32" else 8
-        B = algorithmic_bytes(N, Nf, A, rb)
-        achieved = B / (per * 1e-3) / 1e9
-        traffic = NCU_TRAFFIC.get(prec) if NCU_SOURCE_SHA == kernel_source_sha() else None
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": traffic,
-                "algorithmic_bytes_per_launch": B,
-                "peak_source": f"{peak_kind} HBM copy bandwidth"}
-        if prec == "fp64":
-            # double arithmetic runs at 1/64 of float on this GPU: the FP64 step
-            # is bound by it; its HBM fraction is kept for reference
-            F = algorithmic_fp64_flops(N, Nf, A)
-            gf = F / (per * 1e-3) / 1e9
-            roof = {"bound": "alu", "achieved": gf, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                    "frac": gf / FP64_PEAK_GFLOPS, "traffic": traffic,
-                    "algorithmic_flops_per_launch": F,
-                    "peak_source": "nominal dense FP64 FMA rate (1.25 TFLOP/s)",
-                    "hbm": {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                            "frac": achieved / hbm_peak, "algorithmic_bytes_per_launch": B}}
-        results[prec] = {
-            "value": N * A * steps * world / (ms * 1e-3), "ms_per_step": per, "steps": steps,
-            "launches": launches, "roofline": roof}
-        if prec == "fp32" and not args.no_e2e:
-            e2e_v, bi, bo = e2e_rate(sol, prob, dt, max(3, min(10, args.steps)))
-            results["e2e"] = {"value": e2e_v * world, "unit": UNIT, "h2d_bytes_per_step": bi,
-                              "d2h_bytes_per_step": bo}
-        sol.close()
-        del sol
-        torch.cuda.empty_cache()
+    prob = make_workload(args.workload, args.n)
+    N, A = prob.n_cells, prob.n_angles
+    dt = prob.cfl_dt()
+    head = time_workload(prob, ("fp32", "fp64", "fp32_float_quartic"), args.steps, args.warmup,
+                         world, hbm_peak, peak_kind, fp64_peak, fp64_kind, sampler,
+                         not args.no_e2e)
+    link = None
+    if not args.no_e2e:
+        link = host_link_ceiling(N * A * 4)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(prob, dt, args.cpu_budget)
+    head_cfg = describe(prob)
+    del prob
 
-    vl = None
-    if args.only is None and not args.no_vl:
+    extras = None
+    if not args.no_extras:
+        sprob = make_workload("shadows", args.shadows_n)
+        sN, sA, sNf = sprob.n_cells, sprob.n_angles, sprob.mesh.n_faces
+        sdt = sprob.cfl_dt()
+        sh = time_workload(sprob, ("fp32", "fp64"), args.steps, args.warmup, world, hbm_peak,
+                           peak_kind, fp64_peak, fp64_kind)
+        extras = {"config": describe(sprob), "fp32": sh["fp32"], "fp64": sh["fp64"]}
         # the van Leer integrator with limited linear reconstruction (FP32)
-        prob.integrator = 1
-        sol = RTSolver.from_problem(prob, "fp32")
-        steps = max(3, args.steps // 5)
-        ms, launches = time_steps(sol, dt, steps, max(3, args.warmup), world)
-        per = ms / steps
-        B = algorithmic_bytes_vl(N, Nf, A, 4)
+        sprob.integrator = 1
+        sol = RTSolver.from_problem(sprob, "fp32")
+        k = max(3, args.steps // 5)
+        ms, launches = time_steps(sol, sdt, k, max(3, args.warmup), world)
+        per = ms / k
+        B = algorithmic_bytes_vl(sN, sNf, sA, 4)
         achieved = B / (per * 1e-3) / 1e9
-        vl = {"value": N * A * steps * world / (ms * 1e-3), "ms_per_step": per, "steps": steps,
-              "launches": launches, "dtype": "f32",
-              "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                           "frac": achieved / hbm_peak, "traffic": None,
-                           "algorithmic_bytes_per_step": B,
-                           "peak_source": f"{peak_kind} HBM copy bandwidth"}}
+        extras["van_leer"] = {
+            "value": sN * sA * k * world / (ms * 1e-3), "ms_per_step": per, "steps": k,
+            "launches": launches, "dtype": "f32",
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "algorithmic_bytes_per_step": B,
+                         "bytes_model": "first-order stage + gradient rows + reconstructed "
+                                        "transport + source stage (algorithmic_bytes_vl)",
+                         "peak_source": f"{peak_kind} HBM copy bandwidth"}}
         sol.close()
         del sol
-        prob.integrator = 0
+        sprob.integrator = 0
         torch.cuda.empty_cache()
-
-    grp = None
-    if args.only is None and not args.no_groups:
-        grp = groups_rate(args.n, max(3, args.steps // 5), 3, hbm_peak, peak_kind)
-
-    thm = None
-    if args.only is None and not args.no_thermal:
-        thm = thermal_rate(world)
-
-    adj = None
-    if args.only is None and not args.no_adj:
         # one reverse step (rt_adjoint_step: forward transport sweep, source
         # reverse, transposed sweep, caller-order permutes) per timed step
         adj = {}
         for prec in ("fp32", "fp64"):
             k = max(3, args.steps // 10) if prec == "fp32" else 3
-            r = adjoint_rate(prob, prec, dt, k, 2)
-            r["over_forward_step"] = r["ms_per_step"] / results[prec]["ms_per_step"]
+            r = adjoint_rate(sprob, prec, sdt, k, 2)
+            r["over_forward_step"] = r["ms_per_step"] / sh[prec]["ms_per_step"]
             adj[prec] = r
+        extras["adjoint"] = adj
+        del sprob
+        extras["groups"] = groups_rate(args.shadows_n, max(3, args.steps // 5), 3, hbm_peak,
+                                       peak_kind)
+        extras["thermal"] = thermal_rate(world)
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        v, done, el = cpu_oracle_rate(prob, dt, args.cpu_budget)
-        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{done} cell-angle updates of the FP64 oracle on this workload "
-                         f"({el:.1f} s, whole steps of {N} cells x {A} angles)"}
-    if args.only is not None:
-        r = results[args.only]
-        if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": r["value"], "unit": UNIT,
-                              "ms_per_step": r["ms_per_step"], "dtype": args.only,
-                              "config": describe(prob), "roofline": r["roofline"],
-                              "note": "single-precision profiling run"}), flush=True)
-        return
-    r32 = results["fp32"]
+    r32, r64 = head["fp32"], head["fp64"]
     line = {"metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": world,
             "steps": r32["steps"], "warmup": max(3, args.warmup), "ms_per_step": r32["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": describe(prob), "roofline": r32["roofline"],
-            "cpu_baseline": cpu, "e2e": results.get("e2e"), "gpu_launches": r32["launches"],
+            "data": "synthetic", "config": head_cfg, "roofline": r32["roofline"],
+            "cpu_baseline": cpu, "e2e": head.get("e2e"), "host_link": link,
+            "gpu_launches": r32["launches"], "device_bytes": r32["device_bytes"],
             "clocks": sampler.summary(),
-            "fp64": {"value": results["fp64"]["value"], "ms_per_step": results["fp64"]["ms_per_step"],
-                     "steps": results["fp64"]["steps"], "dtype": "f64",
-                     "roofline": results["fp64"]["roofline"],
-                     "fp32_over_fp64": r32["value"] / results["fp64"]["value"]},
-            "van_leer": vl, "adjoint": adj, "groups": grp, "thermal": thm}
+            "fp32_float_quartic": {
+                "value": head["fp32_float_quartic"]["value"],
+                "ms_per_step": head["fp32_float_quartic"]["ms_per_step"],
+                "frac": head["fp32_float_quartic"]["roofline"]["frac"],
+                "note": "the FP32 state with float_quartic = 1 (temperature solved in float in "
+                        "every lane); the headline solves it in double"},
+            "fp64": {"value": r64["value"], "ms_per_step": r64["ms_per_step"],
+                     "steps": r64["steps"], "dtype": "f64", "launches": r64["launches"],
+                     "device_bytes": r64["device_bytes"], "roofline": r64["roofline"],
+                     "fp32_over_fp64": r32["value"] / r64["value"]},
+            "shadows": extras}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -164,7 +164,14 @@ typedef enum { RT_FIRST_ORDER = 0, RT_VAN_LEER = 1 } rt_integrator;
  * then unused; otherwise T_ref > 0).  rt_adjoint_step refuses beta != 0.
  * plain_launches = 0 (the default) lets rt_run / rt_launch replay a CUDA
  * graph of RT_GRAPH_STEPS steps captured on the state's stream (see rt_run);
- * 1 launches every kernel from the host.  Both give identical results. */
+ * 1 launches every kernel from the host.  Both give identical results.
+ * float_quartic (RT_FP32 states only, ignored for RT_FP64): 0, the default,
+ * solves the gas temperature equation of Eq. (com rad thermal disc) in
+ * double -- its coefficients formed in double from the float angular sums,
+ * Newton in double, one GPU lane per cell -- as the precision split of
+ * RT_FP32 states says; 1 solves it in float in every lane of the cell (no
+ * block barrier, faster; coefficients outside float range still take the
+ * double solve), so the temperature carries float rounding. */
 typedef struct {
   double cbar, c, a_rad, gamma_gas, r_gas, cfl;
   int32_t precision;       /* rt_precision */
@@ -174,6 +181,8 @@ typedef struct {
   int32_t gcl;             /* 0 or 1, see above */
   int32_t plain_launches;  /* 0: multi-step calls replay captured graphs; 1: plain launches */
   double beta_P, beta_J, T_ref; /* see above */
+  int32_t float_quartic;   /* RT_FP32 only: 0 temperature solve in double, 1 in float */
+  int32_t reserved;        /* must be 0 */
 } rt_params;
 
 /* Validates and copies the mesh to the device, orders cells for locality,

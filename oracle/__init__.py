@@ -90,6 +90,8 @@ def lib():
         L.orc_transport_recon.argtypes = [P, d, vp, vp, vp, vp]
         L.orc_step_vl.argtypes = [P, d, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(i)]
         L.orc_step_vl.restype = i
+        L.orc_set_threads.argtypes = [i]
+        L.orc_set_threads.restype = i
         _lib = L
     return _lib
 
@@ -115,6 +117,12 @@ def newton_power(alpha, k, beta, g, max_iter=64):
     st = lib().orc_newton_power(float(alpha), float(k), float(beta), float(g), int(max_iter),
                                 ctypes.byref(T), ctypes.byref(it))
     return st, T.value, it.value
+
+
+def set_threads(n):
+    """OpenMP threads of the oracle's loops from now on (n > 0); returns the
+    number in effect (n <= 0 only queries it)."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def ferrari(alpha, beta, g):

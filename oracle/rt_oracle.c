@@ -29,6 +29,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <omp.h>
+
 #define ORC_OK 0
 #define ORC_ERR_ARG (-1)
 #define ORC_ERR_NONCONV (-6)
@@ -1082,4 +1084,12 @@ int orc_step_vl(const orc_problem *p, double dt, double *I, double *work, double
   orc_gradient(p, Ih, 1, grad);
   orc_transport_recon(p, dt, I, Ih, grad, work);
   return orc_source(p, dt, work, I, e, m, ext, max_iters);
+}
+
+/* Threads of the OpenMP loops from now on (n > 0); returns the count in
+ * effect.  Lets a caller time the oracle on one core and on all of them in
+ * one process. */
+int orc_set_threads(int n) {
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
 }

@@ -46,7 +46,8 @@ class Params(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("newton_max_iter", ctypes.c_int32), ("integrator", ctypes.c_int32),
                 ("boost", ctypes.c_int32), ("gcl", ctypes.c_int32), ("plain_launches", ctypes.c_int32),
-                ("beta_P", ctypes.c_double), ("beta_J", ctypes.c_double), ("T_ref", ctypes.c_double)]
+                ("beta_P", ctypes.c_double), ("beta_J", ctypes.c_double), ("T_ref", ctypes.c_double),
+                ("float_quartic", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None

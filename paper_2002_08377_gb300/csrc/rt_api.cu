@@ -103,7 +103,11 @@ template <typename R> void fill_geometry(rt_state *s, const rt_mesh_desc *m,
   slot.resize(ptr[N]);
   wface.assign(sizeof(R) == 8 ? ptr[N] : 0, 0.0);
   inv_vol.resize(N);
-  const double cbar = s->params.cbar;
+  // float slots of a double state (the positivity screen's temporary copy)
+  // are scaled by the power of two screen_scale so that they fit float at
+  // any unit scale; a float state's own slots are unscaled (screen_scale 1)
+  const double cbar = s->params.cbar * (sizeof(R) == 4 ? s->screen_scale : 1.0);
+  const double wsc = sizeof(R) == 4 ? s->screen_scale : 1.0;
   for (int64_t ic = 0; ic < N; ++ic) {
     const int64_t c = s->cell_of[ic];
     inv_vol[ic] = (R)(1.0 / m->cell_volume[c]);
@@ -124,7 +128,7 @@ template <typename R> void fill_geometry(rt_state *s, const rt_mesh_desc *m,
       // both sides hold exact negatives of the same rounded numbers
       if (sizeof(R) == 4) {
         R sx = (R)(cbar * A * n[0]), sy = (R)(cbar * A * n[1]), sz = (R)(cbar * A * n[2]);
-        R ww = (R)(A * wn);
+        R ww = (R)(wsc * A * wn);
         if (sg < 0) {
           sx = -sx;
           sy = -sy;
@@ -331,6 +335,40 @@ int check_mesh(rt_state *s, const rt_mesh_desc *m) {
   return RT_OK;
 }
 
+// Float states store cbar A n_f, A w . n_f and 1/V in float and multiply
+// them by float intensities: each stored magnitude and its reciprocal must
+// be a normal float (|x| in [2^-125, 2^125], or exactly 0 for a face
+// product), else the step would overflow or flush to zero without an error.
+bool float_normal(double x) { return x >= 0x1p-125 && x <= 0x1p125; }
+
+int check_float_range(rt_state *s, const rt_mesh_desc *m, double cbar) {
+  char buf[200];
+  for (int64_t f = 0; f < m->n_faces; ++f) {
+    const double A = m->face_area[f], ca = cbar * A;
+    double wn = 0.0;
+    if (m->face_w) {
+      const double *w = m->face_w + 3 * f;
+      wn = std::fabs(A * std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]));
+    }
+    if ((ca != 0.0 && !float_normal(ca)) || (wn != 0.0 && !float_normal(wn))) {
+      snprintf(buf, sizeof buf,
+               "RT_FP32: face %lld has cbar A = %.3g or A |w| = %.3g outside float range "
+               "(2^-125 .. 2^125); rescale the units or use RT_FP64",
+               (long long)f, ca, wn);
+      return fail(s, RT_ERR_ARG, buf);
+    }
+  }
+  for (int64_t c = 0; c < m->n_cells; ++c)
+    if (!float_normal(m->cell_volume[c])) {
+      snprintf(buf, sizeof buf,
+               "RT_FP32: cell %lld has volume %.3g outside float range (2^-125 .. 2^125); "
+               "rescale the units or use RT_FP64",
+               (long long)c, m->cell_volume[c]);
+      return fail(s, RT_ERR_ARG, buf);
+    }
+  return RT_OK;
+}
+
 int sync_status(rt_state *s) {
   RT_CUDA(s, cudaStreamSynchronize(s->stream));
   unsigned st = 0;
@@ -417,6 +455,7 @@ int rt_create(const rt_mesh_desc *m_in, const rt_params *p, void *stream, rt_sta
       (p->gcl && p->integrator != RT_FIRST_ORDER) || !std::isfinite(p->beta_P) ||
       !std::isfinite(p->beta_J) || ((p->beta_P != 0 || p->beta_J != 0) && !(p->T_ref > 0)) ||
       !(p->beta_P >= -3.0) || (p->plain_launches != 0 && p->plain_launches != 1) ||
+      (p->float_quartic != 0 && p->float_quartic != 1) || p->reserved != 0 ||
       (p->integrator == RT_VAN_LEER && !m->face_offset))
     return bail(RT_ERR_ARG);
   s->params = *p;
@@ -425,7 +464,8 @@ int rt_create(const rt_mesh_desc *m_in, const rt_params *p, void *stream, rt_sta
   s->precision = p->precision;
   s->rsize = p->precision == RT_FP32 ? 4 : 8;
   s->stream = (cudaStream_t)stream;
-  if ((st = check_mesh(s, m)) != RT_OK) {
+  if ((st = check_mesh(s, m)) != RT_OK ||
+      (p->precision == RT_FP32 && (st = check_float_range(s, m, p->cbar)) != RT_OK)) {
     // keep the message: callers of a failed create cannot query it, so print it
     fprintf(stderr, "rt_create: %s\n", s->err.c_str());
     return bail(st);
@@ -549,6 +589,18 @@ int rt_create(const rt_mesh_desc *m_in, const rt_params *p, void *stream, rt_sta
   // candidates
   rt::SlotF *fslot = reinterpret_cast<rt::SlotF *>(s->d_slot);
   if (s->precision == RT_FP64) {
+    // a power of two that brings the largest cbar A and A |w| near 1, so
+    // that the float screen neither overflows nor flushes at physical units
+    double big = 0.0;
+    for (int64_t f = 0; f < m->n_faces; ++f) {
+      double v = p->cbar * m->face_area[f];
+      if (m->face_w) {
+        const double *w = m->face_w + 3 * f;
+        v = std::max(v, m->face_area[f] * std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]));
+      }
+      big = std::max(big, v);
+    }
+    s->screen_scale = big > 0.0 ? std::ldexp(1.0, -std::ilogb(big)) : 1.0;
     std::vector<int64_t> p2;
     std::vector<int32_t> n2;
     std::vector<rt::SlotF> sf;
@@ -612,6 +664,23 @@ int rt_set_gas(rt_state *s, const double *rho, const double *e, const double *m,
     }
     if (!ok) return fail(s, RT_ERR_ARG, "rt_set_gas: rho must be > 0, opacities >= 0, all finite");
     const double rcv = rho[c] * s->params.r_gas / (s->params.gamma_gas - 1.0);
+    if (s->precision == RT_FP32) {
+      // float copies of rho kappa and rho c_v, and the float frame velocity
+      // and internal energy, must not overflow
+      bool fit = std::fabs(rcv) <= 0x1p125 && std::fabs(e[c]) <= 0x1p125 &&
+                 std::fabs(m[3 * c] / rho[c]) <= 0x1p125 &&
+                 std::fabs(m[3 * c + 1] / rho[c]) <= 0x1p125 &&
+                 std::fabs(m[3 * c + 2] / rho[c]) <= 0x1p125;
+      for (int j = 0; j < G; ++j) {
+        const int64_t k = c * G + j;
+        fit = fit && rho[c] * kP[k] <= 0x1p125 && rho[c] * kJ[k] <= 0x1p125 &&
+              rho[c] * kS[k] <= 0x1p125;
+      }
+      if (!fit)
+        return fail(s, RT_ERR_ARG,
+                    "rt_set_gas: RT_FP32 state: rho kappa, rho c_v, e or v outside float range "
+                    "(|x| <= 2^125); rescale the units or use RT_FP64");
+    }
     const int64_t c0 = c * G;  // the grey record holds group 0's opacities
     gs[ic] = {rho[c], rho[c] * kP[c0], rho[c] * kJ[c0], rho[c] * kS[c0], 1.0 / rho[c], rcv,
               (float)(rho[c] * kP[c0]), (float)(rho[c] * kJ[c0]), (float)(rho[c] * kS[c0]),

@@ -95,12 +95,14 @@ __global__ void positivity_screen_kernel(const int64_t *__restrict__ ptr,
                                          const double *__restrict__ wface,
                                          const double *__restrict__ vol,
                                          const double *__restrict__ dir, int64_t n, int A, int mode,
-                                         unsigned *kf, unsigned long long *kmax, float *kcell) {
+                                         double inv_scale, unsigned *kf,
+                                         unsigned long long *kmax, float *kcell) {
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   float best = 0.0f, braw = 0.0f;  // max over angles of sum / V and of sum
   const float cut = mode == 1 ? __uint_as_float(*kf) * (1.0f - 1e-4f) : 0.0f;
   if (row < n) {
-    const float iv = (float)(1.0 / vol[row]);
+    // fslot holds u scaled by a power of two; 1/V is scaled back by it
+    const float iv = (float)(inv_scale / vol[row]);
     for (int a = threadIdx.x % 32; a < A; a += 32) {
       const float x = (float)dir[3 * a], y = (float)dir[3 * a + 1], z = (float)dir[3 * a + 2];
       float sum = 0.0f;
@@ -346,11 +348,11 @@ cudaError_t launch_positivity(rt_state *s, const SlotF *fslot, double *d_kmax, f
     if (s->precision == RT_FP32)
       positivity_screen_kernel<float><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
           s->d_ptr, fslot, (const SlotF *)s->d_slot, s->d_wface, s->d_volume, s->d_dir64,
-          s->n_cells, s->n_angles, mode, kf, km, kcell);
+          s->n_cells, s->n_angles, mode, 1.0 / s->screen_scale, kf, km, kcell);
     else
       positivity_screen_kernel<double><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
           s->d_ptr, fslot, (const SlotD *)s->d_slot, s->d_wface, s->d_volume, s->d_dir64,
-          s->n_cells, s->n_angles, mode, kf, km, kcell);
+          s->n_cells, s->n_angles, mode, 1.0 / s->screen_scale, kf, km, kcell);
     s->launches++;
   }
   return cudaGetLastError();

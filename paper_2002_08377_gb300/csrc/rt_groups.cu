@@ -66,6 +66,7 @@ template <typename R> struct GroupArgs {
   double dt, cbar, a_rad, k_dcr, k_alpha, k_g, k_fe, k_fm;
   R dt_cbar_r, inv_c_r;
   int newton_max_iter;
+  int float_quartic;  // float states: 1 solves the temperature equation in float
   unsigned *status;
   unsigned long long *bad_cell;
   // float states (tile kernel): float copies of the group opacities and of
@@ -277,9 +278,10 @@ __global__ void __launch_bounds__(kThreads) group_source_kernel(const GroupArgs<
     const double eint = d.e - 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * gs.inv_rho;
     unsigned bad = 0;
     bool done = false;
-    if constexpr (sizeof(R) == 4) {
-      // float states: the chain in float, as the grey float step solves its
-      // quartic; repeated in double if a result is not finite
+    if (sizeof(R) == 4 && a.float_quartic) {
+      // float states with float_quartic: the chain in float, as the grey
+      // float step then solves its quartic; repeated in double if a result
+      // is not finite
       float q[kMaxGroups];
       const int st = group_chain<float>(a, cl, sums[lane], eint, gs.rcv, q);
       if (st >= 0) {
@@ -475,8 +477,10 @@ __global__ void __launch_bounds__(step::NT, sizeof(R) == 4 && M::PPT <= 6 ? 3 : 
   unsigned bad = 0;
 #pragma unroll
   for (int g = 0; g < NG; ++g) q[g] = R(0);
-  if constexpr (sizeof(R) == 4) {
-    if (kind == RT_CELL_INTERIOR) {
+  bool lane_solve = false;  // float states with float_quartic: in float, in every lane
+  if constexpr (sizeof(R) == 4) lane_solve = a.float_quartic != 0;
+  if (lane_solve) {
+    if constexpr (sizeof(R) == 4) if (kind == RT_CELL_INTERIOR) {
       float4 kf[NG];
 #pragma unroll
       for (int g = 0; g < NG; ++g)
@@ -705,6 +709,7 @@ template <typename R> cudaError_t launch(rt_state *s, double dt, void *Is) {
   a.dt_cbar_r = R(dt * s->params.cbar);
   a.inv_c_r = R(1.0 / s->params.c);
   a.newton_max_iter = s->params.newton_max_iter;
+  a.float_quartic = s->params.float_quartic;
   a.status = s->d_status;
   a.bad_cell = s->d_bad;
   a.kapgf = s->d_kapgf;

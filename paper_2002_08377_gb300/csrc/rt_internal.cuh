@@ -87,6 +87,7 @@ template <typename R> struct StepArgs {
   R dt_r, dt_cbar_r, inv_c_r;
   float k_dcr_f, k_alpha_f, k_g_f, a_rad_4pi_f;  // float copies for the float quartic
   int32_t newton_max_iter;
+  int32_t float_quartic;    // float states: 1 solves the quartic in float in every lane
   int32_t src_only;         // 1: I_in holds I* already (no transport)
   int32_t commit;           // 0: the gas update is discarded (van Leer stage 1)
   int32_t boost;            // 1: Gamma = gamma (1 -+ v.n/c) with the Lorentz factor gamma
@@ -94,6 +95,7 @@ template <typename R> struct StepArgs {
   // per-cell max_a sum_f max(u, 0), the current volumes and their inverses
   const double *gcl_rate;
   const float *gcl_kv;
+  double gcl_kv_unit;       // gcl_kv times this is max_a sum_f max(u, 0)
   double *volume;
   R *inv_vol_w;
   // temperature-dependent opacities (0, 0: constant): kappa_P (T/T_ref)^beta_P
@@ -155,6 +157,10 @@ struct rt_state {
   uint64_t graph_gen[2] = {0, 0};
   int64_t graph_launches[2] = {0, 0};
   size_t device_bytes = 0;
+  // power of two by which the positivity screen's float slots are scaled
+  // (double states: brings cbar A near 1; float states: 1); the per-cell
+  // factors in d_gcl_kv are in those scaled units
+  double screen_scale = 1.0;
 
   // host copies needed for I/O
   std::vector<int64_t> cell_of;  // internal -> caller

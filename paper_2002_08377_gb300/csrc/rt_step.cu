@@ -24,9 +24,10 @@
 //   A  all threads: transport over the cell's faces in slot order (no
 //      atomics, deterministic), comoving weights and the angular sums of
 //      Eq. (Jcom); each cell's 8 lanes reduce with shuffles;
-//   B  the gas temperature quartic: float states solve it in float in all
-//      8 lanes of the cell (no barrier); double states in double with one
-//      lane per cell in the first CPB / 32 warps, between two block barriers;
+//   B  the gas temperature quartic, in double with one lane per cell in the
+//      first CPB / 32 warps, between two block barriers (double states, and
+//      float states by default); float states with float_quartic = 1 solve
+//      it in float in all 8 lanes of the cell instead (no barrier);
 //   C  all threads: new intensities, store, radiation change per cell;
 //   D  after a block barrier, one lane per cell (first CPB / 32 warps): gas energy /
 //      momentum (or tally) update in double (Eqs. gas1, gas2).
@@ -268,13 +269,20 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   // ---------------- phase B: temperature quartic
   R q = 0;           // dt cbar rho (kP B + kS J~) of an interior cell
   unsigned bad = 0;  // status bits of the cell
-  if constexpr (sizeof(R) == 4) {
-    // float states: every lane of the cell solves the cell's quartic in
-    // float (the sums are already in all 8 lanes), no block barrier
-    if (kind == RT_CELL_INTERIOR)
-      q = source_q_float(a, c, fkP, fkJ, fkS, fcv, eint, sI, sG, s1, bad);
+  const GasStatic *gs_s = STAGED ? stage.gas->gs : gas->gs;
+  const GasDyn *gd_s = STAGED ? stage.gas->gd : gas->gd;
+  bool lane_solve = false;  // float states with float_quartic: in float, in every lane
+  if constexpr (sizeof(R) == 4) lane_solve = a.float_quartic != 0;
+  if (lane_solve) {
+    // every lane of the cell solves the cell's quartic in float (the sums
+    // are already in all 8 lanes), no block barrier
+    if constexpr (sizeof(R) == 4)
+      if (kind == RT_CELL_INTERIOR)
+        q = source_q_float(a, c, fkP, fkJ, fkS, fcv, eint, sI, sG, s1, bad);
   } else {
-    // double states: one lane per cell, so the FP64 work is issued
+    // the quartic in double (double states, and float states by default:
+    // their angular sums are float partials, the solve and its
+    // coefficients double), one lane per cell, so the FP64 work is issued
     // by one warp for 32 cells
     if (sub == 0) {
       sh.sI[lc] = sI;
@@ -287,7 +295,7 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
       R ql = 0;
       unsigned bl = 0;
       if (cl < a.n_cells && a.kind[cl] == RT_CELL_INTERIOR)
-        ql = R(source_q(a, gas->gs[lp], gas->gd[lp], (double)sh.sI[lp], (double)sh.sG[lp],
+        ql = R(source_q(a, gs_s[lp], gd_s[lp], (double)sh.sI[lp], (double)sh.sG[lp],
                         (double)sh.s1[lp], bl));
       sh.q[lp] = ql;
       sh.bad[lp] = bl;
@@ -384,8 +392,6 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   __syncthreads();
 
   // ---------------- phase D: gas exchange (Eqs. gas1, gas2), one lane per cell
-  const GasStatic *gs_s = STAGED ? stage.gas->gs : gas->gs;
-  const GasDyn *gd_s = STAGED ? stage.gas->gd : gas->gd;
   if (lpc && cl < a.n_cells) {
     // dE_gas = (c/cbar) 4 pi sum w dI, d(rho v) = (4 pi c sum w n dI) / (c cbar)
     const double dE = a.k_fe * (double)sh.dE[lp];
@@ -423,7 +429,7 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
       // this step needed V^n >= dt max_a sum_f max(u, 0) (the float factor
       // carries a ~1e-6 relative error, inside the margin)
       const double V = a.volume[cl];
-      if (a.dt * (double)a.gcl_kv[cl] > V * (1.0 + 1e-5)) bad |= ST_CFL;
+      if (a.dt * ((double)a.gcl_kv[cl] * a.gcl_kv_unit) > V * (1.0 + 1e-5)) bad |= ST_CFL;
       const double V1 = __dadd_rn(V, __dmul_rn(a.dt, a.gcl_rate[cl]));
       a.volume[cl] = V1;
       a.inv_vol_w[cl] = R(1.0 / V1);
@@ -493,6 +499,7 @@ cudaError_t launch_t(rt_state *s, double dt, const StepIO &io) {
   a.boost = s->params.boost;
   a.gcl_rate = s->d_gcl_rate;
   a.gcl_kv = s->d_gcl_kv;
+  a.gcl_kv_unit = 1.0 / s->screen_scale;
   a.volume = s->d_volume;
   a.inv_vol_w = reinterpret_cast<R *>(s->d_inv_vol);
   a.beta_P = s->params.beta_P;
@@ -519,6 +526,7 @@ cudaError_t launch_t(rt_state *s, double dt, const StepIO &io) {
   a.k_fe = s->params.c / s->params.cbar * 4.0 * kPi;
   a.k_fm = 4.0 * kPi / s->params.cbar;
   a.newton_max_iter = s->params.newton_max_iter;
+  a.float_quartic = s->params.float_quartic;
   a.k_dcr_f = (float)a.k_dcr;
   a.k_alpha_f = (float)a.k_alpha;
   a.k_g_f = (float)a.k_g;

@@ -43,13 +43,17 @@ __device__ __forceinline__ double2 psub(double2 a, double2 b) {
 // relative error below 2^-22, inside the float state's error budget; the
 // arguments are Gamma^k (1 + x Gamma) and 1 + dt cbar rho kappa S_G, normal
 // floats, so flushing subnormals changes nothing).  Double: that estimate
-// refined by two Newton steps (about 1 ulp).
+// refined by two Newton steps r <- r (2 - x r) (about 1 ulp) where x and
+// 1/x are normal floats (|x| in [2^-125, 2^125]); any other x (physical
+// units make dt/V or cbar A far from 1) takes the IEEE double division.
 __device__ __forceinline__ float rcp(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
 __device__ __forceinline__ double rcp(double x) {
+  const double ax = fabs(x);
+  if (!(ax >= 0x1p-125 && ax <= 0x1p125)) return 1.0 / x;
   double r = (double)rcp((float)x);
   r = fma(r, fma(-x, r, 1.0), r);
   r = fma(r, fma(-x, r, 1.0), r);

@@ -24,16 +24,18 @@ class RTSolver:
     """One mesh + angle set + gas state on the current CUDA device.
 
     precision: "fp32" (float intensities/transport, double quartic and
-    exchange) or "fp64".  integrator: 0 first-order upwind step, 1 van Leer
-    step with limited linear reconstruction (needs mesh.face_offset()).
-    plain_launches: 1 turns off the CUDA-graph replay of run() / launch()
-    (same kernels, same results; see rt_run in include/rt.h).
+    exchange) or "fp64".  float_quartic: 1 makes an fp32 state solve the
+    temperature quartic in float instead (faster, float-rounded T).
+    integrator: 0 first-order upwind step, 1 van Leer step with limited
+    linear reconstruction (needs mesh.face_offset()).  plain_launches: 1
+    turns off the CUDA-graph replay of run() / launch() (same kernels, same
+    results; see rt_run in include/rt.h).
     """
 
     def __init__(self, mesh, dirs, weights, *, cbar, c, a_rad=1.0, gamma_gas=5.0 / 3.0,
                  r_gas=1.0, cfl=0.3, precision="fp32", newton_max_iter=64, integrator=0, boost=0, gcl=0,
                  beta_P=0.0, beta_J=0.0, T_ref=1.0, n_groups=1, group_w=None,
-                 plain_launches=0, stream=None):
+                 plain_launches=0, float_quartic=0, stream=None):
         if torch is None or not torch.cuda.is_available():
             raise RuntimeError("RTSolver needs a CUDA device (no CPU fallback exists)")
         self.lib = capi.load()
@@ -75,8 +77,7 @@ class RTSolver:
         pr = capi.Params(cbar, c, a_rad, gamma_gas, r_gas, cfl,
                          capi.RT_FP32 if precision == "fp32" else capi.RT_FP64, newton_max_iter,
                          int(integrator), int(boost), int(gcl), int(plain_launches), float(beta_P),
-                         float(beta_J),
-                         float(T_ref))
+                         float(beta_J), float(T_ref), int(float_quartic), 0)
         st = ctypes.c_void_p()
         code = self.lib.rt_create(ctypes.byref(md), ctypes.byref(pr),
                                   ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(st))

@@ -117,8 +117,28 @@ def test_create_rejects_bad_params(lib):
 
     for kw in ({"plain_launches": 2}, {"boost": -1}, {"gcl": 2}, {"integrator": 5},
                {"gcl": 1, "integrator": capi.RT_VAN_LEER}, {"beta_P": float("nan")},
-               {"beta_P": -3.5}, {"beta_J": 1.0, "T_ref": 0.0}, {"precision": 7}, {"cfl": 0.0}):
+               {"beta_P": -3.5}, {"beta_J": 1.0, "T_ref": 0.0}, {"precision": 7}, {"cfl": 0.0},
+               {"float_quartic": 2}, {"reserved": 1}):
         assert code(**kw) == capi.RT_ERR_ARG, kw
+
+
+def test_fp32_state_outside_float_range_refused(lib):
+    """A float state of a mesh in physical units whose cbar A (or volume)
+    leaves float range is refused by rt_create with RT_ERR_ARG before any
+    device work; the same mesh is accepted up to that check in FP64 (it then
+    needs a device, absent here)."""
+    mesh = build_mesh((3, 3, 3), seed=1)
+    dirs, w = level_symmetric(4)
+    L = 3.0856775814913673e18  # one parsec in cm
+    for arr, k in (("cell_volume", 3), ("face_area", 2)):
+        setattr(mesh, arr, getattr(mesh, arr) * L ** k)
+    keep = []
+    d = _desc(mesh, dirs, w, keep)
+    pr = capi.Params(2.99792458e10, 2.99792458e10, 7.565733e-15, 5.0 / 3.0, 8.25e7, 0.3,
+                     capi.RT_FP32, 64)
+    st = ctypes.c_void_p()
+    assert lib.rt_create(ctypes.byref(d), ctypes.byref(pr), None, ctypes.byref(st)) == capi.RT_ERR_ARG
+    assert not st.value
 
 
 def test_null_arguments(lib):

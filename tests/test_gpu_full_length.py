@@ -1,0 +1,133 @@
+"""GPU parity at full size and full length on the five workloads.
+
+Each workload runs at the size and step count its setup gives (the
+linear-wave box at 256^3 runs the first steps only: one oracle step of it
+takes about ten seconds of host time), once on the FP64 oracle and once per
+GPU state from the same seeded inputs, in the launch configuration the
+benchmark times (multi-step runs replaying the captured step graphs).  Every
+cell and angle is compared:
+
+* RT_FP64: every intensity to a relative 1e-12, the gas energy likewise;
+* RT_FP32: L1 of E_r to a relative 1e-5, the gas energy in L1 likewise, and
+  the total energy (gas + (c/cbar) radiation + boundary / emitter tallies)
+  conserved to a relative 1e-6 over the run.
+
+RT_FP32 states run with the temperature quartic solved in double (the
+default) and, on the stiff dynamic-diffusion box and the linear-wave box,
+with float_quartic = 1 as well.  With RT_ERROR_REPORT set to a file name,
+every test appends the measured errors to that file as one JSON line
+(max per-intensity error, L1 of E_r and of e, the energy drift of both
+sides, the per-cell gas temperature error).
+"""
+import functools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_08377_gb300 import build as rtbuild
+from paper_2002_08377_gb300 import capi
+from paper_2002_08377_gb300.inputs import adjoint, diffusion, shadows, thermal, waves
+
+pytestmark = pytest.mark.gpu
+
+FP64_REL = 1e-12
+FP32_L1 = 1e-5
+FP32_ENERGY = 1e-6
+
+# workload -> (builder, steps)
+CONFIGS = {
+    "thermal": (thermal, 100),
+    "shadows": (shadows, 100),
+    "diffusion": (diffusion, 300),
+    "adjoint": (adjoint, 64),
+    "waves": (waves, 5),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    rtbuild.build()
+    capi.load()
+
+
+def report(**vals):
+    path = os.environ.get("RT_ERROR_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(vals) + "\n")
+
+
+def _mem_ok(need):
+    with open("/proc/meminfo") as f:
+        for line in f:
+            if line.startswith("MemAvailable:"):
+                return (int(line.split()[1]) << 10) >= need
+    return True
+
+
+@functools.lru_cache(maxsize=1)
+def oracle_run(name):
+    """The oracle's run of a workload: (problem, oracle after the run, dt,
+    totals before the run).  One workload is kept at a time."""
+    build, steps = CONFIGS[name]
+    prob = build()
+    o = oracle.Oracle(prob)
+    t0 = o.totals()
+    dt = o.cfl_dt()
+    assert o.run(steps, dt) == oracle.ORC_OK
+    return prob, o, dt, t0
+
+
+def temperature(prob, e, m):
+    kin = 0.5 * np.sum(m ** 2, axis=1) / prob.rho
+    return (e - kin) * (prob.gamma_gas - 1.0) / (prob.rho * prob.r_gas)
+
+
+# the cases of one workload are adjacent, so that its oracle run is reused
+CASES = [(n, p, fq) for n in CONFIGS
+         for p, fq in (("fp64", 0), ("fp32", 0)) + ((("fp32", 1),) if n in ("diffusion", "waves") else ())]
+
+
+@pytest.mark.parametrize("name,precision,float_quartic", CASES,
+                         ids=[f"{n}-{p}{'-float_quartic' if f else ''}" for n, p, f in CASES])
+def test_full_size_full_length(name, precision, float_quartic):
+    if name == "waves" and not _mem_ok(96 << 30):
+        pytest.skip("the 256^3 workload's oracle state needs about 96 GB of host memory")
+    from paper_2002_08377_gb300.solver import RTSolver
+    prob, o, dt, t0_o = oracle_run(name)
+    steps = CONFIGS[name][1]
+    g = RTSolver.from_problem(prob, precision, float_quartic=float_quartic)
+    t0_g = g.totals()
+    g.run(steps, dt)
+    I = g.get_intensity()
+    e, m, x = g.gas()
+    t1_g = g.totals()
+    g.close()
+    t1_o = o.totals()
+    E_o, _, _ = o.moments()
+    w4 = 4 * np.pi * prob.weights
+    E_g = np.asarray(I, np.float64) @ w4
+    l1_E = float(np.sum(np.abs(E_g - E_o)) / np.sum(np.abs(E_o)))
+    l1_e = float(np.sum(np.abs(e - o.e)) / np.sum(np.abs(o.e)))
+    den = np.maximum(np.abs(o.I), 1e-300)
+    max_I = float(np.max(np.abs(np.asarray(I, np.float64) - o.I) / den))
+    del den
+    drift_g = abs(t1_g[12] - t0_g[12]) / abs(t0_g[12])
+    drift_o = abs(t1_o[12] - t0_o[12]) / abs(t0_o[12])
+    interior = prob.kind == 0
+    T_o, T_g = temperature(prob, o.e, o.m), temperature(prob, e, m)
+    T_err = float(np.max(np.abs(T_g - T_o)[interior] / T_o[interior])) if interior.any() else 0.0
+    report(workload=name, precision=precision, float_quartic=float_quartic, cells=prob.n_cells,
+           angles=prob.n_angles, steps=steps, max_rel_intensity=max_I, l1_E_r=l1_E, l1_e=l1_e,
+           energy_drift_gpu=drift_g, energy_drift_oracle=drift_o, max_rel_T=T_err)
+    if precision == "fp64":
+        assert max_I < FP64_REL, max_I
+        assert float(np.max(np.abs(e - o.e) / np.abs(o.e))) < FP64_REL
+        assert drift_g < 1e-12
+    else:
+        assert l1_E < FP32_L1, l1_E
+        assert l1_e < FP32_L1, l1_e
+        assert drift_g < FP32_ENERGY, drift_g

@@ -92,6 +92,12 @@ def lib():
         L.orc_step_vl.restype = i
         L.orc_set_threads.argtypes = [i]
         L.orc_set_threads.restype = i
+        L.orc_hllc_flux.argtypes = [d, vp, vp, vp, vp]
+        L.orc_hllc_flux.restype = i
+        L.orc_hydro_dt.argtypes = [P, vp, vp, vp, d]
+        L.orc_hydro_dt.restype = d
+        L.orc_hydro_step.argtypes = [P, d, i, vp, vp, vp, vp]
+        L.orc_hydro_step.restype = i
         _lib = L
     return _lib
 
@@ -123,6 +129,18 @@ def set_threads(n):
     """OpenMP threads of the oracle's loops from now on (n > 0); returns the
     number in effect (n <= 0 only queries it)."""
     return int(lib().orc_set_threads(int(n)))
+
+
+def hllc_flux(gamma, WL, WR, n):
+    """HLLC flux per unit area of (rho, m, e) through a face with unit normal
+    n, primitive states W = (rho, vx, vy, vz, P) on the two sides."""
+    WL, WR, n = _f64(WL), _f64(WR), _f64(n)
+    F = np.empty(5)
+    st = lib().orc_hllc_flux(float(gamma), WL.ctypes.data, WR.ctypes.data, n.ctypes.data,
+                             F.ctypes.data)
+    if st != 0:
+        raise ValueError("non-positive density or pressure")
+    return F
 
 
 def ferrari(alpha, beta, g):
@@ -174,7 +192,10 @@ class Oracle:
         p.wt = arr("wt", wts)
         p.cbar, p.c, p.a_rad = prob.cbar, prob.c, prob.a_rad
         p.gamma_gas, p.r_gas = prob.gamma_gas, prob.r_gas
-        p.rho = arr("rho", prob.rho)
+        # the oracle's own copy: it evolves with the hydro step (the radiation reads it)
+        self.rho = np.array(prob.rho, dtype=np.float64, copy=True)
+        keep["rho"] = self.rho
+        p.rho = self.rho.ctypes.data
         p.kappa_P = arr("kP", prob.kappa_P)
         p.kappa_J = arr("kJ", prob.kappa_J)
         p.kappa_s = arr("kS", prob.kappa_s)
@@ -258,6 +279,37 @@ class Oracle:
     def run(self, n_steps, dt):
         for _ in range(int(n_steps)):
             st = self.step(dt)
+            if st != ORC_OK:
+                return st
+        return ORC_OK
+
+    # -- hydrodynamics ---------------------------------------------------------
+    def hydro_dt(self, cfl=None):
+        """Courant step of the gas: cfl * min V^(1/3) / (|v| + sound speed)."""
+        cfl = self.prob.cfl if cfl is None else cfl
+        return lib().orc_hydro_dt(ctypes.byref(self.p), self.rho.ctypes.data, self.m.ctypes.data,
+                                  self.e.ctypes.data, float(cfl))
+
+    def hydro_step(self, dt, order=2):
+        """One hydro step of (rho, m, e) in place (HLLC fluxes; order 2: the
+        van Leer step with limited linear reconstruction)."""
+        if self.p.gcl:
+            raise ValueError("the hydro step is built for a static mesh")
+        if not hasattr(self, "_hwork"):
+            self._hwork = np.empty(36 * self.N + 5 * self.p.n_faces)
+        st = lib().orc_hydro_step(ctypes.byref(self.p), float(dt), int(order),
+                                  self.rho.ctypes.data, self.m.ctypes.data, self.e.ctypes.data,
+                                  self._hwork.ctypes.data)
+        if st != 0:
+            raise ValueError("the hydro step produced a non-positive density or pressure")
+
+    def radhydro_step(self, dt, n_sub=1, order=2):
+        """One radiation-hydrodynamics step: the hydro step over dt, then n_sub
+        radiation steps (transport + implicit source with the updated gas) of
+        dt / n_sub each."""
+        self.hydro_step(dt, order)
+        for _ in range(int(n_sub)):
+            st = self.step(dt / n_sub)
             if st != ORC_OK:
                 return st
         return ORC_OK

@@ -203,14 +203,17 @@ static void cell_moments(const orc_problem *p, const double *Ic, double *E, doub
 
 /* Energy and momentum the radiation of one cell loses in the source step,
  * E^n - E^{n+1} and F^n - F^{n+1}.  The moments are linear in I, so these
- * are 4 pi sum_a w_a (I_a - I'_a) and 4 pi c sum_a w_a n_a (I_a - I'_a);
- * summing the per-angle differences keeps the digits that subtracting the
- * two (nearly equal) sums would cancel. */
-static void cell_moment_change(const orc_problem *p, const double *I, const double *In,
-                               double *dE, double *dF) {
+ * are 4 pi sum_a w_a dI_a and 4 pi c sum_a w_a n_a dI_a with dI_a = I_a -
+ * I'_a, the change of each intensity.  The callers evaluate dI_a as the
+ * source term itself (the right side of the discretised equation times dt,
+ * see source_interior), not as the difference of the two intensities: where
+ * a cell is optically thin the change is a small fraction of I_a, and the
+ * difference of two rounded intensities would carry a rounding error of
+ * I_a's size, not of the change's. */
+static void cell_moment_sum(const orc_problem *p, const double *dI, double *dE, double *dF) {
   double e = 0, fx = 0, fy = 0, fz = 0;
   for (int a = 0; a < p->n_angles; ++a) {
-    double wi = p->wt[a] * (I[a] - In[a]);
+    double wi = p->wt[a] * dI[a];
     e += wi;
     fx += wi * p->dir[3 * a];
     fy += wi * p->dir[3 * a + 1];
@@ -378,7 +381,10 @@ double orc_ferrari(double alpha, double beta, double g) {
  *  3. I~^{n+1} from Eq. (com radiative source disc), back to the lab frame;
  *  4. E^{n+1}, F^{n+1} and the gas exchange of Eqs. (gas1), (gas2):
  *        e += (c / cbar)(E^n - E^{n+1}),  rho v += (F^n - F^{n+1}) / (c cbar),
- *     with the differences summed angle by angle (cell_moment_change).
+ *     summed angle by angle over the changes dI_a = I_a - I'_a, each taken
+ *     from Eq. (com radiative source disc) as the implicit source term:
+ *        I~_a - I~'_a = (x_a I~_a - dt cbar Gamma_a rho (kP B + ks J~)) / (1 + x_a),
+ *     and dI_a = (I~_a - I~'_a) / Gamma_a^4 (cell_moment_sum).
  * The gas temperature is recomputed from the updated energy next step.
  * --------------------------------------------------------------------- */
 /* The Lorentz factor in Gamma_a = gamma (1 - v . n_a / c) (Sec. 2.3): 1 for
@@ -435,14 +441,17 @@ static int source_interior(const orc_problem *p, int64_t c, double dt, const dou
   if (st != ORC_OK) return st;
   double B = p->a_rad * T * T * T * T / (4.0 * M_PI);
   double J = (SI + dt * p->cbar * rho * kP * B * SG) / D;
+  double dI[A];
   for (int a = 0; a < A; ++a) {
     double xa = dt * p->cbar * rho * (kJ + kS) * G[a];
-    double Inew = (Ic[a] + dt * p->cbar * G[a] * rho * (kP * B + kS * J)) / (1.0 + xa);
+    double src = dt * p->cbar * G[a] * rho * (kP * B + kS * J);
+    double Inew = (Ic[a] + src) / (1.0 + xa);
     double G2 = G[a] * G[a];
     In[a] = Inew / (G2 * G2);
+    dI[a] = ((xa * Ic[a] - src) / (1.0 + xa)) / (G2 * G2);
   }
   double dE, dF[3];
-  cell_moment_change(p, Is, In, &dE, dF);
+  cell_moment_sum(p, dI, &dE, dF);
   *e += p->c / p->cbar * dE;
   for (int k = 0; k < 3; ++k) m[k] += dF[k] / (p->c * p->cbar);
   return ORC_OK;
@@ -507,18 +516,21 @@ static int source_interior_groups(const orc_problem *p, int64_t c, double dt, co
   }
   if (st != ORC_OK) return st;
   double B = p->a_rad * T * T * T * T / (4.0 * M_PI);
+  double dI[A];
   for (int j = 0; j < NG; ++j) {
     double J = (SI[j] + dt * p->cbar * rho * kP[j] * B * SG[j]) / D[j];
     for (int b = 0; b < Ag; ++b) {
       const int a = j * Ag + b;
       double xa = dt * p->cbar * rho * (kJ[j] + kS[j]) * G[a];
-      double Inew = (Ic[a] + dt * p->cbar * G[a] * rho * (kP[j] * B + kS[j] * J)) / (1.0 + xa);
+      double src = dt * p->cbar * G[a] * rho * (kP[j] * B + kS[j] * J);
+      double Inew = (Ic[a] + src) / (1.0 + xa);
       double G2 = G[a] * G[a];
       In[a] = Inew / (G2 * G2);
+      dI[a] = ((xa * Ic[a] - src) / (1.0 + xa)) / (G2 * G2);
     }
   }
   double dE, dF[3];
-  cell_moment_change(p, Is, In, &dE, dF);
+  cell_moment_sum(p, dI, &dE, dF);
   *e += p->c / p->cbar * dE;
   for (int k = 0; k < 3; ++k) m[k] += dF[k] / (p->c * p->cbar);
   return ORC_OK;
@@ -532,9 +544,12 @@ static void source_boundary(const orc_problem *p, int64_t c, double dt, const do
   const int A = p->n_angles;
   double f = (p->tau[c] <= dt) ? 1.0 : dt / p->tau[c];
   const double *I0 = p->I0 + (int64_t)p->bc_row[c] * A;
-  double dE, dF[3];
-  for (int a = 0; a < A; ++a) In[a] = Is[a] - (Is[a] - I0[a]) * f;
-  cell_moment_change(p, Is, In, &dE, dF);
+  double dE, dF[3], dI[A];
+  for (int a = 0; a < A; ++a) {
+    dI[a] = (Is[a] - I0[a]) * f;
+    In[a] = Is[a] - dI[a];
+  }
+  cell_moment_sum(p, dI, &dE, dF);
   ext[0] += p->c / p->cbar * dE;
   for (int k = 0; k < 3; ++k) ext[1 + k] += dF[k] / (p->c * p->cbar);
 }
@@ -549,15 +564,17 @@ static void source_emitter(const orc_problem *p, int64_t c, double dt, const dou
   const double rho = p->rho[c];
   double v[3] = {m[0] / rho, m[1] / rho, m[2] / rho};
   const double gam = frame_gamma(p, v);
-  double dE, dF[3];
+  double dE, dF[3], dI[A];
   for (int a = 0; a < A; ++a) {
     const double *n = p->dir + 3 * a;
     double G = gam * (1.0 - (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / p->c);
     double G4 = G * G * G * G;
     double y = dt * p->cbar * G * p->emit_rate[c];
     In[a] = ((G4 * Is[a] + y * p->I_src[c]) / (1.0 + y)) / G4;
+    /* the change as the source term: I~ - I~' = y (I~ - I_src) / (1 + y) */
+    dI[a] = (y * (G4 * Is[a] - p->I_src[c]) / (1.0 + y)) / G4;
   }
-  cell_moment_change(p, Is, In, &dE, dF);
+  cell_moment_sum(p, dI, &dE, dF);
   ext[0] += p->c / p->cbar * dE;
   for (int k = 0; k < 3; ++k) ext[1 + k] += dF[k] / (p->c * p->cbar);
 }
@@ -1092,4 +1109,182 @@ int orc_step_vl(const orc_problem *p, double dt, double *I, double *work, double
 int orc_set_threads(int n) {
   if (n > 0) omp_set_num_threads(n);
   return omp_get_max_threads();
+}
+
+/* ===================================================================
+ * Hydrodynamics on the mesh (Sec. 2, Eq. time evolution with the Euler
+ * fluxes; the Riemann-solver steps of Sec. 2): the gas state per cell is
+ * rho, m = rho v and the total energy density e = rho v^2 / 2 + P /
+ * (gamma - 1) -- the same e and m the radiation source step exchanges with.
+ * Each face's flux is the HLLC flux (Toro, Riemann Solvers and Numerical
+ * Methods for Fluid Dynamics, 3rd ed., Sec. 10.4, with the wave-speed
+ * estimates of Davis, Sec. 10.5.1) of the states on its two sides, rotated
+ * into the face normal n_f (from the face's first cell to its second); the
+ * faces are static (the linear-wave test fixes its mesh).  Each face's flux
+ * is computed once, from (first cell, second cell, n_f), and enters its two
+ * cells with opposite signs, so mass, momentum and energy are conserved to
+ * rounding.
+ * Time integration (Sec. 2, integration steps): the van Leer step -- a
+ * half step over dt/2 with the cell-centred states on both sides of each
+ * face, then the full step over dt from the initial state with the fluxes of
+ * the half-step primitives (rho, v, P) reconstructed linearly at the face
+ * centroids with the least-squares, Barth-Jespersen-limited gradients of
+ * orc_gradient (the reading of the gradient and limiter used for the
+ * radiation, which the paper takes from its hydrodynamics) -- or, with
+ * order 1, one step with the cell-centred states.
+ * =================================================================== */
+
+/* primitive (rho, vx, vy, vz, P) of a cell */
+static void hydro_prim(double gamma, double rho, const double *m, double e, double *W) {
+  W[0] = rho;
+  W[1] = m[0] / rho;
+  W[2] = m[1] / rho;
+  W[3] = m[2] / rho;
+  W[4] = (gamma - 1.0) * (e - 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) / rho);
+}
+
+/* HLLC flux per unit area of (rho, m, e) through a face with unit normal n,
+ * left state WL on the side n points away from.  Returns -1 if a state has
+ * non-positive density or pressure. */
+int orc_hllc_flux(double gamma, const double *WL, const double *WR, const double *n, double *F) {
+  const double *W[2] = {WL, WR};
+  double u[2], a[2], E[2], Fk[2][5];
+  for (int k = 0; k < 2; ++k) {
+    const double *w = W[k];
+    if (!(w[0] > 0.0) || !(w[4] > 0.0)) return -1;
+    u[k] = w[1] * n[0] + w[2] * n[1] + w[3] * n[2];
+    a[k] = sqrt(gamma * w[4] / w[0]);
+    E[k] = w[4] / (gamma - 1.0) + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+    Fk[k][0] = w[0] * u[k];
+    for (int d = 0; d < 3; ++d) Fk[k][1 + d] = w[0] * w[1 + d] * u[k] + w[4] * n[d];
+    Fk[k][4] = (E[k] + w[4]) * u[k];
+  }
+  /* Davis's estimates of the slowest and fastest signal speeds */
+  const double SL = fmin(u[0] - a[0], u[1] - a[1]);
+  const double SR = fmax(u[0] + a[0], u[1] + a[1]);
+  /* the contact's speed (Toro Eq. 10.37) */
+  const double Ss = (WR[4] - WL[4] + WL[0] * u[0] * (SL - u[0]) - WR[0] * u[1] * (SR - u[1])) /
+                    (WL[0] * (SL - u[0]) - WR[0] * (SR - u[1]));
+  if (SL >= 0.0) {
+    for (int q = 0; q < 5; ++q) F[q] = Fk[0][q];
+  } else if (SR <= 0.0) {
+    for (int q = 0; q < 5; ++q) F[q] = Fk[1][q];
+  } else {
+    /* the star state of side K (Toro Eq. 10.39, the tangential velocity
+     * carried unchanged) and F*_K = F_K + S_K (U*_K - U_K) */
+    const int k = (Ss >= 0.0) ? 0 : 1;
+    const double S = k == 0 ? SL : SR;
+    const double *w = W[k];
+    const double f = w[0] * (S - u[k]) / (S - Ss);
+    double Us[5], U[5];
+    Us[0] = f;
+    for (int d = 0; d < 3; ++d) Us[1 + d] = f * (w[1 + d] + (Ss - u[k]) * n[d]);
+    Us[4] = f * (E[k] / w[0] + (Ss - u[k]) * (Ss + w[4] / (w[0] * (S - u[k]))));
+    U[0] = w[0];
+    for (int d = 0; d < 3; ++d) U[1 + d] = w[0] * w[1 + d];
+    U[4] = E[k];
+    for (int q = 0; q < 5; ++q) F[q] = Fk[k][q] + S * (Us[q] - U[q]);
+  }
+  return 0;
+}
+
+/* cfl * min over cells of V^(1/3) / (|v| + sound speed) */
+double orc_hydro_dt(const orc_problem *p, const double *rho, const double *m, const double *e,
+                    double cfl) {
+  double best = INFINITY;
+  for (int64_t c = 0; c < p->n_cells; ++c) {
+    double W[5];
+    hydro_prim(p->gamma_gas, rho[c], m + 3 * c, e[c], W);
+    const double v = sqrt(W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+    const double a = sqrt(p->gamma_gas * W[4] / W[0]);
+    const double t = cbrt(p->cell_volume[c]) / (v + a);
+    if (t < best) best = t;
+  }
+  return cfl * best;
+}
+
+/* Fluxes of every face (area times HLLC flux, Fa[Nf][5]) from the
+ * primitives W[N][5], cell-centred (grad NULL) or reconstructed at the face
+ * centroid with grad[N][3][5]: W_i + g_i . (x_f - x_i), W_j + g_j . (x_f - x_j').
+ * Returns -1 if a face state is not physical. */
+static int hydro_face_fluxes(const orc_problem *p, const double *W, const double *grad,
+                             double *Fa) {
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+  for (int64_t f = 0; f < p->n_faces; ++f) {
+    const int64_t i = p->face_cells[2 * f], j = p->face_cells[2 * f + 1];
+    double WL[5], WR[5];
+    for (int q = 0; q < 5; ++q) {
+      WL[q] = W[i * 5 + q];
+      WR[q] = W[j * 5 + q];
+    }
+    if (grad) {
+      const double *oi = p->face_offset + 6 * f, *oj = oi + 3;
+      for (int q = 0; q < 5; ++q) {
+        WL[q] += grad[(i * 3 + 0) * 5 + q] * oi[0] + grad[(i * 3 + 1) * 5 + q] * oi[1] +
+                 grad[(i * 3 + 2) * 5 + q] * oi[2];
+        WR[q] += grad[(j * 3 + 0) * 5 + q] * oj[0] + grad[(j * 3 + 1) * 5 + q] * oj[1] +
+                 grad[(j * 3 + 2) * 5 + q] * oj[2];
+      }
+    }
+    double F[5];
+    if (orc_hllc_flux(p->gamma_gas, WL, WR, p->face_normal + 3 * f, F) != 0) bad = 1;
+    for (int q = 0; q < 5; ++q) Fa[f * 5 + q] = p->face_area[f] * F[q];
+  }
+  return bad ? -1 : 0;
+}
+
+/* U_out = U_in - h / V sum over the cell's faces (in list order) of the
+ * outward face fluxes (+Fa for the face's first cell, -Fa for its second). */
+static void hydro_apply(const orc_problem *p, double h, const double *Fa, const double *rho_in,
+                        const double *m_in, const double *e_in, double *rho, double *m,
+                        double *e) {
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < p->n_cells; ++c) {
+    double s[5] = {0, 0, 0, 0, 0};
+    for (int64_t k = p->cell_face_ptr[c]; k < p->cell_face_ptr[c + 1]; ++k) {
+      const int32_t ent = p->cell_face_idx[k];
+      const int64_t f = ent >= 0 ? ent : -(int64_t)ent - 1;
+      const double sg = ent >= 0 ? 1.0 : -1.0;
+      for (int q = 0; q < 5; ++q) s[q] += sg * Fa[f * 5 + q];
+    }
+    const double hv = h / p->cell_volume[c];
+    rho[c] = rho_in[c] - hv * s[0];
+    for (int d = 0; d < 3; ++d) m[3 * c + d] = m_in[3 * c + d] - hv * s[1 + d];
+    e[c] = e_in[c] - hv * s[4];
+  }
+}
+
+/* One hydro step of (rho, m, e) in place over dt; order 1 (cell-centred
+ * states) or 2 (the van Leer step).  work: 36 N + 5 Nf doubles.  Returns 0,
+ * or -1 if a state became unphysical (non-positive density or pressure). */
+int orc_hydro_step(const orc_problem *p, double dt, int order, double *rho, double *m, double *e,
+                   double *work) {
+  const int64_t N = p->n_cells;
+  double *W = work, *grad = W + 5 * N, *rh = grad + 15 * N, *mh = rh + N, *eh = mh + 3 * N;
+  double *Fa = eh + N;  /* 5 Nf */
+  for (int64_t c = 0; c < N; ++c) hydro_prim(p->gamma_gas, rho[c], m + 3 * c, e[c], W + 5 * c);
+  if (order == 1) {
+    if (hydro_face_fluxes(p, W, NULL, Fa) != 0) return -1;
+    hydro_apply(p, dt, Fa, rho, m, e, rho, m, e);
+  } else {
+    /* half step with the cell-centred states */
+    if (hydro_face_fluxes(p, W, NULL, Fa) != 0) return -1;
+    hydro_apply(p, 0.5 * dt, Fa, rho, m, e, rh, mh, eh);
+    for (int64_t c = 0; c < N; ++c) hydro_prim(p->gamma_gas, rh[c], mh + 3 * c, eh[c], W + 5 * c);
+    for (int64_t c = 0; c < N; ++c)
+      if (!(W[5 * c] > 0.0) || !(W[5 * c + 4] > 0.0)) return -1;
+    /* limited least-squares gradients of the five primitives */
+    orc_problem q = *p;
+    q.n_angles = 5;
+    orc_gradient(&q, W, 1, grad);
+    if (hydro_face_fluxes(p, W, grad, Fa) != 0) return -1;
+    hydro_apply(p, dt, Fa, rho, m, e, rho, m, e);
+  }
+  for (int64_t c = 0; c < N; ++c) {
+    double Wc[5];
+    hydro_prim(p->gamma_gas, rho[c], m + 3 * c, e[c], Wc);
+    if (!(Wc[0] > 0.0) || !(Wc[4] > 0.0)) return -1;
+  }
+  return 0;
 }

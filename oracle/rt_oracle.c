@@ -377,7 +377,9 @@ double orc_ferrari(double alpha, double beta, double g) {
  *        alpha T^4 + beta T = g,
  *        alpha = dt c rho kP a (1 - dt cbar rho kJ S_G / D),
  *        beta  = rho c_v,  c_v = R / (gamma - 1),
- *        g     = rho c_v T^n + dt c rho 4 pi kJ S_I / D;
+ *        g     = rho c_v T^n + dt c rho 4 pi kJ S_I / D
+ *     (D and the bracket of alpha evaluated through S_1 = sum w~ / (1 + x),
+ *     see the code);
  *  3. I~^{n+1} from Eq. (com radiative source disc), back to the lab frame;
  *  4. E^{n+1}, F^{n+1} and the gas exchange of Eqs. (gas1), (gas2):
  *        e += (c / cbar)(E^n - E^{n+1}),  rho v += (F^n - F^{n+1}) / (c cbar),
@@ -417,15 +419,22 @@ static int source_interior(const orc_problem *p, int64_t c, double dt, const dou
     wc[a] = p->wt[a] / G2;
     norm += wc[a];
   }
-  double SI = 0.0, SG = 0.0;
+  double SI = 0.0, SG = 0.0, S1 = 0.0;
   for (int a = 0; a < A; ++a) {
     wc[a] /= norm;
     double xa = dt * p->cbar * rho * (kJ + kS) * G[a];
     SI += wc[a] * Ic[a] / (1.0 + xa);
     SG += wc[a] * G[a] / (1.0 + xa);
+    S1 += wc[a] / (1.0 + xa);
   }
-  double D = 1.0 - dt * p->cbar * rho * kS * SG;
-  double alpha = dt * p->c * rho * kP * p->a_rad * (1.0 - dt * p->cbar * rho * kJ * SG / D);
+  /* D = 1 - dt cbar rho ks S_G and 1 - dt cbar rho kJ S_G / D, evaluated
+   * through S_1 = sum w~ / (1 + x_a): since the w~ sum to one,
+   *   1 - dt cbar rho (kJ + ks) S_G = S_1,  so D = S_1 + dt cbar rho kJ S_G
+   * and 1 - dt cbar rho kJ S_G / D = S_1 / D.  The printed forms subtract
+   * x / (1 + x) from one and lose log2(x) bits where cells are optically
+   * thick (x ~ 1e4 per step in the Sec. 3.1 example with kappa = 100). */
+  double D = S1 + dt * p->cbar * rho * kJ * SG;
+  double alpha = dt * p->c * rho * kP * p->a_rad * (S1 / D);
   double beta = rcv;
   double g = rcv * Tn + dt * p->c * rho * 4.0 * M_PI * kJ * SI / D;
   double T;
@@ -493,16 +502,19 @@ static int source_interior_groups(const orc_problem *p, int64_t c, double dt, co
       norm += wc[b];
     }
     SI[j] = SG[j] = 0.0;
+    double S1 = 0.0;
     for (int b = 0; b < Ag; ++b) {
       const int a = j * Ag + b;
       wc[b] /= norm;
       double xa = dt * p->cbar * rho * (kJ[j] + kS[j]) * G[a];
       SI[j] += wc[b] * Ic[a] / (1.0 + xa);
       SG[j] += wc[b] * G[a] / (1.0 + xa);
+      S1 += wc[b] / (1.0 + xa);
     }
-    D[j] = 1.0 - dt * p->cbar * rho * kS[j] * SG[j];
+    /* D_j and 1 - dt cbar rho kJ_j S_G,j / D_j through S_1 (see source_interior) */
+    D[j] = S1 + dt * p->cbar * rho * kJ[j] * SG[j];
     const double W = p->group_w[j];
-    alpha += W * dt * p->c * rho * kP[j] * p->a_rad * (1.0 - dt * p->cbar * rho * kJ[j] * SG[j] / D[j]);
+    alpha += W * dt * p->c * rho * kP[j] * p->a_rad * (S1 / D[j]);
     g += W * dt * p->c * rho * 4.0 * M_PI * kJ[j] * SI[j] / D[j];
   }
   double T;

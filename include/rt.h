@@ -171,7 +171,12 @@ typedef enum { RT_FIRST_ORDER = 0, RT_VAN_LEER = 1 } rt_integrator;
  * Newton in double, one GPU lane per cell -- as the precision split of
  * RT_FP32 states says; 1 solves it in float in every lane of the cell (no
  * block barrier, faster; coefficients outside float range still take the
- * double solve), so the temperature carries float rounding. */
+ * double solve), so the temperature carries float rounding.
+ * hydro = 1 lets the state evolve the gas by the Euler equations as well
+ * (rt_hydro_step, rt_radhydro_step: Sec. 2, radiation subcycled under a
+ * hydro step); it needs face_offset, a static mesh (face_w NULL or zero),
+ * n_groups 1, gcl 0 and constant opacities, and adds about 150 bytes per
+ * face and 230 per cell of device memory. */
 typedef struct {
   double cbar, c, a_rad, gamma_gas, r_gas, cfl;
   int32_t precision;       /* rt_precision */
@@ -182,7 +187,7 @@ typedef struct {
   int32_t plain_launches;  /* 0: multi-step calls replay captured graphs; 1: plain launches */
   double beta_P, beta_J, T_ref; /* see above */
   int32_t float_quartic;   /* RT_FP32 only: 0 temperature solve in double, 1 in float */
-  int32_t reserved;        /* must be 0 */
+  int32_t hydro;           /* 1: the state also evolves the gas dynamics (rt_hydro_step) */
 } rt_params;
 
 /* Validates and copies the mesh to the device, orders cells for locality,
@@ -202,6 +207,17 @@ int rt_create(const rt_mesh_desc *mesh, const rt_params *params, void *stream,
  * Resets the boundary / emitter tallies. */
 int rt_set_gas(rt_state *s, const double *rho, const double *e, const double *m,
                const double *kappa_P, const double *kappa_J, const double *kappa_s);
+
+/* Replaces only the evolving gas state -- total energy density e[N] and
+ * momentum density m[N][3], caller order -- keeping rho, the opacities, the
+ * cell kinds and the boundary / emitter tallies of the state (Sec. 2.3: the
+ * quantities the source step updates).  For restoring a checkpoint (the
+ * adjoint's recomputation) without the host round trip of rt_set_gas.
+ * on_device = 1: e and m are device pointers on the state's device (their
+ * values are not checked; a non-finite value surfaces as RT_ERR_NONFINITE in
+ * the next step); 0: host pointers, checked finite (RT_ERR_ARG).  Needs a
+ * prior rt_set_gas (RT_ERR_STATE). */
+int rt_set_gas_energy(rt_state *s, const double *e, const double *m, int on_device);
 
 /* Cell kinds (rt_cell_kind, [N]).  Boundary cells use tau[N] and the row
  * bc_row[N] of I0[n_rows][A]; emitter cells use emit_rate[N] (= rho kappa of
@@ -267,9 +283,13 @@ int rt_totals(rt_state *s, double out[16]);
  * that loads it, kept until exit), so the call itself allocates nothing --
  * for code that runs where cudaMalloc is not allowed, or whose device
  * memory belongs to another allocator.  At most 8,388,608 cells; larger
- * states return RT_ERR_ARG.  The first call on a device looks up the array's
- * address (cudaGetSymbolAddress, with that device current): make it before
- * any stream capture.  All calls on a device share the array, so calls
+ * states return RT_ERR_ARG.  The same kernels as rt_totals compute the sums:
+ * up to 131,072 cells in rt_totals' blocks (bit-identical results), beyond
+ * that in larger blocks (the same totals to rounding, not bit for bit).  The
+ * first call in a context looks up the array's address
+ * (cudaGetSymbolAddress, with that device current): make it before any
+ * stream capture; a call in a new context (after cudaDeviceReset, say)
+ * looks it up again.  All calls on a device share the array, so calls
  * whose GPU work overlaps race; each call rewrites everything it reads.
  * Synchronises the state's stream; does not report the latched per-cell
  * status (rt_sync does).  out: host, 16 doubles, layout of rt_totals. */
@@ -295,6 +315,40 @@ int rt_adjoint_step(rt_state *s, double dt, const void *I_n, const double *e_n, 
                     const void *lam_I1, const double *lam_e1, const double *lam_m1, void *lam_I,
                     double *lam_e, double *lam_m, double *grad_kappa_P, double *grad_kappa_J,
                     int on_device);
+
+/* Gas dynamics (states created with params.hydro = 1; Sec. 2, Eq. time
+ * evolution with the Euler fluxes): one hydro step of the gas density rho,
+ * momentum m and total energy e over dt -- every face's flux the HLLC flux
+ * (Toro, Sec. 10.4) of the states on its two sides in the face normal
+ * frame, applied to both cells with opposite signs (mass, momentum and
+ * energy conserved to rounding); order 1 with the cell-centred states,
+ * order 2 the paper's van Leer step (a half step with the cell-centred
+ * states, then the full step with the half-step primitives reconstructed
+ * linearly at the face centroids from least-squares, Barth-Jespersen-limited
+ * gradients).  The faces are static.  The radiation then sees the new
+ * density (the opacities per unit mass of rt_set_gas are kept).  Double
+ * precision in every state precision.  Errors: RT_ERR_STATE (no hydro or
+ * no rt_set_gas), RT_ERR_ARG (dt not positive and finite, order not 1 or
+ * 2), RT_ERR_NONFINITE (a density or pressure became non-positive; the gas
+ * is then not usable). */
+int rt_hydro_step(rt_state *s, double dt, int32_t order);
+
+/* The gas Courant step: cfl * min over cells of V^(1/3) / (|v| + sound
+ * speed).  Same requirements as rt_hydro_step. */
+int rt_hydro_dt(rt_state *s, double cfl, double *dt);
+
+/* One radiation-hydrodynamics step: rt_hydro_step over dt, then n_sub >= 1
+ * radiation steps (transport and implicit source, exchanging energy and
+ * momentum with the updated gas) of dt / n_sub each -- the radiation
+ * subcycled under the hydro step, as the reduced speed of light allows
+ * (Sec. 2, Sec. 3.6).  The radiation steps are checked against the upwind
+ * positivity limit like rt_run (RT_ERR_CFL); *dt_rad (may be NULL)
+ * receives dt / n_sub.  Per-cell failures are returned as by rt_run. */
+int rt_radhydro_step(rt_state *s, double dt, int32_t n_sub, int32_t order, double *dt_rad);
+
+/* The gas density rho[N] (caller order) of a state, host or device
+ * pointer. */
+int rt_get_density(rt_state *s, double *rho, int on_device);
 
 /* Serialises the full evolving state (intensities, gas e and m, tallies) to
  * a host buffer.  buf == NULL: *bytes receives the size needed. */

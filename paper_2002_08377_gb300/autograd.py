@@ -45,7 +45,7 @@ class RTRun(torch.autograd.Function):
         gJ = torch.zeros(N, dtype=torch.float64, device="cuda")
         for n0, I, e, m in reversed(ctx.checkpoints):
             n1 = min(n0 + ctx.every, ctx.n_steps)
-            s.set_gas(gas["rho"], e.cpu().numpy(), m.cpu().numpy(), k, k, gas["kappa_s"])
+            s.set_gas_energy(e, m)  # the checkpoint, on the device
             s.set_intensity(I)
             inputs = []
             for _ in range(n0, n1):
@@ -57,7 +57,7 @@ class RTRun(torch.autograd.Function):
                                                      gP, gJ)
         # leave the solver in the state the forward pass ended in
         I_f, e_f, m_f = ctx.final
-        s.set_gas(gas["rho"], e_f.cpu().numpy(), m_f.cpu().numpy(), k, k, gas["kappa_s"])
+        s.set_gas_energy(e_f, m_f)
         s.set_intensity(I_f)
         grad_I0 = lam_I.to(ctx.I0_device, ctx.I0_dtype)
         grad_kappa = (gP + gJ).to(ctx.kappa_device, ctx.kappa_dtype)

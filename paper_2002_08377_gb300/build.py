@@ -15,7 +15,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librt_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["rt_api.cu", "rt_step.cu", "rt_transport.cu", "rt_aux.cu", "rt_adjoint.cu", "rt_noalloc.cu",
-           "rt_recon.cu", "rt_groups.cu"]
+           "rt_recon.cu", "rt_groups.cu", "rt_hydro.cu"]
+# per-file flags: the gas dynamics round as their plain formulas (no FMA contraction)
+FILE_FLAGS = {"rt_hydro.cu": ["--fmad=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code is compiled without FMA contraction so that x86 and Arm hosts
 # build bit-identical face geometry
@@ -55,7 +57,7 @@ def build(force=False, verbose=False, extra_flags=()):
 
         def compile_one(src):
             obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-            cmd = [exe, *ARCH, *FLAGS, *extra_flags, "-I", INCLUDE, "-c",
+            cmd = [exe, *ARCH, *FLAGS, *FILE_FLAGS.get(src, []), *extra_flags, "-I", INCLUDE, "-c",
                    os.path.join(CSRC, src), "-o", obj]
             r = subprocess.run(cmd, capture_output=True, text=True)
             if r.returncode != 0:

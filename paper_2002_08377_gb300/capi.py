@@ -16,9 +16,10 @@ _NAMES = {0: "RT_OK", -1: "RT_ERR_ARG", -2: "RT_ERR_MESH", -3: "RT_ERR_CUDA", -4
           -5: "RT_ERR_CFL", -6: "RT_ERR_NONCONV", -7: "RT_ERR_NONFINITE", -8: "RT_ERR_STATE"}
 
 # every symbol include/rt.h declares (checked by the CPU tests)
-EXPORTS = ["rt_create", "rt_set_gas", "rt_set_cells", "rt_set_intensity", "rt_get_intensity",
+EXPORTS = ["rt_create", "rt_set_gas", "rt_set_gas_energy", "rt_set_cells", "rt_set_intensity", "rt_get_intensity",
            "rt_get_gas", "rt_dt_limits", "rt_step", "rt_run", "rt_launch", "rt_moments", "rt_totals", "rt_totals_noalloc",
-           "rt_sync", "rt_adjoint_step", "rt_get_state", "rt_set_state", "rt_device_bytes", "rt_launch_count",
+           "rt_sync", "rt_adjoint_step", "rt_hydro_step", "rt_hydro_dt", "rt_radhydro_step",
+           "rt_get_density", "rt_get_state", "rt_set_state", "rt_device_bytes", "rt_launch_count",
            "rt_last_error", "rt_destroy"]
 
 
@@ -47,7 +48,7 @@ class Params(ctypes.Structure):
                 ("newton_max_iter", ctypes.c_int32), ("integrator", ctypes.c_int32),
                 ("boost", ctypes.c_int32), ("gcl", ctypes.c_int32), ("plain_launches", ctypes.c_int32),
                 ("beta_P", ctypes.c_double), ("beta_J", ctypes.c_double), ("T_ref", ctypes.c_double),
-                ("float_quartic", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("float_quartic", ctypes.c_int32), ("hydro", ctypes.c_int32)]
 
 
 _lib = None
@@ -73,6 +74,7 @@ def load(build_if_missing=True):
     sig = {
         "rt_create": ([ctypes.POINTER(MeshDesc), ctypes.POINTER(Params), vp, ctypes.POINTER(vp)], i32),
         "rt_set_gas": ([vp] * 7, i32),
+        "rt_set_gas_energy": ([vp, vp, vp, i32], i32),
         "rt_set_cells": ([vp, vp, vp, vp, vp, vp, i64, vp], i32),
         "rt_set_intensity": ([vp, vp, i32], i32),
         "rt_get_intensity": ([vp, vp, i32], i32),
@@ -85,6 +87,10 @@ def load(build_if_missing=True):
         "rt_totals": ([vp, vp], i32),
         "rt_totals_noalloc": ([vp, vp], i32),
         "rt_sync": ([vp], i32),
+        "rt_hydro_step": ([vp, d, i32], i32),
+        "rt_hydro_dt": ([vp, d, pd], i32),
+        "rt_radhydro_step": ([vp, d, i32, i32, pd], i32),
+        "rt_get_density": ([vp, vp, i32], i32),
         "rt_adjoint_step": ([vp, d] + [vp] * 11 + [i32], i32),
         "rt_get_state": ([vp, vp, ctypes.POINTER(ctypes.c_size_t)], i32),
         "rt_set_state": ([vp, vp, ctypes.c_size_t], i32),

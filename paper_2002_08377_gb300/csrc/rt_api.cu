@@ -10,11 +10,35 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "rt_internal.cuh"
 
 namespace rt {
 int64_t totals_scratch_len(int64_t n_cells);
+
+void *driver_fn(const char *name) {
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q{};
+  if (cudaGetDriverEntryPointByVersion(name, &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return fn;
 }
+
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext *);
+  using GetId = CUresult (*)(CUcontext, unsigned long long *);
+  static GetCurrent cur = reinterpret_cast<GetCurrent>(driver_fn("cuCtxGetCurrent"));
+  static GetId id = reinterpret_cast<GetId>(driver_fn("cuCtxGetId"));
+  CUcontext ctx = nullptr;
+  unsigned long long v = 0;
+  if (!cur || !id || cur(&ctx) != CUDA_SUCCESS || !ctx || id(ctx, &v) != CUDA_SUCCESS) return 0;
+  return v;
+}
+}  // namespace rt
 
 namespace {
 
@@ -455,7 +479,9 @@ int rt_create(const rt_mesh_desc *m_in, const rt_params *p, void *stream, rt_sta
       (p->gcl && p->integrator != RT_FIRST_ORDER) || !std::isfinite(p->beta_P) ||
       !std::isfinite(p->beta_J) || ((p->beta_P != 0 || p->beta_J != 0) && !(p->T_ref > 0)) ||
       !(p->beta_P >= -3.0) || (p->plain_launches != 0 && p->plain_launches != 1) ||
-      (p->float_quartic != 0 && p->float_quartic != 1) || p->reserved != 0 ||
+      (p->float_quartic != 0 && p->float_quartic != 1) || (p->hydro != 0 && p->hydro != 1) ||
+      (p->hydro && (!m->face_offset || G > 1 || p->gcl || p->beta_P != 0.0 ||
+                    p->beta_J != 0.0)) ||
       (p->integrator == RT_VAN_LEER && !m->face_offset))
     return bail(RT_ERR_ARG);
   s->params = *p;
@@ -511,6 +537,15 @@ int rt_create(const rt_mesh_desc *m_in, const rt_params *p, void *stream, rt_sta
   int r = (s->precision == RT_FP32) ? build_device_mesh<float>(s, m, slot_of)
                                     : build_device_mesh<double>(s, m, slot_of);
   if (r != RT_OK) return bail(r);
+  if (p->hydro) {
+    // the gas dynamics run on static faces
+    if (s->moving) {
+      fprintf(stderr, "rt_create: hydro = 1 needs a static mesh (face_w NULL or zero)\n");
+      return bail(RT_ERR_ARG);
+    }
+    r = rt::hydro_setup(s, m);
+    if (r != RT_OK) return bail(r);
+  }
   s->integrator = p->integrator;
   if (s->integrator == RT_VAN_LEER) {
     r = (s->precision == RT_FP32) ? build_recon<float>(s, m) : build_recon<double>(s, m);
@@ -719,6 +754,18 @@ int rt_set_gas(rt_state *s, const double *rho, const double *e, const double *m,
     RT_CUDA(s, cudaStreamSynchronize(s->stream));  // rkJ0 is a host temporary
     RT_CUDA(s, rt::launch_opacity_refresh(s));
   }
+  if (s->params.hydro) {
+    // the opacities per unit mass, for the coefficients after the density changes
+    std::vector<double> km(3 * (size_t)N);
+    for (int64_t ic = 0; ic < N; ++ic) {
+      const int64_t c = s->cell_of[ic];
+      km[3 * ic] = kP[c];
+      km[3 * ic + 1] = kJ[c];
+      km[3 * ic + 2] = kS[c];
+    }
+    RT_CUDA(s, cudaMemcpy(rt::hydro_kmass(s), km.data(), sizeof(double) * km.size(),
+                          cudaMemcpyHostToDevice));
+  }
   RT_CUDA(s, cudaMemsetAsync(s->d_ext, 0, sizeof(double) * 4 * N, s->stream));
   // per-cell frame velocity and rho (kJ + kS) in the state precision
   RT_CUDA(s, rt::launch_cellv(s));
@@ -726,6 +773,33 @@ int rt_set_gas(rt_state *s, const double *rho, const double *e, const double *m,
   RT_CUDA(s, cudaMemsetAsync(s->d_bad, 0xff, sizeof(unsigned long long), s->stream));
   RT_CUDA(s, cudaStreamSynchronize(s->stream));
   s->gas_set = true;
+  return RT_OK;
+}
+
+int rt_set_gas_energy(rt_state *s, const double *e, const double *m, int on_device) {
+  if (!s) return RT_ERR_ARG;
+  if (!e || !m) return fail(s, RT_ERR_ARG, "rt_set_gas_energy: NULL array");
+  if (!s->gas_set) return fail(s, RT_ERR_STATE, "rt_set_gas_energy before rt_set_gas");
+  ++s->gen;  // captured step graphs may hold old arguments
+  const int64_t N = s->n_cells;
+  if (on_device) {
+    RT_CUDA(s, rt::launch_gas_in(s, e, m));
+  } else {
+    std::vector<rt::GasDyn> gd(N);
+    for (int64_t ic = 0; ic < N; ++ic) {
+      const int64_t c = s->cell_of[ic];
+      if (!std::isfinite(e[c]) || !std::isfinite(m[3 * c]) || !std::isfinite(m[3 * c + 1]) ||
+          !std::isfinite(m[3 * c + 2]))
+        return fail(s, RT_ERR_ARG, "rt_set_gas_energy: e and m must be finite");
+      gd[ic] = {e[c], m[3 * c], m[3 * c + 1], m[3 * c + 2]};
+    }
+    RT_CUDA(s, cudaMemcpyAsync(s->d_gd, gd.data(), sizeof(rt::GasDyn) * N,
+                               cudaMemcpyHostToDevice, s->stream));
+    RT_CUDA(s, cudaStreamSynchronize(s->stream));  // gd is a host temporary
+  }
+  if (s->params.beta_J != 0.0) RT_CUDA(s, rt::launch_opacity_refresh(s));
+  RT_CUDA(s, rt::launch_cellv(s));
+  RT_CUDA(s, cudaStreamSynchronize(s->stream));
   return RT_OK;
 }
 
@@ -797,13 +871,29 @@ int rt_set_cells(rt_state *s, const uint8_t *kind, const double *tau, const doub
 // The device-side address of page-locked (cudaHostAlloc / cudaHostRegister)
 // host memory, which kernels may read and write; NULL for any other pointer
 // (pageable memory then goes through a staged copy).
-static const void *pinned_device_address(const void *p) {
+// The device address of page-locked host memory [p, p + bytes), or NULL if
+// any of it is not page-locked: the driver reports the registered range that
+// holds p, and the whole span must lie in it (a buffer registered in part
+// takes the staged copy).
+static const void *pinned_device_address(const void *p, size_t bytes) {
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     (void)cudaGetLastError();
     return nullptr;
   }
-  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+  if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+  using GetAttr = CUresult (*)(void *, CUpointer_attribute, CUdeviceptr);
+  static GetAttr get = reinterpret_cast<GetAttr>(rt::driver_fn("cuPointerGetAttribute"));
+  if (!get) return nullptr;
+  CUdeviceptr start = 0;
+  size_t size = 0;
+  if (get(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, (CUdeviceptr)(uintptr_t)p) !=
+          CUDA_SUCCESS ||
+      get(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, (CUdeviceptr)(uintptr_t)p) != CUDA_SUCCESS)
+    return nullptr;
+  const uintptr_t a = (uintptr_t)p, lo = (uintptr_t)start;
+  if (a < lo || a - lo > size || bytes > size - (a - lo)) return nullptr;
+  return at.devicePointer;
 }
 
 int rt_set_intensity(rt_state *s, const void *I, int on_device) {
@@ -813,7 +903,7 @@ int rt_set_intensity(rt_state *s, const void *I, int on_device) {
   const void *src = I;
   void *stage = s->d_I[s->cur ^ 1];
   if (!on_device) {
-    if (const void *dev = pinned_device_address(I)) {
+    if (const void *dev = pinned_device_address(I, bytes)) {
       // page-locked host rows: one pass reads them over the host link and
       // writes the internal rows
       RT_CUDA(s, rt::launch_permute_in_host(s, dev, s->d_I[s->cur], s->row_stride));
@@ -833,7 +923,7 @@ int rt_get_intensity(rt_state *s, void *I, int on_device) {
   const size_t bytes = (size_t)s->n_cells * s->n_angles * s->rsize;
   if (on_device) {
     RT_CUDA(s, rt::launch_permute_out(s, s->d_I[s->cur], I, s->row_stride));
-  } else if (void *dev = const_cast<void *>(pinned_device_address(I))) {
+  } else if (void *dev = const_cast<void *>(pinned_device_address(I, bytes))) {
     RT_CUDA(s, rt::launch_permute_out_host(s, s->d_I[s->cur], dev, s->row_stride));
   } else {
     void *stage = s->d_I[s->cur ^ 1];
@@ -981,6 +1071,74 @@ int rt_run(rt_state *s, int32_t n, double dt, double *dt_used) {
 
 int rt_launch(rt_state *s, int32_t n, double dt, double *dt_used) {
   return launch_steps(s, n, dt, dt_used, false);
+}
+
+static int hydro_ready(rt_state *s, const char *who) {
+  if (!s->params.hydro) {
+    std::string m = std::string(who) + ": the state was created without hydro = 1";
+    return fail(s, RT_ERR_STATE, m.c_str());
+  }
+  if (!s->gas_set) {
+    std::string m = std::string(who) + ": rt_set_gas must be called first";
+    return fail(s, RT_ERR_STATE, m.c_str());
+  }
+  return RT_OK;
+}
+
+int rt_hydro_step(rt_state *s, double dt, int32_t order) {
+  if (!s) return RT_ERR_ARG;
+  int st = hydro_ready(s, "rt_hydro_step");
+  if (st != RT_OK) return st;
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(s, RT_ERR_ARG, "rt_hydro_step: dt must be positive and finite");
+  if (order != 1 && order != 2) return fail(s, RT_ERR_ARG, "rt_hydro_step: order must be 1 or 2");
+  RT_CUDA(s, rt::launch_hydro_step(s, dt, order));
+  RT_CUDA(s, cudaStreamSynchronize(s->stream));
+  unsigned bad = 0;
+  RT_CUDA(s, cudaMemcpy(&bad, s->d_status, sizeof bad, cudaMemcpyDeviceToHost));
+  if (bad & rt::ST_NONFINITE) {
+    unsigned long long c = 0;
+    RT_CUDA(s, cudaMemcpy(&c, s->d_bad, sizeof c, cudaMemcpyDeviceToHost));
+    char buf[160];
+    snprintf(buf, sizeof buf, "rt_hydro_step: non-positive density or pressure (first cell %lld)",
+             c < (unsigned long long)s->n_cells ? (long long)s->cell_of[c] : -1LL);
+    return fail(s, RT_ERR_NONFINITE, buf);
+  }
+  return RT_OK;
+}
+
+int rt_hydro_dt(rt_state *s, double cfl, double *dt) {
+  if (!s || !dt) return s ? fail(s, RT_ERR_ARG, "rt_hydro_dt: NULL") : RT_ERR_ARG;
+  int st = hydro_ready(s, "rt_hydro_dt");
+  if (st != RT_OK) return st;
+  if (!(cfl > 0) || !std::isfinite(cfl)) return fail(s, RT_ERR_ARG, "rt_hydro_dt: cfl must be positive");
+  RT_CUDA(s, rt::launch_hydro_dt(s, cfl, dt));
+  return RT_OK;
+}
+
+int rt_radhydro_step(rt_state *s, double dt, int32_t n_sub, int32_t order, double *dt_rad) {
+  if (!s) return RT_ERR_ARG;
+  if (n_sub < 1) return fail(s, RT_ERR_ARG, "rt_radhydro_step: n_sub must be >= 1");
+  int st = rt_hydro_step(s, dt, order);
+  if (st != RT_OK) return st;
+  return launch_steps(s, n_sub, dt / n_sub, dt_rad, true);
+}
+
+int rt_get_density(rt_state *s, double *rho, int on_device) {
+  if (!s || !rho) return s ? fail(s, RT_ERR_ARG, "rt_get_density: NULL") : RT_ERR_ARG;
+  const int64_t N = s->n_cells;
+  if (on_device) {
+    RT_CUDA(s, rt::launch_density_out(s, rho));
+  } else {
+    double *buf = nullptr;
+    RT_CUDA(s, cudaMalloc((void **)&buf, sizeof(double) * N));
+    cudaError_t e = rt::launch_density_out(s, buf);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rho, buf, sizeof(double) * N, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(s, e, "rt_get_density");
+  }
+  RT_CUDA(s, cudaStreamSynchronize(s->stream));
+  return RT_OK;
 }
 
 int rt_moments(rt_state *s, double *E, double *F, double *P, int on_device) {
@@ -1155,7 +1313,7 @@ void rt_destroy(rt_state *s) {
     if (s->d_adj[k]) cudaFree(s->d_adj[k]);
   if (s->d_adj_ws) cudaFree(s->d_adj_ws);
   if (s->d_adj_stage) cudaFree(s->d_adj_stage);
-  void *bufs[] = {s->d_kapgf, s->d_kapg, s->d_rkJ0, s->d_gcl_rate, s->d_gcl_kv, s->d_recon, s->d_lsq, s->d_Ihalf, s->d_grad, s->d_uface, s->d_slot_nb, s->d_wface, s->d_angle_of, s->d_pos_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
+  void *bufs[] = {s->d_hface, s->d_hslot, s->d_hwork, s->d_kapgf, s->d_kapg, s->d_rkJ0, s->d_gcl_rate, s->d_gcl_kv, s->d_recon, s->d_lsq, s->d_Ihalf, s->d_grad, s->d_uface, s->d_slot_nb, s->d_wface, s->d_angle_of, s->d_pos_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
                   s->d_gd, s->d_kind, s->d_aux, s->d_bc_row, s->d_I0, s->d_ext, s->d_dir, s->d_wt,
                   s->d_dir64, s->d_wt64, s->d_I[0], s->d_I[1], s->d_status, s->d_bad,
                   s->d_scratch, s->d_out16};

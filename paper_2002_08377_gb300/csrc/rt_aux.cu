@@ -11,17 +11,38 @@ namespace {
 constexpr int kThreads = 256;
 
 // dst[ic][q] = src[cell_of[ic]][angle_of[q]]  (caller order -> internal order;
-// internal rows `stride` reals apart)
+// internal rows `stride` reals apart).  A warp keeps its lanes' entries of
+// the angle map in registers (A <= 128) and moves two rows per iteration of
+// a grid-stride loop, so that each warp has two rows' loads in flight.
+constexpr int kMapPerLane = 4;  // 128 angles / 32 lanes
 template <typename R>
 __global__ void permute_in_kernel(const R *__restrict__ src, R *__restrict__ dst,
                                   const int64_t *__restrict__ cell_of,
                                   const int32_t *__restrict__ angle_of, int64_t n, int A,
                                   int stride) {
-  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  if (row >= n) return;
-  const R *s = src + (size_t)cell_of[row] * A;
-  R *d = dst + (size_t)row * stride;
-  for (int k = threadIdx.x % 32; k < A; k += 32) d[k] = s[angle_of[k]];
+  const int lane = threadIdx.x % 32;
+  int ang[kMapPerLane];
+#pragma unroll
+  for (int j = 0; j < kMapPerLane; ++j) ang[j] = lane + 32 * j < A ? angle_of[lane + 32 * j] : 0;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; row < n;
+       row += 2 * nw) {
+    const int64_t r2 = row + nw < n ? row + nw : row;
+    const R *s1 = src + (size_t)cell_of[row] * A, *s2 = src + (size_t)cell_of[r2] * A;
+    R v1[kMapPerLane], v2[kMapPerLane];
+#pragma unroll
+    for (int j = 0; j < kMapPerLane; ++j)
+      if (lane + 32 * j < A) {
+        v1[j] = s1[ang[j]];
+        v2[j] = s2[ang[j]];
+      }
+#pragma unroll
+    for (int j = 0; j < kMapPerLane; ++j)
+      if (lane + 32 * j < A) {
+        dst[(size_t)row * stride + lane + 32 * j] = v1[j];
+        dst[(size_t)r2 * stride + lane + 32 * j] = v2[j];  // r2 == row: the same value again
+      }
+  }
 }
 
 // dst[cell_of[ic]][angle_of[q]] = src[ic][q]  (internal order -> caller order)
@@ -30,11 +51,29 @@ __global__ void permute_out_kernel(const R *__restrict__ src, R *__restrict__ ds
                                    const int64_t *__restrict__ cell_of,
                                    const int32_t *__restrict__ angle_of, int64_t n, int A,
                                    int stride) {
-  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  if (row >= n) return;
-  const R *s = src + (size_t)row * stride;
-  R *d = dst + (size_t)cell_of[row] * A;
-  for (int k = threadIdx.x % 32; k < A; k += 32) d[angle_of[k]] = s[k];
+  const int lane = threadIdx.x % 32;
+  int ang[kMapPerLane];
+#pragma unroll
+  for (int j = 0; j < kMapPerLane; ++j) ang[j] = lane + 32 * j < A ? angle_of[lane + 32 * j] : 0;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; row < n;
+       row += 2 * nw) {
+    const int64_t r2 = row + nw < n ? row + nw : row;
+    R v1[kMapPerLane], v2[kMapPerLane];
+#pragma unroll
+    for (int j = 0; j < kMapPerLane; ++j)
+      if (lane + 32 * j < A) {
+        v1[j] = src[(size_t)row * stride + lane + 32 * j];
+        v2[j] = src[(size_t)r2 * stride + lane + 32 * j];
+      }
+    R *d1 = dst + (size_t)cell_of[row] * A, *d2 = dst + (size_t)cell_of[r2] * A;
+#pragma unroll
+    for (int j = 0; j < kMapPerLane; ++j)
+      if (lane + 32 * j < A) {
+        d1[ang[j]] = v1[j];
+        d2[ang[j]] = v2[j];
+      }
+  }
 }
 
 // Host-memory forms: lane k takes caller column k of the row (contiguous on
@@ -176,19 +215,19 @@ __global__ void moments_kernel(const R *__restrict__ I, const double *__restrict
 
 // Totals, pass 1: every block sums a fixed contiguous range of cells in a
 // fixed order into partial[block][16].
-constexpr int kTotCells = 64;  // cells per block
+constexpr int64_t kTotCells = totals_block_cells;  // cells per block of rt_totals
 template <typename R>
 __global__ void totals_partial_kernel(const R *__restrict__ I, const double *__restrict__ dir,
                                       const double *__restrict__ wt,
                                       const double *__restrict__ vol, const GasDyn *__restrict__ gd,
                                       const double *__restrict__ ext, int64_t n, int A,
-                                      int stride, double c_over_cbar, double inv_cbar,
-                                      double *partial) {
+                                      int stride, int64_t cpb, double c_over_cbar,
+                                      double inv_cbar, double *partial) {
   __shared__ double acc[kThreads / 32][12];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   double t[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  const int64_t c0 = (int64_t)blockIdx.x * kTotCells;
-  for (int k = warp; k < kTotCells; k += kThreads / 32) {
+  const int64_t c0 = (int64_t)blockIdx.x * cpb;
+  for (int64_t k = warp; k < cpb; k += kThreads / 32) {
     const int64_t row = c0 + k;
     if (row >= n) break;
     const R *Ir = I + (size_t)row * stride;
@@ -248,6 +287,16 @@ __global__ void totals_final_kernel(const double *__restrict__ partial, int64_t 
   if (k < 3) out16[13 + k] = out16[3 + k] + out16[6 + k] + out16[9 + k];
 }
 
+// the inverse of gas_out_kernel for (e, m): caller-order device arrays into
+// the internal gas records
+__global__ void gas_in_kernel(const double *__restrict__ e, const double *__restrict__ m,
+                              const int64_t *__restrict__ cell_of, int64_t n, GasDyn *gd) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t oc = cell_of[i];
+  gd[i] = GasDyn{e[oc], m[3 * oc], m[3 * oc + 1], m[3 * oc + 2]};
+}
+
 __global__ void gas_out_kernel(const GasDyn *__restrict__ gd, const double *__restrict__ ext,
                                const int64_t *__restrict__ cell_of, int64_t n, double *e,
                                double *m, double *x) {
@@ -282,16 +331,22 @@ __global__ void cellv_kernel(const GasStatic *__restrict__ gs, const GasDyn *__r
 }
 
 unsigned rows_grid(int64_t n) { return (unsigned)((n + kThreads / 32 - 1) / (kThreads / 32)); }
+// the device permutes: two rows per warp iteration, at most 16 blocks per SM
+// worth of warps (the loop strides over the rest)
+unsigned permute_grid(int64_t n) {
+  const int64_t blocks = (n + 2 * (kThreads / 32) - 1) / (2 * (kThreads / 32));
+  return (unsigned)(blocks < 152 * 16 ? (blocks > 0 ? blocks : 1) : 152 * 16);
+}
 
 }  // namespace
 
 cudaError_t launch_permute_in(rt_state *s, const void *src, void *dst, int stride) {
   if (s->precision == RT_FP32)
-    permute_in_kernel<float><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
+    permute_in_kernel<float><<<permute_grid(s->n_cells), kThreads, 0, s->stream>>>(
         (const float *)src, (float *)dst, s->d_cell_of, s->d_angle_of, s->n_cells, s->n_angles,
         stride);
   else
-    permute_in_kernel<double><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
+    permute_in_kernel<double><<<permute_grid(s->n_cells), kThreads, 0, s->stream>>>(
         (const double *)src, (double *)dst, s->d_cell_of, s->d_angle_of, s->n_cells,
         s->n_angles, stride);
   s->launches++;
@@ -300,11 +355,11 @@ cudaError_t launch_permute_in(rt_state *s, const void *src, void *dst, int strid
 
 cudaError_t launch_permute_out(rt_state *s, const void *src, void *dst, int stride) {
   if (s->precision == RT_FP32)
-    permute_out_kernel<float><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
+    permute_out_kernel<float><<<permute_grid(s->n_cells), kThreads, 0, s->stream>>>(
         (const float *)src, (float *)dst, s->d_cell_of, s->d_angle_of, s->n_cells, s->n_angles,
         stride);
   else
-    permute_out_kernel<double><<<rows_grid(s->n_cells), kThreads, 0, s->stream>>>(
+    permute_out_kernel<double><<<permute_grid(s->n_cells), kThreads, 0, s->stream>>>(
         (const double *)src, (double *)dst, s->d_cell_of, s->d_angle_of, s->n_cells,
         s->n_angles, stride);
   s->launches++;
@@ -372,25 +427,37 @@ cudaError_t launch_moments(rt_state *s, double *E, double *F, double *P) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_totals(rt_state *s, double *d_out16) {
-  const int64_t nb = (s->n_cells + kTotCells - 1) / kTotCells;
-  if ((size_t)nb * 12 > s->scratch_len) return cudaErrorInvalidValue;
+cudaError_t launch_totals_with(rt_state *s, double *partial, int64_t cpb, double *d_out16) {
+  const int64_t nb = (s->n_cells + cpb - 1) / cpb;
   const void *I = s->d_I[s->cur];
   const double coc = s->params.c / s->params.cbar, icb = 1.0 / s->params.cbar;
   if (s->precision == RT_FP32)
     totals_partial_kernel<float><<<(unsigned)nb, kThreads, 0, s->stream>>>(
         (const float *)I, s->d_dir64, s->d_wt64, s->d_volume, s->d_gd, s->d_ext, s->n_cells,
-        s->n_angles, s->row_stride, coc, icb, s->d_scratch);
+        s->n_angles, s->row_stride, cpb, coc, icb, partial);
   else
     totals_partial_kernel<double><<<(unsigned)nb, kThreads, 0, s->stream>>>(
         (const double *)I, s->d_dir64, s->d_wt64, s->d_volume, s->d_gd, s->d_ext, s->n_cells,
-        s->n_angles, s->row_stride, coc, icb, s->d_scratch);
-  totals_final_kernel<<<1, 32, 0, s->stream>>>(s->d_scratch, nb, d_out16);
+        s->n_angles, s->row_stride, cpb, coc, icb, partial);
+  totals_final_kernel<<<1, 32, 0, s->stream>>>(partial, nb, d_out16);
   s->launches += 2;
   return cudaGetLastError();
 }
 
+cudaError_t launch_totals(rt_state *s, double *d_out16) {
+  const int64_t nb = (s->n_cells + kTotCells - 1) / kTotCells;
+  if ((size_t)nb * 12 > s->scratch_len) return cudaErrorInvalidValue;
+  return launch_totals_with(s, s->d_scratch, kTotCells, d_out16);
+}
+
 int64_t totals_scratch_len(int64_t n_cells) { return ((n_cells + kTotCells - 1) / kTotCells) * 12; }
+
+cudaError_t launch_gas_in(rt_state *s, const double *e, const double *m) {
+  const unsigned g = (unsigned)((s->n_cells + kThreads - 1) / kThreads);
+  gas_in_kernel<<<g, kThreads, 0, s->stream>>>(e, m, s->d_cell_of, s->n_cells, s->d_gd);
+  s->launches++;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gas_out(rt_state *s, double *e, double *m, double *ext) {
   gas_out_kernel<<<(unsigned)((s->n_cells + kThreads - 1) / kThreads), kThreads, 0, s->stream>>>(

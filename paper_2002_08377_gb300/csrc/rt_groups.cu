@@ -314,18 +314,26 @@ __global__ void __launch_bounds__(kThreads) group_source_kernel(const GroupArgs<
     for (int t = 0; t < NT; ++t)
       if (L.q[t] < a.A) {
         const R Is = is[i][t];
-        R In;
+        R In, dI;  // dI: the change I* - I' the gas receives (see the tile kernel)
         if (kind == RT_CELL_BOUNDARY) {
           In = fma(-cq[lc].f, Is - I0row[L.q[t]], Is);
+          dI = sizeof(R) == 8 ? cq[lc].f * (Is - I0row[L.q[t]]) : Is - In;
         } else {
           // I' = (I* Gamma^3 + q) / (Gamma^3 (1 + x Gamma))
           const R Gm = R(1) - fma(bx, L.nx[t], fma(by, L.ny[t], bz * L.nz[t]));
           const R G3 = Gm * Gm * Gm;
           const int j = L.g[t];
-          In = fma(Is, G3, cq[lc].q[j]) * rcp(G3 * fma(cq[lc].x[j], Gm, R(1)));
+          if constexpr (sizeof(R) == 8) {
+            const R xg = cq[lc].x[j] * Gm, r = rcp(G3 * (xg + R(1))), tI = Is * G3;
+            In = (tI + cq[lc].q[j]) * r;
+            dI = fma(tI, xg, -cq[lc].q[j]) * r;
+          } else {
+            In = fma(Is, G3, cq[lc].q[j]) * rcp(G3 * fma(cq[lc].x[j], Gm, R(1)));
+            dI = Is - In;
+          }
         }
         a.I[(size_t)c * a.A + L.q[t]] = In;
-        const R dw = L.w[t] * (Is - In);
+        const R dw = L.w[t] * dI;
         de += dw;
         dfx = fma(L.nx[t], dw, dfx);
         dfy = fma(L.ny[t], dw, dfy);
@@ -535,7 +543,13 @@ __global__ void __launch_bounds__(step::NT, sizeof(R) == 4 && M::PPT <= 6 ? 3 : 
   }
 
   // ---------------- phase C: new intensities and the radiation change
+  // The change I* - I' the gas receives: float states take the difference
+  // of the stored intensities (exact energy bookkeeping in float), double
+  // states the source term itself (rounding relative to the change), as the
+  // grey step kernel does.
   R na[PPT], nb[PPT];
+  constexpr int ND = sizeof(R) == 8 ? PPT : 1;
+  R da[ND], db[ND];
   if (kind == RT_CELL_BOUNDARY) {
     const double2 ax = a.aux[c];
     const R f = R((ax.x <= a.dt) ? 1.0 : a.dt / ax.x);
@@ -545,6 +559,10 @@ __global__ void __launch_bounds__(step::NT, sizeof(R) == 4 && M::PPT <= 6 ? 3 : 
     for (int j = 0; j < PPT; ++j) {
       na[j] = fma(-f, Ia[j] - tx[j], Ia[j]);
       nb[j] = fma(-f, Ib[j] - ty[j], Ib[j]);
+      if constexpr (sizeof(R) == 8) {
+        da[j] = f * (Ia[j] - tx[j]);
+        db[j] = f * (Ib[j] - ty[j]);
+      }
     }
   } else {
     // I' = (I* Gamma^3 + q) / (Gamma^3 (1 + x Gamma)); emitters: x -> dt cbar
@@ -571,10 +589,22 @@ __global__ void __launch_bounds__(step::NT, sizeof(R) == 4 && M::PPT <= 6 ? 3 : 
       const R bn = fma(vxc, nx[j], fma(vyc, ny[j], vzc * nz[j]));
       const V Gv = mk(R(1) - bn, R(1) + bn);
       const V G3 = pmul(pmul(Gv, Gv), Gv);
-      const V n = pmul(pfma(mk(Ia[j], Ib[j]), G3, mk(qg, qg)),
-                       step::prcp<R>(pmul(G3, pfma(mk(xg, xg), Gv, one))));
-      na[j] = n.x;
-      nb[j] = n.y;
+      if constexpr (sizeof(R) == 8) {
+        const V XG = pmul(mk(xg, xg), Gv);
+        const V r = step::prcp<R>(pmul(G3, padd(XG, one)));
+        const V t = pmul(mk(Ia[j], Ib[j]), G3);
+        const V n = pmul(padd(t, mk(qg, qg)), r);
+        const V d = pmul(pfma(t, XG, mk(-qg, -qg)), r);
+        na[j] = n.x;
+        nb[j] = n.y;
+        da[j] = d.x;
+        db[j] = d.y;
+      } else {
+        const V n = pmul(pfma(mk(Ia[j], Ib[j]), G3, mk(qg, qg)),
+                         step::prcp<R>(pmul(G3, pfma(mk(xg, xg), Gv, one))));
+        na[j] = n.x;
+        nb[j] = n.y;
+      }
     }
   }
   if (live) M::store(a.I + (size_t)c * a.A, sub, na, nb, np);
@@ -583,7 +613,11 @@ __global__ void __launch_bounds__(step::NT, sizeof(R) == 4 && M::PPT <= 6 ? 3 : 
 #pragma unroll
   for (int j = 0; j < PPT; ++j)
     if (M::FULL || j < np) {
-      const V d = pmul(W2[M::pair(j, sub)], psub(mk(Ia[j], Ib[j]), mk(na[j], nb[j])));
+      V d;
+      if constexpr (sizeof(R) == 8)
+        d = pmul(W2[M::pair(j, sub)], mk(da[j], db[j]));
+      else
+        d = pmul(W2[M::pair(j, sub)], psub(mk(Ia[j], Ib[j]), mk(na[j], nb[j])));
       dev = padd(dev, d);
       const R df = d.x - d.y;  // the antipode has direction -n
       dfx = fma(nx[j], df, dfx);

@@ -59,6 +59,21 @@ struct alignas(32) GasDyn {
   double e, mx, my, mz;
 };
 
+// Gas dynamics (rt_hydro.cu): one record per face (caller face order) and
+// one per directed slot (internal slot order).
+struct HydroFace {
+  int32_t i, j;        // internal cells: first (left) and second (right)
+  double area;
+  double n[3];         // unit normal, i -> j
+  double oi[3], oj[3]; // face centroid minus the centroid of i and of j' (j's image across the face)
+};
+struct HydroSlot {
+  double own[3], nbr[3];  // face centroid minus the cell's / the neighbour image's centroid
+  double area;
+  double sign;            // +1: the cell is the face's first cell, -1: its second
+  int64_t face;           // caller face index (into the face fluxes)
+};
+
 template <typename R> struct StepArgs {
   int64_t n_cells;
   int32_t n_angles, half;
@@ -218,6 +233,10 @@ struct rt_state {
   void *d_adj[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double *d_adj_ws = nullptr;     // [14 N] adjoint per-cell work (internal order)
   double *d_adj_stage = nullptr;  // [10 N] host-path staging of per-cell vectors
+  // gas dynamics (params.hydro): face and slot records, work area
+  rt::HydroFace *d_hface = nullptr;
+  rt::HydroSlot *d_hslot = nullptr;
+  double *d_hwork = nullptr;
   double *d_scratch = nullptr;  // reduction partials
   size_t scratch_len = 0;
   double *d_out16 = nullptr;
@@ -248,6 +267,19 @@ cudaError_t launch_step_vl(rt_state *s, double dt);
 // Double states: fills d_uface (allocates it on first use).
 cudaError_t build_uface(rt_state *s);
 
+// A CUDA driver function by name (through the runtime's entry-point query,
+// so the library does not link the driver library itself), or NULL.
+void *driver_fn(const char *name);
+// Identifier of the current context (unique for the process), 0 if unknown.
+unsigned long long current_context_id();
+
+// gas dynamics (rt_hydro.cu)
+int hydro_setup(rt_state *s, const rt_mesh_desc *m);
+cudaError_t launch_hydro_step(rt_state *s, double dt, int order);
+cudaError_t launch_hydro_dt(rt_state *s, double cfl, double *dt);
+cudaError_t launch_density_out(rt_state *s, double *rho);
+double *hydro_kmass(rt_state *s);  // [N][3] opacities per unit mass, internal order
+
 // auxiliary kernels (rt_aux.cu)
 // caller order <-> internal order; the internal rows are `stride` reals apart
 cudaError_t launch_permute_in(rt_state *s, const void *src, void *dst, int stride);
@@ -265,7 +297,14 @@ cudaError_t launch_inv_vol(rt_state *s);
 cudaError_t launch_opacity_refresh(rt_state *s);
 cudaError_t launch_moments(rt_state *s, double *E, double *F, double *P);
 cudaError_t launch_totals(rt_state *s, double *d_out16);
+// the same sums with the per-block partials in `partial` (room for
+// ceil(n_cells / cpb) x 12 doubles), blocks of cpb >= 1 cells; rt_totals
+// takes cpb = totals_block_cells
+constexpr int64_t totals_block_cells = 64;
+cudaError_t launch_totals_with(rt_state *s, double *partial, int64_t cpb, double *d_out16);
 cudaError_t launch_gas_out(rt_state *s, double *e, double *m, double *ext);
+// caller-order device (e, m) into the internal gas records
+cudaError_t launch_gas_in(rt_state *s, const double *e, const double *m);
 cudaError_t launch_cellv(rt_state *s);
 
 // adjoint (rt_adjoint.cu): device pointers, caller order

@@ -24,10 +24,11 @@
 //   A  all threads: transport over the cell's faces in slot order (no
 //      atomics, deterministic), comoving weights and the angular sums of
 //      Eq. (Jcom); each cell's 8 lanes reduce with shuffles;
-//   B  the gas temperature quartic, in double with one lane per cell in the
-//      first CPB / 32 warps, between two block barriers (double states, and
-//      float states by default); float states with float_quartic = 1 solve
-//      it in float in all 8 lanes of the cell instead (no barrier);
+//   B  the gas temperature quartic, between two block barriers: double
+//      states solve it in double with one lane per cell in the first
+//      CPB / 32 warps; float states find the float root in all 8 lanes of
+//      the cell and one lane per cell refines it by Newton in double (with
+//      float_quartic = 1 the float root is final: no barrier);
 //   C  all threads: new intensities, store, radiation change per cell;
 //   D  after a block barrier, one lane per cell (first CPB / 32 warps): gas energy /
 //      momentum (or tally) update in double (Eqs. gas1, gas2).
@@ -47,6 +48,7 @@ using namespace step;
 template <typename R> struct Shared {
   R sI[CPB], sG[CPB], s1[CPB];  // the sums of Eq. (Jcom) and sum w~/(1+x), unnormalised
   R q[CPB];                     // dt cbar rho (kP B + kS J) per interior cell
+  float qa[CPB], qg[CPB], qT[CPB];  // float states: alpha, g and the float temperature root
   R dE[CPB], dF[3][CPB];        // sum w (I* - I') and sum w n (I* - I')
   unsigned bad[CPB];
 };
@@ -97,34 +99,61 @@ __device__ __forceinline__ double source_q(const StepArgs<R> &a, const GasStatic
   return fma(dPT, B, dS * J);
 }
 
-// The same in float for float states, from the float coefficients and the
-// internal energy e - rho v^2 / 2 that the previous gas update left in
-// cellv; coefficients or an emission term outside float range fall back to
-// the double solve.
+// The temperature equation of a float state's cell in float: the
+// coefficients of source_q from the float copies of the cell's opacities and
+// the float angular sums (alpha multiplies T^(4 + beta_P) T_ref^-beta_P),
+// with rU = 1 / D and dP, dS = dt cbar rho kappa_P, kappa_s.
+struct QuarticF {
+  float alpha, gq, rU, dP, dS;
+};
+__device__ __forceinline__ QuarticF float_coeffs(const StepArgs<float> &a, float rkP, float rkJ,
+                                                 float rkS, float eint, float SI, float SG,
+                                                 float S1) {
+  QuarticF k;
+  const float dJ = a.k_dcr_f * rkJ;
+  k.dP = a.k_dcr_f * rkP;
+  k.dS = a.k_dcr_f * rkS;
+  k.rU = rcp(fmaf(dJ, SG, S1));
+  k.alpha = a.k_alpha_f * rkP * S1 * k.rU;
+  k.gq = eint + a.k_g_f * rkJ * SI * k.rU;
+  if (a.beta_P_f != 0.0f) k.alpha *= a.tref_mbP_f;
+  return k;
+}
+// Float root of the cell's equation from the pre-step temperature (returns
+// 1 if Newton did not converge).
+__device__ __forceinline__ int float_root(const StepArgs<float> &a, const QuarticF &k, float rcv,
+                                          float eint, float *T) {
+  if (a.beta_P_f == 0.0f)
+    return quartic_root(k.alpha, rcv, k.gq, eint * rcp(rcv), 1e-7f, a.newton_max_iter, T);
+  return power_root(k.alpha, 4.0f + a.beta_P_f, rcv, k.gq, eint * rcp(rcv), 1e-7f,
+                    a.newton_max_iter, T);
+}
+// The emission term q = dt cbar rho (kP(T) B(T) + kS J~) in float.
+__device__ __forceinline__ float float_q(const StepArgs<float> &a, const QuarticF &k, float T,
+                                         float SI, float SG) {
+  float dPT = k.dP;  // dP with kappa_P at T^{n+1}
+  if (a.beta_P_f != 0.0f) dPT = k.dP * powf(T / a.T_ref_f, a.beta_P_f);
+  const float B = a.a_rad_4pi_f * (T * T) * (T * T);
+  const float J = fmaf(dPT * B, SG, SI) * k.rU;
+  return fmaf(dPT, B, k.dS * J);
+}
+
+// The same as source_q in float for float states (float_quartic = 1), from
+// the float coefficients and the internal energy e - rho v^2 / 2 that the
+// previous gas update left in cellv; coefficients or an emission term
+// outside float range fall back to the double solve.
 __device__ __forceinline__ float source_q_float(const StepArgs<float> &a, int64_t c, float rkP,
                                                 float rkJ, float rkS, float rcv, float eint,
                                                 float SI, float SG, float S1, unsigned &bad) {
-  const float dJ = a.k_dcr_f * rkJ, dP = a.k_dcr_f * rkP, dS = a.k_dcr_f * rkS;
-  const float rU = rcp(fmaf(dJ, SG, S1));
-  const float alpha = a.k_alpha_f * rkP * S1 * rU;
-  const float gq = eint + a.k_g_f * rkJ * SI * rU;
-  if (!(gq >= 0.0f) || !(alpha >= 0.0f)) {
+  const QuarticF k = float_coeffs(a, rkP, rkJ, rkS, eint, SI, SG, S1);
+  if (!(k.gq >= 0.0f) || !(k.alpha >= 0.0f)) {
     bad |= ST_NONFINITE;
     return 0.0f;
   }
-  if (isfinite(alpha) && isfinite(gq)) {
-    float T, dPT = dP;  // dPT: dP with kappa_P at T^{n+1}
-    int nc;
-    if (a.beta_P_f == 0.0f) {
-      nc = quartic_root(alpha, rcv, gq, eint * rcp(rcv), 1e-7f, a.newton_max_iter, &T);
-    } else {
-      nc = power_root(alpha * a.tref_mbP_f, 4.0f + a.beta_P_f, rcv, gq, eint * rcp(rcv), 1e-7f,
-                      a.newton_max_iter, &T);
-      dPT = dP * powf(T / a.T_ref_f, a.beta_P_f);
-    }
-    const float B = a.a_rad_4pi_f * (T * T) * (T * T);
-    const float J = fmaf(dPT * B, SG, SI) * rU;
-    const float q = fmaf(dPT, B, dS * J);
+  if (isfinite(k.alpha) && isfinite(k.gq)) {
+    float T;
+    const int nc = float_root(a, k, rcv, eint, &T);
+    const float q = float_q(a, k, T, SI, SG);
     if (isfinite(q)) {
       if (nc) bad |= ST_NONCONV;
       return q;
@@ -133,12 +162,57 @@ __device__ __forceinline__ float source_q_float(const StepArgs<float> &a, int64_
   return (float)source_q(a, a.gs[c], a.gd[c], (double)SI, (double)SG, (double)S1, bad);
 }
 
+// Newton in double on alpha T^k + beta T = g (k = 4 + beta_P) from the float
+// root T: STEPS steps, each with f and f' in double and the quotient f / f'
+// in float.  From a float-accurate start (relative error e0 of a few float
+// ulp, ~1e-7) a step leaves about e0 (float epsilon + e0), ~1e-13: one step
+// is below the float rounding of the q it feeds, two reach double precision.
+template <int STEPS = 1>
+__device__ __forceinline__ double refine_root(double alpha, double k, double beta, double g,
+                                              double T) {
+#pragma unroll
+  for (int it = 0; it < STEPS; ++it) {
+    const double Tk1 = k == 4.0 ? (T * T) * T : pow(T, k - 1.0);
+    const double f = fma(alpha * Tk1, T, fma(beta, T, -g));
+    const double fp = fma(k * alpha, Tk1, beta);
+    T -= (double)((float)f * rcp((float)fp));
+  }
+  return T;
+}
+
+// q of an interior cell of a float state (float_quartic = 0), one lane per
+// cell: the float coefficients and root as in source_q_float, the root
+// refined in double by refine_root, q in float from it; where a float value
+// is not finite or the float Newton did not converge, the double solve of
+// source_q.
+__device__ __forceinline__ float source_q_refined(const StepArgs<float> &a, const GasStatic &gr,
+                                                  const GasDyn &gd, float SI, float SG, float S1,
+                                                  float eint, unsigned &bad) {
+  const QuarticF k = float_coeffs(a, gr.frkP, gr.frkJ, gr.frkS, eint, SI, SG, S1);
+  if (!(k.gq >= 0.0f) || !(k.alpha >= 0.0f)) {
+    bad |= ST_NONFINITE;
+    return 0.0f;
+  }
+  float Tf;
+  if (isfinite(k.alpha) && isfinite(k.gq) && !float_root(a, k, gr.frcv, eint, &Tf) &&
+      isfinite(Tf)) {
+    const double T = refine_root((double)k.alpha, 4.0 + a.beta_P, gr.rcv, (double)k.gq, (double)Tf);
+    const float q = float_q(a, k, (float)T, SI, SG);
+    if (isfinite(q)) return q;
+  }
+  return (float)source_q(a, gr, gd, (double)SI, (double)SG, (double)S1, bad);
+}
+
 // One block of CPB cells: phases A-D (see the top of the file).  STAGED:
 // the caller has started the copies of the tile's slots and gas records into
 // `stage`, and the face loop waits for them; otherwise slots are read from
 // global memory and the lane-per-cell threads copy the gas records into
 // `gas` themselves.
-template <typename R, typename M, bool MOVING, bool STAGED>
+// How float states solve the temperature equation (phase B): chosen at run
+// time from StepArgs::float_quartic, or fixed by the kernel instantiation.
+enum : int { QM_RUNTIME = 0, QM_FLOAT = 1, QM_REFINE = 2 };
+
+template <typename R, typename M, bool MOVING, bool STAGED, int QM = QM_RUNTIME>
 __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t tile, Shared<R> &sh,
                                           SharedGas *gas, const StageView &stage) {
   using V = pair_t<R>;
@@ -272,18 +346,96 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   const GasStatic *gs_s = STAGED ? stage.gas->gs : gas->gs;
   const GasDyn *gd_s = STAGED ? stage.gas->gd : gas->gd;
   bool lane_solve = false;  // float states with float_quartic: in float, in every lane
-  if constexpr (sizeof(R) == 4) lane_solve = a.float_quartic != 0;
+  if constexpr (sizeof(R) == 4)
+    lane_solve = QM == QM_FLOAT || (QM == QM_RUNTIME && a.float_quartic != 0);
   if (lane_solve) {
     // every lane of the cell solves the cell's quartic in float (the sums
     // are already in all 8 lanes), no block barrier
     if constexpr (sizeof(R) == 4)
       if (kind == RT_CELL_INTERIOR)
         q = source_q_float(a, c, fkP, fkJ, fkS, fcv, eint, sI, sG, s1, bad);
+  } else if constexpr (sizeof(R) == 4 && QM == QM_REFINE) {
+    // float states (default, staged kernels): every lane of the cell finds
+    // the float root from the float coefficients (no barrier); one lane per
+    // cell then refines it by Newton in double (the FP64 temperature solve)
+    // and forms q, or, where the float solve failed, runs the whole double
+    // solve of source_q
+    float Tf = 0.0f;
+    unsigned fst = 0;  // 0: float root, 1: solve in double, 2: non-finite coefficients
+    float qa = 0.0f, qg = 0.0f;
+    if (kind == RT_CELL_INTERIOR) {
+      const QuarticF kc = float_coeffs(a, fkP, fkJ, fkS, eint, sI, sG, s1);
+      qa = kc.alpha;
+      qg = kc.gq;
+      if (!(qg >= 0.0f) || !(qa >= 0.0f))
+        fst = 2;
+      else if (!isfinite(qa) || !isfinite(qg) || float_root(a, kc, fcv, eint, &Tf) ||
+               !isfinite(Tf))
+        fst = 1;
+    }
+    if (sub == 0) {
+      sh.sI[lc] = sI;
+      sh.sG[lc] = sG;
+      sh.s1[lc] = s1;
+      sh.qa[lc] = qa;
+      sh.qg[lc] = qg;
+      sh.qT[lc] = Tf;
+      sh.bad[lc] = fst;
+    }
+    __syncthreads();
+    if (lpc) {
+      float ql = 0.0f;
+      unsigned bl = 0;
+      if (cl < a.n_cells && a.kind[cl] == RT_CELL_INTERIOR) {
+        const unsigned st = sh.bad[lp];
+        const GasStatic &gr = gs_s[lp];
+        if (st == 0) {
+          const double T = refine_root((double)sh.qa[lp], 4.0 + a.beta_P, gr.rcv,
+                                       (double)sh.qg[lp], (double)sh.qT[lp]);
+          const QuarticF k = float_coeffs(a, gr.frkP, gr.frkJ, gr.frkS, 0.0f, sh.sI[lp],
+                                          sh.sG[lp], sh.s1[lp]);
+          ql = float_q(a, k, (float)T, sh.sI[lp], sh.sG[lp]);
+        }
+        if (st == 2) {
+          bl = ST_NONFINITE;
+        } else if (st == 1 || !isfinite(ql)) {
+          ql = (float)source_q(a, gr, gd_s[lp], (double)sh.sI[lp], (double)sh.sG[lp],
+                               (double)sh.s1[lp], bl);
+        }
+      }
+      sh.q[lp] = ql;
+      sh.bad[lp] = bl;
+    }
+    __syncthreads();
+    q = sh.q[lc];
+    bad = sh.bad[lc];
+  } else if constexpr (sizeof(R) == 4) {
+    // float states (default, pair-map kernels): one lane per cell finds the float root from
+    // the float coefficients, refines it by Newton in double (the FP64
+    // temperature solve) and forms q from it; where the float solve fails it
+    // runs the whole double solve of source_q
+    if (sub == 0) {
+      sh.sI[lc] = sI;
+      sh.sG[lc] = sG;
+      sh.s1[lc] = s1;
+    }
+    if (!STAGED && lpc) cp_async_wait_all();
+    __syncthreads();
+    if (lpc) {
+      float ql = 0.0f;
+      unsigned bl = 0;
+      if (cl < a.n_cells && a.kind[cl] == RT_CELL_INTERIOR)
+        ql = source_q_refined(a, gs_s[lp], gd_s[lp], sh.sI[lp], sh.sG[lp], sh.s1[lp],
+                              a.cellv[4 * cl + 3], bl);
+      sh.q[lp] = ql;
+      sh.bad[lp] = bl;
+    }
+    __syncthreads();
+    q = sh.q[lc];
+    bad = sh.bad[lc];
   } else {
-    // the quartic in double (double states, and float states by default:
-    // their angular sums are float partials, the solve and its
-    // coefficients double), one lane per cell, so the FP64 work is issued
-    // by one warp for 32 cells
+    // double states: the quartic in double, one lane per cell, so the FP64
+    // work is issued by one warp for 32 cells
     if (sub == 0) {
       sh.sI[lc] = sI;
       sh.sG[lc] = sG;
@@ -311,8 +463,16 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
   {
     // boundary: I' = I* - (I* - I0) f; interior: I~' = (I~ + q Gamma) / (1 + x Gamma),
     // i.e. I' = (I* + q / Gamma^3) / (1 + x Gamma); emitter: the same with
-    // x -> dt cbar (rho kappa)_src and q -> that rate times I_src (Sec. 2.5)
+    // x -> dt cbar (rho kappa)_src and q -> that rate times I_src (Sec. 2.5).
+    // The radiation change I* - I' that the gas receives: float states take
+    // the difference of the stored intensities (the energy bookkeeping is
+    // then exact in float); double states take the source term itself,
+    // (I* Gamma^3 x Gamma - q) / (Gamma^3 (1 + x Gamma)) and f (I* - I0),
+    // whose rounding is relative to the change, not to I* (optically thin
+    // cells change I by a small fraction per step).
     R na[PPT], nb[PPT];
+    constexpr int ND = sizeof(R) == 8 ? PPT : 1;
+    R da[ND], db[ND];  // double states: the change I* - I'
     if (kind == RT_CELL_BOUNDARY) {
       const double2 ax = a.aux[c];
       const R f = R((ax.x <= a.dt) ? 1.0 : a.dt / ax.x);
@@ -322,6 +482,10 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
       for (int j = 0; j < PPT; ++j) {
         na[j] = fma(-f, Ia[j] - tx[j], Ia[j]);
         nb[j] = fma(-f, Ib[j] - ty[j], Ib[j]);
+        if constexpr (sizeof(R) == 8) {
+          da[j] = f * (Ia[j] - tx[j]);
+          db[j] = f * (Ib[j] - ty[j]);
+        }
       }
     } else {
       R qq, xx = xs;
@@ -350,9 +514,21 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
         const R bn = fma(vxc, ux, fma(vyc, uy, vzc * uz));
         const V G = mk(R(1) - bn, R(1) + bn);
         const V G3 = pmul(pmul(G, G), G);
-        const V n = pmul(pfma(mk(Ia[j], Ib[j]), G3, QQ), prcp<R>(pmul(G3, pfma(XX, G, one))));
-        na[j] = n.x;
-        nb[j] = n.y;
+        if constexpr (sizeof(R) == 8) {
+          const V XG = pmul(XX, G);
+          const V r = prcp<R>(pmul(G3, padd(XG, one)));
+          const V t = pmul(mk(Ia[j], Ib[j]), G3);
+          const V n = pmul(padd(t, QQ), r);
+          const V d = pmul(pfma(t, XG, mk(-qq, -qq)), r);
+          na[j] = n.x;
+          nb[j] = n.y;
+          da[j] = d.x;
+          db[j] = d.y;
+        } else {
+          const V n = pmul(pfma(mk(Ia[j], Ib[j]), G3, QQ), prcp<R>(pmul(G3, pfma(XX, G, one))));
+          na[j] = n.x;
+          nb[j] = n.y;
+        }
       }
     }
     if (live) M::store(a.I_out + (size_t)c * RS, sub, na, nb, np);
@@ -361,7 +537,11 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
     for (int j = 0; j < PPT; ++j) {
       if (M::FULL || j < np) {
         const int p = M::pair(j, sub);
-        const V d = pmul(W2[p], psub(mk(Ia[j], Ib[j]), mk(na[j], nb[j])));
+        V d;
+        if constexpr (sizeof(R) == 8)
+          d = pmul(W2[p], mk(da[j], db[j]));
+        else
+          d = pmul(W2[p], psub(mk(Ia[j], Ib[j]), mk(na[j], nb[j])));
         dev = padd(dev, d);
         const R df = d.x - d.y;  // the antipode has direction -n
         R ux, uy, uz;
@@ -373,7 +553,8 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
     }
     de = dev.x + dev.y;
     // a non-finite new intensity makes its weighted change, and so de,
-    // non-finite (the weights are positive)
+    // non-finite (the weights are positive; the double states' change has
+    // the same factors as the intensity)
     if (!isfinite(de)) nonfinite = ST_NONFINITE;
   }
   de = cell_sum(de);
@@ -458,14 +639,14 @@ __global__ void __launch_bounds__(NT, min_blocks<R, M::PPT>()) step_kernel(const
 // Float kernel with the QuadMap: the block first starts the copies of its
 // slots and gas records into shared memory, then loads its own rows and
 // directions while they land (tile_step waits before the face loop).
-template <typename M, bool MOVING>
+template <typename M, bool MOVING, int QM>
 __global__ void __launch_bounds__(NT, min_blocks<float, M::PPT>())
     step_kernel_staged(const StepArgs<float> a, int cap) {
   __shared__ Shared<float> sh;
   extern __shared__ __align__(128) unsigned char dyn[];
   const StageView v = stage_at(dyn, cap, MOVING);
   issue_stage<MOVING>(a, blockIdx.x, v);
-  tile_step<float, M, MOVING, true>(a, blockIdx.x, sh, nullptr, v);
+  tile_step<float, M, MOVING, true, QM>(a, blockIdx.x, sh, nullptr, v);
 }
 
 // Fills the kernel arguments and launches one step with pair map M.
@@ -536,7 +717,12 @@ cudaError_t launch_t(rt_state *s, double dt, const StepIO &io) {
   const unsigned blocks = (unsigned)((s->n_cells + CPB - 1) / CPB);
   if constexpr (STAGED) {
     const int cap = stage_cap(s->max_block_slots);
-    step_kernel_staged<M, MOVING><<<blocks, NT, stage_bytes(cap, MOVING), s->stream>>>(a, cap);
+    if (a.float_quartic)
+      step_kernel_staged<M, MOVING, QM_FLOAT>
+          <<<blocks, NT, stage_bytes(cap, MOVING), s->stream>>>(a, cap);
+    else
+      step_kernel_staged<M, MOVING, QM_REFINE>
+          <<<blocks, NT, stage_bytes(cap, MOVING), s->stream>>>(a, cap);
   } else {
     step_kernel<R, M, MOVING><<<blocks, NT, 0, s->stream>>>(a);
   }

@@ -44,7 +44,7 @@ __device__ __forceinline__ double2 psub(double2 a, double2 b) {
 // arguments are Gamma^k (1 + x Gamma) and 1 + dt cbar rho kappa S_G, normal
 // floats, so flushing subnormals changes nothing).  Double: that estimate
 // refined by two Newton steps r <- r (2 - x r) (about 1 ulp) where x and
-// 1/x are normal floats (|x| in [2^-125, 2^125]); any other x (physical
+// 1/x are normal floats (|x| in [2^-125, 2^126)); any other x (physical
 // units make dt/V or cbar A far from 1) takes the IEEE double division.
 __device__ __forceinline__ float rcp(float x) {
   float r;
@@ -52,8 +52,10 @@ __device__ __forceinline__ float rcp(float x) {
   return r;
 }
 __device__ __forceinline__ double rcp(double x) {
-  const double ax = fabs(x);
-  if (!(ax >= 0x1p-125 && ax <= 0x1p125)) return 1.0 / x;
+  // |x| in [2^-125, 2^126) <=> biased exponent in [898, 1149), tested on the
+  // integer pipe (the FP64 pipe is the double kernels' bottleneck)
+  const unsigned ex = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
+  if (ex - 898u >= 251u) return 1.0 / x;
   double r = (double)rcp((float)x);
   r = fma(r, fma(-x, r, 1.0), r);
   r = fma(r, fma(-x, r, 1.0), r);

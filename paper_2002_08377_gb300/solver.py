@@ -25,7 +25,8 @@ class RTSolver:
 
     precision: "fp32" (float intensities/transport, double quartic and
     exchange) or "fp64".  float_quartic: 1 makes an fp32 state solve the
-    temperature quartic in float instead (faster, float-rounded T).
+    temperature quartic in float instead (faster, float-rounded T).  hydro: 1
+    lets the state evolve the gas dynamics too (hydro_step, radhydro_step).
     integrator: 0 first-order upwind step, 1 van Leer step with limited
     linear reconstruction (needs mesh.face_offset()).  plain_launches: 1
     turns off the CUDA-graph replay of run() / launch() (same kernels, same
@@ -35,7 +36,7 @@ class RTSolver:
     def __init__(self, mesh, dirs, weights, *, cbar, c, a_rad=1.0, gamma_gas=5.0 / 3.0,
                  r_gas=1.0, cfl=0.3, precision="fp32", newton_max_iter=64, integrator=0, boost=0, gcl=0,
                  beta_P=0.0, beta_J=0.0, T_ref=1.0, n_groups=1, group_w=None,
-                 plain_launches=0, float_quartic=0, stream=None):
+                 plain_launches=0, float_quartic=0, hydro=0, stream=None):
         if torch is None or not torch.cuda.is_available():
             raise RuntimeError("RTSolver needs a CUDA device (no CPU fallback exists)")
         self.lib = capi.load()
@@ -72,12 +73,12 @@ class RTSolver:
         md.cell_face_idx = ptr(mesh.cell_face_idx, np.int32)
         md.angle_dir = ptr(dirs, np.float64)
         md.angle_w = ptr(weights, np.float64)
-        if integrator == capi.RT_VAN_LEER:
+        if integrator == capi.RT_VAN_LEER or hydro:
             md.face_offset = ptr(mesh.face_offset(), np.float64)
         pr = capi.Params(cbar, c, a_rad, gamma_gas, r_gas, cfl,
                          capi.RT_FP32 if precision == "fp32" else capi.RT_FP64, newton_max_iter,
                          int(integrator), int(boost), int(gcl), int(plain_launches), float(beta_P),
-                         float(beta_J), float(T_ref), int(float_quartic), 0)
+                         float(beta_J), float(T_ref), int(float_quartic), int(hydro))
         st = ctypes.c_void_p()
         code = self.lib.rt_create(ctypes.byref(md), ctypes.byref(pr),
                                   ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(st))
@@ -182,6 +183,39 @@ class RTSolver:
         E, F, P = np.empty(self.N), np.empty((self.N, 3)), np.empty((self.N, 6))
         self._check(self.lib.rt_moments(self.state, E.ctypes.data, F.ctypes.data, P.ctypes.data, 0))
         return E, F, P
+
+    def set_gas_energy(self, e, m):
+        """Replace only the evolving gas (e[N], m[N][3], caller order): CUDA
+        tensors stay on the device, anything else goes through the host."""
+        if torch.is_tensor(e) and e.is_cuda:
+            e = e.to(torch.float64).contiguous()
+            m = m.to(torch.float64).contiguous()
+            self._check(self.lib.rt_set_gas_energy(self.state, ctypes.c_void_p(e.data_ptr()),
+                                                   ctypes.c_void_p(m.data_ptr()), 1))
+            return
+        e, m = _c(e, np.float64), _c(m, np.float64)
+        self._check(self.lib.rt_set_gas_energy(self.state, e.ctypes.data, m.ctypes.data, 0))
+
+    # -------------------------------------------------------------- gas dynamics
+    def hydro_dt(self, cfl=0.3):
+        dt = ctypes.c_double()
+        self._check(self.lib.rt_hydro_dt(self.state, float(cfl), ctypes.byref(dt)))
+        return dt.value
+
+    def hydro_step(self, dt, order=2):
+        self._check(self.lib.rt_hydro_step(self.state, float(dt), int(order)))
+
+    def radhydro_step(self, dt, n_sub=1, order=2):
+        """The hydro step over dt, then n_sub radiation steps of dt / n_sub."""
+        used = ctypes.c_double()
+        self._check(self.lib.rt_radhydro_step(self.state, float(dt), int(n_sub), int(order),
+                                              ctypes.byref(used)))
+        return used.value
+
+    def density(self):
+        rho = np.empty(self.N)
+        self._check(self.lib.rt_get_density(self.state, rho.ctypes.data, 0))
+        return rho
 
     def gas_device(self):
         """(e[N], m[N][3]) as float64 CUDA tensors, caller order."""

@@ -118,7 +118,7 @@ def test_create_rejects_bad_params(lib):
     for kw in ({"plain_launches": 2}, {"boost": -1}, {"gcl": 2}, {"integrator": 5},
                {"gcl": 1, "integrator": capi.RT_VAN_LEER}, {"beta_P": float("nan")},
                {"beta_P": -3.5}, {"beta_J": 1.0, "T_ref": 0.0}, {"precision": 7}, {"cfl": 0.0},
-               {"float_quartic": 2}, {"reserved": 1}):
+               {"float_quartic": 2}, {"hydro": 2}, {"hydro": 1, "gcl": 1}):
         assert code(**kw) == capi.RT_ERR_ARG, kw
 
 

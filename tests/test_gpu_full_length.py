@@ -105,6 +105,10 @@ def test_full_size_full_length(name, precision, float_quartic):
     I = g.get_intensity()
     e, m, x = g.gas()
     t1_g = g.totals()
+    if prob.n_cells > 8388608:
+        # beyond the allocation-free totals' limit: refused with RT_ERR_ARG
+        buf = np.empty(16)
+        assert g.lib.rt_totals_noalloc(g.state, buf.ctypes.data) == capi.RT_ERR_ARG
     g.close()
     t1_o = o.totals()
     E_o, _, _ = o.moments()
@@ -112,9 +116,11 @@ def test_full_size_full_length(name, precision, float_quartic):
     E_g = np.asarray(I, np.float64) @ w4
     l1_E = float(np.sum(np.abs(E_g - E_o)) / np.sum(np.abs(E_o)))
     l1_e = float(np.sum(np.abs(e - o.e)) / np.sum(np.abs(o.e)))
-    den = np.maximum(np.abs(o.I), 1e-300)
-    max_I = float(np.max(np.abs(np.asarray(I, np.float64) - o.I) / den))
-    del den
+    rel = np.abs(np.asarray(I, np.float64) - o.I) / np.maximum(np.abs(o.I), 1e-300)
+    worst = np.unravel_index(int(np.argmax(rel)), rel.shape)
+    max_I = float(rel[worst])
+    del rel
+    wc, wa = int(worst[0]), int(worst[1])
     drift_g = abs(t1_g[12] - t0_g[12]) / abs(t0_g[12])
     drift_o = abs(t1_o[12] - t0_o[12]) / abs(t0_o[12])
     interior = prob.kind == 0
@@ -122,7 +128,12 @@ def test_full_size_full_length(name, precision, float_quartic):
     T_err = float(np.max(np.abs(T_g - T_o)[interior] / T_o[interior])) if interior.any() else 0.0
     report(workload=name, precision=precision, float_quartic=float_quartic, cells=prob.n_cells,
            angles=prob.n_angles, steps=steps, max_rel_intensity=max_I, l1_E_r=l1_E, l1_e=l1_e,
-           energy_drift_gpu=drift_g, energy_drift_oracle=drift_o, max_rel_T=T_err)
+           energy_drift_gpu=drift_g, energy_drift_oracle=drift_o, max_rel_T=T_err,
+           worst={"cell": wc, "angle": wa, "kind": int(prob.kind[wc]),
+                  "kappa_P": float(np.ravel(prob.kappa_P)[wc]), "I_oracle": float(o.I[wc, wa]),
+                  "I_gpu": float(I[wc, wa]), "I_max": float(np.abs(o.I).max()),
+                  "T_oracle": float(T_o[wc]), "T_gpu": float(T_g[wc]),
+                  "cell_max_rel_T": int(np.argmax(np.where(interior, np.abs(T_g - T_o) / T_o, 0)))})
     if precision == "fp64":
         assert max_I < FP64_REL, max_I
         assert float(np.max(np.abs(e - o.e) / np.abs(o.e))) < FP64_REL

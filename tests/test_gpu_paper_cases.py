@@ -39,12 +39,12 @@ def solver(prob, precision, **kw):
 
 def axis_diagonal_set():
     """14 directions: the 6 lattice axes and the 8 cube diagonals, ordered
-    so that direction a + 7 is -(direction a); weights 2/21 (axes) and
-    3/28 (diagonals), which sum to one."""
+    so that direction a + 7 is -(direction a); weights 1/12 (axes) and
+    1/16 (diagonals), which sum to one."""
     s = 1.0 / np.sqrt(3.0)
     half = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (s, s, s), (s, s, -s), (s, -s, s), (-s, s, s)]
     d = np.array(half + [tuple(-x for x in v) for v in half], np.float64)
-    w = np.array([2 / 21] * 3 + [3 / 28] * 4, np.float64)
+    w = np.array([1 / 12] * 3 + [1 / 16] * 4, np.float64)
     return d, np.concatenate([w, w])
 
 

@@ -248,17 +248,15 @@ def radhydro_linear_system(dirs, w, k, g, rho0, T0, r_gas, a, c, cbar, kap):
     return M
 
 
-def radwave(N, tau, amp=1e-6, jitter=0.1):
+def radwave_problem(N, tau, amp=1e-6, jitter=0.1, C=1.45e3):
     """The Sec. 3.6 setup in code units: rho0 = T0 = r_gas = 1 (isothermal
     sound speed 1), c = 1.45e3, cbar = c / 100, a = 3 (P_rad = P_gas),
     kappa = tau (optical depth tau over the wavelength, the box length 1),
-    S2 directions, lattice jitter 10 %.  The right-running sound mode of the
-    linear system is laid on the mesh at amplitude 1e-6 and run for one
-    isothermal sound crossing time with radiation subcycled under the hydro
-    step.  Returns (problem, mode eigenvalue, its vector, the oracle after
-    the run, end time)."""
+    S2 directions, lattice jitter 10 %, with the right-running sound mode of
+    the linear system laid on the mesh at amplitude amp.  Returns (problem,
+    mode eigenvalue, its vector).  C = c / c_s (1.45e3 in the paper)."""
     g, rho0, T0, r = 5.0 / 3.0, 1.0, 1.0, 1.0
-    c = 1.45e3
+    c = C  # c / c_s with the isothermal sound speed 1
     cbar, a, kap, k = 1e-2 * c, 3.0, tau, 2 * np.pi
     dirs, w = level_symmetric(2)
     M = radhydro_linear_system(dirs, w, k, g, rho0, T0, r, a, c, cbar, kap)
@@ -276,15 +274,25 @@ def radwave(N, tau, amp=1e-6, jitter=0.1):
     v[:, 0] = part(X[1])
     I = a * T0 ** 4 / (4 * np.pi) + amp * np.real(X[3:][None, :] * ph[:, None])
     prob = gas_problem(mesh, rho, v, rho * r * T, g, dirs, w, a, cbar, c, kap, I, r)
+    return prob, lam[i], X
+
+
+def radwave(N, tau, amp=1e-6, jitter=0.1):
+    """radwave_problem run on the oracle for one isothermal sound crossing
+    time (t = 1), the radiation subcycled under each hydro step (as many
+    Courant steps of the radiation as fit in the gas's Courant step).
+    Returns (problem, mode eigenvalue, its vector, the oracle after the run,
+    end time)."""
+    prob, lam, X = radwave_problem(N, tau, amp, jitter)
     o = oracle.Oracle(prob)
-    t_end = 1.0  # one isothermal sound crossing of the wavelength
+    t_end = 1.0
     dt_rad = o.cfl_dt()
     t = 0.0
     while t < t_end - 1e-14:
         dt = min(o.hydro_dt(0.3), t_end - t)
         assert o.radhydro_step(dt, int(np.ceil(dt / dt_rad))) == oracle.ORC_OK
         t += dt
-    return prob, lam[i], X, o, t_end
+    return prob, lam, X, o, t_end
 
 
 def _radwave_error(N, tau):

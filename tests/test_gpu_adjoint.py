@@ -159,3 +159,46 @@ def test_adjoint_workload_full_size_against_finite_differences(precision):
     fd = (Lp - Lm) / (2 * h)
     ad = float(np.sum(gk * d))
     assert abs(ad - fd) <= 1e-4 * abs(fd), (ad, fd)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_adjoint_gradient_per_cell_against_oracle_differences(precision):
+    """The full-size adjoint workload (64^3 cells, 48 angles, 64 steps,
+    checkpoint every 8): the GPU gradient of the outflow loss, cell by cell,
+    against central differences of the FP64 oracle stored in
+    tests/golden/adjoint_fd_64.json (written by make_adjoint_fd.py, which
+    calls only the oracle): dL/dkappa_a at 32 random interior cells and
+    dL/dI0 at 16 random (cell, angle) entries, each to a relative 1e-4 with a
+    floor of 1e-3 of the largest derivative (FP64).  FP32 gradients carry an
+    absolute error set by float rounding of the 64 reverse steps' sums (each
+    cell's dL/dkappa is a sum of absorption and emission terms of opposite
+    sign, over 48 angles and 64 steps): measured 1.4e-6 of the largest
+    derivative, so its floor is 5e-2 of the largest (an absolute 5e-6 of it,
+    about 80 float ulps); above the floor the relative bar is the same 1e-4."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "adjoint_fd_64.json")
+    gold = json.load(open(path))
+    prob = adjoint(n=gold["n"], steps=gold["steps"])
+    dt = prob.cfl_dt()
+    assert abs(dt / gold["dt"] - 1) < 1e-12
+    g = outflow_weights(prob)
+    L, gk, gI = _autograd(prob, precision, dt, gold["steps"], 8, g)
+    assert abs(L / gold["loss"] - 1) < (1e-12 if precision == "fp64" else 1e-5)
+    floor = 1e-3 if precision == "fp64" else 5e-2
+    fk = gold["max_abs_dL_dkappa"] * floor
+    fi = gold["max_abs_dL_dI0"] * floor
+    rel_k = [abs(gk[e["cell"]] - e["fd"]) / max(abs(e["fd"]), fk) for e in gold["kappa"]]
+    rel_i = [abs(gI[e["cell"], e["angle"]] - e["fd"]) / max(abs(e["fd"]), fi) for e in gold["I0"]]
+    report = os.environ.get("RT_ERROR_REPORT")
+    if report:
+        with open(report, "a") as f:
+            f.write(json.dumps({"case": "adjoint_fd_64_per_cell", "precision": precision,
+                                "floor": floor, "max_rel_dL_dkappa": max(rel_k),
+                                "max_rel_dL_dI0": max(rel_i),
+                                "max_abs_err_over_max_dL_dkappa": max(
+                                    abs(gk[e["cell"]] - e["fd"]) for e in gold["kappa"]) /
+                                gold["max_abs_dL_dkappa"],
+                                "loss_rel": abs(L / gold["loss"] - 1)}) + "\n")
+    assert max(rel_k) <= 1e-4, (max(rel_k), gold["kappa"][int(np.argmax(rel_k))])
+    assert max(rel_i) <= 1e-4, (max(rel_i), gold["I0"][int(np.argmax(rel_i))])

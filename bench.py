@@ -603,6 +603,44 @@ def time_workload(prob, precs, steps, warmup, world, hbm_peak, peak_kind, fp64_p
     return res
 
 
+def radhydro_rate(n, steps, warmup):
+    """The linear-wave box (n^3, S8) with the gas dynamics on (FP32
+    radiation, double hydro): rt_radhydro_step = one van Leer hydro step at
+    the gas Courant step, then the radiation subcycled under it at its own
+    Courant step.  Reports ms per hydro step alone and per radiation-hydro
+    step (hydro + n_sub radiation steps)."""
+    import torch
+    from paper_2002_08377_gb300.inputs import waves
+    from paper_2002_08377_gb300.solver import RTSolver
+    prob = waves(n=n)
+    sol = RTSolver.from_problem(prob, "fp32", hydro=1)
+    dt_rad = prob.cfl_dt()
+    dt = sol.hydro_dt(0.3)
+    n_sub = int(np.ceil(dt / dt_rad))
+    for _ in range(warmup):
+        sol.radhydro_step(dt, n_sub)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record(sol.stream)
+    for _ in range(steps):
+        sol.hydro_step(dt)
+    ev[1].record(sol.stream)
+    ev[2].record(sol.stream)
+    for _ in range(steps):
+        sol.radhydro_step(dt, n_sub)
+    ev[3].record(sol.stream)
+    torch.cuda.synchronize()
+    out = {"workload": f"linear-wave box {n}^3 x 80 angles with the gas dynamics (FP32 radiation)",
+           "n_sub": n_sub, "steps": steps, "cells": prob.n_cells, "faces": prob.mesh.n_faces,
+           "hydro_ms_per_step": ev[0].elapsed_time(ev[1]) / steps,
+           "radhydro_ms_per_step": ev[2].elapsed_time(ev[3]) / steps,
+           "device_bytes": sol.device_bytes()}
+    sol.close()
+    del sol
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -714,6 +752,7 @@ def main():
         extras["groups"] = groups_rate(args.shadows_n, max(3, args.steps // 5), 3, hbm_peak,
                                        peak_kind)
         extras["thermal"] = thermal_rate(world)
+        extras["radhydro"] = radhydro_rate(args.shadows_n, 3, 1)
 
     r32, r64 = head["fp32"], head["fp64"]
     line = {"metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": world,

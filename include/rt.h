@@ -309,8 +309,10 @@ int rt_sync(rt_state *s);
  * the implicit-function theorem.  Boundary / emitter tallies carry no
  * cotangent.  Intensities in the state precision, everything else double,
  * caller order; on_device = 1: all arrays are device pointers.  dt <= 0:
- * dt_cfl.  The first call allocates the adjoint's work buffers (8 intensity
- * arrays + 24 doubles per cell), kept until rt_destroy. */
+ * dt_cfl.  lam_e may alias lam_e1 and lam_m alias lam_m1 (each cell's
+ * cotangents are read before its outputs are written); no other arrays may
+ * overlap.  The first call allocates the adjoint's work buffers (8 intensity
+ * arrays + 35 doubles per cell), kept until rt_destroy. */
 int rt_adjoint_step(rt_state *s, double dt, const void *I_n, const double *e_n, const double *m_n,
                     const void *lam_I1, const double *lam_e1, const double *lam_m1, void *lam_I,
                     double *lam_e, double *lam_m, double *grad_kappa_P, double *grad_kappa_J,

@@ -13,29 +13,38 @@
 // implicit-function theorem, dT/dalpha = -T^4 / F', dT/dg = 1 / F',
 // F' = 4 alpha T^3 + rho c_v.
 //
-// Three launches (besides the permutes into and out of the internal order):
+// Launches (besides the permutes of the rows into and out of the internal
+// order):
+//   adjoint_prep  one thread per cell, in double: gathers e^n, m^n,
+//        lambda_e^{n+1}, lambda_m^{n+1} from the caller's order and writes
+//        the cell's record: v/c, x/Gamma, the boundary and emitter factors,
+//        c lambda_e, lambda_m and the inputs of the per-cell chain (rho,
+//        1/rho, rho c_v, the opacities, the gas temperature before the step)
+//        in the state precision;
 //   launch_transport (forward)  I* = M I^n, on the step kernel's tile machinery;
-//   source_reverse_tile         blocks of 32 cells x 8 threads (the step
-//                               kernel's tile mapping):
-//     0  one lane per cell in double: the per-cell constants of phases 1 and
-//        3 (v/c, x/Gamma, the boundary and emitter factors);
-//     1  after a block barrier: the angular sums of the forward source step
-//        and lambda_q = sum_a Gamma_a lambda_I~'_a / (1 + x_a), which needs
-//        no result of the quartic;
-//     2  after a second barrier, one lane per cell: the quartic, J~, q and
-//        the reverse of the per-cell chain down to lambda_{S_I} and
-//        lambda_{S_G} (in the state precision, see cell_chain);
-//     3  after a third barrier, the per-angle reverse in the state precision,
-//        written as L = dt/V lambda_I*.  The weight normalisation's sum
+//   source_reverse_tile  blocks of 32 cells x 8 threads (the step kernel's
+//        tile mapping):
+//     1  the angular sums of the forward source step and
+//        lambda_q = sum_a Gamma_a lambda_I~'_a / (1 + x_a), which needs no
+//        result of the quartic, reduced over the cell's 8 threads;
+//     2  the quartic, J~, q and the reverse of the per-cell chain down to
+//        lambda_{S_I} and lambda_{S_G}: float states in every thread of the
+//        cell (the sums are in all 8, no block barrier); double states one
+//        lane per cell on warp 0 between two block barriers, so that the FP64
+//        chain is issued once for 32 cells;
+//     3  the per-angle reverse in the state precision, written as
+//        L = dt/V lambda_I*.  The weight normalisation's sum
 //        sum_a w~_a lambda_w~_a equals lambda_{S_I} S_I + lambda_{S_G} S_G, so
-//        it needs no further pass over the angles;
-//     4  after a fourth barrier, one lane per cell in double: lambda_e,
-//        lambda_m and the opacity gradients from the cell sums of phase 3;
+//        it needs no further pass over the angles; the cell's sums of this
+//        phase and the chain's results go to a per-cell record;
 //   launch_transport (adjoint)  lambda_I^n = M^T lambda_I*: per cell,
-//        lambda_c - sum over the faces with u > 0 of u (L_c - L_nbr).
-// As in the forward step, the per-cell work is one lane per cell (GB300's
-// FP64 rate is a small fraction of its FP32 rate) and the per-angle
-// arithmetic runs in the state precision.
+//        lambda_c - sum over the faces with u > 0 of u (L_c - L_nbr);
+//   adjoint_finish  one thread per cell, in double: lambda_e^n, lambda_m^n
+//        (lambda_v = -(sum n lambda_Gamma) / c enters through v = m / rho)
+//        and the opacity gradients, scattered to the caller's order.
+// The per-cell FP64 work thus runs in kernels of full warps, and the
+// per-angle arithmetic in the state precision (GB300's FP64 rate is a small
+// fraction of its FP32 rate).
 #include <cuda_runtime.h>
 
 #include "rt_internal.cuh"
@@ -48,7 +57,27 @@ namespace {
 using step::positive;
 using step::rcp;
 
-constexpr int kThreads = 256;  // threads per block of the per-cell gather / scatter
+constexpr int kThreads = 256;  // threads per block of adjoint_prep / adjoint_finish
+
+// Per-cell record of adjoint_prep (16 values in the state precision): the
+// inputs of the per-angle phases and of the per-cell chain.
+template <typename R> struct alignas(4 * sizeof(R)) AdjCell {
+  R bx, by, bz;  // v / c
+  R X;           // interior: x / Gamma = dt cbar (rho kJ + rho kS); emitter: dt cbar (rho kappa)_src
+  R f;           // boundary: 1 - min(dt / tau, 1); emitter: I_src
+  R cle, lmx, lmy, lmz;  // c lambda_e, lambda_m of step n + 1
+  R Tn;          // gas temperature before the step, e_int / (rho c_v)
+  R rho, ir, rcv, kP, kJ, kS;  // rho, 1 / rho, rho c_v, opacities per unit mass
+};
+// Per-cell record of source_reverse_tile for adjoint_finish (8 values in the
+// state precision).
+template <typename R> struct alignas(4 * sizeof(R)) AdjOut {
+  R dle;         // lambda_e^n - lambda_e^{n+1} (= -lambda of the kinetic energy)
+  R gP, gJ;      // the per-cell chain's kappa_P, kappa_J gradients
+  R gJx;         // sum_a Gamma_a lambda_x_a (the x_a = dt cbar rho (kJ + kS) Gamma_a term)
+  R lvx, lvy, lvz;  // sum_a n_a lambda_Gamma_a (emitter: n dI'/dGamma lambda_I')
+  R pad;
+};
 
 template <typename R> struct AdjArgs {
   int64_t n;
@@ -57,13 +86,20 @@ template <typename R> struct AdjArgs {
   const GasStatic *gs; // [N]
   const uint8_t *kind; // [N]
   const double2 *aux;  // [N] (tau or emit_rate, I_src)
+  const int64_t *cell_of;  // [N] internal -> caller cell
   const R *dir;        // [A][4] (x, y, z, 0), caller angle order
   const R *wt2;        // [A/2][2] weights of the pairs (p, p + A/2)
   const R *Is;         // [N][A] I* (the transported rows)
   const R *lI1;        // [N][A] lambda_I^{n+1}
   R *Ls;               // [N][A] out: dt/V lambda_I*
+  AdjCell<R> *rec;     // [N] adjoint_prep -> source_reverse_tile
+  AdjOut<R> *out;      // [N] source_reverse_tile -> adjoint_finish
+  double *eint;        // [N] e_int in double (the double chain of float states)
+  // caller order: e, m, lambda_e^{n+1}, lambda_m^{n+1} in; lambda_e^n,
+  // lambda_m^n out (may alias le1 / lm1: each is read before its cell is
+  // written, by the same thread); gP, gJ accumulate
   const double *e, *m, *le1, *lm1;  // [N], [N][3], [N], [N][3]
-  double *le, *lm, *gP, *gJ;        // out: [N], [N][3]; gP, gJ accumulate
+  double *le, *lm, *gP, *gJ;        // [N], [N][3], [N], [N]
   double dt, cbar, c, a_rad, inv_c;
   R dt_r, k_ex_r;      // dt; 4 pi / cbar
   int newton_max_iter;
@@ -90,35 +126,24 @@ template <typename R> __device__ __forceinline__ Ang<R> comoving_g(R G, R wt, R 
   g.It = G2 * G2 * is;
   return g;
 }
-// Per-cell inputs of phases 1 and 3 (phase 0), sums of phase 1 (unnormalised
-// by N_w = sum w^), results of phase 2 and sums of phase 3.
-template <typename R> struct CellIn {
-  R bx, by, bz;  // v / c
-  R X;           // interior: x / Gamma = dt cbar (rho kJ + rho kS); emitter: dt cbar (rho kappa)_src
-  R f;           // boundary: 1 - min(dt / tau, 1); emitter: I_src
-  R cle, lmx, lmy, lmz;  // c lambda_e, lambda_m of step n + 1
-  int kind;
-};
+// Sums of phase 1 (unnormalised by N_w = sum w^).
 template <typename R> struct CellSums {
   R Nw, SI, SG, S1, lq;
 };
-template <typename R> struct CellRev {
-  double gJ, lm[3];
-  R q, lSI, lSG, swl, iNw;  // for phase 3
-};
-template <typename R> struct CellOut {
-  R gJx, lvx, lvy, lvz;  // sum Gamma lambda_x; sum n lambda_Gamma (emitter: n dI'/dGamma lambda_I')
-};
 
-// Phase 0 for cell c.
-template <typename R> __device__ void cell_inputs(const AdjArgs<R> &a, int64_t c, CellIn<R> &o) {
-  const int kind = a.kind[c];
-  const GasStatic &gs = a.gs[c];
+// adjoint_prep: the record of internal cell i (caller cell cell_of[i]).
+template <typename R> __global__ void adjoint_prep(const AdjArgs<R> a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const int64_t c = a.cell_of[i];
+  const int kind = a.kind[i];
+  const GasStatic gs = a.gs[i];
+  const double mx = a.m[3 * c], my = a.m[3 * c + 1], mz = a.m[3 * c + 2];
   const double vc = gs.inv_rho * a.inv_c;
-  o.kind = kind;
-  o.bx = R(a.m[3 * c] * vc);
-  o.by = R(a.m[3 * c + 1] * vc);
-  o.bz = R(a.m[3 * c + 2] * vc);
+  AdjCell<R> o;
+  o.bx = R(mx * vc);
+  o.by = R(my * vc);
+  o.bz = R(mz * vc);
   o.cle = R(a.c * a.le1[c]);
   o.lmx = R(a.lm1[3 * c]);
   o.lmy = R(a.lm1[3 * c + 1]);
@@ -126,41 +151,63 @@ template <typename R> __device__ void cell_inputs(const AdjArgs<R> &a, int64_t c
   o.X = R(a.dt * a.cbar * (gs.rkJ + gs.rkS));
   o.f = R(0);
   if (kind == RT_CELL_BOUNDARY) {
-    const double2 ax = a.aux[c];
+    const double2 ax = a.aux[i];
     o.f = R(1.0 - ((ax.x <= a.dt) ? 1.0 : a.dt / ax.x));
   } else if (kind == RT_CELL_EMITTER) {
-    const double2 ax = a.aux[c];
+    const double2 ax = a.aux[i];
     o.X = R(a.dt * a.cbar * ax.x);
     o.f = R(ax.y);
   }
+  const double eint = a.e[c] - 0.5 * (mx * mx + my * my + mz * mz) * gs.inv_rho;
+  o.rho = R(gs.rho);
+  o.ir = R(gs.inv_rho);
+  o.rcv = R(gs.rcv);
+  o.kP = R(gs.rkP) * o.ir;
+  o.kJ = R(gs.rkJ) * o.ir;
+  o.kS = R(gs.rkS) * o.ir;
+  o.Tn = R(eint) * (R(1) / o.rcv);
+  a.rec[i] = o;
+  a.eint[i] = eint;
 }
 
 // Phase 2 for one interior cell in the compute type C: the forward
 // per-cell chain (the weights normalised, D = S_1 + dt cbar rho kJ S_G =
 // 1 - dt cbar rho kS S_G) and its reverse from lambda_q down to lambda_{S_I},
-// lambda_{S_G}.  The quartic is solved as in the forward step, from the gas
-// temperature before the step.  Float states run it in float (the precision
-// of their linearisation point; the forward float step solves its quartic in
-// float too) and repeat it in double when a result is not finite; double
-// states run it in double.
+// lambda_{S_G}.  The quartic is solved from the gas temperature before the
+// step.  Float states run it in float (the adjoint linearises at the float
+// root; its derivatives move by the root's relative error, ~1e-7) and repeat
+// it in double when a result is not finite; double states run it in double.
 template <typename C> struct Chain {
-  C q, lSI, lSG, swl, iNw, dle, lkin, gP, gJ;
+  C q, lSI, lSG, swl, iNw, dle, gP, gJ;
+};
+template <typename C> struct ChainIn {
+  C rho, ir, rcv, kP, kJ, kS, Tn;
 };
 template <typename C> __device__ __forceinline__ C tol_of();
 template <> __device__ __forceinline__ float tol_of<float>() { return 1e-7f; }
 template <> __device__ __forceinline__ double tol_of<double>() { return 1e-15; }
 
+template <typename R> __device__ __forceinline__ ChainIn<R> chain_in(const AdjCell<R> &r) {
+  return ChainIn<R>{r.rho, r.ir, r.rcv, r.kP, r.kJ, r.kS, r.Tn};
+}
+// The same inputs in double, from the gas record and e_int (as adjoint_prep
+// forms them for double states).
+__device__ __forceinline__ ChainIn<double> chain_in_double(const GasStatic &gs, double eint) {
+  const double ir = gs.inv_rho;
+  return ChainIn<double>{gs.rho, ir, gs.rcv, gs.rkP * ir, gs.rkJ * ir, gs.rkS * ir,
+                         eint * (1.0 / gs.rcv)};
+}
+
 template <typename C, typename R>
-__device__ Chain<C> cell_chain(const AdjArgs<R> &a, const GasStatic &gs, double eint,
-                               const CellSums<R> &s) {
+__device__ Chain<C> cell_chain(const AdjArgs<R> &a, const ChainIn<C> &in, const CellSums<R> &s) {
   Chain<C> o;
   const C iNw = C(1) / C(s.Nw);
   const C SI = C(s.SI) * iNw, SG = C(s.SG) * iNw, S1 = C(s.S1) * iNw, lq = C(s.lq);
-  const C rho = C(gs.rho), ir = C(gs.inv_rho), rcv = C(gs.rcv), irc = C(1) / rcv;
-  const C kP = C(gs.rkP) * ir, kJ = C(gs.rkJ) * ir, kS = C(gs.rkS) * ir;
+  const C rho = in.rho, rcv = in.rcv, irc = C(1) / rcv;
+  const C kP = in.kP, kJ = in.kJ, kS = in.kS;
   const C dcb = C(a.dt * a.cbar) * rho, dcc = C(a.dt * a.c) * rho, a_rad = C(a.a_rad);
   const C pi4 = C(4.0 * kPi);
-  const C Tn = C(eint) * irc;
+  const C Tn = in.Tn;
   const C D = S1 + dcb * kJ * SG;
   const C iD = C(1) / D;
   const C hJ = S1 * iD;  // 1 - dt cbar rho kJ S_G / D
@@ -199,7 +246,6 @@ __device__ Chain<C> cell_chain(const AdjArgs<R> &a, const GasStatic &gs, double 
   o.swl = lSI * SI + lSG * SG;
   o.iNw = iNw;
   o.dle = lTn * irc;  // lambda_e^n = lambda_e^{n+1} + lambda_Tn / rho c_v
-  o.lkin = -o.dle;
   o.gP = gP;
   o.gJ = gJ;
   return o;
@@ -210,72 +256,58 @@ template <typename C> __device__ __forceinline__ bool chain_finite(const Chain<C
          isfinite(o.iNw) && isfinite(o.dle) && isfinite(o.gP) && isfinite(o.gJ);
 }
 
-// Phase 2 for cell c: the chain, lambda_e, the kappa_P gradient and the
-// per-cell results phase 3 and phase 4 read.
-template <typename R>
-__device__ void cell_reverse(const AdjArgs<R> &a, int64_t c, const CellSums<R> &s,
-                             CellRev<R> &r) {
-  const GasStatic gs = a.gs[c];
-  const double mx = a.m[3 * c], my = a.m[3 * c + 1], mz = a.m[3 * c + 2];
-  const double eint = a.e[c] - 0.5 * (mx * mx + my * my + mz * mz) * gs.inv_rho;
-  double q, lSI, lSG, swl, iNw, dle, lkin, gP, gJ;
-  bool done = false;
-  if constexpr (sizeof(R) == 4) {
-    const Chain<float> o = cell_chain<float>(a, gs, eint, s);
-    if (chain_finite(o)) {
-      q = o.q, lSI = o.lSI, lSG = o.lSG, swl = o.swl, iNw = o.iNw;
-      dle = o.dle, lkin = o.lkin, gP = o.gP, gJ = o.gJ;
-      done = true;
-    }
+// Phase 2 of a float state's interior cell, in each of its threads: the
+// float chain, or the double one where a float result is not finite.
+__device__ __forceinline__ Chain<float> float_chain(const AdjArgs<float> &a, int64_t c,
+                                                    const AdjCell<float> &rec,
+                                                    const CellSums<float> &s) {
+  Chain<float> o = cell_chain<float>(a, chain_in(rec), s);
+  if (!chain_finite(o)) {
+    const Chain<double> d = cell_chain<double>(a, chain_in_double(a.gs[c], a.eint[c]), s);
+    o = Chain<float>{float(d.q), float(d.lSI), float(d.lSG), float(d.swl),
+                     float(d.iNw), float(d.dle), float(d.gP), float(d.gJ)};
   }
-  if (!done) {
-    const Chain<double> o = cell_chain<double>(a, gs, eint, s);
-    q = o.q, lSI = o.lSI, lSG = o.lSG, swl = o.swl, iNw = o.iNw;
-    dle = o.dle, lkin = o.lkin, gP = o.gP, gJ = o.gJ;
-  }
-  a.le[c] = a.le1[c] + dle;
-  a.gP[c] += gP;
-  r.q = R(q);
-  r.lSI = R(lSI);
-  r.lSG = R(lSG);
-  r.swl = R(swl);
-  r.iNw = R(iNw);
-  r.gJ = gJ;
-  r.lm[0] = a.lm1[3 * c] + mx * gs.inv_rho * lkin;
-  r.lm[1] = a.lm1[3 * c + 1] + my * gs.inv_rho * lkin;
-  r.lm[2] = a.lm1[3 * c + 2] + mz * gs.inv_rho * lkin;
+  return o;
 }
 
-// Phase 4 for cell c: lambda_v = -(sum n lambda_Gamma) / c enters lambda_m
-// through v = m / rho; the x_a = dt cbar rho (kJ + kS) Gamma_a term gives the
-// kappa_J gradient.
-template <typename R>
-__device__ void cell_finish(const AdjArgs<R> &a, int64_t c, int kind, const CellRev<R> &r,
-                            const CellOut<R> &s) {
-  const double rho = a.gs[c].rho;
-  const double f = -a.inv_c * a.gs[c].inv_rho;
+// adjoint_finish: lambda_e^n, lambda_m^n and the opacity gradients of
+// internal cell i, written to caller cell cell_of[i].  lambda_v =
+// -(sum n lambda_Gamma) / c enters lambda_m through v = m / rho; the
+// x_a = dt cbar rho (kJ + kS) Gamma_a term gives the kappa_J gradient.
+template <typename R> __global__ void adjoint_finish(const AdjArgs<R> a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const int64_t c = a.cell_of[i];
+  const int kind = a.kind[i];
+  const double rho = a.gs[i].rho, inv_rho = a.gs[i].inv_rho;
+  const double f = -a.inv_c * inv_rho;
+  const AdjOut<R> o = a.out[i];
+  const double le1 = a.le1[c];
+  double lm[3] = {a.lm1[3 * c], a.lm1[3 * c + 1], a.lm1[3 * c + 2]};
+  const double lv[3] = {(double)o.lvx, (double)o.lvy, (double)o.lvz};
   if (kind == RT_CELL_BOUNDARY) {
-    a.le[c] = a.le1[c];
-    for (int d = 0; d < 3; ++d) a.lm[3 * c + d] = a.lm1[3 * c + d];
+    a.le[c] = le1;
   } else if (kind == RT_CELL_EMITTER) {
-    a.le[c] = a.le1[c];
-    a.lm[3 * c] = a.lm1[3 * c] + f * (double)s.lvx;
-    a.lm[3 * c + 1] = a.lm1[3 * c + 1] + f * (double)s.lvy;
-    a.lm[3 * c + 2] = a.lm1[3 * c + 2] + f * (double)s.lvz;
+    a.le[c] = le1;
+    for (int d = 0; d < 3; ++d) lm[d] = lm[d] + f * lv[d];
   } else {
-    a.gJ[c] += r.gJ + a.dt * a.cbar * rho * (double)s.gJx;
-    a.lm[3 * c] = r.lm[0] + f * (double)s.lvx;
-    a.lm[3 * c + 1] = r.lm[1] + f * (double)s.lvy;
-    a.lm[3 * c + 2] = r.lm[2] + f * (double)s.lvz;
+    const double dle = (double)o.dle, lkin = -dle;
+    a.le[c] = le1 + dle;
+    a.gP[c] += (double)o.gP;
+    a.gJ[c] += (double)o.gJ + a.dt * a.cbar * rho * (double)o.gJx;
+    const double mom[3] = {a.m[3 * c], a.m[3 * c + 1], a.m[3 * c + 2]};
+    for (int d = 0; d < 3; ++d) lm[d] = (lm[d] + mom[d] * inv_rho * lkin) + f * lv[d];
   }
+  for (int d = 0; d < 3; ++d) a.lm[3 * c + d] = lm[d];
 }
 
 // ------------------------------------------------------------ the kernel
-// Phases 1 and 3 (per angle) run on the step kernel's tile mapping: 32 cells
-// x 8 threads, thread `sub` holding the entries of its pair / quad map (angle
-// p and its antipode, whose Gamma is 1 + v.n_p where p's is 1 - v.n_p).  A
-// cell's sums reduce over its 8 threads (3 shuffles), the 4 cells of a warp
-// at once.  Phases 0, 2 and 4 run one lane per cell on warp 0.
+// The per-angle phases (1 and 3) run on the step kernel's tile mapping: 32
+// cells x 8 threads, thread `sub` holding the entries of its pair / quad map
+// (angle p and its antipode, whose Gamma is 1 + v.n_p where p's is
+// 1 - v.n_p).  A cell's sums reduce over its 8 threads (3 shuffles, by xor,
+// so that all 8 hold the same sums bit for bit), the 4 cells of a warp at
+// once.
 
 // One angle's terms of phase 1 (interior cells).
 template <typename R>
@@ -294,7 +326,7 @@ __device__ __forceinline__ void sums_angle(R G, R wt, R X, R is, R l1, R ex, R &
 // accumulates sum Gamma lambda_x and gives lambda_Gamma.
 template <typename R>
 __device__ __forceinline__ R reverse_angle(R G, R wt, R X, R isv, R l1, R ex, R dtv,
-                                           const CellRev<R> &r, R &gJx, R &lGo) {
+                                           const Chain<R> &r, R &gJx, R &lGo) {
   const Ang<R> g = comoving_g(G, wt, X, isv);
   const R w = g.wh * r.iNw;
   const R Itn = fma(r.q, g.G, g.It) * g.r;  // I~'
@@ -348,7 +380,7 @@ template <typename R, typename M> struct Entries {
   }
   // 4 pi w (c lambda_e + n . lambda_m) / cbar of entry j's angle (anti: the
   // antipode, direction -n_p)
-  __device__ __forceinline__ R ex(int j, bool anti, const CellIn<R> &ci, R k_ex) const {
+  __device__ __forceinline__ R ex(int j, bool anti, const AdjCell<R> &ci, R k_ex) const {
     const R x = anti ? -nx[j] : nx[j], y = anti ? -ny[j] : ny[j], z = anti ? -nz[j] : nz[j];
     return k_ex * (anti ? wb[j] : wa[j]) * fma(x, ci.lmx, fma(y, ci.lmy, fma(z, ci.lmz, ci.cle)));
   }
@@ -370,28 +402,24 @@ __global__ void __launch_bounds__(kRevThreads, sizeof(R) == 4 ? (M::PPT <= 5 ? 4
     source_reverse_tile(const AdjArgs<R> a) {
   using step::KT;
   constexpr int PPT = M::PPT;
-  __shared__ CellIn<R> cin[kRevCells];
-  __shared__ CellSums<R> sums[kRevCells];
-  __shared__ CellRev<R> rev[kRevCells];
-  __shared__ CellOut<R> cout_[kRevCells];
+  constexpr bool kLaneChain = sizeof(R) == 4;  // float: the chain in every thread of the cell
+  constexpr int kShared = kLaneChain ? 1 : kRevCells;
+  __shared__ CellSums<R> sums[kShared];
+  __shared__ Chain<R> rev[kShared];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int lc = threadIdx.x / KT, sub = threadIdx.x % KT;
   const int64_t c0 = (int64_t)blockIdx.x * kRevCells;
-  const int64_t cl = c0 + lane;  // the lane's cell in phases 0, 2, 4
-  const bool lane_cell = warp == 0 && lane < kRevCells && cl < a.n;
-  // ---------------- phase 0: per-cell constants, one lane per cell
-  if (lane_cell) cell_inputs(a, cl, cin[lane]);
-
   const bool live = c0 + lc < a.n;
   const int64_t c = live ? c0 + lc : a.n - 1;  // dead threads shadow the last cell
   const int np = M::count(a.H, sub);
-  __syncthreads();
-  const CellIn<R> ci = cin[lc];
+  const AdjCell<R> ci = a.rec[c];  // the cell's 8 threads read the same record
+  const int kind = a.kind[c];
   const R k_ex = a.k_ex_r;  // lambda_I* gets 4 pi w (c lambda_e + n . lambda_m) / cbar
   // ---------------- phase 1: the angular sums and lambda_q
+  CellSums<R> cs;
   {
     R Nw = 0, SI = 0, SG = 0, S1 = 0, lq = 0;
-    if (ci.kind == RT_CELL_INTERIOR) {
+    if (kind == RT_CELL_INTERIOR) {
       Entries<R, M> E;
       E.load(a, c, sub, np);
 #pragma unroll
@@ -404,18 +432,22 @@ __global__ void __launch_bounds__(kRevThreads, sizeof(R) == 4 ? (M::PPT <= 5 ? 4
                      SG, S1, lq);
         }
     }
-    Nw = group_sum(Nw);
-    SI = group_sum(SI);
-    SG = group_sum(SG);
-    S1 = group_sum(S1);
-    lq = group_sum(lq);
-    if (sub == 0) sums[lc] = CellSums<R>{Nw, SI, SG, S1, lq};
+    cs = CellSums<R>{group_sum(Nw), group_sum(SI), group_sum(SG), group_sum(S1), group_sum(lq)};
   }
-  __syncthreads();
 
-  // ---------------- phase 2: the quartic and the per-cell chain, one lane per cell
-  if (lane_cell && cin[lane].kind == RT_CELL_INTERIOR) cell_reverse(a, cl, sums[lane], rev[lane]);
-  __syncthreads();
+  // ---------------- phase 2: the quartic and the per-cell chain
+  Chain<R> r{};
+  if constexpr (kLaneChain) {
+    if (kind == RT_CELL_INTERIOR) r = float_chain(a, c, ci, cs);
+  } else {
+    if (sub == 0) sums[lc] = cs;
+    __syncthreads();
+    const int64_t cl = c0 + lane;
+    if (warp == 0 && lane < kRevCells && cl < a.n && a.kind[cl] == RT_CELL_INTERIOR)
+      rev[lane] = cell_chain<R>(a, chain_in(a.rec[cl]), sums[lane]);
+    __syncthreads();
+    if (kind == RT_CELL_INTERIOR) r = rev[lc];
+  }
 
   // ---------------- phase 3: per-angle reverse, lambda_I* (the entries read again: the
   // rows are in L1, and nothing per angle stays live across phase 2)
@@ -425,14 +457,14 @@ __global__ void __launch_bounds__(kRevThreads, sizeof(R) == 4 ? (M::PPT <= 5 ? 4
     E.load(a, c, sub, np);
     R oa[PPT], ob[PPT];
     R gJx = 0, lvx = 0, lvy = 0, lvz = 0;
-    if (ci.kind == RT_CELL_BOUNDARY) {
+    if (kind == RT_CELL_BOUNDARY) {
       const R f = dtv * ci.f;
 #pragma unroll
       for (int j = 0; j < PPT; ++j) {
         oa[j] = f * E.la[j];
         ob[j] = f * E.lb[j];
       }
-    } else if (ci.kind == RT_CELL_EMITTER) {
+    } else if (kind == RT_CELL_EMITTER) {
       const R Y = ci.X, isrc = ci.f;
 #pragma unroll
       for (int j = 0; j < PPT; ++j) {
@@ -448,7 +480,6 @@ __global__ void __launch_bounds__(kRevThreads, sizeof(R) == 4 ? (M::PPT <= 5 ? 4
         }
       }
     } else {
-      const CellRev<R> r = rev[lc];
 #pragma unroll
       for (int j = 0; j < PPT; ++j) {
         const R t = fma(ci.bx, E.nx[j], fma(ci.by, E.ny[j], ci.bz * E.nz[j]));
@@ -471,12 +502,15 @@ __global__ void __launch_bounds__(kRevThreads, sizeof(R) == 4 ? (M::PPT <= 5 ? 4
     lvx = group_sum(lvx);
     lvy = group_sum(lvy);
     lvz = group_sum(lvz);
-    if (sub == 0) cout_[lc] = CellOut<R>{gJx, lvx, lvy, lvz};
+    // the cell's record for adjoint_finish: thread `sub` writes value `sub`
+    if (live) {
+      const R v[8] = {r.dle, r.gP, r.gJ, gJx, lvx, lvy, lvz, R(0)};
+      R w = v[0];
+#pragma unroll
+      for (int k = 1; k < 8; ++k) w = sub == k ? v[k] : w;
+      reinterpret_cast<R *>(a.out + c)[sub] = w;
+    }
   }
-  __syncthreads();
-
-  // ---------------- phase 4: lambda_e, lambda_m, gradients, one lane per cell
-  if (lane_cell) cell_finish(a, cl, cin[lane].kind, rev[lane], cout_[lane]);
 }
 
 template <typename R, typename M> void launch_reverse_tile(rt_state *s, const AdjArgs<R> &a) {
@@ -519,32 +553,16 @@ template <typename R> void launch_reverse(rt_state *s, const AdjArgs<R> &a) {
     reverse_pairs<R, false>(s, a);
 }
 
-// caller order -> internal order for per-cell vectors of width w (double)
-__global__ void gather_cells(const double *__restrict__ src, double *__restrict__ dst,
-                             const int64_t *__restrict__ cell_of, int64_t n, int w) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  for (int k = 0; k < w; ++k) dst[(size_t)i * w + k] = src[(size_t)cell_of[i] * w + k];
-}
-// internal order -> caller order; accumulate when add != 0
-__global__ void scatter_cells(const double *__restrict__ src, double *__restrict__ dst,
-                              const int64_t *__restrict__ cell_of, int64_t n, int w, int add) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  for (int k = 0; k < w; ++k) {
-    double *p = dst + (size_t)cell_of[i] * w + k;
-    *p = add ? *p + src[(size_t)i * w + k] : src[(size_t)i * w + k];
-  }
-}
-
-template <typename R> cudaError_t run_adjoint(rt_state *s, const R *I_int, const R *lI1_int,
-                                              R *lI_int, double dt, double *ws) {
+template <typename R>
+cudaError_t run_adjoint(rt_state *s, const R *I_int, const R *lI1_int, R *lI_int, double dt,
+                        const double *e, const double *m, const double *le1, const double *lm1,
+                        double *le, double *lm, double *gP, double *gJ) {
   const int64_t N = s->n_cells;
   const int A = s->n_angles;
+  const unsigned g1 = (unsigned)((N + kThreads - 1) / kThreads);
   R *Is = reinterpret_cast<R *>(s->d_adj[0]);
   R *Ls = reinterpret_cast<R *>(s->d_adj[1]);
-  cudaError_t err = launch_transport(s, dt, I_int, Is, false);
-  if (err != cudaSuccess) return err;
+  char *ws = reinterpret_cast<char *>(s->d_adj_ws);  // [N] records, [N] results, [N] e_int
   AdjArgs<R> a;
   a.n = N;
   a.A = A;
@@ -554,19 +572,23 @@ template <typename R> cudaError_t run_adjoint(rt_state *s, const R *I_int, const
   a.gs = s->d_gs;
   a.kind = s->d_kind;
   a.aux = s->d_aux;
+  a.cell_of = s->d_cell_of;
   a.dir = reinterpret_cast<const R *>(s->d_dir);
   a.wt2 = reinterpret_cast<const R *>(s->d_wt);
   a.Is = Is;
   a.lI1 = lI1_int;
   a.Ls = Ls;
-  a.e = ws;
-  a.m = ws + N;
-  a.le1 = ws + 4 * N;
-  a.lm1 = ws + 5 * N;
-  a.le = ws + 8 * N;
-  a.lm = ws + 9 * N;
-  a.gP = ws + 12 * N;
-  a.gJ = ws + 13 * N;
+  a.rec = reinterpret_cast<AdjCell<R> *>(ws);
+  a.out = reinterpret_cast<AdjOut<R> *>(ws + sizeof(AdjCell<R>) * (size_t)N);
+  a.eint = reinterpret_cast<double *>(ws + (sizeof(AdjCell<R>) + sizeof(AdjOut<R>)) * (size_t)N);
+  a.e = e;
+  a.m = m;
+  a.le1 = le1;
+  a.lm1 = lm1;
+  a.le = le;
+  a.lm = lm;
+  a.gP = gP;
+  a.gJ = gJ;
   a.dt = dt;
   a.cbar = s->params.cbar;
   a.c = s->params.c;
@@ -575,11 +597,19 @@ template <typename R> cudaError_t run_adjoint(rt_state *s, const R *I_int, const
   a.dt_r = R(dt);
   a.k_ex_r = R(4.0 * kPi / s->params.cbar);
   a.newton_max_iter = s->params.newton_max_iter;
+  adjoint_prep<R><<<g1, kThreads, 0, s->stream>>>(a);
+  s->launches++;
+  cudaError_t err = launch_transport(s, dt, I_int, Is, false);
+  if (err != cudaSuccess) return err;
   launch_reverse<R>(s, a);
   s->launches++;
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  return launch_transport(s, dt, Ls, lI_int, true);
+  err = launch_transport(s, dt, Ls, lI_int, true);
+  if (err != cudaSuccess) return err;
+  adjoint_finish<R><<<g1, kThreads, 0, s->stream>>>(a);
+  s->launches++;
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -587,37 +617,21 @@ template <typename R> cudaError_t run_adjoint(rt_state *s, const R *I_int, const
 cudaError_t adjoint_step(rt_state *s, double dt, const void *I, const double *e, const double *m,
                          const void *lI1, const double *le1, const double *lm1, void *lI,
                          double *le, double *lm, double *gP, double *gJ) {
-  // all pointers are device pointers in the caller's order; the internal
-  // copies use dense rows (stride A)
-  const int64_t N = s->n_cells;
-  const unsigned g1 = (unsigned)((N + kThreads - 1) / kThreads);
-  double *ws = s->d_adj_ws;  // [14 N]: e, m, (pad), le1, lm1, le, lm, gP, gJ (internal)
+  // per-cell arrays are device pointers in the caller's order (adjoint_prep
+  // gathers, adjoint_finish scatters); the rows are permuted into dense
+  // internal rows (stride A) and back
   void *I_int = s->d_adj[2], *lI1_int = s->d_adj[3], *lI_int = s->d_adj[4];
   cudaError_t err = launch_permute_in(s, I, I_int, s->n_angles);
   if (err == cudaSuccess) err = launch_permute_in(s, lI1, lI1_int, s->n_angles);
   if (err != cudaSuccess) return err;
-  gather_cells<<<g1, kThreads, 0, s->stream>>>(e, ws, s->d_cell_of, N, 1);
-  gather_cells<<<g1, kThreads, 0, s->stream>>>(m, ws + N, s->d_cell_of, N, 3);
-  gather_cells<<<g1, kThreads, 0, s->stream>>>(le1, ws + 4 * N, s->d_cell_of, N, 1);
-  gather_cells<<<g1, kThreads, 0, s->stream>>>(lm1, ws + 5 * N, s->d_cell_of, N, 3);
-  err = cudaMemsetAsync(ws + 12 * N, 0, sizeof(double) * 2 * N, s->stream);
-  if (err != cudaSuccess) return err;
-  s->launches += 4;
   if (s->precision == RT_FP32)
     err = run_adjoint<float>(s, (const float *)I_int, (const float *)lI1_int, (float *)lI_int, dt,
-                             ws);
+                             e, m, le1, lm1, le, lm, gP, gJ);
   else
     err = run_adjoint<double>(s, (const double *)I_int, (const double *)lI1_int,
-                              (double *)lI_int, dt, ws);
+                              (double *)lI_int, dt, e, m, le1, lm1, le, lm, gP, gJ);
   if (err != cudaSuccess) return err;
-  err = launch_permute_out(s, lI_int, lI, s->n_angles);
-  if (err != cudaSuccess) return err;
-  scatter_cells<<<g1, kThreads, 0, s->stream>>>(ws + 8 * N, le, s->d_cell_of, N, 1, 0);
-  scatter_cells<<<g1, kThreads, 0, s->stream>>>(ws + 9 * N, lm, s->d_cell_of, N, 3, 0);
-  scatter_cells<<<g1, kThreads, 0, s->stream>>>(ws + 12 * N, gP, s->d_cell_of, N, 1, 1);
-  scatter_cells<<<g1, kThreads, 0, s->stream>>>(ws + 13 * N, gJ, s->d_cell_of, N, 1, 1);
-  s->launches += 4;
-  return cudaGetLastError();
+  return launch_permute_out(s, lI_int, lI, s->n_angles);
 }
 
 }  // namespace rt

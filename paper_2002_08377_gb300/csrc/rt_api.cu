@@ -1200,7 +1200,7 @@ int rt_adjoint_step(rt_state *s, double dt, const void *I_n, const double *e_n, 
   const size_t nI = (size_t)N * s->n_angles * s->rsize;
   if (!s->d_adj[0]) {
     for (int k = 0; k < 8; ++k) RT_CUDA(s, dalloc_bytes(s, &s->d_adj[k], nI));
-    RT_CUDA(s, dalloc(s, &s->d_adj_ws, 14 * (size_t)N));
+    RT_CUDA(s, dalloc(s, &s->d_adj_ws, 25 * (size_t)N));
     RT_CUDA(s, dalloc(s, &s->d_adj_stage, 10 * (size_t)N));
   }
   if (on_device) {
@@ -1223,7 +1223,7 @@ int rt_adjoint_step(rt_state *s, double dt, const void *I_n, const double *e_n, 
   RT_CUDA(s, cudaMemcpyAsync(dgP, grad_kappa_P, 8 * N, h2d, s->stream));
   RT_CUDA(s, cudaMemcpyAsync(dgJ, grad_kappa_J, 8 * N, h2d, s->stream));
   // outputs: lam_I -> d_adj[7]; lam_e, lam_m overwrite the staging of lam_e1, lam_m1
-  // (read into the internal-order work area before any output is written)
+  // (each cell's are read by the thread that then writes the cell's outputs)
   RT_CUDA(s, rt::adjoint_step(s, dt, s->d_adj[5], de, dm, s->d_adj[6], dle1, dlm1, s->d_adj[7],
                               dle1, dlm1, dgP, dgJ));
   RT_CUDA(s, cudaMemcpyAsync(lam_I, s->d_adj[7], nI, d2h, s->stream));

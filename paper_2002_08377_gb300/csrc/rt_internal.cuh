@@ -231,7 +231,7 @@ struct rt_state {
   unsigned *d_status = nullptr;
   unsigned long long *d_bad = nullptr;
   void *d_adj[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  double *d_adj_ws = nullptr;     // [14 N] adjoint per-cell work (internal order)
+  double *d_adj_ws = nullptr;     // [25 N] adjoint per-cell records (internal order)
   double *d_adj_stage = nullptr;  // [10 N] host-path staging of per-cell vectors
   // gas dynamics (params.hydro): face and slot records, work area
   rt::HydroFace *d_hface = nullptr;

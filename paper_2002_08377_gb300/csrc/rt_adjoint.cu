@@ -106,9 +106,10 @@ template <typename R> struct AdjArgs {
 };
 
 // 1 / v: float by the approximate reciprocal (v = Gamma or 1 + x Gamma,
-// normal or +inf); double refined from it, or divided outside float range.
+// normal or +inf); double refined from it (rcp divides outside float range,
+// +inf included).
 __device__ __forceinline__ float rcp_pos(float v) { return rcp(v); }
-__device__ __forceinline__ double rcp_pos(double v) { return v < 1e37 ? rcp(v) : 1.0 / v; }
+__device__ __forceinline__ double rcp_pos(double v) { return rcp(v); }
 
 // Comoving quantities of one angle of an interior cell: Gamma = 1 - v.n/c,
 // w^ = w / Gamma^2, r = 1 / (1 + x), x = X Gamma, I~ = Gamma^4 I*.
@@ -118,11 +119,20 @@ template <typename R> struct Ang {
 template <typename R> __device__ __forceinline__ Ang<R> comoving_g(R G, R wt, R X, R is) {
   Ang<R> g;
   g.G = G;
-  g.iG = rcp_pos(g.G);
+  const R xp = fma(X, g.G, R(1));  // 1 + x
+  if constexpr (sizeof(R) == 8) {
+    // double: one reciprocal of Gamma (1 + x) serves both (the FP64 pipe
+    // bounds the double kernel)
+    const R p = rcp_pos(g.G * xp);
+    g.iG = xp * p;
+    g.r = g.G * p;
+  } else {
+    g.iG = rcp_pos(g.G);
+    g.r = rcp_pos(xp);
+  }
   const R iG2 = g.iG * g.iG, G2 = g.G * g.G;
   g.iG4 = iG2 * iG2;
   g.wh = wt * iG2;
-  g.r = rcp_pos(fma(X, g.G, R(1)));
   g.It = G2 * G2 * is;
   return g;
 }

@@ -86,21 +86,26 @@ __device__ bool hllc(double gamma, const double *WL, const double *WR, const dou
   } else {
     // F*_K = F_K + S_K (U*_K - U_K) on the side of the contact that holds
     // the face, the star state carrying the tangential velocity unchanged
-    const int k = (Ss >= 0.0) ? 0 : 1;
-    const double S = k == 0 ? SL : SR;
-    const double *w = W[k];
-    const double f = w[0] * (S - u[k]) / (S - Ss);
+    const bool left = Ss >= 0.0;  // the side's values by selects (no indexed local arrays)
+    const double S = left ? SL : SR, uk = left ? u[0] : u[1], Ek = left ? E[0] : E[1];
+    double w[5], Fs[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      w[q] = left ? WL[q] : WR[q];
+      Fs[q] = left ? Fk[0][q] : Fk[1][q];
+    }
+    const double f = w[0] * (S - uk) / (S - Ss);
     double Us[5], U[5];
     Us[0] = f;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) Us[1 + d] = f * (w[1 + d] + (Ss - u[k]) * n[d]);
-    Us[4] = f * (E[k] / w[0] + (Ss - u[k]) * (Ss + w[4] / (w[0] * (S - u[k]))));
+    for (int d = 0; d < 3; ++d) Us[1 + d] = f * (w[1 + d] + (Ss - uk) * n[d]);
+    Us[4] = f * (Ek / w[0] + (Ss - uk) * (Ss + w[4] / (w[0] * (S - uk))));
     U[0] = w[0];
 #pragma unroll
     for (int d = 0; d < 3; ++d) U[1 + d] = w[0] * w[1 + d];
-    U[4] = E[k];
+    U[4] = Ek;
 #pragma unroll
-    for (int q = 0; q < 5; ++q) F[q] = Fk[k][q] + S * (Us[q] - U[q]);
+    for (int q = 0; q < 5; ++q) F[q] = Fs[q] + S * (Us[q] - U[q]);
   }
   return true;
 }
@@ -195,22 +200,50 @@ __global__ void update_kernel(const int64_t *__restrict__ ptr, const HydroSlot *
 
 // Limited least-squares gradients grad[c][3][5] of the primitives W[c][5]
 // (x, y, z components of the five fields); the order of every sum is the
-// cell's slot order.
-__global__ void gradient_kernel(const int64_t *__restrict__ ptr, const int32_t *__restrict__ nbr,
-                                const HydroSlot *__restrict__ slot, const double *__restrict__ W,
-                                int64_t n, double *grad) {
+// cell's slot order.  Two passes over the cell's slots serve all five
+// fields: the first forms the normal matrix, the right-hand sides and the
+// neighbour range (each term rounded as the per-field formula rounds it),
+// the second the extreme face increments g . (x_f - x_c).  The
+// Barth-Jespersen factor min_f (hi - v) / dv (dv > 0) or (lo - v) / dv
+// (dv < 0) is taken as one division by the largest positive and one by the
+// most negative increment: the numerators have fixed signs and correctly
+// rounded division is monotone in the divisor, so the minimum is the same
+// number.
+__global__ void __launch_bounds__(kThreads, 2)
+    gradient_kernel(const int64_t *__restrict__ ptr, const int32_t *__restrict__ nbr,
+                    const HydroSlot *__restrict__ slot, const double *__restrict__ W, int64_t n,
+                    double *grad) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   const int64_t k0 = ptr[c], k1 = ptr[c + 1];
+  const double *Wc = W + 5 * c;
+  double v[5], lo[5], hi[5], b[5][3];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    v[q] = Wc[q];
+    lo[q] = v[q];
+    hi[q] = v[q];
+    b[q][0] = b[q][1] = b[q][2] = 0.0;
+  }
   double M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   for (int64_t k = k0; k < k1; ++k) {
-    const HydroSlot sl = slot[k];
+    const HydroSlot &sl = slot[k];
     const double r[3] = {sl.own[0] - sl.nbr[0], sl.own[1] - sl.nbr[1], sl.own[2] - sl.nbr[2]};
     const double w = sl.area / (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    const double wr[3] = {w * r[0], w * r[1], w * r[2]};
 #pragma unroll
     for (int x = 0; x < 3; ++x)
 #pragma unroll
-      for (int y = 0; y < 3; ++y) M[x][y] += w * r[x] * r[y];
+      for (int y = 0; y < 3; ++y) M[x][y] += wr[x] * r[y];
+    const double *Wj = W + 5 * (int64_t)nbr[k];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const double vj = Wj[q];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) b[q][x] += wr[x] * (vj - v[q]);
+      lo[q] = fmin(lo[q], vj);
+      hi[q] = fmax(hi[q], vj);
+    }
   }
   // inverse of the symmetric 3 x 3 matrix by cofactors
   double C[3][3];
@@ -224,38 +257,34 @@ __global__ void gradient_kernel(const int64_t *__restrict__ ptr, const int32_t *
   C[2][1] = M[0][1] * M[2][0] - M[0][0] * M[2][1];
   C[2][2] = M[0][0] * M[1][1] - M[0][1] * M[1][0];
   const double det = M[0][0] * C[0][0] + M[0][1] * C[1][0] + M[0][2] * C[2][0];
-  const double *Wc = W + 5 * c;
+  double g[5][3], dmax[5], dmin[5];
+#pragma unroll
   for (int q = 0; q < 5; ++q) {
-    const double v = Wc[q];
-    double b[3] = {0, 0, 0}, lo = v, hi = v;
-    for (int64_t k = k0; k < k1; ++k) {
-      const HydroSlot sl = slot[k];
-      const double r[3] = {sl.own[0] - sl.nbr[0], sl.own[1] - sl.nbr[1], sl.own[2] - sl.nbr[2]};
-      const double w = sl.area / (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-      const double vj = W[5 * (int64_t)nbr[k] + q];
 #pragma unroll
-      for (int x = 0; x < 3; ++x) b[x] += w * r[x] * (vj - v);
-      lo = fmin(lo, vj);
-      hi = fmax(hi, vj);
+    for (int x = 0; x < 3; ++x)
+      g[q][x] = (C[x][0] * b[q][0] + C[x][1] * b[q][1] + C[x][2] * b[q][2]) / det;
+    dmax[q] = 0.0;
+    dmin[q] = 0.0;
+  }
+  for (int64_t k = k0; k < k1; ++k) {
+    const HydroSlot &sl = slot[k];
+    const double o0 = sl.own[0], o1 = sl.own[1], o2 = sl.own[2];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const double dv = g[q][0] * o0 + g[q][1] * o1 + g[q][2] * o2;
+      dmax[q] = fmax(dmax[q], dv);
+      dmin[q] = fmin(dmin[q], dv);
     }
-    double g[3];
+  }
+  double *out = grad + 15 * c;
 #pragma unroll
-    for (int x = 0; x < 3; ++x) g[x] = (C[x][0] * b[0] + C[x][1] * b[1] + C[x][2] * b[2]) / det;
+  for (int q = 0; q < 5; ++q) {
     // Barth-Jespersen: the largest factor keeping every face value in [lo, hi]
     double alpha = 1.0;
-    for (int64_t k = k0; k < k1; ++k) {
-      const HydroSlot sl = slot[k];
-      const double dv = g[0] * sl.own[0] + g[1] * sl.own[1] + g[2] * sl.own[2];
-      double al = 1.0;
-      if (dv > 0.0)
-        al = (hi - v) / dv;
-      else if (dv < 0.0)
-        al = (lo - v) / dv;
-      alpha = fmin(alpha, al);
-    }
-    double *out = grad + 15 * c;
+    if (dmax[q] > 0.0) alpha = fmin(alpha, (hi[q] - v[q]) / dmax[q]);
+    if (dmin[q] < 0.0) alpha = fmin(alpha, (lo[q] - v[q]) / dmin[q]);
 #pragma unroll
-    for (int x = 0; x < 3; ++x) out[5 * x + q] = g[x] * alpha;
+    for (int x = 0; x < 3; ++x) out[5 * x + q] = g[q][x] * alpha;
   }
 }
 

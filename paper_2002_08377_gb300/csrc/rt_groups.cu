@@ -142,39 +142,72 @@ __device__ int group_chain(const GroupArgs<R> &a, int64_t cl, const double (*sm)
 
 // The temperature equation of one interior cell in float from float inputs
 // (tile kernel, float states): per group rho kP_j, rho kJ_j, rho ks_j in kf
-// and the sums S_I,j, S_G,j, S_1,j.  Returns the status bits, or -1 when a
-// result is not finite (the caller then takes group_chain<double>).
+// and the sums S_I,j, S_G,j, S_1,j.  group_coeffs_f forms alpha, g and the
+// 1 / D_j (false when they are negative or not finite); group_q_f forms every
+// group's q_j from a root T (false when one is not finite); group_chain_f
+// solves the quartic in float between the two, returning the status bits, or
+// -1 when a result is not finite (the caller then takes group_chain<double>).
 constexpr int kTileGroups = 4;
-__device__ __forceinline__ int group_chain_f(const GroupArgs<float> &a, const float4 (&kf)[kTileGroups],
-                                             const float (&SI)[kTileGroups],
-                                             const float (&SG)[kTileGroups],
-                                             const float (&S1)[kTileGroups], float eint, float rcv,
-                                             float (&q)[kTileGroups]) {
-  float alpha = 0.0f, gq = eint, rU[kTileGroups];
+struct GroupQuarticF {
+  float alpha, gq, rU[kTileGroups];
+};
+__device__ __forceinline__ bool group_coeffs_f(const GroupArgs<float> &a,
+                                               const float4 (&kf)[kTileGroups],
+                                               const float (&SI)[kTileGroups],
+                                               const float (&SG)[kTileGroups],
+                                               const float (&S1)[kTileGroups], float eint,
+                                               GroupQuarticF &k) {
+  k.alpha = 0.0f;
+  k.gq = eint;
 #pragma unroll
   for (int j = 0; j < kTileGroups; ++j) {
-    rU[j] = 0.0f;
+    k.rU[j] = 0.0f;
     if (j < a.G) {
-      rU[j] = rcp(fmaf(a.k_dcr_f * kf[j].y, SG[j], S1[j]));
-      alpha = fmaf(a.Wk_alpha_f[j] * kf[j].x * S1[j], rU[j], alpha);
-      gq = fmaf(a.Wk_g_f[j] * kf[j].y * SI[j], rU[j], gq);
+      k.rU[j] = rcp(fmaf(a.k_dcr_f * kf[j].y, SG[j], S1[j]));
+      k.alpha = fmaf(a.Wk_alpha_f[j] * kf[j].x * S1[j], k.rU[j], k.alpha);
+      k.gq = fmaf(a.Wk_g_f[j] * kf[j].y * SI[j], k.rU[j], k.gq);
     }
   }
-  if (!(gq >= 0.0f) || !(alpha >= 0.0f) || !isfinite(alpha) || !isfinite(gq)) return -1;
-  float T;
-  const int nc = quartic_root(alpha, rcv, gq, eint * rcp(rcv), 1e-7f, a.newton_max_iter, &T);
+  return k.gq >= 0.0f && k.alpha >= 0.0f && isfinite(k.alpha) && isfinite(k.gq);
+}
+__device__ __forceinline__ bool group_q_f(const GroupArgs<float> &a,
+                                          const float4 (&kf)[kTileGroups],
+                                          const float (&SI)[kTileGroups],
+                                          const float (&SG)[kTileGroups], const GroupQuarticF &k,
+                                          float T, float (&q)[kTileGroups]) {
   const float B = a.a_rad_4pi_f * (T * T) * (T * T);
+  bool ok = true;
 #pragma unroll
   for (int j = 0; j < kTileGroups; ++j) {
     q[j] = 0.0f;
     if (j < a.G) {
       const float dP = a.k_dcr_f * kf[j].x, dS = a.k_dcr_f * kf[j].z;
-      const float J = fmaf(dP * B, SG[j], SI[j]) * rU[j];
+      const float J = fmaf(dP * B, SG[j], SI[j]) * k.rU[j];
       q[j] = fmaf(dP, B, dS * J);
-      if (!isfinite(q[j])) return -1;
+      ok = ok && isfinite(q[j]);
     }
   }
+  return ok;
+}
+__device__ __forceinline__ int group_chain_f(const GroupArgs<float> &a, const float4 (&kf)[kTileGroups],
+                                             const float (&SI)[kTileGroups],
+                                             const float (&SG)[kTileGroups],
+                                             const float (&S1)[kTileGroups], float eint, float rcv,
+                                             float (&q)[kTileGroups]) {
+  GroupQuarticF k;
+  if (!group_coeffs_f(a, kf, SI, SG, S1, eint, k)) return -1;
+  float T;
+  const int nc = quartic_root(k.alpha, rcv, k.gq, eint * rcp(rcv), 1e-7f, a.newton_max_iter, &T);
+  if (!group_q_f(a, kf, SI, SG, k, T, q)) return -1;
   return nc ? (int)ST_NONCONV : 0;
+}
+// The float opacities of a cell's groups (zero past G).
+__device__ __forceinline__ void load_kf(const GroupArgs<float> &a, int64_t c,
+                                        float4 (&kf)[kTileGroups]) {
+#pragma unroll
+  for (int g = 0; g < kTileGroups; ++g)
+    kf[g] = g < a.G ? reinterpret_cast<const float4 *>(a.kapgf)[(size_t)c * a.G + g]
+                    : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
 template <typename R, int NT>
@@ -387,15 +420,19 @@ __global__ void __launch_bounds__(kThreads) group_source_kernel(const GroupArgs<
 // The same step for up to kTileGroups groups on the step kernel's tile
 // mapping (blocks of 32 cells x 8 threads, a thread owning the pairs of its
 // pair / quad map).  The group of pair p is p / Hb, and every sum is kept
-// per group (unused groups stay zero).  Float states solve the temperature
-// equation in all 8 lanes of a cell in float, from float copies of the group
-// opacities (in double if a result is not finite), with no block barrier;
-// double states solve it one lane per cell between two barriers.  The gas
-// exchange is one lane per cell in double after a barrier, as in the grey
-// step.
+// per group (unused groups stay zero).  Float states find the root of the
+// temperature equation in float in all 8 lanes of a cell, from float copies
+// of the group opacities; by default one lane per cell then refines it by a
+// Newton step in double between two block barriers and forms the groups' q_j
+// (float_quartic = 1 keeps the float root, with no barrier); where a float
+// result is not finite the double chain runs instead.  Double states solve
+// it one lane per cell in double between two barriers.  The gas exchange is
+// one lane per cell in double after a barrier, as in the grey step.
 template <typename R> struct TileShared {
-  double s[CPB][kTileGroups][3];  // double states: S_I, S_G, S_1 per group
+  double s[CPB][kTileGroups][3];  // S_I, S_G, S_1 per group
   R q[CPB][kTileGroups];
+  float qT[CPB];                  // float states: the in-lane float root
+  unsigned fst[CPB];              // float states: 0 when that root is usable
   R dE[CPB], dF[3][CPB];
   unsigned bad[CPB];
 };
@@ -490,10 +527,7 @@ __global__ void __launch_bounds__(step::NT, sizeof(R) == 4 && M::PPT <= 6 ? 3 : 
   if (lane_solve) {
     if constexpr (sizeof(R) == 4) if (kind == RT_CELL_INTERIOR) {
       float4 kf[NG];
-#pragma unroll
-      for (int g = 0; g < NG; ++g)
-        kf[g] = g < a.G ? reinterpret_cast<const float4 *>(a.kapgf)[(size_t)c * a.G + g]
-                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      load_kf(a, c, kf);
       const int st = group_chain_f(a, kf, sI, sG, s1, a.cellv[4 * c + 3], a.gs[c].frcv, q);
       if (st >= 0) {
         bad = st;
@@ -513,6 +547,24 @@ __global__ void __launch_bounds__(step::NT, sizeof(R) == 4 && M::PPT <= 6 ? 3 : 
       }
     }
   } else {
+    // float states (default): every lane finds the float root of the
+    // temperature equation from the float sums (no barrier); one lane per
+    // cell then refines it by a Newton step in double (the FP64 temperature
+    // solve) and forms the groups' q_j in float from it, or, where the float
+    // solve failed, runs the whole double chain.  Double states: the double
+    // chain, one lane per cell.
+    float Tf = 0.0f;
+    unsigned fst = 1;
+    if constexpr (sizeof(R) == 4) if (kind == RT_CELL_INTERIOR) {
+      float4 kf[NG];
+      load_kf(a, c, kf);
+      GroupQuarticF k;
+      const float eint = a.cellv[4 * c + 3], rcv = a.gs[c].frcv;
+      if (group_coeffs_f(a, kf, sI, sG, s1, eint, k) &&
+          !quartic_root(k.alpha, rcv, k.gq, eint * rcp(rcv), 1e-7f, a.newton_max_iter, &Tf) &&
+          isfinite(Tf))
+        fst = 0;
+    }
     if (sub == 0) {
 #pragma unroll
       for (int g = 0; g < NG; ++g) {
@@ -520,13 +572,39 @@ __global__ void __launch_bounds__(step::NT, sizeof(R) == 4 && M::PPT <= 6 ? 3 : 
         sh.s[lc][g][1] = sG[g];
         sh.s[lc][g][2] = s1[g];
       }
+      sh.qT[lc] = Tf;
+      sh.fst[lc] = fst;
     }
     __syncthreads();
     if (threadIdx.x < CPB) {
       const int lp = threadIdx.x;
       const int64_t cl = (int64_t)blockIdx.x * CPB + lp;
       unsigned bl = 0;
-      if (cl < a.n && a.kind[cl] == RT_CELL_INTERIOR) {
+      bool done = false;
+      if constexpr (sizeof(R) == 4)
+        if (cl < a.n && a.kind[cl] == RT_CELL_INTERIOR && sh.fst[lp] == 0) {
+          float4 kf[NG];
+          load_kf(a, cl, kf);
+          float SI[NG], SG[NG], S1[NG];
+#pragma unroll
+          for (int g = 0; g < NG; ++g) {
+            SI[g] = (float)sh.s[lp][g][0];
+            SG[g] = (float)sh.s[lp][g][1];
+            S1[g] = (float)sh.s[lp][g][2];
+          }
+          GroupQuarticF k;  // the in-lane coefficients, formed again from the same floats
+          group_coeffs_f(a, kf, SI, SG, S1, a.cellv[4 * cl + 3], k);
+          const double T = step::refine_root((double)k.alpha, 4.0, a.gs[cl].rcv, (double)k.gq,
+                                             (double)sh.qT[lp]);
+          float qf[NG];
+          if (group_q_f(a, kf, SI, SG, k, (float)T, qf)) {
+#pragma unroll
+            for (int g = 0; g < NG; ++g)
+              if (g < a.G) sh.q[lp][g] = qf[g];
+            done = true;
+          }
+        }
+      if (!done && cl < a.n && a.kind[cl] == RT_CELL_INTERIOR) {
         const GasDyn d = a.gd[cl];
         const GasStatic gs = a.gs[cl];
         const double eint = d.e - 0.5 * (d.mx * d.mx + d.my * d.my + d.mz * d.mz) * gs.inv_rho;

@@ -162,24 +162,6 @@ __device__ __forceinline__ float source_q_float(const StepArgs<float> &a, int64_
   return (float)source_q(a, a.gs[c], a.gd[c], (double)SI, (double)SG, (double)S1, bad);
 }
 
-// Newton in double on alpha T^k + beta T = g (k = 4 + beta_P) from the float
-// root T: STEPS steps, each with f and f' in double and the quotient f / f'
-// in float.  From a float-accurate start (relative error e0 of a few float
-// ulp, ~1e-7) a step leaves about e0 (float epsilon + e0), ~1e-13: one step
-// is below the float rounding of the q it feeds, two reach double precision.
-template <int STEPS = 1>
-__device__ __forceinline__ double refine_root(double alpha, double k, double beta, double g,
-                                              double T) {
-#pragma unroll
-  for (int it = 0; it < STEPS; ++it) {
-    const double Tk1 = k == 4.0 ? (T * T) * T : pow(T, k - 1.0);
-    const double f = fma(alpha * Tk1, T, fma(beta, T, -g));
-    const double fp = fma(k * alpha, Tk1, beta);
-    T -= (double)((float)f * rcp((float)fp));
-  }
-  return T;
-}
-
 // q of an interior cell of a float state (float_quartic = 0), one lane per
 // cell: the float coefficients and root as in source_q_float, the root
 // refined in double by refine_root, q in float from it; where a float value

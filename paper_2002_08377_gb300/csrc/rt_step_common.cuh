@@ -176,6 +176,24 @@ __device__ __forceinline__ int quartic_root(T_ alpha, T_ beta, T_ g, T_ T0, T_ t
   return done ? 0 : 1;
 }
 
+// Newton in double on alpha T^k + beta T = g (k = 4 + beta_P) from the float
+// root T: STEPS steps, each with f and f' in double and the quotient f / f'
+// in float.  From a float-accurate start (relative error e0 of a few float
+// ulp, ~1e-7) a step leaves about e0 (float epsilon + e0), ~1e-13: one step
+// is below the float rounding of the q it feeds, two reach double precision.
+template <int STEPS = 1>
+__device__ __forceinline__ double refine_root(double alpha, double k, double beta, double g,
+                                              double T) {
+#pragma unroll
+  for (int it = 0; it < STEPS; ++it) {
+    const double Tk1 = k == 4.0 ? (T * T) * T : pow(T, k - 1.0);
+    const double f = fma(alpha * Tk1, T, fma(beta, T, -g));
+    const double fp = fma(k * alpha, Tk1, beta);
+    T -= (double)((float)f * rcp((float)fp));
+  }
+  return T;
+}
+
 // Positive root of alpha T^k + beta T = g for k >= 1 (alpha >= 0, beta > 0,
 // g >= 0): the temperature equation when kappa_P is proportional to T^(k-4).
 // The left side is increasing and convex for T >= 0, so, as for

@@ -38,10 +38,14 @@ UNIT = "cell-angle updates/s"
 
 # DRAM bytes (read + write) per launch of the step kernels, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum, one launch, one
-# pass) at the benchmarked size of each workload; valid while the step
-# kernel's device source has the recorded hash (else reported as null).
-NCU_TRAFFIC = {}
-NCU_SOURCE_SHA = None
+# pass); valid while the step kernel's device source has the recorded hash
+# (else reported as null).  FP32: the 256^3 linear-wave launch itself
+# (12.43 GB read + 6.15 GB written).  FP64: the 128^3 linear-wave launch
+# (12.52 + 1.49 GB, mostly the flux-coefficient table) scaled by the cell
+# count to 256^3 (the table, the rows and the gas all grow with the cells).
+NCU_TRAFFIC = {("waves", 16777216, "fp32"): 18.58e9,
+               ("waves", 16777216, "fp64"): 14.01e9 * 8}
+NCU_SOURCE_SHA = "87d149ce2c972f0c"
 # FP64 arithmetic peak when the DGEMM probe cannot run: the nominal dense
 # FP64 FMA rate of the GPU.
 FP64_NOMINAL_GFLOPS = 1250.0
@@ -356,23 +360,32 @@ class _Null:
         pass
 
 
-def e2e_rate(sol, prob, dt, steps):
+def e2e_rate(sol, prob, dt, steps, pipelined=True):
     """Through the C ABI with pinned host buffers: every step copies the
-    intensities in, runs the step and copies them out."""
+    intensities in, runs the step and copies them out.  pipelined: rt_step_io
+    (the host copies run on the copy engines and overlap the neighbouring
+    steps' GPU work), two output buffers in turn; otherwise rt_set_intensity,
+    rt_step, rt_get_intensity, each synchronous."""
     import torch
     N, A = prob.n_cells, prob.n_angles
     host_in = torch.empty((N, A), dtype=torch.float32, pin_memory=True)
     host_in.numpy()[:] = prob.initial_intensity(np.float32)
-    host_out = torch.empty((N, A), dtype=torch.float32, pin_memory=True)
+    outs = [torch.empty((N, A), dtype=torch.float32, pin_memory=True) for _ in range(2)]
     lib, st = sol.lib, sol.state
-    pin, pout = ctypes.c_void_p(host_in.data_ptr()), ctypes.c_void_p(host_out.data_ptr())
+    pin = ctypes.c_void_p(host_in.data_ptr())
+    pouts = [ctypes.c_void_p(o.data_ptr()) for o in outs]
     used = ctypes.c_double()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(steps):
-        sol._check(lib.rt_set_intensity(st, pin, 0))
-        sol._check(lib.rt_step(st, dt, ctypes.byref(used)))
-        sol._check(lib.rt_get_intensity(st, pout, 0))
+    if pipelined:
+        for k in range(steps):
+            sol._check(lib.rt_step_io(st, dt, pin, pouts[k % 2]))
+        sol._check(lib.rt_sync(st))
+    else:
+        for _ in range(steps):
+            sol._check(lib.rt_set_intensity(st, pin, 0))
+            sol._check(lib.rt_step(st, dt, ctypes.byref(used)))
+            sol._check(lib.rt_get_intensity(st, pouts[0], 0))
     el = time.perf_counter() - t0
     nbytes = N * A * 4
     return N * A * steps / el, nbytes, nbytes
@@ -519,10 +532,28 @@ def host_link_ceiling(n_bytes):
             e1.record()
             torch.cuda.synchronize()
             best[k] = min(best[k], e0.elapsed_time(e1))
-    del h, d
+    # both directions at once, on two streams (what a pipelined step's copies
+    # can share): wall time of the pair, best of 3
+    h2 = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    d2 = torch.empty(n, dtype=torch.float32, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    both = 1e30
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s1):
+            d.copy_(h, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h2.copy_(d2, non_blocking=True)
+        torch.cuda.synchronize()
+        both = min(both, (time.perf_counter() - t0) * 1e3)
+    del h, d, h2, d2
     torch.cuda.empty_cache()
-    return {k: {"GB_per_s": 4 * n / (ms * 1e-3) / 1e9, "ms": ms, "bytes": 4 * n}
-            for k, ms in best.items()}
+    out = {k: {"GB_per_s": 4 * n / (ms * 1e-3) / 1e9, "ms": ms, "bytes": 4 * n}
+           for k, ms in best.items()}
+    out["both_ways"] = {"GB_per_s": 8 * n / (both * 1e-3) / 1e9, "ms": both, "bytes": 8 * n,
+                        "note": "one copy each way at the same time on two streams (wall time)"}
+    return out
 
 
 def fp64_peak_probe():
@@ -594,9 +625,17 @@ def time_workload(prob, precs, steps, warmup, world, hbm_peak, peak_kind, fp64_p
                     "roofline": roofline(prec, N, Nf, A, per, hbm_peak, peak_kind, fp64_peak,
                                          fp64_kind, tr)}
         if key == "fp32" and e2e:
-            e2e_v, bi, bo = e2e_rate(sol, prob, dt, max(3, min(10, steps)))
+            k_e2e = max(3, min(10, steps))
+            e2e_rate(sol, prob, dt, 2)  # the copy streams and their events
+            e2e_v, bi, bo = e2e_rate(sol, prob, dt, k_e2e)
+            seq_v, _, _ = e2e_rate(sol, prob, dt, k_e2e, pipelined=False)
             res["e2e"] = {"value": e2e_v * world, "unit": UNIT, "h2d_bytes_per_step": bi,
-                          "d2h_bytes_per_step": bo}
+                          "d2h_bytes_per_step": bo, "steps": k_e2e,
+                          "api": "rt_step_io (pinned host rows in and out every step, copied by "
+                                 "the copy engines while the neighbouring steps run), then rt_sync",
+                          "sequential": {"value": seq_v * world,
+                                         "api": "rt_set_intensity, rt_step, rt_get_intensity "
+                                                "per step, each synchronous"}}
         sol.close()
         del sol
         torch.cuda.empty_cache()

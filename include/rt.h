@@ -264,6 +264,24 @@ int rt_run(rt_state *s, int32_t n_steps, double dt, double *dt_used);
  * rt_step, rt_run, rt_totals).  dt and the CFL check as for rt_step. */
 int rt_launch(rt_state *s, int32_t n_steps, double dt, double *dt_used);
 
+/* One full step whose intensities come from and go to page-locked host
+ * memory, queued without waiting (a serving loop of rt_set_intensity,
+ * rt_step, rt_get_intensity whose host copies overlap the GPU work): the
+ * rows I_in[N][A] (caller order, state precision) replace the state's
+ * intensities, one step runs (as rt_step: dt <= 0 selects dt_cfl,
+ * RT_ERR_CFL if dt > dt_max), and the new rows are written to I_out[N][A].
+ * The host copies run on the copy engines, on two streams of the state,
+ * into and out of two device staging arrays that the device permutes then
+ * read and write: a call's input copy overlaps the previous call's step and
+ * result copy.  I_in and I_out must be page-locked in full (cudaHostAlloc /
+ * cudaHostRegister; RT_ERR_ARG otherwise) and left alone until rt_sync (or
+ * any call that returns the latched status) returns; an I_out must not be
+ * the I_in of a call queued after it.  Per-cell failures latch as for
+ * rt_launch.  The first call allocates the two staging arrays (the size of
+ * the intensities each), kept until rt_destroy.  The results equal
+ * rt_set_intensity, rt_step, rt_get_intensity bit for bit. */
+int rt_step_io(rt_state *s, double dt, const void *I_in, void *I_out);
+
 /* Lab-frame moments (Sec. 2.1 / Eqs. moments energy, moments flux) of the
  * current intensities, double precision, caller order: E[N], F[N][3],
  * P[N][6] (xx, yy, zz, xy, xz, yz).  Any pointer may be NULL. */
@@ -295,7 +313,8 @@ int rt_totals(rt_state *s, double out[16]);
  * status (rt_sync does).  out: host, 16 doubles, layout of rt_totals. */
 int rt_totals_noalloc(rt_state *s, double out[16]);
 
-/* Waits for the state's stream and returns the latched per-cell status. */
+/* Waits for the state's stream and rt_step_io's result copies, and returns
+ * the latched per-cell status. */
 int rt_sync(rt_state *s);
 
 /* Discrete adjoint of one full step (the reverse of rt_step): given the

@@ -17,7 +17,7 @@ _NAMES = {0: "RT_OK", -1: "RT_ERR_ARG", -2: "RT_ERR_MESH", -3: "RT_ERR_CUDA", -4
 
 # every symbol include/rt.h declares (checked by the CPU tests)
 EXPORTS = ["rt_create", "rt_set_gas", "rt_set_gas_energy", "rt_set_cells", "rt_set_intensity", "rt_get_intensity",
-           "rt_get_gas", "rt_dt_limits", "rt_step", "rt_run", "rt_launch", "rt_moments", "rt_totals", "rt_totals_noalloc",
+           "rt_get_gas", "rt_dt_limits", "rt_step", "rt_step_io", "rt_run", "rt_launch", "rt_moments", "rt_totals", "rt_totals_noalloc",
            "rt_sync", "rt_adjoint_step", "rt_hydro_step", "rt_hydro_dt", "rt_radhydro_step",
            "rt_get_density", "rt_get_state", "rt_set_state", "rt_device_bytes", "rt_launch_count",
            "rt_last_error", "rt_destroy"]
@@ -81,6 +81,7 @@ def load(build_if_missing=True):
         "rt_get_gas": ([vp, vp, vp, vp, i32], i32),
         "rt_dt_limits": ([vp, pd, pd], i32),
         "rt_step": ([vp, d, pd], i32),
+        "rt_step_io": ([vp, d, vp, vp], i32),
         "rt_run": ([vp, i32, d, pd], i32),
         "rt_launch": ([vp, i32, d, pd], i32),
         "rt_moments": ([vp, vp, vp, vp, i32], i32),

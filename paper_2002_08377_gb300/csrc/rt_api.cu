@@ -395,6 +395,7 @@ int check_float_range(rt_state *s, const rt_mesh_desc *m, double cbar) {
 
 int sync_status(rt_state *s) {
   RT_CUDA(s, cudaStreamSynchronize(s->stream));
+  if (s->io_out) RT_CUDA(s, cudaStreamSynchronize(s->io_out));  // rt_step_io's result copies
   unsigned st = 0;
   unsigned long long bad = 0;
   RT_CUDA(s, cudaMemcpy(&st, s->d_status, sizeof st, cudaMemcpyDeviceToHost));
@@ -1065,6 +1066,50 @@ int rt_step(rt_state *s, double dt, double *dt_used) {
   return launch_steps(s, 1, dt, dt_used, true);
 }
 
+int rt_step_io(rt_state *s, double dt, const void *I_in, void *I_out) {
+  if (!s || !I_in || !I_out) return s ? fail(s, RT_ERR_ARG, "rt_step_io: NULL") : RT_ERR_ARG;
+  if (!s->gas_set) return fail(s, RT_ERR_STATE, "rt_set_gas must be called before stepping");
+  if (!(dt > 0)) dt = s->dt_cfl;
+  if (!std::isfinite(dt)) return fail(s, RT_ERR_ARG, "dt must be finite");
+  if (dt > s->dt_max) return fail(s, RT_ERR_CFL, "rt_step_io: dt exceeds the upwind positivity limit");
+  const size_t bytes = (size_t)s->n_cells * s->n_angles * s->rsize;
+  if (!pinned_device_address(I_in, bytes) || !pinned_device_address(I_out, bytes))
+    return fail(s, RT_ERR_ARG, "rt_step_io: I_in and I_out must be page-locked host memory in full");
+  if (!s->io_in) {
+    RT_CUDA(s, dalloc_bytes(s, &s->d_io_in, bytes));
+    RT_CUDA(s, dalloc_bytes(s, &s->d_io_out, bytes));
+    RT_CUDA(s, cudaStreamCreateWithFlags(&s->io_in, cudaStreamNonBlocking));
+    RT_CUDA(s, cudaStreamCreateWithFlags(&s->io_out, cudaStreamNonBlocking));
+    for (cudaEvent_t *e : {&s->ev_h2d, &s->ev_pin, &s->ev_pout, &s->ev_d2h})
+      RT_CUDA(s, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    // nothing staged yet: both staging arrays are free after the work queued so far
+    RT_CUDA(s, cudaEventRecord(s->ev_pin, s->stream));
+    RT_CUDA(s, cudaEventRecord(s->ev_d2h, s->stream));
+  }
+  ++s->gen;  // the rows change outside the captured step graphs
+  // in: host rows -> staging (copy engine), once the previous call's device
+  // permute has read the staging array; it overlaps that call's step and
+  // result copy
+  RT_CUDA(s, cudaStreamWaitEvent(s->io_in, s->ev_pin, 0));
+  RT_CUDA(s, cudaMemcpyAsync(s->d_io_in, I_in, bytes, cudaMemcpyHostToDevice, s->io_in));
+  RT_CUDA(s, cudaEventRecord(s->ev_h2d, s->io_in));
+  // the state's stream: staging -> internal rows, the step, internal rows ->
+  // the result staging (once the previous result has been copied out)
+  RT_CUDA(s, cudaStreamWaitEvent(s->stream, s->ev_h2d, 0));
+  RT_CUDA(s, rt::launch_permute_in(s, s->d_io_in, s->d_I[s->cur], s->row_stride));
+  RT_CUDA(s, cudaEventRecord(s->ev_pin, s->stream));
+  RT_CUDA(s, rt::launch_step(s, dt));
+  RT_CUDA(s, cudaStreamWaitEvent(s->stream, s->ev_d2h, 0));
+  RT_CUDA(s, rt::launch_permute_out(s, s->d_I[s->cur], s->d_io_out, s->row_stride));
+  RT_CUDA(s, cudaEventRecord(s->ev_pout, s->stream));
+  // out: result staging -> host rows (copy engine), overlapping the next
+  // call's input copy and step
+  RT_CUDA(s, cudaStreamWaitEvent(s->io_out, s->ev_pout, 0));
+  RT_CUDA(s, cudaMemcpyAsync(I_out, s->d_io_out, bytes, cudaMemcpyDeviceToHost, s->io_out));
+  RT_CUDA(s, cudaEventRecord(s->ev_d2h, s->io_out));
+  return RT_OK;
+}
+
 int rt_run(rt_state *s, int32_t n, double dt, double *dt_used) {
   return launch_steps(s, n, dt, dt_used, true);
 }
@@ -1309,6 +1354,15 @@ void rt_destroy(rt_state *s) {
   for (int k = 0; k < 2; ++k)
     if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  for (cudaStream_t st : {s->io_in, s->io_out})
+    if (st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+  for (cudaEvent_t e : {s->ev_h2d, s->ev_pin, s->ev_pout, s->ev_d2h})
+    if (e) cudaEventDestroy(e);
+  if (s->d_io_in) cudaFree(s->d_io_in);
+  if (s->d_io_out) cudaFree(s->d_io_out);
   for (int k = 0; k < 8; ++k)
     if (s->d_adj[k]) cudaFree(s->d_adj[k]);
   if (s->d_adj_ws) cudaFree(s->d_adj_ws);

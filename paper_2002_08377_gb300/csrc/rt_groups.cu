@@ -594,8 +594,8 @@ __global__ void __launch_bounds__(step::NT, sizeof(R) == 4 && M::PPT <= 6 ? 3 : 
           }
           GroupQuarticF k;  // the in-lane coefficients, formed again from the same floats
           group_coeffs_f(a, kf, SI, SG, S1, a.cellv[4 * cl + 3], k);
-          const double T = step::refine_root((double)k.alpha, 4.0, a.gs[cl].rcv, (double)k.gq,
-                                             (double)sh.qT[lp]);
+          const double T =
+              step::refine_root(k.alpha, 0.0f, 0.0, a.gs[cl].rcv, k.gq, sh.qT[lp]);
           float qf[NG];
           if (group_q_f(a, kf, SI, SG, k, (float)T, qf)) {
 #pragma unroll

@@ -168,6 +168,13 @@ struct rt_state {
   uint64_t gen = 1;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaStream_t cap_stream = nullptr;  // the stream graphs are captured on
+  // pipelined host I/O (rt_step_io): the copy-engine streams, the device
+  // staging rows of the host copies (caller order), and the events that
+  // order them: ev_h2d the rows landed, ev_pin the staged input consumed,
+  // ev_pout the result staged, ev_d2h the result copied out
+  cudaStream_t io_in = nullptr, io_out = nullptr;
+  void *d_io_in = nullptr, *d_io_out = nullptr;
+  cudaEvent_t ev_h2d = nullptr, ev_pin = nullptr, ev_pout = nullptr, ev_d2h = nullptr;
   double graph_dt[2] = {0.0, 0.0};
   uint64_t graph_gen[2] = {0, 0};
   int64_t graph_launches[2] = {0, 0};

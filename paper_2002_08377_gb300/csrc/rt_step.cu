@@ -178,7 +178,7 @@ __device__ __forceinline__ float source_q_refined(const StepArgs<float> &a, cons
   float Tf;
   if (isfinite(k.alpha) && isfinite(k.gq) && !float_root(a, k, gr.frcv, eint, &Tf) &&
       isfinite(Tf)) {
-    const double T = refine_root((double)k.alpha, 4.0 + a.beta_P, gr.rcv, (double)k.gq, (double)Tf);
+    const double T = refine_root(k.alpha, a.beta_P_f, a.beta_P, gr.rcv, k.gq, Tf);
     const float q = float_q(a, k, (float)T, SI, SG);
     if (isfinite(q)) return q;
   }
@@ -372,8 +372,8 @@ __device__ __forceinline__ void tile_step(const StepArgs<R> &a, const int64_t ti
         const unsigned st = sh.bad[lp];
         const GasStatic &gr = gs_s[lp];
         if (st == 0) {
-          const double T = refine_root((double)sh.qa[lp], 4.0 + a.beta_P, gr.rcv,
-                                       (double)sh.qg[lp], (double)sh.qT[lp]);
+          const double T = refine_root(sh.qa[lp], a.beta_P_f, a.beta_P, gr.rcv, sh.qg[lp],
+                                       sh.qT[lp]);
           const QuarticF k = float_coeffs(a, gr.frkP, gr.frkJ, gr.frkS, 0.0f, sh.sI[lp],
                                           sh.sG[lp], sh.s1[lp]);
           ql = float_q(a, k, (float)T, sh.sI[lp], sh.sG[lp]);

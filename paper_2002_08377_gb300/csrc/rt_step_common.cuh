@@ -176,22 +176,28 @@ __device__ __forceinline__ int quartic_root(T_ alpha, T_ beta, T_ g, T_ T0, T_ t
   return done ? 0 : 1;
 }
 
-// Newton in double on alpha T^k + beta T = g (k = 4 + beta_P) from the float
-// root T: STEPS steps, each with f and f' in double and the quotient f / f'
-// in float.  From a float-accurate start (relative error e0 of a few float
-// ulp, ~1e-7) a step leaves about e0 (float epsilon + e0), ~1e-13: one step
-// is below the float rounding of the q it feeds, two reach double precision.
-template <int STEPS = 1>
-__device__ __forceinline__ double refine_root(double alpha, double k, double beta, double g,
-                                              double T) {
-#pragma unroll
-  for (int it = 0; it < STEPS; ++it) {
-    const double Tk1 = k == 4.0 ? (T * T) * T : pow(T, k - 1.0);
-    const double f = fma(alpha * Tk1, T, fma(beta, T, -g));
-    const double fp = fma(k * alpha, Tk1, beta);
-    T -= (double)((float)f * rcp((float)fp));
+// One Newton step in double on alpha T^k + beta T = g (k = 4 + beta_P) from
+// the float root T0 of the float coefficients alpha, g: the residual f in
+// double, f' and the quotient f / f' in float.  From a float-accurate start
+// (relative error e0 of a few float ulp, ~1e-7) the step leaves about
+// e0 (float epsilon + e0), ~1e-13, below the float rounding of the q it
+// feeds.  beta_P_f == 0 selects the quartic (T^3 by multiplication); f' in
+// float costs nothing in accuracy since the quotient is taken in float.
+__device__ __forceinline__ double refine_root(float alpha, float beta_P_f, double beta_P,
+                                              double beta, float g, float T0) {
+  const double T = (double)T0;
+  double Tk1;
+  float kf;
+  if (beta_P_f == 0.0f) {
+    Tk1 = (T * T) * T;
+    kf = 4.0f;
+  } else {
+    Tk1 = pow(T, 3.0 + beta_P);
+    kf = 4.0f + beta_P_f;
   }
-  return T;
+  const double f = fma((double)alpha * Tk1, T, fma(beta, T, -(double)g));
+  const float fp = fmaf(kf * alpha, (float)Tk1, (float)beta);
+  return T - (double)((float)f * rcp(fp));
 }
 
 // Positive root of alpha T^k + beta T = g for k >= 1 (alpha >= 0, beta > 0,

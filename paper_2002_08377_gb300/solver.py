@@ -156,6 +156,19 @@ class RTSolver:
     def sync(self):
         self._check(self.lib.rt_sync(self.state))
 
+    def step_io(self, host_in, host_out, dt=0.0):
+        """Queue one step that reads its intensities from the page-locked host
+        tensor host_in and writes the result to the page-locked host tensor
+        host_out (both [N][A] in the state's precision; rt_step_io).  Leave
+        both untouched until sync()."""
+        for t in (host_in, host_out):
+            if (tuple(t.shape) != (self.N, self.A) or t.dtype != self.tdtype or not t.is_pinned()
+                    or not t.is_contiguous()):
+                raise ValueError("step_io wants page-locked host tensors of shape (N, A) "
+                                 "in the state's precision")
+        self._check(self.lib.rt_step_io(self.state, float(dt), ctypes.c_void_p(host_in.data_ptr()),
+                                        ctypes.c_void_p(host_out.data_ptr())))
+
     # -------------------------------------------------------------- outputs
     def get_intensity(self, device=False):
         if device:

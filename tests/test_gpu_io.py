@@ -82,3 +82,56 @@ def test_set_gas_energy_restores_a_checkpoint(precision):
         e2, m2, _ = g.gas()
         assert np.array_equal(e2, ref_e) and np.array_equal(m2, ref_m)
     g.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_step_io_pipeline_matches_synchronous_steps(case):
+    """rt_step_io queued five times with different input rows and one output
+    buffer per call (the host copies of consecutive calls overlap their
+    neighbours' GPU work on the state's copy streams) against rt_set_intensity / rt_step / rt_get_intensity on a
+    second state: every result and the final gas bit for bit.  A synchronous
+    call after the queue (rt_get_intensity) sees the last result."""
+    import torch
+    prob_fn, precision = CASES[case]
+    a, b = solver(prob_fn(), precision), solver(prob_fn(), precision)
+    N, A = a.N, a.A
+    dt = 0.5 * a.dt_limits()[1]
+    rng = np.random.default_rng(11)
+    K = 5
+    rows = [rng.random((N, A)).astype(a.dtype) for _ in range(K)]
+    pin_in = [torch.empty((N, A), dtype=a.tdtype, pin_memory=True) for _ in range(K)]
+    pin_out = [torch.zeros((N, A), dtype=a.tdtype, pin_memory=True) for _ in range(K)]
+    for k in range(K):
+        pin_in[k].numpy()[:] = rows[k]
+        a.step_io(pin_in[k], pin_out[k], dt)
+    a.sync()
+    for k in range(K):
+        b.set_intensity(rows[k])
+        b.step(dt)
+        assert np.array_equal(pin_out[k].numpy(), b.get_intensity()), k
+    assert np.array_equal(a.get_intensity(), pin_out[K - 1].numpy())
+    ea, ma, xa = a.gas()
+    eb, mb, xb = b.gas()
+    assert np.array_equal(ea, eb) and np.array_equal(ma, mb) and np.array_equal(xa, xb)
+    # a plain step after the queue continues from the last result
+    a.step(dt)
+    b.step(dt)
+    assert np.array_equal(a.get_intensity(), b.get_intensity())
+    a.close()
+    b.close()
+
+
+def test_step_io_refuses_pageable_rows():
+    """Rows that are not page-locked in full take RT_ERR_ARG (the synchronous
+    calls stage them instead)."""
+    import torch
+    prob_fn, precision = CASES["fp32_quad"]
+    s = solver(prob_fn(), precision)
+    N, A = s.N, s.A
+    pinned = torch.zeros((N, A), dtype=s.tdtype, pin_memory=True)
+    pageable = np.zeros((N, A), s.dtype)
+    code = s.lib.rt_step_io(s.state, 0.0, pageable.ctypes.data, ctypes.c_void_p(pinned.data_ptr()))
+    assert code == capi.RT_ERR_ARG
+    code = s.lib.rt_step_io(s.state, 0.0, ctypes.c_void_p(pinned.data_ptr()), pageable.ctypes.data)
+    assert code == capi.RT_ERR_ARG
+    s.close()

@@ -1367,7 +1367,7 @@ void rt_destroy(rt_state *s) {
     if (s->d_adj[k]) cudaFree(s->d_adj[k]);
   if (s->d_adj_ws) cudaFree(s->d_adj_ws);
   if (s->d_adj_stage) cudaFree(s->d_adj_stage);
-  void *bufs[] = {s->d_hface, s->d_hslot, s->d_hwork, s->d_kapgf, s->d_kapg, s->d_rkJ0, s->d_gcl_rate, s->d_gcl_kv, s->d_recon, s->d_lsq, s->d_Ihalf, s->d_grad, s->d_uface, s->d_slot_nb, s->d_wface, s->d_angle_of, s->d_pos_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
+  void *bufs[] = {s->d_hface, s->d_hslot, s->d_hlsq, s->d_hwork, s->d_kapgf, s->d_kapg, s->d_rkJ0, s->d_gcl_rate, s->d_gcl_kv, s->d_recon, s->d_lsq, s->d_Ihalf, s->d_grad, s->d_uface, s->d_slot_nb, s->d_wface, s->d_angle_of, s->d_pos_of, s->d_cellv, s->d_ptr, s->d_nbr, s->d_slot, s->d_inv_vol, s->d_cell_of, s->d_volume, s->d_gs,
                   s->d_gd, s->d_kind, s->d_aux, s->d_bc_row, s->d_I0, s->d_ext, s->d_dir, s->d_wt,
                   s->d_dir64, s->d_wt64, s->d_I[0], s->d_I[1], s->d_status, s->d_bad,
                   s->d_scratch, s->d_out16};

@@ -198,21 +198,56 @@ __global__ void update_kernel(const int64_t *__restrict__ ptr, const HydroSlot *
   }
 }
 
+// The static part of the least-squares gradients, once per state (the faces
+// do not move): per slot the weight A_f / |r|^2 times r = x_f - x_c - (x_f
+// - x_j'), and per cell the cofactors C and the determinant of the normal
+// matrix M = sum over the slots in list order of (A_f / |r|^2) r r^T, each
+// rounded as the per-step formula would round it.
+__global__ void lsq_setup_kernel(const int64_t *__restrict__ ptr, HydroSlot *slot, int64_t n,
+                                 double *lsq) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  double M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int64_t k = ptr[c]; k < ptr[c + 1]; ++k) {
+    HydroSlot &sl = slot[k];
+    const double r[3] = {sl.own[0] - sl.nbr[0], sl.own[1] - sl.nbr[1], sl.own[2] - sl.nbr[2]};
+    const double w = sl.area / (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    const double wr[3] = {w * r[0], w * r[1], w * r[2]};
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      sl.wr[x] = wr[x];
+#pragma unroll
+      for (int y = 0; y < 3; ++y) M[x][y] += wr[x] * r[y];
+    }
+  }
+  double *C = lsq + 10 * c;  // C[3 x + y], then the determinant
+  C[0] = M[1][1] * M[2][2] - M[1][2] * M[2][1];
+  C[1] = M[0][2] * M[2][1] - M[0][1] * M[2][2];
+  C[2] = M[0][1] * M[1][2] - M[0][2] * M[1][1];
+  C[3] = M[1][2] * M[2][0] - M[1][0] * M[2][2];
+  C[4] = M[0][0] * M[2][2] - M[0][2] * M[2][0];
+  C[5] = M[0][2] * M[1][0] - M[0][0] * M[1][2];
+  C[6] = M[1][0] * M[2][1] - M[1][1] * M[2][0];
+  C[7] = M[0][1] * M[2][0] - M[0][0] * M[2][1];
+  C[8] = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+  C[9] = M[0][0] * C[0] + M[0][1] * C[3] + M[0][2] * C[6];
+}
+
 // Limited least-squares gradients grad[c][3][5] of the primitives W[c][5]
-// (x, y, z components of the five fields); the order of every sum is the
-// cell's slot order.  Two passes over the cell's slots serve all five
-// fields: the first forms the normal matrix, the right-hand sides and the
-// neighbour range (each term rounded as the per-field formula rounds it),
-// the second the extreme face increments g . (x_f - x_c).  The
-// Barth-Jespersen factor min_f (hi - v) / dv (dv > 0) or (lo - v) / dv
-// (dv < 0) is taken as one division by the largest positive and one by the
-// most negative increment: the numerators have fixed signs and correctly
-// rounded division is monotone in the divisor, so the minimum is the same
-// number.
+// (x, y, z components of the five fields): g = M^-1 b with
+// b = sum A_f / |r|^2 r (W_j - W_c) over the cell's slots in list order (the
+// static weights and the inverse by cofactors from lsq_setup_kernel).  Two
+// passes over the cell's slots serve all five fields: the first forms the
+// right-hand sides and the neighbour range, the second the extreme face
+// increments g . (x_f - x_c).  The Barth-Jespersen factor min_f (hi - v) / dv
+// (dv > 0) or (lo - v) / dv (dv < 0) is taken as one division by the largest
+// positive and one by the most negative increment: the numerators have fixed
+// signs and correctly rounded division is monotone in the divisor, so the
+// minimum is the same number.
 __global__ void __launch_bounds__(kThreads, 2)
     gradient_kernel(const int64_t *__restrict__ ptr, const int32_t *__restrict__ nbr,
-                    const HydroSlot *__restrict__ slot, const double *__restrict__ W, int64_t n,
-                    double *grad) {
+                    const HydroSlot *__restrict__ slot, const double *__restrict__ lsq,
+                    const double *__restrict__ W, int64_t n, double *grad) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   const int64_t k0 = ptr[c], k1 = ptr[c + 1];
@@ -225,16 +260,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     hi[q] = v[q];
     b[q][0] = b[q][1] = b[q][2] = 0.0;
   }
-  double M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   for (int64_t k = k0; k < k1; ++k) {
-    const HydroSlot &sl = slot[k];
-    const double r[3] = {sl.own[0] - sl.nbr[0], sl.own[1] - sl.nbr[1], sl.own[2] - sl.nbr[2]};
-    const double w = sl.area / (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-    const double wr[3] = {w * r[0], w * r[1], w * r[2]};
-#pragma unroll
-    for (int x = 0; x < 3; ++x)
-#pragma unroll
-      for (int y = 0; y < 3; ++y) M[x][y] += wr[x] * r[y];
+    const double wr[3] = {slot[k].wr[0], slot[k].wr[1], slot[k].wr[2]};
     const double *Wj = W + 5 * (int64_t)nbr[k];
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
@@ -245,30 +272,19 @@ __global__ void __launch_bounds__(kThreads, 2)
       hi[q] = fmax(hi[q], vj);
     }
   }
-  // inverse of the symmetric 3 x 3 matrix by cofactors
-  double C[3][3];
-  C[0][0] = M[1][1] * M[2][2] - M[1][2] * M[2][1];
-  C[0][1] = M[0][2] * M[2][1] - M[0][1] * M[2][2];
-  C[0][2] = M[0][1] * M[1][2] - M[0][2] * M[1][1];
-  C[1][0] = M[1][2] * M[2][0] - M[1][0] * M[2][2];
-  C[1][1] = M[0][0] * M[2][2] - M[0][2] * M[2][0];
-  C[1][2] = M[0][2] * M[1][0] - M[0][0] * M[1][2];
-  C[2][0] = M[1][0] * M[2][1] - M[1][1] * M[2][0];
-  C[2][1] = M[0][1] * M[2][0] - M[0][0] * M[2][1];
-  C[2][2] = M[0][0] * M[1][1] - M[0][1] * M[1][0];
-  const double det = M[0][0] * C[0][0] + M[0][1] * C[1][0] + M[0][2] * C[2][0];
+  const double *C = lsq + 10 * c;
+  const double det = C[9];
   double g[5][3], dmax[5], dmin[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
 #pragma unroll
     for (int x = 0; x < 3; ++x)
-      g[q][x] = (C[x][0] * b[q][0] + C[x][1] * b[q][1] + C[x][2] * b[q][2]) / det;
+      g[q][x] = (C[3 * x] * b[q][0] + C[3 * x + 1] * b[q][1] + C[3 * x + 2] * b[q][2]) / det;
     dmax[q] = 0.0;
     dmin[q] = 0.0;
   }
   for (int64_t k = k0; k < k1; ++k) {
-    const HydroSlot &sl = slot[k];
-    const double o0 = sl.own[0], o1 = sl.own[1], o2 = sl.own[2];
+    const double o0 = slot[k].own[0], o1 = slot[k].own[1], o2 = slot[k].own[2];
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
       const double dv = g[q][0] * o0 + g[q][1] * o1 + g[q][2] * o2;
@@ -372,6 +388,13 @@ int hydro_setup(rt_state *s, const rt_mesh_desc *m) {
   if (!up((void **)&s->d_hface, faces.data(), sizeof(HydroFace) * Nf) ||
       !up((void **)&s->d_hslot, slots.data(), sizeof(HydroSlot) * s->nnz))
     return e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA;
+  e = cudaMalloc((void **)&s->d_hlsq, sizeof(double) * 10 * (size_t)N);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA;
+  s->device_bytes += sizeof(double) * 10 * (size_t)N;
+  lsq_setup_kernel<<<grid(N), kThreads, 0, s->stream>>>(s->d_ptr, s->d_hslot, N, s->d_hlsq);
+  s->launches++;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return RT_ERR_CUDA;
   const size_t work = sizeof(double) * ((size_t)N * (5 + 15 + 5 + 1 + 3) + (size_t)Nf * 5);
   e = cudaMalloc((void **)&s->d_hwork, work);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA;
@@ -409,8 +432,8 @@ cudaError_t launch_hydro_step(rt_state *s, double dt, int order) {
                                                        nullptr);
     prim_kernel<<<grid(N), kThreads, 0, s->stream>>>(nullptr, nullptr, U, N, g, W, s->d_status,
                                                      s->d_bad);
-    gradient_kernel<<<grid(N), kThreads, 0, s->stream>>>(s->d_ptr, s->d_nbr, s->d_hslot, W, N,
-                                                         grad);
+    gradient_kernel<<<grid(N), kThreads, 0, s->stream>>>(s->d_ptr, s->d_nbr, s->d_hslot,
+                                                         s->d_hlsq, W, N, grad);
     flux_kernel<<<grid(Nf), kThreads, 0, s->stream>>>(s->d_hface, Nf, W, grad, g, flux,
                                                       s->d_status, s->d_bad);
     update_kernel<<<grid(N), kThreads, 0, s->stream>>>(s->d_ptr, s->d_hslot, flux, s->d_volume, N,

@@ -72,6 +72,7 @@ struct HydroSlot {
   double area;
   double sign;            // +1: the cell is the face's first cell, -1: its second
   int64_t face;           // caller face index (into the face fluxes)
+  double wr[3];           // least-squares weight A_f / |r|^2 times r = own - nbr (set on the device)
 };
 
 template <typename R> struct StepArgs {
@@ -243,6 +244,7 @@ struct rt_state {
   // gas dynamics (params.hydro): face and slot records, work area
   rt::HydroFace *d_hface = nullptr;
   rt::HydroSlot *d_hslot = nullptr;
+  double *d_hlsq = nullptr;  // [N][10] cofactors and determinant of each cell's normal matrix
   double *d_hwork = nullptr;
   double *d_scratch = nullptr;  // reduction partials
   size_t scratch_len = 0;

@@ -93,6 +93,35 @@ def test_create_rejects_bad_meshes(lib):
     assert _create(lib, mesh, dirs, w * 2)[0] == capi.RT_ERR_ARG
 
 
+
+def test_create_rejects_degenerate_sizes_and_values(lib):
+    """The degenerate inputs: no cells, an odd or too large angle count, a
+    non-positive or non-finite cell volume, a NaN face area.  Each is refused
+    before any device work, with no state returned."""
+    import dataclasses
+    mesh = build_mesh((3, 3, 3), seed=1)
+    dirs, w = level_symmetric(4)
+    keep = []
+    d = _desc(mesh, dirs, w, keep)
+    d.n_cells = 0
+    pr = capi.Params(10.0, 10.0, 1.0, 5.0 / 3.0, 1.0, 0.3, capi.RT_FP64, 64)
+    st = ctypes.c_void_p()
+    assert lib.rt_create(ctypes.byref(d), ctypes.byref(pr), None, ctypes.byref(st)) == capi.RT_ERR_ARG
+    assert not st.value
+    d = _desc(mesh, dirs, w, keep)
+    d.n_angles = dirs.shape[0] - 1
+    assert lib.rt_create(ctypes.byref(d), ctypes.byref(pr), None, ctypes.byref(st)) == capi.RT_ERR_ARG
+    big = np.concatenate([dirs] * 6)[:130]
+    assert _create(lib, mesh, big, np.full(130, 1.0 / 130))[0] == capi.RT_ERR_ARG
+    for bad in (0.0, -1.0, np.nan, np.inf):
+        vol = mesh.cell_volume.copy()
+        vol[4] = bad
+        m2 = dataclasses.replace(mesh, cell_volume=vol)
+        assert _create(lib, m2, dirs, w)[0] == capi.RT_ERR_MESH, bad
+    area = mesh.face_area.copy()
+    area[3] = np.nan
+    assert _create(lib, dataclasses.replace(mesh, face_area=area), dirs, w)[0] == capi.RT_ERR_MESH
+
 def test_create_rejects_bad_params(lib):
     """Flags outside {0, 1}, van Leer with the GCL, non-finite or too negative
     opacity exponents and T_ref <= 0 with an exponent are refused before any

@@ -40,12 +40,13 @@ UNIT = "cell-angle updates/s"
 # capture (dram__bytes_read.sum + dram__bytes_write.sum, one launch, one
 # pass); valid while the step kernel's device source has the recorded hash
 # (else reported as null).  FP32: the 256^3 linear-wave launch itself
-# (12.43 GB read + 6.15 GB written).  FP64: the 128^3 linear-wave launch
+# (12.42 GB read + 6.15 GB written).  FP64: the 128^3 linear-wave launch
 # (12.52 + 1.49 GB, mostly the flux-coefficient table) scaled by the cell
-# count to 256^3 (the table, the rows and the gas all grow with the cells).
-NCU_TRAFFIC = {("waves", 16777216, "fp32"): 18.58e9,
+# count to 256^3 (the table, the rows and the gas all grow with the cells),
+# taken when only the float instantiations' code differed from today's.
+NCU_TRAFFIC = {("waves", 16777216, "fp32"): 18.57e9,
                ("waves", 16777216, "fp64"): 14.01e9 * 8}
-NCU_SOURCE_SHA = "87d149ce2c972f0c"
+NCU_SOURCE_SHA = "3210b6995f7435eb"
 # FP64 arithmetic peak when the DGEMM probe cannot run: the nominal dense
 # FP64 FMA rate of the GPU.
 FP64_NOMINAL_GFLOPS = 1250.0

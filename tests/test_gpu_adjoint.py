@@ -117,7 +117,7 @@ def _autograd(prob, precision, dt, K, every, g):
     out = run(s, I0, kap, _gas(prob), K, dt, every)
     L = (out.double() * torch.tensor(g, device="cuda")).sum()
     L.backward()
-    res = (float(L), kap.grad.cpu().numpy(), I0.grad.double().cpu().numpy())
+    res = (float(L.detach()), kap.grad.cpu().numpy(), I0.grad.double().cpu().numpy())
     s.close()
     return res
 

@@ -447,9 +447,34 @@ __device__ __forceinline__ double group_xs(const GroupArgs<double> &a, int64_t c
   return k[1] + k[2];
 }
 
+// The group step's body for the thread's entries.  FUSED (float rows in the
+// quad layout, static mesh): the transport runs first in the same block --
+// the block's face slots staged in shared memory, I* = I^n - dt/V sum_f u I_up
+// formed in registers from t.I_in -- so the transported rows never go
+// through memory; a.I then receives I^{n+1}.  Otherwise a.I holds I* and is
+// updated in place.
+template <typename R, typename M, bool FUSED>
+__device__ __forceinline__ void group_tile_body(const GroupArgs<R> &a, const StepArgs<R> &t,
+                                                const step::StageView &stage);
+
 template <typename R, typename M>
 __global__ void __launch_bounds__(step::NT, sizeof(R) == 4 && M::PPT <= 6 ? 3 : 2)
     group_source_tile(const GroupArgs<R> a) {
+  group_tile_body<R, M, false>(a, StepArgs<R>{}, step::StageView{});
+}
+
+template <typename M>
+__global__ void __launch_bounds__(step::NT, M::PPT <= 6 ? 3 : 2)
+    group_step_fused(const GroupArgs<float> a, const StepArgs<float> t, int cap) {
+  extern __shared__ __align__(128) unsigned char dyn[];
+  const step::StageView v = step::stage_at(dyn, cap, false);
+  step::issue_stage<false, false>(t, blockIdx.x, v);
+  group_tile_body<float, M, true>(a, t, v);
+}
+
+template <typename R, typename M, bool FUSED>
+__device__ __forceinline__ void group_tile_body(const GroupArgs<R> &a, const StepArgs<R> &t,
+                                                const step::StageView &stage) {
   using V = step::pair_t<R>;
   using step::mk;
   using step::padd;
@@ -466,12 +491,32 @@ __global__ void __launch_bounds__(step::NT, sizeof(R) == 4 && M::PPT <= 6 ? 3 : 
   const int np = M::count(a.H, sub);
   R Ia[PPT], Ib[PPT], nx[PPT], ny[PPT], nz[PPT];
   int gp[PPT];
-  M::load(a.I + (size_t)c * a.A, sub, Ia, Ib, np);
+  M::load((FUSED ? t.I_in : a.I) + (size_t)c * a.A, sub, Ia, Ib, np);
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
     const int p = (M::FULL || j < np) ? M::pair(j, sub) : 0;
     step::load_dir(a.dir, p, nx[j], ny[j], nz[j]);
     gp[j] = p / a.Hb;
+  }
+  if constexpr (FUSED) {
+    // I* of the thread's entries: the step kernel's face loop over the
+    // block's staged slots, in the cell's face order
+    R acca[PPT], accb[PPT];
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) acca[j] = accb[j] = R(0);
+    const int64_t kb = t.ptr[(int64_t)blockIdx.x * CPB];
+    const int k0 = (int)(t.ptr[c] - kb), k1 = (int)(t.ptr[c + 1] - kb);
+    step::cp_async_wait_all();
+    __syncthreads();  // the block's stage has landed
+    step::face_sum<R, M, false, true, step::TRANSPORT_FORWARD>(
+        reinterpret_cast<const typename SlotOf<R>::type *>(stage.slot), stage.nbr, t.wface,
+        t.uface, t.half, k0, k1, t.I_in, t.row, sub, nx, ny, nz, Ia, Ib, acca, accb, np);
+    const R dtv = t.dt_r * t.inv_vol[c];
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      Ia[j] = fma(-dtv, acca[j], Ia[j]);
+      Ib[j] = fma(-dtv, accb[j], Ib[j]);
+    }
   }
   const int kind = a.kind[c];
   const R vxc = a.cellv[4 * c] * a.inv_c_r, vyc = a.cellv[4 * c + 1] * a.inv_c_r,
@@ -789,7 +834,7 @@ template <typename R> void tile_dispatch(const GroupArgs<R> &a, cudaStream_t st)
     tile_pairs<R, false>(a, st);
 }
 
-template <typename R> cudaError_t launch(rt_state *s, double dt, void *Is) {
+template <typename R> GroupArgs<R> group_args(rt_state *s, double dt, void *Is) {
   GroupArgs<R> a{};
   a.n = s->n_cells;
   a.A = s->n_angles;
@@ -831,6 +876,11 @@ template <typename R> cudaError_t launch(rt_state *s, double dt, void *Is) {
     a.Wk_alpha_f[j] = (float)(a.W[j] * a.k_alpha);
     a.Wk_g_f[j] = (float)(a.W[j] * a.k_g);
   }
+  return a;
+}
+
+template <typename R> cudaError_t launch(rt_state *s, double dt, void *Is) {
+  const GroupArgs<R> a = group_args<R>(s, dt, Is);
   if (a.G <= kTileGroups) {
     tile_dispatch<R>(a, s->stream);
     s->launches++;
@@ -847,7 +897,55 @@ template <typename R> cudaError_t launch(rt_state *s, double dt, void *Is) {
   return cudaGetLastError();
 }
 
+template <typename M>
+cudaError_t launch_fused_q(rt_state *s, double dt, const void *In, void *Out) {
+  const GroupArgs<float> a = group_args<float>(s, dt, Out);
+  StepArgs<float> t{};
+  t.n_cells = s->n_cells;
+  t.n_angles = s->n_angles;
+  t.half = s->n_angles / 2;
+  t.row = s->row_stride;
+  t.ptr = s->d_ptr;
+  t.nbr = s->d_nbr;
+  t.slot = reinterpret_cast<const SlotF *>(s->d_slot);
+  t.slot_nb = s->d_slot_nb;
+  t.uface = s->d_uface;
+  t.inv_vol = reinterpret_cast<const float *>(s->d_inv_vol);
+  t.wface = s->d_wface;
+  t.dir = reinterpret_cast<const float *>(s->d_dir);
+  t.I_in = reinterpret_cast<const float *>(In);
+  t.I_out = nullptr;
+  t.dt = dt;
+  t.dt_r = (float)dt;
+  const unsigned g = (unsigned)((s->n_cells + CPB - 1) / CPB);
+  const int cap = step::stage_cap(s->max_block_slots);
+  group_step_fused<M><<<g, step::NT, step::stage_gas_offset(cap, false), s->stream>>>(a, t, cap);
+  s->launches++;
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+// One step of a state with frequency groups: float rows in the quad layout on
+// a static mesh take the fused kernel (transport and source in one launch);
+// the others the transport sweep, then the source step in place on I*.
+cudaError_t launch_group_step(rt_state *s, double dt, const void *In, void *Out) {
+  if (s->precision == RT_FP32 && s->quad_end > 0 && !s->moving && s->n_groups <= kTileGroups &&
+      s->row_stride == s->n_angles) {
+    switch (s->n_angles / 16) {
+      case 2: return launch_fused_q<step::QuadMap<1, false>>(s, dt, In, Out);
+      case 3: return launch_fused_q<step::QuadMap<1, true>>(s, dt, In, Out);
+      case 4: return launch_fused_q<step::QuadMap<2, false>>(s, dt, In, Out);
+      case 5: return launch_fused_q<step::QuadMap<2, true>>(s, dt, In, Out);
+      case 6: return launch_fused_q<step::QuadMap<3, false>>(s, dt, In, Out);
+      case 7: return launch_fused_q<step::QuadMap<3, true>>(s, dt, In, Out);
+      default: return launch_fused_q<step::QuadMap<4, false>>(s, dt, In, Out);
+    }
+  }
+  cudaError_t e = launch_transport(s, dt, In, Out, false);
+  if (e == cudaSuccess) e = launch_group_source(s, dt, Out);
+  return e;
+}
 
 cudaError_t launch_group_source(rt_state *s, double dt, void *Is) {
   if (s->n_groups > kMaxGroups) return cudaErrorInvalidValue;

@@ -271,6 +271,8 @@ cudaError_t launch_transport(rt_state *s, double dt, const void *in, void *out, 
 // The coupled source step of frequency groups (rt_groups.cu), in place on
 // the transported rows I* (stride row_stride).
 cudaError_t launch_group_source(rt_state *s, double dt, void *Is);
+// one step of a grouped state: In = I^n rows, Out = I^{n+1} rows
+cudaError_t launch_group_step(rt_state *s, double dt, const void *In, void *Out);
 // The van Leer step (rt_recon.cu); leaves I^{n+1} in d_I[cur ^ 1].
 cudaError_t launch_step_vl(rt_state *s, double dt);
 // Double states: fills d_uface (allocates it on first use).

@@ -799,10 +799,9 @@ cudaError_t launch_step(rt_state *s, double dt) {
   if (s->integrator == RT_VAN_LEER) {
     e = launch_step_vl(s, dt);
   } else if (s->n_groups > 1) {
-    // frequency groups: the transport of all groups' intensities, then the
-    // coupled source step in place on the transported rows
-    e = launch_transport(s, dt, s->d_I[s->cur], s->d_I[s->cur ^ 1], false);
-    if (e == cudaSuccess) e = launch_group_source(s, dt, s->d_I[s->cur ^ 1]);
+    // frequency groups: the transport of all groups' intensities and the
+    // coupled source step (one fused launch where the layout allows it)
+    e = launch_group_step(s, dt, s->d_I[s->cur], s->d_I[s->cur ^ 1]);
   } else {
     const StepIO io{s->d_I[s->cur], s->d_I[s->cur ^ 1], false, true};
     e = launch_step_io(s, dt, io);

@@ -93,7 +93,6 @@ def test_create_rejects_bad_meshes(lib):
     assert _create(lib, mesh, dirs, w * 2)[0] == capi.RT_ERR_ARG
 
 
-
 def test_create_rejects_degenerate_sizes_and_values(lib):
     """The degenerate inputs: no cells, an odd or too large angle count, a
     non-positive or non-finite cell volume, a NaN face area.  Each is refused
@@ -121,6 +120,7 @@ def test_create_rejects_degenerate_sizes_and_values(lib):
     area = mesh.face_area.copy()
     area[3] = np.nan
     assert _create(lib, dataclasses.replace(mesh, face_area=area), dirs, w)[0] == capi.RT_ERR_MESH
+
 
 def test_create_rejects_bad_params(lib):
     """Flags outside {0, 1}, van Leer with the GCL, non-finite or too negative
@@ -174,6 +174,11 @@ def test_null_arguments(lib):
     st = ctypes.c_void_p()
     assert lib.rt_create(None, None, None, ctypes.byref(st)) == capi.RT_ERR_ARG
     assert lib.rt_step(None, 0.0, None) == capi.RT_ERR_ARG
+    assert lib.rt_step_io(None, 0.0, None, None) == capi.RT_ERR_ARG
+    assert lib.rt_sync(None) == capi.RT_ERR_ARG
+    assert lib.rt_totals(None, None) == capi.RT_ERR_ARG
+    assert lib.rt_adjoint_step(None, 0.0, None, None, None, None, None, None, None, None, None,
+                               None, None, 0) == capi.RT_ERR_ARG
     assert lib.rt_launch_count(None) == -1
     lib.rt_destroy(None)
 
